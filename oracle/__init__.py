@@ -1,0 +1,112 @@
+"""CPU oracle for U = sign(T) of a real upper-triangular T.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg use it; the library never does.  It shares no code with the
+CUDA path.  The arithmetic lives in oracle.c (plain C, float64, no FMA
+contraction); this module only marshals numpy arrays.
+
+Matrices are numpy float64 arrays in column-major (Fortran) order, element
+(i, j) of an n x n matrix at offset i + j*n.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, BAD_ARG, ZERO_EIGENVALUE, NONFINITE = 0, 1, 2, 3
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        for name in ("oracle_sign_tri", "oracle_sign_spectral"):
+            f = getattr(L, name)
+            f.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int]
+            f.restype = ctypes.c_int
+        L.oracle_sign_tri_count.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_longlong)]
+        L.oracle_sign_tri_count.restype = ctypes.c_int
+        L.oracle_sign_tri_antidiag.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int,
+                                               ctypes.c_int]
+        L.oracle_sign_tri_antidiag.restype = ctypes.c_int
+        L.oracle_max_threads.argtypes = []
+        L.oracle_max_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class OracleError(RuntimeError):
+    def __init__(self, status):
+        super().__init__("oracle status %d" % status)
+        self.status = status
+
+
+def _colmajor(T):
+    T = np.asarray(T, dtype=np.float64)
+    if T.ndim != 2 or T.shape[0] != T.shape[1]:
+        raise ValueError("T must be square")
+    return np.asfortranarray(T)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def sign_tri(T, *, threads=None, schedule="paper"):
+    """sign(T) by Algorithm 3.  schedule='paper' runs the printed loop order;
+    'antidiag' runs the anti-diagonal order (OpenMP, bit-identical)."""
+    T = _colmajor(T)
+    n = T.shape[0]
+    U = np.zeros((n, n), dtype=np.float64, order="F")
+    ld = max(n, 1)
+    if schedule == "paper":
+        st = lib().oracle_sign_tri(n, _ptr(T), ld, _ptr(U), ld)
+    elif schedule == "antidiag":
+        st = lib().oracle_sign_tri_antidiag(n, _ptr(T), ld, _ptr(U), ld, int(threads or 0))
+    else:
+        raise ValueError(schedule)
+    if st != OK:
+        raise OracleError(st)
+    return U
+
+
+def sign_tri_status(T):
+    """Status code of Algorithm 3 on T (0 when it succeeds)."""
+    T = _colmajor(T)
+    n = T.shape[0]
+    U = np.zeros((n, n), dtype=np.float64, order="F")
+    return lib().oracle_sign_tri(n, _ptr(T), max(n, 1), _ptr(U), max(n, 1))
+
+
+def useful_flops(T):
+    """Floating-point operations executed by the inner sums of Algorithm 3."""
+    T = _colmajor(T)
+    n = T.shape[0]
+    U = np.zeros((n, n), dtype=np.float64, order="F")
+    c = ctypes.c_longlong(0)
+    st = lib().oracle_sign_tri_count(n, _ptr(T), max(n, 1), _ptr(U), max(n, 1), ctypes.byref(c))
+    if st != OK:
+        raise OracleError(st)
+    return int(c.value)
+
+
+def sign_spectral(T):
+    """Brute force sign(T) = Z sign(D) Z^{-1} in long double (n <= 64)."""
+    T = _colmajor(T)
+    n = T.shape[0]
+    U = np.zeros((n, n), dtype=np.float64, order="F")
+    st = lib().oracle_sign_spectral(n, _ptr(T), max(n, 1), _ptr(U), max(n, 1))
+    if st != OK:
+        raise OracleError(st)
+    return U
+
+
+def max_threads():
+    return int(lib().oracle_max_threads())

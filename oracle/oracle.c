@@ -1,0 +1,237 @@
+/*
+ * oracle.c -- the CPU oracle for U = sign(T), T real upper triangular.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library path links, loads or calls
+ * this file; only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark do.  It shares no code, header, table or helper with the CUDA
+ * library.
+ *
+ * Storage: column-major float64, element (i,j) at M[i + j*ld], 0-based.
+ * Compile with -ffp-contract=off (the build script does) so that every a*b and
+ * every + below is one separately rounded IEEE operation: the rounding of the
+ * oracle is then fixed by the order written here.
+ *
+ * Functions
+ *   oracle_sign_tri        Parlett-Higham substitution, Algorithm 3 of the
+ *                          paper (Higham's Algorithm 5.5), loops in the order
+ *                          printed there: j = 2..n outer, i = j-1..1 inner.
+ *   oracle_sign_tri_count  Same, and counts the floating-point operations that
+ *                          the inner sums execute (the useful-flop count).
+ *   oracle_sign_tri_antidiag
+ *                          Same per-entry arithmetic as oracle_sign_tri, but
+ *                          entries are visited by anti-diagonal d = j-i, whose
+ *                          entries depend only on entries with smaller d; the
+ *                          entries of one anti-diagonal may run in parallel
+ *                          (OpenMP).  The result is bit-identical to
+ *                          oracle_sign_tri (a test checks this).
+ *   oracle_sign_spectral   Brute force from the definition in Section 1:
+ *                          sign(T) = Z sign(D) Z^{-1}, with Z the (unit upper
+ *                          triangular) eigenvector matrix of T, in long double.
+ *                          For small n only.
+ *
+ * Status codes: 0 ok, 1 bad argument, 2 a diagonal entry is zero (sign(0) is
+ * undefined, Section 1), 3 a diagonal entry is NaN or infinite.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_OK 0
+#define ORACLE_BAD_ARG 1
+#define ORACLE_ZERO_EIGENVALUE 2
+#define ORACLE_NONFINITE 3
+
+#define AT(M, ld, i, j) ((M)[(size_t)(i) + (size_t)(j) * (size_t)(ld)])
+
+/* Scalar sign of Section 1 for a real nonzero argument. */
+static double scalar_sign(double x) { return x > 0.0 ? 1.0 : -1.0; }
+
+static int check_args(int n, const double *T, int ldt, const double *U, int ldu)
+{
+    if (n < 0 || ldt < (n > 1 ? n : 1) || ldu < (n > 1 ? n : 1)) return ORACLE_BAD_ARG;
+    if (n > 0 && (T == NULL || U == NULL)) return ORACLE_BAD_ARG;
+    for (int i = 0; i < n; i++) {
+        double t = AT(T, ldt, i, i);
+        if (!isfinite(t)) return ORACLE_NONFINITE;
+        if (t == 0.0) return ORACLE_ZERO_EIGENVALUE;
+    }
+    return ORACLE_OK;
+}
+
+/*
+ * Algorithm 3 (Parlett-Higham).  For i < j:
+ *   if u_ii + u_jj = 0 (signs differ), from TU = UT (Eq. 1):
+ *       u_ij = t_ij (u_ii - u_jj)/(t_ii - t_jj)
+ *              + [sum_{k=i+1}^{j-1} (u_ik t_kj - t_ik u_kj)] / (t_ii - t_jj)
+ *   else, from U^2 = I (Eq. 2):
+ *       u_ij = -[sum_{k=i+1}^{j-1} u_ik u_kj] / (u_ii + u_jj)
+ * The strictly lower triangle of U is set to zero.
+ * inner_flops, when not NULL, receives the number of floating-point
+ * operations executed by the inner sums: 2 per term of the U^2 = I sum
+ * (one multiply, one add) and 4 per term of the TU = UT sum (two multiplies,
+ * one subtract, one add).
+ */
+int oracle_sign_tri_count(int n, const double *T, int ldt, double *U, int ldu,
+                          long long *inner_flops)
+{
+    int st = check_args(n, T, ldt, U, ldu);
+    if (st != ORACLE_OK) return st;
+    long long flops = 0;
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) AT(U, ldu, i, j) = 0.0;
+    for (int i = 0; i < n; i++) AT(U, ldu, i, i) = scalar_sign(AT(T, ldt, i, i));
+    for (int j = 1; j < n; j++) {
+        for (int i = j - 1; i >= 0; i--) {
+            double uii = AT(U, ldu, i, i), ujj = AT(U, ldu, j, j);
+            if (uii + ujj == 0.0) {
+                double s = 0.0;
+                for (int k = i + 1; k <= j - 1; k++) {
+                    double a = AT(U, ldu, i, k) * AT(T, ldt, k, j);
+                    double b = AT(T, ldt, i, k) * AT(U, ldu, k, j);
+                    s = s + (a - b);
+                }
+                flops += 4LL * (j - i - 1);
+                double den = AT(T, ldt, i, i) - AT(T, ldt, j, j);
+                AT(U, ldu, i, j) = AT(T, ldt, i, j) * (uii - ujj) / den + s / den;
+            } else {
+                double s = 0.0;
+                for (int k = i + 1; k <= j - 1; k++) s = s + AT(U, ldu, i, k) * AT(U, ldu, k, j);
+                flops += 2LL * (j - i - 1);
+                AT(U, ldu, i, j) = -s / (uii + ujj);
+            }
+        }
+    }
+    if (inner_flops) *inner_flops = flops;
+    return ORACLE_OK;
+}
+
+int oracle_sign_tri(int n, const double *T, int ldt, double *U, int ldu)
+{
+    return oracle_sign_tri_count(n, T, ldt, U, ldu, NULL);
+}
+
+/*
+ * The same entries, visited by anti-diagonal d = j - i = 1..n-1.  Entry (i,j)
+ * reads u_ik (k < j, anti-diagonal k-i < d) and u_kj (k > i, anti-diagonal
+ * j-k < d), so every entry of anti-diagonal d can be computed once all
+ * smaller anti-diagonals are done.  Row-major copies UR, TR give contiguous
+ * access to the rows u_i*, t_i*; they hold the same values as U and T, and
+ * each entry performs exactly the operations of oracle_sign_tri in the same
+ * order, so the results are bit-identical.
+ * nthreads <= 0 uses the OpenMP default.
+ */
+int oracle_sign_tri_antidiag(int n, const double *T, int ldt, double *U, int ldu, int nthreads)
+{
+    int st = check_args(n, T, ldt, U, ldu);
+    if (st != ORACLE_OK) return st;
+    size_t nn = (size_t)n * (size_t)n;
+    double *UR = (double *)calloc(nn > 0 ? nn : 1, sizeof(double));
+    double *TR = (double *)calloc(nn > 0 ? nn : 1, sizeof(double));
+    if (!UR || !TR) { free(UR); free(TR); return ORACLE_BAD_ARG; }
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+            AT(U, ldu, i, j) = 0.0;
+            TR[(size_t)i * n + j] = (i <= j) ? AT(T, ldt, i, j) : 0.0;
+        }
+    for (int i = 0; i < n; i++) {
+        double u = scalar_sign(AT(T, ldt, i, i));
+        AT(U, ldu, i, i) = u;
+        UR[(size_t)i * n + i] = u;
+    }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    for (int d = 1; d < n; d++) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+        for (int i = 0; i < n - d; i++) {
+            int j = i + d;
+            const double *urow = UR + (size_t)i * n;
+            const double *trow = TR + (size_t)i * n;
+            const double *ucol = &AT(U, ldu, 0, j);
+            const double *tcol = &AT(T, ldt, 0, j);
+            double uii = urow[i], ujj = UR[(size_t)j * n + j];
+            double uij;
+            if (uii + ujj == 0.0) {
+                double s = 0.0;
+                for (int k = i + 1; k <= j - 1; k++) {
+                    double a = urow[k] * tcol[k];
+                    double b = trow[k] * ucol[k];
+                    s = s + (a - b);
+                }
+                double den = trow[i] - TR[(size_t)j * n + j];
+                uij = tcol[i] * (uii - ujj) / den + s / den;
+            } else {
+                double s = 0.0;
+                for (int k = i + 1; k <= j - 1; k++) s = s + urow[k] * ucol[k];
+                uij = -s / (uii + ujj);
+            }
+            AT(U, ldu, i, j) = uij;
+            UR[(size_t)i * n + j] = uij;
+        }
+    }
+    free(UR);
+    free(TR);
+    return ORACLE_OK;
+}
+
+/*
+ * Brute force from the spectral definition (Section 1): for T with distinct
+ * diagonal entries, T = Z D Z^{-1} with D = diag(t_ii) and Z unit upper
+ * triangular, column j solving (T - t_jj I) z = 0 with z_jj = 1:
+ *     z_ij = [sum_{k=i+1}^{j} t_ik z_kj] / (t_jj - t_ii),   i = j-1, ..., 1.
+ * W = Z^{-1} is unit upper triangular, from Z W = I column by column:
+ *     w_ij = -sum_{k=i+1}^{j} z_ik w_kj.
+ * Then sign(T) = Z diag(sign(t_ii)) W.  All in long double.  Requires
+ * distinct diagonal entries; n <= 64.
+ */
+int oracle_sign_spectral(int n, const double *T, int ldt, double *U, int ldu)
+{
+    int st = check_args(n, T, ldt, U, ldu);
+    if (st != ORACLE_OK) return st;
+    if (n > 64) return ORACLE_BAD_ARG;
+    long double Z[64][64], W[64][64];
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) { Z[i][j] = 0.0L; W[i][j] = 0.0L; }
+    for (int j = 0; j < n; j++) {
+        Z[j][j] = 1.0L;
+        for (int i = j - 1; i >= 0; i--) {
+            long double s = 0.0L;
+            for (int k = i + 1; k <= j; k++) s += (long double)AT(T, ldt, i, k) * Z[k][j];
+            long double den = (long double)AT(T, ldt, j, j) - (long double)AT(T, ldt, i, i);
+            if (den == 0.0L) return ORACLE_BAD_ARG;
+            Z[i][j] = s / den;
+        }
+    }
+    for (int j = 0; j < n; j++) {
+        W[j][j] = 1.0L;
+        for (int i = j - 1; i >= 0; i--) {
+            long double s = 0.0L;
+            for (int k = i + 1; k <= j; k++) s += Z[i][k] * W[k][j];
+            W[i][j] = -s;
+        }
+    }
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+            long double s = 0.0L;
+            for (int k = i; k <= j; k++)
+                s += Z[i][k] * (long double)scalar_sign(AT(T, ldt, k, k)) * W[k][j];
+            AT(U, ldu, i, j) = (i <= j) ? (double)s : 0.0;
+        }
+    return ORACLE_OK;
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,77 @@
+"""Seeded synthetic inputs: dense real upper-triangular T with a prescribed
+inertia (number of negative diagonal entries).
+
+This module serves both the CUDA path and the oracle.  It holds none of the
+method's arithmetic: it only draws random numbers.
+
+Recipe (the paper's forced-inertia workload, Section 6, with a Gaussian
+strictly-upper part in place of a Schur form):
+  1. the sign pattern: exactly n_neg = floor(p*n + 0.5) negative diagonal
+     entries, at positions drawn uniformly without replacement
+     (order="random"), or all positives first (order="sorted");
+  2. |t_ii| ~ U[0.5, 2], i = 1..n;
+  3. strictly-upper t_ij ~ N(0, 1/n), drawn column by column (j outer,
+     i = 1..j-1 inner);
+  the strictly lower triangle is zero.
+Matrices are numpy float64 arrays in column-major (Fortran) order.
+"""
+import math
+
+import numpy as np
+
+
+def n_negative(n: int, p: float) -> int:
+    return int(math.floor(p * n + 0.5))
+
+
+def sign_pattern(rng, n: int, n_neg: int, order: str) -> np.ndarray:
+    s = np.ones(n)
+    if n_neg <= 0:
+        return s
+    if order == "random":
+        s[rng.permutation(n)[:n_neg]] = -1.0
+    elif order == "sorted":
+        s[n - n_neg:] = -1.0
+    else:
+        raise ValueError("order must be 'random' or 'sorted'")
+    return s
+
+
+def make_T(n: int, p: float = 0.5, seed: int = 0, order: str = "random",
+           n_neg: int = None) -> np.ndarray:
+    """Upper-triangular T (column-major float64) from the recipe above."""
+    if n < 0:
+        raise ValueError("n must be >= 0")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = n_negative(n, p) if n_neg is None else int(n_neg)
+    s = sign_pattern(rng, n, k, order)
+    mags = rng.uniform(0.5, 2.0, size=n)
+    T = np.zeros((n, n), dtype=np.float64, order="F")
+    if n == 0:
+        return T
+    m = n * (n - 1) // 2
+    off = rng.standard_normal(m) * (1.0 / math.sqrt(n))
+    o = 0
+    for j in range(1, n):
+        T[:j, j] = off[o:o + j]
+        o += j
+    T[np.arange(n), np.arange(n)] = s * mags
+    return T
+
+
+def batch_sizes(count: int, seed: int = 0, n_min: int = 32, n_max: int = 2048):
+    """Sizes n_i = round(exp(U[ln n_min, ln n_max])) and inertias p_i ~ U[0,1]
+    of a batch of independent problems."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ln = rng.uniform(math.log(n_min), math.log(n_max), size=count)
+    ns = np.clip(np.floor(np.exp(ln) + 0.5).astype(np.int64), n_min, n_max)
+    ps = rng.uniform(0.0, 1.0, size=count)
+    return [int(x) for x in ns], [float(x) for x in ps]
+
+
+def make_batch(count: int, seed: int = 0, n_min: int = 32, n_max: int = 2048):
+    """A batch of independent problems: list of (T_i, seed_i), T_i from make_T
+    with n_i, p_i from batch_sizes and random diagonal order."""
+    ns, ps = batch_sizes(count, seed, n_min, n_max)
+    return [make_T(n, p, seed=seed * 1000003 + i + 1, order="random")
+            for i, (n, p) in enumerate(zip(ns, ps))]

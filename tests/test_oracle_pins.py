@@ -1,0 +1,189 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics,
+independent of the oracle's own code:
+
+* hand-worked small cases (tests/golden/sign_small.txt, Algorithm 3 and the
+  2x2 closed form u_12 = t_12 (u_11 - u_22)/(t_11 - t_22));
+* the spectral definition sign(A) = Z sign(D) Z^{-1} (Section 1), by the
+  oracle's long-double brute force AND by numpy's eigendecomposition;
+* scipy.linalg.signm (a library routine for the same function);
+* the Newton iteration X <- (X + X^{-1})/2, a textbook route to sign(A);
+* the Parlett-Sylvester identity for a sign-sorted diagonal (Section 2):
+  U = [I X; 0 -I] with T11 X - X T22 = 2 T12, by scipy's Sylvester solver;
+* invariants UT = TU, U^2 = I, trace U = n_+ - n_- (Sections 1-2);
+* special cases: all t_ii > 0 gives I, all < 0 gives -I, diagonal T gives
+  sign(D), all exactly (Section 3);
+* the principal-window property: u_ij depends only on T[i..j, i..j]
+  (Algorithm 3's index ranges), so the oracle on a window equals the full
+  oracle there bit for bit;
+* the flop count of Algorithm 3's inner sums in closed form (Section 3).
+A dropped term, a wrong sign, a shifted sum index or a transposed operand in
+the oracle fails at least the brute-force, Newton, signm and invariant pins.
+"""
+import fractions
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1607_06303_gb300.inputs import make_T
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sign_small.txt")
+
+
+def _parse_golden():
+    cases, lines = [], []
+    with open(GOLDEN) as f:
+        for raw in f:
+            s = raw.split("#")[0].strip()
+            if s:
+                lines.append(s)
+    i = 0
+    while i < len(lines):
+        n = int(lines[i]); i += 1
+        T = [[float(fractions.Fraction(x)) for x in lines[i + r].split()] for r in range(n)]; i += n
+        U = [[float(fractions.Fraction(x)) for x in lines[i + r].split()] for r in range(n)]; i += n
+        cases.append((np.array(T), np.array(U)))
+    return cases
+
+
+def relerr(A, B):
+    return np.linalg.norm(A - B) / max(np.linalg.norm(B), 1e-300)
+
+
+def test_golden_hand_cases(oracle_mod):
+    cases = _parse_golden()
+    assert len(cases) == 5
+    for T, U in cases:
+        got = oracle_mod.sign_tri(T)
+        np.testing.assert_allclose(got, U, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_2x2_closed_form(oracle_mod, seed):
+    rng = np.random.default_rng(100 + seed)
+    a, c = rng.uniform(0.5, 2, 2) * rng.choice([-1, 1], 2)
+    b = rng.standard_normal()
+    U = oracle_mod.sign_tri(np.array([[a, b], [0, c]]))
+    sa, sc = np.sign(a), np.sign(c)
+    expect = b * (sa - sc) / (a - c)
+    assert U[0, 0] == sa and U[1, 1] == sc and U[1, 0] == 0.0
+    assert abs(U[0, 1] - expect) <= 1e-15 * max(1, abs(expect))
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 7, 9, 12])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_brute_force_spectral(oracle_mod, n, seed):
+    for p in (0.5, 0.25):
+        T = make_T(n, p, seed=seed)
+        U = oracle_mod.sign_tri(T)
+        Ub = oracle_mod.sign_spectral(T)
+        assert relerr(U, Ub) < 1e-10
+        # numpy eigendecomposition: an implementation that shares nothing
+        w, V = np.linalg.eig(T)
+        Ue = (V * np.sign(w.real)) @ np.linalg.inv(V)
+        assert relerr(U, Ue.real) < 1e-9
+
+
+@pytest.mark.parametrize("n,p,order", [(40, 0.5, "random"), (80, 0.3, "random"), (100, 0.5, "sorted")])
+def test_scipy_signm(oracle_mod, n, p, order):
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    T = make_T(n, p, seed=7, order=order)
+    U = oracle_mod.sign_tri(T)
+    Us = scipy_linalg.signm(T)
+    assert relerr(U, Us) < 1e-9
+
+
+def test_newton_iteration(oracle_mod):
+    # X_{k+1} = (X_k + X_k^{-1})/2 converges quadratically to sign(A)
+    n = 200
+    T = make_T(n, 0.5, seed=3)
+    X = T.copy()
+    for _ in range(60):
+        Xn = 0.5 * (X + np.linalg.inv(X))
+        if np.linalg.norm(Xn - X) <= 1e-15 * np.linalg.norm(Xn):
+            X = Xn
+            break
+        X = Xn
+    U = oracle_mod.sign_tri(T)
+    assert relerr(U, X) < 1e-11
+
+
+@pytest.mark.parametrize("p", [0.1, 0.5])
+def test_sylvester_sorted(oracle_mod, p):
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    n = 150
+    T = make_T(n, p, seed=4, order="sorted")
+    npos = int((np.diag(T) > 0).sum())
+    T11, T12, T22 = T[:npos, :npos], T[:npos, npos:], T[npos:, npos:]
+    # T11 X - X T22 = 2 T12  <=>  T11 X + X (-T22) = 2 T12
+    X = scipy_linalg.solve_sylvester(T11, -T22, 2 * T12)
+    U = oracle_mod.sign_tri(T)
+    np.testing.assert_array_equal(U[:npos, :npos], np.eye(npos))
+    np.testing.assert_array_equal(U[npos:, npos:], -np.eye(n - npos))
+    assert relerr(U[:npos, npos:], X) < 1e-11
+
+
+@pytest.mark.parametrize("n,p,seed", [(300, 0.5, 0), (257, 0.1, 1), (333, 0.9, 2)])
+def test_invariants(oracle_mod, n, p, seed):
+    T = make_T(n, p, seed=seed)
+    U = oracle_mod.sign_tri(T)
+    I = np.eye(n)
+    nU, nT = np.linalg.norm(U), np.linalg.norm(T)
+    assert np.linalg.norm(U @ U - I) <= 1e-12 * nU ** 2
+    assert np.linalg.norm(U @ T - T @ U) <= 1e-12 * nT * nU
+    npos = int((np.diag(T) > 0).sum())
+    assert np.trace(U) == npos - (n - npos)
+    assert np.all(np.tril(U, -1) == 0)
+    assert np.all(np.diag(U) == np.sign(np.diag(T)))
+
+
+def test_trivial_inertia_and_diagonal(oracle_mod):
+    n = 50
+    T = make_T(n, 0.0, seed=5)
+    np.testing.assert_array_equal(oracle_mod.sign_tri(T), np.eye(n))
+    Tn = make_T(n, 1.0, seed=5)
+    np.testing.assert_array_equal(oracle_mod.sign_tri(Tn), -np.eye(n))
+    D = np.diag(np.diag(make_T(n, 0.5, seed=6)))
+    np.testing.assert_array_equal(oracle_mod.sign_tri(D), np.diag(np.sign(np.diag(D))))
+
+
+def test_window_property_bitexact(oracle_mod):
+    n = 120
+    T = make_T(n, 0.5, seed=8)
+    U = oracle_mod.sign_tri(T)
+    for a, b in [(0, 50), (17, 90), (70, 120), (33, 34)]:
+        Uw = oracle_mod.sign_tri(T[a:b, a:b])
+        np.testing.assert_array_equal(Uw, U[a:b, a:b])
+
+
+def test_antidiag_schedule_bitexact(oracle_mod):
+    for n, p in [(257, 0.5), (130, 0.2)]:
+        T = make_T(n, p, seed=9)
+        U1 = oracle_mod.sign_tri(T, schedule="paper")
+        U2 = oracle_mod.sign_tri(T, schedule="antidiag", threads=4)
+        np.testing.assert_array_equal(U1, U2)
+
+
+def test_status_codes(oracle_mod):
+    T = make_T(6, 0.5, seed=1)
+    T[3, 3] = 0.0
+    assert oracle_mod.sign_tri_status(T) == oracle_mod.ZERO_EIGENVALUE
+    T[3, 3] = np.nan
+    assert oracle_mod.sign_tri_status(T) == oracle_mod.NONFINITE
+    T[3, 3] = np.inf
+    assert oracle_mod.sign_tri_status(T) == oracle_mod.NONFINITE
+    assert oracle_mod.sign_tri_status(np.zeros((0, 0))) == oracle_mod.OK
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 10, 37])
+def test_flop_count_closed_forms(oracle_mod, n):
+    # all signs equal: every term uses U^2 = I (2 flops): 2 * C(n,3)
+    T = make_T(n, 0.0, seed=2)
+    assert oracle_mod.useful_flops(T) == 2 * math.comb(n, 3)
+    # alternating signs: pairs at odd distance differ (4 flops per term),
+    # pairs at even distance agree (2 flops per term)
+    d = np.array([(1.0 if i % 2 == 0 else -1.0) for i in range(n)])
+    Ta = np.diag(d) + np.triu(np.ones((n, n)), 1)
+    expect = sum((n - g) * (g - 1) * (4 if g % 2 else 2) for g in range(1, n))
+    assert oracle_mod.useful_flops(Ta) == expect
