@@ -1,0 +1,131 @@
+/*
+ * signtri.h -- C ABI of libsigntri.so: U = sign(T) for a dense real upper
+ * triangular matrix T on one GB300 (sm_103a).
+ *
+ * The operation (Stotland, Schwartz, Toledo, "High-Performance Algorithms
+ * for Computing the Sign Function of Triangular Matrices", Section 1 and
+ * Section 2): for T upper triangular with no zero diagonal entry, U = sign(T)
+ * is the upper triangular matrix with u_ii = sign(t_ii), UT = TU and U^2 = I.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are float64, column-major: element (i,j) (0-based) of a matrix
+ *     M with leading dimension ld is M[i + j*ld].  ld >= max(1, n).
+ *   - Pointers named T, U are DEVICE pointers unless the name says _host.
+ *     They are owned by the caller.  T and U must not overlap.
+ *   - Only the upper triangle of T (i <= j) is read.  All of the n x n part of
+ *     U is written; its strictly lower triangle is set to 0.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; see each call for the points where
+ *     the host waits.
+ *   - Errors are returned as signtri_status; nothing is thrown.  On any error
+ *     other than SIGNTRI_ERR_CUDA the contents of U are unspecified but no
+ *     memory outside U and the library workspace is written.
+ *   - The library keeps one workspace per device (grown on demand with
+ *     cudaMalloc, or set by signtri_set_workspace).  Calls that share a
+ *     workspace must not run concurrently: issue them from one host thread,
+ *     or on one stream, at a time.
+ */
+#ifndef SIGNTRI_H
+#define SIGNTRI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    /* Choose Parlett-Higham or Parlett-Sylvester per input from the
+       work estimates of Section 3 (inertia and swap count). */
+    SIGNTRI_AUTO = 0,
+    /* Recursive Parlett-Higham (Algorithms 3-6), float64 throughout. */
+    SIGNTRI_PH_FP64 = 1,
+    /* Parlett-Sylvester for the sign function (Section 2, Section 3,
+       Section 5.1): reorder by sign with adjacent Givens swaps, solve
+       T11 X - X T22 = 2 T12, transform back. */
+    SIGNTRI_PS_FP64 = 2,
+    /* Parlett-Higham with TF32 tensor-core block updates, then float64
+       refinement of both defining equations. */
+    SIGNTRI_PH_MIXED_TF32 = 3,
+    /* Parlett-Higham with BF16 tensor-core block updates, then float64
+       refinement of both defining equations. */
+    SIGNTRI_PH_MIXED_BF16 = 4
+} signtri_variant;
+
+typedef enum {
+    SIGNTRI_OK = 0,
+    SIGNTRI_ERR_BAD_ARG = 1,          /* n < 0, ld too small, NULL pointer, bad variant */
+    SIGNTRI_ERR_ZERO_EIGENVALUE = 2,  /* some t_ii == 0: sign(0) is undefined (Section 1) */
+    SIGNTRI_ERR_NONFINITE = 3,        /* some t_ii is NaN or infinite */
+    SIGNTRI_ERR_NO_CONVERGENCE = 4,   /* refinement did not reach the tolerance */
+    SIGNTRI_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up */
+    SIGNTRI_ERR_CUDA = 6,             /* a CUDA runtime call or launch failed */
+    SIGNTRI_ERR_NO_WORKSPACE = 7,     /* workspace could not be allocated / too small */
+    SIGNTRI_ERR_UNSUPPORTED = 8       /* option not available in this build */
+} signtri_status;
+
+/* What the last sign_tri call on the calling host thread did. */
+typedef struct {
+    int variant;            /* signtri_variant actually run */
+    int n;                  /* problem size */
+    int n_pos, n_neg;       /* inertia of T: counts of t_ii > 0 and t_ii < 0 */
+    long long swaps;        /* #{i<j : t_ii < 0 < t_jj}: adjacent swaps that
+                               group positives first (Section 3) */
+    double work_ph;         /* Section 3 flop estimate, Parlett-Higham */
+    double work_ps;         /* Section 3 flop estimate, Parlett-Sylvester */
+    int cutoff;             /* leaf (block) size used by Parlett-Higham */
+    int refine_steps;       /* refinement steps taken (mixed variants) */
+    double resid_commute;   /* ||TU-UT||_F / (||T||_F ||U||_F) after the last step */
+    double resid_involution;/* ||U^2-I||_F / ||U||_F^2 after the last step */
+    int bad_index;          /* first offending diagonal index on ZERO/NONFINITE, else -1 */
+} signtri_info;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *signtri_status_string(signtri_status s);
+
+/* Bytes of device workspace sign_tri needs for size n and variant v with the
+   current cutoff (0 when none).  Returns 0 for invalid arguments. */
+size_t signtri_workspace_bytes(int n, signtri_variant v);
+
+/* Use caller-owned device memory [dev_ptr, dev_ptr+bytes) as the workspace of
+   the current device from now on (dev_ptr 256-byte aligned).  dev_ptr == NULL
+   returns to library-owned workspace.  The library never frees caller
+   memory.  A call whose need exceeds `bytes` fails with
+   SIGNTRI_ERR_NO_WORKSPACE. */
+signtri_status signtri_set_workspace(void *dev_ptr, size_t bytes);
+
+/* Leaf (recursion cutoff) size b of Parlett-Higham: the order of the diagonal
+   and off-diagonal blocks solved element by element (Section 6 uses 16).
+   b in {16, 32, 64}; 0 restores the default.  Process-wide setting. */
+signtri_status signtri_set_cutoff(int b);
+
+/* U = sign(T).  T, U device pointers (see conventions).  Enqueued on
+   `stream`; the host waits once, after the inertia scan, to read three
+   integers (n_pos, n_neg, swaps) and the error flags, then enqueues the
+   chosen variant and returns without waiting for it.
+   n == 0 is a no-op returning SIGNTRI_OK.  n == 1 writes sign(t_11).
+   If all t_ii > 0 (all < 0) U = I (U = -I) exactly (Section 3). */
+signtri_status sign_tri(int n, const double *T, int ldt, double *U, int ldu,
+                        signtri_variant v, void *stream);
+
+/* Same as sign_tri, with T_host and U_host in host memory (pinned memory
+   gives full copy bandwidth).  Copies T to the device, computes, copies U
+   back, and returns after U_host is written (synchronous). */
+signtri_status sign_tri_host(int n, const double *T_host, int ldt, double *U_host, int ldu,
+                             signtri_variant v, void *stream);
+
+/* Inertia scan alone (Section 3): counts of positive and negative diagonal
+   entries and the number of adjacent swaps that group positives first.
+   Synchronous on `stream`.  Any output pointer may be NULL. */
+signtri_status signtri_inertia(int n, const double *T, int ldt, int *n_pos, int *n_neg,
+                               long long *swaps, void *stream);
+
+/* Copy of the record of the last sign_tri / sign_tri_host call made by the
+   calling host thread. */
+signtri_status signtri_get_info(signtri_info *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIGNTRI_H */

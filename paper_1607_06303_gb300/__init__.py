@@ -1,0 +1,9 @@
+"""GB300 (sm_103a) implementation of U = sign(T) for dense real upper
+triangular T: recursive Parlett-Higham and Parlett-Sylvester (Stotland,
+Schwartz, Toledo).  The computation lives in the CUDA library
+_lib/libsigntri.so behind the C ABI of include/signtri.h; `signtri` is its
+ctypes binding.
+"""
+from .signtri import (Info, SignTriError, Status, Variant, load, sign, sign_tri, sign_tri_host,  # noqa: F401
+                      signtri_get_info, signtri_inertia, signtri_set_cutoff, signtri_set_workspace,
+                      signtri_status_string, signtri_workspace_bytes, to_device, to_numpy)

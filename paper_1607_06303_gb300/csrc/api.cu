@@ -1,0 +1,297 @@
+// api.cu -- the extern "C" entry points of libsigntri.so (include/signtri.h).
+//
+// Host side of sign_tri: argument checks, the inertia scan (the one point
+// where the host waits), the variant choice from the Section 3 work
+// estimates, workspace management, and dispatch to the variant's kernels.
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "internal.cuh"
+
+using namespace signtri;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+constexpr int kDefaultCutoff = 64;
+
+struct DeviceState {
+    void *lib_ptr = nullptr;       // library-owned workspace (cudaMalloc)
+    size_t lib_bytes = 0;
+    void *user_ptr = nullptr;      // caller-owned workspace, if set
+    size_t user_bytes = 0;
+    ScanResult *scan_dev = nullptr;
+    ScanResult *scan_host = nullptr;   // pinned
+    double *stage_T = nullptr;     // device staging for sign_tri_host
+    double *stage_U = nullptr;
+    size_t stage_elems = 0;
+};
+
+std::mutex g_mu;
+DeviceState g_dev[kMaxDevices];
+int g_cutoff = kDefaultCutoff;
+thread_local signtri_info g_info;
+
+bool valid_variant(int v) { return v >= SIGNTRI_AUTO && v <= SIGNTRI_PH_MIXED_BF16; }
+
+signtri_status current_state(DeviceState **out)
+{
+    int dev = 0;
+    SGT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return SIGNTRI_ERR_CUDA;
+    DeviceState &s = g_dev[dev];
+    if (!s.scan_dev) {
+        SGT_CUDA_TRY(cudaMalloc(&s.scan_dev, sizeof(ScanResult)));
+        SGT_CUDA_TRY(cudaMallocHost(&s.scan_host, sizeof(ScanResult)));
+    }
+    *out = &s;
+    return SIGNTRI_OK;
+}
+
+// Workspace of at least `need` bytes for the current device.
+signtri_status get_workspace(DeviceState &s, size_t need, Arena &a)
+{
+    a = Arena();
+    if (need == 0) return SIGNTRI_OK;
+    if (s.user_ptr) {
+        if (s.user_bytes < need) return SIGNTRI_ERR_NO_WORKSPACE;
+        a.base = static_cast<char *>(s.user_ptr);
+        a.bytes = s.user_bytes;
+        return SIGNTRI_OK;
+    }
+    if (s.lib_bytes < need) {
+        if (s.lib_ptr) {
+            // the previous workspace may still be in use by enqueued work
+            if (cudaDeviceSynchronize() != cudaSuccess) return SIGNTRI_ERR_CUDA;
+            cudaFree(s.lib_ptr);
+            s.lib_ptr = nullptr;
+            s.lib_bytes = 0;
+        }
+        if (cudaMalloc(&s.lib_ptr, need) != cudaSuccess) {
+            cudaGetLastError();
+            return SIGNTRI_ERR_NO_WORKSPACE;
+        }
+        s.lib_bytes = need;
+    }
+    a.base = static_cast<char *>(s.lib_ptr);
+    a.bytes = s.lib_bytes;
+    return SIGNTRI_OK;
+}
+
+size_t workspace_need(int n, signtri_variant v, int cutoff)
+{
+    switch (v) {
+    case SIGNTRI_AUTO:
+    case SIGNTRI_PH_FP64:
+    case SIGNTRI_PS_FP64:
+    case SIGNTRI_PH_MIXED_TF32:
+    case SIGNTRI_PH_MIXED_BF16:
+        return ph_fp64_workspace_bytes(n, cutoff);
+    }
+    return 0;
+}
+
+// Section 3 estimates.  Parlett-Higham: the inner sums of Algorithm 3,
+// 2 flops per U^2 = I term and 4 per TU = UT term.  Parlett-Sylvester:
+// 12 n k for k swaps (including Q), n_- n_+ (n_- + n_+) for the Sylvester
+// solve, and for the back-transform by GEMM when k > 0
+// 2 n min(n_-,n_+) (n + max(n_-,n_+)).
+void work_estimates(int n, const ScanResult &r, double *w_ph, double *w_ps)
+{
+    const double nd = n;
+    const double all_terms = nd * (nd - 1.0) * (nd - 2.0) / 6.0;   // sum_{i<j} (j-i-1)
+    const double same = (double)r.same_terms;
+    *w_ph = 2.0 * same + 4.0 * (all_terms - same);
+    const double np = r.n_pos, nm = r.n_neg, k = (double)r.swaps;
+    double w = 12.0 * nd * k + np * nm * nd;
+    if (r.swaps > 0) w += 2.0 * nd * std::fmin(np, nm) * (nd + std::fmax(np, nm));
+    *w_ps = w;
+}
+
+signtri_status run_variant(int n, const double *T, int ldt, double *U, int ldu, signtri_variant v,
+                           cudaStream_t st, DeviceState &s)
+{
+    Arena ws;
+    const int b = g_cutoff;
+    signtri_status rs = get_workspace(s, workspace_need(n, v, b), ws);
+    if (rs != SIGNTRI_OK) return rs;
+    switch (v) {
+    case SIGNTRI_PH_FP64:
+        g_info.cutoff = b;
+        return ph_fp64_run(n, T, ldt, U, ldu, b, ws, st);
+    default:
+        return SIGNTRI_ERR_UNSUPPORTED;
+    }
+}
+
+signtri_status sign_tri_locked(int n, const double *T, int ldt, double *U, int ldu, signtri_variant v,
+                               cudaStream_t st, DeviceState &s)
+{
+    if (n == 0) return SIGNTRI_OK;
+    signtri_status rs = launch_inertia_scan(n, T, ldt, s.scan_dev, st);
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaMemcpyAsync(s.scan_host, s.scan_dev, sizeof(ScanResult), cudaMemcpyDeviceToHost, st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    const ScanResult r = *s.scan_host;
+    g_info.n_pos = r.n_pos;
+    g_info.n_neg = r.n_neg;
+    g_info.swaps = r.swaps;
+    if (r.bad_key != INT_MAX) {
+        g_info.bad_index = r.bad_key / 4;
+        return (signtri_status)(r.bad_key % 4);
+    }
+    work_estimates(n, r, &g_info.work_ph, &g_info.work_ps);
+    if (r.n_neg == 0 || r.n_pos == 0) {
+        // sign(T) = I or -I exactly (Section 3, the trivial case)
+        g_info.variant = v;
+        return launch_fill_identity(n, U, ldu, r.n_neg == 0 ? 1.0 : -1.0, st);
+    }
+    signtri_variant run = v;
+    if (v == SIGNTRI_AUTO) run = SIGNTRI_PH_FP64;
+    g_info.variant = run;
+    return run_variant(n, T, ldt, U, ldu, run, st, s);
+}
+
+void reset_info(int n)
+{
+    std::memset(&g_info, 0, sizeof(g_info));
+    g_info.n = n;
+    g_info.bad_index = -1;
+    g_info.variant = -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *signtri_status_string(signtri_status s)
+{
+    switch (s) {
+    case SIGNTRI_OK: return "SIGNTRI_OK";
+    case SIGNTRI_ERR_BAD_ARG: return "SIGNTRI_ERR_BAD_ARG";
+    case SIGNTRI_ERR_ZERO_EIGENVALUE: return "SIGNTRI_ERR_ZERO_EIGENVALUE";
+    case SIGNTRI_ERR_NONFINITE: return "SIGNTRI_ERR_NONFINITE";
+    case SIGNTRI_ERR_NO_CONVERGENCE: return "SIGNTRI_ERR_NO_CONVERGENCE";
+    case SIGNTRI_ERR_TIMEOUT: return "SIGNTRI_ERR_TIMEOUT";
+    case SIGNTRI_ERR_CUDA: return "SIGNTRI_ERR_CUDA";
+    case SIGNTRI_ERR_NO_WORKSPACE: return "SIGNTRI_ERR_NO_WORKSPACE";
+    case SIGNTRI_ERR_UNSUPPORTED: return "SIGNTRI_ERR_UNSUPPORTED";
+    }
+    return "SIGNTRI_ERR_UNKNOWN";
+}
+
+size_t signtri_workspace_bytes(int n, signtri_variant v)
+{
+    if (n < 0 || !valid_variant(v)) return 0;
+    std::lock_guard<std::mutex> lk(g_mu);
+    return workspace_need(n, v, g_cutoff);
+}
+
+signtri_status signtri_set_workspace(void *dev_ptr, size_t bytes)
+{
+    if (dev_ptr && ((uintptr_t)dev_ptr % 256) != 0) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    s->user_ptr = dev_ptr;
+    s->user_bytes = dev_ptr ? bytes : 0;
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_set_cutoff(int b)
+{
+    if (b == 0) b = kDefaultCutoff;
+    if (b != 16 && b != 32 && b != 64) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cutoff = b;
+    return SIGNTRI_OK;
+}
+
+signtri_status sign_tri(int n, const double *T, int ldt, double *U, int ldu, signtri_variant v,
+                        void *stream)
+{
+    reset_info(n);
+    if (n < 0 || !valid_variant(v)) return SIGNTRI_ERR_BAD_ARG;
+    if (n == 0) return SIGNTRI_OK;
+    if (!T || !U || ldt < n || ldu < n) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    return sign_tri_locked(n, T, ldt, U, ldu, v, static_cast<cudaStream_t>(stream), *s);
+}
+
+signtri_status sign_tri_host(int n, const double *T_host, int ldt, double *U_host, int ldu,
+                             signtri_variant v, void *stream)
+{
+    reset_info(n);
+    if (n < 0 || !valid_variant(v)) return SIGNTRI_ERR_BAD_ARG;
+    if (n == 0) return SIGNTRI_OK;
+    if (!T_host || !U_host || ldt < n || ldu < n) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t elems = (size_t)n * n;
+    if (s->stage_elems < elems) {
+        SGT_CUDA_TRY(cudaStreamSynchronize(st));
+        cudaFree(s->stage_T);
+        cudaFree(s->stage_U);
+        s->stage_T = s->stage_U = nullptr;
+        s->stage_elems = 0;
+        if (cudaMalloc(&s->stage_T, elems * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&s->stage_U, elems * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return SIGNTRI_ERR_NO_WORKSPACE;
+        }
+        s->stage_elems = elems;
+    }
+    SGT_CUDA_TRY(cudaMemcpy2DAsync(s->stage_T, (size_t)n * sizeof(double), T_host, (size_t)ldt * sizeof(double),
+                                   (size_t)n * sizeof(double), n, cudaMemcpyHostToDevice, st));
+    rs = sign_tri_locked(n, s->stage_T, n, s->stage_U, n, v, st, *s);
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaMemcpy2DAsync(U_host, (size_t)ldu * sizeof(double), s->stage_U, (size_t)n * sizeof(double),
+                                   (size_t)n * sizeof(double), n, cudaMemcpyDeviceToHost, st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_inertia(int n, const double *T, int ldt, int *n_pos, int *n_neg, long long *swaps,
+                               void *stream)
+{
+    if (n < 0 || (n > 0 && (!T || ldt < n))) return SIGNTRI_ERR_BAD_ARG;
+    if (n == 0) {
+        if (n_pos) *n_pos = 0;
+        if (n_neg) *n_neg = 0;
+        if (swaps) *swaps = 0;
+        return SIGNTRI_OK;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rs = launch_inertia_scan(n, T, ldt, s->scan_dev, st);
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaMemcpyAsync(s->scan_host, s->scan_dev, sizeof(ScanResult), cudaMemcpyDeviceToHost, st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    const ScanResult r = *s->scan_host;
+    if (n_pos) *n_pos = r.n_pos;
+    if (n_neg) *n_neg = r.n_neg;
+    if (swaps) *swaps = r.swaps;
+    if (r.bad_key != INT_MAX) return (signtri_status)(r.bad_key % 4);
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_get_info(signtri_info *out)
+{
+    if (!out) return SIGNTRI_ERR_BAD_ARG;
+    *out = g_info;
+    return SIGNTRI_OK;
+}
+
+}  // extern "C"

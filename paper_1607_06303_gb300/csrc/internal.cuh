@@ -1,0 +1,57 @@
+// internal.cuh -- declarations shared by the translation units of libsigntri.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/signtri.h"
+
+namespace signtri {
+
+// Column-major element access, 0-based.
+#define SGT_AT(M, ld, i, j) ((M)[(size_t)(i) + (size_t)(j) * (size_t)(ld)])
+
+#define SGT_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) return SIGNTRI_ERR_CUDA;      \
+    } while (0)
+
+#define SGT_LAUNCH_CHECK() SGT_CUDA_TRY(cudaGetLastError())
+
+// Result of the inertia scan (written by the device, read by the host).
+struct ScanResult {
+    int n_pos;
+    int n_neg;
+    long long swaps;       // #{i<j : t_ii < 0 < t_jj}
+    long long same_terms;  // sum over equal-sign pairs i<j of (j-i-1)
+    int bad_key;       // min over bad i of (4*i + kind), INT_MAX when none
+    int pad;
+};
+
+// Device workspace carved into aligned slices.
+struct Arena {
+    char *base = nullptr;
+    size_t bytes = 0;
+    size_t used = 0;
+    void *take(size_t n) {
+        size_t off = (used + 255) & ~(size_t)255;
+        if (off + n > bytes) return nullptr;
+        used = off + n;
+        return base + off;
+    }
+};
+
+// Scan / init kernels (scan.cu)
+signtri_status launch_inertia_scan(int n, const double *T, int ldt, ScanResult *d_out,
+                                   cudaStream_t st);
+signtri_status launch_fill_identity(int n, double *U, int ldu, double diag, cudaStream_t st);
+signtri_status launch_zero_strict_lower(int n, double *U, int ldu, cudaStream_t st);
+
+// Recursive Parlett-Higham, float64 (ph_fp64.cu)
+size_t ph_fp64_workspace_bytes(int n, int b);
+signtri_status ph_fp64_run(int n, const double *T, int ldt, double *U, int ldu, int b,
+                           Arena &ws, cudaStream_t st);
+
+}  // namespace signtri

@@ -1,0 +1,181 @@
+"""Thin ctypes binding of libsigntri.so (include/signtri.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  The functions keep the C names; the helpers at the end wrap torch
+tensors (device memory and streams only).
+
+A column-major n x n matrix M is held in a torch tensor `Mt` of shape
+(n, n), contiguous, with Mt[j, i] = M[i, j] (the row-major storage of M^T);
+its data pointer is then exactly the column-major array with ld = n.
+"""
+import ctypes
+import enum
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsigntri.so")
+
+
+class Variant(enum.IntEnum):
+    AUTO = 0
+    PH_FP64 = 1
+    PS_FP64 = 2
+    PH_MIXED_TF32 = 3
+    PH_MIXED_BF16 = 4
+
+
+class Status(enum.IntEnum):
+    OK = 0
+    ERR_BAD_ARG = 1
+    ERR_ZERO_EIGENVALUE = 2
+    ERR_NONFINITE = 3
+    ERR_NO_CONVERGENCE = 4
+    ERR_TIMEOUT = 5
+    ERR_CUDA = 6
+    ERR_NO_WORKSPACE = 7
+    ERR_UNSUPPORTED = 8
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("variant", ctypes.c_int),
+        ("n", ctypes.c_int),
+        ("n_pos", ctypes.c_int),
+        ("n_neg", ctypes.c_int),
+        ("swaps", ctypes.c_longlong),
+        ("work_ph", ctypes.c_double),
+        ("work_ps", ctypes.c_double),
+        ("cutoff", ctypes.c_int),
+        ("refine_steps", ctypes.c_int),
+        ("resid_commute", ctypes.c_double),
+        ("resid_involution", ctypes.c_double),
+        ("bad_index", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SignTriError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = Status(status)
+        super().__init__("%s%s" % (where + ": " if where else "", self.status.name))
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_SZ = ctypes.c_size_t
+
+# name -> (restype, argtypes)
+_SIGNATURES = {
+    "signtri_status_string": (ctypes.c_char_p, [_I]),
+    "signtri_workspace_bytes": (_SZ, [_I, _I]),
+    "signtri_set_workspace": (_I, [_VP, _SZ]),
+    "signtri_set_cutoff": (_I, [_I]),
+    "sign_tri": (_I, [_I, _VP, _I, _VP, _I, _I, _VP]),
+    "sign_tri_host": (_I, [_I, _VP, _I, _VP, _I, _I, _VP]),
+    "signtri_inertia": (_I, [_I, _VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                             ctypes.POINTER(ctypes.c_longlong), _VP]),
+    "signtri_get_info": (_I, [ctypes.POINTER(Info)]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libsigntri.so.  Raises if it has not been built: there is no
+    fallback implementation."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libsigntri.so not built (%s); run __graft_entry__.build()" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+# ---- the C entry points, same names ---------------------------------------
+
+def signtri_status_string(s: int) -> str:
+    return load().signtri_status_string(int(s)).decode()
+
+
+def signtri_workspace_bytes(n: int, v: int) -> int:
+    return int(load().signtri_workspace_bytes(n, int(v)))
+
+
+def signtri_set_workspace(dev_ptr: int, nbytes: int) -> int:
+    return load().signtri_set_workspace(dev_ptr or None, nbytes)
+
+
+def signtri_set_cutoff(b: int) -> int:
+    return load().signtri_set_cutoff(b)
+
+
+def sign_tri(n, T_ptr, ldt, U_ptr, ldu, v, stream) -> int:
+    return load().sign_tri(n, T_ptr or None, ldt, U_ptr or None, ldu, int(v), stream or None)
+
+
+def sign_tri_host(n, T_ptr, ldt, U_ptr, ldu, v, stream) -> int:
+    return load().sign_tri_host(n, T_ptr or None, ldt, U_ptr or None, ldu, int(v), stream or None)
+
+
+def signtri_inertia(n, T_ptr, ldt, stream=None):
+    p, m, k = _I(0), _I(0), ctypes.c_longlong(0)
+    st = load().signtri_inertia(n, T_ptr or None, ldt, ctypes.byref(p), ctypes.byref(m), ctypes.byref(k),
+                                stream or None)
+    return st, p.value, m.value, k.value
+
+
+def signtri_get_info() -> Info:
+    out = Info()
+    st = load().signtri_get_info(ctypes.byref(out))
+    if st != 0:
+        raise SignTriError(st, "signtri_get_info")
+    return out
+
+
+# ---- torch helpers (device memory and streams only) ------------------------
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def sign(Tt, variant=Variant.AUTO, out=None, stream=None, check=True):
+    """U = sign(T) for a CUDA float64 tensor holding T column-major (see the
+    module docstring).  Returns the tensor holding U in the same layout."""
+    import torch
+    if Tt.dtype != torch.float64 or not Tt.is_cuda or Tt.dim() != 2 or Tt.shape[0] != Tt.shape[1]:
+        raise ValueError("T must be a square CUDA float64 tensor")
+    if not Tt.is_contiguous():
+        raise ValueError("T must be contiguous")
+    n = Tt.shape[0]
+    Ut = out if out is not None else torch.empty_like(Tt)
+    st = sign_tri(n, Tt.data_ptr(), max(n, 1), Ut.data_ptr(), max(n, 1), variant, _stream_handle(stream))
+    if check and st != 0:
+        raise SignTriError(st, "sign_tri")
+    return Ut
+
+
+def to_device(T_colmajor, device="cuda"):
+    """numpy column-major (Fortran-order) n x n float64 -> CUDA tensor in the
+    layout above."""
+    import numpy as np
+    import torch
+    a = np.asfortranarray(np.asarray(T_colmajor, dtype=np.float64))
+    return torch.from_numpy(np.ascontiguousarray(a.T)).to(device)
+
+
+def to_numpy(Mt):
+    """Inverse of to_device: CUDA tensor -> numpy column-major array."""
+    import numpy as np
+    return np.asfortranarray(Mt.cpu().numpy().T)
