@@ -1,0 +1,333 @@
+#!/usr/bin/env python3
+"""Throughput of U = sign(T) on GB300: useful GFLOP/s (the oracle's flop count
+of Algorithm 3) at n = 16384, p = 0.5 (random interleaved diagonal signs,
+|t_ii| ~ U[0.5, 2], strictly-upper N(0, 1/n)), seed = rank.
+
+One step = one sign_tri call on a resident input: inertia scan, variant
+choice, and the chosen variant's kernels.  The input (2.1 GB) and output are
+each larger than L2 (129 MB), so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--variant V]
+    python bench.py --impl reference      # the CPU oracle, the reference arm
+
+Under torchrun (N > 1) every rank solves its own replica (the method does
+not shard a single matrix); value = total useful flops / max-over-ranks time.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sign(T) seconds & useful GFLOP/s at n=16384: mixed+refine vs FP64, ≤1e-12 err"
+UNIT = "GFLOP/s"
+
+# DRAM bytes per launch of the dominant kernel from an ncu capture, keyed by
+# the sha256 of the source file it came from; reported only while the source
+# is unchanged (see profiles/).
+TRAFFIC = {}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--p", type=float, default=0.5)
+    ap.add_argument("--order", default="random")
+    ap.add_argument("--variant", default="AUTO")
+    ap.add_argument("--cutoff", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=4096,
+                    help="order of the leading principal window the oracle solves")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks ---
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1].split()[0]))
+                    smax.append(float(parts[2].split()[0]))
+                    power.append(float(parts[3].split()[0]))
+                except ValueError:
+                    continue
+                for name, val in zip(names[1:], parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- reference ---
+def run_reference(args, rank):
+    """The CPU oracle (Algorithm 3, OpenMP anti-diagonal schedule) on the
+    leading principal window of the same input: a bounded sample of the
+    workload with the same structure (u_ij of a window depends on the window
+    only)."""
+    import numpy as np
+
+    import oracle
+    from paper_1607_06303_gb300 import workload
+    from paper_1607_06303_gb300.inputs import make_T
+    if rank != 0:
+        return None
+    m = min(args.cpu_sample if args.cpu_sample else 3072, args.n)
+    T = make_T(args.n, args.p, seed=0, order=args.order)
+    Tw = np.asfortranarray(T[:m, :m])
+    flops = workload.useful_flops(np.sign(np.diag(Tw)))
+    threads = oracle.max_threads()
+    for _ in range(args.warmup):
+        oracle.sign_tri(Tw, schedule="antidiag", threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sign_tri(Tw, schedule="antidiag", threads=threads)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    val = flops / dt / 1e9
+    sample = "leading %dx%d principal window of the n=%d input (%.3g useful flops/step)" % (m, m, args.n, flops)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "sign(T) n=%d p=%g %s, seed 0; oracle on a %d-window" % (args.n, args.p, args.order, m),
+                   "n": args.n, "p": args.p, "order": args.order},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    return line
+
+
+# ------------------------------------------------------------------- ours ---
+def block_sum_flops(n, b):
+    """Algorithmic flops of all block-sum launches of one call: 6 flops per
+    (row, k, column) triple with k in the K-blocks strictly between the row
+    and column blocks (the matrix-multiply form of Section 5.3)."""
+    nb = (n + b - 1) // b
+    total = 0
+    for d in range(2, nb):
+        for I in range(nb - d):
+            J = I + d
+            bj = min(b, n - J * b)
+            total += 6 * b * (d - 1) * b * bj
+    return total
+
+
+def src_sha(rel):
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return 0
+
+    import numpy as np
+    import torch
+
+    import paper_1607_06303_gb300 as st
+    from paper_1607_06303_gb300 import workload
+    from paper_1607_06303_gb300.inputs import make_T
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    st.load()
+    variant = st.Variant[args.variant]
+    if args.cutoff:
+        assert st.signtri_set_cutoff(args.cutoff) == 0
+    n = args.n
+    T = make_T(n, args.p, seed=rank, order=args.order)
+    signs = np.sign(np.diag(T))
+    useful = workload.useful_flops(signs)
+    Tt = st.to_device(T)
+    Ut = torch.empty_like(Tt)
+    stream = torch.cuda.current_stream()
+    h = stream.cuda_stream
+
+    def step():
+        s = st.sign_tri(n, Tt.data_ptr(), n, Ut.data_ptr(), n, variant, h)
+        if s != 0:
+            raise st.SignTriError(s, "sign_tri")
+
+    fp64_peak = st.signtri_probe_fp64_peak(h)
+    for _ in range(max(args.warmup, 0)):
+        step()
+    barrier()
+    st.signtri_profile_reset()
+    st.signtri_profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    st.signtri_profile_enable(False)
+    ms_total = e0.elapsed_time(e1)
+    per_class = {}
+    launches = 0
+    for c in range(st.signtri.KC_COUNT):
+        cnt, ms = st.signtri_profile_read(c)
+        launches += cnt
+        if cnt:
+            per_class[st.signtri_kernel_class_name(c)] = {"launches": cnt, "device_ms": ms}
+    info = st.signtri_get_info()
+    ms_step = ms_total / max(args.steps, 1)
+    t_max = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_step_max = float(t_max.item())
+    value = world * useful / (ms_step_max * 1e-3) / 1e9
+
+    # roofline of the dominant kernel class
+    dom = max(per_class.items(), key=lambda kv: kv[1]["device_ms"])[0] if per_class else None
+    roof = None
+    if dom == "block_sums_f64":
+        b = info.cutoff
+        flops_step = block_sum_flops(n, b)
+        launches_dom = per_class[dom]["launches"]
+        per_launch = flops_step * args.steps / launches_dom
+        avg_ms = per_class[dom]["device_ms"] / launches_dom
+        ach = per_launch / (avg_ms * 1e-3) / 1e12
+        peak = fp64_peak / 1e3
+        sha = src_sha("paper_1607_06303_gb300/csrc/ph_fp64.cu")
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": TRAFFIC.get(("block_sums_f64", sha)),
+                "kernel": "ph_gemm_kernel (float64 DFMA block sums)",
+                "peak_source": "float64 FMA issue rate measured live by signtri_probe_fp64_peak (no FP64 entry "
+                               "in MEASURED_PEAKS.json)",
+                "share_of_step": per_class[dom]["device_ms"] / ms_total}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step_max, "seconds_per_solve": ms_step_max / 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "sign(T) n=%d p=%g %s diagonal, |t_ii|~U[0.5,2], t_ij~N(0,1/n), seed=rank"
+                               % (n, args.p, args.order),
+                   "n": n, "p": args.p, "order": args.order, "variant_requested": args.variant,
+                   "variant_run": st.Variant(info.variant).name if info.variant >= 0 else None,
+                   "cutoff": info.cutoff, "useful_flops_per_solve": useful,
+                   "l2": "no flush: T and U are 2.1 GB each, > 129 MB L2", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "gpu_launches": launches, "kernel_time_ms": per_class, "roofline": roof, "clocks": clk,
+    }
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        Th = torch.from_numpy(np.ascontiguousarray(T.T)).pin_memory()
+        Uh = torch.empty_like(Th).pin_memory()
+        s = st.sign_tri_host(n, Th.data_ptr(), n, Uh.data_ptr(), n, variant, h)   # warm (staging alloc)
+        if s != 0:
+            raise st.SignTriError(s, "sign_tri_host")
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s = st.sign_tri_host(n, Th.data_ptr(), n, Uh.data_ptr(), n, variant, h)
+            if s != 0:
+                raise st.SignTriError(s, "sign_tri_host")
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / max(args.steps, 1)
+        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        line["e2e"] = {"value": world * useful / float(te.item()) / 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": Th.numel() * 8, "d2h_bytes_per_step": Uh.numel() * 8,
+                       "seconds_per_solve": float(te.item())}
+        del Th, Uh
+
+    # CPU oracle baseline on a bounded sample (rank 0, N = 1) and the parity of
+    # this run's output on that window
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        m = min(args.cpu_sample, n)
+        Tw = np.asfortranarray(T[:m, :m])
+        threads = oracle.max_threads()
+        t0 = time.perf_counter()
+        Uo = oracle.sign_tri(Tw, schedule="antidiag", threads=threads)
+        dt = time.perf_counter() - t0
+        fw = workload.useful_flops(np.sign(np.diag(Tw)))
+        line["cpu_baseline"] = {"value": fw / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": "leading %dx%d principal window of the same input, one solve "
+                                          "(%.3g useful flops, %.1f s)" % (m, m, fw, dt)}
+        Ug = Ut[:m, :m].cpu().numpy().T      # U[:m,:m] (column-major storage transposed back)
+        line["rel_err_vs_oracle_window"] = float(np.linalg.norm(Ug - Uo) / np.linalg.norm(Uo))
+        # the trailing window: the same principal-window property
+        Tw2 = np.asfortranarray(T[n - m:, n - m:])
+        Uo2 = oracle.sign_tri(Tw2, schedule="antidiag", threads=threads)
+        Ug2 = Ut[n - m:, n - m:].cpu().numpy().T
+        line["rel_err_vs_oracle_trailing_window"] = float(np.linalg.norm(Ug2 - Uo2) / np.linalg.norm(Uo2))
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -124,6 +124,39 @@ signtri_status signtri_inertia(int n, const double *T, int ldt, int *n_pos, int 
    calling host thread. */
 signtri_status signtri_get_info(signtri_info *out);
 
+/* ---- Observability (not part of the method) ------------------------------
+   Kernel classes, for the launch counters and device-time accounting. */
+enum {
+    SIGNTRI_KC_SCAN = 0,          /* inertia scan */
+    SIGNTRI_KC_FILL = 1,          /* identity / zero fills */
+    SIGNTRI_KC_DIAG_LEAF = 2,     /* diagonal-block leaves (Algorithm 3 per block) */
+    SIGNTRI_KC_BLOCK_SUMS_F64 = 3,/* float64 block sums X, Y (Section 5.2) */
+    SIGNTRI_KC_OFFDIAG_LEAF = 4,  /* off-diagonal leaves (Algorithm 6, 1x1 case) */
+    SIGNTRI_KC_BLOCK_SUMS_TC = 5, /* tensor-core block sums */
+    SIGNTRI_KC_OFFDIAG_LEAF_F32 = 6,
+    SIGNTRI_KC_CONVERT = 7,
+    SIGNTRI_KC_RESIDUAL = 8,
+    SIGNTRI_KC_CORRECTION = 9,
+    SIGNTRI_KC_OTHER = 10,
+    SIGNTRI_KC_COUNT = 11
+};
+
+/* on != 0: bracket every library kernel launch with CUDA events on its
+   stream from now on (adds two event records per launch).  Launch counts
+   are kept either way. */
+signtri_status signtri_profile_enable(int on);
+/* Zero the launch counters and timers. */
+signtri_status signtri_profile_reset(void);
+/* Launches of class `cls` since the last reset and their summed device time
+   in milliseconds (waits for the recorded events).  Either pointer may be
+   NULL. */
+signtri_status signtri_profile_read(int cls, long long *launches, double *device_ms);
+/* Name of a kernel class ("" when out of range). */
+const char *signtri_kernel_class_name(int cls);
+/* Float64 fused-multiply-add issue rate of the current device, GFLOP/s
+   (independent FMA chains; best of three launches on `stream`). */
+signtri_status signtri_probe_fp64_peak(double *gflops, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

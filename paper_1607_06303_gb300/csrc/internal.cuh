@@ -43,6 +43,17 @@ struct Arena {
     }
 };
 
+// Launch accounting (prof.cu): bracket every library launch.
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, cudaStream_t st);
+
+struct ProfScope {
+    int cls;
+    cudaStream_t st;
+    ProfScope(int c, cudaStream_t s) : cls(c), st(s) { prof_begin(c, s); }
+    ~ProfScope() { prof_end(cls, st); }
+};
+
 // Scan / init kernels (scan.cu)
 signtri_status launch_inertia_scan(int n, const double *T, int ldt, ScanResult *d_out,
                                    cudaStream_t st);

@@ -276,8 +276,11 @@ signtri_status run_b(int n, const double *T, int ldt, double *U, int ldu, Arena 
                                       (int)diag_smem<B>()));
     signtri_status rs = launch_zero_strict_lower(n, U, ldu, st);
     if (rs != SIGNTRI_OK) return rs;
-    diag_leaf_kernel<B><<<nb, kThreads, diag_smem<B>(), st>>>(n, T, ldt, U, ldu);
-    SGT_LAUNCH_CHECK();
+    {
+        ProfScope ps(SIGNTRI_KC_DIAG_LEAF, st);
+        diag_leaf_kernel<B><<<nb, kThreads, diag_smem<B>(), st>>>(n, T, ldt, U, ldu);
+        SGT_LAUNCH_CHECK();
+    }
     for (int d = 1; d < nb; d++) {
         const int ntiles = nb - d;
         const int kmax = d - 1;
@@ -287,13 +290,17 @@ signtri_status run_b(int n, const double *T, int ldt, double *U, int ldu, Arena 
             nsplit = std::max(1, std::min(want, std::min(kSplitMax, kmax)));
             const int kc = (kmax + nsplit - 1) / nsplit;
             nsplit = (kmax + kc - 1) / kc;
+            ProfScope ps(SIGNTRI_KC_BLOCK_SUMS_F64, st);
             ph_gemm_kernel<B><<<dim3(ntiles, nsplit), kThreads, 0, st>>>(n, T, ldt, U, ldu, d, kc, PX, PY,
                                                                         split_stride);
             SGT_LAUNCH_CHECK();
         }
-        offdiag_leaf_kernel<B><<<ntiles, kThreads, leaf_smem<B>(), st>>>(n, T, ldt, U, ldu, d, nsplit,
-                                                                         PX, PY, split_stride);
-        SGT_LAUNCH_CHECK();
+        {
+            ProfScope ps(SIGNTRI_KC_OFFDIAG_LEAF, st);
+            offdiag_leaf_kernel<B><<<ntiles, kThreads, leaf_smem<B>(), st>>>(n, T, ldt, U, ldu, d, nsplit,
+                                                                             PX, PY, split_stride);
+            SGT_LAUNCH_CHECK();
+        }
     }
     return SIGNTRI_OK;
 }

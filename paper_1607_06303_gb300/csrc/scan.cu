@@ -95,6 +95,7 @@ __global__ void zero_strict_lower_kernel(int n, double *__restrict__ U, int ldu)
 signtri_status launch_inertia_scan(int n, const double *T, int ldt, ScanResult *d_out,
                                    cudaStream_t st)
 {
+    ProfScope ps(SIGNTRI_KC_SCAN, st);
     inertia_scan_kernel<<<1, kScanThreads, 0, st>>>(n, T, ldt, d_out);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
@@ -103,6 +104,7 @@ signtri_status launch_inertia_scan(int n, const double *T, int ldt, ScanResult *
 signtri_status launch_fill_identity(int n, double *U, int ldu, double diag, cudaStream_t st)
 {
     if (n <= 0) return SIGNTRI_OK;
+    ProfScope ps(SIGNTRI_KC_FILL, st);
     fill_identity_kernel<<<n, 256, 0, st>>>(n, U, ldu, diag);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
@@ -111,6 +113,7 @@ signtri_status launch_fill_identity(int n, double *U, int ldu, double diag, cuda
 signtri_status launch_zero_strict_lower(int n, double *U, int ldu, cudaStream_t st)
 {
     if (n <= 1) return SIGNTRI_OK;
+    ProfScope ps(SIGNTRI_KC_FILL, st);
     zero_strict_lower_kernel<<<n, 256, 0, st>>>(n, U, ldu);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;

@@ -78,7 +78,17 @@ _SIGNATURES = {
     "signtri_inertia": (_I, [_I, _VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                              ctypes.POINTER(ctypes.c_longlong), _VP]),
     "signtri_get_info": (_I, [ctypes.POINTER(Info)]),
+    "signtri_profile_enable": (_I, [_I]),
+    "signtri_profile_reset": (_I, []),
+    "signtri_profile_read": (_I, [_I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
+    "signtri_kernel_class_name": (ctypes.c_char_p, [_I]),
+    "signtri_probe_fp64_peak": (_I, [ctypes.POINTER(ctypes.c_double), _VP]),
 }
+
+# kernel classes of the launch accounting (include/signtri.h)
+KC_SCAN, KC_FILL, KC_DIAG_LEAF, KC_BLOCK_SUMS_F64, KC_OFFDIAG_LEAF = 0, 1, 2, 3, 4
+KC_BLOCK_SUMS_TC, KC_OFFDIAG_LEAF_F32, KC_CONVERT, KC_RESIDUAL, KC_CORRECTION, KC_OTHER = 5, 6, 7, 8, 9, 10
+KC_COUNT = 11
 
 
 def load(path: str = LIB_PATH):
@@ -140,6 +150,34 @@ def signtri_get_info() -> Info:
     if st != 0:
         raise SignTriError(st, "signtri_get_info")
     return out
+
+
+def signtri_profile_enable(on: bool) -> int:
+    return load().signtri_profile_enable(1 if on else 0)
+
+
+def signtri_profile_reset() -> int:
+    return load().signtri_profile_reset()
+
+
+def signtri_profile_read(cls: int):
+    n, ms = ctypes.c_longlong(0), ctypes.c_double(0)
+    st = load().signtri_profile_read(cls, ctypes.byref(n), ctypes.byref(ms))
+    if st != 0:
+        raise SignTriError(st, "signtri_profile_read")
+    return n.value, ms.value
+
+
+def signtri_kernel_class_name(cls: int) -> str:
+    return load().signtri_kernel_class_name(cls).decode()
+
+
+def signtri_probe_fp64_peak(stream=None) -> float:
+    g = ctypes.c_double(0)
+    st = load().signtri_probe_fp64_peak(ctypes.byref(g), stream or None)
+    if st != 0:
+        raise SignTriError(st, "signtri_probe_fp64_peak")
+    return g.value
 
 
 # ---- torch helpers (device memory and streams only) ------------------------
