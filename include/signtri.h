@@ -157,6 +157,34 @@ const char *signtri_kernel_class_name(int cls);
    (independent FMA chains; best of three launches on `stream`). */
 signtri_status signtri_probe_fp64_peak(double *gflops, void *stream);
 
+/* ---- Entry point that allocates nothing -----------------------------------
+   The paper has no counterpart to this call.  It is for callers that cannot
+   allocate device memory: code inside a host program that owns all device
+   memory through its own pool (a serving runtime, a plugin), where a raw
+   cudaMalloc would bypass the owner's accounting or fail, and code that must
+   not stall the device (cudaMalloc and cudaFree can synchronize it).
+
+   Same result as sign_tri with SIGNTRI_PH_FP64 (the same kernels and the
+   process-wide cutoff), but the scratch lives in a file-scope device array of
+   32 MiB + 4 KiB inside the library: every GPU that loads the library holds it
+   until the process exits.  Limits and behaviour:
+     - n <= SIGNTRI_NOALLOC_MAX_N (1024); larger n returns
+       SIGNTRI_ERR_NO_WORKSPACE without launching anything.
+     - Calls no cudaMalloc, cudaFree or allocating library routine.  (With
+       signtri_profile_enable on, the library creates CUDA events; leave
+       profiling off on such paths.)
+     - The first call on a device looks up the array's device address with
+       cudaGetSymbolAddress (the device must be current); make that first call
+       before any stream capture.
+     - All calls share the one array, which keeps the last call's contents;
+       nothing in it needs to start at zero.  Calls that overlap on the GPU
+       (different streams, or different host threads) race on it: serialize
+       them.
+     - Waits once on `stream` after the inertia scan, like sign_tri. */
+#define SIGNTRI_NOALLOC_MAX_N 1024
+signtri_status sign_tri_noalloc(int n, const double *T, int ldt, double *U, int ldu,
+                                void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -164,6 +164,12 @@ void reset_info(int n)
 
 }  // namespace
 
+int signtri::current_cutoff()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_cutoff;
+}
+
 extern "C" {
 
 const char *signtri_status_string(signtri_status s)

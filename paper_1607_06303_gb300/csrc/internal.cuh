@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <climits>
 
 #include "../../include/signtri.h"
 
@@ -59,6 +60,9 @@ signtri_status launch_inertia_scan(int n, const double *T, int ldt, ScanResult *
                                    cudaStream_t st);
 signtri_status launch_fill_identity(int n, double *U, int ldu, double diag, cudaStream_t st);
 signtri_status launch_zero_strict_lower(int n, double *U, int ldu, cudaStream_t st);
+
+// Process-wide leaf size of Parlett-Higham (api.cu).
+int current_cutoff();
 
 // Recursive Parlett-Higham, float64 (ph_fp64.cu)
 size_t ph_fp64_workspace_bytes(int n, int b);

@@ -83,7 +83,10 @@ _SIGNATURES = {
     "signtri_profile_read": (_I, [_I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
     "signtri_kernel_class_name": (ctypes.c_char_p, [_I]),
     "signtri_probe_fp64_peak": (_I, [ctypes.POINTER(ctypes.c_double), _VP]),
+    "sign_tri_noalloc": (_I, [_I, _VP, _I, _VP, _I, _VP]),
 }
+
+SIGNTRI_NOALLOC_MAX_N = 1024
 
 # kernel classes of the launch accounting (include/signtri.h)
 KC_SCAN, KC_FILL, KC_DIAG_LEAF, KC_BLOCK_SUMS_F64, KC_OFFDIAG_LEAF = 0, 1, 2, 3, 4
@@ -131,6 +134,12 @@ def signtri_set_cutoff(b: int) -> int:
 
 def sign_tri(n, T_ptr, ldt, U_ptr, ldu, v, stream) -> int:
     return load().sign_tri(n, T_ptr or None, ldt, U_ptr or None, ldu, int(v), stream or None)
+
+
+def sign_tri_noalloc(n, T_ptr, ldt, U_ptr, ldu, stream) -> int:
+    """sign_tri with SIGNTRI_PH_FP64, scratch in a static device array (no
+    allocation); n <= SIGNTRI_NOALLOC_MAX_N."""
+    return load().sign_tri_noalloc(n, T_ptr or None, ldt, U_ptr or None, ldu, stream or None)
 
 
 def sign_tri_host(n, T_ptr, ldt, U_ptr, ldu, v, stream) -> int:
