@@ -94,6 +94,11 @@ size_t signtri_workspace_bytes(int n, signtri_variant v);
    SIGNTRI_ERR_NO_WORKSPACE. */
 signtri_status signtri_set_workspace(void *dev_ptr, size_t bytes);
 
+/* Per-variant throughput used by SIGNTRI_AUTO to turn the Section 3 work
+   estimates into times: flops/s of the float64 block products and of the
+   Givens reorder rounds.  Values <= 0 restore the defaults. */
+signtri_status signtri_set_rates(double gemm_flops_per_s, double givens_flops_per_s);
+
 /* Leaf (recursion cutoff) size b of Parlett-Higham: the order of the diagonal
    and off-diagonal blocks solved element by element (Section 6 uses 16).
    b in {16, 32, 64}; 0 restores the default.  Process-wide setting. */
@@ -124,21 +129,46 @@ signtri_status signtri_inertia(int n, const double *T, int ldt, int *n_pos, int 
    calling host thread. */
 signtri_status signtri_get_info(signtri_info *out);
 
+/* ---- Building blocks of Parlett-Sylvester (Section 2, Section 5.1) -------- */
+
+/* Schur reordering by sign: Tr = Q^T T Q with Q orthogonal and Tr upper
+   triangular whose diagonal holds the diagonal of T permuted so that all
+   positive entries come first, each sign group in its original order.
+   Adjacent Givens swaps, *swaps of them (the number of pairs i<j with
+   t_ii < 0 < t_jj, the minimum).  T, Tr, Q device pointers, n x n
+   column-major; T is only read (its upper triangle), Tr's strictly lower part
+   is written as 0.  Synchronous on `stream` (the swap schedule is built on
+   the host from the diagonal signs).  swaps may be NULL. */
+signtri_status signtri_reorder_by_sign(int n, const double *T, int ldt, double *Tr, int ldtr,
+                                       double *Q, int ldq, long long *swaps, void *stream);
+
+/* Triangular Sylvester equation A X - X B = C for X (m x p): A (m x m) and
+   B (p x p) upper triangular (only their upper triangles are read) with
+   a_ii != b_jj for all i, j; C (m x p).  All device pointers, column-major;
+   X must not overlap A, B or C.  Enqueued on `stream`.  m == 0 or p == 0 is a
+   no-op. */
+signtri_status signtri_sylvester(int m, int p, const double *A, int lda, const double *B, int ldb,
+                                 const double *C, int ldc, double *X, int ldx, void *stream);
+
 /* ---- Observability (not part of the method) ------------------------------
    Kernel classes, for the launch counters and device-time accounting. */
 enum {
     SIGNTRI_KC_SCAN = 0,          /* inertia scan */
-    SIGNTRI_KC_FILL = 1,          /* identity / zero fills */
+    SIGNTRI_KC_FILL = 1,          /* identity / zero / copy fills */
     SIGNTRI_KC_DIAG_LEAF = 2,     /* diagonal-block leaves (Algorithm 3 per block) */
     SIGNTRI_KC_BLOCK_SUMS_F64 = 3,/* float64 block sums X, Y (Section 5.2) */
     SIGNTRI_KC_OFFDIAG_LEAF = 4,  /* off-diagonal leaves (Algorithm 6, 1x1 case) */
-    SIGNTRI_KC_BLOCK_SUMS_TC = 5, /* tensor-core block sums */
-    SIGNTRI_KC_OFFDIAG_LEAF_F32 = 6,
-    SIGNTRI_KC_CONVERT = 7,
-    SIGNTRI_KC_RESIDUAL = 8,
-    SIGNTRI_KC_CORRECTION = 9,
-    SIGNTRI_KC_OTHER = 10,
-    SIGNTRI_KC_COUNT = 11
+    SIGNTRI_KC_BLOCK_SUMS_TC = 5, /* tensor-core block sums (mixed variants) */
+    SIGNTRI_KC_OFFDIAG_LEAF_F32 = 6, /* off-diagonal leaves of the mixed variants */
+    SIGNTRI_KC_CONVERT = 7,       /* precision conversion / splitting */
+    SIGNTRI_KC_RESIDUAL = 8,      /* refinement residuals */
+    SIGNTRI_KC_CORRECTION = 9,    /* refinement corrections */
+    SIGNTRI_KC_GIVENS = 10,       /* Parlett-Sylvester reorder rounds */
+    SIGNTRI_KC_SYLV_SUMS = 11,    /* Sylvester block sums */
+    SIGNTRI_KC_SYLV_LEAF = 12,    /* Sylvester in-block recurrence */
+    SIGNTRI_KC_GEMM_F64 = 13,     /* float64 GEMM (back-transform) */
+    SIGNTRI_KC_OTHER = 14,
+    SIGNTRI_KC_COUNT = 15
 };
 
 /* on != 0: bracket every library kernel launch with CUDA events on its

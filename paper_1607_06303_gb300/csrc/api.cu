@@ -5,6 +5,7 @@
 // estimates, workspace management, and dispatch to the variant's kernels.
 #include <climits>
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -32,6 +33,11 @@ struct DeviceState {
 std::mutex g_mu;
 DeviceState g_dev[kMaxDevices];
 int g_cutoff = kDefaultCutoff;
+// flops/s used by the AUTO choice (float64 block products; Givens rounds)
+constexpr double kDefaultGemmRate = 1.0e12;
+constexpr double kDefaultGivensRate = 0.35e12;
+double g_rate_gemm = kDefaultGemmRate;
+double g_rate_givens = kDefaultGivensRate;
 thread_local signtri_info g_info;
 
 bool valid_variant(int v) { return v >= SIGNTRI_AUTO && v <= SIGNTRI_PH_MIXED_BF16; }
@@ -80,15 +86,19 @@ signtri_status get_workspace(DeviceState &s, size_t need, Arena &a)
     return SIGNTRI_OK;
 }
 
-size_t workspace_need(int n, signtri_variant v, int cutoff)
+// swaps < 0: the worst case over inertia (n^2/4 swaps).
+size_t workspace_need(int n, signtri_variant v, int cutoff, long long swaps)
 {
+    if (swaps < 0) swaps = (long long)n * n / 4;
     switch (v) {
-    case SIGNTRI_AUTO:
     case SIGNTRI_PH_FP64:
-    case SIGNTRI_PS_FP64:
     case SIGNTRI_PH_MIXED_TF32:
     case SIGNTRI_PH_MIXED_BF16:
         return ph_fp64_workspace_bytes(n, cutoff);
+    case SIGNTRI_PS_FP64:
+        return ps_workspace_bytes(n, swaps);
+    case SIGNTRI_AUTO:
+        return std::max(ph_fp64_workspace_bytes(n, cutoff), ps_workspace_bytes(n, swaps));
     }
     return 0;
 }
@@ -100,6 +110,7 @@ size_t workspace_need(int n, signtri_variant v, int cutoff)
 // 2 n min(n_-,n_+) (n + max(n_-,n_+)).
 void work_estimates(int n, const ScanResult &r, double *w_ph, double *w_ps)
 {
+    // (the useful count of Algorithm 3 for Parlett-Higham)
     const double nd = n;
     const double all_terms = nd * (nd - 1.0) * (nd - 2.0) / 6.0;   // sum_{i<j} (j-i-1)
     const double same = (double)r.same_terms;
@@ -110,17 +121,35 @@ void work_estimates(int n, const ScanResult &r, double *w_ph, double *w_ps)
     *w_ps = w;
 }
 
+// Times predicted from the Section 3 work of what each variant executes:
+// Parlett-Higham runs the matrix-multiply form (6 flops per (i<k<j) block
+// triple, n^3 to leading order); Parlett-Sylvester runs 12 n k flops of
+// Givens rounds, n_- n_+ n of Sylvester solve and, when k > 0, the
+// back-transform products.
+signtri_variant choose_variant(int n, const ScanResult &r)
+{
+    const double nd = n;
+    const double t_ph = nd * nd * nd / g_rate_gemm;
+    const double np = r.n_pos, nm = r.n_neg, k = (double)r.swaps;
+    double bt = 0.0;
+    if (r.swaps > 0) bt = 2.0 * nd * std::fmin(np, nm) * (nd + std::fmax(np, nm));
+    const double t_ps = 12.0 * nd * k / g_rate_givens + (np * nm * nd + bt) / g_rate_gemm;
+    return t_ps < t_ph ? SIGNTRI_PS_FP64 : SIGNTRI_PH_FP64;
+}
+
 signtri_status run_variant(int n, const double *T, int ldt, double *U, int ldu, signtri_variant v,
-                           cudaStream_t st, DeviceState &s)
+                           const ScanResult &r, cudaStream_t st, DeviceState &s)
 {
     Arena ws;
     const int b = g_cutoff;
-    signtri_status rs = get_workspace(s, workspace_need(n, v, b), ws);
+    signtri_status rs = get_workspace(s, workspace_need(n, v, b, r.swaps), ws);
     if (rs != SIGNTRI_OK) return rs;
     switch (v) {
     case SIGNTRI_PH_FP64:
         g_info.cutoff = b;
         return ph_fp64_run(n, T, ldt, U, ldu, b, ws, st);
+    case SIGNTRI_PS_FP64:
+        return ps_fp64_run(n, T, ldt, U, ldu, r.n_pos, r.swaps, ws, st);
     default:
         return SIGNTRI_ERR_UNSUPPORTED;
     }
@@ -149,9 +178,9 @@ signtri_status sign_tri_locked(int n, const double *T, int ldt, double *U, int l
         return launch_fill_identity(n, U, ldu, r.n_neg == 0 ? 1.0 : -1.0, st);
     }
     signtri_variant run = v;
-    if (v == SIGNTRI_AUTO) run = SIGNTRI_PH_FP64;
+    if (v == SIGNTRI_AUTO) run = choose_variant(n, r);
     g_info.variant = run;
-    return run_variant(n, T, ldt, U, ldu, run, st, s);
+    return run_variant(n, T, ldt, U, ldu, run, r, st, s);
 }
 
 void reset_info(int n)
@@ -192,7 +221,55 @@ size_t signtri_workspace_bytes(int n, signtri_variant v)
 {
     if (n < 0 || !valid_variant(v)) return 0;
     std::lock_guard<std::mutex> lk(g_mu);
-    return workspace_need(n, v, g_cutoff);
+    return workspace_need(n, v, g_cutoff, -1);
+}
+
+signtri_status signtri_set_rates(double gemm_flops_per_s, double givens_flops_per_s)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_rate_gemm = gemm_flops_per_s > 0 ? gemm_flops_per_s : kDefaultGemmRate;
+    g_rate_givens = givens_flops_per_s > 0 ? givens_flops_per_s : kDefaultGivensRate;
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_reorder_by_sign(int n, const double *T, int ldt, double *Tr, int ldtr, double *Q, int ldq,
+                                       long long *swaps, void *stream)
+{
+    if (swaps) *swaps = 0;
+    if (n < 0) return SIGNTRI_ERR_BAD_ARG;
+    if (n == 0) return SIGNTRI_OK;
+    if (!T || !Tr || !Q || ldt < n || ldtr < n || ldq < n) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rs = launch_inertia_scan(n, T, ldt, s->scan_dev, st);
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaMemcpyAsync(s->scan_host, s->scan_dev, sizeof(ScanResult), cudaMemcpyDeviceToHost, st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    const ScanResult r = *s->scan_host;
+    if (r.bad_key != INT_MAX) return (signtri_status)(r.bad_key % 4);
+    Arena ws;
+    rs = get_workspace(s[0], reorder_workspace_bytes(n) + (size_t)r.swaps * sizeof(int) + 256, ws);
+    if (rs != SIGNTRI_OK) return rs;
+    return reorder_run(n, T, ldt, Tr, ldtr, Q, ldq, swaps, ws, st);
+}
+
+signtri_status signtri_sylvester(int m, int p, const double *A, int lda, const double *B, int ldb, const double *C,
+                                 int ldc, double *X, int ldx, void *stream)
+{
+    if (m < 0 || p < 0) return SIGNTRI_ERR_BAD_ARG;
+    if (m == 0 || p == 0) return SIGNTRI_OK;
+    if (!A || !B || !C || !X || lda < m || ldb < p || ldc < m || ldx < m) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    Arena ws;
+    rs = get_workspace(*s, sylvester_workspace_bytes(m, p), ws);
+    if (rs != SIGNTRI_OK) return rs;
+    return sylvester_run(m, p, A, lda, B, ldb, C, ldc, 1.0, X, ldx, ws, static_cast<cudaStream_t>(stream));
 }
 
 signtri_status signtri_set_workspace(void *dev_ptr, size_t bytes)

@@ -69,4 +69,20 @@ size_t ph_fp64_workspace_bytes(int n, int b);
 signtri_status ph_fp64_run(int n, const double *T, int ldt, double *U, int ldu, int b,
                            Arena &ws, cudaStream_t st);
 
+// Float64 GEMM (gemm_f64.cu): C = alpha op(A) op(B) + beta C, optional upper
+// triangle only.
+signtri_status gemm_f64(bool transA, bool transB, int m, int n, int k, double alpha, const double *A, int lda,
+                        const double *B, int ldb, double beta, double *C, int ldc, bool upper, cudaStream_t st);
+
+// Parlett-Sylvester pieces (ps_fp64.cu)
+size_t sylvester_workspace_bytes(int m, int p);
+signtri_status sylvester_run(int m, int p, const double *A, int lda, const double *Bm, int ldb, const double *C,
+                             int ldc, double cscale, double *X, int ldx, Arena &ws, cudaStream_t st);
+size_t reorder_workspace_bytes(int n);
+signtri_status reorder_run(int n, const double *T, int ldt, double *Tr, int ldtr, double *Q, int ldq,
+                           long long *swaps_out, Arena &ws, cudaStream_t st);
+size_t ps_workspace_bytes(int n, long long swaps);
+signtri_status ps_fp64_run(int n, const double *T, int ldt, double *U, int ldu, int npos, long long swaps,
+                           Arena &ws, cudaStream_t st);
+
 }  // namespace signtri

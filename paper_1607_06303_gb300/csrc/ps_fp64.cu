@@ -1,0 +1,465 @@
+// ps_fp64.cu -- Parlett-Sylvester for the sign function, float64
+// (Section 2, Section 3, Section 5.1).
+//
+// With the eigenvalues grouped by sign, positives first, T~ = [T11 T12; 0 T22]
+// and sign(T~) = [I X; 0 -I] where T11 X - X T22 = 2 T12 (the off-diagonal
+// block of T~ U~ = U~ T~).  For a general order, T = Q T~ Q^T with Q
+// orthogonal from adjacent Givens swaps (Schur reordering), and
+// sign(T) = Q sign(T~) Q^T.  Three steps:
+//
+//  1. Reorder by sign.  A swap of neighbours (k, k+1) with diagonal a, c and
+//     coupling b uses the rotation G = [cs -sn; sn cs], (cs, sn) = (b, c-a)/r,
+//     r = hypot(b, c-a): G's first column is the eigenvector of c, so
+//     G^T [a b; 0 c] G = [c b; 0 a], and T <- G^T T G on rows/columns k, k+1,
+//     Q <- Q G.  Swaps of disjoint neighbour pairs commute (each rotation
+//     depends only on its own 2x2 diagonal block, and left and right
+//     multiplications commute), so the stable partition runs as odd-even
+//     transposition rounds: in round r every pair (k, k+1), k = r mod 2, with
+//     a negative above a positive is swapped at once.  The total number of
+//     swaps is k = #{i<j : t_ii < 0 < t_jj}, the minimum (Section 3).
+//  2. Triangular Sylvester solve A X - X B = C by the element recurrence
+//     (a_ii - b_jj) x_ij = c_ij - sum_{k>i} a_ik x_kj + sum_{k<j} x_ik b_kj,
+//     blocked: b x b blocks by anti-diagonal (bottom-left first), float64 block
+//     sums of the finished blocks (split along K, fixed summation order), then
+//     the recurrence inside each block.
+//  3. Back-transform: with Q = [Q1 Q2] (n x n_+, n x n_-),
+//     Q U~ Q^T = I + (Q1 X - 2 Q2) Q2^T = -I + Q1 (2 Q1^T + X Q2^T);
+//     the form with the smaller inner dimension is used, only the upper
+//     triangle is formed, the diagonal is set to sign(t_ii) exactly.
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace signtri {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int SB = 64;            // Sylvester block size
+constexpr int kSplitMax = 32;
+constexpr int kTargetCtas = 4 * 152;
+
+// --------------------------------------------------------------- reorder ---
+
+// Rotation of every pair of round r: exact swap of the 2x2 diagonal block.
+__global__ void givens_rot_kernel(const int *__restrict__ pairs, int npairs, double *__restrict__ T, int ldt,
+                                  double *__restrict__ cs, double *__restrict__ sn, int *__restrict__ act_round,
+                                  int round)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= npairs) return;
+    const int k = pairs[idx];
+    const double a = SGT_AT(T, ldt, k, k), c = SGT_AT(T, ldt, k + 1, k + 1), b = SGT_AT(T, ldt, k, k + 1);
+    const double d = c - a;
+    const double r = hypot(b, d);
+    cs[k] = b / r;
+    sn[k] = d / r;
+    SGT_AT(T, ldt, k, k) = c;
+    SGT_AT(T, ldt, k + 1, k + 1) = a;
+    act_round[k] = round;
+    act_round[k + 1] = round;
+}
+
+// Apply the rotations of round r.  blockIdx.y = pair, blockIdx.z = kind:
+//   0: rows k, k+1, columns j >= k+2 (left product; joint 2x2 update where
+//      column j starts another active pair of this round),
+//   1: rows i < k not in an active pair, columns k, k+1 (right product),
+//   2: Q, all rows, columns k, k+1 (right product).
+__global__ void givens_apply_kernel(const int *__restrict__ pairs, int n, double *__restrict__ T, int ldt,
+                                    double *__restrict__ Q, int ldq, const double *__restrict__ cs,
+                                    const double *__restrict__ sn, const int *__restrict__ act_round, int round)
+{
+    const int k = pairs[blockIdx.y];
+    const double c1 = cs[k], s1 = sn[k];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int kind = blockIdx.z;
+    if (kind == 0) {
+        const int j = k + 2 + t;
+        if (j >= n) return;
+        const bool jact = (act_round[j] == round);
+        const bool jfirst = jact && ((j & 1) == (round & 1));
+        if (jact && !jfirst) return;               // handled with its partner
+        double *x0 = &SGT_AT(T, ldt, k, j);
+        double *x1 = &SGT_AT(T, ldt, k + 1, j);
+        const double u = *x0, v = *x1;
+        const double nu = c1 * u + s1 * v;          // G^T on rows k, k+1
+        const double nv = -s1 * u + c1 * v;
+        if (!jact) {
+            *x0 = nu;
+            *x1 = nv;
+        } else {
+            const double c2 = cs[j], s2 = sn[j];
+            double *y0 = &SGT_AT(T, ldt, k, j + 1);
+            double *y1 = &SGT_AT(T, ldt, k + 1, j + 1);
+            const double up = *y0, vp = *y1;
+            const double nup = c1 * up + s1 * vp;
+            const double nvp = -s1 * up + c1 * vp;
+            *x0 = nu * c2 + nup * s2;                // then G on columns j, j+1
+            *y0 = -nu * s2 + nup * c2;
+            *x1 = nv * c2 + nvp * s2;
+            *y1 = -nv * s2 + nvp * c2;
+        }
+    } else if (kind == 1) {
+        const int i = t;
+        if (i >= k) return;
+        if (act_round[i] == round) return;          // row pair: handled in kind 0
+        double *x0 = &SGT_AT(T, ldt, i, k);
+        double *x1 = &SGT_AT(T, ldt, i, k + 1);
+        const double u = *x0, v = *x1;
+        *x0 = u * c1 + v * s1;
+        *x1 = -u * s1 + v * c1;
+    } else {
+        const int i = t;
+        if (i >= n) return;
+        double *x0 = &SGT_AT(Q, ldq, i, k);
+        double *x1 = &SGT_AT(Q, ldq, i, k + 1);
+        const double u = *x0, v = *x1;
+        *x0 = u * c1 + v * s1;
+        *x1 = -u * s1 + v * c1;
+    }
+}
+
+// dst (upper triangle, zeros below) = src; Q = I.
+__global__ void copy_upper_identity_kernel(int n, const double *__restrict__ src, int lds, double *__restrict__ dst,
+                                           int ldd, double *__restrict__ Q, int ldq)
+{
+    const int j = blockIdx.x;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        SGT_AT(dst, ldd, i, j) = (i <= j) ? SGT_AT(src, lds, i, j) : 0.0;
+        SGT_AT(Q, ldq, i, j) = (i == j) ? 1.0 : 0.0;
+    }
+}
+
+// Odd-even transposition rounds of the stable partition, from the signs:
+// flat list of the upper index k of each swapped pair, and round offsets.
+void schedule_rounds(const std::vector<double> &diag, std::vector<int> &pairs, std::vector<int> &offsets)
+{
+    const int n = (int)diag.size();
+    std::vector<signed char> s(n);
+    for (int i = 0; i < n; i++) s[i] = diag[i] > 0.0 ? 1 : -1;
+    pairs.clear();
+    offsets.assign(1, 0);
+    int lo = 0, hi = n - 1;                       // unsorted window
+    int idle = 0;
+    for (int r = 0; idle < 2; r++) {
+        while (lo < n && s[lo] > 0) lo++;         // leading positives are final
+        while (hi >= 0 && s[hi] < 0) hi--;        // trailing negatives are final
+        bool any = false;
+        const int start = std::max(0, lo - 1);
+        for (int k = start + ((start & 1) != (r & 1) ? 1 : 0); k + 1 <= hi; k += 2) {
+            if (s[k] < 0 && s[k + 1] > 0) {
+                std::swap(s[k], s[k + 1]);
+                pairs.push_back(k);
+                any = true;
+            }
+        }
+        offsets.push_back((int)pairs.size());
+        idle = any ? 0 : idle + 1;
+    }
+    while (offsets.size() > 1 && offsets[offsets.size() - 1] == offsets[offsets.size() - 2]) offsets.pop_back();
+}
+
+// ------------------------------------------------------------- Sylvester ---
+
+// Block sums of anti-diagonal s for A X - X B = C (m x p), block (I, J) with
+// I = nbr - 1 - s + J:  P = -sum_{I'>I} A[I, I'] X[I', J] + sum_{J'<J} X[I, J'] B[J', J].
+// The s K-blocks of a tile are numbered v = 0..s-1: first the row blocks
+// I' = I+1.. (the last may be partial), then the column blocks J' = 0..J-1.
+__global__ void __launch_bounds__(kThreads)
+sylv_sums_kernel(int m, int p, const double *__restrict__ A, int lda, const double *__restrict__ Bm, int ldb,
+                 const double *__restrict__ X, int ldx, int s, int nbr, int j_lo, int kc, double *__restrict__ P,
+                 size_t split_stride)
+{
+    constexpr int KT = 16;
+    __shared__ double As[KT][SB], Bs[KT][SB];
+    const int J = j_lo + blockIdx.x;
+    const int I = nbr - 1 - s + J;
+    const int split = blockIdx.y;
+    const int v0 = split * kc, v1 = min(v0 + kc, s);
+    const int r0 = I * SB, c0 = J * SB;
+    const int bi = min(SB, m - r0), bj = min(SB, p - c0);
+    const int nrow_blocks = nbr - 1 - I;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
+    for (int v = v0; v < v1; v++) {
+        const bool phase1 = v < nrow_blocks;
+        const int kb = phase1 ? (I + 1 + v) : (v - nrow_blocks);
+        const int k_base = kb * SB;
+        const int kext = phase1 ? min(SB, m - k_base) : SB;
+        for (int k0 = 0; k0 < kext; k0 += KT) {
+            for (int idx = threadIdx.x; idx < SB * KT; idx += kThreads) {
+                const int r = idx % SB, kk = idx / SB;
+                const int gk = k0 + kk;
+                double av = 0.0;
+                if (r < bi && gk < kext)
+                    av = phase1 ? -SGT_AT(A, lda, r0 + r, k_base + gk) : SGT_AT(X, ldx, r0 + r, k_base + gk);
+                As[kk][r] = av;
+            }
+            for (int idx = threadIdx.x; idx < SB * KT; idx += kThreads) {
+                const int kk = idx % KT, c = idx / KT;
+                const int gk = k0 + kk;
+                double bv = 0.0;
+                if (c < bj && gk < kext)
+                    bv = phase1 ? SGT_AT(X, ldx, k_base + gk, c0 + c) : SGT_AT(Bm, ldb, k_base + gk, c0 + c);
+                Bs[kk][c] = bv;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < KT; kk++) {
+                double a[4], b[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) { a[q] = As[kk][tx + 16 * q]; b[q] = Bs[kk][ty + 16 * q]; }
+#pragma unroll
+                for (int pp = 0; pp < 4; pp++)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) acc[pp][q] = fma(a[pp], b[q], acc[pp][q]);
+            }
+            __syncthreads();
+        }
+    }
+    double *out = P + (size_t)split * split_stride + (size_t)blockIdx.x * SB * SB;
+#pragma unroll
+    for (int pp = 0; pp < 4; pp++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) out[(tx + 16 * pp) + (ty + 16 * q) * SB] = acc[pp][q];
+}
+
+// In-block recurrence for block (I, J) of anti-diagonal s:
+//   (a_pp - b_qq) x_pq = cscale*c_pq + sums_pq - sum_{p'>p} A[p,p'] x_p'q + sum_{q'<q} x_pq' B[q',q]
+__global__ void __launch_bounds__(kThreads)
+sylv_leaf_kernel(int m, int p, const double *__restrict__ A, int lda, const double *__restrict__ Bm, int ldb,
+                 const double *__restrict__ C, int ldc, double cscale, double *__restrict__ X, int ldx, int s,
+                 int nbr, int j_lo, int nsplit, const double *__restrict__ P, size_t split_stride)
+{
+    constexpr int LD = SB + 1;
+    extern __shared__ double sm[];
+    double *As = sm;
+    double *Bs = As + SB * LD;
+    double *Xs = Bs + SB * LD;
+    const int J = j_lo + blockIdx.x;
+    const int I = nbr - 1 - s + J;
+    const int r0 = I * SB, c0 = J * SB;
+    const int bi = min(SB, m - r0), bj = min(SB, p - c0);
+    for (int idx = threadIdx.x; idx < SB * SB; idx += kThreads) {
+        const int i = idx % SB, j = idx / SB;
+        As[i + j * LD] = (i <= j && j < bi) ? SGT_AT(A, lda, r0 + i, r0 + j) : 0.0;
+        Bs[i + j * LD] = (i <= j && j < bj) ? SGT_AT(Bm, ldb, c0 + i, c0 + j) : 0.0;
+        double c = 0.0;
+        if (i < bi && j < bj) {
+            c = cscale * SGT_AT(C, ldc, r0 + i, c0 + j);
+            for (int t = 0; t < nsplit; t++) c += P[(size_t)t * split_stride + (size_t)blockIdx.x * SB * SB + i + j * SB];
+        }
+        Xs[i + j * LD] = c;
+    }
+    __syncthreads();
+    const int nsteps = bi + bj - 1;
+    for (int st = 0; st < nsteps; st++) {
+        const int plo = max(0, bi - 1 - st);
+        const int phi = min(bi - 1, bi - 1 - st + bj - 1);
+        for (int pp = plo + threadIdx.x; pp <= phi; pp += kThreads) {
+            const int q = st - (bi - 1 - pp);
+            double a = 0.0, b = 0.0;
+            for (int k = pp + 1; k < bi; k++) a = fma(As[pp + k * LD], Xs[k + q * LD], a);
+            for (int k = 0; k < q; k++) b = fma(Xs[pp + k * LD], Bs[k + q * LD], b);
+            Xs[pp + q * LD] = (Xs[pp + q * LD] - a + b) / (As[pp + pp * LD] - Bs[q + q * LD]);
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < bi * bj; idx += kThreads) {
+        const int i = idx % bi, j = idx / bi;
+        SGT_AT(X, ldx, r0 + i, c0 + j) = Xs[i + j * LD];
+    }
+}
+
+// ---------------------------------------------------------- back-transform ---
+
+__global__ void scale_copy_kernel(int rows, int cols, const double *__restrict__ src, int lds, double alpha,
+                                  bool transpose, double *__restrict__ dst, int ldd)
+{
+    const int j = blockIdx.x;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x)
+        SGT_AT(dst, ldd, i, j) = alpha * (transpose ? SGT_AT(src, lds, j, i) : SGT_AT(src, lds, i, j));
+}
+
+// Diagonal of U set to sign(t_ii) of the input, strictly lower part to 0.
+__global__ void finish_sign_kernel(int n, const double *__restrict__ T, int ldt, double *__restrict__ U, int ldu)
+{
+    const int j = blockIdx.x;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (i == j) SGT_AT(U, ldu, i, j) = SGT_AT(T, ldt, i, i) > 0.0 ? 1.0 : -1.0;
+        else if (i > j) SGT_AT(U, ldu, i, j) = 0.0;
+    }
+}
+
+// U = [I X; 0 -I] for the sorted case (X already in place).
+__global__ void sorted_blocks_kernel(int n, int npos, double *__restrict__ U, int ldu)
+{
+    const int j = blockIdx.x;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const bool in_x = (i < npos && j >= npos);
+        if (!in_x) SGT_AT(U, ldu, i, j) = (i == j) ? (j < npos ? 1.0 : -1.0) : 0.0;
+    }
+}
+
+}  // namespace
+
+size_t sylvester_workspace_bytes(int m, int p)
+{
+    if (m <= 0 || p <= 0) return 0;
+    const size_t nbr = (m + SB - 1) / SB, nbc = (p + SB - 1) / SB;
+    const size_t tiles = std::min(nbr, nbc);
+    return tiles * SB * SB * kSplitMax * sizeof(double) + 256;
+}
+
+signtri_status sylvester_run(int m, int p, const double *A, int lda, const double *Bm, int ldb, const double *C,
+                             int ldc, double cscale, double *X, int ldx, Arena &ws, cudaStream_t st)
+{
+    if (m <= 0 || p <= 0) return SIGNTRI_OK;
+    const int nbr = (m + SB - 1) / SB, nbc = (p + SB - 1) / SB;
+    const size_t split_stride = (size_t)std::min(nbr, nbc) * SB * SB;
+    double *P = static_cast<double *>(ws.take(split_stride * kSplitMax * sizeof(double)));
+    if (!P) return SIGNTRI_ERR_NO_WORKSPACE;
+    const size_t leaf_smem = 3 * (size_t)SB * (SB + 1) * sizeof(double);
+    SGT_CUDA_TRY(cudaFuncSetAttribute(sylv_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem));
+    const int nsteps = nbr + nbc - 1;
+    for (int s = 0; s < nsteps; s++) {
+        const int j_lo = std::max(0, s - (nbr - 1));
+        const int j_hi = std::min(nbc - 1, s);
+        const int ntiles = j_hi - j_lo + 1;
+        int nsplit = 0;
+        if (s > 0) {
+            const int want = (kTargetCtas + ntiles - 1) / ntiles;
+            nsplit = std::max(1, std::min(want, std::min(kSplitMax, s)));
+            const int kc = (s + nsplit - 1) / nsplit;
+            nsplit = (s + kc - 1) / kc;
+            ProfScope ps(SIGNTRI_KC_SYLV_SUMS, st);
+            sylv_sums_kernel<<<dim3(ntiles, nsplit), kThreads, 0, st>>>(m, p, A, lda, Bm, ldb, X, ldx, s, nbr, j_lo,
+                                                                       kc, P, split_stride);
+            SGT_LAUNCH_CHECK();
+        }
+        ProfScope ps(SIGNTRI_KC_SYLV_LEAF, st);
+        sylv_leaf_kernel<<<ntiles, kThreads, leaf_smem, st>>>(m, p, A, lda, Bm, ldb, C, ldc, cscale, X, ldx, s, nbr,
+                                                               j_lo, nsplit, P, split_stride);
+        SGT_LAUNCH_CHECK();
+    }
+    return SIGNTRI_OK;
+}
+
+size_t reorder_workspace_bytes(int n)
+{
+    if (n <= 0) return 0;
+    // cs, sn, act_round; the pair list is sized per call (at most n^2/4)
+    return 3 * ((size_t)n * sizeof(double) + 256);
+}
+
+signtri_status reorder_run(int n, const double *T, int ldt, double *Tr, int ldtr, double *Q, int ldq,
+                           long long *swaps_out, Arena &ws, cudaStream_t st)
+{
+    if (n <= 0) return SIGNTRI_OK;
+    double *cs = static_cast<double *>(ws.take((size_t)n * sizeof(double)));
+    double *sn = static_cast<double *>(ws.take((size_t)n * sizeof(double)));
+    int *act = static_cast<int *>(ws.take((size_t)n * sizeof(int)));
+    if (!cs || !sn || !act) return SIGNTRI_ERR_NO_WORKSPACE;
+    {
+        ProfScope ps(SIGNTRI_KC_FILL, st);
+        copy_upper_identity_kernel<<<n, 256, 0, st>>>(n, T, ldt, Tr, ldtr, Q, ldq);
+        SGT_LAUNCH_CHECK();
+    }
+    SGT_CUDA_TRY(cudaMemsetAsync(act, 0xff, (size_t)n * sizeof(int), st));
+    std::vector<double> diag(n);
+    SGT_CUDA_TRY(cudaMemcpy2DAsync(diag.data(), sizeof(double), T, ((size_t)ldt + 1) * sizeof(double), sizeof(double),
+                                   n, cudaMemcpyDeviceToHost, st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int> pairs, offsets;
+    schedule_rounds(diag, pairs, offsets);
+    if (swaps_out) *swaps_out = (long long)pairs.size();
+    if (pairs.empty()) return SIGNTRI_OK;
+    int *d_pairs = static_cast<int *>(ws.take(pairs.size() * sizeof(int)));
+    if (!d_pairs) return SIGNTRI_ERR_NO_WORKSPACE;
+    SGT_CUDA_TRY(cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    const int nrounds = (int)offsets.size() - 1;
+    for (int r = 0; r < nrounds; r++) {
+        const int off = offsets[r], np = offsets[r + 1] - offsets[r];
+        if (np == 0) continue;
+        ProfScope ps(SIGNTRI_KC_GIVENS, st);
+        givens_rot_kernel<<<(np + 127) / 128, 128, 0, st>>>(d_pairs + off, np, Tr, ldtr, cs, sn, act, r);
+        SGT_LAUNCH_CHECK();
+        givens_apply_kernel<<<dim3((n + 255) / 256, np, 3), 256, 0, st>>>(d_pairs + off, n, Tr, ldtr, Q, ldq, cs, sn,
+                                                                          act, r);
+        SGT_LAUNCH_CHECK();
+    }
+    // the pair list must stay valid until the copy above has been consumed
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIGNTRI_OK;
+}
+
+size_t ps_workspace_bytes(int n, long long swaps)
+{
+    if (n <= 0) return 0;
+    const size_t nn = (size_t)n * n * sizeof(double) + 256;
+    size_t b = sylvester_workspace_bytes(n, n) + nn /* X */;
+    if (swaps > 0) b += 2 * nn /* T~, Q */ + nn /* W */ + reorder_workspace_bytes(n) + (size_t)swaps * sizeof(int) + 256;
+    return b;
+}
+
+signtri_status ps_fp64_run(int n, const double *T, int ldt, double *U, int ldu, int npos, long long swaps,
+                           Arena &ws, cudaStream_t st)
+{
+    const int nneg = n - npos;
+    if (swaps == 0) {
+        // already grouped: T~ = T, Q = I, sign(T) = [I X; 0 -I]
+        signtri_status rs = sylvester_run(npos, nneg, T, ldt, &SGT_AT(T, ldt, npos, npos), ldt, &SGT_AT(T, ldt, 0, npos),
+                                          ldt, 2.0, &SGT_AT(U, ldu, 0, npos), ldu, ws, st);
+        if (rs != SIGNTRI_OK) return rs;
+        ProfScope ps(SIGNTRI_KC_FILL, st);
+        sorted_blocks_kernel<<<n, 256, 0, st>>>(n, npos, U, ldu);
+        SGT_LAUNCH_CHECK();
+        return SIGNTRI_OK;
+    }
+    double *Tr = static_cast<double *>(ws.take((size_t)n * n * sizeof(double)));
+    double *Q = static_cast<double *>(ws.take((size_t)n * n * sizeof(double)));
+    double *X = static_cast<double *>(ws.take((size_t)n * n * sizeof(double)));
+    double *W = static_cast<double *>(ws.take((size_t)n * n * sizeof(double)));
+    if (!Tr || !Q || !X || !W) return SIGNTRI_ERR_NO_WORKSPACE;
+    long long done = 0;
+    signtri_status rs = reorder_run(n, T, ldt, Tr, n, Q, n, &done, ws, st);
+    if (rs != SIGNTRI_OK) return rs;
+    rs = sylvester_run(npos, nneg, Tr, n, &SGT_AT(Tr, n, npos, npos), n, &SGT_AT(Tr, n, 0, npos), n, 2.0, X, npos,
+                       ws, st);
+    if (rs != SIGNTRI_OK) return rs;
+    const double *Q1 = Q;
+    const double *Q2 = &SGT_AT(Q, n, 0, npos);
+    if (nneg <= npos) {
+        // W = Q1 X - 2 Q2 (n x n_-),  U = I + W Q2^T
+        {
+            ProfScope ps(SIGNTRI_KC_FILL, st);
+            scale_copy_kernel<<<nneg, 256, 0, st>>>(n, nneg, Q2, n, -2.0, false, W, n);
+            SGT_LAUNCH_CHECK();
+        }
+        rs = gemm_f64(false, false, n, nneg, npos, 1.0, Q1, n, X, npos, 1.0, W, n, false, st);
+        if (rs != SIGNTRI_OK) return rs;
+        rs = gemm_f64(false, true, n, n, nneg, 1.0, W, n, Q2, n, 0.0, U, ldu, true, st);
+    } else {
+        // W = 2 Q1^T + X Q2^T (n_+ x n),  U = -I + Q1 W
+        {
+            ProfScope ps(SIGNTRI_KC_FILL, st);
+            scale_copy_kernel<<<n, 256, 0, st>>>(npos, n, Q1, n, 2.0, true, W, npos);
+            SGT_LAUNCH_CHECK();
+        }
+        rs = gemm_f64(false, true, npos, n, nneg, 1.0, X, npos, Q2, n, 1.0, W, npos, false, st);
+        if (rs != SIGNTRI_OK) return rs;
+        rs = gemm_f64(false, false, n, n, npos, 1.0, Q1, n, W, npos, 0.0, U, ldu, true, st);
+    }
+    if (rs != SIGNTRI_OK) return rs;
+    ProfScope ps(SIGNTRI_KC_FILL, st);
+    finish_sign_kernel<<<n, 256, 0, st>>>(n, T, ldt, U, ldu);
+    SGT_LAUNCH_CHECK();
+    return SIGNTRI_OK;
+}
+
+}  // namespace signtri

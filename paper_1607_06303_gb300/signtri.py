@@ -84,14 +84,18 @@ _SIGNATURES = {
     "signtri_kernel_class_name": (ctypes.c_char_p, [_I]),
     "signtri_probe_fp64_peak": (_I, [ctypes.POINTER(ctypes.c_double), _VP]),
     "sign_tri_noalloc": (_I, [_I, _VP, _I, _VP, _I, _VP]),
+    "signtri_reorder_by_sign": (_I, [_I, _VP, _I, _VP, _I, _VP, _I, ctypes.POINTER(ctypes.c_longlong), _VP]),
+    "signtri_sylvester": (_I, [_I, _I, _VP, _I, _VP, _I, _VP, _I, _VP, _I, _VP]),
+    "signtri_set_rates": (_I, [ctypes.c_double, ctypes.c_double]),
 }
 
 SIGNTRI_NOALLOC_MAX_N = 1024
 
 # kernel classes of the launch accounting (include/signtri.h)
 KC_SCAN, KC_FILL, KC_DIAG_LEAF, KC_BLOCK_SUMS_F64, KC_OFFDIAG_LEAF = 0, 1, 2, 3, 4
-KC_BLOCK_SUMS_TC, KC_OFFDIAG_LEAF_F32, KC_CONVERT, KC_RESIDUAL, KC_CORRECTION, KC_OTHER = 5, 6, 7, 8, 9, 10
-KC_COUNT = 11
+KC_BLOCK_SUMS_TC, KC_OFFDIAG_LEAF_MIXED, KC_CONVERT, KC_RESIDUAL, KC_CORRECTION = 5, 6, 7, 8, 9
+KC_GIVENS, KC_SYLV_SUMS, KC_SYLV_LEAF, KC_GEMM_F64, KC_OTHER = 10, 11, 12, 13, 14
+KC_COUNT = 15
 
 
 def load(path: str = LIB_PATH):
@@ -134,6 +138,22 @@ def signtri_set_cutoff(b: int) -> int:
 
 def sign_tri(n, T_ptr, ldt, U_ptr, ldu, v, stream) -> int:
     return load().sign_tri(n, T_ptr or None, ldt, U_ptr or None, ldu, int(v), stream or None)
+
+
+def signtri_reorder_by_sign(n, T_ptr, ldt, Tr_ptr, ldtr, Q_ptr, ldq, stream=None):
+    k = ctypes.c_longlong(0)
+    st = load().signtri_reorder_by_sign(n, T_ptr or None, ldt, Tr_ptr or None, ldtr, Q_ptr or None, ldq,
+                                        ctypes.byref(k), stream or None)
+    return st, k.value
+
+
+def signtri_sylvester(m, p, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, X_ptr, ldx, stream=None) -> int:
+    return load().signtri_sylvester(m, p, A_ptr or None, lda, B_ptr or None, ldb, C_ptr or None, ldc,
+                                    X_ptr or None, ldx, stream or None)
+
+
+def signtri_set_rates(gemm_flops_per_s: float, givens_flops_per_s: float) -> int:
+    return load().signtri_set_rates(float(gemm_flops_per_s), float(givens_flops_per_s))
 
 
 def sign_tri_noalloc(n, T_ptr, ldt, U_ptr, ldu, stream) -> int:
