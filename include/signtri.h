@@ -129,6 +129,19 @@ signtri_status signtri_inertia(int n, const double *T, int ldt, int *n_pos, int 
    calling host thread. */
 signtri_status signtri_get_info(signtri_info *out);
 
+/* ---- Emulated float64 product on the tensor cores --------------------------
+   C = A B (A m x k, B k x n, C m x n; device pointers, column-major) with
+   float64-level accuracy from bf16 tensor-core products: each row of A and
+   column of B is split exactly into 8 integer slices of 7 bits under a
+   power-of-two scale; the 36 slice products with s + t <= 7 are accumulated
+   in fp32 over K-chunks of at most 1024 (exact: every partial sum is an
+   integer below 2^24) and summed in double-float (fp32 hi + lo).  Error
+   below 2^-44 relative to |A| |B| entrywise (independent of k).  This is the product used for the refinement
+   residuals TU - UT and U^2 - I of the mixed variants.  Synchronous on
+   `stream`; SIGNTRI_ERR_TIMEOUT if a bounded device wait expired. */
+signtri_status signtri_gemm_emulated(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                                     double *C, int ldc, void *stream);
+
 /* ---- Building blocks of Parlett-Sylvester (Section 2, Section 5.1) -------- */
 
 /* Schur reordering by sign: Tr = Q^T T Q with Q orthogonal and Tr upper

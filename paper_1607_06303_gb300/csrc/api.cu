@@ -25,6 +25,8 @@ struct DeviceState {
     size_t user_bytes = 0;
     ScanResult *scan_dev = nullptr;
     ScanResult *scan_host = nullptr;   // pinned
+    int *err_dev = nullptr;            // device error word of bounded waits
+    int *err_host = nullptr;           // pinned
     double *stage_T = nullptr;     // device staging for sign_tri_host
     double *stage_U = nullptr;
     size_t stage_elems = 0;
@@ -51,6 +53,9 @@ signtri_status current_state(DeviceState **out)
     if (!s.scan_dev) {
         SGT_CUDA_TRY(cudaMalloc(&s.scan_dev, sizeof(ScanResult)));
         SGT_CUDA_TRY(cudaMallocHost(&s.scan_host, sizeof(ScanResult)));
+        SGT_CUDA_TRY(cudaMalloc(&s.err_dev, sizeof(int)));
+        SGT_CUDA_TRY(cudaMemset(s.err_dev, 0, sizeof(int)));
+        SGT_CUDA_TRY(cudaMallocHost(&s.err_host, sizeof(int)));
     }
     *out = &s;
     return SIGNTRI_OK;
@@ -254,6 +259,28 @@ signtri_status signtri_reorder_by_sign(int n, const double *T, int ldt, double *
     rs = get_workspace(s[0], reorder_workspace_bytes(n) + (size_t)r.swaps * sizeof(int) + 256, ws);
     if (rs != SIGNTRI_OK) return rs;
     return reorder_run(n, T, ldt, Tr, ldtr, Q, ldq, swaps, ws, st);
+}
+
+signtri_status signtri_gemm_emulated(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                                     double *C, int ldc, void *stream)
+{
+    if (m < 0 || n < 0 || k < 0) return SIGNTRI_ERR_BAD_ARG;
+    if (m == 0 || n == 0) return SIGNTRI_OK;
+    if (!A || !B || !C || lda < m || ldb < std::max(k, 1) || ldc < m) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    Arena ws;
+    rs = get_workspace(*s, emulated_gemm_workspace_bytes(m, n, k, 8), ws);
+    if (rs != SIGNTRI_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SGT_CUDA_TRY(cudaMemsetAsync(s->err_dev, 0, sizeof(int), st));
+    rs = emulated_gemm_run(m, n, k, A, lda, B, ldb, C, ldc, 8, ws, s->err_dev, st);
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaMemcpyAsync(s->err_host, s->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    return *s->err_host ? SIGNTRI_ERR_TIMEOUT : SIGNTRI_OK;
 }
 
 signtri_status signtri_sylvester(int m, int p, const double *A, int lda, const double *B, int ldb, const double *C,

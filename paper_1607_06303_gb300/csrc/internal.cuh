@@ -85,4 +85,12 @@ size_t ps_workspace_bytes(int n, long long swaps);
 signtri_status ps_fp64_run(int n, const double *T, int ldt, double *U, int ldu, int npos, long long swaps,
                            Arena &ws, cudaStream_t st);
 
+// bf16 slices and the emulated-float64 GEMM (slices.cu)
+int pad64(int x);
+signtri_status make_scales(int m, int k, const double *M, int ldm, int tri, bool rows, int nout,
+                           unsigned long long *tmp, float *scale, cudaStream_t st);
+size_t emulated_gemm_workspace_bytes(int m, int n, int k, int S);
+signtri_status emulated_gemm_run(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C,
+                                 int ldc, int S, Arena &ws, int *d_err, cudaStream_t st);
+
 }  // namespace signtri

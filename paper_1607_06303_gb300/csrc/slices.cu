@@ -1,0 +1,272 @@
+// slices.cu -- bf16 slice representations of float64 matrices for the
+// tensor-core block products (tc_gemm.cu), and the emulated-float64 GEMM.
+//
+// Two kinds of slices:
+//  * exact integer slices (error-free split in the style of Ozaki, Ogita,
+//    Oishi and Rump): with a power-of-two scale sigma_i >= max_k |m_ik| per row
+//    (or per column), r = m_ik / sigma_i in (-1, 1) is cut into S pieces of
+//    7 bits, q_s = trunc(128 r_s), r_{s+1} = 128 r_s - q_s, so that
+//    m_ik = sigma_i sum_s q_s 2^{-7(s+1)} + O(sigma_i 2^{-7S}); every q_s is an
+//    integer of magnitude <= 127, exact in bf16;
+//  * rounding splits: x_0 = bf16(m), x_1 = bf16(m - x_0), x_2 = bf16(m - x_0 - x_1)
+//    (unit scale), for products accurate to ~2^-8S.
+// Slices are stored K-contiguous: "row" slices R[s][i][k] of an m x k matrix
+// (the A operand) and "column" slices C[s][j][k] of a k x n matrix (the B
+// operand), rows padded to a multiple of 64 and K to the pitch, with zeros.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace signtri {
+
+namespace {
+
+constexpr int TS = 32;   // transpose tile
+
+// max |m_ik| over the selected part (tri: 1 = strictly upper) of each row
+// (rows = true) or column, per 32 x 32 tile with a shared-memory reduction,
+// then atomicMax on the float64 bit pattern (values are >= 0, so the bit
+// patterns order like the values).
+__global__ void absmax_kernel(int m, int k, const double *__restrict__ M, int ldm, int tri, bool rows,
+                              unsigned long long *__restrict__ out)
+{
+    __shared__ double tile[TS][TS + 1];
+    const int i0 = blockIdx.y * TS, j0 = blockIdx.x * TS;
+    for (int y = threadIdx.y; y < TS; y += blockDim.y) {
+        const int i = i0 + threadIdx.x, j = j0 + y;
+        double v = 0.0;
+        if (i < m && j < k && (tri == 0 || i < j)) v = fabs(SGT_AT(M, ldm, i, j));
+        tile[threadIdx.x][y] = v;
+    }
+    __syncthreads();
+    if (threadIdx.y == 0) {
+        double best = 0.0;
+        const int line = threadIdx.x;
+        for (int t = 0; t < TS; t++) best = fmax(best, rows ? tile[line][t] : tile[t][line]);
+        const int g = (rows ? i0 : j0) + line;
+        if (best > 0.0 && g < (rows ? m : k)) atomicMax(&out[g], (unsigned long long)__double_as_longlong(best));
+    }
+}
+
+// power-of-two scale 2^e with max < 2^e (frexp exponent); 1 for an all-zero line
+__global__ void pow2_scale_kernel(int n, const unsigned long long *__restrict__ maxbits, float *__restrict__ scale)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double mx = __longlong_as_double((long long)maxbits[i]);
+    int e = 0;
+    if (mx > 0.0) {
+        frexp(mx, &e);
+        e = max(e, -120);
+    }
+    scale[i] = ldexpf(1.0f, e);
+}
+
+__device__ __forceinline__ void exact_slices(double x, double inv_scale, int S, float *q)
+{
+    double r = x * inv_scale;            // exact (power of two), |r| < 1
+    for (int s = 0; s < S; s++) {
+        r *= 128.0;
+        const double t = trunc(r);
+        q[s] = (float)t;
+        r -= t;
+    }
+}
+
+__device__ __forceinline__ void round_slices(double x, int S, float *q)
+{
+    double r = x;
+    for (int s = 0; s < S; s++) {
+        const __nv_bfloat16 b = __double2bfloat16(r);
+        const double bd = (double)__bfloat162float(b);
+        q[s] = (float)bd;
+        r -= bd;
+    }
+}
+
+// Row slices of an m x k column-major matrix: R[s][i][kk] for i < m_pad,
+// kk < k_pad.  Tiled transpose through shared memory.  tri: 0 = all entries,
+// 1 = strictly upper (i < kk) only.  scale == nullptr: rounding split.
+__global__ void row_slices_kernel(int m, int k, const double *__restrict__ M, int ldm, int tri, int S,
+                                  const float *__restrict__ scale, __nv_bfloat16 *__restrict__ R, int rows_pad,
+                                  int ldr)
+{
+    __shared__ double tile[TS][TS + 1];
+    const int i0 = blockIdx.y * TS, k0 = blockIdx.x * TS;
+    for (int y = threadIdx.y; y < TS; y += blockDim.y) {     // y: column offset
+        const int kk = k0 + y, i = i0 + threadIdx.x;
+        double v = 0.0;
+        if (i < m && kk < k && (tri == 0 || i < kk)) v = SGT_AT(M, ldm, i, kk);
+        tile[threadIdx.x][y] = v;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < TS; y += blockDim.y) {     // y: row offset
+        const int i = i0 + y, kk = k0 + threadIdx.x;
+        if (i >= rows_pad || kk >= ldr) continue;
+        const double v = tile[y][threadIdx.x];
+        float q[8];
+        if (scale) exact_slices(v, i < m ? 1.0 / (double)scale[i] : 1.0, S, q);
+        else round_slices(v, S, q);
+        for (int s = 0; s < S; s++) R[((size_t)s * rows_pad + i) * ldr + kk] = __float2bfloat16_rn(q[s]);
+    }
+}
+
+// Column slices of a k x n column-major matrix: C[s][j][kk] (same order as
+// the source, no transpose).  tri: 1 = strictly upper (kk < j) only.
+__global__ void col_slices_kernel(int k, int n, const double *__restrict__ M, int ldm, int tri, int S,
+                                  const float *__restrict__ scale, __nv_bfloat16 *__restrict__ C, int rows_pad,
+                                  int ldc)
+{
+    const int j = blockIdx.y;
+    const int kk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kk >= ldc) return;
+    double v = 0.0;
+    if (j < n && kk < k && (tri == 0 || kk < j)) v = SGT_AT(M, ldm, kk, j);
+    float q[8];
+    if (scale) exact_slices(v, j < n ? 1.0 / (double)scale[j] : 1.0, S, q);
+    else round_slices(v, S, q);
+    for (int s = 0; s < S; s++) C[((size_t)s * rows_pad + j) * ldc + kk] = __float2bfloat16_rn(q[s]);
+}
+
+// C (m x n) from the top-left / top-right quadrants of the job outputs.
+__global__ void gather_gemm_kernel(int m, int n, const double *__restrict__ out, int ntj, double *__restrict__ C,
+                                   int ldc)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    if (j >= n || i >= m) return;
+    const int I = i / 64, J2 = j / 128, jj = j % 128;
+    const size_t slot = (size_t)I * ntj + J2;
+    const int quad = jj < 64 ? 0 : 1;
+    SGT_AT(C, ldc, i, j) = out[slot * 16384 + (size_t)quad * 4096 + (i % 64) + (size_t)(jj % 64) * 64];
+}
+
+}  // namespace
+
+int pad64(int x) { return (x + 63) / 64 * 64; }
+
+signtri_status make_scales(int m, int k, const double *M, int ldm, int tri, bool rows, int nout,
+                           unsigned long long *tmp, float *scale, cudaStream_t st)
+{
+    SGT_CUDA_TRY(cudaMemsetAsync(tmp, 0, (size_t)nout * sizeof(unsigned long long), st));
+    {
+        ProfScope ps(SIGNTRI_KC_CONVERT, st);
+        dim3 grid((k + TS - 1) / TS, (m + TS - 1) / TS), block(TS, 8);
+        absmax_kernel<<<grid, block, 0, st>>>(m, k, M, ldm, tri, rows, tmp);
+        SGT_LAUNCH_CHECK();
+        pow2_scale_kernel<<<(nout + 255) / 256, 256, 0, st>>>(nout, tmp, scale);
+        SGT_LAUNCH_CHECK();
+    }
+    return SIGNTRI_OK;
+}
+
+signtri_status make_row_slices(int m, int k, const double *M, int ldm, int tri, int S, const float *scale,
+                               __nv_bfloat16 *R, int rows_pad, int ldr, cudaStream_t st)
+{
+    if (S > 8) return SIGNTRI_ERR_BAD_ARG;
+    dim3 grid((ldr + TS - 1) / TS, (rows_pad + TS - 1) / TS), block(TS, 8);
+    ProfScope ps(SIGNTRI_KC_CONVERT, st);
+    row_slices_kernel<<<grid, block, 0, st>>>(m, k, M, ldm, tri, S, scale, R, rows_pad, ldr);
+    SGT_LAUNCH_CHECK();
+    return SIGNTRI_OK;
+}
+
+signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, int S, const float *scale,
+                               __nv_bfloat16 *C, int rows_pad, int ldc, cudaStream_t st)
+{
+    if (S > 8) return SIGNTRI_ERR_BAD_ARG;
+    dim3 grid((ldc + 255) / 256, rows_pad);
+    ProfScope ps(SIGNTRI_KC_CONVERT, st);
+    col_slices_kernel<<<grid, 256, 0, st>>>(k, n, M, ldm, tri, S, scale, C, rows_pad, ldc);
+    SGT_LAUNCH_CHECK();
+    return SIGNTRI_OK;
+}
+
+// Exact-split pair list: slices s, t with s + t <= S - 1, weights
+// 2^{-7(s+t+2)}, in order of decreasing weight.
+TcPairs ozaki_pairs(int S)
+{
+    TcPairs p;
+    std::memset(&p, 0, sizeof(p));
+    for (int g = 0; g < S; g++)
+        for (int s = 0; s <= g; s++) {
+            p.s[p.n] = s;
+            p.t[p.n] = g - s;
+            p.w[p.n] = ldexpf(1.0f, -7 * (g + 2));
+            p.n++;
+        }
+    return p;
+}
+
+// Rounding-split pair list: s + t <= S - 1, unit weights.
+TcPairs split_pairs(int S)
+{
+    TcPairs p;
+    std::memset(&p, 0, sizeof(p));
+    for (int g = 0; g < S; g++)
+        for (int s = 0; s <= g; s++) {
+            p.s[p.n] = s;
+            p.t[p.n] = g - s;
+            p.w[p.n] = 1.0f;
+            p.n++;
+        }
+    return p;
+}
+
+size_t emulated_gemm_workspace_bytes(int m, int n, int k, int S)
+{
+    const size_t mp = pad64(m), np = (size_t)(n + 127) / 128 * 128, kp = pad64(k);
+    const size_t jobs = (mp / 64) * (np / 128);
+    return (size_t)S * (mp + np) * kp * 2 + (mp + np) * 12 + jobs * (sizeof(TcJob) + 16384 * 8) + sizeof(TcPairs) +
+           64 + 16 * 256;
+}
+
+signtri_status emulated_gemm_run(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C,
+                                 int ldc, int S, Arena &ws, int *d_err, cudaStream_t st)
+{
+    if (m <= 0 || n <= 0) return SIGNTRI_OK;
+    const int mp = pad64(m), np = (n + 127) / 128 * 128, kp = pad64(std::max(k, 1));
+    const int ntI = mp / 64, ntJ = np / 128, njobs = ntI * ntJ;
+    auto *AR = static_cast<__nv_bfloat16 *>(ws.take((size_t)S * mp * kp * 2));
+    auto *BC = static_cast<__nv_bfloat16 *>(ws.take((size_t)S * np * kp * 2));
+    auto *sa = static_cast<float *>(ws.take((size_t)mp * 4));
+    auto *sb = static_cast<float *>(ws.take((size_t)np * 4));
+    auto *tmpa = static_cast<unsigned long long *>(ws.take((size_t)mp * 8));
+    auto *tmpb = static_cast<unsigned long long *>(ws.take((size_t)np * 8));
+    auto *jobs = static_cast<TcJob *>(ws.take((size_t)njobs * sizeof(TcJob)));
+    auto *out = static_cast<double *>(ws.take((size_t)njobs * 16384 * 8));
+    auto *dp = static_cast<TcPairs *>(ws.take(sizeof(TcPairs)));
+    if (!AR || !BC || !sa || !sb || !tmpa || !tmpb || !jobs || !out || !dp) return SIGNTRI_ERR_NO_WORKSPACE;
+    signtri_status rs;
+    if ((rs = make_scales(m, k, A, lda, 0, true, mp, tmpa, sa, st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_scales(k, n, B, ldb, 0, false, np, tmpb, sb, st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_row_slices(m, k, A, lda, 0, S, sa, AR, mp, kp, st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_col_slices(k, n, B, ldb, 0, S, sb, BC, np, kp, st)) != SIGNTRI_OK) return rs;
+    std::vector<TcJob> hj(njobs);
+    for (int I = 0; I < ntI; I++)
+        for (int J = 0; J < ntJ; J++) {
+            TcJob &j = hj[I * ntJ + J];
+            j.rt = I * 64; j.rb = I * 64; j.cl = J * 128; j.cr = J * 128 + 64;
+            j.kb0 = 0; j.kb1 = kp / 64; j.slot = I * ntJ + J; j.pad = 0;
+        }
+    const TcPairs pairs = ozaki_pairs(S);
+    SGT_CUDA_TRY(cudaMemcpyAsync(jobs, hj.data(), hj.size() * sizeof(TcJob), cudaMemcpyHostToDevice, st));
+    SGT_CUDA_TRY(cudaMemcpyAsync(dp, &pairs, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
+    TcSource top{AR, S, mp, kp, kp, sa}, left{BC, S, np, kp, kp, sb}, right{BC, S, np, kp, kp, sb};
+    rs = tc_blocksums(top, top, left, right, jobs, njobs, pairs, dp, 16, out, d_err, SIGNTRI_KC_RESIDUAL, st);
+    if (rs != SIGNTRI_OK) return rs;
+    {
+        ProfScope ps(SIGNTRI_KC_OTHER, st);
+        gather_gemm_kernel<<<dim3((n + 255) / 256, m), 256, 0, st>>>(m, n, out, ntJ, C, ldc);
+        SGT_LAUNCH_CHECK();
+    }
+    // the host job table and pair list were copied from pageable memory
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIGNTRI_OK;
+}
+
+}  // namespace signtri

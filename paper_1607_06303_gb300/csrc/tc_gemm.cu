@@ -1,0 +1,436 @@
+// tc_gemm.cu -- block products on the 5th-generation tensor cores (tcgen05).
+//
+// One CTA computes one 128 x 128 product tile D = A B^T over a K range, with
+// A = [A_top; A_bot] (two 64-row panels) and B = [B_left; B_right] (two
+// 64-row panels), every panel K-contiguous in global memory and loaded by TMA
+// (128-byte swizzle).  The four 64 x 64 quadrants of D are four different
+// products, e.g. for the Parlett-Higham block sums with A = [U_I.; T_I.] and
+// B = [T_.J^T; U_.J^T]:  D_TL = U T,  D_TR = U U,  D_BR = T U.
+//
+// Operands are bf16 "slices": a float64 matrix is written as a sum of S bf16
+// matrices (plain rounding, a hi/lo split, or integer slices scaled per row
+// for an exact split), and D = sum over a list of slice pairs (s, t) of
+// weight(s,t) * A_s B_t.  Each (pair, K-chunk) unit is accumulated in fp32 in
+// TMEM (kind::f16, M = 128, N = 128) and then added into a double-float
+// (fp32 hi + fp32 lo) accumulator in the epilogue registers.  With integer
+// slices of 7 bits and K-chunks of at most 1024, every fp32 unit sum is an
+// integer below 2^24 and therefore exact, which makes the emulated product
+// accurate to the split (about 2^-48 relative to |A||B| with 7 slices).
+//
+// Warp roles (576 threads): warp 0 issues TMA loads into a 4-stage ring,
+// warp 1 issues the MMAs (one thread) into 3 TMEM buffers of 128 columns,
+// warps 2..17 drain TMEM (four warps per 32-lane quadrant, 32 columns each)
+// and keep the fp32 hi parts of the accumulators in the 4th 128-column TMEM
+// buffer and the lo parts in registers.
+// Every mbarrier wait is bounded; on expiry the CTA records an error and
+// returns after draining what it issued.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace signtri {
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kTcThreads = 576;            // 2 control warps + 16 epilogue warps
+constexpr int kStageBytes = 32768;          // A 128x64 + B 128x64 bf16
+constexpr int kBufs = 3;                    // TMEM accumulator buffers of 128 columns; the 4th holds hi
+constexpr long long kWaitCycles = 4000000000LL;   // about 2 s at 2 GHz
+
+// Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A and B bf16
+// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait for the phase of parity `parity`; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    const uint32_t addr = smem_u32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// K-major, 128-byte swizzle smem matrix descriptor: start >> 4, LBO 16 B
+// (unused for this layout), SBO 1024 B (8 rows x 128 B), version 1 (bit 46),
+// layout SWIZZLE_128B (2 at bit 61).
+__device__ __forceinline__ uint64_t smem_desc(const void *p)
+{
+    const uint64_t a = (smem_u32(p) & 0x3FFFFu) >> 4;
+    return a | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Error-free addition of a into (hi, lo): Knuth's two-sum.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float a)
+{
+    const float s = __fadd_rn(hi, a);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(a, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_constant__ CUtensorMap mBot,
+                   const __grid_constant__ CUtensorMap mLeft, const __grid_constant__ CUtensorMap mRight,
+                   int rowsA, int rowsB, const TcJob *__restrict__ jobs, const TcPairs *__restrict__ pairs_g, int chunk_kb,
+                   const float *__restrict__ sTop, const float *__restrict__ sBot, const float *__restrict__ sLeft,
+                   const float *__restrict__ sRight, double *__restrict__ out, int *__restrict__ err)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+    uint64_t *empty = full + kStages;
+    uint64_t *tfull = empty + kStages;
+    uint64_t *tempty = tfull + 4;
+    uint64_t *done_bar = tempty + 4;
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(done_bar + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const TcJob job = jobs[blockIdx.x];
+    const int nkb = job.kb1 - job.kb0;
+    const int nchunks = nkb > 0 ? (nkb + chunk_kb - 1) / chunk_kb : 0;
+    const TcPairs &pairs = *pairs_g;
+    const int nunits = pairs.n * nchunks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; s++) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < kBufs; b++) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 16); }
+        mbar_init(done_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_holder))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+
+    if (warp == 0) {
+        if (lane == 0 && nunits > 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&mTop) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&mBot) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&mLeft) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&mRight) : "memory");
+            int stage = 0;
+            uint32_t phase = 0;
+            long long issued = 0;
+            bool ok = true;
+            for (int u = 0; u < nunits && ok; u++) {
+                const int p = u / nchunks, c = u % nchunks;
+                const int ya = pairs.s[p] * rowsA, yb = pairs.t[p] * rowsB;
+                const int kbs = job.kb0 + c * chunk_kb, kbe = min(kbs + chunk_kb, job.kb1);
+                for (int kb = kbs; kb < kbe; kb++) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) { ok = false; break; }
+                    mbar_expect_tx(&full[stage], kStageBytes);
+                    unsigned char *a = smem + stage * kStageBytes;
+                    unsigned char *b = a + kStageBytes / 2;
+                    const int x = kb * 64;
+                    tma_load_2d(a, &mTop, &full[stage], x, ya + job.rt);
+                    tma_load_2d(a + 8192, &mBot, &full[stage], x, ya + job.rb);
+                    tma_load_2d(b, &mLeft, &full[stage], x, yb + job.cl);
+                    tma_load_2d(b + 8192, &mRight, &full[stage], x, yb + job.cr);
+                    issued++;
+                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                }
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                atomicExch(err, 1);
+                // drain: wait (bounded) for the loads of the last stages issued
+                const long long tail = issued < kStages ? issued : kStages;
+                for (long long i = 0; i < tail; i++) {
+                    if (stage == 0) { stage = kStages - 1; phase ^= 1; } else stage--;
+                    const uint32_t a = smem_u32(&full[stage]);
+                    const long long t0 = clock64();
+                    while (clock64() - t0 < kWaitCycles) {
+                        uint32_t done;
+                        asm volatile(
+                            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                            " selp.u32 %0, 1, 0, p;\n}\n"
+                            : "=r"(done)
+                            : "r"(a), "r"(phase)
+                            : "memory");
+                        if (done) break;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && nunits > 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int u = 0; u < nunits && ok; u++) {
+                const int buf = u % kBufs;
+                const uint32_t tphase = (u / kBufs) & 1;
+                if (!mbar_wait(&tempty[buf], tphase ^ 1, abort_flag)) { ok = false; break; }
+                fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(buf * 128);
+                const int c = u % nchunks;
+                const int kbs = job.kb0 + c * chunk_kb, kbe = min(kbs + chunk_kb, job.kb1);
+                for (int kb = kbs; kb < kbe; kb++) {
+                    if (!mbar_wait(&full[stage], phase, abort_flag)) { ok = false; break; }
+                    fence_after();
+                    unsigned char *a = smem + stage * kStageBytes;
+                    const uint64_t ad = smem_desc(a), bd = smem_desc(a + kStageBytes / 2);
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (kb > kbs || k > 0) ? 1u : 0u);
+                    mma_commit(&empty[stage]);
+                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                }
+                if (!ok) break;
+                mma_commit(&tfull[buf]);
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                atomicExch(err, 1);
+            }
+            // arrives once every MMA issued by this thread has completed
+            mma_commit(done_bar);
+        }
+    } else {
+        const int q = warp & 3;                 // TMEM lane quadrant this warp may read
+        const int cg = (warp - 2) >> 2;         // 32-column group 0..3
+        float lo[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) lo[i] = 0.f;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
+        const uint32_t taddr_hi = lane_base + (uint32_t)(kBufs * 128 + cg * 32);
+        bool ok = true;
+        for (int u = 0; u < nunits && ok; u++) {
+            const int buf = u % kBufs;
+            const uint32_t tphase = (u / kBufs) & 1;
+            if (!mbar_wait(&tfull[buf], tphase, abort_flag)) { ok = false; break; }
+            fence_after();
+            const float w = pairs.w[u / nchunks];
+            const uint32_t taddr = lane_base + (uint32_t)(buf * 128 + cg * 32);
+#pragma unroll
+            for (int cc = 0; cc < 32; cc += 8) {
+                float v[8], h[8];
+                tmem_ld8(taddr + cc, v);
+                if (u == 0) {
+#pragma unroll
+                    for (int i = 0; i < 8; i++) h[i] = __fmul_rn(v[i], w);
+                } else {
+                    tmem_ld8(taddr_hi + cc, h);
+#pragma unroll
+                    for (int i = 0; i < 8; i++) df_add(h[i], lo[cc + i], __fmul_rn(v[i], w));
+                }
+                tmem_st8(taddr_hi + cc, h);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicExch(err, 1);
+        } else {
+            const int row = 32 * q + lane;
+            const int r = row & 63;
+            const bool bottom = row >= 64;
+            const int half = cg >> 1;
+            const int c0 = (cg & 1) * 32;           // first column inside the quadrant
+            double srow = 1.0;
+            if (bottom) { if (sBot) srow = sBot[job.rb + r]; }
+            else if (sTop) srow = sTop[job.rt + r];
+            const float *scol = half ? sRight : sLeft;
+            const int cbase = (half ? job.cr : job.cl) + c0;
+            double *o = out + (size_t)job.slot * 16384 + (size_t)((bottom ? 2 : 0) + half) * 4096 + (size_t)c0 * 64;
+#pragma unroll
+            for (int cc = 0; cc < 32; cc += 8) {
+                float h[8];
+                if (nunits > 0) tmem_ld8(taddr_hi + cc, h);
+                else {
+#pragma unroll
+                    for (int i = 0; i < 8; i++) h[i] = 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < 8; i++) {
+                    const double sc = scol ? (double)scol[cbase + cc + i] : 1.0;
+                    o[r + (cc + i) * 64] = ((double)h[i] + (double)lo[cc + i]) * srow * sc;
+                }
+            }
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        // done_bar completes once, when all MMAs of this CTA have finished
+        if (nunits > 0) {
+            const uint32_t a = smem_u32(done_bar);
+            const long long t0 = clock64();
+            while (clock64() - t0 < kWaitCycles) {
+                uint32_t done;
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                    : "=r"(done)
+                    : "r"(a), "r"(0u)
+                    : "memory");
+                if (done) break;
+            }
+        }
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+signtri_status get_encoder()
+{
+    if (g_encode) return SIGNTRI_OK;
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return SIGNTRI_ERR_CUDA;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return SIGNTRI_OK;
+}
+
+// 2-D map over `rows` rows of `cols` bf16 (cols contiguous, row pitch ld
+// elements), box 64 x 64, 128-byte swizzle, zero fill out of bounds.
+signtri_status make_map(CUtensorMap *m, const __nv_bfloat16 *base, long long rows, long long cols, long long ld)
+{
+    if (((uintptr_t)base & 15) || (ld * 2) % 16) return SIGNTRI_ERR_BAD_ARG;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint32_t box[2] = {64, 64};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims, strides,
+                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SIGNTRI_OK : SIGNTRI_ERR_CUDA;
+}
+
+}  // namespace
+
+size_t tc_smem_bytes() { return (size_t)kStages * kStageBytes + 1024 + 256; }
+
+signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSource &left, const TcSource &right,
+                            const TcJob *d_jobs, int njobs, const TcPairs &pairs, const TcPairs *d_pairs, int chunk_kb,
+                            double *out, int *d_err, int kernel_class, cudaStream_t st)
+{
+    if (njobs <= 0) return SIGNTRI_OK;
+    if (pairs.n <= 0 || pairs.n > kTcMaxPairs || chunk_kb <= 0 || !d_pairs) return SIGNTRI_ERR_BAD_ARG;
+    signtri_status rs = get_encoder();
+    if (rs != SIGNTRI_OK) return rs;
+    CUtensorMap mt, mb, ml, mr;
+    if ((rs = make_map(&mt, top.base, (long long)top.nslices * top.rows, top.cols, top.ld)) != SIGNTRI_OK) return rs;
+    if ((rs = make_map(&mb, bot.base, (long long)bot.nslices * bot.rows, bot.cols, bot.ld)) != SIGNTRI_OK) return rs;
+    if ((rs = make_map(&ml, left.base, (long long)left.nslices * left.rows, left.cols, left.ld)) != SIGNTRI_OK) return rs;
+    if ((rs = make_map(&mr, right.base, (long long)right.nslices * right.rows, right.cols, right.ld)) != SIGNTRI_OK)
+        return rs;
+    if (top.rows != bot.rows || left.rows != right.rows) return SIGNTRI_ERR_BAD_ARG;
+    const size_t smem = tc_smem_bytes();
+    SGT_CUDA_TRY(cudaFuncSetAttribute(tc_blocksum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ProfScope ps(kernel_class, st);
+    tc_blocksum_kernel<<<njobs, kTcThreads, smem, st>>>(mt, mb, ml, mr, top.rows, left.rows, d_jobs, d_pairs, chunk_kb,
+                                                        top.scale, bot.scale, left.scale, right.scale, out, d_err);
+    SGT_LAUNCH_CHECK();
+    return SIGNTRI_OK;
+}
+
+}  // namespace signtri

@@ -87,6 +87,7 @@ _SIGNATURES = {
     "signtri_reorder_by_sign": (_I, [_I, _VP, _I, _VP, _I, _VP, _I, ctypes.POINTER(ctypes.c_longlong), _VP]),
     "signtri_sylvester": (_I, [_I, _I, _VP, _I, _VP, _I, _VP, _I, _VP, _I, _VP]),
     "signtri_set_rates": (_I, [ctypes.c_double, ctypes.c_double]),
+    "signtri_gemm_emulated": (_I, [_I, _I, _I, _VP, _I, _VP, _I, _VP, _I, _VP]),
 }
 
 SIGNTRI_NOALLOC_MAX_N = 1024
@@ -150,6 +151,11 @@ def signtri_reorder_by_sign(n, T_ptr, ldt, Tr_ptr, ldtr, Q_ptr, ldq, stream=None
 def signtri_sylvester(m, p, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, X_ptr, ldx, stream=None) -> int:
     return load().signtri_sylvester(m, p, A_ptr or None, lda, B_ptr or None, ldb, C_ptr or None, ldc,
                                     X_ptr or None, ldx, stream or None)
+
+
+def signtri_gemm_emulated(m, n, k, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, stream=None) -> int:
+    return load().signtri_gemm_emulated(m, n, k, A_ptr or None, lda, B_ptr or None, ldb, C_ptr or None, ldc,
+                                        stream or None)
 
 
 def signtri_set_rates(gemm_flops_per_s: float, givens_flops_per_s: float) -> int:
