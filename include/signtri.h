@@ -99,6 +99,14 @@ signtri_status signtri_set_workspace(void *dev_ptr, size_t bytes);
    Givens reorder rounds.  Values <= 0 restore the defaults. */
 signtri_status signtri_set_rates(double gemm_flops_per_s, double givens_flops_per_s);
 
+/* Refinement of the mixed variants: stop when ||TU-UT||_F/(||T||_F||U||_F)
+   and ||U^2-I||_F/||U||_F^2 are both <= tol (default 1e-13; tol <= 0
+   restores it), or fall back to SIGNTRI_PH_FP64 after max_steps correction
+   steps or when a step does not reduce the larger residual tenfold
+   (max_steps < 0: 3 for SIGNTRI_PH_MIXED_TF32, 8 for SIGNTRI_PH_MIXED_BF16).
+   Process-wide setting. */
+signtri_status signtri_set_refinement(double tol, int max_steps);
+
 /* Leaf (recursion cutoff) size b of Parlett-Higham: the order of the diagonal
    and off-diagonal blocks solved element by element (Section 6 uses 16).
    b in {16, 32, 64}; 0 restores the default.  Process-wide setting. */

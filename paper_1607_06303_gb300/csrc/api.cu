@@ -27,6 +27,7 @@ struct DeviceState {
     ScanResult *scan_host = nullptr;   // pinned
     int *err_dev = nullptr;            // device error word of bounded waits
     int *err_host = nullptr;           // pinned
+    double *norms_host = nullptr;      // pinned, refinement norms
     double *stage_T = nullptr;     // device staging for sign_tri_host
     double *stage_U = nullptr;
     size_t stage_elems = 0;
@@ -40,6 +41,11 @@ constexpr double kDefaultGemmRate = 1.0e12;
 constexpr double kDefaultGivensRate = 0.35e12;
 double g_rate_gemm = kDefaultGemmRate;
 double g_rate_givens = kDefaultGivensRate;
+// stopping tolerance of the mixed variants on ||TU-UT||_F/(||T||_F||U||_F)
+// and ||U^2-I||_F/||U||_F^2
+constexpr double kDefaultMixedTol = 1e-13;
+double g_mixed_tol = kDefaultMixedTol;
+int g_mixed_max_steps = -1;   // < 0: per-variant default
 thread_local signtri_info g_info;
 
 bool valid_variant(int v) { return v >= SIGNTRI_AUTO && v <= SIGNTRI_PH_MIXED_BF16; }
@@ -56,6 +62,7 @@ signtri_status current_state(DeviceState **out)
         SGT_CUDA_TRY(cudaMalloc(&s.err_dev, sizeof(int)));
         SGT_CUDA_TRY(cudaMemset(s.err_dev, 0, sizeof(int)));
         SGT_CUDA_TRY(cudaMallocHost(&s.err_host, sizeof(int)));
+        SGT_CUDA_TRY(cudaMallocHost(&s.norms_host, 8 * sizeof(double)));
     }
     *out = &s;
     return SIGNTRI_OK;
@@ -97,9 +104,12 @@ size_t workspace_need(int n, signtri_variant v, int cutoff, long long swaps)
     if (swaps < 0) swaps = (long long)n * n / 4;
     switch (v) {
     case SIGNTRI_PH_FP64:
+        return ph_fp64_workspace_bytes(n, cutoff);
     case SIGNTRI_PH_MIXED_TF32:
     case SIGNTRI_PH_MIXED_BF16:
-        return ph_fp64_workspace_bytes(n, cutoff);
+        // the float64 fallback reuses the same memory
+        return std::max(mixed_workspace_bytes(n, v == SIGNTRI_PH_MIXED_TF32 ? 3 : 1),
+                        ph_fp64_workspace_bytes(n, cutoff));
     case SIGNTRI_PS_FP64:
         return ps_workspace_bytes(n, swaps);
     case SIGNTRI_AUTO:
@@ -155,6 +165,32 @@ signtri_status run_variant(int n, const double *T, int ldt, double *U, int ldu, 
         return ph_fp64_run(n, T, ldt, U, ldu, b, ws, st);
     case SIGNTRI_PS_FP64:
         return ps_fp64_run(n, T, ldt, U, ldu, r.n_pos, r.swaps, ws, st);
+    case SIGNTRI_PH_MIXED_TF32:
+    case SIGNTRI_PH_MIXED_BF16: {
+        const int S = (v == SIGNTRI_PH_MIXED_TF32) ? 3 : 1;
+        MixedParams prm{g_mixed_tol, g_mixed_max_steps >= 0 ? g_mixed_max_steps : (S == 3 ? 3 : 8), 10.0};
+        MixedReport rep{};
+        SGT_CUDA_TRY(cudaMemsetAsync(s.err_dev, 0, sizeof(int), st));
+        rs = mixed_run(n, T, ldt, U, ldu, S, prm, rep, ws, s.err_dev, s.norms_host, st);
+        if (rs != SIGNTRI_OK) return rs;
+        SGT_CUDA_TRY(cudaMemcpyAsync(s.err_host, s.err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SGT_CUDA_TRY(cudaStreamSynchronize(st));
+        if (*s.err_host) return SIGNTRI_ERR_TIMEOUT;
+        g_info.refine_steps = rep.steps;
+        g_info.resid_commute = rep.resid_commute;
+        g_info.resid_involution = rep.resid_involution;
+        g_info.cutoff = 64;
+        if (rep.fallback) {
+            // the residual did not contract: plain float64 path
+            g_info.variant = SIGNTRI_PH_FP64;
+            g_info.cutoff = b;
+            Arena ws2;
+            rs = get_workspace(s, ph_fp64_workspace_bytes(n, b), ws2);
+            if (rs != SIGNTRI_OK) return rs;
+            return ph_fp64_run(n, T, ldt, U, ldu, b, ws2, st);
+        }
+        return SIGNTRI_OK;
+    }
     default:
         return SIGNTRI_ERR_UNSUPPORTED;
     }
@@ -234,6 +270,14 @@ signtri_status signtri_set_rates(double gemm_flops_per_s, double givens_flops_pe
     std::lock_guard<std::mutex> lk(g_mu);
     g_rate_gemm = gemm_flops_per_s > 0 ? gemm_flops_per_s : kDefaultGemmRate;
     g_rate_givens = givens_flops_per_s > 0 ? givens_flops_per_s : kDefaultGivensRate;
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_set_refinement(double tol, int max_steps)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_mixed_tol = tol > 0 ? tol : kDefaultMixedTol;
+    g_mixed_max_steps = max_steps;
     return SIGNTRI_OK;
 }
 

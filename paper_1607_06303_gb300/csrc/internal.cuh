@@ -66,6 +66,7 @@ int current_cutoff();
 
 // Recursive Parlett-Higham, float64 (ph_fp64.cu)
 size_t ph_fp64_workspace_bytes(int n, int b);
+signtri_status diag_leaves_f64(int n, const double *T, int ldt, double *U, int ldu, int b, cudaStream_t st);
 signtri_status ph_fp64_run(int n, const double *T, int ldt, double *U, int ldu, int b,
                            Arena &ws, cudaStream_t st);
 
@@ -92,5 +93,20 @@ signtri_status make_scales(int m, int k, const double *M, int ldm, int tri, bool
 size_t emulated_gemm_workspace_bytes(int m, int n, int k, int S);
 signtri_status emulated_gemm_run(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C,
                                  int ldc, int S, Arena &ws, int *d_err, cudaStream_t st);
+
+// Mixed precision with refinement (mixed.cu)
+struct MixedParams {
+    double tol;              // stopping test on both relative residuals
+    int max_steps;           // refinement steps before falling back
+    double min_contraction;  // required reduction of the residual per step
+};
+struct MixedReport {
+    int steps;
+    int fallback;            // 1: the caller must run the float64 path
+    double resid_commute, resid_involution, resid0;
+};
+size_t mixed_workspace_bytes(int n, int S);
+signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, int S, const MixedParams &prm,
+                         MixedReport &rep, Arena &ws, int *d_err, double *norms_host, cudaStream_t st);
 
 }  // namespace signtri

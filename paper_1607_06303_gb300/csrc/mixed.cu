@@ -1,0 +1,591 @@
+// mixed.cu -- Parlett-Higham with tensor-core block sums and float64
+// refinement of both defining equations.
+//
+// 1. Low-precision solve.  The block anti-diagonal schedule of the float64
+//    path (Algorithms 4-6 reordered, blocks of 64), with the block sums
+//      X_IJ = sum_K U_IK T_KJ - T_IK U_KJ,   Y_IJ = sum_K U_IK U_KJ
+//    formed on the tensor cores (tc_gemm.cu) from bf16 splits of U and T:
+//    one bf16 term (BF16 variant) or a three-term split hi + mid + lo with the
+//    six products of s + t <= 2 (about fp32 accuracy, the "FP32" variant);
+//    in-block recurrences (Algorithm 6, 1x1 case) in fp32.
+// 2. Refinement.  With U = U0 + E and E strictly upper triangular, UT = TU
+//    and U^2 = I become, entry by entry (i < j):
+//      signs differ: (t_ii - t_jj) e_ij = -Rc_ij + sum_{i<k<j} (e_ik t_kj - t_ik e_kj)
+//      signs equal:  (u_ii + u_jj) e_ij = -Rs_ij - sum_{i<k<j} (u0_ik e_kj + e_ik u0_kj)
+//    (the second dropping e_ik e_kj), with the residuals Rc = T U0 - U0 T and
+//    Rs = U0^2 - I.  These are the Parlett-Higham recurrences with U replaced
+//    by E, so E is computed by the same schedule (block sums X^E = E T - T E,
+//    Y^E = U0 E + E U0 on the tensor cores, recurrences in fp32).  Newton's
+//    iteration X <- X(3I - X^2)/2 alone would only drive U^2 = I and cannot
+//    correct the entries fixed by UT = TU, hence both equations.
+//    The residuals are formed from exact 7-bit integer slices of the strictly
+//    upper parts of T and U0 (emulated float64 products, about 2^-45
+//    relative to |T||U|) plus the diagonal terms in float64:
+//      Rc_ij = (N_T N_U - N_U N_T)_ij + t_ii u_ij + t_ij u_jj - u_ii t_ij - u_ij t_jj
+//      Rs_ij = (N_U N_U)_ij + u_ii u_ij + u_ij u_jj.
+//    Stop when ||Rc||_F / (||T||_F ||U||_F) and ||Rs||_F / ||U||_F^2 are both
+//    below the tolerance; fall back to the float64 path when a step does not
+//    reduce the larger of the two by a factor 10, or after the step limit.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace signtri {
+
+namespace {
+
+constexpr int MB = 64;
+constexpr int kLeafThreads = 256;
+constexpr int kTargetJobs = 2 * 152;
+constexpr int kOzakiSlices = 7;
+
+__device__ __forceinline__ float fsgn(double t) { return t > 0.0 ? 1.f : -1.f; }
+
+// --------------------------------------------------------------- leaves ---
+
+// MODE 0: V = U (initial solve).  MODE 1: V = E (correction), with U0, Rc, Rs.
+// Shared memory (fp32, 64 x 65 each): T_II, T_JJ, the same-sign wavefront
+// blocks A_II, A_JJ (U in mode 0, U0 in mode 1), V, the seeds C; mode 1 adds
+// the diagonal blocks E_II, E_JJ and U0_IJ for the seeds.  V holds T_IJ until
+// the seeds are formed.
+template <int MODE>
+constexpr int leaf_buffers() { return MODE == 0 ? 6 : 9; }
+
+template <int MODE>
+__global__ void __launch_bounds__(kLeafThreads)
+mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restrict__ V, int ldv,
+                  const double *__restrict__ U0, int ldu0, const double *__restrict__ Rc,
+                  const double *__restrict__ Rs, int ldr, int d, int nsplit, const double *__restrict__ PA,
+                  const double *__restrict__ PB, __nv_bfloat16 *__restrict__ Vr, __nv_bfloat16 *__restrict__ Vc,
+                  int S, int rows_pad, int ldsl)
+{
+    constexpr int LD = MB + 1;
+    extern __shared__ float fsm[];
+    float *TI = fsm;
+    float *TJ = TI + MB * LD;
+    float *AI = TJ + MB * LD;
+    float *AJ = AI + MB * LD;
+    float *Vs = AJ + MB * LD;
+    float *Cs = Vs + MB * LD;
+    float *EI = Cs + MB * LD;      // mode 1 only
+    float *EJ = EI + MB * LD;
+    float *WS = EJ + MB * LD;      // U0_IJ
+    __shared__ float srow[MB], scol[MB];
+    const int I = blockIdx.x, J = I + d;
+    const int r0 = I * MB, c0 = J * MB;
+    const int bj = min(MB, n - c0);
+    const double *A = (MODE == 0) ? V : U0;
+    const int lda = (MODE == 0) ? ldv : ldu0;
+
+    for (int idx = threadIdx.x; idx < MB * MB; idx += kLeafThreads) {
+        const int i = idx % MB, j = idx / MB;
+        const bool up = (i < j);
+        TI[i + j * LD] = (i <= j) ? (float)SGT_AT(T, ldt, r0 + i, r0 + j) : 0.f;
+        AI[i + j * LD] = up ? (float)SGT_AT(A, lda, r0 + i, r0 + j) : 0.f;
+        const bool inJ = (i <= j) && (j < bj);
+        TJ[i + j * LD] = inJ ? (float)SGT_AT(T, ldt, c0 + i, c0 + j) : 0.f;
+        AJ[i + j * LD] = (inJ && up) ? (float)SGT_AT(A, lda, c0 + i, c0 + j) : 0.f;
+        Vs[i + j * LD] = (j < bj) ? (float)SGT_AT(T, ldt, r0 + i, c0 + j) : 0.f;     // T_IJ
+        if (MODE == 1) {
+            EI[i + j * LD] = up ? (float)SGT_AT(V, ldv, r0 + i, r0 + j) : 0.f;
+            EJ[i + j * LD] = (inJ && up) ? (float)SGT_AT(V, ldv, c0 + i, c0 + j) : 0.f;
+            WS[i + j * LD] = (j < bj) ? (float)SGT_AT(U0, ldu0, r0 + i, c0 + j) : 0.f;
+        }
+    }
+    for (int i = threadIdx.x; i < MB; i += kLeafThreads) {
+        srow[i] = fsgn(SGT_AT(T, ldt, r0 + i, r0 + i));
+        scol[i] = (i < bj) ? fsgn(SGT_AT(T, ldt, c0 + i, c0 + i)) : 1.f;
+    }
+    __syncthreads();
+
+    // seeds: block sums, base terms and the in-block products of known blocks
+    // (D = diagonal blocks of V: U_II, U_JJ in mode 0, E_II, E_JJ in mode 1)
+    const float *DI = (MODE == 0) ? AI : EI;
+    const float *DJ = (MODE == 0) ? AJ : EJ;
+    for (int idx = threadIdx.x; idx < MB * bj; idx += kLeafThreads) {
+        const int p = idx % MB, q = idx / MB;
+        const int gi = r0 + p, gj = c0 + q;
+        const bool opp = (srow[p] + scol[q] == 0.f);
+        double x = 0.0, y = 0.0;
+        for (int s = 0; s < nsplit; s++) {
+            const double *pa = PA + ((size_t)I * nsplit + s) * 16384 + p + (size_t)q * 64;
+            if (opp) x += pa[0] - pa[3 * 4096];
+            else if (MODE == 0) y += pa[4096];
+            else {
+                const double *pb = PB + ((size_t)I * nsplit + s) * 16384 + p + (size_t)q * 64;
+                y += pb[0] + pb[3 * 4096];
+            }
+        }
+        float c;
+        if (opp) {
+            float a = 0.f, b = 0.f;
+            for (int k = p + 1; k < MB; k++) a = fmaf(DI[p + k * LD], Vs[k + q * LD], a);
+            for (int k = 0; k < q; k++) b = fmaf(Vs[p + k * LD], DJ[k + q * LD], b);
+            const double base = (MODE == 0) ? SGT_AT(T, ldt, gi, gj) * (double)(srow[p] - scol[q])
+                                            : -SGT_AT(Rc, ldr, gi, gj);
+            c = (float)(base + x) + a - b;
+        } else if (MODE == 0) {
+            c = (float)(-y);
+        } else {
+            float a = 0.f, b = 0.f;
+            for (int k = p + 1; k < MB; k++) a = fmaf(EI[p + k * LD], WS[k + q * LD], a);
+            for (int k = 0; k < q; k++) b = fmaf(WS[p + k * LD], EJ[k + q * LD], b);
+            c = (float)(-SGT_AT(Rs, ldr, gi, gj) - y) - a - b;
+        }
+        Cs[p + q * LD] = c;
+    }
+    __syncthreads();
+
+    const int nsteps = MB + bj - 1;
+    for (int st = 0; st < nsteps; st++) {
+        const int plo = max(0, MB - 1 - st);
+        const int phi = min(MB - 1, MB - 1 - st + bj - 1);
+        for (int p = plo + threadIdx.x; p <= phi; p += kLeafThreads) {
+            const int q = st - (MB - 1 - p);
+            const bool opp = (srow[p] + scol[q] == 0.f);
+            const float *Am = opp ? TI : AI;
+            const float *Bm = opp ? TJ : AJ;
+            float a = 0.f, b = 0.f;
+            for (int k = p + 1; k < MB; k++) a = fmaf(Am[p + k * LD], Vs[k + q * LD], a);
+            for (int k = 0; k < q; k++) b = fmaf(Vs[p + k * LD], Bm[k + q * LD], b);
+            float v;
+            if (opp) v = (Cs[p + q * LD] - a + b) / (TI[p + p * LD] - TJ[q + q * LD]);
+            else v = (Cs[p + q * LD] - a - b) / (srow[p] + scol[q]);
+            Vs[p + q * LD] = v;
+        }
+        __syncthreads();
+    }
+    // V (float64) and its bf16 splits: row slices Vr[s][row][col], column
+    // slices Vc[s][col][row]
+    for (int idx = threadIdx.x; idx < MB * bj; idx += kLeafThreads) {
+        const int p = idx % MB, q = idx / MB;
+        SGT_AT(V, ldv, r0 + p, c0 + q) = (double)Vs[p + q * LD];
+        double r = (double)Vs[p + q * LD];
+        for (int s = 0; s < S; s++) {
+            const __nv_bfloat16 h = __double2bfloat16(r);
+            Vc[((size_t)s * rows_pad + c0 + q) * ldsl + r0 + p] = h;
+            r -= (double)__bfloat162float(h);
+        }
+    }
+    for (int idx = threadIdx.x; idx < MB * bj; idx += kLeafThreads) {
+        const int q = idx % bj, p = idx / bj;
+        double r = (double)Vs[p + q * LD];
+        for (int s = 0; s < S; s++) {
+            const __nv_bfloat16 h = __double2bfloat16(r);
+            Vr[((size_t)s * rows_pad + r0 + p) * ldsl + c0 + q] = h;
+            r -= (double)__bfloat162float(h);
+        }
+    }
+}
+
+// Correction on the diagonal blocks: the recurrences above restricted to one
+// block, by anti-diagonal, float64.
+__global__ void __launch_bounds__(kLeafThreads)
+corr_diag_leaf_kernel(int n, const double *__restrict__ T, int ldt, const double *__restrict__ U0, int ldu0,
+                      const double *__restrict__ Rc, const double *__restrict__ Rs, int ldr, double *__restrict__ E,
+                      int lde)
+{
+    constexpr int LD = MB + 1;
+    extern __shared__ double dsm[];
+    double *Ts = dsm;
+    double *Us = Ts + MB * LD;
+    double *Es = Us + MB * LD;
+    const int r0 = blockIdx.x * MB;
+    const int bs = min(MB, n - r0);
+    for (int idx = threadIdx.x; idx < bs * bs; idx += kLeafThreads) {
+        const int i = idx % bs, j = idx / bs;
+        Ts[i + j * LD] = (i <= j) ? SGT_AT(T, ldt, r0 + i, r0 + j) : 0.0;
+        Us[i + j * LD] = (i <= j) ? SGT_AT(U0, ldu0, r0 + i, r0 + j) : 0.0;
+        Es[i + j * LD] = 0.0;
+    }
+    __syncthreads();
+    for (int dd = 1; dd < bs; dd++) {
+        for (int i = threadIdx.x; i < bs - dd; i += kLeafThreads) {
+            const int j = i + dd;
+            const double si = Ts[i + i * LD] > 0.0 ? 1.0 : -1.0, sj = Ts[j + j * LD] > 0.0 ? 1.0 : -1.0;
+            double e;
+            if (si + sj == 0.0) {
+                double s = -SGT_AT(Rc, ldr, r0 + i, r0 + j);
+                for (int k = i + 1; k < j; k++) s += Es[i + k * LD] * Ts[k + j * LD] - Ts[i + k * LD] * Es[k + j * LD];
+                e = s / (Ts[i + i * LD] - Ts[j + j * LD]);
+            } else {
+                double s = -SGT_AT(Rs, ldr, r0 + i, r0 + j);
+                for (int k = i + 1; k < j; k++) s -= Us[i + k * LD] * Es[k + j * LD] + Es[i + k * LD] * Us[k + j * LD];
+                e = s / (si + sj);
+            }
+            Es[i + j * LD] = e;
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < bs * bs; idx += kLeafThreads) {
+        const int i = idx % bs, j = idx / bs;
+        if (i < j) SGT_AT(E, lde, r0 + i, r0 + j) = Es[i + j * LD];
+    }
+}
+
+// ------------------------------------------------------------- residual ---
+
+// In place: Ptu -> Rc, Puu -> Rs (i < j; other entries 0), and the squared
+// Frobenius norms of Rc, Rs, T, U accumulated into norms[0..3].
+__global__ void residual_finalize_kernel(int n, const double *__restrict__ T, int ldt, const double *__restrict__ U,
+                                         int ldu, double *__restrict__ Ptu, const double *__restrict__ Put,
+                                         double *__restrict__ Puu, int ldp, double *__restrict__ norms)
+{
+    const int j = blockIdx.x;
+    double nc = 0.0, ns = 0.0, nt = 0.0, nu = 0.0;
+    const double tjj = SGT_AT(T, ldt, j, j), ujj = SGT_AT(U, ldu, j, j);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double rc = 0.0, rs = 0.0;
+        if (i < j) {
+            const double tii = SGT_AT(T, ldt, i, i), uii = SGT_AT(U, ldu, i, i);
+            const double tij = SGT_AT(T, ldt, i, j), uij = SGT_AT(U, ldu, i, j);
+            rc = SGT_AT(Ptu, ldp, i, j) - SGT_AT(Put, ldp, i, j) + (tii * uij - uij * tjj) + (tij * ujj - uii * tij);
+            rs = SGT_AT(Puu, ldp, i, j) + uii * uij + uij * ujj;
+            nt += tij * tij;
+            nu += uij * uij;
+        } else if (i == j) {
+            nt += tjj * tjj;
+            nu += ujj * ujj;
+        }
+        SGT_AT(Ptu, ldp, i, j) = rc;
+        SGT_AT(Puu, ldp, i, j) = rs;
+        nc += rc * rc;
+        ns += rs * rs;
+    }
+    __shared__ double red[4][256];
+    red[0][threadIdx.x] = nc; red[1][threadIdx.x] = ns; red[2][threadIdx.x] = nt; red[3][threadIdx.x] = nu;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off)
+            for (int c = 0; c < 4; c++) red[c][threadIdx.x] += red[c][threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 4; c++) atomicAdd(&norms[c], red[c][0]);
+}
+
+// U += E on the strictly upper part; ||E||_F^2 into norms[4].
+__global__ void apply_correction_kernel(int n, double *__restrict__ U, int ldu, const double *__restrict__ E, int lde,
+                                        double *__restrict__ norms)
+{
+    const int j = blockIdx.x;
+    double ne = 0.0;
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        const double e = SGT_AT(E, lde, i, j);
+        SGT_AT(U, ldu, i, j) += e;
+        ne += e * e;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = ne;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&norms[4], red[0]);
+}
+
+__global__ void zero_kernel(size_t count, double *__restrict__ p)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = 0.0;
+}
+
+// ------------------------------------------------------------ host side ---
+
+struct Schedule {
+    int nb = 0;
+    std::vector<int> job_off;   // per anti-diagonal d: first job index (d = 0..nb)
+    std::vector<int> nsplit;    // per anti-diagonal
+    std::vector<TcJob> jobs;
+    int max_jobs = 0;
+};
+
+void build_schedule(int n, Schedule &sc)
+{
+    const int nb = (n + MB - 1) / MB;
+    sc.nb = nb;
+    sc.job_off.assign(nb + 1, 0);
+    sc.nsplit.assign(nb + 1, 0);
+    sc.jobs.clear();
+    sc.max_jobs = 0;
+    for (int d = 0; d <= nb; d++) {
+        sc.job_off[d] = (int)sc.jobs.size();
+        if (d < 2 || d >= nb) continue;
+        const int ntiles = nb - d, kmax = d - 1;
+        int ns = std::max(1, std::min(kmax, (kTargetJobs + ntiles - 1) / ntiles));
+        const int kc = (kmax + ns - 1) / ns;
+        ns = (kmax + kc - 1) / kc;
+        sc.nsplit[d] = ns;
+        for (int I = 0; I < ntiles; I++) {
+            const int J = I + d;
+            for (int s = 0; s < ns; s++) {
+                TcJob j;
+                j.rt = I * MB; j.rb = I * MB; j.cl = J * MB; j.cr = J * MB;
+                j.kb0 = I + 1 + s * kc;
+                j.kb1 = std::min(j.kb0 + kc, J);
+                j.slot = I * ns + s;
+                j.pad = 0;
+                sc.jobs.push_back(j);
+            }
+        }
+        sc.max_jobs = std::max(sc.max_jobs, ntiles * ns);
+    }
+}
+
+struct MixedCtx {
+    int n, np, S;
+    cudaStream_t st;
+    int *d_err;
+    Schedule sc;
+    TcJob *d_jobs;
+    TcPairs pairs_split, pairs_oz;
+    TcPairs *d_pairs_split, *d_pairs_oz;
+    // bf16 splits (S slices) of T and of the unknowns, row and column forms
+    __nv_bfloat16 *Tr, *Tc, *Ur, *Uc, *Er, *Ec;
+    // exact slices of the strictly upper parts (residual products)
+    __nv_bfloat16 *NTr, *NTc, *NUr, *NUc;
+    float *sTr, *sTc, *sUr, *sUc;
+    unsigned long long *tmpmax;
+    double *PA, *PB;            // block-sum partials
+    double *E, *Rc, *Rs, *Put;  // correction, residuals
+    double *norms, *norms_host; // [0] Rc^2 [1] Rs^2 [2] T^2 [3] U^2 [4] E^2
+    TcJob *d_res_jobs;
+    int n_res_jobs;
+};
+
+size_t bytes_for(int n, int S)
+{
+    const size_t np = (size_t)pad64(n);
+    const size_t nb = np / MB;
+    size_t b = 0;
+    b += 6 * (size_t)S * np * np * 2 + 6 * 256;                       // split slices
+    b += 4 * (size_t)kOzakiSlices * np * np * 2 + 4 * 256;             // exact slices
+    b += 4 * np * 4 + np * 8 + 6 * 256;                                 // scales, tmp
+    const size_t maxjobs = (size_t)kTargetJobs + nb + 8;
+    b += 2 * maxjobs * 16384 * 8 + 2 * 256;                             // partials
+    b += 4 * (size_t)n * n * 8 + 4 * 256;                               // E, Rc, Rs, Put
+    b += 64 + 256;                                                      // norms
+    b += (size_t)nb * (nb + 1) / 2 * sizeof(TcJob) + 256;               // residual jobs
+    b += nb * (size_t)(kTargetJobs + nb) * sizeof(TcJob) + 256;         // wavefront jobs (bound)
+    b += 2 * sizeof(TcPairs) + 512;
+    return b;
+}
+
+template <typename P>
+P *take(Arena &ws, size_t count)
+{
+    return static_cast<P *>(ws.take(count * sizeof(P)));
+}
+
+signtri_status split_full(MixedCtx &c, const double *M, int ldm, __nv_bfloat16 *R, __nv_bfloat16 *C)
+{
+    signtri_status rs;
+    if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, c.S, nullptr, R, c.np, c.np, c.st)) != SIGNTRI_OK) return rs;
+    return make_col_slices(c.n, c.n, M, ldm, 1, c.S, nullptr, C, c.np, c.np, c.st);
+}
+
+signtri_status exact_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bfloat16 *R, __nv_bfloat16 *C, float *sR,
+                               float *sC)
+{
+    signtri_status rs;
+    if ((rs = make_scales(c.n, c.n, M, ldm, 1, true, c.np, c.tmpmax, sR, c.st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_scales(c.n, c.n, M, ldm, 1, false, c.np, c.tmpmax, sC, c.st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, sR, R, c.np, c.np, c.st)) != SIGNTRI_OK) return rs;
+    return make_col_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, sC, C, c.np, c.np, c.st);
+}
+
+// One low-precision sweep: MODE 0 solves for U (into V = U), MODE 1 for E.
+template <int MODE>
+signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, __nv_bfloat16 *Vr,
+                     __nv_bfloat16 *Vc, const double *U0, int ldu0)
+{
+    const int n = c.n, nb = c.sc.nb;
+    const size_t leaf_smem = (size_t)leaf_buffers<MODE>() * MB * (MB + 1) * sizeof(float);
+    SGT_CUDA_TRY(cudaFuncSetAttribute(mixed_leaf_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)leaf_smem));
+    const TcSource srcT_r{c.Tr, c.S, c.np, c.np, c.np, nullptr}, srcT_c{c.Tc, c.S, c.np, c.np, c.np, nullptr};
+    const TcSource srcV_r{Vr, c.S, c.np, c.np, c.np, nullptr}, srcV_c{Vc, c.S, c.np, c.np, c.np, nullptr};
+    const TcSource srcU_r{c.Ur, c.S, c.np, c.np, c.np, nullptr}, srcU_c{c.Uc, c.S, c.np, c.np, c.np, nullptr};
+    const TcQuadOut slots{{nullptr, nullptr, nullptr, nullptr}, 0, 0, 0};
+    // K-blocks per tensor-core unit: small when several slice pairs share a
+    // chunk (they re-read its panels from L2), larger for a single pair
+    const int chunk = c.pairs_split.n > 1 ? 4 : 16;
+    for (int d = 1; d < nb; d++) {
+        const int ntiles = nb - d;
+        const int njobs = c.sc.job_off[d + 1] - c.sc.job_off[d];
+        const TcJob *jobs = c.d_jobs + c.sc.job_off[d];
+        signtri_status rs;
+        if (njobs > 0) {
+            if (MODE == 0) {
+                // [U_I.; T_I.] x [T_.J | U_.J]: TL = U T, TR = U U, BR = T U
+                rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
+                                  c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st);
+                if (rs != SIGNTRI_OK) return rs;
+            } else {
+                // X^E: [E_I.; T_I.] x [T_.J | E_.J]: TL = E T, BR = T E
+                rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
+                                  c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st);
+                if (rs != SIGNTRI_OK) return rs;
+                // Y^E: [U0_I.; E_I.] x [E_.J | U0_.J]: TL = U0 E, BR = E U0
+                rs = tc_blocksums(srcU_r, srcV_r, srcV_c, srcU_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
+                                  c.PB, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st);
+                if (rs != SIGNTRI_OK) return rs;
+            }
+        }
+        ProfScope ps(MODE == 0 ? SIGNTRI_KC_OFFDIAG_LEAF_F32 : SIGNTRI_KC_CORRECTION, c.st);
+        mixed_leaf_kernel<MODE><<<ntiles, kLeafThreads, leaf_smem, c.st>>>(
+            n, T, ldt, V, ldv, U0, ldu0, c.Rc, c.Rs, n, d, c.sc.nsplit[d], c.PA, c.PB, Vr, Vc, c.S, c.np, c.np);
+        SGT_LAUNCH_CHECK();
+    }
+    return SIGNTRI_OK;
+}
+
+// Residuals of U into c.Rc, c.Rs and the norms (host copy in c.norms_host).
+signtri_status residual(MixedCtx &c, const double *T, int ldt, const double *U, int ldu)
+{
+    signtri_status rs = exact_slices_of(c, U, ldu, c.NUr, c.NUc, c.sUr, c.sUc);
+    if (rs != SIGNTRI_OK) return rs;
+    // [N_T I.; N_U I.] x [N_U .J | N_T .J]: TL = N_T N_U, BR = N_U N_T, BL = N_U N_U
+    const TcSource top{c.NTr, kOzakiSlices, c.np, c.np, c.np, c.sTr}, bot{c.NUr, kOzakiSlices, c.np, c.np, c.np, c.sUr};
+    const TcSource left{c.NUc, kOzakiSlices, c.np, c.np, c.np, c.sUc},
+        right{c.NTc, kOzakiSlices, c.np, c.np, c.np, c.sTc};
+    const TcQuadOut qo{{c.Rc, nullptr, c.Rs, c.Put}, c.n, c.n, c.n};
+    rs = tc_blocksums(top, bot, left, right, c.d_res_jobs, c.n_res_jobs, c.pairs_oz, c.d_pairs_oz, 4, nullptr, qo,
+                      c.d_err, SIGNTRI_KC_RESIDUAL, c.st);
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaMemsetAsync(c.norms, 0, 8 * sizeof(double), c.st));
+    {
+        ProfScope ps(SIGNTRI_KC_RESIDUAL, c.st);
+        residual_finalize_kernel<<<c.n, 256, 0, c.st>>>(c.n, T, ldt, U, ldu, c.Rc, c.Put, c.Rs, c.n, c.norms);
+        SGT_LAUNCH_CHECK();
+    }
+    SGT_CUDA_TRY(cudaMemcpyAsync(c.norms_host, c.norms, 8 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(c.st));
+    return SIGNTRI_OK;
+}
+
+}  // namespace
+
+size_t mixed_workspace_bytes(int n, int S) { return n > 0 ? bytes_for(n, S) + (64 << 10) : 0; }
+
+signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, int S, const MixedParams &prm,
+                         MixedReport &rep, Arena &ws, int *d_err, double *norms_host, cudaStream_t st)
+{
+    MixedCtx c{};
+    c.n = n;
+    c.np = pad64(n);
+    c.S = S;
+    c.st = st;
+    c.d_err = d_err;
+    build_schedule(n, c.sc);
+    const size_t np = c.np;
+    const size_t split_elems = (size_t)S * np * np, oz_elems = (size_t)kOzakiSlices * np * np;
+    c.Tr = take<__nv_bfloat16>(ws, split_elems); c.Tc = take<__nv_bfloat16>(ws, split_elems);
+    c.Ur = take<__nv_bfloat16>(ws, split_elems); c.Uc = take<__nv_bfloat16>(ws, split_elems);
+    c.Er = take<__nv_bfloat16>(ws, split_elems); c.Ec = take<__nv_bfloat16>(ws, split_elems);
+    c.NTr = take<__nv_bfloat16>(ws, oz_elems); c.NTc = take<__nv_bfloat16>(ws, oz_elems);
+    c.NUr = take<__nv_bfloat16>(ws, oz_elems); c.NUc = take<__nv_bfloat16>(ws, oz_elems);
+    c.sTr = take<float>(ws, np); c.sTc = take<float>(ws, np); c.sUr = take<float>(ws, np); c.sUc = take<float>(ws, np);
+    c.tmpmax = take<unsigned long long>(ws, np);
+    const size_t maxjobs = (size_t)std::max(c.sc.max_jobs, 1);
+    c.PA = take<double>(ws, maxjobs * 16384); c.PB = take<double>(ws, maxjobs * 16384);
+    c.E = take<double>(ws, (size_t)n * n); c.Rc = take<double>(ws, (size_t)n * n);
+    c.Rs = take<double>(ws, (size_t)n * n); c.Put = take<double>(ws, (size_t)n * n);
+    c.norms = take<double>(ws, 8);
+    const int nb = c.sc.nb;
+    c.n_res_jobs = nb * (nb + 1) / 2;
+    c.d_res_jobs = take<TcJob>(ws, (size_t)c.n_res_jobs);
+    c.d_jobs = take<TcJob>(ws, std::max<size_t>(c.sc.jobs.size(), 1));
+    c.d_pairs_split = take<TcPairs>(ws, 1);
+    c.d_pairs_oz = take<TcPairs>(ws, 1);
+    c.norms_host = norms_host;
+    if (!c.Tr || !c.Tc || !c.Ur || !c.Uc || !c.Er || !c.Ec || !c.NTr || !c.NTc || !c.NUr || !c.NUc || !c.sTr ||
+        !c.sTc || !c.sUr || !c.sUc || !c.tmpmax || !c.PA || !c.PB || !c.E || !c.Rc || !c.Rs || !c.Put || !c.norms ||
+        !c.d_res_jobs || !c.d_jobs || !c.d_pairs_split || !c.d_pairs_oz)
+        return SIGNTRI_ERR_NO_WORKSPACE;
+    c.pairs_split = split_pairs(S);
+    c.pairs_oz = ozaki_pairs_impl(kOzakiSlices);
+    // residual jobs by block row: CTAs resident together share the row panels
+    std::vector<TcJob> rj;
+    rj.reserve(c.n_res_jobs);
+    for (int I = 0; I < nb; I++)
+        for (int J = I; J < nb; J++) {
+            TcJob j;
+            j.rt = I * MB; j.rb = I * MB; j.cl = J * MB; j.cr = J * MB;
+            j.kb0 = I; j.kb1 = J + 1; j.slot = 0; j.pad = 0;
+            rj.push_back(j);
+        }
+    SGT_CUDA_TRY(cudaMemcpyAsync(c.d_res_jobs, rj.data(), rj.size() * sizeof(TcJob), cudaMemcpyHostToDevice, st));
+    if (!c.sc.jobs.empty())
+        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_jobs, c.sc.jobs.data(), c.sc.jobs.size() * sizeof(TcJob),
+                                     cudaMemcpyHostToDevice, st));
+    SGT_CUDA_TRY(cudaMemcpyAsync(c.d_pairs_split, &c.pairs_split, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
+    SGT_CUDA_TRY(cudaMemcpyAsync(c.d_pairs_oz, &c.pairs_oz, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
+    // slices start from zero (padding and the not-yet-computed blocks)
+    SGT_CUDA_TRY(cudaMemsetAsync(c.Ur, 0, split_elems * 2, st));
+    SGT_CUDA_TRY(cudaMemsetAsync(c.Uc, 0, split_elems * 2, st));
+    SGT_CUDA_TRY(cudaMemsetAsync(c.Er, 0, split_elems * 2, st));
+    SGT_CUDA_TRY(cudaMemsetAsync(c.Ec, 0, split_elems * 2, st));
+    signtri_status rs;
+    if ((rs = split_full(c, T, ldt, c.Tr, c.Tc)) != SIGNTRI_OK) return rs;
+    if ((rs = exact_slices_of(c, T, ldt, c.NTr, c.NTc, c.sTr, c.sTc)) != SIGNTRI_OK) return rs;
+
+    // 1. low-precision solve: diagonal blocks in float64, the rest by sweep
+    if ((rs = launch_zero_strict_lower(n, U, ldu, st)) != SIGNTRI_OK) return rs;
+    if ((rs = diag_leaves_f64(n, T, ldt, U, ldu, MB, st)) != SIGNTRI_OK) return rs;
+    if ((rs = sweep<0>(c, T, ldt, U, ldu, c.Ur, c.Uc, nullptr, 0)) != SIGNTRI_OK) return rs;
+
+    // 2. refinement
+    double prev = 1e300;
+    rep.steps = 0;
+    rep.fallback = 0;
+    for (int step = 0;; step++) {
+        if ((rs = residual(c, T, ldt, U, ldu)) != SIGNTRI_OK) return rs;
+        const double *h = c.norms_host;
+        const double nT = std::sqrt(h[2]), nU = std::sqrt(h[3]);
+        rep.resid_commute = std::sqrt(h[0]) / (nT * nU);
+        rep.resid_involution = std::sqrt(h[1]) / (nU * nU);
+        const double worst = std::max(rep.resid_commute, rep.resid_involution);
+        if (step == 0) rep.resid0 = worst;
+        if (!(worst == worst)) { rep.fallback = 1; return SIGNTRI_OK; }   // NaN
+        if (worst <= prm.tol) return SIGNTRI_OK;
+        if (step >= prm.max_steps || (step > 0 && worst > prev / prm.min_contraction)) {
+            rep.fallback = 1;
+            return SIGNTRI_OK;
+        }
+        prev = worst;
+        // E: zero, diagonal blocks in float64, off-diagonal blocks by sweep
+        {
+            ProfScope ps(SIGNTRI_KC_FILL, st);
+            zero_kernel<<<1024, 256, 0, st>>>((size_t)n * n, c.E);
+            SGT_LAUNCH_CHECK();
+        }
+        SGT_CUDA_TRY(cudaMemsetAsync(c.Er, 0, split_elems * 2, st));
+        SGT_CUDA_TRY(cudaMemsetAsync(c.Ec, 0, split_elems * 2, st));
+        if ((rs = split_full(c, U, ldu, c.Ur, c.Uc)) != SIGNTRI_OK) return rs;
+        {
+            const size_t dsm = 3 * (size_t)MB * (MB + 1) * sizeof(double);
+            SGT_CUDA_TRY(cudaFuncSetAttribute(corr_diag_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)dsm));
+            ProfScope ps(SIGNTRI_KC_CORRECTION, st);
+            corr_diag_leaf_kernel<<<nb, kLeafThreads, dsm, st>>>(n, T, ldt, U, ldu, c.Rc, c.Rs, n, c.E, n);
+            SGT_LAUNCH_CHECK();
+        }
+        if ((rs = sweep<1>(c, T, ldt, c.E, n, c.Er, c.Ec, U, ldu)) != SIGNTRI_OK) return rs;
+        {
+            ProfScope ps(SIGNTRI_KC_CORRECTION, st);
+            apply_correction_kernel<<<n, 256, 0, st>>>(n, U, ldu, c.E, n, c.norms);
+            SGT_LAUNCH_CHECK();
+        }
+        rep.steps = step + 1;
+    }
+}
+
+}  // namespace signtri

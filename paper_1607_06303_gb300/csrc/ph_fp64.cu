@@ -307,6 +307,29 @@ signtri_status run_b(int n, const double *T, int ldt, double *U, int ldu, Arena 
 
 }  // namespace
 
+signtri_status diag_leaves_f64(int n, const double *T, int ldt, double *U, int ldu, int b, cudaStream_t st)
+{
+    const int nb = (n + b - 1) / b;
+    ProfScope ps(SIGNTRI_KC_DIAG_LEAF, st);
+    switch (b) {
+    case 64:
+        SGT_CUDA_TRY(cudaFuncSetAttribute(diag_leaf_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)diag_smem<64>()));
+        diag_leaf_kernel<64><<<nb, kThreads, diag_smem<64>(), st>>>(n, T, ldt, U, ldu);
+        break;
+    case 32:
+        diag_leaf_kernel<32><<<nb, kThreads, diag_smem<32>(), st>>>(n, T, ldt, U, ldu);
+        break;
+    case 16:
+        diag_leaf_kernel<16><<<nb, kThreads, diag_smem<16>(), st>>>(n, T, ldt, U, ldu);
+        break;
+    default:
+        return SIGNTRI_ERR_BAD_ARG;
+    }
+    SGT_LAUNCH_CHECK();
+    return SIGNTRI_OK;
+}
+
 size_t ph_fp64_workspace_bytes(int n, int b)
 {
     if (n <= 0 || b <= 0) return 0;

@@ -67,25 +67,35 @@ __global__ void pow2_scale_kernel(int n, const unsigned long long *__restrict__ 
     scale[i] = ldexpf(1.0f, e);
 }
 
-__device__ __forceinline__ void exact_slices(double x, double inv_scale, int S, float *q)
+// Exact slices by integer arithmetic: |x| / scale < 1 written as the 56-bit
+// fixed-point integer F = trunc(|x| / scale * 2^56) (from the float64
+// significand and exponent, no rounding), digits q_s = bits [49-7s, 56-7s)
+// of F with the sign of x.  Same digits as repeated q_s = trunc(128 r),
+// r <- 128 r - q_s, without float64 arithmetic (slow on this part).
+__device__ __forceinline__ void exact_slices(double x, int scale_exp, int S, float *q)
 {
-    double r = x * inv_scale;            // exact (power of two), |r| < 1
-    for (int s = 0; s < S; s++) {
-        r *= 128.0;
-        const double t = trunc(r);
-        q[s] = (float)t;
-        r -= t;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int bexp = (int)((bits >> 52) & 0x7ff);
+    unsigned long long F = 0;
+    if (bexp != 0) {   // zero and subnormals (far below any scale used here) give 0
+        const unsigned long long mant = (bits & 0xfffffffffffffull) | (1ull << 52);
+        // |x| = mant * 2^(bexp - 1075); F = |x| * 2^(56 - scale_exp)
+        const int sh = bexp - 1075 + 56 - scale_exp;   // <= 3 since |x| < 2^scale_exp
+        if (sh >= 0) F = mant << sh;
+        else if (sh > -64) F = mant >> (-sh);
     }
+    const float sgn = (bits >> 63) ? -1.f : 1.f;
+    for (int s = 0; s < S; s++) q[s] = sgn * (float)((F >> (49 - 7 * s)) & 127ull);
 }
 
+// Rounding split of the fp32 value of x: x0 = bf16(x), x1 = bf16(x - x0), ...
 __device__ __forceinline__ void round_slices(double x, int S, float *q)
 {
-    double r = x;
+    float r = (float)x;
     for (int s = 0; s < S; s++) {
-        const __nv_bfloat16 b = __double2bfloat16(r);
-        const double bd = (double)__bfloat162float(b);
-        q[s] = (float)bd;
-        r -= bd;
+        const float b = __bfloat162float(__float2bfloat16_rn(r));
+        q[s] = b;
+        r = __fsub_rn(r, b);
     }
 }
 
@@ -110,7 +120,7 @@ __global__ void row_slices_kernel(int m, int k, const double *__restrict__ M, in
         if (i >= rows_pad || kk >= ldr) continue;
         const double v = tile[y][threadIdx.x];
         float q[8];
-        if (scale) exact_slices(v, i < m ? 1.0 / (double)scale[i] : 1.0, S, q);
+        if (scale) exact_slices(v, i < m ? ilogbf(scale[i]) : 0, S, q);
         else round_slices(v, S, q);
         for (int s = 0; s < S; s++) R[((size_t)s * rows_pad + i) * ldr + kk] = __float2bfloat16_rn(q[s]);
     }
@@ -128,7 +138,7 @@ __global__ void col_slices_kernel(int k, int n, const double *__restrict__ M, in
     double v = 0.0;
     if (j < n && kk < k && (tri == 0 || kk < j)) v = SGT_AT(M, ldm, kk, j);
     float q[8];
-    if (scale) exact_slices(v, j < n ? 1.0 / (double)scale[j] : 1.0, S, q);
+    if (scale) exact_slices(v, j < n ? ilogbf(scale[j]) : 0, S, q);
     else round_slices(v, S, q);
     for (int s = 0; s < S; s++) C[((size_t)s * rows_pad + j) * ldc + kk] = __float2bfloat16_rn(q[s]);
 }
@@ -188,7 +198,7 @@ signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, 
 
 // Exact-split pair list: slices s, t with s + t <= S - 1, weights
 // 2^{-7(s+t+2)}, in order of decreasing weight.
-TcPairs ozaki_pairs(int S)
+TcPairs ozaki_pairs_impl(int S)
 {
     TcPairs p;
     std::memset(&p, 0, sizeof(p));
@@ -253,11 +263,12 @@ signtri_status emulated_gemm_run(int m, int n, int k, const double *A, int lda, 
             j.rt = I * 64; j.rb = I * 64; j.cl = J * 128; j.cr = J * 128 + 64;
             j.kb0 = 0; j.kb1 = kp / 64; j.slot = I * ntJ + J; j.pad = 0;
         }
-    const TcPairs pairs = ozaki_pairs(S);
+    const TcPairs pairs = ozaki_pairs_impl(S);
     SGT_CUDA_TRY(cudaMemcpyAsync(jobs, hj.data(), hj.size() * sizeof(TcJob), cudaMemcpyHostToDevice, st));
     SGT_CUDA_TRY(cudaMemcpyAsync(dp, &pairs, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
     TcSource top{AR, S, mp, kp, kp, sa}, left{BC, S, np, kp, kp, sb}, right{BC, S, np, kp, kp, sb};
-    rs = tc_blocksums(top, top, left, right, jobs, njobs, pairs, dp, 16, out, d_err, SIGNTRI_KC_RESIDUAL, st);
+    TcQuadOut none{{nullptr, nullptr, nullptr, nullptr}, 0, 0, 0};
+    rs = tc_blocksums(top, top, left, right, jobs, njobs, pairs, dp, 16, out, none, d_err, SIGNTRI_KC_RESIDUAL, st);
     if (rs != SIGNTRI_OK) return rs;
     {
         ProfScope ps(SIGNTRI_KC_OTHER, st);

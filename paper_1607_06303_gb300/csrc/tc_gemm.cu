@@ -166,7 +166,8 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
                    const __grid_constant__ CUtensorMap mLeft, const __grid_constant__ CUtensorMap mRight,
                    int rowsA, int rowsB, const TcJob *__restrict__ jobs, const TcPairs *__restrict__ pairs_g, int chunk_kb,
                    const float *__restrict__ sTop, const float *__restrict__ sBot, const float *__restrict__ sLeft,
-                   const float *__restrict__ sRight, double *__restrict__ out, int *__restrict__ err)
+                   const float *__restrict__ sRight, double *__restrict__ out, TcQuadOut qo,
+                   int *__restrict__ err)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -213,7 +214,8 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
             long long issued = 0;
             bool ok = true;
             for (int u = 0; u < nunits && ok; u++) {
-                const int p = u / nchunks, c = u % nchunks;
+                const int c = u / pairs.n, p = u % pairs.n;   // chunk-major: the pairs of one
+                                                              // K-chunk reuse its panels in L2
                 const int ya = pairs.s[p] * rowsA, yb = pairs.t[p] * rowsB;
                 const int kbs = job.kb0 + c * chunk_kb, kbe = min(kbs + chunk_kb, job.kb1);
                 for (int kb = kbs; kb < kbe; kb++) {
@@ -263,7 +265,7 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
                 if (!mbar_wait(&tempty[buf], tphase ^ 1, abort_flag)) { ok = false; break; }
                 fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(buf * 128);
-                const int c = u % nchunks;
+                const int c = u / pairs.n;
                 const int kbs = job.kb0 + c * chunk_kb, kbe = min(kbs + chunk_kb, job.kb1);
                 for (int kb = kbs; kb < kbe; kb++) {
                     if (!mbar_wait(&full[stage], phase, abort_flag)) { ok = false; break; }
@@ -300,7 +302,7 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
             const uint32_t tphase = (u / kBufs) & 1;
             if (!mbar_wait(&tfull[buf], tphase, abort_flag)) { ok = false; break; }
             fence_after();
-            const float w = pairs.w[u / nchunks];
+            const float w = pairs.w[u % pairs.n];
             const uint32_t taddr = lane_base + (uint32_t)(buf * 128 + cg * 32);
 #pragma unroll
             for (int cc = 0; cc < 32; cc += 8) {
@@ -335,7 +337,21 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
             else if (sTop) srow = sTop[job.rt + r];
             const float *scol = half ? sRight : sLeft;
             const int cbase = (half ? job.cr : job.cl) + c0;
-            double *o = out + (size_t)job.slot * 16384 + (size_t)((bottom ? 2 : 0) + half) * 4096 + (size_t)c0 * 64;
+            const int quad = (bottom ? 2 : 0) + half;
+            double *o;
+            size_t ldo;
+            if (qo.m[0] || qo.m[1] || qo.m[2] || qo.m[3]) {
+                // quadrant-matrix mode: element (row, col) of quadrant q goes to
+                // m[q][(row base + r) + (col base + c) * ld]; null m[q] = skip
+                o = qo.m[quad];
+                const int grow = (bottom ? job.rb : job.rt) + r;
+                if (grow >= qo.nrows) o = nullptr;
+                if (o) o += (size_t)grow + (size_t)cbase * qo.ld;
+                ldo = qo.ld;
+            } else {
+                o = out + (size_t)job.slot * 16384 + (size_t)quad * 4096 + (size_t)c0 * 64 + r;
+                ldo = 64;
+            }
 #pragma unroll
             for (int cc = 0; cc < 32; cc += 8) {
                 float h[8];
@@ -344,10 +360,13 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
 #pragma unroll
                     for (int i = 0; i < 8; i++) h[i] = 0.f;
                 }
+                if (o) {
 #pragma unroll
-                for (int i = 0; i < 8; i++) {
-                    const double sc = scol ? (double)scol[cbase + cc + i] : 1.0;
-                    o[r + (cc + i) * 64] = ((double)h[i] + (double)lo[cc + i]) * srow * sc;
+                    for (int i = 0; i < 8; i++) {
+                        if (ldo != 64 && cbase + cc + i >= qo.ncols) continue;
+                        const double sc = scol ? (double)scol[cbase + cc + i] : 1.0;
+                        o[(size_t)(cc + i) * ldo] = ((double)h[i] + (double)lo[cc + i]) * srow * sc;
+                    }
                 }
             }
         }
@@ -411,7 +430,7 @@ size_t tc_smem_bytes() { return (size_t)kStages * kStageBytes + 1024 + 256; }
 
 signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSource &left, const TcSource &right,
                             const TcJob *d_jobs, int njobs, const TcPairs &pairs, const TcPairs *d_pairs, int chunk_kb,
-                            double *out, int *d_err, int kernel_class, cudaStream_t st)
+                            double *out, const TcQuadOut &qo, int *d_err, int kernel_class, cudaStream_t st)
 {
     if (njobs <= 0) return SIGNTRI_OK;
     if (pairs.n <= 0 || pairs.n > kTcMaxPairs || chunk_kb <= 0 || !d_pairs) return SIGNTRI_ERR_BAD_ARG;
@@ -428,7 +447,7 @@ signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSo
     SGT_CUDA_TRY(cudaFuncSetAttribute(tc_blocksum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps(kernel_class, st);
     tc_blocksum_kernel<<<njobs, kTcThreads, smem, st>>>(mt, mb, ml, mr, top.rows, left.rows, d_jobs, d_pairs, chunk_kb,
-                                                        top.scale, bot.scale, left.scale, right.scale, out, d_err);
+                                                        top.scale, bot.scale, left.scale, right.scale, out, qo, d_err);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }

@@ -41,10 +41,30 @@ struct TcSource {
     const float *scale;
 };
 
+// Alternative output: quadrant q of every job written into its own
+// column-major matrix m[q] (ld) at rows (q < 2 ? rt : rb) + r and columns
+// (q even ? cl : cr) + c (only those below nrows, ncols); m[q] == nullptr
+// skips the quadrant.  All four null:
+// slot mode (the `out` slabs).
+struct TcQuadOut {
+    double *m[4];
+    int ld;
+    int nrows, ncols;   // entries at or beyond these are not written
+};
+
 size_t tc_smem_bytes();
+
+// Slice pair lists (slices.cu): exact integer slices of 7 bits (weights
+// 2^{-7(s+t+2)}) and rounding splits (unit weights), s + t <= S - 1.
+TcPairs ozaki_pairs_impl(int S);
+TcPairs split_pairs(int S);
+signtri_status make_row_slices(int m, int k, const double *M, int ldm, int tri, int S, const float *scale,
+                               __nv_bfloat16 *R, int rows_pad, int ldr, cudaStream_t st);
+signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, int S, const float *scale,
+                               __nv_bfloat16 *C, int rows_pad, int ldc, cudaStream_t st);
 
 signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSource &left, const TcSource &right,
                             const TcJob *d_jobs, int njobs, const TcPairs &pairs, const TcPairs *d_pairs, int chunk_kb,
-                            double *out, int *d_err, int kernel_class, cudaStream_t st);
+                            double *out, const TcQuadOut &qo, int *d_err, int kernel_class, cudaStream_t st);
 
 }  // namespace signtri

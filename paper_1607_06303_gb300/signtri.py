@@ -88,6 +88,7 @@ _SIGNATURES = {
     "signtri_sylvester": (_I, [_I, _I, _VP, _I, _VP, _I, _VP, _I, _VP, _I, _VP]),
     "signtri_set_rates": (_I, [ctypes.c_double, ctypes.c_double]),
     "signtri_gemm_emulated": (_I, [_I, _I, _I, _VP, _I, _VP, _I, _VP, _I, _VP]),
+    "signtri_set_refinement": (_I, [ctypes.c_double, _I]),
 }
 
 SIGNTRI_NOALLOC_MAX_N = 1024
@@ -156,6 +157,10 @@ def signtri_sylvester(m, p, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, X_ptr, ldx, stre
 def signtri_gemm_emulated(m, n, k, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, stream=None) -> int:
     return load().signtri_gemm_emulated(m, n, k, A_ptr or None, lda, B_ptr or None, ldb, C_ptr or None, ldc,
                                         stream or None)
+
+
+def signtri_set_refinement(tol: float, max_steps: int) -> int:
+    return load().signtri_set_refinement(float(tol), int(max_steps))
 
 
 def signtri_set_rates(gemm_flops_per_s: float, givens_flops_per_s: float) -> int:

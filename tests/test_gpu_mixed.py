@@ -1,0 +1,61 @@
+"""GPU parity of the mixed-precision variants (tensor-core block sums, fp32
+leaves, refinement with emulated-float64 residuals) against the oracle.
+Bar: relative Frobenius error <= 1e-12 after refinement."""
+import numpy as np
+import pytest
+
+from paper_1607_06303_gb300.inputs import make_T
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-12
+
+
+def relerr(A, B):
+    nb = np.linalg.norm(B)
+    return np.linalg.norm(A - B) / (nb if nb > 0 else 1.0)
+
+
+def solve(p, T, variant):
+    import torch
+    Ut = p.sign(p.to_device(T), variant)
+    torch.cuda.synchronize()
+    return p.to_numpy(Ut), p.signtri_get_info()
+
+
+@pytest.mark.parametrize("variant", ["PH_MIXED_TF32", "PH_MIXED_BF16"])
+@pytest.mark.parametrize("n,pr,order", [(50, 0.5, "random"), (64, 0.5, "random"), (65, 0.4, "random"),
+                                        (130, 0.5, "random"), (257, 0.3, "random"), (300, 0.5, "sorted"),
+                                        (700, 0.5, "random"), (1000, 0.1, "random")])
+def test_mixed_vs_oracle(gpu_lib, oracle_mod, variant, n, pr, order):
+    T = make_T(n, pr, seed=41, order=order)
+    U, info = solve(gpu_lib, T, gpu_lib.Variant[variant])
+    Uo = oracle_mod.sign_tri(T, schedule="antidiag")
+    assert np.all(np.diag(U) == np.sign(np.diag(T)))
+    assert np.all(np.tril(U, -1) == 0.0)
+    err = relerr(U, Uo)
+    assert err <= TOL_MIXED, (err, info.as_dict())
+    assert info.variant == gpu_lib.Variant[variant], info.as_dict()     # no fallback needed
+    assert max(info.resid_commute, info.resid_involution) <= 1e-13
+
+
+@pytest.mark.parametrize("n", [1500, 2048])
+def test_mixed_medium(gpu_lib, oracle_mod, n):
+    T = make_T(n, 0.5, seed=42)
+    Uo = oracle_mod.sign_tri(T, schedule="antidiag")
+    for variant in ("PH_MIXED_TF32", "PH_MIXED_BF16"):
+        U, info = solve(gpu_lib, T, gpu_lib.Variant[variant])
+        assert relerr(U, Uo) <= TOL_MIXED, (variant, relerr(U, Uo), info.as_dict())
+
+
+def test_mixed_fallback_to_fp64(gpu_lib, oracle_mod):
+    # no refinement step allowed: the solver must fall back to float64
+    T = make_T(400, 0.5, seed=43)
+    try:
+        assert gpu_lib.signtri_set_refinement(1e-13, 0) == 0
+        U, info = solve(gpu_lib, T, gpu_lib.Variant.PH_MIXED_BF16)
+    finally:
+        gpu_lib.signtri_set_refinement(0, -1)
+    assert info.variant == gpu_lib.Variant.PH_FP64
+    assert info.refine_steps == 0
+    assert relerr(U, oracle_mod.sign_tri(T)) <= 1e-11
