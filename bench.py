@@ -7,6 +7,12 @@ One step = one sign_tri call on a resident input: inertia scan, variant
 choice, and the chosen variant's kernels.  The input (2.1 GB) and output are
 each larger than L2 (129 MB), so no flush is needed between steps.
 
+The headline is the mixed-precision form with refinement (PH_MIXED_TF32:
+tensor-core block sums, fp32 leaves, float64 defect correction with
+emulated-float64 residuals); the plain float64 form (PH_FP64) is timed on the
+same input for the comparison the metric names, and both are checked against
+the oracle on the leading and trailing 4096 principal windows.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--variant V]
     python bench.py --impl reference      # the CPU oracle, the reference arm
 
@@ -46,7 +52,9 @@ def parse_args():
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--p", type=float, default=0.5)
     ap.add_argument("--order", default="random")
-    ap.add_argument("--variant", default="AUTO")
+    ap.add_argument("--variant", default="PH_MIXED_TF32")
+    ap.add_argument("--compare", default="PH_FP64",
+                    help="variant timed beside the headline on the same input ('' to skip)")
     ap.add_argument("--cutoff", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -158,6 +166,14 @@ def block_sum_flops(n, b):
     return total
 
 
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "MEASURED_PEAKS.json"
+    except (OSError, ValueError):
+        return {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0}, "fallback"
+
+
 def src_sha(rel):
     with open(os.path.join(ROOT, rel), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()
@@ -262,11 +278,30 @@ def main():
                 "peak_source": "float64 FMA issue rate measured live by signtri_probe_fp64_peak (no FP64 entry "
                                "in MEASURED_PEAKS.json)",
                 "share_of_step": per_class[dom]["device_ms"] / ms_total}
+    elif dom in ("residual", "block_sums_tc"):
+        peaks, src = measured_peaks()
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        launches_dom = per_class[dom]["launches"]
+        cls = st.signtri.KC_RESIDUAL if dom == "residual" else st.signtri.KC_BLOCK_SUMS_TC
+        flops_all = st.signtri_profile_read_flops(cls)
+        per_launch = flops_all / launches_dom
+        avg_ms = per_class[dom]["device_ms"] / launches_dom
+        ach = per_launch / (avg_ms * 1e-3) / 1e12
+        sha = src_sha("paper_1607_06303_gb300/csrc/tc_gemm.cu")
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": TRAFFIC.get((dom, sha)),
+                "kernel": "tc_blocksum_kernel (tcgen05 bf16, %s)" % ("emulated-float64 residual products"
+                                                                     if dom == "residual" else "block sums"),
+                "algorithmic_flops_per_launch": per_launch,
+                "peak_source": "bf16_tflops_sustained of %s (kernel timed inside a long step)" % src,
+                "share_of_step": per_class[dom]["device_ms"] / ms_total}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step_max, "seconds_per_solve": ms_step_max / 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if variant in (st.Variant.PH_FP64, st.Variant.PS_FP64) else "bf16+f32+f64",
+        "data": "synthetic",
         "config": {"workload": "sign(T) n=%d p=%g %s diagonal, |t_ii|~U[0.5,2], t_ij~N(0,1/n), seed=rank"
                                % (n, args.p, args.order),
                    "n": n, "p": args.p, "order": args.order, "variant_requested": args.variant,
@@ -274,7 +309,37 @@ def main():
                    "cutoff": info.cutoff, "useful_flops_per_solve": useful,
                    "l2": "no flush: T and U are 2.1 GB each, > 129 MB L2", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "gpu_launches": launches, "kernel_time_ms": per_class, "roofline": roof, "clocks": clk,
+        "refinement": {"steps": info.refine_steps, "resid_commute": info.resid_commute,
+                       "resid_involution": info.resid_involution},
     }
+
+    # the comparison variant on the same input (float64 form), fewer steps
+    Uc = None
+    if args.compare and args.compare != args.variant:
+        cv = st.Variant[args.compare]
+        Uc = torch.empty_like(Tt)
+
+        def cstep():
+            s_ = st.sign_tri(n, Tt.data_ptr(), n, Uc.data_ptr(), n, cv, h)
+            if s_ != 0:
+                raise st.SignTriError(s_, "sign_tri")
+        cstep()
+        barrier()
+        ck = max(1, min(args.steps, 2))
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(ck):
+            cstep()
+        c1.record(stream)
+        barrier()
+        cms = c0.elapsed_time(c1) / ck
+        tc_ = torch.tensor([cms], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(tc_, op=dist.ReduceOp.MAX)
+        cms = float(tc_.item())
+        line["compare"] = {"variant": args.compare, "steps": ck, "seconds_per_solve": cms / 1e3,
+                           "value": world * useful / (cms * 1e-3) / 1e9, "unit": UNIT,
+                           "speedup_of_headline": cms / ms_step_max}
 
     # end to end through the public API with host buffers
     if not args.no_e2e:
@@ -313,13 +378,20 @@ def main():
         line["cpu_baseline"] = {"value": fw / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": "leading %dx%d principal window of the same input, one solve "
                                           "(%.3g useful flops, %.1f s)" % (m, m, fw, dt)}
-        Ug = Ut[:m, :m].cpu().numpy().T      # U[:m,:m] (column-major storage transposed back)
-        line["rel_err_vs_oracle_window"] = float(np.linalg.norm(Ug - Uo) / np.linalg.norm(Uo))
-        # the trailing window: the same principal-window property
         Tw2 = np.asfortranarray(T[n - m:, n - m:])
         Uo2 = oracle.sign_tri(Tw2, schedule="antidiag", threads=threads)
-        Ug2 = Ut[n - m:, n - m:].cpu().numpy().T
-        line["rel_err_vs_oracle_trailing_window"] = float(np.linalg.norm(Ug2 - Uo2) / np.linalg.norm(Uo2))
+
+        def window_errs(Udev):
+            Ug = Udev[:m, :m].cpu().numpy().T      # U[:m,:m] (column-major storage transposed back)
+            Ug2 = Udev[n - m:, n - m:].cpu().numpy().T
+            return (float(np.linalg.norm(Ug - Uo) / np.linalg.norm(Uo)),
+                    float(np.linalg.norm(Ug2 - Uo2) / np.linalg.norm(Uo2)))
+        # principal-window property: u_ij depends on T[i..j, i..j] only, so the
+        # oracle on a window equals the full oracle there
+        line["rel_err_vs_oracle_window"], line["rel_err_vs_oracle_trailing_window"] = window_errs(Ut)
+        if Uc is not None:
+            line["compare"]["rel_err_vs_oracle_window"], line["compare"]["rel_err_vs_oracle_trailing_window"] = \
+                window_errs(Uc)
 
     if rank == 0:
         print(json.dumps(line), flush=True)

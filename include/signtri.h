@@ -182,14 +182,15 @@ enum {
     SIGNTRI_KC_BLOCK_SUMS_TC = 5, /* tensor-core block sums (mixed variants) */
     SIGNTRI_KC_OFFDIAG_LEAF_F32 = 6, /* off-diagonal leaves of the mixed variants */
     SIGNTRI_KC_CONVERT = 7,       /* precision conversion / splitting */
-    SIGNTRI_KC_RESIDUAL = 8,      /* refinement residuals */
+    SIGNTRI_KC_RESIDUAL = 8,      /* refinement residual products (tensor cores) */
     SIGNTRI_KC_CORRECTION = 9,    /* refinement corrections */
     SIGNTRI_KC_GIVENS = 10,       /* Parlett-Sylvester reorder rounds */
     SIGNTRI_KC_SYLV_SUMS = 11,    /* Sylvester block sums */
     SIGNTRI_KC_SYLV_LEAF = 12,    /* Sylvester in-block recurrence */
     SIGNTRI_KC_GEMM_F64 = 13,     /* float64 GEMM (back-transform) */
     SIGNTRI_KC_OTHER = 14,
-    SIGNTRI_KC_COUNT = 15
+    SIGNTRI_KC_RESIDUAL_SUM = 15, /* residual assembly and norms */
+    SIGNTRI_KC_COUNT = 16
 };
 
 /* on != 0: bracket every library kernel launch with CUDA events on its
@@ -202,6 +203,10 @@ signtri_status signtri_profile_reset(void);
    in milliseconds (waits for the recorded events).  Either pointer may be
    NULL. */
 signtri_status signtri_profile_read(int cls, long long *launches, double *device_ms);
+/* Algorithmic tensor-core flops issued by launches of class `cls` since the
+   last reset: 2*64*64*64 per (slice pair, K-block, used 64x64 quadrant) of
+   every tensor-core job.  Zero for classes that do not use tensor cores. */
+signtri_status signtri_profile_read_flops(int cls, double *flops);
 /* Name of a kernel class ("" when out of range). */
 const char *signtri_kernel_class_name(int cls);
 /* Float64 fused-multiply-add issue rate of the current device, GFLOP/s

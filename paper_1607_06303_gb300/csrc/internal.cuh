@@ -47,6 +47,8 @@ struct Arena {
 // Launch accounting (prof.cu): bracket every library launch.
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st);
+// Algorithmic tensor-core flops of a launch (counted on the host).
+void prof_add_flops(int cls, double flops);
 
 struct ProfScope {
     int cls;

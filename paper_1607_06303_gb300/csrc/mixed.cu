@@ -112,14 +112,22 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
         const int p = idx % MB, q = idx / MB;
         const int gi = r0 + p, gj = c0 + q;
         const bool opp = (srow[p] + scol[q] == 0.f);
-        double x = 0.0, y = 0.0;
+        // partial block sums: float2 (hi, lo) per element, summed in fp32
+        float x = 0.f, y = 0.f;
+        const float2 *PA2 = reinterpret_cast<const float2 *>(PA);
+        const float2 *PB2 = reinterpret_cast<const float2 *>(PB);
+#pragma unroll 4
         for (int s = 0; s < nsplit; s++) {
-            const double *pa = PA + ((size_t)I * nsplit + s) * 16384 + p + (size_t)q * 64;
-            if (opp) x += pa[0] - pa[3 * 4096];
-            else if (MODE == 0) y += pa[4096];
-            else {
-                const double *pb = PB + ((size_t)I * nsplit + s) * 16384 + p + (size_t)q * 64;
-                y += pb[0] + pb[3 * 4096];
+            const size_t e = ((size_t)I * nsplit + s) * 16384 + p + (size_t)q * 64;
+            if (opp) {
+                const float2 tl = PA2[e], br = PA2[e + 3 * 4096];
+                x += (tl.x - br.x) + (tl.y - br.y);
+            } else if (MODE == 0) {
+                const float2 tr = PA2[e + 4096];
+                y += tr.x + tr.y;
+            } else {
+                const float2 tl = PB2[e], br = PB2[e + 3 * 4096];
+                y += (tl.x + br.x) + (tl.y + br.y);
             }
         }
         float c;
@@ -127,16 +135,16 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
             float a = 0.f, b = 0.f;
             for (int k = p + 1; k < MB; k++) a = fmaf(DI[p + k * LD], Vs[k + q * LD], a);
             for (int k = 0; k < q; k++) b = fmaf(Vs[p + k * LD], DJ[k + q * LD], b);
-            const double base = (MODE == 0) ? SGT_AT(T, ldt, gi, gj) * (double)(srow[p] - scol[q])
-                                            : -SGT_AT(Rc, ldr, gi, gj);
-            c = (float)(base + x) + a - b;
+            const float base = (MODE == 0) ? (float)SGT_AT(T, ldt, gi, gj) * (srow[p] - scol[q])
+                                           : -(float)SGT_AT(Rc, ldr, gi, gj);
+            c = base + x + a - b;
         } else if (MODE == 0) {
-            c = (float)(-y);
+            c = -y;
         } else {
             float a = 0.f, b = 0.f;
             for (int k = p + 1; k < MB; k++) a = fmaf(EI[p + k * LD], WS[k + q * LD], a);
             for (int k = 0; k < q; k++) b = fmaf(WS[p + k * LD], EJ[k + q * LD], b);
-            c = (float)(-SGT_AT(Rs, ldr, gi, gj) - y) - a - b;
+            c = -(float)SGT_AT(Rs, ldr, gi, gj) - y - a - b;
         }
         Cs[p + q * LD] = c;
     }
@@ -415,27 +423,31 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
     const TcSource srcU_r{c.Ur, c.S, c.np, c.np, c.np, nullptr}, srcU_c{c.Uc, c.S, c.np, c.np, c.np, nullptr};
     const TcQuadOut slots{{nullptr, nullptr, nullptr, nullptr}, 0, 0, 0};
     // K-blocks per tensor-core unit: small when several slice pairs share a
-    // chunk (they re-read its panels from L2), larger for a single pair
+    // unit (they re-read its panels from L2), larger for a single pair
     const int chunk = c.pairs_split.n > 1 ? 4 : 16;
     for (int d = 1; d < nb; d++) {
         const int ntiles = nb - d;
         const int njobs = c.sc.job_off[d + 1] - c.sc.job_off[d];
         const TcJob *jobs = c.d_jobs + c.sc.job_off[d];
+        const long long sum_kb = (long long)ntiles * (d - 1);
         signtri_status rs;
         if (njobs > 0) {
             if (MODE == 0) {
                 // [U_I.; T_I.] x [T_.J | U_.J]: TL = U T, TR = U U, BR = T U
                 rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
-                                  c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st);
+                                  c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st,
+                                  tc_flops(c.pairs_split.n, sum_kb, 3));
                 if (rs != SIGNTRI_OK) return rs;
             } else {
                 // X^E: [E_I.; T_I.] x [T_.J | E_.J]: TL = E T, BR = T E
                 rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
-                                  c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st);
+                                  c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st,
+                                  tc_flops(c.pairs_split.n, sum_kb, 2));
                 if (rs != SIGNTRI_OK) return rs;
                 // Y^E: [U0_I.; E_I.] x [E_.J | U0_.J]: TL = U0 E, BR = E U0
                 rs = tc_blocksums(srcU_r, srcV_r, srcV_c, srcU_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
-                                  c.PB, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st);
+                                  c.PB, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st,
+                                  tc_flops(c.pairs_split.n, sum_kb, 2));
                 if (rs != SIGNTRI_OK) return rs;
             }
         }
@@ -457,12 +469,14 @@ signtri_status residual(MixedCtx &c, const double *T, int ldt, const double *U, 
     const TcSource left{c.NUc, kOzakiSlices, c.np, c.np, c.np, c.sUc},
         right{c.NTc, kOzakiSlices, c.np, c.np, c.np, c.sTc};
     const TcQuadOut qo{{c.Rc, nullptr, c.Rs, c.Put}, c.n, c.n, c.n};
-    rs = tc_blocksums(top, bot, left, right, c.d_res_jobs, c.n_res_jobs, c.pairs_oz, c.d_pairs_oz, 4, nullptr, qo,
-                      c.d_err, SIGNTRI_KC_RESIDUAL, c.st);
+    const long long nbl = c.sc.nb;
+    const long long sum_kb = (nbl + 2) * (nbl + 1) * nbl / 6;   // sum over I <= J of (J - I + 1)
+    rs = tc_blocksums(top, bot, left, right, c.d_res_jobs, c.n_res_jobs, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qo,
+                      c.d_err, SIGNTRI_KC_RESIDUAL, c.st, tc_flops(c.pairs_oz.n, sum_kb, 3));
     if (rs != SIGNTRI_OK) return rs;
     SGT_CUDA_TRY(cudaMemsetAsync(c.norms, 0, 8 * sizeof(double), c.st));
     {
-        ProfScope ps(SIGNTRI_KC_RESIDUAL, c.st);
+        ProfScope ps(SIGNTRI_KC_RESIDUAL_SUM, c.st);
         residual_finalize_kernel<<<c.n, 256, 0, c.st>>>(c.n, T, ldt, U, ldu, c.Rc, c.Put, c.Rs, c.n, c.norms);
         SGT_LAUNCH_CHECK();
     }
@@ -512,11 +526,15 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
         return SIGNTRI_ERR_NO_WORKSPACE;
     c.pairs_split = split_pairs(S);
     c.pairs_oz = ozaki_pairs_impl(kOzakiSlices);
-    // residual jobs by block row: CTAs resident together share the row panels
+    // residual jobs in 8 x 8 groups of tiles: the CTAs resident together
+    // share row and column panels in L2
     std::vector<TcJob> rj;
     rj.reserve(c.n_res_jobs);
-    for (int I = 0; I < nb; I++)
-        for (int J = I; J < nb; J++) {
+    constexpr int G = 8;
+    for (int I0 = 0; I0 < nb; I0 += G)
+        for (int J0 = I0 / G * G; J0 < nb; J0 += G)
+            for (int I = I0; I < std::min(I0 + G, nb); I++)
+                for (int J = std::max(J0, I); J < std::min(J0 + G, nb); J++) {
             TcJob j;
             j.rt = I * MB; j.rb = I * MB; j.cl = J * MB; j.cr = J * MB;
             j.kb0 = I; j.kb1 = J + 1; j.slot = 0; j.pad = 0;

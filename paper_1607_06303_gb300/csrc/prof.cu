@@ -23,6 +23,7 @@ std::mutex p_mu;
 bool p_enabled = false;
 long long p_launches[SIGNTRI_KC_COUNT] = {};
 double p_ms[SIGNTRI_KC_COUNT] = {};
+double p_flops[SIGNTRI_KC_COUNT] = {};
 std::vector<Pending> p_pending;
 std::vector<cudaEvent_t> p_free;
 thread_local int p_open_cls = -1;
@@ -43,7 +44,7 @@ cudaEvent_t take_event()
 const char *kClassNames[SIGNTRI_KC_COUNT] = {
     "inertia_scan", "fill", "diag_leaf_f64", "block_sums_f64", "offdiag_leaf_f64",
     "block_sums_tc", "offdiag_leaf_mixed", "convert", "residual", "correction",
-    "givens_rounds", "sylvester_sums", "sylvester_leaf", "gemm_f64", "other",
+    "givens_rounds", "sylvester_sums", "sylvester_leaf", "gemm_f64", "other", "residual_sum",
 };
 
 }  // namespace
@@ -56,6 +57,12 @@ void prof_begin(int cls, cudaStream_t st)
     p_open_cls = cls;
     p_open_ev = take_event();
     if (p_open_ev) cudaEventRecord(p_open_ev, st);
+}
+
+void prof_add_flops(int cls, double flops)
+{
+    std::lock_guard<std::mutex> lk(p_mu);
+    if (cls >= 0 && cls < SIGNTRI_KC_COUNT) p_flops[cls] += flops;
 }
 
 void prof_end(int cls, cudaStream_t st)
@@ -111,7 +118,7 @@ signtri_status signtri_profile_reset(void)
     std::lock_guard<std::mutex> lk(p_mu);
     for (auto &p : p_pending) { p_free.push_back(p.a); p_free.push_back(p.b); }
     p_pending.clear();
-    for (int i = 0; i < SIGNTRI_KC_COUNT; i++) { p_launches[i] = 0; p_ms[i] = 0.0; }
+    for (int i = 0; i < SIGNTRI_KC_COUNT; i++) { p_launches[i] = 0; p_ms[i] = 0.0; p_flops[i] = 0.0; }
     return SIGNTRI_OK;
 }
 
@@ -130,6 +137,14 @@ signtri_status signtri_profile_read(int cls, long long *launches, double *device
     p_pending.clear();
     if (launches) *launches = p_launches[cls];
     if (device_ms) *device_ms = p_ms[cls];
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_profile_read_flops(int cls, double *flops)
+{
+    if (cls < 0 || cls >= SIGNTRI_KC_COUNT || !flops) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(p_mu);
+    *flops = p_flops[cls];
     return SIGNTRI_OK;
 }
 

@@ -152,7 +152,9 @@ __global__ void gather_gemm_kernel(int m, int n, const double *__restrict__ out,
     const int I = i / 64, J2 = j / 128, jj = j % 128;
     const size_t slot = (size_t)I * ntj + J2;
     const int quad = jj < 64 ? 0 : 1;
-    SGT_AT(C, ldc, i, j) = out[slot * 16384 + (size_t)quad * 4096 + (i % 64) + (size_t)(jj % 64) * 64];
+    const float2 v = reinterpret_cast<const float2 *>(out)[slot * 16384 + (size_t)quad * 4096 + (i % 64) +
+                                                            (size_t)(jj % 64) * 64];
+    SGT_AT(C, ldc, i, j) = (double)v.x + (double)v.y;
 }
 
 }  // namespace

@@ -17,7 +17,7 @@
 // integer below 2^24 and therefore exact, which makes the emulated product
 // accurate to the split (about 2^-48 relative to |A||B| with 7 slices).
 //
-// Warp roles (576 threads): warp 0 issues TMA loads into a 4-stage ring,
+// Warp roles (576 threads): warp 0 issues TMA loads into a 6-stage ring,
 // warp 1 issues the MMAs (one thread) into 3 TMEM buffers of 128 columns,
 // warps 2..17 drain TMEM (four warps per 32-lane quadrant, 32 columns each)
 // and keep the fp32 hi parts of the accumulators in the 4th 128-column TMEM
@@ -35,7 +35,7 @@ namespace signtri {
 
 namespace {
 
-constexpr int kStages = 4;
+constexpr int kStages = 6;
 constexpr int kTcThreads = 576;            // 2 control warps + 16 epilogue warps
 constexpr int kStageBytes = 32768;          // A 128x64 + B 128x64 bf16
 constexpr int kBufs = 3;                    // TMEM accumulator buffers of 128 columns; the 4th holds hi
@@ -178,12 +178,16 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
     uint64_t *done_bar = tempty + 4;
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(done_bar + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+    TcPairs *pairs_s = reinterpret_cast<TcPairs *>(smem + kStages * kStageBytes + 512);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const TcJob job = jobs[blockIdx.x];
     const int nkb = job.kb1 - job.kb0;
     const int nchunks = nkb > 0 ? (nkb + chunk_kb - 1) / chunk_kb : 0;
-    const TcPairs &pairs = *pairs_g;
+    for (int i = threadIdx.x; i < (int)(sizeof(TcPairs) / 4); i += blockDim.x)
+        reinterpret_cast<int *>(pairs_s)[i] = reinterpret_cast<const int *>(pairs_g)[i];
+    __syncthreads();
+    const TcPairs &pairs = *pairs_s;
     const int nunits = pairs.n * nchunks;
 
     if (threadIdx.x == 0) {
@@ -338,20 +342,22 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
             const float *scol = half ? sRight : sLeft;
             const int cbase = (half ? job.cr : job.cl) + c0;
             const int quad = (bottom ? 2 : 0) + half;
-            double *o;
-            size_t ldo;
-            if (qo.m[0] || qo.m[1] || qo.m[2] || qo.m[3]) {
+            const bool quad_mode = qo.m[0] || qo.m[1] || qo.m[2] || qo.m[3];
+            double *o = nullptr;
+            float2 *o2 = nullptr;
+            if (quad_mode) {
                 // quadrant-matrix mode: element (row, col) of quadrant q goes to
-                // m[q][(row base + r) + (col base + c) * ld]; null m[q] = skip
+                // m[q][(row base + r) + (col base + c) * ld] as float64; null m[q] = skip
                 o = qo.m[quad];
                 const int grow = (bottom ? job.rb : job.rt) + r;
                 if (grow >= qo.nrows) o = nullptr;
                 if (o) o += (size_t)grow + (size_t)cbase * qo.ld;
-                ldo = qo.ld;
             } else {
-                o = out + (size_t)job.slot * 16384 + (size_t)quad * 4096 + (size_t)c0 * 64 + r;
-                ldo = 64;
+                // slot mode: (hi, lo) pairs, float2 per element
+                o2 = reinterpret_cast<float2 *>(out) + (size_t)job.slot * 16384 + (size_t)quad * 4096 +
+                     (size_t)c0 * 64 + r;
             }
+            const float srow_f = (float)srow;
 #pragma unroll
             for (int cc = 0; cc < 32; cc += 8) {
                 float h[8];
@@ -360,13 +366,13 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
 #pragma unroll
                     for (int i = 0; i < 8; i++) h[i] = 0.f;
                 }
-                if (o) {
 #pragma unroll
-                    for (int i = 0; i < 8; i++) {
-                        if (ldo != 64 && cbase + cc + i >= qo.ncols) continue;
-                        const double sc = scol ? (double)scol[cbase + cc + i] : 1.0;
-                        o[(size_t)(cc + i) * ldo] = ((double)h[i] + (double)lo[cc + i]) * srow * sc;
-                    }
+                for (int i = 0; i < 8; i++) {
+                    // scales are powers of two: exact in fp32
+                    const float sc = __fmul_rn(srow_f, scol ? scol[cbase + cc + i] : 1.f);
+                    const float hs = __fmul_rn(h[i], sc), ls = __fmul_rn(lo[cc + i], sc);
+                    if (o2) o2[(size_t)(cc + i) * 64] = make_float2(hs, ls);
+                    else if (o && cbase + cc + i < qo.ncols) o[(size_t)(cc + i) * qo.ld] = (double)hs + (double)ls;
                 }
             }
         }
@@ -426,11 +432,12 @@ signtri_status make_map(CUtensorMap *m, const __nv_bfloat16 *base, long long row
 
 }  // namespace
 
-size_t tc_smem_bytes() { return (size_t)kStages * kStageBytes + 1024 + 256; }
+size_t tc_smem_bytes() { return (size_t)kStages * kStageBytes + 1024 + 512 + sizeof(TcPairs) + 64; }
 
 signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSource &left, const TcSource &right,
                             const TcJob *d_jobs, int njobs, const TcPairs &pairs, const TcPairs *d_pairs, int chunk_kb,
-                            double *out, const TcQuadOut &qo, int *d_err, int kernel_class, cudaStream_t st)
+                            double *out, const TcQuadOut &qo, int *d_err, int kernel_class, cudaStream_t st,
+                            double useful_flops)
 {
     if (njobs <= 0) return SIGNTRI_OK;
     if (pairs.n <= 0 || pairs.n > kTcMaxPairs || chunk_kb <= 0 || !d_pairs) return SIGNTRI_ERR_BAD_ARG;
@@ -445,6 +452,7 @@ signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSo
     if (top.rows != bot.rows || left.rows != right.rows) return SIGNTRI_ERR_BAD_ARG;
     const size_t smem = tc_smem_bytes();
     SGT_CUDA_TRY(cudaFuncSetAttribute(tc_blocksum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    prof_add_flops(kernel_class, useful_flops);
     ProfScope ps(kernel_class, st);
     tc_blocksum_kernel<<<njobs, kTcThreads, smem, st>>>(mt, mb, ml, mr, top.rows, left.rows, d_jobs, d_pairs, chunk_kb,
                                                         top.scale, bot.scale, left.scale, right.scale, out, qo, d_err);

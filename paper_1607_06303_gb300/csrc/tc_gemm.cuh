@@ -12,8 +12,9 @@ constexpr int kTcMaxPairs = 36;
 // One CTA's work: rows [rt, rt+64) of the top source and [rb, rb+64) of the
 // bottom source form A; rows [cl, cl+64) of the left and [cr, cr+64) of the
 // right source form B; K = 64-blocks [kb0, kb1).  The four 64 x 64 quadrants
-// of A B^T go to out + slot * 16384 doubles, quadrant q (0 top-left,
-// 1 top-right, 2 bottom-left, 3 bottom-right) at + q * 4096, column-major.
+// of A B^T go to out + slot * 16384 float2 (hi, lo) pairs, quadrant q
+// (0 top-left, 1 top-right, 2 bottom-left, 3 bottom-right) at + q * 4096,
+// column-major; the value is hi + lo.
 struct TcJob {
     int rt, rb, cl, cr;
     int kb0, kb1;
@@ -65,6 +66,13 @@ signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, 
 
 signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSource &left, const TcSource &right,
                             const TcJob *d_jobs, int njobs, const TcPairs &pairs, const TcPairs *d_pairs, int chunk_kb,
-                            double *out, const TcQuadOut &qo, int *d_err, int kernel_class, cudaStream_t st);
+                            double *out, const TcQuadOut &qo, int *d_err, int kernel_class, cudaStream_t st,
+                            double useful_flops = 0.0);
+
+// 2 * 64^3 flops per (slice pair, K-block, used quadrant)
+inline double tc_flops(int npairs, long long sum_kb, int quadrants)
+{
+    return 2.0 * 64.0 * 64.0 * 64.0 * (double)npairs * (double)sum_kb * (double)quadrants;
+}
 
 }  // namespace signtri

@@ -89,6 +89,7 @@ _SIGNATURES = {
     "signtri_set_rates": (_I, [ctypes.c_double, ctypes.c_double]),
     "signtri_gemm_emulated": (_I, [_I, _I, _I, _VP, _I, _VP, _I, _VP, _I, _VP]),
     "signtri_set_refinement": (_I, [ctypes.c_double, _I]),
+    "signtri_profile_read_flops": (_I, [_I, ctypes.POINTER(ctypes.c_double)]),
 }
 
 SIGNTRI_NOALLOC_MAX_N = 1024
@@ -96,8 +97,8 @@ SIGNTRI_NOALLOC_MAX_N = 1024
 # kernel classes of the launch accounting (include/signtri.h)
 KC_SCAN, KC_FILL, KC_DIAG_LEAF, KC_BLOCK_SUMS_F64, KC_OFFDIAG_LEAF = 0, 1, 2, 3, 4
 KC_BLOCK_SUMS_TC, KC_OFFDIAG_LEAF_MIXED, KC_CONVERT, KC_RESIDUAL, KC_CORRECTION = 5, 6, 7, 8, 9
-KC_GIVENS, KC_SYLV_SUMS, KC_SYLV_LEAF, KC_GEMM_F64, KC_OTHER = 10, 11, 12, 13, 14
-KC_COUNT = 15
+KC_GIVENS, KC_SYLV_SUMS, KC_SYLV_LEAF, KC_GEMM_F64, KC_OTHER, KC_RESIDUAL_SUM = 10, 11, 12, 13, 14, 15
+KC_COUNT = 16
 
 
 def load(path: str = LIB_PATH):
@@ -206,6 +207,14 @@ def signtri_profile_read(cls: int):
     if st != 0:
         raise SignTriError(st, "signtri_profile_read")
     return n.value, ms.value
+
+
+def signtri_profile_read_flops(cls: int) -> float:
+    f = ctypes.c_double(0)
+    st = load().signtri_profile_read_flops(cls, ctypes.byref(f))
+    if st != 0:
+        raise SignTriError(st, "signtri_profile_read_flops")
+    return f.value
 
 
 def signtri_kernel_class_name(cls: int) -> str:
