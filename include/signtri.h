@@ -127,6 +127,30 @@ signtri_status sign_tri(int n, const double *T, int ldt, double *U, int ldu,
 signtri_status sign_tri_host(int n, const double *T_host, int ldt, double *U_host, int ldu,
                              signtri_variant v, void *stream);
 
+/* Many independent problems in one call.  Host arrays of length count:
+   n[m], ldt[m], ldu[m], and T[m], U[m] (DEVICE pointers, the same conventions
+   as sign_tri).  info[m] (host) receives each problem's status; a bad matrix
+   does not stop the others.  Per matrix: the inertia scan (one batched
+   launch), +-I for trivial inertia, and for the rest the variant `v` (AUTO:
+   Parlett-Higham or Parlett-Sylvester from the Section 3 estimates).  All
+   Parlett-Higham float64 problems run together as one CUDA graph of
+   level-synchronous launches (leaf size per problem from the cutoff table);
+   the others run one after another.  Returns after all U[m] are written.
+   The return value reports failures of the call itself. */
+signtri_status sign_tri_batched(int count, const int *n, const double *const *T, const int *ldt,
+                                double *const *U, const int *ldu, signtri_variant v, int *info,
+                                void *stream);
+
+/* Leaf-size table of the batched path: b[k] (16, 32, 64, or 0 = the
+   process-wide cutoff) for problems with floor(log2 n) == k, k < len <= 32. */
+signtri_status signtri_set_cutoff_table(const int *b, int len);
+signtri_status signtri_get_cutoff_table(int *b, int len);
+
+/* Autotuner: for n = 32, 64, ..., up to n_max (<= 32768), time the float64
+   Parlett-Higham path on a synthetic problem with each leaf size and store
+   the fastest in the cutoff table.  Allocates two n_max x n_max matrices. */
+signtri_status signtri_autotune(int n_max, void *stream);
+
 /* Inertia scan alone (Section 3): counts of positive and negative diagonal
    entries and the number of adjacent swaps that group positives first.
    Synchronous on `stream`.  Any output pointer may be NULL. */
@@ -190,7 +214,8 @@ enum {
     SIGNTRI_KC_GEMM_F64 = 13,     /* float64 GEMM (back-transform) */
     SIGNTRI_KC_OTHER = 14,
     SIGNTRI_KC_RESIDUAL_SUM = 15, /* residual assembly and norms */
-    SIGNTRI_KC_COUNT = 16
+    SIGNTRI_KC_BATCH_GRAPH = 16,  /* one launch of the captured batch graph */
+    SIGNTRI_KC_COUNT = 17
 };
 
 /* on != 0: bracket every library kernel launch with CUDA events on its

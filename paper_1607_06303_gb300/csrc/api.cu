@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -36,6 +38,8 @@ struct DeviceState {
 std::mutex g_mu;
 DeviceState g_dev[kMaxDevices];
 int g_cutoff = kDefaultCutoff;
+// leaf size per size bucket floor(log2 n) for the batched path; 0 = g_cutoff
+int g_cutoff_table[32] = {};
 // flops/s used by the AUTO choice (float64 block products; Givens rounds)
 constexpr double kDefaultGemmRate = 1.0e12;
 constexpr double kDefaultGivensRate = 0.35e12;
@@ -232,6 +236,39 @@ void reset_info(int n)
     g_info.variant = -1;
 }
 
+int cutoff_for(int n)
+{
+    int k = 0;
+    while ((2 << k) <= n && k < 31) k++;
+    return g_cutoff_table[k] ? g_cutoff_table[k] : g_cutoff;
+}
+
+// Synthetic upper-triangular T for the autotuner: counter-based hash
+// (splitmix64) of (seed, i, j); diagonal sign +-1 with probability 1/2 and
+// magnitude in [0.5, 2]; strictly upper N(0, 1/n) by Box-Muller.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void synth_kernel(int n, double *T, unsigned long long seed)
+{
+    const int j = blockIdx.x;
+    const double sc = rsqrt((double)n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long h1 = mix64(seed ^ ((unsigned long long)i << 32 | (unsigned)j));
+        const unsigned long long h2 = mix64(h1);
+        const double u1 = ((h1 >> 11) + 1) * (1.0 / 9007199254740993.0), u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);
+        double v = 0.0;
+        if (i == j) v = ((h2 & 1) ? -1.0 : 1.0) * (0.5 + 1.5 * u1);
+        else if (i < j) v = sc * sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+        SGT_AT(T, n, i, j) = v;
+    }
+}
+
 }  // namespace
 
 int signtri::current_cutoff()
@@ -271,6 +308,169 @@ signtri_status signtri_set_rates(double gemm_flops_per_s, double givens_flops_pe
     g_rate_gemm = gemm_flops_per_s > 0 ? gemm_flops_per_s : kDefaultGemmRate;
     g_rate_givens = givens_flops_per_s > 0 ? givens_flops_per_s : kDefaultGivensRate;
     return SIGNTRI_OK;
+}
+
+signtri_status sign_tri_batched(int count, const int *n, const double *const *T, const int *ldt, double *const *U,
+                                const int *ldu, signtri_variant v, int *info, void *stream)
+{
+    reset_info(-1);
+    if (count < 0 || !valid_variant(v)) return SIGNTRI_ERR_BAD_ARG;
+    if (count == 0) return SIGNTRI_OK;
+    if (!n || !T || !ldt || !U || !ldu || !info) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<BatchDesc> descs;
+    std::vector<int> owner, sizes, bs;
+    int nmax = 0;
+    for (int m = 0; m < count; m++) {
+        info[m] = SIGNTRI_OK;
+        if (n[m] < 0 || (n[m] > 0 && (!T[m] || !U[m] || ldt[m] < n[m] || ldu[m] < n[m]))) {
+            info[m] = SIGNTRI_ERR_BAD_ARG;
+            continue;
+        }
+        if (n[m] == 0) continue;
+        descs.push_back({T[m], U[m], n[m], ldt[m], ldu[m], 0});
+        owner.push_back(m);
+        sizes.push_back(n[m]);
+        bs.push_back(cutoff_for(n[m]));
+        nmax = std::max(nmax, n[m]);
+    }
+    const int cnt = (int)descs.size();
+    if (cnt == 0) return SIGNTRI_OK;
+    // workspace: descriptors, scan results, fill lists, then the batched plan
+    // for every matrix with its cutoff (an upper bound of what runs batched)
+    size_t plan = 0;
+    for (int B : {16, 32, 64}) {
+        std::vector<int> ns;
+        for (int k = 0; k < cnt; k++)
+            if (bs[k] == B) ns.push_back(sizes[k]);
+        if (!ns.empty()) plan = std::max(plan, batched_workspace_bytes((int)ns.size(), ns.data(), B));
+    }
+    const size_t fixed = (size_t)cnt * (sizeof(BatchDesc) + sizeof(ScanResult) + sizeof(int) + sizeof(double)) +
+                         8 * 256;
+    Arena ws;
+    rs = get_workspace(*s, fixed + plan, ws);
+    if (rs != SIGNTRI_OK) return rs;
+    auto *d_descs = static_cast<BatchDesc *>(ws.take(cnt * sizeof(BatchDesc)));
+    auto *d_scan = static_cast<ScanResult *>(ws.take(cnt * sizeof(ScanResult)));
+    auto *d_which = static_cast<int *>(ws.take(cnt * sizeof(int)));
+    auto *d_diag = static_cast<double *>(ws.take(cnt * sizeof(double)));
+    if (!d_descs || !d_scan || !d_which || !d_diag) return SIGNTRI_ERR_NO_WORKSPACE;
+    SGT_CUDA_TRY(cudaMemcpyAsync(d_descs, descs.data(), cnt * sizeof(BatchDesc), cudaMemcpyHostToDevice, st));
+    rs = launch_inertia_scan_batched(cnt, d_descs, d_scan, st);
+    if (rs != SIGNTRI_OK) return rs;
+    std::vector<ScanResult> sr(cnt);
+    SGT_CUDA_TRY(cudaMemcpyAsync(sr.data(), d_scan, cnt * sizeof(ScanResult), cudaMemcpyDeviceToHost, st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    // per matrix: error, +-I, batched Parlett-Higham, or a single-matrix variant
+    std::vector<int> which;
+    std::vector<double> diagv;
+    std::vector<int> ph_bs(cnt, 0);
+    std::vector<std::pair<int, signtri_variant>> singles;
+    for (int k = 0; k < cnt; k++) {
+        const ScanResult &r = sr[k];
+        const int m = owner[k];
+        if (r.bad_key != INT_MAX) { info[m] = r.bad_key % 4; continue; }
+        if (r.n_neg == 0 || r.n_pos == 0) {
+            which.push_back(k);
+            diagv.push_back(r.n_neg == 0 ? 1.0 : -1.0);
+            continue;
+        }
+        signtri_variant run = v;
+        if (v == SIGNTRI_AUTO) run = choose_variant(sizes[k], r);
+        if (run == SIGNTRI_PH_FP64) {
+            ph_bs[k] = bs[k];
+            which.push_back(k);
+            diagv.push_back(0.0);      // zero the strictly lower part
+        } else {
+            singles.push_back({k, run});
+        }
+    }
+    if (!which.empty()) {
+        SGT_CUDA_TRY(cudaMemcpyAsync(d_which, which.data(), which.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        SGT_CUDA_TRY(cudaMemcpyAsync(d_diag, diagv.data(), diagv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        rs = launch_fill_batched((int)which.size(), d_descs, d_which, d_diag, st);
+        if (rs != SIGNTRI_OK) return rs;
+    }
+    rs = batched_ph_run(cnt, descs.data(), d_descs, ph_bs.data(), ws, st);
+    if (rs != SIGNTRI_OK) return rs;
+    for (auto &sv : singles) {
+        const int k = sv.first;
+        rs = run_variant(sizes[k], descs[k].T, descs[k].ldt, descs[k].U, descs[k].ldu, sv.second, sr[k], st, *s);
+        if (rs != SIGNTRI_OK) info[owner[k]] = rs;
+    }
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_set_cutoff_table(const int *b, int len)
+{
+    if (len < 0 || len > 32 || (len > 0 && !b)) return SIGNTRI_ERR_BAD_ARG;
+    for (int k = 0; k < len; k++)
+        if (b[k] != 0 && b[k] != 16 && b[k] != 32 && b[k] != 64) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int k = 0; k < 32; k++) g_cutoff_table[k] = k < len ? b[k] : 0;
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_get_cutoff_table(int *b, int len)
+{
+    if (len < 0 || len > 32 || (len > 0 && !b)) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int k = 0; k < len; k++) b[k] = g_cutoff_table[k];
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_autotune(int n_max, void *stream)
+{
+    if (n_max < 32 || n_max > 32768) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int saved = g_cutoff;
+    double *T = nullptr, *U = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc(&T, (size_t)n_max * n_max * 8) != cudaSuccess ||
+        cudaMalloc(&U, (size_t)n_max * n_max * 8) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess)
+        rs = SIGNTRI_ERR_CUDA;
+    for (int k = 5; rs == SIGNTRI_OK && (1 << k) <= n_max; k++) {
+        const int nn = 1 << k;
+        synth_kernel<<<nn, 256, 0, st>>>(nn, T, 0x5eed0000ull + k);
+        if (cudaGetLastError() != cudaSuccess) { rs = SIGNTRI_ERR_CUDA; break; }
+        ScanResult r{};
+        rs = launch_inertia_scan(nn, T, nn, s->scan_dev, st);
+        if (rs != SIGNTRI_OK) break;
+        SGT_CUDA_TRY(cudaMemcpyAsync(&r, s->scan_dev, sizeof(ScanResult), cudaMemcpyDeviceToHost, st));
+        SGT_CUDA_TRY(cudaStreamSynchronize(st));
+        float best = 1e30f;
+        int best_b = saved;
+        for (int b : {16, 32, 64}) {
+            g_cutoff = b;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && rs == SIGNTRI_OK; rep++) {
+                cudaEventRecord(e0, st);
+                rs = run_variant(nn, T, nn, U, nn, SIGNTRI_PH_FP64, r, st, *s);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rs = SIGNTRI_ERR_CUDA;
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (rs != SIGNTRI_OK) break;
+            if (ms < best) { best = ms; best_b = b; }
+        }
+        g_cutoff_table[k] = best_b;
+    }
+    g_cutoff = saved;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(T);
+    cudaFree(U);
+    return rs;
 }
 
 signtri_status signtri_set_refinement(double tol, int max_steps)

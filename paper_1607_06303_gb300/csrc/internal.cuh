@@ -31,6 +31,13 @@ struct ScanResult {
     int pad;
 };
 
+// One matrix of a batch (device copy).
+struct BatchDesc {
+    const double *T;
+    double *U;
+    int n, ldt, ldu, pad;
+};
+
 // Device workspace carved into aligned slices.
 struct Arena {
     char *base = nullptr;
@@ -49,6 +56,9 @@ void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st);
 // Algorithmic tensor-core flops of a launch (counted on the host).
 void prof_add_flops(int cls, double flops);
+// While paused (stream capture), launches are counted but not timed.
+void prof_pause(bool on);
+void prof_count(int cls, long long launches);
 
 struct ProfScope {
     int cls;
@@ -61,6 +71,10 @@ struct ProfScope {
 signtri_status launch_inertia_scan(int n, const double *T, int ldt, ScanResult *d_out,
                                    cudaStream_t st);
 signtri_status launch_fill_identity(int n, double *U, int ldu, double diag, cudaStream_t st);
+signtri_status launch_inertia_scan_batched(int count, const BatchDesc *d_mats, ScanResult *d_out, cudaStream_t st);
+// U_m = diag * I for the listed matrices (diag 0: zero the strictly lower part)
+signtri_status launch_fill_batched(int count, const BatchDesc *d_mats, const int *d_which, const double *d_diag,
+                                   cudaStream_t st);
 signtri_status launch_zero_strict_lower(int n, double *U, int ldu, cudaStream_t st);
 
 // Process-wide leaf size of Parlett-Higham (api.cu).
@@ -95,6 +109,11 @@ signtri_status make_scales(int m, int k, const double *M, int ldm, int tri, bool
 size_t emulated_gemm_workspace_bytes(int m, int n, int k, int S);
 signtri_status emulated_gemm_run(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C,
                                  int ldc, int S, Arena &ws, int *d_err, cudaStream_t st);
+
+// Batched float64 Parlett-Higham (batched.cu)
+size_t batched_workspace_bytes(int count, const int *n, int cutoff_for_all);
+signtri_status batched_ph_run(int count, const BatchDesc *h_mats, const BatchDesc *d_mats, const int *bs,
+                              Arena &ws, cudaStream_t st);
 
 // Mixed precision with refinement (mixed.cu)
 struct MixedParams {

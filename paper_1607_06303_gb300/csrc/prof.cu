@@ -44,16 +44,30 @@ cudaEvent_t take_event()
 const char *kClassNames[SIGNTRI_KC_COUNT] = {
     "inertia_scan", "fill", "diag_leaf_f64", "block_sums_f64", "offdiag_leaf_f64",
     "block_sums_tc", "offdiag_leaf_mixed", "convert", "residual", "correction",
-    "givens_rounds", "sylvester_sums", "sylvester_leaf", "gemm_f64", "other", "residual_sum",
+    "givens_rounds", "sylvester_sums", "sylvester_leaf", "gemm_f64", "other", "residual_sum", "batch_graph",
 };
 
+bool p_paused = false;
+
 }  // namespace
+
+void prof_pause(bool on)
+{
+    std::lock_guard<std::mutex> lk(p_mu);
+    p_paused = on;
+}
+
+void prof_count(int cls, long long launches)
+{
+    std::lock_guard<std::mutex> lk(p_mu);
+    if (cls >= 0 && cls < SIGNTRI_KC_COUNT) p_launches[cls] += launches;
+}
 
 void prof_begin(int cls, cudaStream_t st)
 {
     std::lock_guard<std::mutex> lk(p_mu);
     p_launches[cls]++;
-    if (!p_enabled) return;
+    if (!p_enabled || p_paused) return;
     p_open_cls = cls;
     p_open_ev = take_event();
     if (p_open_ev) cudaEventRecord(p_open_ev, st);
@@ -68,7 +82,7 @@ void prof_add_flops(int cls, double flops)
 void prof_end(int cls, cudaStream_t st)
 {
     std::lock_guard<std::mutex> lk(p_mu);
-    if (!p_enabled || p_open_cls != cls || !p_open_ev) return;
+    if (!p_enabled || p_paused || p_open_cls != cls || !p_open_ev) return;
     cudaEvent_t b = take_event();
     if (b) {
         cudaEventRecord(b, st);

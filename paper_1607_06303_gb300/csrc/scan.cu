@@ -22,8 +22,7 @@ constexpr int kScanThreads = 1024;
 //   same    += c_s * (i - 1) - S_s        for each entry i of sign s,
 // where `same` = sum over equal-sign pairs i<j of (j - i - 1): the number of
 // inner-sum terms of Algorithm 3 that use U^2 = I.
-__global__ void __launch_bounds__(kScanThreads)
-inertia_scan_kernel(int n, const double *__restrict__ T, int ldt, ScanResult *out)
+__device__ __forceinline__ void inertia_scan_body(int n, const double *__restrict__ T, int ldt, ScanResult *out)
 {
     __shared__ long long s_a[kScanThreads], s_b[kScanThreads], s_c[kScanThreads], s_d[kScanThreads];
     __shared__ int s_bad[kScanThreads];
@@ -77,6 +76,35 @@ inertia_scan_kernel(int n, const double *__restrict__ T, int ldt, ScanResult *ou
     }
 }
 
+__global__ void __launch_bounds__(kScanThreads)
+inertia_scan_kernel(int n, const double *__restrict__ T, int ldt, ScanResult *out)
+{
+    inertia_scan_body(n, T, ldt, out);
+}
+
+// One CTA per matrix of a batch.
+__global__ void __launch_bounds__(kScanThreads)
+inertia_scan_batched_kernel(const BatchDesc *__restrict__ mats, ScanResult *out)
+{
+    const BatchDesc m = mats[blockIdx.x];
+    inertia_scan_body(m.n, m.T, m.ldt, out + blockIdx.x);
+}
+
+// Batched fills: U_m = diag_m * I (diag_m = 0: only the strictly lower part
+// set to 0).  blockIdx.x = matrix, blockIdx.y strides the columns.
+__global__ void fill_batched_kernel(const BatchDesc *__restrict__ mats, const int *__restrict__ which,
+                                    const double *__restrict__ diag)
+{
+    const int k = blockIdx.x;
+    const BatchDesc m = mats[which[k]];
+    const double dv = diag[k];
+    for (int j = blockIdx.y; j < m.n; j += gridDim.y)
+        for (int i = threadIdx.x; i < m.n; i += blockDim.x) {
+            if (dv != 0.0) SGT_AT(m.U, m.ldu, i, j) = (i == j) ? dv : 0.0;
+            else if (i > j) SGT_AT(m.U, m.ldu, i, j) = 0.0;
+        }
+}
+
 // U = diag * I on the n x n part (used when n_- = 0 or n_+ = 0).
 __global__ void fill_identity_kernel(int n, double *__restrict__ U, int ldu, double diag)
 {
@@ -97,6 +125,25 @@ signtri_status launch_inertia_scan(int n, const double *T, int ldt, ScanResult *
 {
     ProfScope ps(SIGNTRI_KC_SCAN, st);
     inertia_scan_kernel<<<1, kScanThreads, 0, st>>>(n, T, ldt, d_out);
+    SGT_LAUNCH_CHECK();
+    return SIGNTRI_OK;
+}
+
+signtri_status launch_inertia_scan_batched(int count, const BatchDesc *d_mats, ScanResult *d_out, cudaStream_t st)
+{
+    if (count <= 0) return SIGNTRI_OK;
+    ProfScope ps(SIGNTRI_KC_SCAN, st);
+    inertia_scan_batched_kernel<<<count, kScanThreads, 0, st>>>(d_mats, d_out);
+    SGT_LAUNCH_CHECK();
+    return SIGNTRI_OK;
+}
+
+signtri_status launch_fill_batched(int count, const BatchDesc *d_mats, const int *d_which, const double *d_diag,
+                                   cudaStream_t st)
+{
+    if (count <= 0) return SIGNTRI_OK;
+    ProfScope ps(SIGNTRI_KC_FILL, st);
+    fill_batched_kernel<<<dim3(count, 64), 256, 0, st>>>(d_mats, d_which, d_diag);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }

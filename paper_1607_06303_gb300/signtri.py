@@ -90,6 +90,11 @@ _SIGNATURES = {
     "signtri_gemm_emulated": (_I, [_I, _I, _I, _VP, _I, _VP, _I, _VP, _I, _VP]),
     "signtri_set_refinement": (_I, [ctypes.c_double, _I]),
     "signtri_profile_read_flops": (_I, [_I, ctypes.POINTER(ctypes.c_double)]),
+    "sign_tri_batched": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_VP), ctypes.POINTER(_I),
+                              ctypes.POINTER(_VP), ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _VP]),
+    "signtri_set_cutoff_table": (_I, [ctypes.POINTER(_I), _I]),
+    "signtri_get_cutoff_table": (_I, [ctypes.POINTER(_I), _I]),
+    "signtri_autotune": (_I, [_I, _VP]),
 }
 
 SIGNTRI_NOALLOC_MAX_N = 1024
@@ -98,7 +103,8 @@ SIGNTRI_NOALLOC_MAX_N = 1024
 KC_SCAN, KC_FILL, KC_DIAG_LEAF, KC_BLOCK_SUMS_F64, KC_OFFDIAG_LEAF = 0, 1, 2, 3, 4
 KC_BLOCK_SUMS_TC, KC_OFFDIAG_LEAF_MIXED, KC_CONVERT, KC_RESIDUAL, KC_CORRECTION = 5, 6, 7, 8, 9
 KC_GIVENS, KC_SYLV_SUMS, KC_SYLV_LEAF, KC_GEMM_F64, KC_OTHER, KC_RESIDUAL_SUM = 10, 11, 12, 13, 14, 15
-KC_COUNT = 16
+KC_BATCH_GRAPH = 16
+KC_COUNT = 17
 
 
 def load(path: str = LIB_PATH):
@@ -158,6 +164,33 @@ def signtri_sylvester(m, p, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, X_ptr, ldx, stre
 def signtri_gemm_emulated(m, n, k, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, stream=None) -> int:
     return load().signtri_gemm_emulated(m, n, k, A_ptr or None, lda, B_ptr or None, ldb, C_ptr or None, ldc,
                                         stream or None)
+
+
+def sign_tri_batched(ns, T_ptrs, ldts, U_ptrs, ldus, v, stream=None):
+    """Batched call on host lists; returns (status, per-matrix info list)."""
+    cnt = len(ns)
+    arr = lambda t, xs: (t * max(cnt, 1))(*xs)
+    info = (_I * max(cnt, 1))()
+    st = load().sign_tri_batched(cnt, arr(_I, ns), arr(_VP, T_ptrs), arr(_I, ldts), arr(_VP, U_ptrs),
+                                 arr(_I, ldus), int(v), info, stream or None)
+    return st, list(info)[:cnt]
+
+
+def signtri_set_cutoff_table(table) -> int:
+    arr = (_I * max(len(table), 1))(*table)
+    return load().signtri_set_cutoff_table(arr, len(table))
+
+
+def signtri_get_cutoff_table(length: int = 32):
+    arr = (_I * length)()
+    st = load().signtri_get_cutoff_table(arr, length)
+    if st != 0:
+        raise SignTriError(st, "signtri_get_cutoff_table")
+    return list(arr)
+
+
+def signtri_autotune(n_max: int, stream=None) -> int:
+    return load().signtri_autotune(int(n_max), stream or None)
 
 
 def signtri_set_refinement(tol: float, max_steps: int) -> int:

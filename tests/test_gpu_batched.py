@@ -1,0 +1,85 @@
+"""Batched entry point: many problems of uneven size and inertia in one call,
+each checked against the oracle; per-matrix status codes; cutoff table and
+autotuner."""
+import numpy as np
+import pytest
+
+from paper_1607_06303_gb300.inputs import make_T
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-11
+
+
+def relerr(A, B):
+    nb = np.linalg.norm(B)
+    return np.linalg.norm(A - B) / (nb if nb > 0 else 1.0)
+
+
+def run_batch(p, Ts, variant, bad_ld=()):
+    import torch
+    dT = [p.to_device(T) if T.shape[0] else torch.empty(0, dtype=torch.float64, device="cuda") for T in Ts]
+    dU = [torch.full_like(t, np.nan) for t in dT]
+    ns = [T.shape[0] for T in Ts]
+    ld = [max(n, 1) for n in ns]
+    ldu = [(n - 1 if i in bad_ld else max(n, 1)) for i, n in enumerate(ns)]
+    st, info = p.sign_tri_batched(ns, [t.data_ptr() for t in dT], ld, [u.data_ptr() for u in dU], ldu, variant,
+                                  torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return st, info, [p.to_numpy(u) if u.numel() else np.zeros((0, 0)) for u in dU]
+
+
+def batch_inputs():
+    rng = np.random.default_rng(5)
+    Ts = []
+    for i, n in enumerate([0, 1, 2, 17, 64, 65, 130, 257, 300, 513, 31, 700]):
+        for pr, order in [(0.5, "random"), (0.0, "random"), (1.0, "random"), (0.2, "random"), (0.9, "sorted"),
+                          (0.05, "random")]:
+            if rng.random() < 0.5:
+                continue
+            Ts.append(make_T(n, pr, seed=100 + 7 * i + int(10 * pr), order=order))
+    return Ts
+
+
+@pytest.mark.parametrize("variant", ["AUTO", "PH_FP64"])
+def test_batched_vs_oracle(gpu_lib, oracle_mod, variant):
+    Ts = batch_inputs()
+    assert len(Ts) > 15
+    st, info, Us = run_batch(gpu_lib, Ts, gpu_lib.Variant[variant])
+    assert st == 0
+    for T, U, code in zip(Ts, Us, info):
+        assert code == 0
+        if T.shape[0] == 0:
+            continue
+        Uo = oracle_mod.sign_tri(T)
+        assert np.all(np.tril(U, -1) == 0.0) and np.all(np.diag(U) == np.diag(Uo))
+        assert relerr(U, Uo) <= TOL_FP64, (T.shape[0], relerr(U, Uo))
+
+
+def test_batched_statuses(gpu_lib, oracle_mod):
+    Ts = [make_T(100, 0.5, seed=1), make_T(80, 0.5, seed=2), make_T(90, 0.5, seed=3), make_T(70, 0.5, seed=4)]
+    Ts[1][40, 40] = 0.0
+    Ts[2][10, 10] = np.nan
+    st, info, Us = run_batch(gpu_lib, Ts, gpu_lib.Variant.PH_FP64, bad_ld=(3,))
+    assert st == 0
+    assert info == [0, gpu_lib.Status.ERR_ZERO_EIGENVALUE, gpu_lib.Status.ERR_NONFINITE, gpu_lib.Status.ERR_BAD_ARG]
+    assert relerr(Us[0], oracle_mod.sign_tri(Ts[0])) <= TOL_FP64
+
+
+def test_cutoff_table_and_autotune(gpu_lib, oracle_mod):
+    import torch
+    old = gpu_lib.signtri_get_cutoff_table()
+    try:
+        for b in (16, 32, 64):
+            assert gpu_lib.signtri_set_cutoff_table([b] * 32) == 0
+            Ts = [make_T(n, 0.5, seed=n) for n in (40, 100, 333)]
+            st, info, Us = run_batch(gpu_lib, Ts, gpu_lib.Variant.PH_FP64)
+            assert st == 0 and info == [0, 0, 0]
+            for T, U in zip(Ts, Us):
+                assert relerr(U, oracle_mod.sign_tri(T)) <= TOL_FP64
+        assert gpu_lib.signtri_set_cutoff_table([48]) == gpu_lib.Status.ERR_BAD_ARG
+        assert gpu_lib.signtri_autotune(512, torch.cuda.current_stream().cuda_stream) == 0
+        table = gpu_lib.signtri_get_cutoff_table()
+        assert all(table[k] in (16, 32, 64) for k in range(5, 10))
+    finally:
+        gpu_lib.signtri_set_cutoff_table(old)
