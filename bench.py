@@ -60,6 +60,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="order of the leading principal window the oracle solves")
+    ap.add_argument("--workload", choices=["single", "batched"], default="single",
+                    help="batched: 2000 problems, n log-uniform in [32, 2048], p ~ U[0,1], random order")
+    ap.add_argument("--batch", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -179,8 +182,87 @@ def src_sha(rel):
         return hashlib.sha256(f.read()).hexdigest()
 
 
+def run_batched(args):
+    """The batched workload: `--batch` independent problems (seed 0), n log-
+    uniform in [32, 2048], p ~ U[0, 1], random diagonal order, in one
+    sign_tri_batched call per step (variant AUTO, autotuned cutoffs)."""
+    import numpy as np
+    import torch
+
+    import paper_1607_06303_gb300 as st
+    from paper_1607_06303_gb300 import workload
+    from paper_1607_06303_gb300.inputs import batch_sizes, make_batch
+
+    st.load()
+    torch.cuda.set_device(0)
+    h = torch.cuda.current_stream().cuda_stream
+    t0 = time.perf_counter()
+    Ts = make_batch(args.batch, seed=0)
+    gen_s = time.perf_counter() - t0
+    ns = [T.shape[0] for T in Ts]
+    useful = sum(workload.useful_flops(np.sign(np.diag(T))) for T in Ts)
+    dT = [st.to_device(T) for T in Ts]
+    dU = [torch.empty_like(t) for t in dT]
+    ptrT, ptrU = [t.data_ptr() for t in dT], [u.data_ptr() for u in dU]
+    assert st.signtri_autotune(2048, h) == 0
+    table = st.signtri_get_cutoff_table()
+    variant = st.Variant[args.variant] if args.variant in ("AUTO", "PH_FP64") else st.Variant.AUTO
+
+    def step():
+        s_, info = st.sign_tri_batched(ns, ptrT, ns, ptrU, ns, variant, h)
+        if s_ != 0 or any(info):
+            raise st.SignTriError(s_ or max(info), "sign_tri_batched")
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    st.signtri_profile_reset()
+    st.signtri_profile_enable(True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    st.signtri_profile_enable(False)
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    per_class, launches = {}, 0
+    for c in range(st.signtri.KC_COUNT):
+        cnt, dms = st.signtri_profile_read(c)
+        launches += cnt
+        if cnt:
+            per_class[st.signtri_kernel_class_name(c)] = {"launches": cnt, "device_ms": dms}
+    # parity on a bounded sample: the largest problem and 20 more, against the oracle
+    import oracle
+    rng = np.random.default_rng(1)
+    sample = sorted(set([int(np.argmax(ns))] + list(rng.choice(len(Ts), 20, replace=False))))
+    errs = []
+    for i in sample:
+        Uo = oracle.sign_tri(Ts[i], schedule="antidiag")
+        Ug = st.to_numpy(dU[i])
+        errs.append(float(np.linalg.norm(Ug - Uo) / np.linalg.norm(Uo)))
+    line = {
+        "metric": "batched sign(T): useful GFLOP/s over %d problems" % len(Ts), "value": useful / (ms * 1e-3) / 1e9,
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batched: %d problems, n log-uniform [32, 2048], p ~ U[0,1], random order, seed 0"
+                               % len(Ts), "sum_n2": int(sum(n * n for n in ns)), "useful_flops": useful,
+                   "variant": variant.name, "cutoff_table": {str(1 << k): table[k] for k in range(5, 12)},
+                   "host_generation_s": gen_s},
+        "gpu_launches": launches, "kernel_time_ms": per_class, "clocks": clk,
+        "max_rel_err_vs_oracle_sample": max(errs), "sample_size": len(sample),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.workload == "batched" and args.impl == "ours":
+        return run_batched(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -132,7 +132,8 @@ signtri_status sign_tri_host(int n, const double *T_host, int ldt, double *U_hos
    as sign_tri).  info[m] (host) receives each problem's status; a bad matrix
    does not stop the others.  Per matrix: the inertia scan (one batched
    launch), +-I for trivial inertia, and for the rest the variant `v` (AUTO:
-   Parlett-Higham or Parlett-Sylvester from the Section 3 estimates).  All
+   Parlett-Sylvester when the diagonal is already grouped by sign, i.e. no
+   swaps, else Parlett-Higham, which shares its launches across the batch).  All
    Parlett-Higham float64 problems run together as one CUDA graph of
    level-synchronous launches (leaf size per problem from the cutoff table);
    the others run one after another.  Returns after all U[m] are written.

@@ -145,14 +145,23 @@ void work_estimates(int n, const ScanResult &r, double *w_ph, double *w_ps)
 // triple, n^3 to leading order); Parlett-Sylvester runs 12 n k flops of
 // Givens rounds, n_- n_+ n of Sylvester solve and, when k > 0, the
 // back-transform products.
+// Plus launch latency: Parlett-Higham issues two launches per block
+// anti-diagonal; Parlett-Sylvester two per Givens round (at most n rounds
+// when swaps are needed) and two per Sylvester anti-diagonal.
+constexpr double kLaunchSeconds = 5e-6;
+
 signtri_variant choose_variant(int n, const ScanResult &r)
 {
     const double nd = n;
-    const double t_ph = nd * nd * nd / g_rate_gemm;
+    const double nb = std::ceil(nd / g_cutoff);
+    const double t_ph = nd * nd * nd / g_rate_gemm + 2.0 * nb * kLaunchSeconds;
     const double np = r.n_pos, nm = r.n_neg, k = (double)r.swaps;
     double bt = 0.0;
     if (r.swaps > 0) bt = 2.0 * nd * std::fmin(np, nm) * (nd + std::fmax(np, nm));
-    const double t_ps = 12.0 * nd * k / g_rate_givens + (np * nm * nd + bt) / g_rate_gemm;
+    const double rounds = r.swaps > 0 ? nd : 0.0;
+    const double sylv_steps = std::ceil(np / 64.0) + std::ceil(nm / 64.0);
+    const double t_ps = 12.0 * nd * k / g_rate_givens + (np * nm * nd + bt) / g_rate_gemm +
+                        2.0 * (rounds + sylv_steps) * kLaunchSeconds;
     return t_ps < t_ph ? SIGNTRI_PS_FP64 : SIGNTRI_PH_FP64;
 }
 
@@ -380,7 +389,10 @@ signtri_status sign_tri_batched(int count, const int *n, const double *const *T,
             continue;
         }
         signtri_variant run = v;
-        if (v == SIGNTRI_AUTO) run = choose_variant(sizes[k], r);
+        // in a batch Parlett-Higham shares its launches with every other
+        // problem, so Parlett-Sylvester (run on its own) is taken only when
+        // no swaps are needed
+        if (v == SIGNTRI_AUTO) run = (r.swaps == 0) ? SIGNTRI_PS_FP64 : SIGNTRI_PH_FP64;
         if (run == SIGNTRI_PH_FP64) {
             ph_bs[k] = bs[k];
             which.push_back(k);
