@@ -235,6 +235,13 @@ signtri_status signtri_profile_read(int cls, long long *launches, double *device
 signtri_status signtri_profile_read_flops(int cls, double *flops);
 /* Name of a kernel class ("" when out of range). */
 const char *signtri_kernel_class_name(int cls);
+/* Self-test of the bounded device waits used by the tensor-core kernels:
+   one thread waits on an mbarrier with a budget of limit_cycles SM cycles
+   (1 .. 4e9); with arrive != 0 another warp completes the barrier and the
+   call returns SIGNTRI_OK, with arrive == 0 nothing does, the wait gives up,
+   and the call returns SIGNTRI_ERR_TIMEOUT (the context stays usable).
+   Synchronous on `stream`. */
+signtri_status signtri_selftest_wait(int arrive, long long limit_cycles, void *stream);
 /* Float64 fused-multiply-add issue rate of the current device, GFLOP/s
    (independent FMA chains; best of three launches on `stream`). */
 signtri_status signtri_probe_fp64_peak(double *gflops, void *stream);

@@ -12,4 +12,4 @@ from .signtri import (Info, SignTriError, Status, Variant, load, sign, sign_tri,
                       signtri_reorder_by_sign, signtri_sylvester, signtri_set_rates,
                       signtri_gemm_emulated, signtri_set_refinement,
                       signtri_profile_read_flops, sign_tri_batched, signtri_set_cutoff_table,
-                      signtri_get_cutoff_table, signtri_autotune)
+                      signtri_get_cutoff_table, signtri_autotune, signtri_selftest_wait)

@@ -485,6 +485,22 @@ signtri_status signtri_autotune(int n_max, void *stream)
     return rs;
 }
 
+signtri_status signtri_selftest_wait(int arrive, long long limit_cycles, void *stream)
+{
+    if (limit_cycles <= 0 || limit_cycles > 4000000000LL) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SGT_CUDA_TRY(cudaMemsetAsync(s->err_dev, 0, sizeof(int), st));
+    rs = wait_selftest(arrive, limit_cycles, s->err_dev, st);
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaMemcpyAsync(s->err_host, s->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    return *s->err_host ? SIGNTRI_ERR_TIMEOUT : SIGNTRI_OK;
+}
+
 signtri_status signtri_set_refinement(double tol, int max_steps)
 {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -115,6 +115,9 @@ size_t batched_workspace_bytes(int count, const int *n, int cutoff_for_all);
 signtri_status batched_ph_run(int count, const BatchDesc *h_mats, const BatchDesc *d_mats, const int *bs,
                               Arena &ws, cudaStream_t st);
 
+// Bounded-wait self-test (tc_gemm.cu)
+signtri_status wait_selftest(int arrive, long long limit, int *d_err, cudaStream_t st);
+
 // Mixed precision with refinement (mixed.cu)
 struct MixedParams {
     double tol;              // stopping test on both relative residuals

@@ -63,8 +63,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Bounded wait for the phase of parity `parity`; false on timeout or abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+// Bounded wait for the phase of parity `parity`; false on timeout (after
+// `limit` SM clock cycles) or abort.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                              long long limit)
 {
     const uint32_t addr = smem_u32(bar);
     const long long t0 = clock64();
@@ -77,8 +79,31 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
             : "memory");
         if (ok) return true;
         if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    return mbar_wait_for(bar, parity, abort_flag, kWaitCycles);
+}
+
+// Self-test of the bounded wait: thread 0 waits on a barrier that a thread of
+// the second warp completes only when `arrive` is set; without it the wait
+// runs out after `limit` cycles and the error word is set.
+__global__ void wait_selftest_kernel(int arrive, long long limit, int *err)
+{
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 32 && arrive) mbar_arrive(&bar);
+    if (threadIdx.x == 0 && !mbar_wait_for(&bar, 0, &abort_flag, limit)) atomicExch(err, 1);
+    __syncthreads();
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
@@ -431,6 +456,14 @@ signtri_status make_map(CUtensorMap *m, const __nv_bfloat16 *base, long long row
 }
 
 }  // namespace
+
+signtri_status wait_selftest(int arrive, long long limit, int *d_err, cudaStream_t st)
+{
+    ProfScope ps(SIGNTRI_KC_OTHER, st);
+    wait_selftest_kernel<<<1, 64, 0, st>>>(arrive, limit, d_err);
+    SGT_LAUNCH_CHECK();
+    return SIGNTRI_OK;
+}
 
 size_t tc_smem_bytes() { return (size_t)kStages * kStageBytes + 1024 + 512 + sizeof(TcPairs) + 64; }
 

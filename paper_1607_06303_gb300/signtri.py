@@ -95,6 +95,7 @@ _SIGNATURES = {
     "signtri_set_cutoff_table": (_I, [ctypes.POINTER(_I), _I]),
     "signtri_get_cutoff_table": (_I, [ctypes.POINTER(_I), _I]),
     "signtri_autotune": (_I, [_I, _VP]),
+    "signtri_selftest_wait": (_I, [_I, ctypes.c_longlong, _VP]),
 }
 
 SIGNTRI_NOALLOC_MAX_N = 1024
@@ -191,6 +192,10 @@ def signtri_get_cutoff_table(length: int = 32):
 
 def signtri_autotune(n_max: int, stream=None) -> int:
     return load().signtri_autotune(int(n_max), stream or None)
+
+
+def signtri_selftest_wait(arrive: bool, limit_cycles: int, stream=None) -> int:
+    return load().signtri_selftest_wait(1 if arrive else 0, int(limit_cycles), stream or None)
 
 
 def signtri_set_refinement(tol: float, max_steps: int) -> int:
