@@ -150,22 +150,34 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
     }
     __syncthreads();
 
+    // wavefront: four threads per entry (strided partial sums, then a
+    // width-4 shuffle reduction); every thread runs the same control flow
+    const int grp = threadIdx.x >> 2, sub = threadIdx.x & 3;
     const int nsteps = MB + bj - 1;
     for (int st = 0; st < nsteps; st++) {
         const int plo = max(0, MB - 1 - st);
         const int phi = min(MB - 1, MB - 1 - st + bj - 1);
-        for (int p = plo + threadIdx.x; p <= phi; p += kLeafThreads) {
-            const int q = st - (MB - 1 - p);
-            const bool opp = (srow[p] + scol[q] == 0.f);
-            const float *Am = opp ? TI : AI;
-            const float *Bm = opp ? TJ : AJ;
-            float a = 0.f, b = 0.f;
-            for (int k = p + 1; k < MB; k++) a = fmaf(Am[p + k * LD], Vs[k + q * LD], a);
-            for (int k = 0; k < q; k++) b = fmaf(Vs[p + k * LD], Bm[k + q * LD], b);
+        const int p = plo + grp;
+        const bool active = (p <= phi);
+        const int pp = active ? p : plo;
+        const int q = st - (MB - 1 - pp);
+        const bool opp = (srow[pp] + scol[q] == 0.f);
+        const float *Am = opp ? TI : AI;
+        const float *Bm = opp ? TJ : AJ;
+        float a = 0.f, b = 0.f;
+        if (active) {
+            for (int k = pp + 1 + sub; k < MB; k += 4) a = fmaf(Am[pp + k * LD], Vs[k + q * LD], a);
+            for (int k = sub; k < q; k += 4) b = fmaf(Vs[pp + k * LD], Bm[k + q * LD], b);
+        }
+        a += __shfl_xor_sync(0xffffffffu, a, 1, 4);
+        b += __shfl_xor_sync(0xffffffffu, b, 1, 4);
+        a += __shfl_xor_sync(0xffffffffu, a, 2, 4);
+        b += __shfl_xor_sync(0xffffffffu, b, 2, 4);
+        if (active && sub == 0) {
             float v;
-            if (opp) v = (Cs[p + q * LD] - a + b) / (TI[p + p * LD] - TJ[q + q * LD]);
-            else v = (Cs[p + q * LD] - a - b) / (srow[p] + scol[q]);
-            Vs[p + q * LD] = v;
+            if (opp) v = (Cs[pp + q * LD] - a + b) / (TI[pp + pp * LD] - TJ[q + q * LD]);
+            else v = (Cs[pp + q * LD] - a - b) / (srow[pp] + scol[q]);
+            Vs[pp + q * LD] = v;
         }
         __syncthreads();
     }

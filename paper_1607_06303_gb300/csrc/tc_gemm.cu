@@ -162,6 +162,30 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8])
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+        "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+        "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
+// 16 columns without waiting; the caller issues tcgen05.wait::ld.
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
     uint32_t r[16];
@@ -334,18 +358,23 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
             const float w = pairs.w[u % pairs.n];
             const uint32_t taddr = lane_base + (uint32_t)(buf * 128 + cg * 32);
 #pragma unroll
-            for (int cc = 0; cc < 32; cc += 8) {
-                float v[8], h[8];
-                tmem_ld8(taddr + cc, v);
+            for (int cc = 0; cc < 32; cc += 16) {
+                uint32_t rv[16], rh[16];
+                tmem_ld16_nowait(taddr + cc, rv);
+                if (u > 0) tmem_ld16_nowait(taddr_hi + cc, rh);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float h[16];
                 if (u == 0) {
 #pragma unroll
-                    for (int i = 0; i < 8; i++) h[i] = __fmul_rn(v[i], w);
+                    for (int i = 0; i < 16; i++) h[i] = __fmul_rn(__uint_as_float(rv[i]), w);
                 } else {
-                    tmem_ld8(taddr_hi + cc, h);
 #pragma unroll
-                    for (int i = 0; i < 8; i++) df_add(h[i], lo[cc + i], __fmul_rn(v[i], w));
+                    for (int i = 0; i < 16; i++) {
+                        h[i] = __uint_as_float(rh[i]);
+                        df_add(h[i], lo[cc + i], __fmul_rn(__uint_as_float(rv[i]), w));
+                    }
                 }
-                tmem_st8(taddr_hi + cc, h);
+                tmem_st16(taddr_hi + cc, h);
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             fence_before();
