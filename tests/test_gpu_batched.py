@@ -83,3 +83,13 @@ def test_cutoff_table_and_autotune(gpu_lib, oracle_mod):
         assert all(table[k] in (16, 32, 64) for k in range(5, 10))
     finally:
         gpu_lib.signtri_set_cutoff_table(old)
+
+
+def test_batched_mixed_variant(gpu_lib, oracle_mod):
+    # mixed-precision problems in a batch run one after another through the
+    # single-matrix path; each meets the mixed bar
+    Ts = [make_T(n, 0.5, seed=200 + n) for n in (70, 200, 513)]
+    st, info, Us = run_batch(gpu_lib, Ts, gpu_lib.Variant.PH_MIXED_TF32)
+    assert st == 0 and info == [0, 0, 0]
+    for T, U in zip(Ts, Us):
+        assert relerr(U, oracle_mod.sign_tri(T)) <= 1e-12
