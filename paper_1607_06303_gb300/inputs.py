@@ -59,6 +59,25 @@ def make_T(n: int, p: float = 0.5, seed: int = 0, order: str = "random",
     return T
 
 
+def make_T_schur(n: int, seed: int = 0, n_neg: int = None) -> np.ndarray:
+    """The paper's workload (Section 6): the real part of the complex Schur
+    form of a random n x n matrix with entries uniform in [-50, 50]; inertia
+    roughly balanced.  With n_neg given, the diagonal keeps its magnitudes but
+    all signs are made positive except at n_neg random positions (the paper's
+    forced inertia).  Column-major float64; needs scipy (host only)."""
+    import scipy.linalg
+    rng = np.random.Generator(np.random.PCG64(seed))
+    A = rng.uniform(-50.0, 50.0, size=(n, n))
+    Tc, _ = scipy.linalg.schur(A, output="complex")
+    T = np.asfortranarray(np.triu(Tc.real))
+    if n_neg is not None:
+        d = np.abs(np.diag(T))
+        s = np.ones(n)
+        s[rng.permutation(n)[:int(n_neg)]] = -1.0
+        T[np.arange(n), np.arange(n)] = s * d
+    return T
+
+
 def batch_sizes(count: int, seed: int = 0, n_min: int = 32, n_max: int = 2048):
     """Sizes n_i = round(exp(U[ln n_min, ln n_max])) and inertias p_i ~ U[0,1]
     of a batch of independent problems."""
