@@ -17,7 +17,8 @@
 // integer below 2^24 and therefore exact, which makes the emulated product
 // accurate to the split (about 2^-48 relative to |A||B| with 7 slices).
 //
-// Warp roles (576 threads): warp 0 issues TMA loads into a 6-stage ring,
+// Warp roles (576 threads): warp 0 issues TMA loads into a 3-stage ring of
+// two K-blocks per stage,
 // warp 1 issues the MMAs (one thread) into 3 TMEM buffers of 128 columns,
 // warps 2..17 drain TMEM (four warps per 32-lane quadrant, 32 columns each)
 // and keep the fp32 hi parts of the accumulators in the 4th 128-column TMEM
@@ -35,9 +36,11 @@ namespace signtri {
 
 namespace {
 
-constexpr int kStages = 6;
+constexpr int kStages = 3;
+constexpr int kKPS = 2;                     // K-blocks of 64 per stage
 constexpr int kTcThreads = 576;            // 2 control warps + 16 epilogue warps
-constexpr int kStageBytes = 32768;          // A 128x64 + B 128x64 bf16
+constexpr int kHalfBytes = 32768;           // A 128x64 + B 128x64 bf16 for one K-block
+constexpr int kStageBytes = kKPS * kHalfBytes;
 constexpr int kBufs = 3;                    // TMEM accumulator buffers of 128 columns; the 4th holds hi
 constexpr long long kWaitCycles = 4000000000LL;   // about 2 s at 2 GHz
 
@@ -271,16 +274,20 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
                                                               // K-chunk reuse its panels in L2
                 const int ya = pairs.s[p] * rowsA, yb = pairs.t[p] * rowsB;
                 const int kbs = job.kb0 + c * chunk_kb, kbe = min(kbs + chunk_kb, job.kb1);
-                for (int kb = kbs; kb < kbe; kb++) {
+                for (int kb = kbs; kb < kbe; kb += kKPS) {
+                    const int nk = min(kKPS, kbe - kb);
                     if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) { ok = false; break; }
-                    mbar_expect_tx(&full[stage], kStageBytes);
-                    unsigned char *a = smem + stage * kStageBytes;
-                    unsigned char *b = a + kStageBytes / 2;
-                    const int x = kb * 64;
-                    tma_load_2d(a, &mTop, &full[stage], x, ya + job.rt);
-                    tma_load_2d(a + 8192, &mBot, &full[stage], x, ya + job.rb);
-                    tma_load_2d(b, &mLeft, &full[stage], x, yb + job.cl);
-                    tma_load_2d(b + 8192, &mRight, &full[stage], x, yb + job.cr);
+                    mbar_expect_tx(&full[stage], nk * kHalfBytes);
+                    for (int h = 0; h < nk; h++) {
+                        // stage layout: A halves [h][top 8 KB | bottom 8 KB], then B halves
+                        unsigned char *a = smem + stage * kStageBytes + h * (kHalfBytes / 2);
+                        unsigned char *b = smem + stage * kStageBytes + kStageBytes / 2 + h * (kHalfBytes / 2);
+                        const int x = (kb + h) * 64;
+                        tma_load_2d(a, &mTop, &full[stage], x, ya + job.rt);
+                        tma_load_2d(a + 8192, &mBot, &full[stage], x, ya + job.rb);
+                        tma_load_2d(b, &mLeft, &full[stage], x, yb + job.cl);
+                        tma_load_2d(b + 8192, &mRight, &full[stage], x, yb + job.cr);
+                    }
                     issued++;
                     if (++stage == kStages) { stage = 0; phase ^= 1; }
                 }
@@ -320,14 +327,19 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
                 const uint32_t d = tmem_base + (uint32_t)(buf * 128);
                 const int c = u / pairs.n;
                 const int kbs = job.kb0 + c * chunk_kb, kbe = min(kbs + chunk_kb, job.kb1);
-                for (int kb = kbs; kb < kbe; kb++) {
+                for (int kb = kbs; kb < kbe; kb += kKPS) {
+                    const int nk = min(kKPS, kbe - kb);
                     if (!mbar_wait(&full[stage], phase, abort_flag)) { ok = false; break; }
                     fence_after();
-                    unsigned char *a = smem + stage * kStageBytes;
-                    const uint64_t ad = smem_desc(a), bd = smem_desc(a + kStageBytes / 2);
+                    for (int h = 0; h < nk; h++) {
+                        unsigned char *a = smem + stage * kStageBytes + h * (kHalfBytes / 2);
+                        unsigned char *b = smem + stage * kStageBytes + kStageBytes / 2 + h * (kHalfBytes / 2);
+                        const uint64_t ad = smem_desc(a), bd = smem_desc(b);
 #pragma unroll
-                    for (int k = 0; k < 4; k++)
-                        mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (kb > kbs || k > 0) ? 1u : 0u);
+                        for (int k = 0; k < 4; k++)
+                            mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k),
+                                     (kb > kbs || h > 0 || k > 0) ? 1u : 0u);
+                    }
                     mma_commit(&empty[stage]);
                     if (++stage == kStages) { stage = 0; phase ^= 1; }
                 }
