@@ -53,8 +53,8 @@ def parse_args():
     ap.add_argument("--p", type=float, default=0.5)
     ap.add_argument("--order", default="random")
     ap.add_argument("--variant", default="PH_MIXED_TF32")
-    ap.add_argument("--compare", default="PH_FP64",
-                    help="variant timed beside the headline on the same input ('' to skip)")
+    ap.add_argument("--compare", default="PH_FP64,PH_FP64_EFFICIENT",
+                    help="comma-separated variants timed beside the headline on the same input ('' to skip)")
     ap.add_argument("--cutoff", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -166,6 +166,28 @@ def block_sum_flops(n, b):
             J = I + d
             bj = min(b, n - J * b)
             total += 6 * b * (d - 1) * b * bj
+    return total
+
+
+def block_sum_flops_efficient(n, b, signs):
+    """Algorithmic flops of the arithmetic-efficient block sums (Section 5.3):
+    per (row, k, column) triple 2 flops when the row and column signs agree
+    (Y only) and 4 when they differ (X only)."""
+    import numpy as np
+    nb = (n + b - 1) // b
+    pos = np.zeros(nb, dtype=np.int64)
+    cnt = np.zeros(nb, dtype=np.int64)
+    for I in range(nb):
+        s_ = signs[I * b:min(n, (I + 1) * b)]
+        pos[I] = int(np.sum(s_ > 0))
+        cnt[I] = len(s_)
+    total = 0
+    for d in range(2, nb):
+        pI, nI = pos[:nb - d], cnt[:nb - d] - pos[:nb - d]
+        pJ, nJ = pos[d:], cnt[d:] - pos[d:]
+        same = pI * pJ + nI * nJ
+        opp = cnt[:nb - d] * cnt[d:] - same
+        total += int(np.sum((2 * same + 4 * opp) * (d - 1) * b))
     return total
 
 
@@ -347,7 +369,8 @@ def main():
     roof = None
     if dom == "block_sums_f64":
         b = info.cutoff
-        flops_step = block_sum_flops(n, b)
+        efficient = info.variant == st.Variant.PH_FP64_EFFICIENT
+        flops_step = block_sum_flops_efficient(n, b, signs) if efficient else block_sum_flops(n, b)
         launches_dom = per_class[dom]["launches"]
         per_launch = flops_step * args.steps / launches_dom
         avg_ms = per_class[dom]["device_ms"] / launches_dom
@@ -356,7 +379,8 @@ def main():
         sha = src_sha("paper_1607_06303_gb300/csrc/ph_fp64.cu")
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": TRAFFIC.get(("block_sums_f64", sha)),
-                "kernel": "ph_gemm_kernel (float64 DFMA block sums)",
+                "kernel": ("ph_gemm_split_kernel (float64 DFMA, one sum per entry)" if efficient
+                           else "ph_gemm_kernel (float64 DFMA block sums)"),
                 "peak_source": "float64 FMA issue rate measured live by signtri_probe_fp64_peak (no FP64 entry "
                                "in MEASURED_PEAKS.json)",
                 "share_of_step": per_class[dom]["device_ms"] / ms_total}
@@ -395,10 +419,10 @@ def main():
                        "resid_involution": info.resid_involution},
     }
 
-    # the comparison variant on the same input (float64 form), fewer steps
-    Uc = None
-    if args.compare and args.compare != args.variant:
-        cv = st.Variant[args.compare]
+    # comparison variants on the same input (float64 forms), fewer steps
+    compares = []
+    for cname in [c for c in (args.compare or "").split(",") if c and c != args.variant]:
+        cv = st.Variant[cname]
         Uc = torch.empty_like(Tt)
 
         def cstep():
@@ -419,9 +443,11 @@ def main():
         if dist is not None:
             dist.all_reduce(tc_, op=dist.ReduceOp.MAX)
         cms = float(tc_.item())
-        line["compare"] = {"variant": args.compare, "steps": ck, "seconds_per_solve": cms / 1e3,
-                           "value": world * useful / (cms * 1e-3) / 1e9, "unit": UNIT,
-                           "speedup_of_headline": cms / ms_step_max}
+        compares.append(({"variant": cname, "steps": ck, "seconds_per_solve": cms / 1e3,
+                          "value": world * useful / (cms * 1e-3) / 1e9, "unit": UNIT,
+                          "speedup_of_headline": cms / ms_step_max}, Uc))
+    if compares:
+        line["compare"] = [c for c, _ in compares]
 
     # end to end through the public API with host buffers
     if not args.no_e2e:
@@ -471,9 +497,8 @@ def main():
         # principal-window property: u_ij depends on T[i..j, i..j] only, so the
         # oracle on a window equals the full oracle there
         line["rel_err_vs_oracle_window"], line["rel_err_vs_oracle_trailing_window"] = window_errs(Ut)
-        if Uc is not None:
-            line["compare"]["rel_err_vs_oracle_window"], line["compare"]["rel_err_vs_oracle_trailing_window"] = \
-                window_errs(Uc)
+        for c, Uc in compares:
+            c["rel_err_vs_oracle_window"], c["rel_err_vs_oracle_trailing_window"] = window_errs(Uc)
 
     if rank == 0:
         print(json.dumps(line), flush=True)

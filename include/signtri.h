@@ -35,10 +35,14 @@ extern "C" {
 #endif
 
 typedef enum {
-    /* Choose Parlett-Higham or Parlett-Sylvester per input from the
-       work estimates of Section 3 (inertia and swap count). */
+    /* Choose Parlett-Higham (its arithmetic-efficient form,
+       SIGNTRI_PH_FP64_EFFICIENT) or Parlett-Sylvester per input from the
+       work estimates of Section 3 (inertia and swap count).  In
+       sign_tri_batched, AUTO picks Parlett-Sylvester when no swaps are
+       needed and the batched Parlett-Higham otherwise. */
     SIGNTRI_AUTO = 0,
-    /* Recursive Parlett-Higham (Algorithms 3-6), float64 throughout. */
+    /* Recursive Parlett-Higham (Algorithms 3-6), float64 throughout; block
+       sums in matrix-multiply form (both X and Y for every entry). */
     SIGNTRI_PH_FP64 = 1,
     /* Parlett-Sylvester for the sign function (Section 2, Section 3,
        Section 5.1): reorder by sign with adjacent Givens swaps, solve
@@ -49,7 +53,14 @@ typedef enum {
     SIGNTRI_PH_MIXED_TF32 = 3,
     /* Parlett-Higham with BF16 tensor-core block updates, then float64
        refinement of both defining equations. */
-    SIGNTRI_PH_MIXED_BF16 = 4
+    SIGNTRI_PH_MIXED_BF16 = 4,
+    /* Arithmetic-efficient recursive Parlett-Higham (Section 5.3), float64:
+       each entry's block sum is X (signs differ) or Y (signs agree) only,
+       n^3/3..2n^3/3 flops instead of n^3.  Every sum runs over the same
+       terms in the same order as in SIGNTRI_PH_FP64, so the two results
+       agree bit for bit (up to the sign of zero).  Workspace: see
+       signtri_workspace_bytes. */
+    SIGNTRI_PH_FP64_EFFICIENT = 5
 } signtri_variant;
 
 typedef enum {

@@ -52,7 +52,7 @@ double g_mixed_tol = kDefaultMixedTol;
 int g_mixed_max_steps = -1;   // < 0: per-variant default
 thread_local signtri_info g_info;
 
-bool valid_variant(int v) { return v >= SIGNTRI_AUTO && v <= SIGNTRI_PH_MIXED_BF16; }
+bool valid_variant(int v) { return v >= SIGNTRI_AUTO && v <= SIGNTRI_PH_FP64_EFFICIENT; }
 
 signtri_status current_state(DeviceState **out)
 {
@@ -109,6 +109,8 @@ size_t workspace_need(int n, signtri_variant v, int cutoff, long long swaps)
     switch (v) {
     case SIGNTRI_PH_FP64:
         return ph_fp64_workspace_bytes(n, cutoff);
+    case SIGNTRI_PH_FP64_EFFICIENT:
+        return ph_fp64_split_workspace_bytes(n, cutoff);
     case SIGNTRI_PH_MIXED_TF32:
     case SIGNTRI_PH_MIXED_BF16:
         // the float64 fallback reuses the same memory
@@ -117,7 +119,7 @@ size_t workspace_need(int n, signtri_variant v, int cutoff, long long swaps)
     case SIGNTRI_PS_FP64:
         return ps_workspace_bytes(n, swaps);
     case SIGNTRI_AUTO:
-        return std::max(ph_fp64_workspace_bytes(n, cutoff), ps_workspace_bytes(n, swaps));
+        return std::max(ph_fp64_split_workspace_bytes(n, cutoff), ps_workspace_bytes(n, swaps));
     }
     return 0;
 }
@@ -141,10 +143,10 @@ void work_estimates(int n, const ScanResult &r, double *w_ph, double *w_ps)
 }
 
 // Times predicted from the Section 3 work of what each variant executes:
-// Parlett-Higham runs the matrix-multiply form (6 flops per (i<k<j) block
-// triple, n^3 to leading order); Parlett-Sylvester runs 12 n k flops of
-// Givens rounds, n_- n_+ n of Sylvester solve and, when k > 0, the
-// back-transform products.
+// Parlett-Higham runs the arithmetic-efficient form (Section 5.3: only the
+// sum each entry needs, exactly the useful count w_ph); Parlett-Sylvester
+// runs 12 n k flops of Givens rounds, n_- n_+ n of Sylvester solve and, when
+// k > 0, the back-transform products.
 // Plus launch latency: Parlett-Higham issues two launches per block
 // anti-diagonal; Parlett-Sylvester two per Givens round (at most n rounds
 // when swaps are needed) and two per Sylvester anti-diagonal.
@@ -154,7 +156,9 @@ signtri_variant choose_variant(int n, const ScanResult &r)
 {
     const double nd = n;
     const double nb = std::ceil(nd / g_cutoff);
-    const double t_ph = nd * nd * nd / g_rate_gemm + 2.0 * nb * kLaunchSeconds;
+    double w_ph = 0.0, w_ps = 0.0;
+    work_estimates(n, r, &w_ph, &w_ps);
+    const double t_ph = w_ph / g_rate_gemm + 2.0 * nb * kLaunchSeconds;
     const double np = r.n_pos, nm = r.n_neg, k = (double)r.swaps;
     double bt = 0.0;
     if (r.swaps > 0) bt = 2.0 * nd * std::fmin(np, nm) * (nd + std::fmax(np, nm));
@@ -162,7 +166,7 @@ signtri_variant choose_variant(int n, const ScanResult &r)
     const double sylv_steps = std::ceil(np / 64.0) + std::ceil(nm / 64.0);
     const double t_ps = 12.0 * nd * k / g_rate_givens + (np * nm * nd + bt) / g_rate_gemm +
                         2.0 * (rounds + sylv_steps) * kLaunchSeconds;
-    return t_ps < t_ph ? SIGNTRI_PS_FP64 : SIGNTRI_PH_FP64;
+    return t_ps < t_ph ? SIGNTRI_PS_FP64 : SIGNTRI_PH_FP64_EFFICIENT;
 }
 
 signtri_status run_variant(int n, const double *T, int ldt, double *U, int ldu, signtri_variant v,
@@ -176,6 +180,9 @@ signtri_status run_variant(int n, const double *T, int ldt, double *U, int ldu, 
     case SIGNTRI_PH_FP64:
         g_info.cutoff = b;
         return ph_fp64_run(n, T, ldt, U, ldu, b, ws, st);
+    case SIGNTRI_PH_FP64_EFFICIENT:
+        g_info.cutoff = b;
+        return ph_fp64_split_run(n, T, ldt, U, ldu, b, ws, st);
     case SIGNTRI_PS_FP64:
         return ps_fp64_run(n, T, ldt, U, ldu, r.n_pos, r.swaps, ws, st);
     case SIGNTRI_PH_MIXED_TF32:

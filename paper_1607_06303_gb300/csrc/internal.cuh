@@ -85,6 +85,10 @@ size_t ph_fp64_workspace_bytes(int n, int b);
 signtri_status diag_leaves_f64(int n, const double *T, int ldt, double *U, int ldu, int b, cudaStream_t st);
 signtri_status ph_fp64_run(int n, const double *T, int ldt, double *U, int ldu, int b,
                            Arena &ws, cudaStream_t st);
+// arithmetic-efficient form (one sum per entry)
+size_t ph_fp64_split_workspace_bytes(int n, int b);
+signtri_status ph_fp64_split_run(int n, const double *T, int ldt, double *U, int ldu, int b, Arena &ws,
+                                 cudaStream_t st);
 
 // Float64 GEMM (gemm_f64.cu): C = alpha op(A) op(B) + beta C, optional upper
 // triangle only.

@@ -134,6 +134,209 @@ __device__ __forceinline__ void ph_gemm_body(int n, const double *__restrict__ T
 }
 
 // ---------------------------------------------------------------------------
+// Arithmetic-efficient block sums (Section 5.3: compute only the sum an entry
+// needs): entry (p, q) needs Y_pq = sum U_pk U_kq when the signs of p and q
+// agree and X_pq = sum U_pk T_kq - T_pk U_kq when they differ.  Rows of block
+// I and columns of block J are gathered positives first (perm, counts npos),
+// so the entries of one kind form rectangles: 1 FMA per term for equal signs,
+// 2 for opposite signs, instead of the 3 of ph_gemm_body.  Each sum runs over
+// the same terms in the same order as there; the single result z is stored at
+// the entry's original position.
+//
+// Thread (tx, ty) owns gathered rows tx + 16 r and columns ty + 16 c.  For a
+// warp, the 16 rows of slab r are all positive (P), all negative (N) or mixed
+// (M), and so are its 2 columns of slab c: warp-uniform classes, monotone in r
+// and c (P.., at most one M, N..).  The column pattern -- X slabs P, Y in
+// {0, 1} slabs M -- selects a template instance, the row class a branch around
+// the k loop; every accumulator's kind is then known at compile time, so a
+// warp issues only the products its entries need, with MT independent chains.
+// In M slabs each lane picks its own operands (2 FMAs, one of them a 0 * t_kq
+// for equal signs).
+// ---------------------------------------------------------------------------
+namespace split {
+
+constexpr int kP = 0, kN = 1, kM = 2;
+
+// ATn holds -T (sign flipped as an integer op when staged), so no product
+// needs a separate float64 negation.
+template <int B, int X, int Y, int RK>
+__device__ __forceinline__ void row_pass(double (&zr)[B / 16], const double (*AU)[B], const double (*ATn)[B],
+                                         const double (*BU)[B], const double (*BT)[B], int row, int ty,
+                                         bool rowpos, const bool (&colpos)[B / 16])
+{
+    constexpr int MT = B / 16;
+#pragma unroll 4
+    for (int kk = 0; kk < 16; kk++) {
+        const double au = AU[kk][row];
+        const double atn = ATn[kk][row];
+        // mixed row slab: per-lane operands for positive (P) and negative (N)
+        // column slabs, so that z += a1 * t_kq + a2 * u_kq is the entry's own sum
+        double a1P = 0.0, a2P = 0.0, a1N = 0.0, a2N = 0.0;
+        if (RK == kM) {
+            a1P = rowpos ? 0.0 : au;
+            a2P = rowpos ? au : atn;
+            a1N = rowpos ? au : 0.0;
+            a2N = rowpos ? atn : au;
+        }
+#pragma unroll
+        for (int c = 0; c < MT; c++) {
+            const int ck = (c < X) ? kP : ((c < X + Y) ? kM : kN);
+            const double bu = BU[kk][ty + 16 * c];
+            if (RK != kM && ck != kM) {
+                if (RK == ck) {
+                    zr[c] = fma(au, bu, zr[c]);
+                } else {
+                    zr[c] = fma(au, BT[kk][ty + 16 * c], zr[c]);
+                    zr[c] = fma(atn, bu, zr[c]);
+                }
+            } else if (RK == kM && ck == kP) {
+                zr[c] = fma(a1P, BT[kk][ty + 16 * c], zr[c]);
+                zr[c] = fma(a2P, bu, zr[c]);
+            } else if (RK == kM && ck == kN) {
+                zr[c] = fma(a1N, BT[kk][ty + 16 * c], zr[c]);
+                zr[c] = fma(a2N, bu, zr[c]);
+            } else {
+                // the one column slab a sign boundary splits (at most one warp)
+                const bool sm_ = (rowpos == colpos[c]);
+                zr[c] = fma(sm_ ? 0.0 : au, BT[kk][ty + 16 * c], zr[c]);
+                zr[c] = fma(sm_ ? au : atn, bu, zr[c]);
+            }
+        }
+    }
+}
+
+template <int B, int X, int Y>
+__device__ __forceinline__ void k_loop(int n, const double *__restrict__ T, int ldt, const double *__restrict__ U,
+                                       int ldu, int r0, int c0, int bj, int kb0, int kb1, const short *pI,
+                                       const short *pJ, const int (&rk)[B / 16], const bool (&rowpos)[B / 16],
+                                       const bool (&colpos)[B / 16], double (&z)[B / 16][B / 16],
+                                       double (*AU)[B], double (*AT)[B], double (*BU)[B], double (*BT)[B])
+{
+    constexpr int MT = B / 16;
+    constexpr int KT = 16;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    for (int k0 = kb0 * B; k0 < kb1 * B; k0 += KT) {
+        for (int idx = threadIdx.x; idx < B * KT; idx += kThreads) {
+            const int r = idx % B, kk = idx / B;
+            const int gr = r0 + pI[r];
+            AU[kk][r] = SGT_AT(U, ldu, gr, k0 + kk);
+            AT[kk][r] = __longlong_as_double(__double_as_longlong(SGT_AT(T, ldt, gr, k0 + kk)) ^
+                                             (long long)0x8000000000000000ull);
+        }
+        for (int idx = threadIdx.x; idx < B * KT; idx += kThreads) {
+            const int kk = idx % KT, c = idx / KT;
+            const int lc = pJ[c];
+            double bu = 0.0, bt = 0.0;
+            if (lc < bj) {
+                bu = SGT_AT(U, ldu, k0 + kk, c0 + lc);
+                bt = SGT_AT(T, ldt, k0 + kk, c0 + lc);
+            }
+            BU[kk][c] = bu;
+            BT[kk][c] = bt;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < MT; r++) {
+            const int row = tx + 16 * r;
+            if (rk[r] == kP)
+                row_pass<B, X, Y, kP>(z[r], AU, AT, BU, BT, row, ty, rowpos[r], colpos);
+            else if (rk[r] == kN)
+                row_pass<B, X, Y, kN>(z[r], AU, AT, BU, BT, row, ty, rowpos[r], colpos);
+            else
+                row_pass<B, X, Y, kM>(z[r], AU, AT, BU, BT, row, ty, rowpos[r], colpos);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace split
+
+template <int B>
+__device__ __forceinline__ void ph_gemm_split_body(int n, const double *__restrict__ T, int ldt,
+                                                   const double *__restrict__ U, int ldu, int I, int J, int kb0,
+                                                   int kb1, const short *__restrict__ perm,
+                                                   const int *__restrict__ npos, double *__restrict__ pz)
+{
+    using namespace split;
+    constexpr int MT = B / 16;
+    __shared__ double AU[16][B], AT[16][B], BU[16][B], BT[16][B];
+    __shared__ short pI[B], pJ[B];
+    const int r0 = I * B, c0 = J * B;
+    const int bj = min(B, n - c0);
+    for (int i = threadIdx.x; i < B; i += kThreads) {
+        pI[i] = perm[r0 + i];
+        pJ[i] = perm[c0 + i];
+    }
+    const int npI = npos[I], npJ = npos[J];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    int rk[MT];
+    bool rowpos[MT], colpos[MT];
+    int X = 0, Y = 0;
+    double z[MT][MT];
+#pragma unroll
+    for (int r = 0; r < MT; r++) {
+        rowpos[r] = (tx + 16 * r) < npI;
+        colpos[r] = (ty + 16 * r) < npJ;
+        const bool rall = __all_sync(0xffffffffu, rowpos[r]), rnone = !__any_sync(0xffffffffu, rowpos[r]);
+        rk[r] = rall ? kP : (rnone ? kN : kM);
+        const bool call = __all_sync(0xffffffffu, colpos[r]), cnone = !__any_sync(0xffffffffu, colpos[r]);
+        X += call ? 1 : 0;
+        Y += (!call && !cnone) ? 1 : 0;
+#pragma unroll
+        for (int c = 0; c < MT; c++) z[r][c] = 0.0;
+    }
+    __syncthreads();
+#define SGT_SPLIT_CASE(XV, YV)                                                                             \
+    else if (X == XV && Y == YV)                                                                           \
+    {                                                                                                      \
+        if constexpr (XV + YV <= MT)                                                                       \
+            k_loop<B, (XV + YV <= MT ? XV : 0), (XV + YV <= MT ? YV : 0)>(n, T, ldt, U, ldu, r0, c0, bj, kb0, \
+                                                                         kb1, pI, pJ, rk, rowpos, colpos, z, AU, AT, BU, BT); \
+    }
+    if (false) {
+    }
+    SGT_SPLIT_CASE(0, 0) SGT_SPLIT_CASE(1, 0) SGT_SPLIT_CASE(2, 0) SGT_SPLIT_CASE(3, 0) SGT_SPLIT_CASE(4, 0)
+    SGT_SPLIT_CASE(0, 1) SGT_SPLIT_CASE(1, 1) SGT_SPLIT_CASE(2, 1) SGT_SPLIT_CASE(3, 1)
+#undef SGT_SPLIT_CASE
+#pragma unroll
+    for (int r = 0; r < MT; r++)
+#pragma unroll
+        for (int c = 0; c < MT; c++) pz[pI[tx + 16 * r] + pJ[ty + 16 * c] * B] = z[r][c];
+}
+
+// Per block of B rows: the rows' positions sorted positives first (stable),
+// beyond n at the end, and the count of positives.  One CTA of B threads per
+// block.
+template <int B>
+__device__ __forceinline__ void sign_perm_body(int n, const double *__restrict__ T, int ldt, int blk,
+                                               short *__restrict__ perm, int *__restrict__ npos)
+{
+    __shared__ int pos_before[B + 1];
+    const int i = threadIdx.x;
+    const int gi = blk * B + i;
+    const bool valid = gi < n;
+    const bool positive = valid && SGT_AT(T, ldt, gi, gi) > 0.0;
+    if (i == 0) pos_before[0] = 0;
+    __syncthreads();
+    if (i < B) pos_before[i + 1] = positive ? 1 : 0;
+    __syncthreads();
+    if (i == 0)
+        for (int t = 1; t <= B; t++) pos_before[t] += pos_before[t - 1];
+    __syncthreads();
+    const int np = pos_before[B];
+    const int nvalid = min(B, n - blk * B);
+    if (i < B) {
+        int slot;
+        if (positive) slot = pos_before[i];
+        else if (valid) slot = np + (i - pos_before[i]);
+        else slot = i;                       // rows beyond n keep their place
+        perm[blk * B + slot] = (short)i;
+    }
+    if (i == 0) npos[blk] = np;
+    (void)nvalid;
+}
+
+// ---------------------------------------------------------------------------
 // Off-diagonal leaf for block (I, J = I+d): rows [r0, r0+B), cols [c0, c0+bj).
 // With p, q the local row and column and V = U_IJ, Algorithm 6's 1x1 case
 // with the in-block part of the sums written out:

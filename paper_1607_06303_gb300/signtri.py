@@ -22,6 +22,7 @@ class Variant(enum.IntEnum):
     PS_FP64 = 2
     PH_MIXED_TF32 = 3
     PH_MIXED_BF16 = 4
+    PH_FP64_EFFICIENT = 5
 
 
 class Status(enum.IntEnum):
