@@ -49,7 +49,7 @@ batched_gemm_kernel(const BatchDesc *__restrict__ mats, const int *__restrict__ 
 {
     const GemmTask t = tasks[blockIdx.x];
     const BatchDesc M = mats[members[t.m]];
-    ph_gemm_body<B>(M.n, M.T, M.ldt, M.U, M.ldu, t.I, t.J, t.kb0, t.kb1, PX + (size_t)t.slot * B * B,
+    ph_gemm_body<B>(M.n, M.T, M.ldt, M.U, M.ldu, t.I, t.J, t.kb0 * B, t.kb1 * B, PX + (size_t)t.slot * B * B,
                     PY + (size_t)t.slot * B * B);
 }
 

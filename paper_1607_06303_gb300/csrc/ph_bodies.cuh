@@ -12,6 +12,22 @@ constexpr int kThreads = 256;
 constexpr int kSplitMax = 32;
 constexpr int kTargetCtas = 4 * 152;   // two resident CTAs per SM, two waves
 
+// Even split of one anti-diagonal's block sums (single-matrix path): the
+// nb-d tiles x (d-1) K-blocks are cut into 16-deep k-chunks, W in all, and
+// CTA c of G = min(kStreamCtas, W) takes chunks [c W / G, (c+1) W / G), so
+// every CTA does the same work whatever the tile count.  A CTA whose range
+// crosses a tile boundary writes one partial slab per tile it touches; the
+// partial of CTA c for tile I goes to slab c + I, and the tile's partials are
+// the consecutive slabs of CTAs first(I)..last(I), summed in that order.
+// G is fixed (not the device's SM count) so that results do not depend on
+// the GPU.
+constexpr int kStreamCtas = 4 * 152;
+
+__host__ __device__ __forceinline__ long long sk_chunks_per_tile(int d, int B) { return (long long)(d - 1) * (B / 16); }
+__host__ __device__ __forceinline__ int sk_ctas(long long W) { return (int)(W < kStreamCtas ? W : kStreamCtas); }
+// the CTA whose range holds chunk x (every CTA's range is non-empty)
+__host__ __device__ __forceinline__ long long sk_owner(long long x, long long W, int G) { return ((x + 1) * G - 1) / W; }
+
 __device__ __forceinline__ double sgn(double t) { return t > 0.0 ? 1.0 : -1.0; }
 
 // ---------------------------------------------------------------------------
@@ -66,15 +82,14 @@ __device__ __forceinline__ void diag_leaf_body(int n, const double *__restrict__
 }
 
 // ---------------------------------------------------------------------------
-// Block sums for anti-diagonal d: for block (I, J = I+d) and K-blocks
-// [kb0, kb1) of the split s,
-//     PX[s][I] = sum_K U_IK T_KJ - T_IK U_KJ,   PY[s][I] = sum_K U_IK U_KJ.
-// One CTA per (I, s), B x B output tile, 256 threads, (B/16)^2 outputs per
-// thread for each of X and Y, K staged through shared memory in steps of 16.
+// Block sums for block (I, J) over the k range [k_lo, k_hi) (multiples of 16):
+//     px = sum_k U_Ik T_kJ - T_Ik U_kJ,   py = sum_k U_Ik U_kJ.
+// B x B output tile per CTA, 256 threads, (B/16)^2 outputs per thread for
+// each of X and Y, k staged through shared memory in steps of 16.
 // ---------------------------------------------------------------------------
 template <int B>
 __device__ __forceinline__ void ph_gemm_body(int n, const double *__restrict__ T, int ldt,
-                                             const double *__restrict__ U, int ldu, int I, int J, int kb0, int kb1,
+                                             const double *__restrict__ U, int ldu, int I, int J, int k_lo, int k_hi,
                                              double *__restrict__ px, double *__restrict__ py)
 {
     constexpr int MT = B / 16;
@@ -89,7 +104,7 @@ __device__ __forceinline__ void ph_gemm_body(int n, const double *__restrict__ T
 #pragma unroll
         for (int c = 0; c < MT; c++) { x[r][c] = 0.0; y[r][c] = 0.0; }
 
-    for (int k0 = kb0 * B; k0 < kb1 * B; k0 += KT) {
+    for (int k0 = k_lo; k0 < k_hi; k0 += KT) {
         for (int idx = threadIdx.x; idx < B * KT; idx += kThreads) {
             const int r = idx % B, kk = idx / B;
             AU[kk][r] = SGT_AT(U, ldu, r0 + r, k0 + kk);
@@ -207,7 +222,7 @@ __device__ __forceinline__ void row_pass(double (&zr)[B / 16], const double (*AU
 
 template <int B, int X, int Y>
 __device__ __forceinline__ void k_loop(int n, const double *__restrict__ T, int ldt, const double *__restrict__ U,
-                                       int ldu, int r0, int c0, int bj, int kb0, int kb1, const short *pI,
+                                       int ldu, int r0, int c0, int bj, int k_lo, int k_hi, const short *pI,
                                        const short *pJ, const int (&rk)[B / 16], const bool (&rowpos)[B / 16],
                                        const bool (&colpos)[B / 16], double (&z)[B / 16][B / 16],
                                        double (*AU)[B], double (*AT)[B], double (*BU)[B], double (*BT)[B])
@@ -215,7 +230,7 @@ __device__ __forceinline__ void k_loop(int n, const double *__restrict__ T, int 
     constexpr int MT = B / 16;
     constexpr int KT = 16;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    for (int k0 = kb0 * B; k0 < kb1 * B; k0 += KT) {
+    for (int k0 = k_lo; k0 < k_hi; k0 += KT) {
         for (int idx = threadIdx.x; idx < B * KT; idx += kThreads) {
             const int r = idx % B, kk = idx / B;
             const int gr = r0 + pI[r];
@@ -253,14 +268,15 @@ __device__ __forceinline__ void k_loop(int n, const double *__restrict__ T, int 
 
 template <int B>
 __device__ __forceinline__ void ph_gemm_split_body(int n, const double *__restrict__ T, int ldt,
-                                                   const double *__restrict__ U, int ldu, int I, int J, int kb0,
-                                                   int kb1, const short *__restrict__ perm,
+                                                   const double *__restrict__ U, int ldu, int I, int J, int k_lo,
+                                                   int k_hi, const short *__restrict__ perm,
                                                    const int *__restrict__ npos, double *__restrict__ pz)
 {
     using namespace split;
     constexpr int MT = B / 16;
     __shared__ double AU[16][B], AT[16][B], BU[16][B], BT[16][B];
     __shared__ short pI[B], pJ[B];
+    __syncthreads();   // a CTA may run several tiles: pI, pJ are still read above
     const int r0 = I * B, c0 = J * B;
     const int bj = min(B, n - c0);
     for (int i = threadIdx.x; i < B; i += kThreads) {
@@ -290,8 +306,8 @@ __device__ __forceinline__ void ph_gemm_split_body(int n, const double *__restri
     else if (X == XV && Y == YV)                                                                           \
     {                                                                                                      \
         if constexpr (XV + YV <= MT)                                                                       \
-            k_loop<B, (XV + YV <= MT ? XV : 0), (XV + YV <= MT ? YV : 0)>(n, T, ldt, U, ldu, r0, c0, bj, kb0, \
-                                                                         kb1, pI, pJ, rk, rowpos, colpos, z, AU, AT, BU, BT); \
+            k_loop<B, (XV + YV <= MT ? XV : 0), (XV + YV <= MT ? YV : 0)>(n, T, ldt, U, ldu, r0, c0, bj, k_lo, \
+                                                                         k_hi, pI, pJ, rk, rowpos, colpos, z, AU, AT, BU, BT); \
     }
     if (false) {
     }
