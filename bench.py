@@ -413,7 +413,9 @@ def main():
                    "n": n, "p": args.p, "order": args.order, "variant_requested": args.variant,
                    "variant_run": st.Variant(info.variant).name if info.variant >= 0 else None,
                    "cutoff": info.cutoff, "useful_flops_per_solve": useful,
-                   "l2": "no flush: T and U are 2.1 GB each, > 129 MB L2", "parallelism": "replicas" if world > 1 else "1 GPU"},
+                   "l2": ("no flush: T and U are %.3g GB each, > 129 MB L2" % (8e-9 * n * n) if 8 * n * n > 129e6
+                          else "T and U (%.3g MB each) fit in L2: warm-cache timing" % (8e-6 * n * n)),
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
         "gpu_launches": launches, "kernel_time_ms": per_class, "roofline": roof, "clocks": clk,
         "refinement": {"steps": info.refine_steps, "resid_commute": info.resid_commute,
                        "resid_involution": info.resid_involution},
