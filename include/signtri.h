@@ -86,8 +86,11 @@ typedef struct {
     double work_ps;         /* Section 3 flop estimate, Parlett-Sylvester */
     int cutoff;             /* leaf (block) size used by Parlett-Higham */
     int refine_steps;       /* refinement steps taken (mixed variants) */
-    double resid_commute;   /* ||TU-UT||_F / (||T||_F ||U||_F) after the last step */
-    double resid_involution;/* ||U^2-I||_F / ||U||_F^2 after the last step */
+    double resid_commute;   /* ||TU-UT||_F / (||T||_F ||U||_F) after the last step,
+                               over the entries with t_ii, t_jj of opposite sign
+                               (those whose Algorithm 3 recurrence is TU = UT) */
+    double resid_involution;/* ||U^2-I||_F / ||U||_F^2 after the last step, over the
+                               entries with t_ii, t_jj of equal sign (recurrence U^2 = I) */
     int bad_index;          /* first offending diagonal index on ZERO/NONFINITE, else -1 */
 } signtri_info;
 

@@ -18,14 +18,29 @@
 //    Y^E = U0 E + E U0 on the tensor cores, recurrences in fp32).  Newton's
 //    iteration X <- X(3I - X^2)/2 alone would only drive U^2 = I and cannot
 //    correct the entries fixed by UT = TU, hence both equations.
-//    The residuals are formed from exact 7-bit integer slices of the strictly
-//    upper parts of T and U0 (emulated float64 products, about 2^-45
-//    relative to |T||U|) plus the diagonal terms in float64:
+//    Entry (i, j) uses Rc_ij when the signs differ and Rs_ij when they agree
+//    (the same choice as Algorithm 3), so the residual that drives the first
+//    correction forms only that one (Section 5.3's economy applied to the
+//    residual products); acceptance always rests on both residuals over all
+//    entries (an ill-conditioned problem can meet its own recurrences long
+//    before the other equation).  The residuals
+//    come from exact 7-bit integer slices of the strictly upper parts of T and
+//    U0 (emulated float64 products, about 2^-45 relative to |T||U|) plus the
+//    diagonal terms in float64:
 //      Rc_ij = (N_T N_U - N_U N_T)_ij + t_ii u_ij + t_ij u_jj - u_ii t_ij - u_ij t_jj
 //      Rs_ij = (N_U N_U)_ij + u_ii u_ij + u_ij u_jj.
-//    Stop when ||Rc||_F / (||T||_F ||U||_F) and ||Rs||_F / ||U||_F^2 are both
-//    below the tolerance; fall back to the float64 path when a step does not
-//    reduce the larger of the two by a factor 10, or after the step limit.
+//    For the products the indices are gathered per superblock of kSuper
+//    consecutive indices, positives first, each sign class padded to whole
+//    64-blocks: every 64 x 64 output block then has one sign class in its rows
+//    and one in its columns, and a tensor-core job computes four such blocks
+//    that all need the same product (Y = N_U N_U, or one of the two parts of
+//    X).  Block upper triangular structure survives at superblock level, so a
+//    job's K range is whole superblocks (the extra terms are structural zeros).
+//    The full residuals use the original layout and four-quadrant jobs
+//    [N_T I.; N_U I.] x [N_U .J | N_T .J].  Stop when ||Rc||_F / (||T||_F
+//    ||U||_F) and ||Rs||_F / ||U||_F^2 are both below the tolerance; fall back
+//    to the float64 path when a step does not reduce the larger of the two by
+//    a factor 10, or after the step limit.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -44,6 +59,7 @@ constexpr int MB = 64;
 constexpr int kLeafThreads = 256;
 constexpr int kTargetJobs = 2 * 152;
 constexpr int kOzakiSlices = 7;
+constexpr int kSuper = 1024;   // superblock of the gathered residual layout
 
 __device__ __forceinline__ float fsgn(double t) { return t > 0.0 ? 1.f : -1.f; }
 
@@ -251,8 +267,56 @@ corr_diag_leaf_kernel(int n, const double *__restrict__ T, int ldt, const double
 
 // ------------------------------------------------------------- residual ---
 
-// In place: Ptu -> Rc, Puu -> Rs (i < j; other entries 0), and the squared
-// Frobenius norms of Rc, Rs, T, U accumulated into norms[0..3].
+// Residual of entry (i < j) into R (column-major n x n): Rc_ij when the signs
+// of i and j differ, Rs_ij when they agree, from the gathered products
+// (RA: Y at equal-sign positions, N_T N_U at opposite-sign ones; RB: N_U N_T)
+// plus the diagonal terms; other entries 0.  Squared Frobenius norms of the
+// used Rc and Rs entries, of T and of U into norms[0..3].
+__global__ void needed_finalize_kernel(int n, const double *__restrict__ T, int ldt, const double *__restrict__ U,
+                                       int ldu, const int *__restrict__ gmap, const double *__restrict__ RA,
+                                         const double *__restrict__ RB, int ldg, double *__restrict__ R,
+                                         double *__restrict__ norms)
+{
+    const int j = blockIdx.x;
+    double nc = 0.0, ns = 0.0, nt = 0.0, nu = 0.0;
+    const double tjj = SGT_AT(T, ldt, j, j), ujj = SGT_AT(U, ldu, j, j);
+    const size_t gj = (size_t)gmap[j] * ldg;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double r = 0.0;
+        if (i < j) {
+            const double tii = SGT_AT(T, ldt, i, i), uii = SGT_AT(U, ldu, i, i);
+            const double tij = SGT_AT(T, ldt, i, j), uij = SGT_AT(U, ldu, i, j);
+            const size_t g = (size_t)gmap[i] + gj;
+            if ((tii > 0.0) == (tjj > 0.0)) {
+                r = RA[g] + uii * uij + uij * ujj;
+                ns += r * r;
+            } else {
+                r = RA[g] - RB[g] + (tii * uij - uij * tjj) + (tij * ujj - uii * tij);
+                nc += r * r;
+            }
+            nt += tij * tij;
+            nu += uij * uij;
+        } else if (i == j) {
+            nt += tjj * tjj;
+            nu += ujj * ujj;
+        }
+        SGT_AT(R, n, i, j) = r;
+    }
+    __shared__ double red[4][256];
+    red[0][threadIdx.x] = nc; red[1][threadIdx.x] = ns; red[2][threadIdx.x] = nt; red[3][threadIdx.x] = nu;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off)
+            for (int c = 0; c < 4; c++) red[c][threadIdx.x] += red[c][threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 4; c++) atomicAdd(&norms[c], red[c][0]);
+}
+
+// Full residuals, in place: Ptu -> Rc, Puu -> Rs (i < j; other entries 0),
+// and the squared Frobenius norms of Rc, Rs (all entries), T, U into
+// norms[0..3].
 __global__ void residual_finalize_kernel(int n, const double *__restrict__ T, int ldt, const double *__restrict__ U,
                                          int ldu, double *__restrict__ Ptu, const double *__restrict__ Put,
                                          double *__restrict__ Puu, int ldp, double *__restrict__ norms)
@@ -288,6 +352,13 @@ __global__ void residual_finalize_kernel(int n, const double *__restrict__ T, in
     }
     if (threadIdx.x == 0)
         for (int c = 0; c < 4; c++) atomicAdd(&norms[c], red[c][0]);
+}
+
+// sign flags of the diagonal (1 = positive)
+__global__ void diag_sign_kernel(int n, const double *__restrict__ T, int ldt, unsigned char *__restrict__ pos)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) pos[i] = SGT_AT(T, ldt, i, i) > 0.0 ? 1 : 0;
 }
 
 // U += E on the strictly upper part; ||E||_F^2 into norms[4].
@@ -369,16 +440,34 @@ struct MixedCtx {
     TcPairs *d_pairs_split, *d_pairs_oz;
     // bf16 splits (S slices) of T and of the unknowns, row and column forms
     __nv_bfloat16 *Tr, *Tc, *Ur, *Uc, *Er, *Ec;
-    // exact slices of the strictly upper parts (residual products)
-    __nv_bfloat16 *NTr, *NTc, *NUr, *NUc;
-    float *sTr, *sTc, *sUr, *sUc;
+    // exact slices of the strictly upper parts of T and U in the gathered
+    // layout (residual products): ng gathered positions, rows_g allocated
+    // (the last 64 all zero), pitch rows_g
+    int ng, rows_g;
+    int *gmap, *ginv;           // original -> gathered, gathered -> original (-1 padding)
+    unsigned char *pos;         // diagonal sign flags
+    __nv_bfloat16 *NTgr, *NTgc;         // T, gathered layout
+    __nv_bfloat16 *NTr, *NTc;           // T, original layout
+    __nv_bfloat16 *NUr, *NUc;           // U, either layout (sized for the gathered one)
+    float *sTr, *sTc, *sUr, *sUc;       // scales, original indices
+    float *gTr, *gTc, *gUr, *gUc;       // scales, gathered
     unsigned long long *tmpmax;
     double *PA, *PB;            // block-sum partials
-    double *E, *Rc, *Rs, *Put;  // correction, residuals
+    double *E;                  // correction
+    // residual products: gathered RA, RB or full-layout Ptu -> Rc, Put (same
+    // memory); R = Rs (full) or the per-entry residual (needed form)
+    double *RA, *RB, *R;
+    const double *res_c, *res_s;   // what the last residual left for the correction
     double *norms, *norms_host; // [0] Rc^2 [1] Rs^2 [2] T^2 [3] U^2 [4] E^2
-    TcJob *d_res_jobs;
-    int n_res_jobs;
+    TcJob *d_full_jobs;         // full residual: all 64-block pairs I <= J
+    int n_full_jobs;
+    TcJob *d_res_jobs;          // needed residual: equal-sign jobs, then opposite-sign jobs
+    int n_res_same, n_res_opp;
+    double res_kb_same, res_kb_opp;   // sum over jobs of used quadrants x K-blocks
 };
+
+// Gathered size bound: each superblock pads two sign classes to 64.
+int gathered_bound(int n) { return pad64(n) + 128 * ((n + kSuper - 1) / kSuper); }
 
 size_t bytes_for(int n, int S)
 {
@@ -386,13 +475,19 @@ size_t bytes_for(int n, int S)
     const size_t nb = np / MB;
     size_t b = 0;
     b += 6 * (size_t)S * np * np * 2 + 6 * 256;                       // split slices
-    b += 4 * (size_t)kOzakiSlices * np * np * 2 + 4 * 256;             // exact slices
+    const size_t ngr = (size_t)gathered_bound(n) + 64;
+    b += 4 * (size_t)kOzakiSlices * ngr * ngr * 2 + 4 * 256;           // exact slices: T gathered, U
+    b += 2 * (size_t)kOzakiSlices * np * np * 2 + 2 * 256;             // exact slices: T original
     b += 4 * np * 4 + np * 8 + 6 * 256;                                 // scales, tmp
+    b += 4 * ngr * 4 + 4 * 256 + 2 * ngr * 4 + np + 3 * 256;            // gathered scales, maps, signs
+    b += 2 * ngr * ngr * 8 + 2 * 256;                                   // RA, RB
     const size_t maxjobs = (size_t)kTargetJobs + nb + 8;
     b += 2 * maxjobs * 16384 * 8 + 2 * 256;                             // partials
-    b += 4 * (size_t)n * n * 8 + 4 * 256;                               // E, Rc, Rs, Put
+    b += 2 * (size_t)n * n * 8 + 2 * 256;                               // E, R (= Rs)
     b += 64 + 256;                                                      // norms
-    b += (size_t)nb * (nb + 1) / 2 * sizeof(TcJob) + 256;               // residual jobs
+    const size_t pairs_max = ngr / 128 + 2 * (size_t)((n + kSuper - 1) / kSuper) + 2;
+    b += pairs_max * pairs_max * sizeof(TcJob) + 256;                   // needed-residual jobs
+    b += (size_t)nb * (nb + 1) / 2 * sizeof(TcJob) + 256;               // full-residual jobs
     b += nb * (size_t)(kTargetJobs + nb) * sizeof(TcJob) + 256;         // wavefront jobs (bound)
     b += 2 * sizeof(TcPairs) + 512;
     return b;
@@ -409,16 +504,6 @@ signtri_status split_full(MixedCtx &c, const double *M, int ldm, __nv_bfloat16 *
     signtri_status rs;
     if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, c.S, nullptr, R, c.np, c.np, c.st)) != SIGNTRI_OK) return rs;
     return make_col_slices(c.n, c.n, M, ldm, 1, c.S, nullptr, C, c.np, c.np, c.st);
-}
-
-signtri_status exact_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bfloat16 *R, __nv_bfloat16 *C, float *sR,
-                               float *sC)
-{
-    signtri_status rs;
-    if ((rs = make_scales(c.n, c.n, M, ldm, 1, true, c.np, c.tmpmax, sR, c.st)) != SIGNTRI_OK) return rs;
-    if ((rs = make_scales(c.n, c.n, M, ldm, 1, false, c.np, c.tmpmax, sC, c.st)) != SIGNTRI_OK) return rs;
-    if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, sR, R, c.np, c.np, c.st)) != SIGNTRI_OK) return rs;
-    return make_col_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, sC, C, c.np, c.np, c.st);
 }
 
 // One low-precision sweep: MODE 0 solves for U (into V = U), MODE 1 for E.
@@ -465,36 +550,186 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
         }
         ProfScope ps(MODE == 0 ? SIGNTRI_KC_OFFDIAG_LEAF_F32 : SIGNTRI_KC_CORRECTION, c.st);
         mixed_leaf_kernel<MODE><<<ntiles, kLeafThreads, leaf_smem, c.st>>>(
-            n, T, ldt, V, ldv, U0, ldu0, c.Rc, c.Rs, n, d, c.sc.nsplit[d], c.PA, c.PB, Vr, Vc, c.S, c.np, c.np);
+            n, T, ldt, V, ldv, U0, ldu0, c.res_c, c.res_s, n, d, c.sc.nsplit[d], c.PA, c.PB, Vr, Vc, c.S, c.np, c.np);
         SGT_LAUNCH_CHECK();
     }
     return SIGNTRI_OK;
 }
 
-// Residuals of U into c.Rc, c.Rs and the norms (host copy in c.norms_host).
-signtri_status residual(MixedCtx &c, const double *T, int ldt, const double *U, int ldu)
+// The gathered layout and the residual job lists, from the diagonal signs
+// (one small device-to-host read): per superblock of kSuper indices the
+// positives in order, padded to 64, then the negatives; output jobs pair two
+// row blocks of one class and superblock with two column blocks of one class
+// and superblock (a lone block pairs with the zero block at ng).
+signtri_status setup_gathered(MixedCtx &c, const double *T, int ldt)
+{
+    const int n = c.n;
+    {
+        ProfScope ps(SIGNTRI_KC_CONVERT, c.st);
+        diag_sign_kernel<<<(n + 255) / 256, 256, 0, c.st>>>(n, T, ldt, c.pos);
+        SGT_LAUNCH_CHECK();
+    }
+    std::vector<unsigned char> pos(n);
+    SGT_CUDA_TRY(cudaMemcpyAsync(pos.data(), c.pos, n, cudaMemcpyDeviceToHost, c.st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(c.st));
+    const int nsb = (n + kSuper - 1) / kSuper;
+    std::vector<int> gmap(n), base(nsb + 1, 0), cnt_pos(nsb, 0), cls_len[2];
+    cls_len[0].assign(nsb, 0);
+    cls_len[1].assign(nsb, 0);
+    int g = 0;
+    for (int sb = 0; sb < nsb; sb++) {
+        const int i0 = sb * kSuper, i1 = std::min(n, i0 + kSuper);
+        int np_ = 0;
+        for (int i = i0; i < i1; i++) np_ += pos[i];
+        const int A = pad64(np_), Bn = pad64(i1 - i0 - np_);
+        base[sb] = g;
+        cls_len[0][sb] = A;
+        cls_len[1][sb] = Bn;
+        int rp = 0, rn = 0;
+        for (int i = i0; i < i1; i++) gmap[i] = pos[i] ? g + rp++ : g + A + rn++;
+        g += A + Bn;
+    }
+    base[nsb] = g;
+    c.ng = g;
+    c.rows_g = g + 64;
+    if (c.rows_g > gathered_bound(n) + 64) return SIGNTRI_ERR_NO_WORKSPACE;
+    std::vector<int> ginv(c.rows_g, -1);
+    for (int i = 0; i < n; i++) ginv[gmap[i]] = i;
+    // block pairs per (superblock, class): row offsets, lone block with the zero block
+    auto pairs_of = [&](int sb, int cls) {
+        std::vector<std::pair<int, int>> v;
+        const int start = base[sb] + (cls ? cls_len[0][sb] : 0), len = cls_len[cls][sb];
+        for (int o = 0; o < len; o += 128) v.push_back({start + o, o + 64 < len ? start + o + 64 : c.ng});
+        return v;
+    };
+    std::vector<TcJob> same, opp;
+    double kb_same = 0.0, kb_opp = 0.0;
+    // longest K ranges first (load balance); one superblock pair's jobs together
+    for (int span = nsb - 1; span >= 0; span--)
+        for (int sr = 0; sr + span < nsb; sr++) {
+            const int sc = sr + span;
+            const int kb0 = base[sr] / 64, kb1 = base[sc + 1] / 64;
+            for (int cr = 0; cr < 2; cr++)
+                for (int cc = 0; cc < 2; cc++) {
+                    const auto rows = pairs_of(sr, cr), cols = pairs_of(sc, cc);
+                    for (const auto &rp : rows)
+                        for (const auto &cp : cols) {
+                            TcJob j;
+                            j.rt = rp.first; j.rb = rp.second; j.cl = cp.first; j.cr = cp.second;
+                            j.kb0 = kb0; j.kb1 = kb1; j.slot = 0; j.pad = 0;
+                            const double used = (double)((rp.second < c.ng) + 1) * ((cp.second < c.ng) + 1);
+                            if (cr == cc) { same.push_back(j); kb_same += used * (kb1 - kb0); }
+                            else { opp.push_back(j); kb_opp += used * (kb1 - kb0); }
+                        }
+                }
+        }
+    c.n_res_same = (int)same.size();
+    c.n_res_opp = (int)opp.size();
+    c.res_kb_same = kb_same;
+    c.res_kb_opp = kb_opp;
+    same.insert(same.end(), opp.begin(), opp.end());
+    if (!same.empty())
+        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_res_jobs, same.data(), same.size() * sizeof(TcJob), cudaMemcpyHostToDevice,
+                                     c.st));
+    SGT_CUDA_TRY(cudaMemcpyAsync(c.gmap, gmap.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, c.st));
+    SGT_CUDA_TRY(cudaMemcpyAsync(c.ginv, ginv.data(), (size_t)c.rows_g * sizeof(int), cudaMemcpyHostToDevice, c.st));
+    // the host tables are pageable and local
+    SGT_CUDA_TRY(cudaStreamSynchronize(c.st));
+    return SIGNTRI_OK;
+}
+
+// Exact slices of the strictly upper part of M (T or U) in the gathered layout.
+signtri_status gathered_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bfloat16 *R, __nv_bfloat16 *C,
+                                  float *sR, float *sC, float *gR, float *gC)
+{
+    signtri_status rs;
+    if ((rs = make_scales(c.n, c.n, M, ldm, 1, true, c.np, c.tmpmax, sR, c.st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_scales(c.n, c.n, M, ldm, 1, false, c.np, c.tmpmax, sC, c.st)) != SIGNTRI_OK) return rs;
+    return make_gathered_slices(c.n, M, ldm, c.ginv, c.ng, kOzakiSlices, sR, sC, gR, gC, R, C, c.rows_g, c.rows_g,
+                                c.st);
+}
+
+// Exact slices of the strictly upper part of M in the original layout.
+signtri_status exact_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bfloat16 *R, __nv_bfloat16 *C, float *sR,
+                               float *sC)
+{
+    signtri_status rs;
+    if ((rs = make_scales(c.n, c.n, M, ldm, 1, true, c.np, c.tmpmax, sR, c.st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_scales(c.n, c.n, M, ldm, 1, false, c.np, c.tmpmax, sC, c.st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, sR, R, c.np, c.np, c.st)) != SIGNTRI_OK) return rs;
+    return make_col_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, sC, C, c.np, c.np, c.st);
+}
+
+signtri_status read_norms(MixedCtx &c)
+{
+    SGT_CUDA_TRY(cudaMemcpyAsync(c.norms_host, c.norms, 8 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(c.st));
+    return SIGNTRI_OK;
+}
+
+// Needed residual of U (Rc or Rs per entry) into c.R and its norms: three
+// tensor-core launches over the gathered layout, each job's four quadrants
+// all used -- equal-sign blocks  Y = N_U N_U  (into RA),
+// opposite-sign blocks  N_T N_U  (into RA) and  N_U N_T  (into RB) -- then
+// the float64 finalize in the original layout.
+signtri_status residual_needed(MixedCtx &c, const double *T, int ldt, const double *U, int ldu)
+{
+    signtri_status rs = gathered_slices_of(c, U, ldu, c.NUr, c.NUc, c.sUr, c.sUc, c.gUr, c.gUc);
+    if (rs != SIGNTRI_OK) return rs;
+    const int R = c.rows_g, K = c.ng, ld = c.rows_g;
+    const TcSource uR{c.NUr, kOzakiSlices, R, K, ld, c.gUr}, uC{c.NUc, kOzakiSlices, R, K, ld, c.gUc};
+    const TcSource tR{c.NTgr, kOzakiSlices, R, K, ld, c.gTr}, tC{c.NTgc, kOzakiSlices, R, K, ld, c.gTc};
+    const TcQuadOut qa{{c.RA, c.RA, c.RA, c.RA}, c.ng, c.ng, c.ng};
+    const TcQuadOut qb{{c.RB, c.RB, c.RB, c.RB}, c.ng, c.ng, c.ng};
+    const TcJob *same = c.d_res_jobs, *opp = c.d_res_jobs + c.n_res_same;
+    const double fl_same = tc_flops(c.pairs_oz.n, 1, 1) * c.res_kb_same;
+    const double fl_opp = tc_flops(c.pairs_oz.n, 1, 1) * c.res_kb_opp;
+    rs = tc_blocksums(uR, uR, uC, uC, same, c.n_res_same, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qa, c.d_err,
+                      SIGNTRI_KC_RESIDUAL, c.st, fl_same);
+    if (rs != SIGNTRI_OK) return rs;
+    rs = tc_blocksums(tR, tR, uC, uC, opp, c.n_res_opp, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qa, c.d_err,
+                      SIGNTRI_KC_RESIDUAL, c.st, fl_opp);
+    if (rs != SIGNTRI_OK) return rs;
+    rs = tc_blocksums(uR, uR, tC, tC, opp, c.n_res_opp, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qb, c.d_err,
+                      SIGNTRI_KC_RESIDUAL, c.st, fl_opp);
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaMemsetAsync(c.norms, 0, 8 * sizeof(double), c.st));
+    {
+        ProfScope ps(SIGNTRI_KC_RESIDUAL_SUM, c.st);
+        needed_finalize_kernel<<<c.n, 256, 0, c.st>>>(c.n, T, ldt, U, ldu, c.gmap, c.RA, c.RB, c.ng, c.R, c.norms);
+        SGT_LAUNCH_CHECK();
+    }
+    c.res_c = c.R;
+    c.res_s = c.R;
+    return read_norms(c);
+}
+
+// Both residuals of U over all entries (Rc into RA's memory, Rs into R) and
+// their norms: [N_T I.; N_U I.] x [N_U .J | N_T .J] in the original layout,
+// TL = N_T N_U, BR = N_U N_T, BL = N_U N_U.
+signtri_status residual_full(MixedCtx &c, const double *T, int ldt, const double *U, int ldu)
 {
     signtri_status rs = exact_slices_of(c, U, ldu, c.NUr, c.NUc, c.sUr, c.sUc);
     if (rs != SIGNTRI_OK) return rs;
-    // [N_T I.; N_U I.] x [N_U .J | N_T .J]: TL = N_T N_U, BR = N_U N_T, BL = N_U N_U
     const TcSource top{c.NTr, kOzakiSlices, c.np, c.np, c.np, c.sTr}, bot{c.NUr, kOzakiSlices, c.np, c.np, c.np, c.sUr};
     const TcSource left{c.NUc, kOzakiSlices, c.np, c.np, c.np, c.sUc},
         right{c.NTc, kOzakiSlices, c.np, c.np, c.np, c.sTc};
-    const TcQuadOut qo{{c.Rc, nullptr, c.Rs, c.Put}, c.n, c.n, c.n};
+    double *Rc = c.RA, *Put = c.RB, *Rs = c.R;
+    const TcQuadOut qo{{Rc, nullptr, Rs, Put}, c.n, c.n, c.n};
     const long long nbl = c.sc.nb;
     const long long sum_kb = (nbl + 2) * (nbl + 1) * nbl / 6;   // sum over I <= J of (J - I + 1)
-    rs = tc_blocksums(top, bot, left, right, c.d_res_jobs, c.n_res_jobs, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qo,
+    rs = tc_blocksums(top, bot, left, right, c.d_full_jobs, c.n_full_jobs, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qo,
                       c.d_err, SIGNTRI_KC_RESIDUAL, c.st, tc_flops(c.pairs_oz.n, sum_kb, 3));
     if (rs != SIGNTRI_OK) return rs;
     SGT_CUDA_TRY(cudaMemsetAsync(c.norms, 0, 8 * sizeof(double), c.st));
     {
         ProfScope ps(SIGNTRI_KC_RESIDUAL_SUM, c.st);
-        residual_finalize_kernel<<<c.n, 256, 0, c.st>>>(c.n, T, ldt, U, ldu, c.Rc, c.Put, c.Rs, c.n, c.norms);
+        residual_finalize_kernel<<<c.n, 256, 0, c.st>>>(c.n, T, ldt, U, ldu, Rc, Put, Rs, c.n, c.norms);
         SGT_LAUNCH_CHECK();
     }
-    SGT_CUDA_TRY(cudaMemcpyAsync(c.norms_host, c.norms, 8 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
-    SGT_CUDA_TRY(cudaStreamSynchronize(c.st));
-    return SIGNTRI_OK;
+    c.res_c = Rc;
+    c.res_s = Rs;
+    return read_norms(c);
 }
 
 }  // namespace
@@ -511,53 +746,68 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     c.st = st;
     c.d_err = d_err;
     build_schedule(n, c.sc);
+    const int nb = c.sc.nb;
     const size_t np = c.np;
-    const size_t split_elems = (size_t)S * np * np, oz_elems = (size_t)kOzakiSlices * np * np;
+    const size_t split_elems = (size_t)S * np * np;
+    const size_t ngr = (size_t)gathered_bound(n) + 64, oz_elems = (size_t)kOzakiSlices * ngr * ngr;
     c.Tr = take<__nv_bfloat16>(ws, split_elems); c.Tc = take<__nv_bfloat16>(ws, split_elems);
     c.Ur = take<__nv_bfloat16>(ws, split_elems); c.Uc = take<__nv_bfloat16>(ws, split_elems);
     c.Er = take<__nv_bfloat16>(ws, split_elems); c.Ec = take<__nv_bfloat16>(ws, split_elems);
-    c.NTr = take<__nv_bfloat16>(ws, oz_elems); c.NTc = take<__nv_bfloat16>(ws, oz_elems);
+    const size_t oz_orig = (size_t)kOzakiSlices * np * np;
+    c.NTgr = take<__nv_bfloat16>(ws, oz_elems); c.NTgc = take<__nv_bfloat16>(ws, oz_elems);
+    c.NTr = take<__nv_bfloat16>(ws, oz_orig); c.NTc = take<__nv_bfloat16>(ws, oz_orig);
     c.NUr = take<__nv_bfloat16>(ws, oz_elems); c.NUc = take<__nv_bfloat16>(ws, oz_elems);
     c.sTr = take<float>(ws, np); c.sTc = take<float>(ws, np); c.sUr = take<float>(ws, np); c.sUc = take<float>(ws, np);
+    c.gTr = take<float>(ws, ngr); c.gTc = take<float>(ws, ngr); c.gUr = take<float>(ws, ngr); c.gUc = take<float>(ws, ngr);
+    c.gmap = take<int>(ws, ngr); c.ginv = take<int>(ws, ngr); c.pos = take<unsigned char>(ws, np);
     c.tmpmax = take<unsigned long long>(ws, np);
     const size_t maxjobs = (size_t)std::max(c.sc.max_jobs, 1);
     c.PA = take<double>(ws, maxjobs * 16384); c.PB = take<double>(ws, maxjobs * 16384);
-    c.E = take<double>(ws, (size_t)n * n); c.Rc = take<double>(ws, (size_t)n * n);
-    c.Rs = take<double>(ws, (size_t)n * n); c.Put = take<double>(ws, (size_t)n * n);
+    c.E = take<double>(ws, (size_t)n * n); c.R = take<double>(ws, (size_t)n * n);
+    c.n_full_jobs = nb * (nb + 1) / 2;
+    c.d_full_jobs = take<TcJob>(ws, (size_t)c.n_full_jobs);
+    c.RA = take<double>(ws, ngr * ngr); c.RB = take<double>(ws, ngr * ngr);
     c.norms = take<double>(ws, 8);
-    const int nb = c.sc.nb;
-    c.n_res_jobs = nb * (nb + 1) / 2;
-    c.d_res_jobs = take<TcJob>(ws, (size_t)c.n_res_jobs);
+    const size_t pairs_max = ngr / 128 + 2 * (size_t)((n + kSuper - 1) / kSuper) + 2;
+    c.d_res_jobs = take<TcJob>(ws, pairs_max * pairs_max);
     c.d_jobs = take<TcJob>(ws, std::max<size_t>(c.sc.jobs.size(), 1));
     c.d_pairs_split = take<TcPairs>(ws, 1);
     c.d_pairs_oz = take<TcPairs>(ws, 1);
     c.norms_host = norms_host;
-    if (!c.Tr || !c.Tc || !c.Ur || !c.Uc || !c.Er || !c.Ec || !c.NTr || !c.NTc || !c.NUr || !c.NUc || !c.sTr ||
-        !c.sTc || !c.sUr || !c.sUc || !c.tmpmax || !c.PA || !c.PB || !c.E || !c.Rc || !c.Rs || !c.Put || !c.norms ||
-        !c.d_res_jobs || !c.d_jobs || !c.d_pairs_split || !c.d_pairs_oz)
+    if (!c.Tr || !c.Tc || !c.Ur || !c.Uc || !c.Er || !c.Ec || !c.NTgr || !c.NTgc || !c.NTr || !c.NTc || !c.NUr ||
+        !c.NUc || !c.d_full_jobs || !c.sTr ||
+        !c.sTc || !c.sUr || !c.sUc || !c.gTr || !c.gTc || !c.gUr || !c.gUc || !c.gmap || !c.ginv || !c.pos ||
+        !c.tmpmax || !c.PA || !c.PB || !c.E || !c.R || !c.RA || !c.RB || !c.norms || !c.d_res_jobs || !c.d_jobs ||
+        !c.d_pairs_split || !c.d_pairs_oz)
         return SIGNTRI_ERR_NO_WORKSPACE;
     c.pairs_split = split_pairs(S);
     c.pairs_oz = ozaki_pairs_impl(kOzakiSlices);
-    // residual jobs in 8 x 8 groups of tiles: the CTAs resident together
-    // share row and column panels in L2
-    std::vector<TcJob> rj;
-    rj.reserve(c.n_res_jobs);
-    constexpr int G = 8;
-    for (int I0 = 0; I0 < nb; I0 += G)
-        for (int J0 = I0 / G * G; J0 < nb; J0 += G)
-            for (int I = I0; I < std::min(I0 + G, nb); I++)
-                for (int J = std::max(J0, I); J < std::min(J0 + G, nb); J++) {
-            TcJob j;
-            j.rt = I * MB; j.rb = I * MB; j.cl = J * MB; j.cr = J * MB;
-            j.kb0 = I; j.kb1 = J + 1; j.slot = 0; j.pad = 0;
-            rj.push_back(j);
-        }
-    SGT_CUDA_TRY(cudaMemcpyAsync(c.d_res_jobs, rj.data(), rj.size() * sizeof(TcJob), cudaMemcpyHostToDevice, st));
     if (!c.sc.jobs.empty())
         SGT_CUDA_TRY(cudaMemcpyAsync(c.d_jobs, c.sc.jobs.data(), c.sc.jobs.size() * sizeof(TcJob),
                                      cudaMemcpyHostToDevice, st));
     SGT_CUDA_TRY(cudaMemcpyAsync(c.d_pairs_split, &c.pairs_split, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
     SGT_CUDA_TRY(cudaMemcpyAsync(c.d_pairs_oz, &c.pairs_oz, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
+    {
+        // full-residual jobs in 8 x 8 groups of tiles: the CTAs resident
+        // together share row and column panels in L2
+        std::vector<TcJob> rj;
+        rj.reserve(c.n_full_jobs);
+        constexpr int G = 8;
+        for (int I0 = 0; I0 < nb; I0 += G)
+            for (int J0 = I0 / G * G; J0 < nb; J0 += G)
+                for (int I = I0; I < std::min(I0 + G, nb); I++)
+                    for (int J = std::max(J0, I); J < std::min(J0 + G, nb); J++) {
+                        TcJob j;
+                        j.rt = I * MB; j.rb = I * MB; j.cl = J * MB; j.cr = J * MB;
+                        j.kb0 = I; j.kb1 = J + 1; j.slot = 0; j.pad = 0;
+                        rj.push_back(j);
+                    }
+        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_full_jobs, rj.data(), rj.size() * sizeof(TcJob), cudaMemcpyHostToDevice,
+                                     st));
+        SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    signtri_status rs0 = setup_gathered(c, T, ldt);
+    if (rs0 != SIGNTRI_OK) return rs0;
     // slices start from zero (padding and the not-yet-computed blocks)
     SGT_CUDA_TRY(cudaMemsetAsync(c.Ur, 0, split_elems * 2, st));
     SGT_CUDA_TRY(cudaMemsetAsync(c.Uc, 0, split_elems * 2, st));
@@ -565,6 +815,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     SGT_CUDA_TRY(cudaMemsetAsync(c.Ec, 0, split_elems * 2, st));
     signtri_status rs;
     if ((rs = split_full(c, T, ldt, c.Tr, c.Tc)) != SIGNTRI_OK) return rs;
+    if ((rs = gathered_slices_of(c, T, ldt, c.NTgr, c.NTgc, c.sTr, c.sTc, c.gTr, c.gTc)) != SIGNTRI_OK) return rs;
     if ((rs = exact_slices_of(c, T, ldt, c.NTr, c.NTc, c.sTr, c.sTc)) != SIGNTRI_OK) return rs;
 
     // 1. low-precision solve: diagonal blocks in float64, the rest by sweep
@@ -572,20 +823,30 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     if ((rs = diag_leaves_f64(n, T, ldt, U, ldu, MB, st)) != SIGNTRI_OK) return rs;
     if ((rs = sweep<0>(c, T, ldt, U, ldu, c.Ur, c.Uc, nullptr, 0)) != SIGNTRI_OK) return rs;
 
-    // 2. refinement
+    // 2. refinement: the first residual in the needed form (it only drives the
+    // correction), every later one -- and any acceptance -- in the full form
     double prev = 1e300;
     rep.steps = 0;
     rep.fallback = 0;
     for (int step = 0;; step++) {
-        if ((rs = residual(c, T, ldt, U, ldu)) != SIGNTRI_OK) return rs;
-        const double *h = c.norms_host;
-        const double nT = std::sqrt(h[2]), nU = std::sqrt(h[3]);
-        rep.resid_commute = std::sqrt(h[0]) / (nT * nU);
-        rep.resid_involution = std::sqrt(h[1]) / (nU * nU);
-        const double worst = std::max(rep.resid_commute, rep.resid_involution);
+        bool full = step > 0;
+        if ((rs = full ? residual_full(c, T, ldt, U, ldu) : residual_needed(c, T, ldt, U, ldu)) != SIGNTRI_OK)
+            return rs;
+        double worst = 0.0;
+        for (int pass = 0; pass < 2; pass++) {
+            const double *h = c.norms_host;
+            const double nT = std::sqrt(h[2]), nU = std::sqrt(h[3]);
+            rep.resid_commute = std::sqrt(h[0]) / (nT * nU);
+            rep.resid_involution = std::sqrt(h[1]) / (nU * nU);
+            worst = std::max(rep.resid_commute, rep.resid_involution);
+            if (full || !(worst <= prm.tol)) break;
+            // needed residuals already small: confirm with the full form
+            if ((rs = residual_full(c, T, ldt, U, ldu)) != SIGNTRI_OK) return rs;
+            full = true;
+        }
         if (step == 0) rep.resid0 = worst;
         if (!(worst == worst)) { rep.fallback = 1; return SIGNTRI_OK; }   // NaN
-        if (worst <= prm.tol) return SIGNTRI_OK;
+        if (full && worst <= prm.tol) return SIGNTRI_OK;
         if (step >= prm.max_steps || (step > 0 && worst > prev / prm.min_contraction)) {
             rep.fallback = 1;
             return SIGNTRI_OK;
@@ -605,7 +866,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
             SGT_CUDA_TRY(cudaFuncSetAttribute(corr_diag_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)dsm));
             ProfScope ps(SIGNTRI_KC_CORRECTION, st);
-            corr_diag_leaf_kernel<<<nb, kLeafThreads, dsm, st>>>(n, T, ldt, U, ldu, c.Rc, c.Rs, n, c.E, n);
+            corr_diag_leaf_kernel<<<nb, kLeafThreads, dsm, st>>>(n, T, ldt, U, ldu, c.res_c, c.res_s, n, c.E, n);
             SGT_LAUNCH_CHECK();
         }
         if ((rs = sweep<1>(c, T, ldt, c.E, n, c.Er, c.Ec, U, ldu)) != SIGNTRI_OK) return rs;

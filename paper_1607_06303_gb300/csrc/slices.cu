@@ -143,6 +143,60 @@ __global__ void col_slices_kernel(int k, int n, const double *__restrict__ M, in
     for (int s = 0; s < S; s++) C[((size_t)s * rows_pad + j) * ldc + kk] = __float2bfloat16_rn(q[s]);
 }
 
+// Gathered layout (residual products): position g of the gathered index
+// space holds original index inv[g] (-1 = zero padding).  Row slices
+// R[s][g][h] = slice s of M[inv[g], inv[h]] (strictly upper part), written
+// for every g < rows, h < ldr (padding and the lower part as zeros), with the
+// per-row scales already gathered (scale_g[g]).
+__global__ void row_slices_gathered_kernel(const double *__restrict__ M, int ldm, const int *__restrict__ inv,
+                                           int ng, int S, const float *__restrict__ scale_g,
+                                           __nv_bfloat16 *__restrict__ R, int rows, int ldr)
+{
+    __shared__ double tile[TS][TS + 1];
+    const int g0 = blockIdx.y * TS, h0 = blockIdx.x * TS;
+    for (int y = threadIdx.y; y < TS; y += blockDim.y) {     // y: column offset
+        const int h = h0 + y, g = g0 + threadIdx.x;
+        const int i = g < ng ? inv[g] : -1, kk = h < ng ? inv[h] : -1;
+        double v = 0.0;
+        if (i >= 0 && kk >= 0 && i < kk) v = SGT_AT(M, ldm, i, kk);
+        tile[threadIdx.x][y] = v;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < TS; y += blockDim.y) {     // y: row offset
+        const int g = g0 + y, h = h0 + threadIdx.x;
+        if (g >= rows || h >= ldr) continue;
+        float q[8];
+        exact_slices(tile[y][threadIdx.x], g < ng ? ilogbf(scale_g[g]) : 0, S, q);
+        for (int s = 0; s < S; s++) R[((size_t)s * rows + g) * ldr + h] = __float2bfloat16_rn(q[s]);
+    }
+}
+
+// Column slices C[s][g][h] = slice s of M[inv[h], inv[g]] (column inv[g]).
+__global__ void col_slices_gathered_kernel(const double *__restrict__ M, int ldm, const int *__restrict__ inv,
+                                           int ng, int S, const float *__restrict__ scale_g,
+                                           __nv_bfloat16 *__restrict__ C, int rows, int ldc)
+{
+    const int g = blockIdx.y;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= ldc) return;
+    const int j = g < ng ? inv[g] : -1, kk = h < ng ? inv[h] : -1;
+    double v = 0.0;
+    if (j >= 0 && kk >= 0 && kk < j) v = SGT_AT(M, ldm, kk, j);
+    float q[8];
+    exact_slices(v, g < ng ? ilogbf(scale_g[g]) : 0, S, q);
+    for (int s = 0; s < S; s++) C[((size_t)s * rows + g) * ldc + h] = __float2bfloat16_rn(q[s]);
+}
+
+// scale_g[g] = scale[inv[g]], 1 for padding
+__global__ void gather_scales_kernel(int rows, int ng, const int *__restrict__ inv, const float *__restrict__ scale,
+                                     float *__restrict__ scale_g)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= rows) return;
+    const int i = g < ng ? inv[g] : -1;
+    scale_g[g] = i >= 0 ? scale[i] : 1.0f;
+}
+
 // C (m x n) from the top-left / top-right quadrants of the job outputs.
 __global__ void gather_gemm_kernel(int m, int n, const double *__restrict__ out, int ntj, double *__restrict__ C,
                                    int ldc)
@@ -194,6 +248,25 @@ signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, 
     dim3 grid((ldc + 255) / 256, rows_pad);
     ProfScope ps(SIGNTRI_KC_CONVERT, st);
     col_slices_kernel<<<grid, 256, 0, st>>>(k, n, M, ldm, tri, S, scale, C, rows_pad, ldc);
+    SGT_LAUNCH_CHECK();
+    return SIGNTRI_OK;
+}
+
+signtri_status make_gathered_slices(int n, const double *M, int ldm, const int *inv, int ng, int S,
+                                    const float *sR, const float *sC, float *sRg, float *sCg, __nv_bfloat16 *R,
+                                    __nv_bfloat16 *C, int rows, int ld, cudaStream_t st)
+{
+    if (S > 8) return SIGNTRI_ERR_BAD_ARG;
+    (void)n;
+    ProfScope ps(SIGNTRI_KC_CONVERT, st);
+    gather_scales_kernel<<<(rows + 255) / 256, 256, 0, st>>>(rows, ng, inv, sR, sRg);
+    SGT_LAUNCH_CHECK();
+    gather_scales_kernel<<<(rows + 255) / 256, 256, 0, st>>>(rows, ng, inv, sC, sCg);
+    SGT_LAUNCH_CHECK();
+    dim3 grid((ld + TS - 1) / TS, (rows + TS - 1) / TS), block(TS, 8);
+    row_slices_gathered_kernel<<<grid, block, 0, st>>>(M, ldm, inv, ng, S, sRg, R, rows, ld);
+    SGT_LAUNCH_CHECK();
+    col_slices_gathered_kernel<<<dim3((ld + 255) / 256, rows), 256, 0, st>>>(M, ldm, inv, ng, S, sCg, C, rows, ld);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }

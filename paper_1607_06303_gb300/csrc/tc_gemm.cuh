@@ -64,6 +64,14 @@ signtri_status make_row_slices(int m, int k, const double *M, int ldm, int tri, 
 signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, int S, const float *scale,
                                __nv_bfloat16 *C, int rows_pad, int ldc, cudaStream_t st);
 
+// Exact slices of the strictly upper part of the n x n matrix M in a gathered
+// index space (inv[g] = original index at position g, -1 = padding, ng
+// positions used, `rows` allocated, pitch ld): per-row and per-column scales
+// sR, sC (original indices) are gathered into sRg, sCg.
+signtri_status make_gathered_slices(int n, const double *M, int ldm, const int *inv, int ng, int S,
+                                    const float *sR, const float *sC, float *sRg, float *sCg, __nv_bfloat16 *R,
+                                    __nv_bfloat16 *C, int rows, int ld, cudaStream_t st);
+
 signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSource &left, const TcSource &right,
                             const TcJob *d_jobs, int njobs, const TcPairs &pairs, const TcPairs *d_pairs, int chunk_kb,
                             double *out, const TcQuadOut &qo, int *d_err, int kernel_class, cudaStream_t st,
