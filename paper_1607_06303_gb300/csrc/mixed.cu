@@ -459,8 +459,9 @@ struct MixedCtx {
     double *RA, *RB, *R;
     const double *res_c, *res_s;   // what the last residual left for the correction
     double *norms, *norms_host; // [0] Rc^2 [1] Rs^2 [2] T^2 [3] U^2 [4] E^2
-    TcJob *d_full_jobs;         // full residual: all 64-block pairs I <= J
+    TcJob *d_full_jobs;         // full residual: 2 x 2 block jobs
     int n_full_jobs;
+    double full_kb;             // sum over full jobs of used quadrants x K-blocks
     TcJob *d_res_jobs;          // needed residual: equal-sign jobs, then opposite-sign jobs
     int n_res_same, n_res_opp;
     double res_kb_same, res_kb_opp;   // sum over jobs of used quadrants x K-blocks
@@ -477,8 +478,8 @@ size_t bytes_for(int n, int S)
     b += 6 * (size_t)S * np * np * 2 + 6 * 256;                       // split slices
     const size_t ngr = (size_t)gathered_bound(n) + 64;
     b += 4 * (size_t)kOzakiSlices * ngr * ngr * 2 + 4 * 256;           // exact slices: T gathered, U
-    b += 2 * (size_t)kOzakiSlices * np * np * 2 + 2 * 256;             // exact slices: T original
-    b += 4 * np * 4 + np * 8 + 6 * 256;                                 // scales, tmp
+    b += 2 * (size_t)kOzakiSlices * (np + 64) * np * 2 + 2 * 256;      // exact slices: T original
+    b += 4 * (np + 64) * 4 + (np + 64) * 8 + 6 * 256;                   // scales, tmp
     b += 4 * ngr * 4 + 4 * 256 + 2 * ngr * 4 + np + 3 * 256;            // gathered scales, maps, signs
     b += 2 * ngr * ngr * 8 + 2 * 256;                                   // RA, RB
     const size_t maxjobs = (size_t)kTargetJobs + nb + 8;
@@ -487,7 +488,8 @@ size_t bytes_for(int n, int S)
     b += 64 + 256;                                                      // norms
     const size_t pairs_max = ngr / 128 + 2 * (size_t)((n + kSuper - 1) / kSuper) + 2;
     b += pairs_max * pairs_max * sizeof(TcJob) + 256;                   // needed-residual jobs
-    b += (size_t)nb * (nb + 1) / 2 * sizeof(TcJob) + 256;               // full-residual jobs
+    const size_t nbp = (nb + 1) / 2;
+    b += nbp * (nbp + 1) / 2 * sizeof(TcJob) + 256;                     // full-residual jobs
     b += nb * (size_t)(kTargetJobs + nb) * sizeof(TcJob) + 256;         // wavefront jobs (bound)
     b += 2 * sizeof(TcPairs) + 512;
     return b;
@@ -519,9 +521,11 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
     const TcSource srcV_r{Vr, c.S, c.np, c.np, c.np, nullptr}, srcV_c{Vc, c.S, c.np, c.np, c.np, nullptr};
     const TcSource srcU_r{c.Ur, c.S, c.np, c.np, c.np, nullptr}, srcU_c{c.Uc, c.S, c.np, c.np, c.np, nullptr};
     const TcQuadOut slots{{nullptr, nullptr, nullptr, nullptr}, 0, 0, 0};
-    // K-blocks per tensor-core unit: small when several slice pairs share a
-    // unit (they re-read its panels from L2), larger for a single pair
-    const int chunk = c.pairs_split.n > 1 ? 4 : 16;
+    // K-blocks per tensor-core unit: with several unit-weight slice pairs the
+    // engine keeps every slice of a K-block resident and accumulates all pairs
+    // into one unit, so 2 K-blocks keep each fp32 accumulation short; a single
+    // pair takes long units
+    const int chunk = c.pairs_split.n > 1 ? 2 : 16;
     for (int d = 1; d < nb; d++) {
         const int ntiles = nb - d;
         const int njobs = c.sc.job_off[d + 1] - c.sc.job_off[d];
@@ -643,8 +647,8 @@ signtri_status gathered_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bf
                                   float *sR, float *sC, float *gR, float *gC)
 {
     signtri_status rs;
-    if ((rs = make_scales(c.n, c.n, M, ldm, 1, true, c.np, c.tmpmax, sR, c.st)) != SIGNTRI_OK) return rs;
-    if ((rs = make_scales(c.n, c.n, M, ldm, 1, false, c.np, c.tmpmax, sC, c.st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_scales(c.n, c.n, M, ldm, 1, true, c.np + 64, c.tmpmax, sR, c.st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_scales(c.n, c.n, M, ldm, 1, false, c.np + 64, c.tmpmax, sC, c.st)) != SIGNTRI_OK) return rs;
     return make_gathered_slices(c.n, M, ldm, c.ginv, c.ng, kOzakiSlices, sR, sC, gR, gC, R, C, c.rows_g, c.rows_g,
                                 c.st);
 }
@@ -654,10 +658,11 @@ signtri_status exact_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bfloa
                                float *sC)
 {
     signtri_status rs;
-    if ((rs = make_scales(c.n, c.n, M, ldm, 1, true, c.np, c.tmpmax, sR, c.st)) != SIGNTRI_OK) return rs;
-    if ((rs = make_scales(c.n, c.n, M, ldm, 1, false, c.np, c.tmpmax, sC, c.st)) != SIGNTRI_OK) return rs;
-    if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, sR, R, c.np, c.np, c.st)) != SIGNTRI_OK) return rs;
-    return make_col_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, sC, C, c.np, c.np, c.st);
+    if ((rs = make_scales(c.n, c.n, M, ldm, 1, true, c.np + 64, c.tmpmax, sR, c.st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_scales(c.n, c.n, M, ldm, 1, false, c.np + 64, c.tmpmax, sC, c.st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, sR, R, c.np + 64, c.np, c.st)) != SIGNTRI_OK)
+        return rs;
+    return make_col_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, sC, C, c.np + 64, c.np, c.st);
 }
 
 signtri_status read_norms(MixedCtx &c)
@@ -705,29 +710,39 @@ signtri_status residual_needed(MixedCtx &c, const double *T, int ldt, const doub
 }
 
 // Both residuals of U over all entries (Rc into RA's memory, Rs into R) and
-// their norms: [N_T I.; N_U I.] x [N_U .J | N_T .J] in the original layout,
-// TL = N_T N_U, BR = N_U N_T, BL = N_U N_U.
+// their norms.  Original layout; each job pairs row blocks (2i, 2i+1) with
+// column blocks (2j, 2j+1), j >= i, over K-blocks [2i, 2j+2) (terms outside
+// an output block's own range are structural zeros), and three launches use
+// all four quadrants: N_U N_U (into Rs), N_T N_U (into Ptu) and N_U N_T
+// (into Put).  A lone last block pairs with the zero block at row np.
 signtri_status residual_full(MixedCtx &c, const double *T, int ldt, const double *U, int ldu)
 {
     signtri_status rs = exact_slices_of(c, U, ldu, c.NUr, c.NUc, c.sUr, c.sUc);
     if (rs != SIGNTRI_OK) return rs;
-    const TcSource top{c.NTr, kOzakiSlices, c.np, c.np, c.np, c.sTr}, bot{c.NUr, kOzakiSlices, c.np, c.np, c.np, c.sUr};
-    const TcSource left{c.NUc, kOzakiSlices, c.np, c.np, c.np, c.sUc},
-        right{c.NTc, kOzakiSlices, c.np, c.np, c.np, c.sTc};
-    double *Rc = c.RA, *Put = c.RB, *Rs = c.R;
-    const TcQuadOut qo{{Rc, nullptr, Rs, Put}, c.n, c.n, c.n};
-    const long long nbl = c.sc.nb;
-    const long long sum_kb = (nbl + 2) * (nbl + 1) * nbl / 6;   // sum over I <= J of (J - I + 1)
-    rs = tc_blocksums(top, bot, left, right, c.d_full_jobs, c.n_full_jobs, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qo,
-                      c.d_err, SIGNTRI_KC_RESIDUAL, c.st, tc_flops(c.pairs_oz.n, sum_kb, 3));
+    const int R = c.np + 64;
+    const TcSource uR{c.NUr, kOzakiSlices, R, c.np, c.np, c.sUr}, uC{c.NUc, kOzakiSlices, R, c.np, c.np, c.sUc};
+    const TcSource tR{c.NTr, kOzakiSlices, R, c.np, c.np, c.sTr}, tC{c.NTc, kOzakiSlices, R, c.np, c.np, c.sTc};
+    double *Ptu = c.RA, *Put = c.RB, *Rs = c.R;
+    const TcQuadOut qs{{Rs, Rs, Rs, Rs}, c.n, c.n, c.n};
+    const TcQuadOut qtu{{Ptu, Ptu, Ptu, Ptu}, c.n, c.n, c.n};
+    const TcQuadOut qut{{Put, Put, Put, Put}, c.n, c.n, c.n};
+    const double fl = tc_flops(c.pairs_oz.n, 1, 1) * c.full_kb;
+    rs = tc_blocksums(uR, uR, uC, uC, c.d_full_jobs, c.n_full_jobs, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qs, c.d_err,
+                      SIGNTRI_KC_RESIDUAL, c.st, fl);
+    if (rs != SIGNTRI_OK) return rs;
+    rs = tc_blocksums(tR, tR, uC, uC, c.d_full_jobs, c.n_full_jobs, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qtu,
+                      c.d_err, SIGNTRI_KC_RESIDUAL, c.st, fl);
+    if (rs != SIGNTRI_OK) return rs;
+    rs = tc_blocksums(uR, uR, tC, tC, c.d_full_jobs, c.n_full_jobs, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qut,
+                      c.d_err, SIGNTRI_KC_RESIDUAL, c.st, fl);
     if (rs != SIGNTRI_OK) return rs;
     SGT_CUDA_TRY(cudaMemsetAsync(c.norms, 0, 8 * sizeof(double), c.st));
     {
         ProfScope ps(SIGNTRI_KC_RESIDUAL_SUM, c.st);
-        residual_finalize_kernel<<<c.n, 256, 0, c.st>>>(c.n, T, ldt, U, ldu, Rc, Put, Rs, c.n, c.norms);
+        residual_finalize_kernel<<<c.n, 256, 0, c.st>>>(c.n, T, ldt, U, ldu, Ptu, Put, Rs, c.n, c.norms);
         SGT_LAUNCH_CHECK();
     }
-    c.res_c = Rc;
+    c.res_c = Ptu;
     c.res_s = Rs;
     return read_norms(c);
 }
@@ -753,18 +768,21 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     c.Tr = take<__nv_bfloat16>(ws, split_elems); c.Tc = take<__nv_bfloat16>(ws, split_elems);
     c.Ur = take<__nv_bfloat16>(ws, split_elems); c.Uc = take<__nv_bfloat16>(ws, split_elems);
     c.Er = take<__nv_bfloat16>(ws, split_elems); c.Ec = take<__nv_bfloat16>(ws, split_elems);
-    const size_t oz_orig = (size_t)kOzakiSlices * np * np;
+    const size_t oz_orig = (size_t)kOzakiSlices * (np + 64) * np;
     c.NTgr = take<__nv_bfloat16>(ws, oz_elems); c.NTgc = take<__nv_bfloat16>(ws, oz_elems);
     c.NTr = take<__nv_bfloat16>(ws, oz_orig); c.NTc = take<__nv_bfloat16>(ws, oz_orig);
     c.NUr = take<__nv_bfloat16>(ws, oz_elems); c.NUc = take<__nv_bfloat16>(ws, oz_elems);
-    c.sTr = take<float>(ws, np); c.sTc = take<float>(ws, np); c.sUr = take<float>(ws, np); c.sUc = take<float>(ws, np);
+    // original-index scales and their max buffer cover the zero block too
+    c.sTr = take<float>(ws, np + 64); c.sTc = take<float>(ws, np + 64);
+    c.sUr = take<float>(ws, np + 64); c.sUc = take<float>(ws, np + 64);
     c.gTr = take<float>(ws, ngr); c.gTc = take<float>(ws, ngr); c.gUr = take<float>(ws, ngr); c.gUc = take<float>(ws, ngr);
     c.gmap = take<int>(ws, ngr); c.ginv = take<int>(ws, ngr); c.pos = take<unsigned char>(ws, np);
-    c.tmpmax = take<unsigned long long>(ws, np);
+    c.tmpmax = take<unsigned long long>(ws, np + 64);
     const size_t maxjobs = (size_t)std::max(c.sc.max_jobs, 1);
     c.PA = take<double>(ws, maxjobs * 16384); c.PB = take<double>(ws, maxjobs * 16384);
     c.E = take<double>(ws, (size_t)n * n); c.R = take<double>(ws, (size_t)n * n);
-    c.n_full_jobs = nb * (nb + 1) / 2;
+    const int nbp = (nb + 1) / 2;
+    c.n_full_jobs = nbp * (nbp + 1) / 2;
     c.d_full_jobs = take<TcJob>(ws, (size_t)c.n_full_jobs);
     c.RA = take<double>(ws, ngr * ngr); c.RB = take<double>(ws, ngr * ngr);
     c.norms = take<double>(ws, 8);
@@ -788,20 +806,25 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     SGT_CUDA_TRY(cudaMemcpyAsync(c.d_pairs_split, &c.pairs_split, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
     SGT_CUDA_TRY(cudaMemcpyAsync(c.d_pairs_oz, &c.pairs_oz, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
     {
-        // full-residual jobs in 8 x 8 groups of tiles: the CTAs resident
+        // full-residual jobs in 8 x 8 groups of block pairs: the CTAs resident
         // together share row and column panels in L2
         std::vector<TcJob> rj;
         rj.reserve(c.n_full_jobs);
+        double kb = 0.0;
         constexpr int G = 8;
-        for (int I0 = 0; I0 < nb; I0 += G)
-            for (int J0 = I0 / G * G; J0 < nb; J0 += G)
-                for (int I = I0; I < std::min(I0 + G, nb); I++)
-                    for (int J = std::max(J0, I); J < std::min(J0 + G, nb); J++) {
+        const int zero = (int)np;   // the zero block
+        for (int I0 = 0; I0 < nbp; I0 += G)
+            for (int J0 = I0 / G * G; J0 < nbp; J0 += G)
+                for (int I = I0; I < std::min(I0 + G, nbp); I++)
+                    for (int J = std::max(J0, I); J < std::min(J0 + G, nbp); J++) {
                         TcJob j;
-                        j.rt = I * MB; j.rb = I * MB; j.cl = J * MB; j.cr = J * MB;
-                        j.kb0 = I; j.kb1 = J + 1; j.slot = 0; j.pad = 0;
+                        j.rt = 2 * I * MB; j.rb = 2 * I + 1 < nb ? (2 * I + 1) * MB : zero;
+                        j.cl = 2 * J * MB; j.cr = 2 * J + 1 < nb ? (2 * J + 1) * MB : zero;
+                        j.kb0 = 2 * I; j.kb1 = std::min(2 * J + 2, nb); j.slot = 0; j.pad = 0;
+                        kb += (double)((j.rb != zero) + 1) * ((j.cr != zero) + 1) * (j.kb1 - j.kb0);
                         rj.push_back(j);
                     }
+        c.full_kb = kb;
         SGT_CUDA_TRY(cudaMemcpyAsync(c.d_full_jobs, rj.data(), rj.size() * sizeof(TcJob), cudaMemcpyHostToDevice,
                                      st));
         SGT_CUDA_TRY(cudaStreamSynchronize(st));

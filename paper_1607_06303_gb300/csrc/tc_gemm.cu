@@ -25,6 +25,8 @@
 // buffer and the lo parts in registers.
 // Every mbarrier wait is bounded; on expiry the CTA records an error and
 // returns after draining what it issued.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -219,7 +221,7 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
                    int rowsA, int rowsB, const TcJob *__restrict__ jobs, const TcPairs *__restrict__ pairs_g, int chunk_kb,
                    const float *__restrict__ sTop, const float *__restrict__ sBot, const float *__restrict__ sLeft,
                    const float *__restrict__ sRight, double *__restrict__ out, TcQuadOut qo,
-                   int *__restrict__ err)
+                   int *__restrict__ err, int resident, int nsl)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -240,7 +242,13 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
         reinterpret_cast<int *>(pairs_s)[i] = reinterpret_cast<const int *>(pairs_g)[i];
     __syncthreads();
     const TcPairs &pairs = *pairs_s;
-    const int nunits = pairs.n * nchunks;
+    // pair mode: one unit per (K-chunk, pair), stages of kKPS K-blocks of one
+    // slice pair.  Resident mode (unit-weight pairs of nsl slices): a stage
+    // holds one K-block of all nsl slices of A and of B, every pair's MMAs
+    // are issued from it into one accumulator, one unit per K-chunk.
+    const int nunits = resident ? nchunks : pairs.n * nchunks;
+    const int sbytes = resident ? 2 * nsl * (kHalfBytes / 2) : kStageBytes;
+    const int nring = resident ? min(kStages, (kStages * kStageBytes) / sbytes) : kStages;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -270,35 +278,51 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
             long long issued = 0;
             bool ok = true;
             for (int u = 0; u < nunits && ok; u++) {
-                const int c = u / pairs.n, p = u % pairs.n;   // chunk-major: the pairs of one
-                                                              // K-chunk reuse its panels in L2
-                const int ya = pairs.s[p] * rowsA, yb = pairs.t[p] * rowsB;
+                const int c = resident ? u : u / pairs.n, p = resident ? 0 : u % pairs.n;
+                // chunk-major: the pairs of one K-chunk reuse its panels in L2
                 const int kbs = job.kb0 + c * chunk_kb, kbe = min(kbs + chunk_kb, job.kb1);
-                for (int kb = kbs; kb < kbe; kb += kKPS) {
-                    const int nk = min(kKPS, kbe - kb);
+                const int step = resident ? 1 : kKPS;
+                for (int kb = kbs; kb < kbe; kb += step) {
                     if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) { ok = false; break; }
-                    mbar_expect_tx(&full[stage], nk * kHalfBytes);
-                    for (int h = 0; h < nk; h++) {
-                        // stage layout: A halves [h][top 8 KB | bottom 8 KB], then B halves
-                        unsigned char *a = smem + stage * kStageBytes + h * (kHalfBytes / 2);
-                        unsigned char *b = smem + stage * kStageBytes + kStageBytes / 2 + h * (kHalfBytes / 2);
-                        const int x = (kb + h) * 64;
-                        tma_load_2d(a, &mTop, &full[stage], x, ya + job.rt);
-                        tma_load_2d(a + 8192, &mBot, &full[stage], x, ya + job.rb);
-                        tma_load_2d(b, &mLeft, &full[stage], x, yb + job.cl);
-                        tma_load_2d(b + 8192, &mRight, &full[stage], x, yb + job.cr);
+                    unsigned char *base = smem + stage * sbytes;
+                    if (resident) {
+                        // [A slice 0 | ... | A slice nsl-1 | B slice 0 | ...], 16 KB each
+                        mbar_expect_tx(&full[stage], 2 * nsl * (kHalfBytes / 2));
+                        const int x = kb * 64;
+                        for (int sl = 0; sl < nsl; sl++) {
+                            unsigned char *a = base + sl * (kHalfBytes / 2);
+                            unsigned char *b = base + (nsl + sl) * (kHalfBytes / 2);
+                            tma_load_2d(a, &mTop, &full[stage], x, sl * rowsA + job.rt);
+                            tma_load_2d(a + 8192, &mBot, &full[stage], x, sl * rowsA + job.rb);
+                            tma_load_2d(b, &mLeft, &full[stage], x, sl * rowsB + job.cl);
+                            tma_load_2d(b + 8192, &mRight, &full[stage], x, sl * rowsB + job.cr);
+                        }
+                    } else {
+                        const int nk = min(kKPS, kbe - kb);
+                        const int ya = pairs.s[p] * rowsA, yb = pairs.t[p] * rowsB;
+                        mbar_expect_tx(&full[stage], nk * kHalfBytes);
+                        for (int h = 0; h < nk; h++) {
+                            // stage layout: A halves [h][top 8 KB | bottom 8 KB], then B halves
+                            unsigned char *a = base + h * (kHalfBytes / 2);
+                            unsigned char *b = base + kStageBytes / 2 + h * (kHalfBytes / 2);
+                            const int x = (kb + h) * 64;
+                            tma_load_2d(a, &mTop, &full[stage], x, ya + job.rt);
+                            tma_load_2d(a + 8192, &mBot, &full[stage], x, ya + job.rb);
+                            tma_load_2d(b, &mLeft, &full[stage], x, yb + job.cl);
+                            tma_load_2d(b + 8192, &mRight, &full[stage], x, yb + job.cr);
+                        }
                     }
                     issued++;
-                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                    if (++stage == nring) { stage = 0; phase ^= 1; }
                 }
             }
             if (!ok) {
                 *abort_flag = 1;
                 atomicExch(err, 1);
                 // drain: wait (bounded) for the loads of the last stages issued
-                const long long tail = issued < kStages ? issued : kStages;
+                const long long tail = issued < nring ? issued : nring;
                 for (long long i = 0; i < tail; i++) {
-                    if (stage == 0) { stage = kStages - 1; phase ^= 1; } else stage--;
+                    if (stage == 0) { stage = nring - 1; phase ^= 1; } else stage--;
                     const uint32_t a = smem_u32(&full[stage]);
                     const long long t0 = clock64();
                     while (clock64() - t0 < kWaitCycles) {
@@ -325,23 +349,36 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
                 if (!mbar_wait(&tempty[buf], tphase ^ 1, abort_flag)) { ok = false; break; }
                 fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(buf * 128);
-                const int c = u / pairs.n;
+                const int c = resident ? u : u / pairs.n;
                 const int kbs = job.kb0 + c * chunk_kb, kbe = min(kbs + chunk_kb, job.kb1);
-                for (int kb = kbs; kb < kbe; kb += kKPS) {
-                    const int nk = min(kKPS, kbe - kb);
+                const int step = resident ? 1 : kKPS;
+                for (int kb = kbs; kb < kbe; kb += step) {
                     if (!mbar_wait(&full[stage], phase, abort_flag)) { ok = false; break; }
                     fence_after();
-                    for (int h = 0; h < nk; h++) {
-                        unsigned char *a = smem + stage * kStageBytes + h * (kHalfBytes / 2);
-                        unsigned char *b = smem + stage * kStageBytes + kStageBytes / 2 + h * (kHalfBytes / 2);
-                        const uint64_t ad = smem_desc(a), bd = smem_desc(b);
+                    unsigned char *base = smem + stage * sbytes;
+                    if (resident) {
+                        for (int p = 0; p < pairs.n; p++) {
+                            const uint64_t ad = smem_desc(base + pairs.s[p] * (kHalfBytes / 2));
+                            const uint64_t bd = smem_desc(base + (nsl + pairs.t[p]) * (kHalfBytes / 2));
 #pragma unroll
-                        for (int k = 0; k < 4; k++)
-                            mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k),
-                                     (kb > kbs || h > 0 || k > 0) ? 1u : 0u);
+                            for (int k = 0; k < 4; k++)
+                                mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k),
+                                         (kb > kbs || p > 0 || k > 0) ? 1u : 0u);
+                        }
+                    } else {
+                        const int nk = min(kKPS, kbe - kb);
+                        for (int h = 0; h < nk; h++) {
+                            unsigned char *a = base + h * (kHalfBytes / 2);
+                            unsigned char *b = base + kStageBytes / 2 + h * (kHalfBytes / 2);
+                            const uint64_t ad = smem_desc(a), bd = smem_desc(b);
+#pragma unroll
+                            for (int k = 0; k < 4; k++)
+                                mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k),
+                                         (kb > kbs || h > 0 || k > 0) ? 1u : 0u);
+                        }
                     }
                     mma_commit(&empty[stage]);
-                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                    if (++stage == nring) { stage = 0; phase ^= 1; }
                 }
                 if (!ok) break;
                 mma_commit(&tfull[buf]);
@@ -367,7 +404,7 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
             const uint32_t tphase = (u / kBufs) & 1;
             if (!mbar_wait(&tfull[buf], tphase, abort_flag)) { ok = false; break; }
             fence_after();
-            const float w = pairs.w[u % pairs.n];
+            const float w = resident ? pairs.w[0] : pairs.w[u % pairs.n];
             const uint32_t taddr = lane_base + (uint32_t)(buf * 128 + cg * 32);
 #pragma unroll
             for (int cc = 0; cc < 32; cc += 16) {
@@ -524,12 +561,23 @@ signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSo
     if ((rs = make_map(&mr, right.base, (long long)right.nslices * right.rows, right.cols, right.ld)) != SIGNTRI_OK)
         return rs;
     if (top.rows != bot.rows || left.rows != right.rows) return SIGNTRI_ERR_BAD_ARG;
+    // resident mode when every pair has the same weight and at most 3 slices
+    // per operand are involved (so that a stage of all slices fits twice)
+    int nsl = 0;
+    bool same_w = true;
+    for (int p = 0; p < pairs.n; p++) {
+        nsl = std::max(nsl, std::max(pairs.s[p], pairs.t[p]) + 1);
+        same_w = same_w && pairs.w[p] == pairs.w[0];
+    }
+    const int resident = (same_w && pairs.n > 1 && nsl <= 3 && nsl <= top.nslices && nsl <= bot.nslices &&
+                          nsl <= left.nslices && nsl <= right.nslices) ? 1 : 0;
     const size_t smem = tc_smem_bytes();
     SGT_CUDA_TRY(cudaFuncSetAttribute(tc_blocksum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     prof_add_flops(kernel_class, useful_flops);
     ProfScope ps(kernel_class, st);
     tc_blocksum_kernel<<<njobs, kTcThreads, smem, st>>>(mt, mb, ml, mr, top.rows, left.rows, d_jobs, d_pairs, chunk_kb,
-                                                        top.scale, bot.scale, left.scale, right.scale, out, qo, d_err);
+                                                        top.scale, bot.scale, left.scale, right.scale, out, qo, d_err,
+                                                        resident, nsl);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }

@@ -59,3 +59,31 @@ def test_mixed_fallback_to_fp64(gpu_lib, oracle_mod):
     assert info.variant == gpu_lib.Variant.PH_FP64
     assert info.refine_steps == 0
     assert relerr(U, oracle_mod.sign_tri(T)) <= 1e-11
+
+
+@pytest.mark.parametrize("pattern", ["blocks_of_one_sign", "alternating", "one_negative", "ragged_tail"])
+def test_mixed_gathered_residual_patterns(gpu_lib, oracle_mod, pattern):
+    # the first residual gathers indices per 1024-index superblock by sign;
+    # cover superblocks of one sign, every class boundary inside 64-blocks,
+    # a single negative index, and a ragged last superblock
+    n = {"ragged_tail": 2200}.get(pattern, 2600)
+    rng = np.random.default_rng(44)
+    T = np.triu(rng.standard_normal((n, n)) / np.sqrt(n), 1)
+    idx = np.arange(n)
+    if pattern == "blocks_of_one_sign":
+        s = np.where((idx // 1024) % 2 == 0, 1.0, -1.0)
+        s[2048:] = np.where(idx[2048:] % 3 == 0, -1.0, 1.0)
+    elif pattern == "alternating":
+        s = np.where(idx % 2 == 0, 1.0, -1.0)
+    elif pattern == "one_negative":
+        s = np.ones(n)
+        s[1500] = -1.0
+    else:
+        s = np.where(rng.random(n) < 0.3, -1.0, 1.0)
+    T[idx, idx] = s * rng.uniform(0.5, 2.0, n)
+    T = np.asfortranarray(T)
+    U, info = solve(gpu_lib, T, gpu_lib.Variant.PH_MIXED_TF32)
+    Uo = oracle_mod.sign_tri(T, schedule="antidiag")
+    assert relerr(U, Uo) <= TOL_MIXED, (pattern, relerr(U, Uo), info.as_dict())
+    assert info.variant == gpu_lib.Variant.PH_MIXED_TF32, info.as_dict()
+    assert max(info.resid_commute, info.resid_involution) <= 1e-13
