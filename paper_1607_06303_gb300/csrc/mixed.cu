@@ -56,8 +56,10 @@ namespace signtri {
 namespace {
 
 constexpr int MB = 64;
-constexpr int kLeafThreads = 256;
+constexpr int kLeafThreads = 512;
+
 constexpr int kTargetJobs = 2 * 152;
+constexpr int kLeafSub = kLeafThreads / MB;   // threads per entry in the wavefront
 constexpr int kOzakiSlices = 7;
 constexpr int kSuper = 1024;   // superblock of the gathered residual layout
 
@@ -166,9 +168,10 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
     }
     __syncthreads();
 
-    // wavefront: four threads per entry (strided partial sums, then a
-    // width-4 shuffle reduction); every thread runs the same control flow
-    const int grp = threadIdx.x >> 2, sub = threadIdx.x & 3;
+    // wavefront: kLeafSub threads per entry (strided partial sums, then a
+    // shuffle reduction within the group); every thread runs the same
+    // control flow
+    const int grp = threadIdx.x / kLeafSub, sub = threadIdx.x % kLeafSub;
     const int nsteps = MB + bj - 1;
     for (int st = 0; st < nsteps; st++) {
         const int plo = max(0, MB - 1 - st);
@@ -182,13 +185,14 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
         const float *Bm = opp ? TJ : AJ;
         float a = 0.f, b = 0.f;
         if (active) {
-            for (int k = pp + 1 + sub; k < MB; k += 4) a = fmaf(Am[pp + k * LD], Vs[k + q * LD], a);
-            for (int k = sub; k < q; k += 4) b = fmaf(Vs[pp + k * LD], Bm[k + q * LD], b);
+            for (int k = pp + 1 + sub; k < MB; k += kLeafSub) a = fmaf(Am[pp + k * LD], Vs[k + q * LD], a);
+            for (int k = sub; k < q; k += kLeafSub) b = fmaf(Vs[pp + k * LD], Bm[k + q * LD], b);
         }
-        a += __shfl_xor_sync(0xffffffffu, a, 1, 4);
-        b += __shfl_xor_sync(0xffffffffu, b, 1, 4);
-        a += __shfl_xor_sync(0xffffffffu, a, 2, 4);
-        b += __shfl_xor_sync(0xffffffffu, b, 2, 4);
+#pragma unroll
+        for (int o = 1; o < kLeafSub; o <<= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o, kLeafSub);
+            b += __shfl_xor_sync(0xffffffffu, b, o, kLeafSub);
+        }
         if (active && sub == 0) {
             float v;
             if (opp) v = (Cs[pp + q * LD] - a + b) / (TI[pp + pp * LD] - TJ[q + q * LD]);
