@@ -25,7 +25,10 @@
 //    entries (an ill-conditioned problem can meet its own recurrences long
 //    before the other equation).  The residuals
 //    come from exact 7-bit integer slices of the strictly upper parts of T and
-//    U0 (emulated float64 products, about 2^-45 relative to |T||U|) plus the
+//    U0 (seven slices, 28 pairs over K-chunks of 1024: emulated float64
+//    products, about 2^-45 relative to |T||U|; 8-bit slices would need 21
+//    pairs but K-chunks of 256, and the fourfold epilogue work costs more than
+//    the pairs save) plus the
 //    diagonal terms in float64:
 //      Rc_ij = (N_T N_U - N_U N_T)_ij + t_ii u_ij + t_ij u_jj - u_ii t_ij - u_ij t_jj
 //      Rs_ij = (N_U N_U)_ij + u_ii u_ij + u_ij u_jj.
@@ -60,7 +63,8 @@ constexpr int kLeafThreads = 512;
 
 constexpr int kTargetJobs = 2 * 152;
 constexpr int kLeafSub = kLeafThreads / MB;   // threads per entry in the wavefront
-constexpr int kOzakiSlices = 7;
+constexpr int kOzakiSlices = 7;   // exact slices of kOzakiBits bits: 49 bits, 28 pairs
+constexpr int kOzakiBits = 7;
 constexpr int kSuper = 1024;   // superblock of the gathered residual layout
 
 __device__ __forceinline__ float fsgn(double t) { return t > 0.0 ? 1.f : -1.f; }
@@ -508,8 +512,8 @@ P *take(Arena &ws, size_t count)
 signtri_status split_full(MixedCtx &c, const double *M, int ldm, __nv_bfloat16 *R, __nv_bfloat16 *C)
 {
     signtri_status rs;
-    if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, c.S, nullptr, R, c.np, c.np, c.st)) != SIGNTRI_OK) return rs;
-    return make_col_slices(c.n, c.n, M, ldm, 1, c.S, nullptr, C, c.np, c.np, c.st);
+    if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, c.S, 0, nullptr, R, c.np, c.np, c.st)) != SIGNTRI_OK) return rs;
+    return make_col_slices(c.n, c.n, M, ldm, 1, c.S, 0, nullptr, C, c.np, c.np, c.st);
 }
 
 // One low-precision sweep: MODE 0 solves for U (into V = U), MODE 1 for E.
@@ -653,7 +657,7 @@ signtri_status gathered_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bf
     signtri_status rs;
     if ((rs = make_scales(c.n, c.n, M, ldm, 1, true, c.np + 64, c.tmpmax, sR, c.st)) != SIGNTRI_OK) return rs;
     if ((rs = make_scales(c.n, c.n, M, ldm, 1, false, c.np + 64, c.tmpmax, sC, c.st)) != SIGNTRI_OK) return rs;
-    return make_gathered_slices(c.n, M, ldm, c.ginv, c.ng, kOzakiSlices, sR, sC, gR, gC, R, C, c.rows_g, c.rows_g,
+    return make_gathered_slices(c.n, M, ldm, c.ginv, c.ng, kOzakiSlices, kOzakiBits, sR, sC, gR, gC, R, C, c.rows_g, c.rows_g,
                                 c.st);
 }
 
@@ -664,9 +668,10 @@ signtri_status exact_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bfloa
     signtri_status rs;
     if ((rs = make_scales(c.n, c.n, M, ldm, 1, true, c.np + 64, c.tmpmax, sR, c.st)) != SIGNTRI_OK) return rs;
     if ((rs = make_scales(c.n, c.n, M, ldm, 1, false, c.np + 64, c.tmpmax, sC, c.st)) != SIGNTRI_OK) return rs;
-    if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, sR, R, c.np + 64, c.np, c.st)) != SIGNTRI_OK)
+    if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, kOzakiBits, sR, R, c.np + 64, c.np, c.st)) !=
+        SIGNTRI_OK)
         return rs;
-    return make_col_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, sC, C, c.np + 64, c.np, c.st);
+    return make_col_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, kOzakiBits, sC, C, c.np + 64, c.np, c.st);
 }
 
 signtri_status read_norms(MixedCtx &c)
@@ -693,13 +698,13 @@ signtri_status residual_needed(MixedCtx &c, const double *T, int ldt, const doub
     const TcJob *same = c.d_res_jobs, *opp = c.d_res_jobs + c.n_res_same;
     const double fl_same = tc_flops(c.pairs_oz.n, 1, 1) * c.res_kb_same;
     const double fl_opp = tc_flops(c.pairs_oz.n, 1, 1) * c.res_kb_opp;
-    rs = tc_blocksums(uR, uR, uC, uC, same, c.n_res_same, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qa, c.d_err,
+    rs = tc_blocksums(uR, uR, uC, uC, same, c.n_res_same, c.pairs_oz, c.d_pairs_oz, kExactChunkKb7, nullptr, qa, c.d_err,
                       SIGNTRI_KC_RESIDUAL, c.st, fl_same);
     if (rs != SIGNTRI_OK) return rs;
-    rs = tc_blocksums(tR, tR, uC, uC, opp, c.n_res_opp, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qa, c.d_err,
+    rs = tc_blocksums(tR, tR, uC, uC, opp, c.n_res_opp, c.pairs_oz, c.d_pairs_oz, kExactChunkKb7, nullptr, qa, c.d_err,
                       SIGNTRI_KC_RESIDUAL, c.st, fl_opp);
     if (rs != SIGNTRI_OK) return rs;
-    rs = tc_blocksums(uR, uR, tC, tC, opp, c.n_res_opp, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qb, c.d_err,
+    rs = tc_blocksums(uR, uR, tC, tC, opp, c.n_res_opp, c.pairs_oz, c.d_pairs_oz, kExactChunkKb7, nullptr, qb, c.d_err,
                       SIGNTRI_KC_RESIDUAL, c.st, fl_opp);
     if (rs != SIGNTRI_OK) return rs;
     SGT_CUDA_TRY(cudaMemsetAsync(c.norms, 0, 8 * sizeof(double), c.st));
@@ -731,13 +736,13 @@ signtri_status residual_full(MixedCtx &c, const double *T, int ldt, const double
     const TcQuadOut qtu{{Ptu, Ptu, Ptu, Ptu}, c.n, c.n, c.n};
     const TcQuadOut qut{{Put, Put, Put, Put}, c.n, c.n, c.n};
     const double fl = tc_flops(c.pairs_oz.n, 1, 1) * c.full_kb;
-    rs = tc_blocksums(uR, uR, uC, uC, c.d_full_jobs, c.n_full_jobs, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qs, c.d_err,
+    rs = tc_blocksums(uR, uR, uC, uC, c.d_full_jobs, c.n_full_jobs, c.pairs_oz, c.d_pairs_oz, kExactChunkKb7, nullptr, qs, c.d_err,
                       SIGNTRI_KC_RESIDUAL, c.st, fl);
     if (rs != SIGNTRI_OK) return rs;
-    rs = tc_blocksums(tR, tR, uC, uC, c.d_full_jobs, c.n_full_jobs, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qtu,
+    rs = tc_blocksums(tR, tR, uC, uC, c.d_full_jobs, c.n_full_jobs, c.pairs_oz, c.d_pairs_oz, kExactChunkKb7, nullptr, qtu,
                       c.d_err, SIGNTRI_KC_RESIDUAL, c.st, fl);
     if (rs != SIGNTRI_OK) return rs;
-    rs = tc_blocksums(uR, uR, tC, tC, c.d_full_jobs, c.n_full_jobs, c.pairs_oz, c.d_pairs_oz, 16, nullptr, qut,
+    rs = tc_blocksums(uR, uR, tC, tC, c.d_full_jobs, c.n_full_jobs, c.pairs_oz, c.d_pairs_oz, kExactChunkKb7, nullptr, qut,
                       c.d_err, SIGNTRI_KC_RESIDUAL, c.st, fl);
     if (rs != SIGNTRI_OK) return rs;
     SGT_CUDA_TRY(cudaMemsetAsync(c.norms, 0, 8 * sizeof(double), c.st));
@@ -803,7 +808,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
         !c.d_pairs_split || !c.d_pairs_oz)
         return SIGNTRI_ERR_NO_WORKSPACE;
     c.pairs_split = split_pairs(S);
-    c.pairs_oz = ozaki_pairs_impl(kOzakiSlices);
+    c.pairs_oz = ozaki_pairs_impl(kOzakiSlices, kOzakiBits);
     if (!c.sc.jobs.empty())
         SGT_CUDA_TRY(cudaMemcpyAsync(c.d_jobs, c.sc.jobs.data(), c.sc.jobs.size() * sizeof(TcJob),
                                      cudaMemcpyHostToDevice, st));

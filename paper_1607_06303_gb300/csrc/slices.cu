@@ -5,9 +5,11 @@
 //  * exact integer slices (error-free split in the style of Ozaki, Ogita,
 //    Oishi and Rump): with a power-of-two scale sigma_i >= max_k |m_ik| per row
 //    (or per column), r = m_ik / sigma_i in (-1, 1) is cut into S pieces of
-//    7 bits, q_s = trunc(128 r_s), r_{s+1} = 128 r_s - q_s, so that
-//    m_ik = sigma_i sum_s q_s 2^{-7(s+1)} + O(sigma_i 2^{-7S}); every q_s is an
-//    integer of magnitude <= 127, exact in bf16;
+//    b = 7 or 8 bits, q_s = trunc(2^b r_s), r_{s+1} = 2^b r_s - q_s, so that
+//    m_ik = sigma_i sum_s q_s 2^{-b(s+1)} + O(sigma_i 2^{-bS}); every q_s is an
+//    integer of magnitude below 2^b, exact in bf16 (8 significant bits), and
+//    a sum of 2^(24-2b) products q_a q_b (1024 for b = 7, 256 for b = 8) stays
+//    below 2^24, exact in fp32;
 //  * rounding splits: x_0 = bf16(m), x_1 = bf16(m - x_0), x_2 = bf16(m - x_0 - x_1)
 //    (unit scale), for products accurate to ~2^-8S.
 // Slices are stored K-contiguous: "row" slices R[s][i][k] of an m x k matrix
@@ -67,25 +69,27 @@ __global__ void pow2_scale_kernel(int n, const unsigned long long *__restrict__ 
     scale[i] = ldexpf(1.0f, e);
 }
 
-// Exact slices by integer arithmetic: |x| / scale < 1 written as the 56-bit
-// fixed-point integer F = trunc(|x| / scale * 2^56) (from the float64
-// significand and exponent, no rounding), digits q_s = bits [49-7s, 56-7s)
-// of F with the sign of x.  Same digits as repeated q_s = trunc(128 r),
-// r <- 128 r - q_s, without float64 arithmetic (slow on this part).
-__device__ __forceinline__ void exact_slices(double x, int scale_exp, int S, float *q)
+// Exact slices by integer arithmetic: |x| / scale < 1 written as the 64-bit
+// fixed-point integer F = trunc(|x| / scale * 2^64) (from the float64
+// significand and exponent, no rounding), digits q_s = bits
+// [64 - b(s+1), 64 - bs) of F with the sign of x.  Same digits as repeated
+// q_s = trunc(2^b r), r <- 2^b r - q_s, without float64 arithmetic (slow on
+// this part).  S b <= 64.
+__device__ __forceinline__ void exact_slices(double x, int scale_exp, int S, int b, float *q)
 {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     const int bexp = (int)((bits >> 52) & 0x7ff);
     unsigned long long F = 0;
     if (bexp != 0) {   // zero and subnormals (far below any scale used here) give 0
         const unsigned long long mant = (bits & 0xfffffffffffffull) | (1ull << 52);
-        // |x| = mant * 2^(bexp - 1075); F = |x| * 2^(56 - scale_exp)
-        const int sh = bexp - 1075 + 56 - scale_exp;   // <= 3 since |x| < 2^scale_exp
+        // |x| = mant * 2^(bexp - 1075); F = |x| * 2^(64 - scale_exp)
+        const int sh = bexp - 1075 + 64 - scale_exp;   // <= 11 since |x| < 2^scale_exp
         if (sh >= 0) F = mant << sh;
         else if (sh > -64) F = mant >> (-sh);
     }
     const float sgn = (bits >> 63) ? -1.f : 1.f;
-    for (int s = 0; s < S; s++) q[s] = sgn * (float)((F >> (49 - 7 * s)) & 127ull);
+    const unsigned long long mask = (1ull << b) - 1ull;
+    for (int s = 0; s < S; s++) q[s] = sgn * (float)((F >> (64 - b * (s + 1))) & mask);
 }
 
 // Rounding split of the fp32 value of x: x0 = bf16(x), x1 = bf16(x - x0), ...
@@ -102,7 +106,7 @@ __device__ __forceinline__ void round_slices(double x, int S, float *q)
 // Row slices of an m x k column-major matrix: R[s][i][kk] for i < m_pad,
 // kk < k_pad.  Tiled transpose through shared memory.  tri: 0 = all entries,
 // 1 = strictly upper (i < kk) only.  scale == nullptr: rounding split.
-__global__ void row_slices_kernel(int m, int k, const double *__restrict__ M, int ldm, int tri, int S,
+__global__ void row_slices_kernel(int m, int k, const double *__restrict__ M, int ldm, int tri, int S, int bits,
                                   const float *__restrict__ scale, __nv_bfloat16 *__restrict__ R, int rows_pad,
                                   int ldr)
 {
@@ -120,7 +124,7 @@ __global__ void row_slices_kernel(int m, int k, const double *__restrict__ M, in
         if (i >= rows_pad || kk >= ldr) continue;
         const double v = tile[y][threadIdx.x];
         float q[8];
-        if (scale) exact_slices(v, i < m ? ilogbf(scale[i]) : 0, S, q);
+        if (scale) exact_slices(v, i < m ? ilogbf(scale[i]) : 0, S, bits, q);
         else round_slices(v, S, q);
         for (int s = 0; s < S; s++) R[((size_t)s * rows_pad + i) * ldr + kk] = __float2bfloat16_rn(q[s]);
     }
@@ -128,7 +132,7 @@ __global__ void row_slices_kernel(int m, int k, const double *__restrict__ M, in
 
 // Column slices of a k x n column-major matrix: C[s][j][kk] (same order as
 // the source, no transpose).  tri: 1 = strictly upper (kk < j) only.
-__global__ void col_slices_kernel(int k, int n, const double *__restrict__ M, int ldm, int tri, int S,
+__global__ void col_slices_kernel(int k, int n, const double *__restrict__ M, int ldm, int tri, int S, int bits,
                                   const float *__restrict__ scale, __nv_bfloat16 *__restrict__ C, int rows_pad,
                                   int ldc)
 {
@@ -138,7 +142,7 @@ __global__ void col_slices_kernel(int k, int n, const double *__restrict__ M, in
     double v = 0.0;
     if (j < n && kk < k && (tri == 0 || kk < j)) v = SGT_AT(M, ldm, kk, j);
     float q[8];
-    if (scale) exact_slices(v, j < n ? ilogbf(scale[j]) : 0, S, q);
+    if (scale) exact_slices(v, j < n ? ilogbf(scale[j]) : 0, S, bits, q);
     else round_slices(v, S, q);
     for (int s = 0; s < S; s++) C[((size_t)s * rows_pad + j) * ldc + kk] = __float2bfloat16_rn(q[s]);
 }
@@ -149,7 +153,7 @@ __global__ void col_slices_kernel(int k, int n, const double *__restrict__ M, in
 // for every g < rows, h < ldr (padding and the lower part as zeros), with the
 // per-row scales already gathered (scale_g[g]).
 __global__ void row_slices_gathered_kernel(const double *__restrict__ M, int ldm, const int *__restrict__ inv,
-                                           int ng, int S, const float *__restrict__ scale_g,
+                                           int ng, int S, int bits, const float *__restrict__ scale_g,
                                            __nv_bfloat16 *__restrict__ R, int rows, int ldr)
 {
     __shared__ double tile[TS][TS + 1];
@@ -166,14 +170,14 @@ __global__ void row_slices_gathered_kernel(const double *__restrict__ M, int ldm
         const int g = g0 + y, h = h0 + threadIdx.x;
         if (g >= rows || h >= ldr) continue;
         float q[8];
-        exact_slices(tile[y][threadIdx.x], g < ng ? ilogbf(scale_g[g]) : 0, S, q);
+        exact_slices(tile[y][threadIdx.x], g < ng ? ilogbf(scale_g[g]) : 0, S, bits, q);
         for (int s = 0; s < S; s++) R[((size_t)s * rows + g) * ldr + h] = __float2bfloat16_rn(q[s]);
     }
 }
 
 // Column slices C[s][g][h] = slice s of M[inv[h], inv[g]] (column inv[g]).
 __global__ void col_slices_gathered_kernel(const double *__restrict__ M, int ldm, const int *__restrict__ inv,
-                                           int ng, int S, const float *__restrict__ scale_g,
+                                           int ng, int S, int bits, const float *__restrict__ scale_g,
                                            __nv_bfloat16 *__restrict__ C, int rows, int ldc)
 {
     const int g = blockIdx.y;
@@ -183,7 +187,7 @@ __global__ void col_slices_gathered_kernel(const double *__restrict__ M, int ldm
     double v = 0.0;
     if (j >= 0 && kk >= 0 && kk < j) v = SGT_AT(M, ldm, kk, j);
     float q[8];
-    exact_slices(v, g < ng ? ilogbf(scale_g[g]) : 0, S, q);
+    exact_slices(v, g < ng ? ilogbf(scale_g[g]) : 0, S, bits, q);
     for (int s = 0; s < S; s++) C[((size_t)s * rows + g) * ldc + h] = __float2bfloat16_rn(q[s]);
 }
 
@@ -230,33 +234,33 @@ signtri_status make_scales(int m, int k, const double *M, int ldm, int tri, bool
     return SIGNTRI_OK;
 }
 
-signtri_status make_row_slices(int m, int k, const double *M, int ldm, int tri, int S, const float *scale,
+signtri_status make_row_slices(int m, int k, const double *M, int ldm, int tri, int S, int bits, const float *scale,
                                __nv_bfloat16 *R, int rows_pad, int ldr, cudaStream_t st)
 {
-    if (S > 8) return SIGNTRI_ERR_BAD_ARG;
+    if (S > 8 || S * bits > 64) return SIGNTRI_ERR_BAD_ARG;
     dim3 grid((ldr + TS - 1) / TS, (rows_pad + TS - 1) / TS), block(TS, 8);
     ProfScope ps(SIGNTRI_KC_CONVERT, st);
-    row_slices_kernel<<<grid, block, 0, st>>>(m, k, M, ldm, tri, S, scale, R, rows_pad, ldr);
+    row_slices_kernel<<<grid, block, 0, st>>>(m, k, M, ldm, tri, S, bits, scale, R, rows_pad, ldr);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }
 
-signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, int S, const float *scale,
+signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, int S, int bits, const float *scale,
                                __nv_bfloat16 *C, int rows_pad, int ldc, cudaStream_t st)
 {
-    if (S > 8) return SIGNTRI_ERR_BAD_ARG;
+    if (S > 8 || S * bits > 64) return SIGNTRI_ERR_BAD_ARG;
     dim3 grid((ldc + 255) / 256, rows_pad);
     ProfScope ps(SIGNTRI_KC_CONVERT, st);
-    col_slices_kernel<<<grid, 256, 0, st>>>(k, n, M, ldm, tri, S, scale, C, rows_pad, ldc);
+    col_slices_kernel<<<grid, 256, 0, st>>>(k, n, M, ldm, tri, S, bits, scale, C, rows_pad, ldc);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }
 
-signtri_status make_gathered_slices(int n, const double *M, int ldm, const int *inv, int ng, int S,
+signtri_status make_gathered_slices(int n, const double *M, int ldm, const int *inv, int ng, int S, int bits,
                                     const float *sR, const float *sC, float *sRg, float *sCg, __nv_bfloat16 *R,
                                     __nv_bfloat16 *C, int rows, int ld, cudaStream_t st)
 {
-    if (S > 8) return SIGNTRI_ERR_BAD_ARG;
+    if (S > 8 || S * bits > 64) return SIGNTRI_ERR_BAD_ARG;
     (void)n;
     ProfScope ps(SIGNTRI_KC_CONVERT, st);
     gather_scales_kernel<<<(rows + 255) / 256, 256, 0, st>>>(rows, ng, inv, sR, sRg);
@@ -264,16 +268,17 @@ signtri_status make_gathered_slices(int n, const double *M, int ldm, const int *
     gather_scales_kernel<<<(rows + 255) / 256, 256, 0, st>>>(rows, ng, inv, sC, sCg);
     SGT_LAUNCH_CHECK();
     dim3 grid((ld + TS - 1) / TS, (rows + TS - 1) / TS), block(TS, 8);
-    row_slices_gathered_kernel<<<grid, block, 0, st>>>(M, ldm, inv, ng, S, sRg, R, rows, ld);
+    row_slices_gathered_kernel<<<grid, block, 0, st>>>(M, ldm, inv, ng, S, bits, sRg, R, rows, ld);
     SGT_LAUNCH_CHECK();
-    col_slices_gathered_kernel<<<dim3((ld + 255) / 256, rows), 256, 0, st>>>(M, ldm, inv, ng, S, sCg, C, rows, ld);
+    col_slices_gathered_kernel<<<dim3((ld + 255) / 256, rows), 256, 0, st>>>(M, ldm, inv, ng, S, bits, sCg, C, rows,
+                                                                              ld);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }
 
 // Exact-split pair list: slices s, t with s + t <= S - 1, weights
-// 2^{-7(s+t+2)}, in order of decreasing weight.
-TcPairs ozaki_pairs_impl(int S)
+// 2^{-b(s+t+2)} for slices of b bits, in order of decreasing weight.
+TcPairs ozaki_pairs_impl(int S, int bits)
 {
     TcPairs p;
     std::memset(&p, 0, sizeof(p));
@@ -281,7 +286,7 @@ TcPairs ozaki_pairs_impl(int S)
         for (int s = 0; s <= g; s++) {
             p.s[p.n] = s;
             p.t[p.n] = g - s;
-            p.w[p.n] = ldexpf(1.0f, -7 * (g + 2));
+            p.w[p.n] = ldexpf(1.0f, -bits * (g + 2));
             p.n++;
         }
     return p;
@@ -329,8 +334,8 @@ signtri_status emulated_gemm_run(int m, int n, int k, const double *A, int lda, 
     signtri_status rs;
     if ((rs = make_scales(m, k, A, lda, 0, true, mp, tmpa, sa, st)) != SIGNTRI_OK) return rs;
     if ((rs = make_scales(k, n, B, ldb, 0, false, np, tmpb, sb, st)) != SIGNTRI_OK) return rs;
-    if ((rs = make_row_slices(m, k, A, lda, 0, S, sa, AR, mp, kp, st)) != SIGNTRI_OK) return rs;
-    if ((rs = make_col_slices(k, n, B, ldb, 0, S, sb, BC, np, kp, st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_row_slices(m, k, A, lda, 0, S, 7, sa, AR, mp, kp, st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_col_slices(k, n, B, ldb, 0, S, 7, sb, BC, np, kp, st)) != SIGNTRI_OK) return rs;
     std::vector<TcJob> hj(njobs);
     for (int I = 0; I < ntI; I++)
         for (int J = 0; J < ntJ; J++) {
@@ -338,12 +343,13 @@ signtri_status emulated_gemm_run(int m, int n, int k, const double *A, int lda, 
             j.rt = I * 64; j.rb = I * 64; j.cl = J * 128; j.cr = J * 128 + 64;
             j.kb0 = 0; j.kb1 = kp / 64; j.slot = I * ntJ + J; j.pad = 0;
         }
-    const TcPairs pairs = ozaki_pairs_impl(S);
+    const TcPairs pairs = ozaki_pairs_impl(S, 7);
     SGT_CUDA_TRY(cudaMemcpyAsync(jobs, hj.data(), hj.size() * sizeof(TcJob), cudaMemcpyHostToDevice, st));
     SGT_CUDA_TRY(cudaMemcpyAsync(dp, &pairs, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
     TcSource top{AR, S, mp, kp, kp, sa}, left{BC, S, np, kp, kp, sb}, right{BC, S, np, kp, kp, sb};
     TcQuadOut none{{nullptr, nullptr, nullptr, nullptr}, 0, 0, 0};
-    rs = tc_blocksums(top, top, left, right, jobs, njobs, pairs, dp, 16, out, none, d_err, SIGNTRI_KC_RESIDUAL, st);
+    rs = tc_blocksums(top, top, left, right, jobs, njobs, pairs, dp, kExactChunkKb7, out, none, d_err, SIGNTRI_KC_RESIDUAL,
+                      st);
     if (rs != SIGNTRI_OK) return rs;
     {
         ProfScope ps(SIGNTRI_KC_OTHER, st);

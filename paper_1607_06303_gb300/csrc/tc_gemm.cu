@@ -13,9 +13,10 @@
 // weight(s,t) * A_s B_t.  Each (pair, K-chunk) unit is accumulated in fp32 in
 // TMEM (kind::f16, M = 128, N = 128) and then added into a double-float
 // (fp32 hi + fp32 lo) accumulator in the epilogue registers.  With integer
-// slices of 7 bits and K-chunks of at most 1024, every fp32 unit sum is an
-// integer below 2^24 and therefore exact, which makes the emulated product
-// accurate to the split (about 2^-48 relative to |A||B| with 7 slices).
+// slices of 7 bits and K-chunks of at most 1024 (8 bits, 256), every fp32
+// unit sum is an integer below 2^24 and therefore exact, which makes the
+// emulated product accurate to the split (about 2^-48 relative to |A||B|
+// with 7 slices of 7 bits or 6 of 8).
 //
 // Warp roles (576 threads): warp 0 issues TMA loads into a 3-stage ring of
 // two K-blocks per stage,

@@ -8,6 +8,11 @@
 namespace signtri {
 
 constexpr int kTcMaxPairs = 36;
+// K-blocks per unit for exact slice pairs of 8 bits (7 bits): 256 (1024)
+// products of magnitude below 2^16 (2^14) sum to less than 2^24, exact in
+// the fp32 accumulator
+constexpr int kExactChunkKb8 = 4;
+constexpr int kExactChunkKb7 = 16;
 
 // One CTA's work: rows [rt, rt+64) of the top source and [rb, rb+64) of the
 // bottom source form A; rows [cl, cl+64) of the left and [cr, cr+64) of the
@@ -55,20 +60,22 @@ struct TcQuadOut {
 
 size_t tc_smem_bytes();
 
-// Slice pair lists (slices.cu): exact integer slices of 7 bits (weights
-// 2^{-7(s+t+2)}) and rounding splits (unit weights), s + t <= S - 1.
-TcPairs ozaki_pairs_impl(int S);
+// Slice pair lists (slices.cu): exact integer slices of `bits` bits (weights
+// 2^{-bits(s+t+2)}) and rounding splits (unit weights), s + t <= S - 1.
+TcPairs ozaki_pairs_impl(int S, int bits);
 TcPairs split_pairs(int S);
-signtri_status make_row_slices(int m, int k, const double *M, int ldm, int tri, int S, const float *scale,
+// Row / column slices: exact integer slices of `bits` bits under the
+// power-of-two scales when scale != nullptr, else a rounding split.
+signtri_status make_row_slices(int m, int k, const double *M, int ldm, int tri, int S, int bits, const float *scale,
                                __nv_bfloat16 *R, int rows_pad, int ldr, cudaStream_t st);
-signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, int S, const float *scale,
+signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, int S, int bits, const float *scale,
                                __nv_bfloat16 *C, int rows_pad, int ldc, cudaStream_t st);
 
 // Exact slices of the strictly upper part of the n x n matrix M in a gathered
 // index space (inv[g] = original index at position g, -1 = padding, ng
 // positions used, `rows` allocated, pitch ld): per-row and per-column scales
 // sR, sC (original indices) are gathered into sRg, sCg.
-signtri_status make_gathered_slices(int n, const double *M, int ldm, const int *inv, int ng, int S,
+signtri_status make_gathered_slices(int n, const double *M, int ldm, const int *inv, int ng, int S, int bits,
                                     const float *sR, const float *sC, float *sRg, float *sCg, __nv_bfloat16 *R,
                                     __nv_bfloat16 *C, int rows, int ld, cudaStream_t st);
 
