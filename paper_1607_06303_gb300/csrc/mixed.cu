@@ -61,7 +61,6 @@ namespace {
 constexpr int MB = 64;
 constexpr int kLeafThreads = 512;
 
-constexpr int kTargetJobs = 2 * 152;
 constexpr int kLeafSub = kLeafThreads / MB;   // threads per entry in the wavefront
 constexpr int kOzakiSlices = 7;   // exact slices of kOzakiBits bits: 49 bits, 28 pairs
 constexpr int kOzakiBits = 7;
@@ -83,7 +82,8 @@ template <int MODE>
 __global__ void __launch_bounds__(kLeafThreads)
 mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restrict__ V, int ldv,
                   const double *__restrict__ U0, int ldu0, const double *__restrict__ Rc,
-                  const double *__restrict__ Rs, int ldr, int d, int nsplit, const double *__restrict__ PA,
+                  const double *__restrict__ Rs, int ldr, int d, const int2 *__restrict__ tslot,
+                  const double *__restrict__ PA,
                   const double *__restrict__ PB, __nv_bfloat16 *__restrict__ Vr, __nv_bfloat16 *__restrict__ Vc,
                   int S, int rows_pad, int ldsl)
 {
@@ -138,9 +138,10 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
         float x = 0.f, y = 0.f;
         const float2 *PA2 = reinterpret_cast<const float2 *>(PA);
         const float2 *PB2 = reinterpret_cast<const float2 *>(PB);
+        const int2 ts = tslot[I];   // this tile's partial slots: first, count
 #pragma unroll 4
-        for (int s = 0; s < nsplit; s++) {
-            const size_t e = ((size_t)I * nsplit + s) * 16384 + p + (size_t)q * 64;
+        for (int s = 0; s < ts.y; s++) {
+            const size_t e = ((size_t)ts.x + s) * 16384 + p + (size_t)q * 64;
             if (opp) {
                 const float2 tl = PA2[e], br = PA2[e + 3 * 4096];
                 x += (tl.x - br.x) + (tl.y - br.y);
@@ -398,12 +399,22 @@ __global__ void zero_kernel(size_t count, double *__restrict__ p)
 
 // ------------------------------------------------------------ host side ---
 
+// Block sums of one anti-diagonal, split evenly over kSweepCtas persistent
+// CTAs (the tiles' K-blocks in a row, cut into equal ranges; a CTA's range
+// may cross tile boundaries): CTA c's partial for tile t goes to slot c + t,
+// and tile t's partials are the slots first(t)+t .. last(t)+t (in K order).
+constexpr int kSweepCtas = 152;
+
 struct Schedule {
     int nb = 0;
     std::vector<int> job_off;   // per anti-diagonal d: first job index (d = 0..nb)
-    std::vector<int> nsplit;    // per anti-diagonal
+    std::vector<int> cta_off;   // concatenated per-diagonal CTA job ranges (local indices)
+    std::vector<int> cta_begin; // per d: first entry in cta_off
+    std::vector<int> nctas;     // per d: CTAs of the block-sum launch (0: none)
+    std::vector<int2> tslot;    // concatenated per-tile (first slot, count)
+    std::vector<int> tile_begin;// per d: first entry in tslot
     std::vector<TcJob> jobs;
-    int max_jobs = 0;
+    int max_jobs = 0;           // partial slots needed by one diagonal
 };
 
 void build_schedule(int n, Schedule &sc)
@@ -411,30 +422,51 @@ void build_schedule(int n, Schedule &sc)
     const int nb = (n + MB - 1) / MB;
     sc.nb = nb;
     sc.job_off.assign(nb + 1, 0);
-    sc.nsplit.assign(nb + 1, 0);
+    sc.cta_begin.assign(nb + 1, 0);
+    sc.nctas.assign(nb + 1, 0);
+    sc.tile_begin.assign(nb + 1, 0);
+    sc.cta_off.clear();
+    sc.tslot.clear();
     sc.jobs.clear();
     sc.max_jobs = 0;
     for (int d = 0; d <= nb; d++) {
         sc.job_off[d] = (int)sc.jobs.size();
-        if (d < 2 || d >= nb) continue;
-        const int ntiles = nb - d, kmax = d - 1;
-        int ns = std::max(1, std::min(kmax, (kTargetJobs + ntiles - 1) / ntiles));
-        const int kc = (kmax + ns - 1) / ns;
-        ns = (kmax + kc - 1) / kc;
-        sc.nsplit[d] = ns;
-        for (int I = 0; I < ntiles; I++) {
-            const int J = I + d;
-            for (int s = 0; s < ns; s++) {
+        sc.cta_begin[d] = (int)sc.cta_off.size();
+        sc.tile_begin[d] = (int)sc.tslot.size();
+        if (d < 1 || d >= nb) continue;
+        const int ntiles = nb - d;
+        const long long kmax = d - 1, W = (long long)ntiles * kmax;
+        if (W == 0) {
+            for (int t = 0; t < ntiles; t++) sc.tslot.push_back(make_int2(0, 0));
+            continue;
+        }
+        const int G = (int)std::min<long long>(kSweepCtas, W);
+        sc.nctas[d] = G;
+        const int base = (int)sc.jobs.size();
+        for (int c = 0; c < G; c++) {
+            sc.cta_off.push_back((int)sc.jobs.size() - base);
+            const long long x1 = (long long)(c + 1) * W / G;
+            for (long long x = (long long)c * W / G; x < x1;) {
+                const int t = (int)(x / kmax);
+                const long long t0 = (long long)t * kmax, xe = std::min(x1, t0 + kmax);
                 TcJob j;
-                j.rt = I * MB; j.rb = I * MB; j.cl = J * MB; j.cr = J * MB;
-                j.kb0 = I + 1 + s * kc;
-                j.kb1 = std::min(j.kb0 + kc, J);
-                j.slot = I * ns + s;
+                j.rt = t * MB; j.rb = t * MB; j.cl = (t + d) * MB; j.cr = (t + d) * MB;
+                j.kb0 = t + 1 + (int)(x - t0);
+                j.kb1 = t + 1 + (int)(xe - t0);
+                j.slot = c + t;
                 j.pad = 0;
                 sc.jobs.push_back(j);
+                x = xe;
             }
         }
-        sc.max_jobs = std::max(sc.max_jobs, ntiles * ns);
+        sc.cta_off.push_back((int)sc.jobs.size() - base);
+        for (int t = 0; t < ntiles; t++) {
+            // the CTA holding chunk x is ((x + 1) G - 1) / W (every CTA's range is non-empty)
+            const long long f = (((long long)t * kmax + 1) * G - 1) / W;
+            const long long l = (((long long)(t + 1) * kmax) * G - 1) / W;
+            sc.tslot.push_back(make_int2((int)(f + t), (int)(l - f + 1)));
+        }
+        sc.max_jobs = std::max(sc.max_jobs, G + ntiles);
     }
 }
 
@@ -444,6 +476,8 @@ struct MixedCtx {
     int *d_err;
     Schedule sc;
     TcJob *d_jobs;
+    int *d_cta_off;
+    int2 *d_tslot;
     TcPairs pairs_split, pairs_oz;
     TcPairs *d_pairs_split, *d_pairs_oz;
     // bf16 splits (S slices) of T and of the unknowns, row and column forms
@@ -490,7 +524,7 @@ size_t bytes_for(int n, int S)
     b += 4 * (np + 64) * 4 + (np + 64) * 8 + 6 * 256;                   // scales, tmp
     b += 4 * ngr * 4 + 4 * 256 + 2 * ngr * 4 + np + 3 * 256;            // gathered scales, maps, signs
     b += 2 * ngr * ngr * 8 + 2 * 256;                                   // RA, RB
-    const size_t maxjobs = (size_t)kTargetJobs + nb + 8;
+    const size_t maxjobs = (size_t)kSweepCtas + nb + 8;
     b += 2 * maxjobs * 16384 * 8 + 2 * 256;                             // partials
     b += 2 * (size_t)n * n * 8 + 2 * 256;                               // E, R (= Rs)
     b += 64 + 256;                                                      // norms
@@ -498,7 +532,9 @@ size_t bytes_for(int n, int S)
     b += pairs_max * pairs_max * sizeof(TcJob) + 256;                   // needed-residual jobs
     const size_t nbp = (nb + 1) / 2;
     b += nbp * (nbp + 1) / 2 * sizeof(TcJob) + 256;                     // full-residual jobs
-    b += nb * (size_t)(kTargetJobs + nb) * sizeof(TcJob) + 256;         // wavefront jobs (bound)
+    b += nb * (size_t)(kSweepCtas + nb) * sizeof(TcJob) + 256;          // wavefront jobs (bound)
+    b += nb * (size_t)(kSweepCtas + 1) * sizeof(int) + 256;              // per-CTA job ranges
+    b += (size_t)nb * nb * sizeof(int2) + 256;                           // per-tile partial slots
     b += 2 * sizeof(TcPairs) + 512;
     return b;
 }
@@ -538,6 +574,8 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
         const int ntiles = nb - d;
         const int njobs = c.sc.job_off[d + 1] - c.sc.job_off[d];
         const TcJob *jobs = c.d_jobs + c.sc.job_off[d];
+        const int *coff = c.d_cta_off + c.sc.cta_begin[d];
+        const int G = c.sc.nctas[d];
         const long long sum_kb = (long long)ntiles * (d - 1);
         signtri_status rs;
         if (njobs > 0) {
@@ -545,24 +583,25 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
                 // [U_I.; T_I.] x [T_.J | U_.J]: TL = U T, TR = U U, BR = T U
                 rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
                                   c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st,
-                                  tc_flops(c.pairs_split.n, sum_kb, 3));
+                                  tc_flops(c.pairs_split.n, sum_kb, 3), coff, G);
                 if (rs != SIGNTRI_OK) return rs;
             } else {
                 // X^E: [E_I.; T_I.] x [T_.J | E_.J]: TL = E T, BR = T E
                 rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
                                   c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st,
-                                  tc_flops(c.pairs_split.n, sum_kb, 2));
+                                  tc_flops(c.pairs_split.n, sum_kb, 2), coff, G);
                 if (rs != SIGNTRI_OK) return rs;
                 // Y^E: [U0_I.; E_I.] x [E_.J | U0_.J]: TL = U0 E, BR = E U0
                 rs = tc_blocksums(srcU_r, srcV_r, srcV_c, srcU_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
                                   c.PB, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st,
-                                  tc_flops(c.pairs_split.n, sum_kb, 2));
+                                  tc_flops(c.pairs_split.n, sum_kb, 2), coff, G);
                 if (rs != SIGNTRI_OK) return rs;
             }
         }
         ProfScope ps(MODE == 0 ? SIGNTRI_KC_OFFDIAG_LEAF_F32 : SIGNTRI_KC_CORRECTION, c.st);
         mixed_leaf_kernel<MODE><<<ntiles, kLeafThreads, leaf_smem, c.st>>>(
-            n, T, ldt, V, ldv, U0, ldu0, c.res_c, c.res_s, n, d, c.sc.nsplit[d], c.PA, c.PB, Vr, Vc, c.S, c.np, c.np);
+            n, T, ldt, V, ldv, U0, ldu0, c.res_c, c.res_s, n, d, c.d_tslot + c.sc.tile_begin[d], c.PA, c.PB, Vr, Vc,
+            c.S, c.np, c.np);
         SGT_LAUNCH_CHECK();
     }
     return SIGNTRI_OK;
@@ -798,6 +837,8 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     const size_t pairs_max = ngr / 128 + 2 * (size_t)((n + kSuper - 1) / kSuper) + 2;
     c.d_res_jobs = take<TcJob>(ws, pairs_max * pairs_max);
     c.d_jobs = take<TcJob>(ws, std::max<size_t>(c.sc.jobs.size(), 1));
+    c.d_cta_off = take<int>(ws, std::max<size_t>(c.sc.cta_off.size(), 1));
+    c.d_tslot = take<int2>(ws, std::max<size_t>(c.sc.tslot.size(), 1));
     c.d_pairs_split = take<TcPairs>(ws, 1);
     c.d_pairs_oz = take<TcPairs>(ws, 1);
     c.norms_host = norms_host;
@@ -805,12 +846,18 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
         !c.NUc || !c.d_full_jobs || !c.sTr ||
         !c.sTc || !c.sUr || !c.sUc || !c.gTr || !c.gTc || !c.gUr || !c.gUc || !c.gmap || !c.ginv || !c.pos ||
         !c.tmpmax || !c.PA || !c.PB || !c.E || !c.R || !c.RA || !c.RB || !c.norms || !c.d_res_jobs || !c.d_jobs ||
-        !c.d_pairs_split || !c.d_pairs_oz)
+        !c.d_pairs_split || !c.d_pairs_oz || !c.d_cta_off || !c.d_tslot)
         return SIGNTRI_ERR_NO_WORKSPACE;
     c.pairs_split = split_pairs(S);
     c.pairs_oz = ozaki_pairs_impl(kOzakiSlices, kOzakiBits);
     if (!c.sc.jobs.empty())
         SGT_CUDA_TRY(cudaMemcpyAsync(c.d_jobs, c.sc.jobs.data(), c.sc.jobs.size() * sizeof(TcJob),
+                                     cudaMemcpyHostToDevice, st));
+    if (!c.sc.cta_off.empty())
+        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_cta_off, c.sc.cta_off.data(), c.sc.cta_off.size() * sizeof(int),
+                                     cudaMemcpyHostToDevice, st));
+    if (!c.sc.tslot.empty())
+        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_tslot, c.sc.tslot.data(), c.sc.tslot.size() * sizeof(int2),
                                      cudaMemcpyHostToDevice, st));
     SGT_CUDA_TRY(cudaMemcpyAsync(c.d_pairs_split, &c.pairs_split, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
     SGT_CUDA_TRY(cudaMemcpyAsync(c.d_pairs_oz, &c.pairs_oz, sizeof(TcPairs), cudaMemcpyHostToDevice, st));

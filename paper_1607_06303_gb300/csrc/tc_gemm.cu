@@ -216,13 +216,25 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float a)
     lo = __fadd_rn(lo, err);
 }
 
+// Units of one job: (K-chunk, pair) in pair mode, K-chunks in resident mode.
+__device__ __forceinline__ int job_units(const TcJob &job, int chunk_kb, int npairs, int resident)
+{
+    const int nkb = job.kb1 - job.kb0;
+    const int nchunks = nkb > 0 ? (nkb + chunk_kb - 1) / chunk_kb : 0;
+    return resident ? nchunks : npairs * nchunks;
+}
+
+// A CTA runs jobs [job_off[b], job_off[b+1]) (job b alone when job_off is
+// null) back to back: the load ring, the MMA buffers and their barrier
+// phases run on across job boundaries, and the epilogue writes each job's
+// result after its last unit.
 __global__ void __launch_bounds__(kTcThreads, 1)
 tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_constant__ CUtensorMap mBot,
                    const __grid_constant__ CUtensorMap mLeft, const __grid_constant__ CUtensorMap mRight,
-                   int rowsA, int rowsB, const TcJob *__restrict__ jobs, const TcPairs *__restrict__ pairs_g, int chunk_kb,
-                   const float *__restrict__ sTop, const float *__restrict__ sBot, const float *__restrict__ sLeft,
-                   const float *__restrict__ sRight, double *__restrict__ out, TcQuadOut qo,
-                   int *__restrict__ err, int resident, int nsl)
+                   int rowsA, int rowsB, const TcJob *__restrict__ jobs, const int *__restrict__ job_off,
+                   const TcPairs *__restrict__ pairs_g, int chunk_kb, const float *__restrict__ sTop,
+                   const float *__restrict__ sBot, const float *__restrict__ sLeft, const float *__restrict__ sRight,
+                   double *__restrict__ out, TcQuadOut qo, int *__restrict__ err, int resident, int nsl)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -236,9 +248,8 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
     TcPairs *pairs_s = reinterpret_cast<TcPairs *>(smem + kStages * kStageBytes + 512);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const TcJob job = jobs[blockIdx.x];
-    const int nkb = job.kb1 - job.kb0;
-    const int nchunks = nkb > 0 ? (nkb + chunk_kb - 1) / chunk_kb : 0;
+    const int j0 = job_off ? job_off[blockIdx.x] : (int)blockIdx.x;
+    const int j1 = job_off ? job_off[blockIdx.x + 1] : (int)blockIdx.x + 1;
     for (int i = threadIdx.x; i < (int)(sizeof(TcPairs) / 4); i += blockDim.x)
         reinterpret_cast<int *>(pairs_s)[i] = reinterpret_cast<const int *>(pairs_g)[i];
     __syncthreads();
@@ -247,9 +258,10 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
     // slice pair.  Resident mode (unit-weight pairs of nsl slices): a stage
     // holds one K-block of all nsl slices of A and of B, every pair's MMAs
     // are issued from it into one accumulator, one unit per K-chunk.
-    const int nunits = resident ? nchunks : pairs.n * nchunks;
     const int sbytes = resident ? 2 * nsl * (kHalfBytes / 2) : kStageBytes;
     const int nring = resident ? min(kStages, (kStages * kStageBytes) / sbytes) : kStages;
+    long long total_units = 0;
+    for (int j = j0; j < j1; j++) total_units += job_units(jobs[j], chunk_kb, pairs.n, resident);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -269,7 +281,7 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
     const uint32_t tmem_base = *tmem_holder;
 
     if (warp == 0) {
-        if (lane == 0 && nunits > 0) {
+        if (lane == 0 && total_units > 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(&mTop) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(&mBot) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(&mLeft) : "memory");
@@ -278,43 +290,47 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
             uint32_t phase = 0;
             long long issued = 0;
             bool ok = true;
-            for (int u = 0; u < nunits && ok; u++) {
-                const int c = resident ? u : u / pairs.n, p = resident ? 0 : u % pairs.n;
-                // chunk-major: the pairs of one K-chunk reuse its panels in L2
-                const int kbs = job.kb0 + c * chunk_kb, kbe = min(kbs + chunk_kb, job.kb1);
-                const int step = resident ? 1 : kKPS;
-                for (int kb = kbs; kb < kbe; kb += step) {
-                    if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) { ok = false; break; }
-                    unsigned char *base = smem + stage * sbytes;
-                    if (resident) {
-                        // [A slice 0 | ... | A slice nsl-1 | B slice 0 | ...], 16 KB each
-                        mbar_expect_tx(&full[stage], 2 * nsl * (kHalfBytes / 2));
-                        const int x = kb * 64;
-                        for (int sl = 0; sl < nsl; sl++) {
-                            unsigned char *a = base + sl * (kHalfBytes / 2);
-                            unsigned char *b = base + (nsl + sl) * (kHalfBytes / 2);
-                            tma_load_2d(a, &mTop, &full[stage], x, sl * rowsA + job.rt);
-                            tma_load_2d(a + 8192, &mBot, &full[stage], x, sl * rowsA + job.rb);
-                            tma_load_2d(b, &mLeft, &full[stage], x, sl * rowsB + job.cl);
-                            tma_load_2d(b + 8192, &mRight, &full[stage], x, sl * rowsB + job.cr);
+            for (int j = j0; j < j1 && ok; j++) {
+                const TcJob job = jobs[j];
+                const int nu = job_units(job, chunk_kb, pairs.n, resident);
+                for (int u = 0; u < nu && ok; u++) {
+                    const int c = resident ? u : u / pairs.n, p = resident ? 0 : u % pairs.n;
+                    // chunk-major: the pairs of one K-chunk reuse its panels in L2
+                    const int kbs = job.kb0 + c * chunk_kb, kbe = min(kbs + chunk_kb, job.kb1);
+                    const int step = resident ? 1 : kKPS;
+                    for (int kb = kbs; kb < kbe; kb += step) {
+                        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) { ok = false; break; }
+                        unsigned char *base = smem + stage * sbytes;
+                        if (resident) {
+                            // [A slice 0 | ... | A slice nsl-1 | B slice 0 | ...], 16 KB each
+                            mbar_expect_tx(&full[stage], 2 * nsl * (kHalfBytes / 2));
+                            const int x = kb * 64;
+                            for (int sl = 0; sl < nsl; sl++) {
+                                unsigned char *a = base + sl * (kHalfBytes / 2);
+                                unsigned char *b = base + (nsl + sl) * (kHalfBytes / 2);
+                                tma_load_2d(a, &mTop, &full[stage], x, sl * rowsA + job.rt);
+                                tma_load_2d(a + 8192, &mBot, &full[stage], x, sl * rowsA + job.rb);
+                                tma_load_2d(b, &mLeft, &full[stage], x, sl * rowsB + job.cl);
+                                tma_load_2d(b + 8192, &mRight, &full[stage], x, sl * rowsB + job.cr);
+                            }
+                        } else {
+                            const int nk = min(kKPS, kbe - kb);
+                            const int ya = pairs.s[p] * rowsA, yb = pairs.t[p] * rowsB;
+                            mbar_expect_tx(&full[stage], nk * kHalfBytes);
+                            for (int h = 0; h < nk; h++) {
+                                // stage layout: A halves [h][top 8 KB | bottom 8 KB], then B halves
+                                unsigned char *a = base + h * (kHalfBytes / 2);
+                                unsigned char *b = base + kStageBytes / 2 + h * (kHalfBytes / 2);
+                                const int x = (kb + h) * 64;
+                                tma_load_2d(a, &mTop, &full[stage], x, ya + job.rt);
+                                tma_load_2d(a + 8192, &mBot, &full[stage], x, ya + job.rb);
+                                tma_load_2d(b, &mLeft, &full[stage], x, yb + job.cl);
+                                tma_load_2d(b + 8192, &mRight, &full[stage], x, yb + job.cr);
+                            }
                         }
-                    } else {
-                        const int nk = min(kKPS, kbe - kb);
-                        const int ya = pairs.s[p] * rowsA, yb = pairs.t[p] * rowsB;
-                        mbar_expect_tx(&full[stage], nk * kHalfBytes);
-                        for (int h = 0; h < nk; h++) {
-                            // stage layout: A halves [h][top 8 KB | bottom 8 KB], then B halves
-                            unsigned char *a = base + h * (kHalfBytes / 2);
-                            unsigned char *b = base + kStageBytes / 2 + h * (kHalfBytes / 2);
-                            const int x = (kb + h) * 64;
-                            tma_load_2d(a, &mTop, &full[stage], x, ya + job.rt);
-                            tma_load_2d(a + 8192, &mBot, &full[stage], x, ya + job.rb);
-                            tma_load_2d(b, &mLeft, &full[stage], x, yb + job.cl);
-                            tma_load_2d(b + 8192, &mRight, &full[stage], x, yb + job.cr);
-                        }
+                        issued++;
+                        if (++stage == nring) { stage = 0; phase ^= 1; }
                     }
-                    issued++;
-                    if (++stage == nring) { stage = 0; phase ^= 1; }
                 }
             }
             if (!ok) {
@@ -340,49 +356,54 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
             }
         }
     } else if (warp == 1) {
-        if (lane == 0 && nunits > 0) {
+        if (lane == 0 && total_units > 0) {
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
-            for (int u = 0; u < nunits && ok; u++) {
-                const int buf = u % kBufs;
-                const uint32_t tphase = (u / kBufs) & 1;
-                if (!mbar_wait(&tempty[buf], tphase ^ 1, abort_flag)) { ok = false; break; }
-                fence_after();
-                const uint32_t d = tmem_base + (uint32_t)(buf * 128);
-                const int c = resident ? u : u / pairs.n;
-                const int kbs = job.kb0 + c * chunk_kb, kbe = min(kbs + chunk_kb, job.kb1);
-                const int step = resident ? 1 : kKPS;
-                for (int kb = kbs; kb < kbe; kb += step) {
-                    if (!mbar_wait(&full[stage], phase, abort_flag)) { ok = false; break; }
+            int g = 0;   // unit index across jobs
+            for (int j = j0; j < j1 && ok; j++) {
+                const TcJob job = jobs[j];
+                const int nu = job_units(job, chunk_kb, pairs.n, resident);
+                for (int u = 0; u < nu && ok; u++, g++) {
+                    const int buf = g % kBufs;
+                    const uint32_t tphase = (uint32_t)((g / kBufs) & 1);
+                    if (!mbar_wait(&tempty[buf], tphase ^ 1, abort_flag)) { ok = false; break; }
                     fence_after();
-                    unsigned char *base = smem + stage * sbytes;
-                    if (resident) {
-                        for (int p = 0; p < pairs.n; p++) {
-                            const uint64_t ad = smem_desc(base + pairs.s[p] * (kHalfBytes / 2));
-                            const uint64_t bd = smem_desc(base + (nsl + pairs.t[p]) * (kHalfBytes / 2));
+                    const uint32_t d = tmem_base + (uint32_t)(buf * 128);
+                    const int c = resident ? u : u / pairs.n;
+                    const int kbs = job.kb0 + c * chunk_kb, kbe = min(kbs + chunk_kb, job.kb1);
+                    const int step = resident ? 1 : kKPS;
+                    for (int kb = kbs; kb < kbe; kb += step) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag)) { ok = false; break; }
+                        fence_after();
+                        unsigned char *base = smem + stage * sbytes;
+                        if (resident) {
+                            for (int p = 0; p < pairs.n; p++) {
+                                const uint64_t ad = smem_desc(base + pairs.s[p] * (kHalfBytes / 2));
+                                const uint64_t bd = smem_desc(base + (nsl + pairs.t[p]) * (kHalfBytes / 2));
 #pragma unroll
-                            for (int k = 0; k < 4; k++)
-                                mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k),
-                                         (kb > kbs || p > 0 || k > 0) ? 1u : 0u);
-                        }
-                    } else {
-                        const int nk = min(kKPS, kbe - kb);
-                        for (int h = 0; h < nk; h++) {
-                            unsigned char *a = base + h * (kHalfBytes / 2);
-                            unsigned char *b = base + kStageBytes / 2 + h * (kHalfBytes / 2);
-                            const uint64_t ad = smem_desc(a), bd = smem_desc(b);
+                                for (int k = 0; k < 4; k++)
+                                    mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k),
+                                             (kb > kbs || p > 0 || k > 0) ? 1u : 0u);
+                            }
+                        } else {
+                            const int nk = min(kKPS, kbe - kb);
+                            for (int h = 0; h < nk; h++) {
+                                unsigned char *a = base + h * (kHalfBytes / 2);
+                                unsigned char *b = base + kStageBytes / 2 + h * (kHalfBytes / 2);
+                                const uint64_t ad = smem_desc(a), bd = smem_desc(b);
 #pragma unroll
-                            for (int k = 0; k < 4; k++)
-                                mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k),
-                                         (kb > kbs || h > 0 || k > 0) ? 1u : 0u);
+                                for (int k = 0; k < 4; k++)
+                                    mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k),
+                                             (kb > kbs || h > 0 || k > 0) ? 1u : 0u);
+                            }
                         }
+                        mma_commit(&empty[stage]);
+                        if (++stage == nring) { stage = 0; phase ^= 1; }
                     }
-                    mma_commit(&empty[stage]);
-                    if (++stage == nring) { stage = 0; phase ^= 1; }
+                    if (!ok) break;
+                    mma_commit(&tfull[buf]);
                 }
-                if (!ok) break;
-                mma_commit(&tfull[buf]);
             }
             if (!ok) {
                 *abort_flag = 1;
@@ -394,59 +415,61 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
     } else {
         const int q = warp & 3;                 // TMEM lane quadrant this warp may read
         const int cg = (warp - 2) >> 2;         // 32-column group 0..3
-        float lo[32];
-#pragma unroll
-        for (int i = 0; i < 32; i++) lo[i] = 0.f;
         const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
         const uint32_t taddr_hi = lane_base + (uint32_t)(kBufs * 128 + cg * 32);
+        const int row = 32 * q + lane;
+        const int r = row & 63;
+        const bool bottom = row >= 64;
+        const int half = cg >> 1;
+        const int c0 = (cg & 1) * 32;           // first column inside the quadrant
+        const int quad = (bottom ? 2 : 0) + half;
+        const bool quad_mode = qo.m[0] || qo.m[1] || qo.m[2] || qo.m[3];
         bool ok = true;
-        for (int u = 0; u < nunits && ok; u++) {
-            const int buf = u % kBufs;
-            const uint32_t tphase = (u / kBufs) & 1;
-            if (!mbar_wait(&tfull[buf], tphase, abort_flag)) { ok = false; break; }
-            fence_after();
-            const float w = resident ? pairs.w[0] : pairs.w[u % pairs.n];
-            const uint32_t taddr = lane_base + (uint32_t)(buf * 128 + cg * 32);
+        int g = 0;   // unit index across jobs
+        for (int j = j0; j < j1 && ok; j++) {
+            const int nu = job_units(jobs[j], chunk_kb, pairs.n, resident);
+            float lo[32];
 #pragma unroll
-            for (int cc = 0; cc < 32; cc += 16) {
-                uint32_t rv[16], rh[16];
-                tmem_ld16_nowait(taddr + cc, rv);
-                if (u > 0) tmem_ld16_nowait(taddr_hi + cc, rh);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                float h[16];
-                if (u == 0) {
+            for (int i = 0; i < 32; i++) lo[i] = 0.f;
+            for (int u = 0; u < nu && ok; u++, g++) {
+                const int buf = g % kBufs;
+                const uint32_t tphase = (uint32_t)((g / kBufs) & 1);
+                if (!mbar_wait(&tfull[buf], tphase, abort_flag)) { ok = false; break; }
+                fence_after();
+                const float w = resident ? pairs.w[0] : pairs.w[u % pairs.n];
+                const uint32_t taddr = lane_base + (uint32_t)(buf * 128 + cg * 32);
 #pragma unroll
-                    for (int i = 0; i < 16; i++) h[i] = __fmul_rn(__uint_as_float(rv[i]), w);
-                } else {
+                for (int cc = 0; cc < 32; cc += 16) {
+                    uint32_t rv[16], rh[16];
+                    tmem_ld16_nowait(taddr + cc, rv);
+                    if (u > 0) tmem_ld16_nowait(taddr_hi + cc, rh);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    float h[16];
+                    if (u == 0) {
 #pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        h[i] = __uint_as_float(rh[i]);
-                        df_add(h[i], lo[cc + i], __fmul_rn(__uint_as_float(rv[i]), w));
+                        for (int i = 0; i < 16; i++) h[i] = __fmul_rn(__uint_as_float(rv[i]), w);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; i++) {
+                            h[i] = __uint_as_float(rh[i]);
+                            df_add(h[i], lo[cc + i], __fmul_rn(__uint_as_float(rv[i]), w));
+                        }
                     }
+                    tmem_st16(taddr_hi + cc, h);
                 }
-                tmem_st16(taddr_hi + cc, h);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
             }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[buf]);
-        }
-        if (!ok) {
-            *abort_flag = 1;
-            atomicExch(err, 1);
-        } else {
-            const int row = 32 * q + lane;
-            const int r = row & 63;
-            const bool bottom = row >= 64;
-            const int half = cg >> 1;
-            const int c0 = (cg & 1) * 32;           // first column inside the quadrant
+            if (!ok) break;
+            // this job's result
+            const TcJob job = jobs[j];
             double srow = 1.0;
             if (bottom) { if (sBot) srow = sBot[job.rb + r]; }
             else if (sTop) srow = sTop[job.rt + r];
             const float *scol = half ? sRight : sLeft;
             const int cbase = (half ? job.cr : job.cl) + c0;
-            const int quad = (bottom ? 2 : 0) + half;
-            const bool quad_mode = qo.m[0] || qo.m[1] || qo.m[2] || qo.m[3];
             double *o = nullptr;
             float2 *o2 = nullptr;
             if (quad_mode) {
@@ -465,7 +488,7 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
 #pragma unroll
             for (int cc = 0; cc < 32; cc += 8) {
                 float h[8];
-                if (nunits > 0) tmem_ld8(taddr_hi + cc, h);
+                if (nu > 0) tmem_ld8(taddr_hi + cc, h);
                 else {
 #pragma unroll
                     for (int i = 0; i < 8; i++) h[i] = 0.f;
@@ -480,6 +503,10 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
                 }
             }
         }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicExch(err, 1);
+        }
     }
 
     fence_before();
@@ -487,7 +514,7 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
     fence_after();
     if (warp == 1) {
         // done_bar completes once, when all MMAs of this CTA have finished
-        if (nunits > 0) {
+        if (total_units > 0) {
             const uint32_t a = smem_u32(done_bar);
             const long long t0 = clock64();
             while (clock64() - t0 < kWaitCycles) {
@@ -549,9 +576,10 @@ size_t tc_smem_bytes() { return (size_t)kStages * kStageBytes + 1024 + 512 + siz
 signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSource &left, const TcSource &right,
                             const TcJob *d_jobs, int njobs, const TcPairs &pairs, const TcPairs *d_pairs, int chunk_kb,
                             double *out, const TcQuadOut &qo, int *d_err, int kernel_class, cudaStream_t st,
-                            double useful_flops)
+                            double useful_flops, const int *d_job_off, int nctas)
 {
     if (njobs <= 0) return SIGNTRI_OK;
+    if (d_job_off && nctas <= 0) return SIGNTRI_ERR_BAD_ARG;
     if (pairs.n <= 0 || pairs.n > kTcMaxPairs || chunk_kb <= 0 || !d_pairs) return SIGNTRI_ERR_BAD_ARG;
     signtri_status rs = get_encoder();
     if (rs != SIGNTRI_OK) return rs;
@@ -576,9 +604,9 @@ signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSo
     SGT_CUDA_TRY(cudaFuncSetAttribute(tc_blocksum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     prof_add_flops(kernel_class, useful_flops);
     ProfScope ps(kernel_class, st);
-    tc_blocksum_kernel<<<njobs, kTcThreads, smem, st>>>(mt, mb, ml, mr, top.rows, left.rows, d_jobs, d_pairs, chunk_kb,
-                                                        top.scale, bot.scale, left.scale, right.scale, out, qo, d_err,
-                                                        resident, nsl);
+    tc_blocksum_kernel<<<d_job_off ? nctas : njobs, kTcThreads, smem, st>>>(
+        mt, mb, ml, mr, top.rows, left.rows, d_jobs, d_job_off, d_pairs, chunk_kb, top.scale, bot.scale, left.scale,
+        right.scale, out, qo, d_err, resident, nsl);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }

@@ -79,10 +79,12 @@ signtri_status make_gathered_slices(int n, const double *M, int ldm, const int *
                                     const float *sR, const float *sC, float *sRg, float *sCg, __nv_bfloat16 *R,
                                     __nv_bfloat16 *C, int rows, int ld, cudaStream_t st);
 
+// d_job_off (device, nctas + 1 entries): CTA b runs jobs [d_job_off[b],
+// d_job_off[b+1]) back to back; null: one CTA per job.
 signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSource &left, const TcSource &right,
                             const TcJob *d_jobs, int njobs, const TcPairs &pairs, const TcPairs *d_pairs, int chunk_kb,
                             double *out, const TcQuadOut &qo, int *d_err, int kernel_class, cudaStream_t st,
-                            double useful_flops = 0.0);
+                            double useful_flops = 0.0, const int *d_job_off = nullptr, int nctas = 0);
 
 // 2 * 64^3 flops per (slice pair, K-block, used quadrant)
 inline double tc_flops(int npairs, long long sum_kb, int quadrants)
