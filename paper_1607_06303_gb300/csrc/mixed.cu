@@ -493,7 +493,7 @@ struct MixedCtx {
     __nv_bfloat16 *NUr, *NUc;           // U, either layout (sized for the gathered one)
     float *sTr, *sTc, *sUr, *sUc;       // scales, original indices
     float *gTr, *gTc, *gUr, *gUc;       // scales, gathered
-    unsigned long long *tmpmax;
+    unsigned long long *tmpmax, *tmpmax2;
     double *PA, *PB;            // block-sum partials
     double *E;                  // correction
     // residual products: gathered RA, RB or full-layout Ptu -> Rc, Put (same
@@ -521,7 +521,7 @@ size_t bytes_for(int n, int S)
     const size_t ngr = (size_t)gathered_bound(n) + 64;
     b += 4 * (size_t)kOzakiSlices * ngr * ngr * 2 + 4 * 256;           // exact slices: T gathered, U
     b += 2 * (size_t)kOzakiSlices * (np + 64) * np * 2 + 2 * 256;      // exact slices: T original
-    b += 4 * (np + 64) * 4 + (np + 64) * 8 + 6 * 256;                   // scales, tmp
+    b += 4 * (np + 64) * 4 + 2 * (np + 64) * 8 + 7 * 256;               // scales, tmp
     b += 4 * ngr * 4 + 4 * 256 + 2 * ngr * 4 + np + 3 * 256;            // gathered scales, maps, signs
     b += 2 * ngr * ngr * 8 + 2 * 256;                                   // RA, RB
     const size_t maxjobs = (size_t)kSweepCtas + nb + 8;
@@ -689,24 +689,28 @@ signtri_status setup_gathered(MixedCtx &c, const double *T, int ldt)
     return SIGNTRI_OK;
 }
 
-// Exact slices of the strictly upper part of M (T or U) in the gathered layout.
+// Exact slices of the strictly upper part of M (T or U) in the gathered layout
+// (scales sR, sC computed here unless `scaled`).
 signtri_status gathered_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bfloat16 *R, __nv_bfloat16 *C,
-                                  float *sR, float *sC, float *gR, float *gC)
+                                  float *sR, float *sC, float *gR, float *gC, bool scaled = false)
 {
     signtri_status rs;
-    if ((rs = make_scales(c.n, c.n, M, ldm, 1, true, c.np + 64, c.tmpmax, sR, c.st)) != SIGNTRI_OK) return rs;
-    if ((rs = make_scales(c.n, c.n, M, ldm, 1, false, c.np + 64, c.tmpmax, sC, c.st)) != SIGNTRI_OK) return rs;
-    return make_gathered_slices(c.n, M, ldm, c.ginv, c.ng, kOzakiSlices, kOzakiBits, sR, sC, gR, gC, R, C, c.rows_g, c.rows_g,
-                                c.st);
+    if (!scaled &&
+        (rs = make_scales_both(c.n, M, ldm, 1, c.np + 64, c.tmpmax, c.tmpmax2, sR, sC, c.st)) != SIGNTRI_OK)
+        return rs;
+    return make_gathered_slices(c.n, M, ldm, c.ginv, c.ng, kOzakiSlices, kOzakiBits, sR, sC, gR, gC, R, C, c.rows_g,
+                                c.rows_g, c.st);
 }
 
-// Exact slices of the strictly upper part of M in the original layout.
+// Exact slices of the strictly upper part of M in the original layout (scales
+// computed here unless `scaled`).
 signtri_status exact_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bfloat16 *R, __nv_bfloat16 *C, float *sR,
-                               float *sC)
+                               float *sC, bool scaled = false)
 {
     signtri_status rs;
-    if ((rs = make_scales(c.n, c.n, M, ldm, 1, true, c.np + 64, c.tmpmax, sR, c.st)) != SIGNTRI_OK) return rs;
-    if ((rs = make_scales(c.n, c.n, M, ldm, 1, false, c.np + 64, c.tmpmax, sC, c.st)) != SIGNTRI_OK) return rs;
+    if (!scaled &&
+        (rs = make_scales_both(c.n, M, ldm, 1, c.np + 64, c.tmpmax, c.tmpmax2, sR, sC, c.st)) != SIGNTRI_OK)
+        return rs;
     if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, kOzakiBits, sR, R, c.np + 64, c.np, c.st)) !=
         SIGNTRI_OK)
         return rs;
@@ -826,6 +830,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     c.gTr = take<float>(ws, ngr); c.gTc = take<float>(ws, ngr); c.gUr = take<float>(ws, ngr); c.gUc = take<float>(ws, ngr);
     c.gmap = take<int>(ws, ngr); c.ginv = take<int>(ws, ngr); c.pos = take<unsigned char>(ws, np);
     c.tmpmax = take<unsigned long long>(ws, np + 64);
+    c.tmpmax2 = take<unsigned long long>(ws, np + 64);
     const size_t maxjobs = (size_t)std::max(c.sc.max_jobs, 1);
     c.PA = take<double>(ws, maxjobs * 16384); c.PB = take<double>(ws, maxjobs * 16384);
     c.E = take<double>(ws, (size_t)n * n); c.R = take<double>(ws, (size_t)n * n);
@@ -845,7 +850,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     if (!c.Tr || !c.Tc || !c.Ur || !c.Uc || !c.Er || !c.Ec || !c.NTgr || !c.NTgc || !c.NTr || !c.NTc || !c.NUr ||
         !c.NUc || !c.d_full_jobs || !c.sTr ||
         !c.sTc || !c.sUr || !c.sUc || !c.gTr || !c.gTc || !c.gUr || !c.gUc || !c.gmap || !c.ginv || !c.pos ||
-        !c.tmpmax || !c.PA || !c.PB || !c.E || !c.R || !c.RA || !c.RB || !c.norms || !c.d_res_jobs || !c.d_jobs ||
+        !c.tmpmax || !c.tmpmax2 || !c.PA || !c.PB || !c.E || !c.R || !c.RA || !c.RB || !c.norms || !c.d_res_jobs || !c.d_jobs ||
         !c.d_pairs_split || !c.d_pairs_oz || !c.d_cta_off || !c.d_tslot)
         return SIGNTRI_ERR_NO_WORKSPACE;
     c.pairs_split = split_pairs(S);
@@ -895,7 +900,8 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     signtri_status rs;
     if ((rs = split_full(c, T, ldt, c.Tr, c.Tc)) != SIGNTRI_OK) return rs;
     if ((rs = gathered_slices_of(c, T, ldt, c.NTgr, c.NTgc, c.sTr, c.sTc, c.gTr, c.gTc)) != SIGNTRI_OK) return rs;
-    if ((rs = exact_slices_of(c, T, ldt, c.NTr, c.NTc, c.sTr, c.sTc)) != SIGNTRI_OK) return rs;
+    // T's scales serve both layouts
+    if ((rs = exact_slices_of(c, T, ldt, c.NTr, c.NTc, c.sTr, c.sTc, true)) != SIGNTRI_OK) return rs;
 
     // 1. low-precision solve: diagonal blocks in float64, the rest by sweep
     if ((rs = launch_zero_strict_lower(n, U, ldu, st)) != SIGNTRI_OK) return rs;

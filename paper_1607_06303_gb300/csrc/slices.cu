@@ -55,6 +55,32 @@ __global__ void absmax_kernel(int m, int k, const double *__restrict__ M, int ld
     }
 }
 
+// Row and column maxima in one pass (square n x n, tri as above).
+__global__ void absmax_both_kernel(int n, const double *__restrict__ M, int ldm, int tri,
+                                   unsigned long long *__restrict__ out_rows, unsigned long long *__restrict__ out_cols)
+{
+    __shared__ double tile[TS][TS + 1];
+    const int i0 = blockIdx.y * TS, j0 = blockIdx.x * TS;
+    for (int y = threadIdx.y; y < TS; y += blockDim.y) {
+        const int i = i0 + threadIdx.x, j = j0 + y;
+        double v = 0.0;
+        if (i < n && j < n && (tri == 0 || i < j)) v = fabs(SGT_AT(M, ldm, i, j));
+        tile[threadIdx.x][y] = v;
+    }
+    __syncthreads();
+    if (threadIdx.y == 0) {
+        double best = 0.0;
+        for (int t = 0; t < TS; t++) best = fmax(best, tile[threadIdx.x][t]);
+        const int g = i0 + threadIdx.x;
+        if (best > 0.0 && g < n) atomicMax(&out_rows[g], (unsigned long long)__double_as_longlong(best));
+    } else if (threadIdx.y == 1) {
+        double best = 0.0;
+        for (int t = 0; t < TS; t++) best = fmax(best, tile[t][threadIdx.x]);
+        const int g = j0 + threadIdx.x;
+        if (best > 0.0 && g < n) atomicMax(&out_cols[g], (unsigned long long)__double_as_longlong(best));
+    }
+}
+
 // power-of-two scale 2^e with max < 2^e (frexp exponent); 1 for an all-zero line
 __global__ void pow2_scale_kernel(int n, const unsigned long long *__restrict__ maxbits, float *__restrict__ scale)
 {
@@ -104,47 +130,68 @@ __device__ __forceinline__ void round_slices(double x, int S, float *q)
 }
 
 // Row slices of an m x k column-major matrix: R[s][i][kk] for i < m_pad,
-// kk < k_pad.  Tiled transpose through shared memory.  tri: 0 = all entries,
-// 1 = strictly upper (i < kk) only.  scale == nullptr: rounding split.
+// kk < k_pad (ldr even).  Tiled transpose through shared memory, tiles of 32
+// rows x 64 columns, two adjacent columns per thread (bf16x2 stores).
+// tri: 0 = all entries, 1 = strictly upper (i < kk) only.  scale == nullptr:
+// rounding split.
 __global__ void row_slices_kernel(int m, int k, const double *__restrict__ M, int ldm, int tri, int S, int bits,
                                   const float *__restrict__ scale, __nv_bfloat16 *__restrict__ R, int rows_pad,
                                   int ldr)
 {
-    __shared__ double tile[TS][TS + 1];
-    const int i0 = blockIdx.y * TS, k0 = blockIdx.x * TS;
-    for (int y = threadIdx.y; y < TS; y += blockDim.y) {     // y: column offset
+    __shared__ double tile[2 * TS][TS + 1];   // [column][row]
+    const int i0 = blockIdx.y * TS, k0 = blockIdx.x * 2 * TS;
+    for (int y = threadIdx.y; y < 2 * TS; y += blockDim.y) {     // y: column offset
         const int kk = k0 + y, i = i0 + threadIdx.x;
         double v = 0.0;
         if (i < m && kk < k && (tri == 0 || i < kk)) v = SGT_AT(M, ldm, i, kk);
-        tile[threadIdx.x][y] = v;
+        tile[y][threadIdx.x] = v;
     }
     __syncthreads();
-    for (int y = threadIdx.y; y < TS; y += blockDim.y) {     // y: row offset
-        const int i = i0 + y, kk = k0 + threadIdx.x;
+    for (int y = threadIdx.y; y < TS; y += blockDim.y) {         // y: row offset
+        const int i = i0 + y, kk = k0 + 2 * threadIdx.x;
         if (i >= rows_pad || kk >= ldr) continue;
-        const double v = tile[y][threadIdx.x];
-        float q[8];
-        if (scale) exact_slices(v, i < m ? ilogbf(scale[i]) : 0, S, bits, q);
-        else round_slices(v, S, q);
-        for (int s = 0; s < S; s++) R[((size_t)s * rows_pad + i) * ldr + kk] = __float2bfloat16_rn(q[s]);
+        float q0[8], q1[8];
+        const int e = (scale && i < m) ? ilogbf(scale[i]) : 0;
+        if (scale) {
+            exact_slices(tile[2 * threadIdx.x][y], e, S, bits, q0);
+            exact_slices(tile[2 * threadIdx.x + 1][y], e, S, bits, q1);
+        } else {
+            round_slices(tile[2 * threadIdx.x][y], S, q0);
+            round_slices(tile[2 * threadIdx.x + 1][y], S, q1);
+        }
+        for (int s = 0; s < S; s++)
+            *reinterpret_cast<__nv_bfloat162 *>(&R[((size_t)s * rows_pad + i) * ldr + kk]) =
+                __floats2bfloat162_rn(q0[s], q1[s]);
     }
 }
 
 // Column slices of a k x n column-major matrix: C[s][j][kk] (same order as
-// the source, no transpose).  tri: 1 = strictly upper (kk < j) only.
+// the source, no transpose), two adjacent kk per thread (ldc even).
+// tri: 1 = strictly upper (kk < j) only.
 __global__ void col_slices_kernel(int k, int n, const double *__restrict__ M, int ldm, int tri, int S, int bits,
                                   const float *__restrict__ scale, __nv_bfloat16 *__restrict__ C, int rows_pad,
                                   int ldc)
 {
     const int j = blockIdx.y;
-    const int kk = blockIdx.x * blockDim.x + threadIdx.x;
+    const int kk = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (kk >= ldc) return;
-    double v = 0.0;
-    if (j < n && kk < k && (tri == 0 || kk < j)) v = SGT_AT(M, ldm, kk, j);
-    float q[8];
-    if (scale) exact_slices(v, j < n ? ilogbf(scale[j]) : 0, S, bits, q);
-    else round_slices(v, S, q);
-    for (int s = 0; s < S; s++) C[((size_t)s * rows_pad + j) * ldc + kk] = __float2bfloat16_rn(q[s]);
+    double v0 = 0.0, v1 = 0.0;
+    if (j < n) {
+        if (kk < k && (tri == 0 || kk < j)) v0 = SGT_AT(M, ldm, kk, j);
+        if (kk + 1 < k && (tri == 0 || kk + 1 < j)) v1 = SGT_AT(M, ldm, kk + 1, j);
+    }
+    float q0[8], q1[8];
+    if (scale) {
+        const int e = j < n ? ilogbf(scale[j]) : 0;
+        exact_slices(v0, e, S, bits, q0);
+        exact_slices(v1, e, S, bits, q1);
+    } else {
+        round_slices(v0, S, q0);
+        round_slices(v1, S, q1);
+    }
+    for (int s = 0; s < S; s++)
+        *reinterpret_cast<__nv_bfloat162 *>(&C[((size_t)s * rows_pad + j) * ldc + kk]) =
+            __floats2bfloat162_rn(q0[s], q1[s]);
 }
 
 // Gathered layout (residual products): position g of the gathered index
@@ -156,39 +203,50 @@ __global__ void row_slices_gathered_kernel(const double *__restrict__ M, int ldm
                                            int ng, int S, int bits, const float *__restrict__ scale_g,
                                            __nv_bfloat16 *__restrict__ R, int rows, int ldr)
 {
-    __shared__ double tile[TS][TS + 1];
-    const int g0 = blockIdx.y * TS, h0 = blockIdx.x * TS;
-    for (int y = threadIdx.y; y < TS; y += blockDim.y) {     // y: column offset
+    __shared__ double tile[2 * TS][TS + 1];   // [column][row]
+    const int g0 = blockIdx.y * TS, h0 = blockIdx.x * 2 * TS;
+    for (int y = threadIdx.y; y < 2 * TS; y += blockDim.y) {     // y: column offset
         const int h = h0 + y, g = g0 + threadIdx.x;
         const int i = g < ng ? inv[g] : -1, kk = h < ng ? inv[h] : -1;
         double v = 0.0;
         if (i >= 0 && kk >= 0 && i < kk) v = SGT_AT(M, ldm, i, kk);
-        tile[threadIdx.x][y] = v;
+        tile[y][threadIdx.x] = v;
     }
     __syncthreads();
-    for (int y = threadIdx.y; y < TS; y += blockDim.y) {     // y: row offset
-        const int g = g0 + y, h = h0 + threadIdx.x;
+    for (int y = threadIdx.y; y < TS; y += blockDim.y) {         // y: row offset
+        const int g = g0 + y, h = h0 + 2 * threadIdx.x;
         if (g >= rows || h >= ldr) continue;
-        float q[8];
-        exact_slices(tile[y][threadIdx.x], g < ng ? ilogbf(scale_g[g]) : 0, S, bits, q);
-        for (int s = 0; s < S; s++) R[((size_t)s * rows + g) * ldr + h] = __float2bfloat16_rn(q[s]);
+        const int e = g < ng ? ilogbf(scale_g[g]) : 0;
+        float q0[8], q1[8];
+        exact_slices(tile[2 * threadIdx.x][y], e, S, bits, q0);
+        exact_slices(tile[2 * threadIdx.x + 1][y], e, S, bits, q1);
+        for (int s = 0; s < S; s++)
+            *reinterpret_cast<__nv_bfloat162 *>(&R[((size_t)s * rows + g) * ldr + h]) =
+                __floats2bfloat162_rn(q0[s], q1[s]);
     }
 }
 
-// Column slices C[s][g][h] = slice s of M[inv[h], inv[g]] (column inv[g]).
+// Column slices C[s][g][h] = slice s of M[inv[h], inv[g]] (column inv[g]),
+// two adjacent h per thread.
 __global__ void col_slices_gathered_kernel(const double *__restrict__ M, int ldm, const int *__restrict__ inv,
                                            int ng, int S, int bits, const float *__restrict__ scale_g,
                                            __nv_bfloat16 *__restrict__ C, int rows, int ldc)
 {
     const int g = blockIdx.y;
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const int h = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (h >= ldc) return;
-    const int j = g < ng ? inv[g] : -1, kk = h < ng ? inv[h] : -1;
-    double v = 0.0;
-    if (j >= 0 && kk >= 0 && kk < j) v = SGT_AT(M, ldm, kk, j);
-    float q[8];
-    exact_slices(v, g < ng ? ilogbf(scale_g[g]) : 0, S, bits, q);
-    for (int s = 0; s < S; s++) C[((size_t)s * rows + g) * ldc + h] = __float2bfloat16_rn(q[s]);
+    const int j = g < ng ? inv[g] : -1;
+    const int k0 = h < ng ? inv[h] : -1, k1 = h + 1 < ng ? inv[h + 1] : -1;
+    double v0 = 0.0, v1 = 0.0;
+    if (j >= 0 && k0 >= 0 && k0 < j) v0 = SGT_AT(M, ldm, k0, j);
+    if (j >= 0 && k1 >= 0 && k1 < j) v1 = SGT_AT(M, ldm, k1, j);
+    const int e = g < ng ? ilogbf(scale_g[g]) : 0;
+    float q0[8], q1[8];
+    exact_slices(v0, e, S, bits, q0);
+    exact_slices(v1, e, S, bits, q1);
+    for (int s = 0; s < S; s++)
+        *reinterpret_cast<__nv_bfloat162 *>(&C[((size_t)s * rows + g) * ldc + h]) =
+            __floats2bfloat162_rn(q0[s], q1[s]);
 }
 
 // scale_g[g] = scale[inv[g]], 1 for padding
@@ -234,11 +292,28 @@ signtri_status make_scales(int m, int k, const double *M, int ldm, int tri, bool
     return SIGNTRI_OK;
 }
 
+signtri_status make_scales_both(int n, const double *M, int ldm, int tri, int nout, unsigned long long *tmp_rows,
+                                unsigned long long *tmp_cols, float *scale_rows, float *scale_cols, cudaStream_t st)
+{
+    SGT_CUDA_TRY(cudaMemsetAsync(tmp_rows, 0, (size_t)nout * sizeof(unsigned long long), st));
+    SGT_CUDA_TRY(cudaMemsetAsync(tmp_cols, 0, (size_t)nout * sizeof(unsigned long long), st));
+    ProfScope ps(SIGNTRI_KC_CONVERT, st);
+    dim3 grid((n + TS - 1) / TS, (n + TS - 1) / TS), block(TS, 8);
+    absmax_both_kernel<<<grid, block, 0, st>>>(n, M, ldm, tri, tmp_rows, tmp_cols);
+    SGT_LAUNCH_CHECK();
+    pow2_scale_kernel<<<(nout + 255) / 256, 256, 0, st>>>(nout, tmp_rows, scale_rows);
+    SGT_LAUNCH_CHECK();
+    pow2_scale_kernel<<<(nout + 255) / 256, 256, 0, st>>>(nout, tmp_cols, scale_cols);
+    SGT_LAUNCH_CHECK();
+    return SIGNTRI_OK;
+}
+
 signtri_status make_row_slices(int m, int k, const double *M, int ldm, int tri, int S, int bits, const float *scale,
                                __nv_bfloat16 *R, int rows_pad, int ldr, cudaStream_t st)
 {
     if (S > 8 || S * bits > 64) return SIGNTRI_ERR_BAD_ARG;
-    dim3 grid((ldr + TS - 1) / TS, (rows_pad + TS - 1) / TS), block(TS, 8);
+    if (ldr & 1) return SIGNTRI_ERR_BAD_ARG;
+    dim3 grid((ldr + 2 * TS - 1) / (2 * TS), (rows_pad + TS - 1) / TS), block(TS, 8);
     ProfScope ps(SIGNTRI_KC_CONVERT, st);
     row_slices_kernel<<<grid, block, 0, st>>>(m, k, M, ldm, tri, S, bits, scale, R, rows_pad, ldr);
     SGT_LAUNCH_CHECK();
@@ -249,7 +324,8 @@ signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, 
                                __nv_bfloat16 *C, int rows_pad, int ldc, cudaStream_t st)
 {
     if (S > 8 || S * bits > 64) return SIGNTRI_ERR_BAD_ARG;
-    dim3 grid((ldc + 255) / 256, rows_pad);
+    if (ldc & 1) return SIGNTRI_ERR_BAD_ARG;
+    dim3 grid((ldc / 2 + 255) / 256, rows_pad);
     ProfScope ps(SIGNTRI_KC_CONVERT, st);
     col_slices_kernel<<<grid, 256, 0, st>>>(k, n, M, ldm, tri, S, bits, scale, C, rows_pad, ldc);
     SGT_LAUNCH_CHECK();
@@ -267,11 +343,12 @@ signtri_status make_gathered_slices(int n, const double *M, int ldm, const int *
     SGT_LAUNCH_CHECK();
     gather_scales_kernel<<<(rows + 255) / 256, 256, 0, st>>>(rows, ng, inv, sC, sCg);
     SGT_LAUNCH_CHECK();
-    dim3 grid((ld + TS - 1) / TS, (rows + TS - 1) / TS), block(TS, 8);
+    if (ld & 1) return SIGNTRI_ERR_BAD_ARG;
+    dim3 grid((ld + 2 * TS - 1) / (2 * TS), (rows + TS - 1) / TS), block(TS, 8);
     row_slices_gathered_kernel<<<grid, block, 0, st>>>(M, ldm, inv, ng, S, bits, sRg, R, rows, ld);
     SGT_LAUNCH_CHECK();
-    col_slices_gathered_kernel<<<dim3((ld + 255) / 256, rows), 256, 0, st>>>(M, ldm, inv, ng, S, bits, sCg, C, rows,
-                                                                              ld);
+    col_slices_gathered_kernel<<<dim3((ld / 2 + 255) / 256, rows), 256, 0, st>>>(M, ldm, inv, ng, S, bits, sCg, C,
+                                                                                  rows, ld);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }

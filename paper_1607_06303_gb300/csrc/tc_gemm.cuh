@@ -71,6 +71,11 @@ signtri_status make_row_slices(int m, int k, const double *M, int ldm, int tri, 
 signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, int S, int bits, const float *scale,
                                __nv_bfloat16 *C, int rows_pad, int ldc, cudaStream_t st);
 
+// Power-of-two row and column scales of the n x n matrix M (tri = 1: its
+// strictly upper part) in one pass; tmp_rows, tmp_cols, scale_* hold nout.
+signtri_status make_scales_both(int n, const double *M, int ldm, int tri, int nout, unsigned long long *tmp_rows,
+                                unsigned long long *tmp_cols, float *scale_rows, float *scale_cols, cudaStream_t st);
+
 // Exact slices of the strictly upper part of the n x n matrix M in a gathered
 // index space (inv[g] = original index at position g, -1 = padding, ng
 // positions used, `rows` allocated, pitch ld): per-row and per-column scales
