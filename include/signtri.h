@@ -39,7 +39,7 @@ typedef enum {
        SIGNTRI_PH_FP64_EFFICIENT) or Parlett-Sylvester per input from the
        work estimates of Section 3 (inertia and swap count).  In
        sign_tri_batched, AUTO picks Parlett-Sylvester when no swaps are
-       needed and the batched Parlett-Higham otherwise. */
+       needed and the batched Parlett-Higham (efficient form) otherwise. */
     SIGNTRI_AUTO = 0,
     /* Recursive Parlett-Higham (Algorithms 3-6), float64 throughout; block
        sums in matrix-multiply form (both X and Y for every entry). */
@@ -162,8 +162,9 @@ signtri_status signtri_set_cutoff_table(const int *b, int len);
 signtri_status signtri_get_cutoff_table(int *b, int len);
 
 /* Autotuner: for n = 32, 64, ..., up to n_max (<= 32768), time the float64
-   Parlett-Higham path on a synthetic problem with each leaf size and store
-   the fastest in the cutoff table.  Allocates two n_max x n_max matrices. */
+   Parlett-Higham path AUTO takes (the arithmetic-efficient form) on a
+   synthetic problem with each leaf size and store the fastest in the cutoff
+   table.  Allocates two n_max x n_max matrices. */
 signtri_status signtri_autotune(int n_max, void *stream);
 
 /* Inertia scan alone (Section 3): counts of positive and negative diagonal

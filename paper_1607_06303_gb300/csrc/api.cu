@@ -399,8 +399,8 @@ signtri_status sign_tri_batched(int count, const int *n, const double *const *T,
         // in a batch Parlett-Higham shares its launches with every other
         // problem, so Parlett-Sylvester (run on its own) is taken only when
         // no swaps are needed
-        if (v == SIGNTRI_AUTO) run = (r.swaps == 0) ? SIGNTRI_PS_FP64 : SIGNTRI_PH_FP64;
-        if (run == SIGNTRI_PH_FP64) {
+        if (v == SIGNTRI_AUTO) run = (r.swaps == 0) ? SIGNTRI_PS_FP64 : SIGNTRI_PH_FP64_EFFICIENT;
+        if (run == SIGNTRI_PH_FP64 || run == SIGNTRI_PH_FP64_EFFICIENT) {
             ph_bs[k] = bs[k];
             which.push_back(k);
             diagv.push_back(0.0);      // zero the strictly lower part
@@ -414,7 +414,8 @@ signtri_status sign_tri_batched(int count, const int *n, const double *const *T,
         rs = launch_fill_batched((int)which.size(), d_descs, d_which, d_diag, st);
         if (rs != SIGNTRI_OK) return rs;
     }
-    rs = batched_ph_run(cnt, descs.data(), d_descs, ph_bs.data(), ws, st);
+    // the efficient form unless the matrix-multiply form was asked for
+    rs = batched_ph_run(cnt, descs.data(), d_descs, ph_bs.data(), v != SIGNTRI_PH_FP64, ws, st);
     if (rs != SIGNTRI_OK) return rs;
     for (auto &sv : singles) {
         const int k = sv.first;
@@ -474,7 +475,7 @@ signtri_status signtri_autotune(int n_max, void *stream)
             float ms = 0.f;
             for (int rep = 0; rep < 2 && rs == SIGNTRI_OK; rep++) {
                 cudaEventRecord(e0, st);
-                rs = run_variant(nn, T, nn, U, nn, SIGNTRI_PH_FP64, r, st, *s);
+                rs = run_variant(nn, T, nn, U, nn, SIGNTRI_PH_FP64_EFFICIENT, r, st, *s);
                 cudaEventRecord(e1, st);
                 if (cudaEventSynchronize(e1) != cudaSuccess) rs = SIGNTRI_ERR_CUDA;
                 cudaEventElapsedTime(&ms, e0, e1);

@@ -53,6 +53,31 @@ batched_gemm_kernel(const BatchDesc *__restrict__ mats, const int *__restrict__ 
                     PY + (size_t)t.slot * B * B);
 }
 
+// arithmetic-efficient form: per-matrix sign permutations at perm + poff[m],
+// positive counts at npos + noff[m]
+template <int B>
+__global__ void __launch_bounds__(kThreads)
+batched_gemm_split_kernel(const BatchDesc *__restrict__ mats, const int *__restrict__ members,
+                          const GemmTask *__restrict__ tasks, const short *__restrict__ perm,
+                          const int *__restrict__ npos, const int *__restrict__ poff, const int *__restrict__ noff,
+                          double *__restrict__ PZ)
+{
+    const GemmTask t = tasks[blockIdx.x];
+    const BatchDesc M = mats[members[t.m]];
+    ph_gemm_split_body<B>(M.n, M.T, M.ldt, M.U, M.ldu, t.I, t.J, t.kb0 * B, t.kb1 * B, perm + poff[t.m],
+                          npos + noff[t.m], PZ + (size_t)t.slot * B * B);
+}
+
+template <int B>
+__global__ void batched_perm_kernel(const BatchDesc *__restrict__ mats, const int *__restrict__ members,
+                                    const DiagTask *__restrict__ tasks, short *__restrict__ perm,
+                                    int *__restrict__ npos, const int *__restrict__ poff, const int *__restrict__ noff)
+{
+    const DiagTask t = tasks[blockIdx.x];
+    const BatchDesc M = mats[members[t.m]];
+    sign_perm_body<B>(M.n, M.T, M.ldt, t.blk, perm + poff[t.m], npos + noff[t.m]);
+}
+
 template <int B>
 __global__ void __launch_bounds__(kThreads)
 batched_leaf_kernel(const BatchDesc *__restrict__ mats, const int *__restrict__ members,
@@ -69,8 +94,10 @@ struct Plan {
     std::vector<GemmTask> gemm;
     std::vector<LeafTask> leaf;
     std::vector<int> gemm_off, leaf_off;   // per level d (size nbmax + 1)
+    std::vector<int> poff, noff;           // per member: sign permutation and count offsets
     int nbmax = 0;
     size_t max_slots = 0;
+    size_t perm_len = 0, npos_len = 0;
 };
 
 // members: indices (into the batch) of the matrices of this group
@@ -79,10 +106,16 @@ void make_plan(const std::vector<int> &ns, int B, Plan &p)
     const int cnt = (int)ns.size();
     std::vector<int> nb(cnt);
     p.nbmax = 0;
+    p.poff.assign(cnt, 0);
+    p.noff.assign(cnt, 0);
     for (int k = 0; k < cnt; k++) {
         nb[k] = (ns[k] + B - 1) / B;
         p.nbmax = std::max(p.nbmax, nb[k]);
         for (int b = 0; b < nb[k]; b++) p.diag.push_back({k, b});
+        p.poff[k] = (int)p.perm_len;
+        p.noff[k] = (int)p.npos_len;
+        p.perm_len += (size_t)nb[k] * B;
+        p.npos_len += (size_t)nb[k];
     }
     p.gemm_off.assign(p.nbmax + 1, 0);
     p.leaf_off.assign(p.nbmax + 1, 0);
@@ -120,12 +153,13 @@ void make_plan(const std::vector<int> &ns, int B, Plan &p)
 size_t plan_bytes(const Plan &p, int B)
 {
     return p.diag.size() * sizeof(DiagTask) + p.gemm.size() * sizeof(GemmTask) + p.leaf.size() * sizeof(LeafTask) +
-           2 * std::max<size_t>(p.max_slots, 1) * B * B * sizeof(double) + 8 * 256;
+           2 * std::max<size_t>(p.max_slots, 1) * B * B * sizeof(double) + p.perm_len * sizeof(short) +
+           p.npos_len * sizeof(int) + 2 * p.poff.size() * sizeof(int) + 12 * 256;
 }
 
 template <int B>
 signtri_status run_group(const BatchDesc *d_mats, const std::vector<int> &members, const std::vector<int> &ns,
-                         Arena &ws, cudaStream_t st)
+                         bool split, Arena &ws, cudaStream_t st)
 {
     Plan p;
     make_plan(ns, B, p);
@@ -135,8 +169,20 @@ signtri_status run_group(const BatchDesc *d_mats, const std::vector<int> &member
     auto *d_leaf = static_cast<LeafTask *>(ws.take(std::max<size_t>(p.leaf.size(), 1) * sizeof(LeafTask)));
     const size_t slots = std::max<size_t>(p.max_slots, 1);
     double *PX = static_cast<double *>(ws.take(slots * B * B * sizeof(double)));
-    double *PY = static_cast<double *>(ws.take(slots * B * B * sizeof(double)));
+    // the efficient form keeps one sum per entry: X and Y share the slabs
+    double *PY = split ? PX : static_cast<double *>(ws.take(slots * B * B * sizeof(double)));
     if (!d_members || !d_diag || !d_gemm || !d_leaf || !PX || !PY) return SIGNTRI_ERR_NO_WORKSPACE;
+    short *d_perm = nullptr;
+    int *d_npos = nullptr, *d_poff = nullptr, *d_noff = nullptr;
+    if (split) {
+        d_perm = static_cast<short *>(ws.take(std::max<size_t>(p.perm_len, 1) * sizeof(short)));
+        d_npos = static_cast<int *>(ws.take(std::max<size_t>(p.npos_len, 1) * sizeof(int)));
+        d_poff = static_cast<int *>(ws.take(p.poff.size() * sizeof(int)));
+        d_noff = static_cast<int *>(ws.take(p.noff.size() * sizeof(int)));
+        if (!d_perm || !d_npos || !d_poff || !d_noff) return SIGNTRI_ERR_NO_WORKSPACE;
+        SGT_CUDA_TRY(cudaMemcpyAsync(d_poff, p.poff.data(), p.poff.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        SGT_CUDA_TRY(cudaMemcpyAsync(d_noff, p.noff.data(), p.noff.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
     SGT_CUDA_TRY(cudaMemcpyAsync(d_members, members.data(), members.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     SGT_CUDA_TRY(cudaMemcpyAsync(d_diag, p.diag.data(), p.diag.size() * sizeof(DiagTask), cudaMemcpyHostToDevice, st));
     if (!p.gemm.empty())
@@ -156,13 +202,22 @@ signtri_status run_group(const BatchDesc *d_mats, const std::vector<int> &member
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rs = SIGNTRI_ERR_CUDA;
     if (rs == SIGNTRI_OK) {
         prof_pause(true);
+        if (split) {
+            batched_perm_kernel<B><<<(unsigned)p.diag.size(), B, 0, cs>>>(d_mats, d_members, d_diag, d_perm, d_npos,
+                                                                          d_poff, d_noff);
+            prof_count(SIGNTRI_KC_DIAG_LEAF, 1);
+        }
         batched_diag_kernel<B><<<(unsigned)p.diag.size(), kThreads, diag_smem<B>(), cs>>>(d_mats, d_members, d_diag);
         prof_count(SIGNTRI_KC_DIAG_LEAF, 1);
         for (int d = 1; d < p.nbmax; d++) {
             const int g0 = p.gemm_off[d], g1 = p.gemm_off[d + 1];
             const int l0 = p.leaf_off[d], l1 = p.leaf_off[d + 1];
             if (g1 > g0) {
-                batched_gemm_kernel<B><<<g1 - g0, kThreads, 0, cs>>>(d_mats, d_members, d_gemm + g0, PX, PY);
+                if (split)
+                    batched_gemm_split_kernel<B><<<g1 - g0, kThreads, 0, cs>>>(d_mats, d_members, d_gemm + g0, d_perm,
+                                                                               d_npos, d_poff, d_noff, PX);
+                else
+                    batched_gemm_kernel<B><<<g1 - g0, kThreads, 0, cs>>>(d_mats, d_members, d_gemm + g0, PX, PY);
                 prof_count(SIGNTRI_KC_BLOCK_SUMS_F64, 1);
             }
             if (l1 > l0) {
@@ -201,7 +256,7 @@ size_t batched_workspace_bytes(int count, const int *n, int B)
 // bs[m]: leaf size of matrix m (16, 32 or 64); matrices with bs[m] == 0 are
 // skipped (handled elsewhere).
 signtri_status batched_ph_run(int count, const BatchDesc *h_mats, const BatchDesc *d_mats, const int *bs,
-                              Arena &ws, cudaStream_t st)
+                              bool split, Arena &ws, cudaStream_t st)
 {
     for (int B : {16, 32, 64}) {
         std::vector<int> members, ns;
@@ -214,9 +269,9 @@ signtri_status batched_ph_run(int count, const BatchDesc *h_mats, const BatchDes
         Arena sub = ws;     // each group reuses the workspace after the previous one finished
         signtri_status rs;
         switch (B) {
-        case 16: rs = run_group<16>(d_mats, members, ns, sub, st); break;
-        case 32: rs = run_group<32>(d_mats, members, ns, sub, st); break;
-        default: rs = run_group<64>(d_mats, members, ns, sub, st); break;
+        case 16: rs = run_group<16>(d_mats, members, ns, split, sub, st); break;
+        case 32: rs = run_group<32>(d_mats, members, ns, split, sub, st); break;
+        default: rs = run_group<64>(d_mats, members, ns, split, sub, st); break;
         }
         if (rs != SIGNTRI_OK) return rs;
     }

@@ -117,7 +117,7 @@ signtri_status emulated_gemm_run(int m, int n, int k, const double *A, int lda, 
 // Batched float64 Parlett-Higham (batched.cu)
 size_t batched_workspace_bytes(int count, const int *n, int cutoff_for_all);
 signtri_status batched_ph_run(int count, const BatchDesc *h_mats, const BatchDesc *d_mats, const int *bs,
-                              Arena &ws, cudaStream_t st);
+                              bool split, Arena &ws, cudaStream_t st);
 
 // Bounded-wait self-test (tc_gemm.cu)
 signtri_status wait_selftest(int arrive, long long limit, int *d_err, cudaStream_t st);

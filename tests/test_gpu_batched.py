@@ -41,7 +41,7 @@ def batch_inputs():
     return Ts
 
 
-@pytest.mark.parametrize("variant", ["AUTO", "PH_FP64"])
+@pytest.mark.parametrize("variant", ["AUTO", "PH_FP64", "PH_FP64_EFFICIENT"])
 def test_batched_vs_oracle(gpu_lib, oracle_mod, variant):
     Ts = batch_inputs()
     assert len(Ts) > 15
