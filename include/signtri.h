@@ -86,11 +86,9 @@ typedef struct {
     double work_ps;         /* Section 3 flop estimate, Parlett-Sylvester */
     int cutoff;             /* leaf (block) size used by Parlett-Higham */
     int refine_steps;       /* refinement steps taken (mixed variants) */
-    double resid_commute;   /* ||TU-UT||_F / (||T||_F ||U||_F) after the last step,
-                               over the entries with t_ii, t_jj of opposite sign
-                               (those whose Algorithm 3 recurrence is TU = UT) */
-    double resid_involution;/* ||U^2-I||_F / ||U||_F^2 after the last step, over the
-                               entries with t_ii, t_jj of equal sign (recurrence U^2 = I) */
+    double resid_commute;   /* ||TU-UT||_F / (||T||_F ||U||_F) after the last step
+                               (mixed variants; see signtri_set_verification) */
+    double resid_involution;/* ||U^2-I||_F / ||U||_F^2 after the last step */
     int bad_index;          /* first offending diagonal index on ZERO/NONFINITE, else -1 */
 } signtri_info;
 
@@ -120,6 +118,21 @@ signtri_status signtri_set_rates(double gemm_flops_per_s, double givens_flops_pe
    (max_steps < 0: 3 for SIGNTRI_PH_MIXED_TF32, 8 for SIGNTRI_PH_MIXED_BF16).
    Process-wide setting. */
 signtri_status signtri_set_refinement(double tol, int max_steps);
+
+/* How the mixed variants accept a refinement step (process-wide).  Both
+   residuals, TU-UT and U^2-I, over all entries must be <= tol:
+   full = 1: formed entry by entry (three emulated-float64 n x n products);
+   full = 0 (default): estimated from 128 random +-1 probe vectors Z,
+     ||R||_F^2 ~ ||R Z||_F^2 / 128 (an unbiased estimate for any R; for a
+     residual 10x above tol the estimate falls below tol with probability
+     below 1e-9 by Maurer's bound for sums of nonnegative variables, with
+     E||Rz||^4 <= 3 ||R||_F^4 for +-1 vectors), with R Z = T(UZ) - U(TZ) and
+     U(UZ) - Z from emulated-float64 n x n by n x 128 products.  resid_commute / resid_involution then report
+     the estimate.
+   Corrections are driven by the needed residuals either way (Rc where the
+   signs of t_ii, t_jj differ, Rs where they agree).  Other values of full
+   return SIGNTRI_ERR_BAD_ARG. */
+signtri_status signtri_set_verification(int full);
 
 /* Leaf (recursion cutoff) size b of Parlett-Higham: the order of the diagonal
    and off-diagonal blocks solved element by element (Section 6 uses 16).

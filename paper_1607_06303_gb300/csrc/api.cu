@@ -50,6 +50,7 @@ double g_rate_givens = kDefaultGivensRate;
 constexpr double kDefaultMixedTol = 1e-13;
 double g_mixed_tol = kDefaultMixedTol;
 int g_mixed_max_steps = -1;   // < 0: per-variant default
+int g_mixed_verify_full = 0;  // 1: accept on the full residuals, 0: on their probe estimate
 thread_local signtri_info g_info;
 
 bool valid_variant(int v) { return v >= SIGNTRI_AUTO && v <= SIGNTRI_PH_FP64_EFFICIENT; }
@@ -188,7 +189,8 @@ signtri_status run_variant(int n, const double *T, int ldt, double *U, int ldu, 
     case SIGNTRI_PH_MIXED_TF32:
     case SIGNTRI_PH_MIXED_BF16: {
         const int S = (v == SIGNTRI_PH_MIXED_TF32) ? 3 : 1;
-        MixedParams prm{g_mixed_tol, g_mixed_max_steps >= 0 ? g_mixed_max_steps : (S == 3 ? 3 : 8), 10.0};
+        MixedParams prm{g_mixed_tol, g_mixed_max_steps >= 0 ? g_mixed_max_steps : (S == 3 ? 3 : 8), 10.0,
+                        g_mixed_verify_full};
         MixedReport rep{};
         SGT_CUDA_TRY(cudaMemsetAsync(s.err_dev, 0, sizeof(int), st));
         rs = mixed_run(n, T, ldt, U, ldu, S, prm, rep, ws, s.err_dev, s.norms_host, st);
@@ -514,6 +516,14 @@ signtri_status signtri_set_refinement(double tol, int max_steps)
     std::lock_guard<std::mutex> lk(g_mu);
     g_mixed_tol = tol > 0 ? tol : kDefaultMixedTol;
     g_mixed_max_steps = max_steps;
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_set_verification(int full)
+{
+    if (full != 0 && full != 1) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_mixed_verify_full = full;
     return SIGNTRI_OK;
 }
 

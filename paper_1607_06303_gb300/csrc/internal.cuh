@@ -127,6 +127,7 @@ struct MixedParams {
     double tol;              // stopping test on both relative residuals
     int max_steps;           // refinement steps before falling back
     double min_contraction;  // required reduction of the residual per step
+    int verify_full;         // 1: accept on the full residuals, 0: on the probe estimate
 };
 struct MixedReport {
     int steps;

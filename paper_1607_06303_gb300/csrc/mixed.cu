@@ -391,6 +391,89 @@ __global__ void apply_correction_kernel(int n, double *__restrict__ U, int ldu, 
     if (threadIdx.x == 0) atomicAdd(&norms[4], red[0]);
 }
 
+// ---------------------------------------------------------- probe check ---
+// Acceptance test by random probes: for Z (n x kProbes) with independent +-1
+// entries, E ||R Z||_F^2 = kProbes ||R||_F^2 for any R, so
+// ||R Z||_F / sqrt(kProbes) estimates ||R||_F.  R Z = T (U Z) - U (T Z) and
+// U (U Z) - Z are formed with the emulated-float64 products of the full
+// residual (n x n by n x kProbes), about 2^-45 |T||U| entrywise.
+constexpr int kProbes = 128;
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
+{
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+// Z[i + j n] = +-1 (bit of a counter hash), its one bf16 column slice
+// Zc[j][i] = +-64 with column scale 2 (+-1 = 2 * 64 * 2^-7 exactly), zero
+// padding up to np.
+__global__ void probe_kernel(int n, int np, unsigned long long seed, double *__restrict__ Z,
+                             __nv_bfloat16 *__restrict__ Zc, float *__restrict__ zscale)
+{
+    const int j = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+        float z = 0.f;
+        if (i < n) {
+            z = (splitmix64(seed ^ ((unsigned long long)j << 32 ^ (unsigned long long)i)) >> 63) ? -1.f : 1.f;
+            Z[(size_t)i + (size_t)j * n] = (double)z;
+        }
+        Zc[(size_t)j * np + i] = __float2bfloat16_rn(64.f * z);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) zscale[j] = 2.f;
+}
+
+// W = Pa + Pb + diag(M) Y  (n x kProbes, column-major, ld n)
+__global__ void probe_combine_kernel(int n, const double *__restrict__ Pa, const double *__restrict__ Pb,
+                                     const double *__restrict__ M, int ldm, const double *__restrict__ Y,
+                                     double *__restrict__ W)
+{
+    const int j = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const size_t e = (size_t)i + (size_t)j * n;
+        W[e] = Pa[e] + Pb[e] + SGT_AT(M, ldm, i, i) * Y[e];
+    }
+}
+
+// R_c Z = N_T W1 + diag(T) W1 - N_U W2 - diag(U) W2 and R_s Z = N_U W1 +
+// diag(U) W1 - Z, squared norms into norms[0], norms[1] (each product as two
+// K halves a, b).
+__global__ void probe_residual_kernel(int n, const double *__restrict__ T, int ldt, const double *__restrict__ U,
+                                      int ldu, const double *__restrict__ Z, const double *__restrict__ W1,
+                                      const double *__restrict__ W2, const double *__restrict__ P1a,
+                                      const double *__restrict__ P1b, const double *__restrict__ P2a,
+                                      const double *__restrict__ P2b, const double *__restrict__ P3a,
+                                      const double *__restrict__ P3b, double *__restrict__ norms)
+{
+    const int j = blockIdx.y;
+    double nc = 0.0, ns = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const size_t e = (size_t)i + (size_t)j * n;
+        const double tii = SGT_AT(T, ldt, i, i), uii = SGT_AT(U, ldu, i, i);
+        const double rc = (P1a[e] + P1b[e]) + tii * W1[e] - (P2a[e] + P2b[e]) - uii * W2[e];
+        const double rs = (P3a[e] + P3b[e]) + uii * W1[e] - Z[e];
+        nc += rc * rc;
+        ns += rs * rs;
+    }
+    __shared__ double red[2][256];
+    red[0][threadIdx.x] = nc;
+    red[1][threadIdx.x] = ns;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + off];
+            red[1][threadIdx.x] += red[1][threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&norms[0], red[0][0]);
+        atomicAdd(&norms[1], red[1][0]);
+    }
+}
+
 __global__ void zero_kernel(size_t count, double *__restrict__ p)
 {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
@@ -501,6 +584,17 @@ struct MixedCtx {
     double *RA, *RB, *R;
     const double *res_c, *res_s;   // what the last residual left for the correction
     double *norms, *norms_host; // [0] Rc^2 [1] Rs^2 [2] T^2 [3] U^2 [4] E^2
+    // probe check: Z, its slice and scale, W1 = U Z, W2 = T Z and their
+    // slices and scales, the product halves, the jobs (row pairs x K halves)
+    double *Z, *W1, *W2, *Pp;
+    __nv_bfloat16 *Zc, *W1c, *W2c;
+    float *zscale, *w1scale, *w2scale;
+    TcJob *d_probe_jobs;
+    int n_probe_jobs;
+    double probe_kb;
+    TcPairs pairs_z;            // (s, 0): Z has one slice
+    TcPairs *d_pairs_z;
+    double nT2, nU2;            // squared norms of T and U from the last needed residual
     TcJob *d_full_jobs;         // full residual: 2 x 2 block jobs
     int n_full_jobs;
     double full_kb;             // sum over full jobs of used quadrants x K-blocks
@@ -535,7 +629,10 @@ size_t bytes_for(int n, int S)
     b += nb * (size_t)(kSweepCtas + nb) * sizeof(TcJob) + 256;          // wavefront jobs (bound)
     b += nb * (size_t)(kSweepCtas + 1) * sizeof(int) + 256;              // per-CTA job ranges
     b += (size_t)nb * nb * sizeof(int2) + 256;                           // per-tile partial slots
-    b += 2 * sizeof(TcPairs) + 512;
+    b += 3 * sizeof(TcPairs) + 768;
+    b += 13 * (size_t)n * kProbes * 8 + 4 * 256;                       // probe Z, W1, W2, product halves
+    b += (1 + 2 * (size_t)kOzakiSlices) * kProbes * np * 2 + 3 * 256;  // their slices
+    b += 3 * kProbes * 4 + (2 * nbp + 2) * sizeof(TcJob) + 4 * 256;     // scales, probe jobs
     return b;
 }
 
@@ -758,7 +855,10 @@ signtri_status residual_needed(MixedCtx &c, const double *T, int ldt, const doub
     }
     c.res_c = c.R;
     c.res_s = c.R;
-    return read_norms(c);
+    if ((rs = read_norms(c)) != SIGNTRI_OK) return rs;
+    c.nT2 = c.norms_host[2];
+    c.nU2 = c.norms_host[3];
+    return SIGNTRI_OK;
 }
 
 // Both residuals of U over all entries (Rc into RA's memory, Rs into R) and
@@ -796,7 +896,91 @@ signtri_status residual_full(MixedCtx &c, const double *T, int ldt, const double
     }
     c.res_c = Ptu;
     c.res_s = Rs;
-    return read_norms(c);
+    if ((rs = read_norms(c)) != SIGNTRI_OK) return rs;
+    c.nT2 = c.norms_host[2];
+    c.nU2 = c.norms_host[3];
+    return SIGNTRI_OK;
+}
+
+// Probe estimate of both residuals of U over all entries, into
+// c.norms_host[0], [1] (squared, scaled to ||R||_F^2), with [2], [3] the
+// squared norms of T and of U from the last needed residual (U moved by the
+// correction only, ~1e-8 relative: immaterial for the test).
+// Products n x n by n x kProbes, jobs = row pairs x two K halves (longest
+// first), each half into its own buffer.
+signtri_status probe_check(MixedCtx &c, const double *T, int ldt, const double *U, int ldu, unsigned long long seed)
+{
+    const int n = c.n, np = c.np;
+    signtri_status rs;
+    if ((rs = make_scales(n, n, U, ldu, 1, true, np + 64, c.tmpmax, c.sUr, c.st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_row_slices(n, n, U, ldu, 1, kOzakiSlices, kOzakiBits, c.sUr, c.NUr, np + 64, np, c.st)) !=
+        SIGNTRI_OK)
+        return rs;
+    const size_t blk = (size_t)n * kProbes;
+    double *P[10];
+    for (int i = 0; i < 10; i++) P[i] = c.Pp + i * blk;
+    {
+        ProfScope ps(SIGNTRI_KC_RESIDUAL_SUM, c.st);
+        probe_kernel<<<dim3(std::min((np + 255) / 256, 64), kProbes), 256, 0, c.st>>>(n, np, seed, c.Z, c.Zc,
+                                                                                      c.zscale);
+        SGT_LAUNCH_CHECK();
+    }
+    const int R = np + 64;
+    const TcSource uR{c.NUr, kOzakiSlices, R, np, np, c.sUr}, tR{c.NTr, kOzakiSlices, R, np, np, c.sTr};
+    const TcSource zC{c.Zc, 1, kProbes, np, np, c.zscale};
+    const TcSource w1C{c.W1c, kOzakiSlices, kProbes, np, np, c.w1scale}, w2C{c.W2c, kOzakiSlices, kProbes, np, np,
+                                                                              c.w2scale};
+    auto out = [&](double *m) { return TcQuadOut{{m, m, m, m}, n, n, kProbes, blk}; };
+    const double flz = tc_flops(c.pairs_z.n, 1, 1) * c.probe_kb, flw = tc_flops(c.pairs_oz.n, 1, 1) * c.probe_kb;
+    // W1 = U Z, W2 = T Z (Z: one slice, pairs (s, 0))
+    if ((rs = tc_blocksums(uR, uR, zC, zC, c.d_probe_jobs, c.n_probe_jobs, c.pairs_z, c.d_pairs_z, kExactChunkKb7,
+                           nullptr, out(P[0]), c.d_err, SIGNTRI_KC_RESIDUAL, c.st, flz)) != SIGNTRI_OK)
+        return rs;
+    if ((rs = tc_blocksums(tR, tR, zC, zC, c.d_probe_jobs, c.n_probe_jobs, c.pairs_z, c.d_pairs_z, kExactChunkKb7,
+                           nullptr, out(P[2]), c.d_err, SIGNTRI_KC_RESIDUAL, c.st, flz)) != SIGNTRI_OK)
+        return rs;
+    {
+        ProfScope ps(SIGNTRI_KC_RESIDUAL_SUM, c.st);
+        const dim3 g(std::min((n + 255) / 256, 64), kProbes);
+        probe_combine_kernel<<<g, 256, 0, c.st>>>(n, P[0], P[1], U, ldu, c.Z, c.W1);
+        SGT_LAUNCH_CHECK();
+        probe_combine_kernel<<<g, 256, 0, c.st>>>(n, P[2], P[3], T, ldt, c.Z, c.W2);
+        SGT_LAUNCH_CHECK();
+    }
+    if ((rs = make_scales(n, kProbes, c.W1, n, 0, false, kProbes, c.tmpmax, c.w1scale, c.st)) != SIGNTRI_OK)
+        return rs;
+    if ((rs = make_scales(n, kProbes, c.W2, n, 0, false, kProbes, c.tmpmax, c.w2scale, c.st)) != SIGNTRI_OK)
+        return rs;
+    if ((rs = make_col_slices(n, kProbes, c.W1, n, 0, kOzakiSlices, kOzakiBits, c.w1scale, c.W1c, kProbes, np,
+                              c.st)) != SIGNTRI_OK)
+        return rs;
+    if ((rs = make_col_slices(n, kProbes, c.W2, n, 0, kOzakiSlices, kOzakiBits, c.w2scale, c.W2c, kProbes, np,
+                              c.st)) != SIGNTRI_OK)
+        return rs;
+    // N_T W1, N_U W2, N_U W1
+    if ((rs = tc_blocksums(tR, tR, w1C, w1C, c.d_probe_jobs, c.n_probe_jobs, c.pairs_oz, c.d_pairs_oz, kExactChunkKb7,
+                           nullptr, out(P[4]), c.d_err, SIGNTRI_KC_RESIDUAL, c.st, flw)) != SIGNTRI_OK)
+        return rs;
+    if ((rs = tc_blocksums(uR, uR, w2C, w2C, c.d_probe_jobs, c.n_probe_jobs, c.pairs_oz, c.d_pairs_oz, kExactChunkKb7,
+                           nullptr, out(P[6]), c.d_err, SIGNTRI_KC_RESIDUAL, c.st, flw)) != SIGNTRI_OK)
+        return rs;
+    if ((rs = tc_blocksums(uR, uR, w1C, w1C, c.d_probe_jobs, c.n_probe_jobs, c.pairs_oz, c.d_pairs_oz, kExactChunkKb7,
+                           nullptr, out(P[8]), c.d_err, SIGNTRI_KC_RESIDUAL, c.st, flw)) != SIGNTRI_OK)
+        return rs;
+    SGT_CUDA_TRY(cudaMemsetAsync(c.norms, 0, 2 * sizeof(double), c.st));
+    {
+        ProfScope ps(SIGNTRI_KC_RESIDUAL_SUM, c.st);
+        probe_residual_kernel<<<dim3(std::min((n + 255) / 256, 64), kProbes), 256, 0, c.st>>>(
+            n, T, ldt, U, ldu, c.Z, c.W1, c.W2, P[4], P[5], P[6], P[7], P[8], P[9], c.norms);
+        SGT_LAUNCH_CHECK();
+    }
+    SGT_CUDA_TRY(cudaMemcpyAsync(c.norms_host, c.norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(c.st));
+    c.norms_host[0] /= kProbes;
+    c.norms_host[1] /= kProbes;
+    c.norms_host[2] = c.nT2;
+    c.norms_host[3] = c.nU2;
+    return SIGNTRI_OK;
 }
 
 }  // namespace
@@ -846,6 +1030,20 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     c.d_tslot = take<int2>(ws, std::max<size_t>(c.sc.tslot.size(), 1));
     c.d_pairs_split = take<TcPairs>(ws, 1);
     c.d_pairs_oz = take<TcPairs>(ws, 1);
+    c.d_pairs_z = take<TcPairs>(ws, 1);
+    {
+        const size_t blk = (size_t)n * kProbes;
+        c.Z = take<double>(ws, blk); c.W1 = take<double>(ws, blk); c.W2 = take<double>(ws, blk);
+        c.Pp = take<double>(ws, 10 * blk);
+        c.Zc = take<__nv_bfloat16>(ws, (size_t)kProbes * np);
+        c.W1c = take<__nv_bfloat16>(ws, (size_t)kOzakiSlices * kProbes * np);
+        c.W2c = take<__nv_bfloat16>(ws, (size_t)kOzakiSlices * kProbes * np);
+        c.zscale = take<float>(ws, kProbes); c.w1scale = take<float>(ws, kProbes); c.w2scale = take<float>(ws, kProbes);
+        c.d_probe_jobs = take<TcJob>(ws, (size_t)2 * nbp + 2);
+        if (!c.Z || !c.W1 || !c.W2 || !c.Pp || !c.Zc || !c.W1c || !c.W2c || !c.zscale || !c.w1scale || !c.w2scale ||
+            !c.d_probe_jobs || !c.d_pairs_z)
+            return SIGNTRI_ERR_NO_WORKSPACE;
+    }
     c.norms_host = norms_host;
     if (!c.Tr || !c.Tc || !c.Ur || !c.Uc || !c.Er || !c.Ec || !c.NTgr || !c.NTgc || !c.NTr || !c.NTc || !c.NUr ||
         !c.NUc || !c.d_full_jobs || !c.sTr ||
@@ -855,6 +1053,37 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
         return SIGNTRI_ERR_NO_WORKSPACE;
     c.pairs_split = split_pairs(S);
     c.pairs_oz = ozaki_pairs_impl(kOzakiSlices, kOzakiBits);
+    // probe products with Z (one slice): pairs (s, 0)
+    std::memset(&c.pairs_z, 0, sizeof(c.pairs_z));
+    for (int sl = 0; sl < kOzakiSlices; sl++) {
+        c.pairs_z.s[sl] = sl;
+        c.pairs_z.t[sl] = 0;
+        c.pairs_z.w[sl] = ldexpf(1.0f, -kOzakiBits * (sl + 2));
+    }
+    c.pairs_z.n = kOzakiSlices;
+    SGT_CUDA_TRY(cudaMemcpyAsync(c.d_pairs_z, &c.pairs_z, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
+    {
+        // probe jobs: row pairs (2I, 2I+1) x K halves of [2I, nb), longest first
+        std::vector<TcJob> pj;
+        double kb = 0.0;
+        for (int I = 0; I < nbp; I++)
+            for (int h = 0; h < 2; h++) {
+                const int k0 = 2 * I, mid = (k0 + nb + 1) / 2;
+                TcJob j;
+                j.rt = 2 * I * MB; j.rb = 2 * I + 1 < nb ? (2 * I + 1) * MB : (int)np;
+                j.cl = 0; j.cr = 64;
+                j.kb0 = h ? mid : k0; j.kb1 = h ? nb : mid; j.slot = h; j.pad = 0;
+                kb += (double)((j.rb != (int)np) + 1) * 2 * std::max(0, j.kb1 - j.kb0);
+                pj.push_back(j);
+            }
+        std::stable_sort(pj.begin(), pj.end(),
+                         [](const TcJob &x, const TcJob &y) { return x.kb1 - x.kb0 > y.kb1 - y.kb0; });
+        c.n_probe_jobs = (int)pj.size();
+        c.probe_kb = kb;
+        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_probe_jobs, pj.data(), pj.size() * sizeof(TcJob), cudaMemcpyHostToDevice,
+                                     st));
+        SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    }
     if (!c.sc.jobs.empty())
         SGT_CUDA_TRY(cudaMemcpyAsync(c.d_jobs, c.sc.jobs.data(), c.sc.jobs.size() * sizeof(TcJob),
                                      cudaMemcpyHostToDevice, st));
@@ -908,35 +1137,45 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     if ((rs = diag_leaves_f64(n, T, ldt, U, ldu, MB, st)) != SIGNTRI_OK) return rs;
     if ((rs = sweep<0>(c, T, ldt, U, ldu, c.Ur, c.Uc, nullptr, 0)) != SIGNTRI_OK) return rs;
 
-    // 2. refinement: the first residual in the needed form (it only drives the
-    // correction), every later one -- and any acceptance -- in the full form
+    // 2. refinement.  Corrections are driven by the needed residuals (Rc at
+    // opposite-sign entries, Rs at equal-sign ones); acceptance rests on both
+    // residuals over all entries: the full products (verify_full) or their
+    // probe estimate.
     double prev = 1e300;
     rep.steps = 0;
     rep.fallback = 0;
+    auto verify = [&](int step) -> signtri_status {
+        return prm.verify_full ? residual_full(c, T, ldt, U, ldu)
+                               : probe_check(c, T, ldt, U, ldu, 0x5eedull * 1315423911ull + (unsigned long long)step);
+    };
+    auto worst_of = [&]() {
+        const double *h = c.norms_host;
+        const double nT = std::sqrt(h[2]), nU = std::sqrt(h[3]);
+        rep.resid_commute = std::sqrt(h[0]) / (nT * nU);
+        rep.resid_involution = std::sqrt(h[1]) / (nU * nU);
+        return std::max(rep.resid_commute, rep.resid_involution);
+    };
     for (int step = 0;; step++) {
-        bool full = step > 0;
-        if ((rs = full ? residual_full(c, T, ldt, U, ldu) : residual_needed(c, T, ldt, U, ldu)) != SIGNTRI_OK)
-            return rs;
-        double worst = 0.0;
-        for (int pass = 0; pass < 2; pass++) {
-            const double *h = c.norms_host;
-            const double nT = std::sqrt(h[2]), nU = std::sqrt(h[3]);
-            rep.resid_commute = std::sqrt(h[0]) / (nT * nU);
-            rep.resid_involution = std::sqrt(h[1]) / (nU * nU);
-            worst = std::max(rep.resid_commute, rep.resid_involution);
-            if (full || !(worst <= prm.tol)) break;
-            // needed residuals already small: confirm with the full form
-            if ((rs = residual_full(c, T, ldt, U, ldu)) != SIGNTRI_OK) return rs;
-            full = true;
+        bool verified = step > 0;
+        if ((rs = verified ? verify(step) : residual_needed(c, T, ldt, U, ldu)) != SIGNTRI_OK) return rs;
+        double worst = worst_of();
+        if (!verified && worst <= prm.tol) {
+            // needed residuals already small: check both equations
+            if ((rs = verify(step)) != SIGNTRI_OK) return rs;
+            verified = true;
+            worst = worst_of();
         }
         if (step == 0) rep.resid0 = worst;
         if (!(worst == worst)) { rep.fallback = 1; return SIGNTRI_OK; }   // NaN
-        if (full && worst <= prm.tol) return SIGNTRI_OK;
+        if (verified && worst <= prm.tol) return SIGNTRI_OK;
         if (step >= prm.max_steps || (step > 0 && worst > prev / prm.min_contraction)) {
             rep.fallback = 1;
             return SIGNTRI_OK;
         }
         prev = worst;
+        // the correction reads Rc / Rs entrywise: the full residual left them;
+        // after a probe test (or a confirmed step 0) form the needed ones
+        if (verified && !prm.verify_full && (rs = residual_needed(c, T, ldt, U, ldu)) != SIGNTRI_OK) return rs;
         // E: zero, diagonal blocks in float64, off-diagonal blocks by sweep
         {
             ProfScope ps(SIGNTRI_KC_FILL, st);

@@ -478,7 +478,7 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
                 o = qo.m[quad];
                 const int grow = (bottom ? job.rb : job.rt) + r;
                 if (grow >= qo.nrows) o = nullptr;
-                if (o) o += (size_t)grow + (size_t)cbase * qo.ld;
+                if (o) o += (size_t)grow + (size_t)cbase * qo.ld + (size_t)job.slot * qo.slot_stride;
             } else {
                 // slot mode: (hi, lo) pairs, float2 per element
                 o2 = reinterpret_cast<float2 *>(out) + (size_t)job.slot * 16384 + (size_t)quad * 4096 +

@@ -56,6 +56,7 @@ struct TcQuadOut {
     double *m[4];
     int ld;
     int nrows, ncols;   // entries at or beyond these are not written
+    size_t slot_stride; // job j writes at m[q] + slot_j * slot_stride (0: no offset)
 };
 
 size_t tc_smem_bytes();

@@ -90,6 +90,7 @@ _SIGNATURES = {
     "signtri_set_rates": (_I, [ctypes.c_double, ctypes.c_double]),
     "signtri_gemm_emulated": (_I, [_I, _I, _I, _VP, _I, _VP, _I, _VP, _I, _VP]),
     "signtri_set_refinement": (_I, [ctypes.c_double, _I]),
+    "signtri_set_verification": (_I, [_I]),
     "signtri_profile_read_flops": (_I, [_I, ctypes.POINTER(ctypes.c_double)]),
     "sign_tri_batched": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_VP), ctypes.POINTER(_I),
                               ctypes.POINTER(_VP), ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _VP]),
@@ -201,6 +202,10 @@ def signtri_selftest_wait(arrive: bool, limit_cycles: int, stream=None) -> int:
 
 def signtri_set_refinement(tol: float, max_steps: int) -> int:
     return load().signtri_set_refinement(float(tol), int(max_steps))
+
+
+def signtri_set_verification(full: int) -> int:
+    return load().signtri_set_verification(int(full))
 
 
 def signtri_set_rates(gemm_flops_per_s: float, givens_flops_per_s: float) -> int:

@@ -87,3 +87,24 @@ def test_mixed_gathered_residual_patterns(gpu_lib, oracle_mod, pattern):
     assert relerr(U, Uo) <= TOL_MIXED, (pattern, relerr(U, Uo), info.as_dict())
     assert info.variant == gpu_lib.Variant.PH_MIXED_TF32, info.as_dict()
     assert max(info.resid_commute, info.resid_involution) <= 1e-13
+
+
+def test_verification_modes(gpu_lib, oracle_mod):
+    # acceptance by the full residuals and by their 128-probe estimate: same
+    # result within the mixed bar, estimates within a small factor of the
+    # full values (the estimator is unbiased; 128 probes)
+    T = make_T(1500, 0.5, seed=45)
+    Uo = oracle_mod.sign_tri(T, schedule="antidiag")
+    try:
+        assert gpu_lib.signtri_set_verification(1) == 0
+        Uf, info_f = solve(gpu_lib, T, gpu_lib.Variant.PH_MIXED_TF32)
+        assert gpu_lib.signtri_set_verification(0) == 0
+        Up, info_p = solve(gpu_lib, T, gpu_lib.Variant.PH_MIXED_TF32)
+    finally:
+        gpu_lib.signtri_set_verification(0)
+    assert relerr(Uf, Uo) <= TOL_MIXED and relerr(Up, Uo) <= TOL_MIXED
+    assert info_f.variant == info_p.variant == gpu_lib.Variant.PH_MIXED_TF32
+    for a, b in [(info_p.resid_commute, info_f.resid_commute), (info_p.resid_involution, info_f.resid_involution)]:
+        assert 0 < a <= 1e-13 and 0 < b <= 1e-13
+        assert b / 3 <= a <= 3 * b, (a, b)
+    assert gpu_lib.signtri_set_verification(2) == gpu_lib.Status.ERR_BAD_ARG
