@@ -421,6 +421,29 @@ def main():
                        "resid_involution": info.resid_involution},
     }
 
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        Th = torch.from_numpy(np.ascontiguousarray(T.T)).pin_memory()
+        Uh = torch.empty_like(Th).pin_memory()
+        s = st.sign_tri_host(n, Th.data_ptr(), n, Uh.data_ptr(), n, variant, h)   # warm (staging alloc)
+        if s != 0:
+            raise st.SignTriError(s, "sign_tri_host")
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s = st.sign_tri_host(n, Th.data_ptr(), n, Uh.data_ptr(), n, variant, h)
+            if s != 0:
+                raise st.SignTriError(s, "sign_tri_host")
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / max(args.steps, 1)
+        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        line["e2e"] = {"value": world * useful / float(te.item()) / 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": Th.numel() * 8, "d2h_bytes_per_step": Uh.numel() * 8,
+                       "seconds_per_solve": float(te.item())}
+        del Th, Uh
+
     # comparison variants on the same input (float64 forms), fewer steps
     compares = []
     for cname in [c for c in (args.compare or "").split(",") if c and c != args.variant]:
@@ -450,29 +473,6 @@ def main():
                           "speedup_of_headline": cms / ms_step_max}, Uc))
     if compares:
         line["compare"] = [c for c, _ in compares]
-
-    # end to end through the public API with host buffers
-    if not args.no_e2e:
-        Th = torch.from_numpy(np.ascontiguousarray(T.T)).pin_memory()
-        Uh = torch.empty_like(Th).pin_memory()
-        s = st.sign_tri_host(n, Th.data_ptr(), n, Uh.data_ptr(), n, variant, h)   # warm (staging alloc)
-        if s != 0:
-            raise st.SignTriError(s, "sign_tri_host")
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            s = st.sign_tri_host(n, Th.data_ptr(), n, Uh.data_ptr(), n, variant, h)
-            if s != 0:
-                raise st.SignTriError(s, "sign_tri_host")
-        barrier()
-        e2e_s = (time.perf_counter() - t0) / max(args.steps, 1)
-        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        line["e2e"] = {"value": world * useful / float(te.item()) / 1e9, "unit": UNIT,
-                       "h2d_bytes_per_step": Th.numel() * 8, "d2h_bytes_per_step": Uh.numel() * 8,
-                       "seconds_per_solve": float(te.item())}
-        del Th, Uh
 
     # CPU oracle baseline on a bounded sample (rank 0, N = 1) and the parity of
     # this run's output on that window
