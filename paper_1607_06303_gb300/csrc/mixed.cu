@@ -72,11 +72,9 @@ __device__ __forceinline__ float fsgn(double t) { return t > 0.0 ? 1.f : -1.f; }
 
 // MODE 0: V = U (initial solve).  MODE 1: V = E (correction), with U0, Rc, Rs.
 // Shared memory (fp32, 64 x 65 each): T_II, T_JJ, the same-sign wavefront
-// blocks A_II, A_JJ (U in mode 0, U0 in mode 1), V, the seeds C; mode 1 adds
-// the diagonal blocks E_II, E_JJ and U0_IJ for the seeds.  V holds T_IJ until
-// the seeds are formed.
+// blocks A_II, A_JJ (U in mode 0, U0 in mode 1), V and the seeds C.
 template <int MODE>
-constexpr int leaf_buffers() { return MODE == 0 ? 6 : 9; }
+constexpr int leaf_buffers() { return 6; }
 
 template <int MODE>
 __global__ void __launch_bounds__(kLeafThreads)
@@ -95,9 +93,6 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
     float *AJ = AI + MB * LD;
     float *Vs = AJ + MB * LD;
     float *Cs = Vs + MB * LD;
-    float *EI = Cs + MB * LD;      // mode 1 only
-    float *EJ = EI + MB * LD;
-    float *WS = EJ + MB * LD;      // U0_IJ
     __shared__ float srow[MB], scol[MB];
     const int I = blockIdx.x, J = I + d;
     const int r0 = I * MB, c0 = J * MB;
@@ -113,12 +108,7 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
         const bool inJ = (i <= j) && (j < bj);
         TJ[i + j * LD] = inJ ? (float)SGT_AT(T, ldt, c0 + i, c0 + j) : 0.f;
         AJ[i + j * LD] = (inJ && up) ? (float)SGT_AT(A, lda, c0 + i, c0 + j) : 0.f;
-        Vs[i + j * LD] = (j < bj) ? (float)SGT_AT(T, ldt, r0 + i, c0 + j) : 0.f;     // T_IJ
-        if (MODE == 1) {
-            EI[i + j * LD] = up ? (float)SGT_AT(V, ldv, r0 + i, r0 + j) : 0.f;
-            EJ[i + j * LD] = (inJ && up) ? (float)SGT_AT(V, ldv, c0 + i, c0 + j) : 0.f;
-            WS[i + j * LD] = (j < bj) ? (float)SGT_AT(U0, ldu0, r0 + i, c0 + j) : 0.f;
-        }
+        Vs[i + j * LD] = 0.f;
     }
     for (int i = threadIdx.x; i < MB; i += kLeafThreads) {
         srow[i] = fsgn(SGT_AT(T, ldt, r0 + i, r0 + i));
@@ -126,10 +116,11 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
     }
     __syncthreads();
 
-    // seeds: block sums, base terms and the in-block products of known blocks
-    // (D = diagonal blocks of V: U_II, U_JJ in mode 0, E_II, E_JJ in mode 1)
-    const float *DI = (MODE == 0) ? AI : EI;
-    const float *DJ = (MODE == 0) ? AJ : EJ;
+    // seeds: block sums (their K range includes the diagonal blocks K = I
+    // and K = J, so they already hold the in-block products of the known
+    // blocks: U_II T_IJ - T_IJ U_JJ for opposite signs in mode 0, E_II T_IJ -
+    // T_IJ E_JJ and E_II U0_IJ + U0_IJ E_JJ in mode 1; terms with the unknown
+    // V_IJ vanish, its slices being still zero) and the base terms
     for (int idx = threadIdx.x; idx < MB * bj; idx += kLeafThreads) {
         const int p = idx % MB, q = idx / MB;
         const int gi = r0 + p, gj = c0 + q;
@@ -155,19 +146,13 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
         }
         float c;
         if (opp) {
-            float a = 0.f, b = 0.f;
-            for (int k = p + 1; k < MB; k++) a = fmaf(DI[p + k * LD], Vs[k + q * LD], a);
-            for (int k = 0; k < q; k++) b = fmaf(Vs[p + k * LD], DJ[k + q * LD], b);
             const float base = (MODE == 0) ? (float)SGT_AT(T, ldt, gi, gj) * (srow[p] - scol[q])
                                            : -(float)SGT_AT(Rc, ldr, gi, gj);
-            c = base + x + a - b;
+            c = base + x;
         } else if (MODE == 0) {
             c = -y;
         } else {
-            float a = 0.f, b = 0.f;
-            for (int k = p + 1; k < MB; k++) a = fmaf(EI[p + k * LD], WS[k + q * LD], a);
-            for (int k = 0; k < q; k++) b = fmaf(WS[p + k * LD], EJ[k + q * LD], b);
-            c = -(float)SGT_AT(Rs, ldr, gi, gj) - y - a - b;
+            c = -(float)SGT_AT(Rs, ldr, gi, gj) - y;
         }
         Cs[p + q * LD] = c;
     }
@@ -391,6 +376,27 @@ __global__ void apply_correction_kernel(int n, double *__restrict__ U, int ldu, 
     if (threadIdx.x == 0) atomicAdd(&norms[4], red[0]);
 }
 
+// Rounding-split bf16 slices of the strictly upper part of the diagonal
+// blocks of V (U after the float64 diagonal leaves, E after the corrections'
+// diagonal leaves), in the layout the leaves write: row slices
+// Vr[s][row][col], column slices Vc[s][col][row].  One CTA per block.
+__global__ void diag_slices_kernel(int n, const double *__restrict__ V, int ldv, __nv_bfloat16 *__restrict__ Vr,
+                                   __nv_bfloat16 *__restrict__ Vc, int S, int rows_pad, int ldsl)
+{
+    const int r0 = blockIdx.x * MB;
+    const int bs = min(MB, n - r0);
+    for (int idx = threadIdx.x; idx < bs * bs; idx += blockDim.x) {
+        const int i = idx % bs, j = idx / bs;
+        double r = (i < j) ? SGT_AT(V, ldv, r0 + i, r0 + j) : 0.0;
+        for (int s = 0; s < S; s++) {
+            const __nv_bfloat16 h = __double2bfloat16(r);
+            Vr[((size_t)s * rows_pad + r0 + i) * ldsl + r0 + j] = h;
+            Vc[((size_t)s * rows_pad + r0 + j) * ldsl + r0 + i] = h;
+            r -= (double)__bfloat162float(h);
+        }
+    }
+}
+
 // ---------------------------------------------------------- probe check ---
 // Acceptance test by random probes: for Z (n x kProbes) with independent +-1
 // entries, E ||R Z||_F^2 = kProbes ||R||_F^2 for any R, so
@@ -518,7 +524,8 @@ void build_schedule(int n, Schedule &sc)
         sc.tile_begin[d] = (int)sc.tslot.size();
         if (d < 1 || d >= nb) continue;
         const int ntiles = nb - d;
-        const long long kmax = d - 1, W = (long long)ntiles * kmax;
+        // K-blocks I .. J: the diagonal blocks carry the known in-block terms
+        const long long kmax = d + 1, W = (long long)ntiles * kmax;
         if (W == 0) {
             for (int t = 0; t < ntiles; t++) sc.tslot.push_back(make_int2(0, 0));
             continue;
@@ -534,8 +541,8 @@ void build_schedule(int n, Schedule &sc)
                 const long long t0 = (long long)t * kmax, xe = std::min(x1, t0 + kmax);
                 TcJob j;
                 j.rt = t * MB; j.rb = t * MB; j.cl = (t + d) * MB; j.cr = (t + d) * MB;
-                j.kb0 = t + 1 + (int)(x - t0);
-                j.kb1 = t + 1 + (int)(xe - t0);
+                j.kb0 = t + (int)(x - t0);
+                j.kb1 = t + (int)(xe - t0);
                 j.slot = c + t;
                 j.pad = 0;
                 sc.jobs.push_back(j);
@@ -673,7 +680,7 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
         const TcJob *jobs = c.d_jobs + c.sc.job_off[d];
         const int *coff = c.d_cta_off + c.sc.cta_begin[d];
         const int G = c.sc.nctas[d];
-        const long long sum_kb = (long long)ntiles * (d - 1);
+        const long long sum_kb = (long long)ntiles * (d + 1);
         signtri_status rs;
         if (njobs > 0) {
             if (MODE == 0) {
@@ -1135,6 +1142,11 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     // 1. low-precision solve: diagonal blocks in float64, the rest by sweep
     if ((rs = launch_zero_strict_lower(n, U, ldu, st)) != SIGNTRI_OK) return rs;
     if ((rs = diag_leaves_f64(n, T, ldt, U, ldu, MB, st)) != SIGNTRI_OK) return rs;
+    {
+        ProfScope ps(SIGNTRI_KC_CONVERT, st);
+        diag_slices_kernel<<<nb, 256, 0, st>>>(n, U, ldu, c.Ur, c.Uc, S, (int)np, (int)np);
+        SGT_LAUNCH_CHECK();
+    }
     if ((rs = sweep<0>(c, T, ldt, U, ldu, c.Ur, c.Uc, nullptr, 0)) != SIGNTRI_OK) return rs;
 
     // 2. refinement.  Corrections are driven by the needed residuals (Rc at
@@ -1191,6 +1203,11 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
                                               (int)dsm));
             ProfScope ps(SIGNTRI_KC_CORRECTION, st);
             corr_diag_leaf_kernel<<<nb, kLeafThreads, dsm, st>>>(n, T, ldt, U, ldu, c.res_c, c.res_s, n, c.E, n);
+            SGT_LAUNCH_CHECK();
+        }
+        {
+            ProfScope ps(SIGNTRI_KC_CONVERT, st);
+            diag_slices_kernel<<<nb, 256, 0, st>>>(n, c.E, n, c.Er, c.Ec, S, (int)np, (int)np);
             SGT_LAUNCH_CHECK();
         }
         if ((rs = sweep<1>(c, T, ldt, c.E, n, c.Er, c.Ec, U, ldu)) != SIGNTRI_OK) return rs;
