@@ -175,8 +175,17 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
         const float *Bm = opp ? TJ : AJ;
         float a = 0.f, b = 0.f;
         if (active) {
-            for (int k = pp + 1 + sub; k < MB; k += kLeafSub) a = fmaf(Am[pp + k * LD], Vs[k + q * LD], a);
-            for (int k = sub; k < q; k += kLeafSub) b = fmaf(Vs[pp + k * LD], Bm[k + q * LD], b);
+            // fixed trip counts (predicated tails): no loop control in the chain
+#pragma unroll
+            for (int it = 0; it < MB / kLeafSub; it++) {
+                const int k = pp + 1 + sub + kLeafSub * it;
+                if (k < MB) a = fmaf(Am[pp + k * LD], Vs[k + q * LD], a);
+            }
+#pragma unroll
+            for (int it = 0; it < MB / kLeafSub; it++) {
+                const int k = sub + kLeafSub * it;
+                if (k < q) b = fmaf(Vs[pp + k * LD], Bm[k + q * LD], b);
+            }
         }
 #pragma unroll
         for (int o = 1; o < kLeafSub; o <<= 1) {
