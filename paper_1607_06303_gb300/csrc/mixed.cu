@@ -1205,7 +1205,10 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
         }
         SGT_CUDA_TRY(cudaMemsetAsync(c.Er, 0, split_elems * 2, st));
         SGT_CUDA_TRY(cudaMemsetAsync(c.Ec, 0, split_elems * 2, st));
-        if ((rs = split_full(c, U, ldu, c.Ur, c.Uc)) != SIGNTRI_OK) return rs;
+        // U0's slices: after the initial sweep they are already in Ur / Uc
+        // (off-diagonal blocks from the leaves, diagonal blocks from
+        // diag_slices_kernel); after a correction U has moved
+        if (step > 0 && (rs = split_full(c, U, ldu, c.Ur, c.Uc)) != SIGNTRI_OK) return rs;
         {
             const size_t dsm = 3 * (size_t)MB * (MB + 1) * sizeof(double);
             SGT_CUDA_TRY(cudaFuncSetAttribute(corr_diag_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
