@@ -61,7 +61,6 @@ namespace {
 constexpr int MB = 64;
 constexpr int kLeafThreads = 512;
 
-constexpr int kLeafSub = kLeafThreads / MB;   // threads per entry in the wavefront
 constexpr int kOzakiSlices = 7;   // exact slices of kOzakiBits bits: 49 bits, 28 pairs
 constexpr int kOzakiBits = 7;
 constexpr int kSuper = 1024;   // superblock of the gathered residual layout
@@ -76,16 +75,35 @@ __device__ __forceinline__ float fsgn(double t) { return t > 0.0 ? 1.f : -1.f; }
 template <int MODE>
 constexpr int leaf_buffers() { return 6; }
 
+constexpr int kSub = 16;             // sub-block edge of the in-tile solve
+constexpr int kNSub = MB / kSub;     // sub-blocks per tile edge
+
+// fp32 copies of the diagonal blocks a leaf reads: DT[I] = the upper
+// triangle of T_II, DA[I] = the strictly upper triangle of A_II, each 64 x 64
+// column-major, zero outside the matrix.
+__global__ void diag32_kernel(int n, const double *__restrict__ T, int ldt, const double *__restrict__ A, int lda,
+                              float *__restrict__ DT, float *__restrict__ DA)
+{
+    const int r0 = blockIdx.x * MB;
+    float *dt = DT + (size_t)blockIdx.x * MB * MB, *da = DA + (size_t)blockIdx.x * MB * MB;
+    for (int idx = threadIdx.x; idx < MB * MB; idx += blockDim.x) {
+        const int i = idx % MB, j = idx / MB;
+        const bool in = r0 + j < n;
+        dt[idx] = (in && i <= j) ? (float)SGT_AT(T, ldt, r0 + i, r0 + j) : 0.f;
+        da[idx] = (in && i < j) ? (float)SGT_AT(A, lda, r0 + i, r0 + j) : 0.f;
+    }
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(kLeafThreads)
+__global__ void __launch_bounds__(kLeafThreads, 2)
 mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restrict__ V, int ldv,
-                  const double *__restrict__ U0, int ldu0, const double *__restrict__ Rc,
+                  const float *__restrict__ DT, const float *__restrict__ DA, const double *__restrict__ Rc,
                   const double *__restrict__ Rs, int ldr, int d, const int2 *__restrict__ tslot,
-                  const double *__restrict__ PA,
-                  const double *__restrict__ PB, __nv_bfloat16 *__restrict__ Vr, __nv_bfloat16 *__restrict__ Vc,
-                  int S, int rows_pad, int ldsl)
+                  const double *__restrict__ PA, const double *__restrict__ PB, __nv_bfloat16 *__restrict__ Vr,
+                  __nv_bfloat16 *__restrict__ Vc, int S, int rows_pad, int ldsl)
 {
     constexpr int LD = MB + 1;
+    constexpr int EPT = MB * MB / kLeafThreads;   // tile entries per thread
     extern __shared__ float fsm[];
     float *TI = fsm;
     float *TJ = TI + MB * LD;
@@ -97,18 +115,46 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
     const int I = blockIdx.x, J = I + d;
     const int r0 = I * MB, c0 = J * MB;
     const int bj = min(MB, n - c0);
-    const double *A = (MODE == 0) ? V : U0;
-    const int lda = (MODE == 0) ? ldv : ldu0;
+    // thread's entries: row p, columns q0 + m * (kLeafThreads / MB)
+    const int p = threadIdx.x % MB, q0 = threadIdx.x / MB;
+    constexpr int QS = kLeafThreads / MB;
 
-    for (int idx = threadIdx.x; idx < MB * MB; idx += kLeafThreads) {
-        const int i = idx % MB, j = idx / MB;
-        const bool up = (i < j);
-        TI[i + j * LD] = (i <= j) ? (float)SGT_AT(T, ldt, r0 + i, r0 + j) : 0.f;
-        AI[i + j * LD] = up ? (float)SGT_AT(A, lda, r0 + i, r0 + j) : 0.f;
-        const bool inJ = (i <= j) && (j < bj);
-        TJ[i + j * LD] = inJ ? (float)SGT_AT(T, ldt, c0 + i, c0 + j) : 0.f;
-        AJ[i + j * LD] = (inJ && up) ? (float)SGT_AT(A, lda, c0 + i, c0 + j) : 0.f;
-        Vs[i + j * LD] = 0.f;
+    // every global read that needs no sign first: the diagonal blocks, the
+    // base terms of the seeds, this tile's partial slots
+    const int2 ts = tslot[I];
+    float base0[EPT], base1[EPT];
+#pragma unroll
+    for (int m = 0; m < EPT; m++) {
+        const int q = q0 + m * QS;
+        const bool ok = q < bj;
+        if (MODE == 0) {
+            base0[m] = ok ? (float)SGT_AT(T, ldt, r0 + p, c0 + q) : 0.f;
+            base1[m] = 0.f;
+        } else {
+            base0[m] = ok ? (float)SGT_AT(Rc, ldr, r0 + p, c0 + q) : 0.f;
+            base1[m] = ok ? (float)SGT_AT(Rs, ldr, r0 + p, c0 + q) : 0.f;
+        }
+    }
+    {
+        const float4 *src[4] = {reinterpret_cast<const float4 *>(DT + (size_t)I * MB * MB),
+                                reinterpret_cast<const float4 *>(DT + (size_t)J * MB * MB),
+                                reinterpret_cast<const float4 *>(DA + (size_t)I * MB * MB),
+                                reinterpret_cast<const float4 *>(DA + (size_t)J * MB * MB)};
+        float *dst[4] = {TI, TJ, AI, AJ};
+        float4 v[4][EPT / 4];
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int m = 0; m < EPT / 4; m++) v[a][m] = src[a][threadIdx.x + m * kLeafThreads];
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int m = 0; m < EPT / 4; m++) {
+                const int e = 4 * (threadIdx.x + m * kLeafThreads);
+                float *o = dst[a] + e % MB + (e / MB) * LD;   // four rows of one column
+                o[0] = v[a][m].x; o[1] = v[a][m].y; o[2] = v[a][m].z; o[3] = v[a][m].w;
+            }
+        for (int idx = threadIdx.x; idx < MB * LD; idx += kLeafThreads) Vs[idx] = 0.f;
     }
     for (int i = threadIdx.x; i < MB; i += kLeafThreads) {
         srow[i] = fsgn(SGT_AT(T, ldt, r0 + i, r0 + i));
@@ -120,105 +166,139 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
     // and K = J, so they already hold the in-block products of the known
     // blocks: U_II T_IJ - T_IJ U_JJ for opposite signs in mode 0, E_II T_IJ -
     // T_IJ E_JJ and E_II U0_IJ + U0_IJ E_JJ in mode 1; terms with the unknown
-    // V_IJ vanish, its slices being still zero) and the base terms
-    for (int idx = threadIdx.x; idx < MB * bj; idx += kLeafThreads) {
-        const int p = idx % MB, q = idx / MB;
-        const int gi = r0 + p, gj = c0 + q;
-        const bool opp = (srow[p] + scol[q] == 0.f);
-        // partial block sums: float2 (hi, lo) per element, summed in fp32
-        float x = 0.f, y = 0.f;
+    // V_IJ vanish, its slices being still zero) and the base terms.  Partial
+    // block sums: float2 (hi, lo) per element, summed in fp32 over the slots.
+    {
         const float2 *PA2 = reinterpret_cast<const float2 *>(PA);
         const float2 *PB2 = reinterpret_cast<const float2 *>(PB);
-        const int2 ts = tslot[I];   // this tile's partial slots: first, count
-#pragma unroll 4
+        float acc[EPT];
+#pragma unroll
+        for (int m = 0; m < EPT; m++) acc[m] = 0.f;
         for (int s = 0; s < ts.y; s++) {
-            const size_t e = ((size_t)ts.x + s) * 16384 + p + (size_t)q * 64;
-            if (opp) {
-                const float2 tl = PA2[e], br = PA2[e + 3 * 4096];
-                x += (tl.x - br.x) + (tl.y - br.y);
-            } else if (MODE == 0) {
-                const float2 tr = PA2[e + 4096];
-                y += tr.x + tr.y;
-            } else {
-                const float2 tl = PB2[e], br = PB2[e + 3 * 4096];
-                y += (tl.x + br.x) + (tl.y + br.y);
+            const size_t sb = ((size_t)ts.x + s) * 16384 + p;
+#pragma unroll
+            for (int m = 0; m < EPT; m++) {
+                const int q = q0 + m * QS;
+                if (q < bj) {
+                    const bool opp = (srow[p] + scol[q] == 0.f);
+                    // opposite signs: TL - BR of PA (X); equal signs: TR of PA
+                    // (Y, mode 0) or TL + BR of PB (Y^E, mode 1)
+                    const float2 *src = opp ? PA2 : (MODE == 0 ? PA2 + 4096 : PB2);
+                    const size_t e = sb + (size_t)q * 64;
+                    const float2 l1 = src[e];
+                    float2 l2 = make_float2(0.f, 0.f);
+                    if (MODE == 1 || opp) l2 = src[e + 3 * 4096];
+                    const float sg = opp ? -1.f : 1.f;
+                    acc[m] += (l1.x + sg * l2.x) + (l1.y + sg * l2.y);
+                }
             }
         }
-        float c;
-        if (opp) {
-            const float base = (MODE == 0) ? (float)SGT_AT(T, ldt, gi, gj) * (srow[p] - scol[q])
-                                           : -(float)SGT_AT(Rc, ldr, gi, gj);
-            c = base + x;
-        } else if (MODE == 0) {
-            c = -y;
-        } else {
-            c = -(float)SGT_AT(Rs, ldr, gi, gj) - y;
+#pragma unroll
+        for (int m = 0; m < EPT; m++) {
+            const int q = q0 + m * QS;
+            float c = 0.f;
+            if (q < bj) {
+                if (srow[p] + scol[q] == 0.f) c = (MODE == 0 ? base0[m] * (srow[p] - scol[q]) : -base0[m]) + acc[m];
+                else c = (MODE == 0) ? -acc[m] : -base1[m] - acc[m];
+            }
+            Cs[p + q * LD] = c;
         }
-        Cs[p + q * LD] = c;
     }
     __syncthreads();
 
-    // wavefront: kLeafSub threads per entry (strided partial sums, then a
-    // shuffle reduction within the group); every thread runs the same
-    // control flow
-    const int grp = threadIdx.x / kLeafSub, sub = threadIdx.x % kLeafSub;
-    const int nsteps = MB + bj - 1;
-    for (int st = 0; st < nsteps; st++) {
-        const int plo = max(0, MB - 1 - st);
-        const int phi = min(MB - 1, MB - 1 - st + bj - 1);
-        const int p = plo + grp;
-        const bool active = (p <= phi);
-        const int pp = active ? p : plo;
-        const int q = st - (MB - 1 - pp);
-        const bool opp = (srow[pp] + scol[q] == 0.f);
-        const float *Am = opp ? TI : AI;
-        const float *Bm = opp ? TJ : AJ;
-        float a = 0.f, b = 0.f;
-        if (active) {
-            // fixed trip counts (predicated tails): no loop control in the chain
-#pragma unroll
-            for (int it = 0; it < MB / kLeafSub; it++) {
-                const int k = pp + 1 + sub + kLeafSub * it;
-                if (k < MB) a = fmaf(Am[pp + k * LD], Vs[k + q * LD], a);
+    // In-tile solve (Algorithm 6, 1x1 case) by 16 x 16 sub-blocks: entry
+    // (p, q) needs the entries below it in its column and left of it in its
+    // row, so sub-block (a, b) (rows 16a.., columns 16b..) needs the
+    // sub-blocks below and left of it, and phase s = (3 - a) + b holds up to
+    // four independent sub-blocks.  A phase first adds to its seeds the sums
+    // over the solved sub-blocks (two threads per entry: the column part and
+    // the row part), then one warp per sub-block runs the 31-step
+    // anti-diagonal wavefront inside it (two lanes per entry, warp-synchronous).
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int s = 0; s < 2 * kNSub - 1; s++) {
+        const int blo = max(0, s - (kNSub - 1)), nblk = min(kNSub - 1, s) - blo + 1;
+        if (s > 0) {
+            const int items = nblk * kSub * kSub * 2;   // a multiple of kLeafThreads: same trip count everywhere
+            for (int it = threadIdx.x; it < items; it += kLeafThreads) {
+                const int part = it & 1, e = it >> 1;
+                const int b = blo + e / (kSub * kSub), pq = e % (kSub * kSub);
+                const int a = kNSub - 1 - s + b;
+                const int P = a * kSub + pq % kSub, Q = b * kSub + pq / kSub;
+                const bool opp = (srow[P] + scol[Q] == 0.f);
+                // part 0: sum_{k >= 16(a+1)} M_Pk V_kQ; part 1: sum_{k < 16b} V_Pk N_kQ
+                const float *X = part == 0 ? (opp ? TI : AI) + P : Vs + P;
+                const float *Y = part == 0 ? Vs + Q * LD : (opp ? TJ : AJ) + Q * LD;
+                const int klo = part == 0 ? (a + 1) * kSub : 0, khi = part == 0 ? MB : b * kSub;
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                for (int k = klo; k < khi; k += 4) {   // lengths are multiples of 16
+                    a0 = fmaf(X[k * LD], Y[k], a0);
+                    a1 = fmaf(X[(k + 1) * LD], Y[k + 1], a1);
+                    a2 = fmaf(X[(k + 2) * LD], Y[k + 2], a2);
+                    a3 = fmaf(X[(k + 3) * LD], Y[k + 3], a3);
+                }
+                const float mine = (a0 + a1) + (a2 + a3);
+                const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+                if (part == 0) Cs[P + Q * LD] += opp ? (other - mine) : (-mine - other);
             }
+            __syncthreads();
+        }
+        if (warp < nblk) {
+            const int b = blo + warp, a = kNSub - 1 - s + b;
+            const int R0 = a * kSub, C0 = b * kSub;
+            if (C0 < bj) {
+                const int el = lane >> 1, role = lane & 1;
+                for (int t = 0; t < 2 * kSub - 1; t++) {
+                    const int qlo = max(0, t - (kSub - 1)), qhi = min(kSub - 1, t);
+                    const bool act = qlo + el <= qhi;
+                    const int qq = act ? qlo + el : qhi;
+                    const int pp = kSub - 1 - t + qq;
+                    const int P = R0 + pp, Q = C0 + qq;
+                    const bool opp = (srow[P] + scol[Q] == 0.f);
+                    // role 0: sum over k in (pp, 16) of M_Pk V_kQ; role 1: sum over
+                    // k in [0, qq) of V_Pk N_kQ (in-sub-block indices)
+                    const float *X = role == 0 ? (opp ? TI : AI) + P : Vs + P;
+                    const float *Y = role == 0 ? Vs + Q * LD : (opp ? TJ : AJ) + Q * LD;
+                    const int klo = role == 0 ? P + 1 : C0, khi = role == 0 ? R0 + kSub : Q;
+                    const float den = opp ? (TI[P + P * LD] - TJ[Q + Q * LD]) : (srow[P] + scol[Q]);
+                    const float rden = __frcp_rn(den);
+                    float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-            for (int it = 0; it < MB / kLeafSub; it++) {
-                const int k = sub + kLeafSub * it;
-                if (k < q) b = fmaf(Vs[pp + k * LD], Bm[k + q * LD], b);
+                    for (int i = 0; i < kSub; i += 2) {
+                        const int k = klo + i;
+                        if (k < khi) a0 = fmaf(X[k * LD], Y[k], a0);
+                        if (k + 1 < khi) a1 = fmaf(X[(k + 1) * LD], Y[k + 1], a1);
+                    }
+                    const float mine = a0 + a1;
+                    const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+                    if (role == 0 && act && Q < bj)
+                        Vs[P + Q * LD] = (Cs[P + Q * LD] - mine + (opp ? other : -other)) * rden;
+                    __syncwarp();
+                }
             }
-        }
-#pragma unroll
-        for (int o = 1; o < kLeafSub; o <<= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o, kLeafSub);
-            b += __shfl_xor_sync(0xffffffffu, b, o, kLeafSub);
-        }
-        if (active && sub == 0) {
-            float v;
-            if (opp) v = (Cs[pp + q * LD] - a + b) / (TI[pp + pp * LD] - TJ[q + q * LD]);
-            else v = (Cs[pp + q * LD] - a - b) / (srow[pp] + scol[q]);
-            Vs[pp + q * LD] = v;
         }
         __syncthreads();
     }
+
     // V (float64) and its bf16 splits: row slices Vr[s][row][col], column
-    // slices Vc[s][col][row]
+    // slices Vc[s][col][row].  The split runs in fp32: each remainder is
+    // exact (V is an fp32 value and a bf16 rounding removes its leading bits)
     for (int idx = threadIdx.x; idx < MB * bj; idx += kLeafThreads) {
-        const int p = idx % MB, q = idx / MB;
-        SGT_AT(V, ldv, r0 + p, c0 + q) = (double)Vs[p + q * LD];
-        double r = (double)Vs[p + q * LD];
+        const int pr = idx % MB, q = idx / MB;
+        float r = Vs[pr + q * LD];
+        SGT_AT(V, ldv, r0 + pr, c0 + q) = (double)r;
         for (int s = 0; s < S; s++) {
-            const __nv_bfloat16 h = __double2bfloat16(r);
-            Vc[((size_t)s * rows_pad + c0 + q) * ldsl + r0 + p] = h;
-            r -= (double)__bfloat162float(h);
+            const __nv_bfloat16 h = __float2bfloat16_rn(r);
+            Vc[((size_t)s * rows_pad + c0 + q) * ldsl + r0 + pr] = h;
+            r -= __bfloat162float(h);
         }
     }
     for (int idx = threadIdx.x; idx < MB * bj; idx += kLeafThreads) {
-        const int q = idx % bj, p = idx / bj;
-        double r = (double)Vs[p + q * LD];
+        const int q = idx % bj, pr = idx / bj;
+        float r = Vs[pr + q * LD];
         for (int s = 0; s < S; s++) {
-            const __nv_bfloat16 h = __double2bfloat16(r);
-            Vr[((size_t)s * rows_pad + r0 + p) * ldsl + c0 + q] = h;
-            r -= (double)__bfloat162float(h);
+            const __nv_bfloat16 h = __float2bfloat16_rn(r);
+            Vr[((size_t)s * rows_pad + r0 + pr) * ldsl + c0 + q] = h;
+            r -= __bfloat162float(h);
         }
     }
 }
@@ -581,6 +661,7 @@ struct MixedCtx {
     TcPairs *d_pairs_split, *d_pairs_oz;
     // bf16 splits (S slices) of T and of the unknowns, row and column forms
     __nv_bfloat16 *Tr, *Tc, *Ur, *Uc, *Er, *Ec;
+    float *DT32, *DA32;         // fp32 diagonal blocks for the leaves (64 x 64 each)
     // exact slices of the strictly upper parts of T and U in the gathered
     // layout (residual products): ng gathered positions, rows_g allocated
     // (the last 64 all zero), pitch rows_g
@@ -638,6 +719,7 @@ size_t bytes_for(int n, int S)
     b += 2 * maxjobs * 16384 * 8 + 2 * 256;                             // partials
     b += 2 * (size_t)n * n * 8 + 2 * 256;                               // E, R (= Rs)
     b += 64 + 256;                                                      // norms
+    b += 2 * nb * MB * MB * sizeof(float) + 2 * 256;                    // fp32 diagonal blocks
     const size_t pairs_max = ngr / 128 + 2 * (size_t)((n + kSuper - 1) / kSuper) + 2;
     b += pairs_max * pairs_max * sizeof(TcJob) + 256;                   // needed-residual jobs
     const size_t nbp = (nb + 1) / 2;
@@ -674,6 +756,15 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
     const size_t leaf_smem = (size_t)leaf_buffers<MODE>() * MB * (MB + 1) * sizeof(float);
     SGT_CUDA_TRY(cudaFuncSetAttribute(mixed_leaf_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)leaf_smem));
+    SGT_CUDA_TRY(cudaFuncSetAttribute(mixed_leaf_kernel<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      cudaSharedmemCarveoutMaxShared));   // two leaves per SM
+    {
+        // fp32 copies of the diagonal blocks of T and of the known blocks
+        // the same-sign recurrences use (U in mode 0, U0 in mode 1)
+        ProfScope ps(MODE == 0 ? SIGNTRI_KC_OFFDIAG_LEAF_F32 : SIGNTRI_KC_CORRECTION, c.st);
+        diag32_kernel<<<nb, 256, 0, c.st>>>(n, T, ldt, MODE == 0 ? V : U0, MODE == 0 ? ldv : ldu0, c.DT32, c.DA32);
+        SGT_LAUNCH_CHECK();
+    }
     const TcSource srcT_r{c.Tr, c.S, c.np, c.np, c.np, nullptr}, srcT_c{c.Tc, c.S, c.np, c.np, c.np, nullptr};
     const TcSource srcV_r{Vr, c.S, c.np, c.np, c.np, nullptr}, srcV_c{Vc, c.S, c.np, c.np, c.np, nullptr};
     const TcSource srcU_r{c.Ur, c.S, c.np, c.np, c.np, nullptr}, srcU_c{c.Uc, c.S, c.np, c.np, c.np, nullptr};
@@ -713,8 +804,8 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
         }
         ProfScope ps(MODE == 0 ? SIGNTRI_KC_OFFDIAG_LEAF_F32 : SIGNTRI_KC_CORRECTION, c.st);
         mixed_leaf_kernel<MODE><<<ntiles, kLeafThreads, leaf_smem, c.st>>>(
-            n, T, ldt, V, ldv, U0, ldu0, c.res_c, c.res_s, n, d, c.d_tslot + c.sc.tile_begin[d], c.PA, c.PB, Vr, Vc,
-            c.S, c.np, c.np);
+            n, T, ldt, V, ldv, c.DT32, c.DA32, c.res_c, c.res_s, n, d, c.d_tslot + c.sc.tile_begin[d], c.PA, c.PB,
+            Vr, Vc, c.S, c.np, c.np);
         SGT_LAUNCH_CHECK();
     }
     return SIGNTRI_OK;
@@ -1034,6 +1125,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     const size_t maxjobs = (size_t)std::max(c.sc.max_jobs, 1);
     c.PA = take<double>(ws, maxjobs * 16384); c.PB = take<double>(ws, maxjobs * 16384);
     c.E = take<double>(ws, (size_t)n * n); c.R = take<double>(ws, (size_t)n * n);
+    c.DT32 = take<float>(ws, (size_t)nb * MB * MB); c.DA32 = take<float>(ws, (size_t)nb * MB * MB);
     const int nbp = (nb + 1) / 2;
     c.n_full_jobs = nbp * (nbp + 1) / 2;
     c.d_full_jobs = take<TcJob>(ws, (size_t)c.n_full_jobs);
@@ -1065,7 +1157,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
         !c.NUc || !c.d_full_jobs || !c.sTr ||
         !c.sTc || !c.sUr || !c.sUc || !c.gTr || !c.gTc || !c.gUr || !c.gUc || !c.gmap || !c.ginv || !c.pos ||
         !c.tmpmax || !c.tmpmax2 || !c.PA || !c.PB || !c.E || !c.R || !c.RA || !c.RB || !c.norms || !c.d_res_jobs || !c.d_jobs ||
-        !c.d_pairs_split || !c.d_pairs_oz || !c.d_cta_off || !c.d_tslot)
+        !c.d_pairs_split || !c.d_pairs_oz || !c.d_cta_off || !c.d_tslot || !c.DT32 || !c.DA32)
         return SIGNTRI_ERR_NO_WORKSPACE;
     c.pairs_split = split_pairs(S);
     c.pairs_oz = ozaki_pairs_impl(kOzakiSlices, kOzakiBits);
