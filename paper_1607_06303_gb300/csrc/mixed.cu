@@ -70,12 +70,13 @@ __device__ __forceinline__ float fsgn(double t) { return t > 0.0 ? 1.f : -1.f; }
 // --------------------------------------------------------------- leaves ---
 
 // MODE 0: V = U (initial solve).  MODE 1: V = E (correction), with U0, Rc, Rs.
-// Shared memory (fp32, 64 x 65 each): T_II, T_JJ, the same-sign wavefront
+// Shared memory (fp32, 64 x 68 each): T_II, T_JJ, the same-sign wavefront
 // blocks A_II, A_JJ (U in mode 0, U0 in mode 1), V and the seeds C.
 template <int MODE>
 constexpr int leaf_buffers() { return 6; }
 
 constexpr int kSub = 16;             // sub-block edge of the in-tile solve
+constexpr int kLeafLD = MB + 4;      // leaf smem pitch: columns stay 16-byte aligned for float4 reads
 constexpr int kNSub = MB / kSub;     // sub-blocks per tile edge
 
 // fp32 copies of the diagonal blocks a leaf reads: DT[I] = the upper
@@ -102,14 +103,14 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
                   const double *__restrict__ PA, const double *__restrict__ PB, __nv_bfloat16 *__restrict__ Vr,
                   __nv_bfloat16 *__restrict__ Vc, int S, int rows_pad, int ldsl)
 {
-    constexpr int LD = MB + 1;
+    constexpr int LD = kLeafLD;
     constexpr int EPT = MB * MB / kLeafThreads;   // tile entries per thread
-    extern __shared__ float fsm[];
-    float *TI = fsm;
+    extern __shared__ float4 fsm4[];
+    float *TI = reinterpret_cast<float *>(fsm4);
     float *TJ = TI + MB * LD;
     float *AI = TJ + MB * LD;
     float *AJ = AI + MB * LD;
-    float *Vs = AJ + MB * LD;
+    float *Vs = AJ + MB * LD + 16;   // 16 banks off T and A: the sub-block updates read both at once
     float *Cs = Vs + MB * LD;
     __shared__ float srow[MB], scol[MB];
     const int I = blockIdx.x, J = I + d;
@@ -151,8 +152,8 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
 #pragma unroll
             for (int m = 0; m < EPT / 4; m++) {
                 const int e = 4 * (threadIdx.x + m * kLeafThreads);
-                float *o = dst[a] + e % MB + (e / MB) * LD;   // four rows of one column
-                o[0] = v[a][m].x; o[1] = v[a][m].y; o[2] = v[a][m].z; o[3] = v[a][m].w;
+                // four rows of one column
+                *reinterpret_cast<float4 *>(dst[a] + e % MB + (e / MB) * LD) = v[a][m];
             }
         for (int idx = threadIdx.x; idx < MB * LD; idx += kLeafThreads) Vs[idx] = 0.f;
     }
@@ -231,10 +232,11 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
                 const int klo = part == 0 ? (a + 1) * kSub : 0, khi = part == 0 ? MB : b * kSub;
                 float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
                 for (int k = klo; k < khi; k += 4) {   // lengths are multiples of 16
-                    a0 = fmaf(X[k * LD], Y[k], a0);
-                    a1 = fmaf(X[(k + 1) * LD], Y[k + 1], a1);
-                    a2 = fmaf(X[(k + 2) * LD], Y[k + 2], a2);
-                    a3 = fmaf(X[(k + 3) * LD], Y[k + 3], a3);
+                    const float4 y = *reinterpret_cast<const float4 *>(Y + k);
+                    a0 = fmaf(X[k * LD], y.x, a0);
+                    a1 = fmaf(X[(k + 1) * LD], y.y, a1);
+                    a2 = fmaf(X[(k + 2) * LD], y.z, a2);
+                    a3 = fmaf(X[(k + 3) * LD], y.w, a3);
                 }
                 const float mine = (a0 + a1) + (a2 + a3);
                 const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
@@ -246,6 +248,11 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
             const int b = blo + warp, a = kNSub - 1 - s + b;
             const int R0 = a * kSub, C0 = b * kSub;
             if (C0 < bj) {
+                // lane pair el: entry el of anti-diagonal t of the sub-block;
+                // role 0 sums M_Pk V_kQ, role 1 V_Pk N_kQ, both over all 16 k
+                // of the sub-block: M and N are zero below their diagonals
+                // and V_PQ is still zero, so the terms outside (P, R0 + 16)
+                // and [C0, Q) vanish and no lane needs a predicate
                 const int el = lane >> 1, role = lane & 1;
                 for (int t = 0; t < 2 * kSub - 1; t++) {
                     const int qlo = max(0, t - (kSub - 1)), qhi = min(kSub - 1, t);
@@ -254,24 +261,22 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
                     const int pp = kSub - 1 - t + qq;
                     const int P = R0 + pp, Q = C0 + qq;
                     const bool opp = (srow[P] + scol[Q] == 0.f);
-                    // role 0: sum over k in (pp, 16) of M_Pk V_kQ; role 1: sum over
-                    // k in [0, qq) of V_Pk N_kQ (in-sub-block indices)
-                    const float *X = role == 0 ? (opp ? TI : AI) + P : Vs + P;
-                    const float *Y = role == 0 ? Vs + Q * LD : (opp ? TJ : AJ) + Q * LD;
-                    const int klo = role == 0 ? P + 1 : C0, khi = role == 0 ? R0 + kSub : Q;
-                    const float den = opp ? (TI[P + P * LD] - TJ[Q + Q * LD]) : (srow[P] + scol[Q]);
-                    const float rden = __frcp_rn(den);
-                    float a0 = 0.f, a1 = 0.f;
+                    const float *X = role == 0 ? (opp ? TI : AI) + P + R0 * LD : Vs + P + C0 * LD;
+                    const float *Y = role == 0 ? Vs + R0 + Q * LD : (opp ? TJ : AJ) + C0 + Q * LD;
+                    const float rden = __frcp_rn(opp ? (TI[P + P * LD] - TJ[Q + Q * LD]) : (srow[P] + scol[Q]));
+                    const float cv = Cs[P + Q * LD];
+                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
-                    for (int i = 0; i < kSub; i += 2) {
-                        const int k = klo + i;
-                        if (k < khi) a0 = fmaf(X[k * LD], Y[k], a0);
-                        if (k + 1 < khi) a1 = fmaf(X[(k + 1) * LD], Y[k + 1], a1);
+                    for (int i = 0; i < kSub; i += 4) {
+                        const float4 y = *reinterpret_cast<const float4 *>(Y + i);
+                        a0 = fmaf(X[i * LD], y.x, a0);
+                        a1 = fmaf(X[(i + 1) * LD], y.y, a1);
+                        a2 = fmaf(X[(i + 2) * LD], y.z, a2);
+                        a3 = fmaf(X[(i + 3) * LD], y.w, a3);
                     }
-                    const float mine = a0 + a1;
+                    const float mine = (a0 + a1) + (a2 + a3);
                     const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-                    if (role == 0 && act && Q < bj)
-                        Vs[P + Q * LD] = (Cs[P + Q * LD] - mine + (opp ? other : -other)) * rden;
+                    if (role == 0 && act && Q < bj) Vs[P + Q * LD] = (cv - mine + (opp ? other : -other)) * rden;
                     __syncwarp();
                 }
             }
@@ -753,7 +758,7 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
                      __nv_bfloat16 *Vc, const double *U0, int ldu0)
 {
     const int n = c.n, nb = c.sc.nb;
-    const size_t leaf_smem = (size_t)leaf_buffers<MODE>() * MB * (MB + 1) * sizeof(float);
+    const size_t leaf_smem = ((size_t)leaf_buffers<MODE>() * MB * kLeafLD + 16) * sizeof(float);
     SGT_CUDA_TRY(cudaFuncSetAttribute(mixed_leaf_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)leaf_smem));
     SGT_CUDA_TRY(cudaFuncSetAttribute(mixed_leaf_kernel<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
