@@ -101,7 +101,7 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
                   const float *__restrict__ DT, const float *__restrict__ DA, const double *__restrict__ Rc,
                   const double *__restrict__ Rs, int ldr, int d, const int2 *__restrict__ tslot,
                   const double *__restrict__ PA, const double *__restrict__ PB, __nv_bfloat16 *__restrict__ Vr,
-                  __nv_bfloat16 *__restrict__ Vc, int S, int rows_pad, int ldsl)
+                  __nv_bfloat16 *__restrict__ Vc, int S, int nbk)
 {
     constexpr int LD = kLeafLD;
     constexpr int EPT = MB * MB / kLeafThreads;   // tile entries per thread
@@ -284,16 +284,19 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
         __syncthreads();
     }
 
-    // V (float64) and its bf16 splits: row slices Vr[s][row][col], column
-    // slices Vc[s][col][row].  The split runs in fp32: each remainder is
+    // V (float64) and its bf16 splits in the blocked slice layout: row
+    // slices tile (I, J) of Vr[s] (row-major), column slices tile (J, I) of
+    // Vc[s] (V^T, row-major).  The split runs in fp32: each remainder is
     // exact (V is an fp32 value and a bf16 rounding removes its leading bits)
+    const size_t tr = ((size_t)I * nbk + J) * MB * MB, tc = ((size_t)J * nbk + I) * MB * MB;
+    const size_t sstride = (size_t)nbk * nbk * MB * MB;
     for (int idx = threadIdx.x; idx < MB * bj; idx += kLeafThreads) {
         const int pr = idx % MB, q = idx / MB;
         float r = Vs[pr + q * LD];
         SGT_AT(V, ldv, r0 + pr, c0 + q) = (double)r;
         for (int s = 0; s < S; s++) {
             const __nv_bfloat16 h = __float2bfloat16_rn(r);
-            Vc[((size_t)s * rows_pad + c0 + q) * ldsl + r0 + pr] = h;
+            Vc[s * sstride + tc + q * MB + pr] = h;
             r -= __bfloat162float(h);
         }
     }
@@ -302,7 +305,7 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
         float r = Vs[pr + q * LD];
         for (int s = 0; s < S; s++) {
             const __nv_bfloat16 h = __float2bfloat16_rn(r);
-            Vr[((size_t)s * rows_pad + r0 + pr) * ldsl + c0 + q] = h;
+            Vr[s * sstride + tr + pr * MB + q] = h;
             r -= __bfloat162float(h);
         }
     }
@@ -472,21 +475,58 @@ __global__ void apply_correction_kernel(int n, double *__restrict__ U, int ldu, 
 
 // Rounding-split bf16 slices of the strictly upper part of the diagonal
 // blocks of V (U after the float64 diagonal leaves, E after the corrections'
-// diagonal leaves), in the layout the leaves write: row slices
-// Vr[s][row][col], column slices Vc[s][col][row].  One CTA per block.
+// diagonal leaves), in the blocked layout the leaves write: tile (I, I) of
+// Vr[s] (row-major) and of Vc[s] (transposed).  One CTA per block.
 __global__ void diag_slices_kernel(int n, const double *__restrict__ V, int ldv, __nv_bfloat16 *__restrict__ Vr,
-                                   __nv_bfloat16 *__restrict__ Vc, int S, int rows_pad, int ldsl)
+                                   __nv_bfloat16 *__restrict__ Vc, int S, int nbk)
 {
-    const int r0 = blockIdx.x * MB;
+    const int I = blockIdx.x, r0 = I * MB;
     const int bs = min(MB, n - r0);
+    const size_t t = ((size_t)I * nbk + I) * MB * MB, sstride = (size_t)nbk * nbk * MB * MB;
     for (int idx = threadIdx.x; idx < bs * bs; idx += blockDim.x) {
         const int i = idx % bs, j = idx / bs;
         double r = (i < j) ? SGT_AT(V, ldv, r0 + i, r0 + j) : 0.0;
         for (int s = 0; s < S; s++) {
             const __nv_bfloat16 h = __double2bfloat16(r);
-            Vr[((size_t)s * rows_pad + r0 + i) * ldsl + r0 + j] = h;
-            Vc[((size_t)s * rows_pad + r0 + j) * ldsl + r0 + i] = h;
+            Vr[s * sstride + t + i * MB + j] = h;
+            Vc[s * sstride + t + j * MB + i] = h;
             r -= (double)__bfloat162float(h);
+        }
+    }
+}
+
+// Rounding-split bf16 slices (of the fp32 value, as the leaves split) of the
+// strictly upper part of the n x n matrix M in the blocked layout: tile
+// (I, K) of R[s] (row-major) and tile (K, I) of C[s] (transposed) for every
+// block K >= I; the blocks below are never read and not written.
+__global__ void blocked_split_kernel(int n, const double *__restrict__ M, int ldm, int S, int nbk,
+                                     __nv_bfloat16 *__restrict__ R, __nv_bfloat16 *__restrict__ C)
+{
+    __shared__ float tile[MB][MB + 1];   // [column][row]
+    const int K = blockIdx.x, I = blockIdx.y;
+    if (K < I) return;
+    const size_t sstride = (size_t)nbk * nbk * MB * MB;
+    const size_t tr = ((size_t)I * nbk + K) * MB * MB, tc = ((size_t)K * nbk + I) * MB * MB;
+    for (int idx = threadIdx.x; idx < MB * MB; idx += blockDim.x) {
+        const int r = idx % MB, k = idx / MB;
+        const int gi = I * MB + r, gk = K * MB + k;
+        const float v = (gi < gk && gk < n) ? (float)SGT_AT(M, ldm, gi, gk) : 0.f;
+        tile[k][r] = v;
+        float x = v;
+        for (int s = 0; s < S; s++) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            C[s * sstride + tc + k * MB + r] = h;
+            x -= __bfloat162float(h);
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < MB * MB; idx += blockDim.x) {
+        const int k = idx % MB, r = idx / MB;
+        float x = tile[k][r];
+        for (int s = 0; s < S; s++) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            R[s * sstride + tr + r * MB + k] = h;
+            x -= __bfloat162float(h);
         }
     }
 }
@@ -664,7 +704,8 @@ struct MixedCtx {
     int2 *d_tslot;
     TcPairs pairs_split, pairs_oz;
     TcPairs *d_pairs_split, *d_pairs_oz;
-    // bf16 splits (S slices) of T and of the unknowns, row and column forms
+    // bf16 splits (S slices) of T and of the unknowns, row and column forms,
+    // blocked layout (each 64 x 64 tile contiguous)
     __nv_bfloat16 *Tr, *Tc, *Ur, *Uc, *Er, *Ec;
     float *DT32, *DA32;         // fp32 diagonal blocks for the leaves (64 x 64 each)
     // exact slices of the strictly upper parts of T and U in the gathered
@@ -745,11 +786,16 @@ P *take(Arena &ws, size_t count)
     return static_cast<P *>(ws.take(count * sizeof(P)));
 }
 
+// Blocked-layout rounding splits of the strictly upper part of M (row and
+// column forms) for the sweeps.
 signtri_status split_full(MixedCtx &c, const double *M, int ldm, __nv_bfloat16 *R, __nv_bfloat16 *C)
 {
-    signtri_status rs;
-    if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, c.S, 0, nullptr, R, c.np, c.np, c.st)) != SIGNTRI_OK) return rs;
-    return make_col_slices(c.n, c.n, M, ldm, 1, c.S, 0, nullptr, C, c.np, c.np, c.st);
+    if (c.S > 8) return SIGNTRI_ERR_BAD_ARG;
+    const int nbk = c.np / MB;
+    ProfScope ps(SIGNTRI_KC_CONVERT, c.st);
+    blocked_split_kernel<<<dim3(nbk, nbk), 256, 0, c.st>>>(c.n, M, ldm, c.S, nbk, R, C);
+    SGT_LAUNCH_CHECK();
+    return SIGNTRI_OK;
 }
 
 // One low-precision sweep: MODE 0 solves for U (into V = U), MODE 1 for E.
@@ -770,9 +816,10 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
         diag32_kernel<<<nb, 256, 0, c.st>>>(n, T, ldt, MODE == 0 ? V : U0, MODE == 0 ? ldv : ldu0, c.DT32, c.DA32);
         SGT_LAUNCH_CHECK();
     }
-    const TcSource srcT_r{c.Tr, c.S, c.np, c.np, c.np, nullptr}, srcT_c{c.Tc, c.S, c.np, c.np, c.np, nullptr};
-    const TcSource srcV_r{Vr, c.S, c.np, c.np, c.np, nullptr}, srcV_c{Vc, c.S, c.np, c.np, c.np, nullptr};
-    const TcSource srcU_r{c.Ur, c.S, c.np, c.np, c.np, nullptr}, srcU_c{c.Uc, c.S, c.np, c.np, c.np, nullptr};
+    // slices in the blocked layout: every 64 x 64 tile one contiguous 8 KB run
+    const TcSource srcT_r{c.Tr, c.S, c.np, c.np, c.np, nullptr, 1}, srcT_c{c.Tc, c.S, c.np, c.np, c.np, nullptr, 1};
+    const TcSource srcV_r{Vr, c.S, c.np, c.np, c.np, nullptr, 1}, srcV_c{Vc, c.S, c.np, c.np, c.np, nullptr, 1};
+    const TcSource srcU_r{c.Ur, c.S, c.np, c.np, c.np, nullptr, 1}, srcU_c{c.Uc, c.S, c.np, c.np, c.np, nullptr, 1};
     const TcQuadOut slots{{nullptr, nullptr, nullptr, nullptr}, 0, 0, 0};
     // K-blocks per tensor-core unit: with several unit-weight slice pairs the
     // engine keeps every slice of a K-block resident and accumulates all pairs
@@ -810,7 +857,7 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
         ProfScope ps(MODE == 0 ? SIGNTRI_KC_OFFDIAG_LEAF_F32 : SIGNTRI_KC_CORRECTION, c.st);
         mixed_leaf_kernel<MODE><<<ntiles, kLeafThreads, leaf_smem, c.st>>>(
             n, T, ldt, V, ldv, c.DT32, c.DA32, c.res_c, c.res_s, n, d, c.d_tslot + c.sc.tile_begin[d], c.PA, c.PB,
-            Vr, Vc, c.S, c.np, c.np);
+            Vr, Vc, c.S, nb);
         SGT_LAUNCH_CHECK();
     }
     return SIGNTRI_OK;
@@ -1250,7 +1297,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     if ((rs = diag_leaves_f64(n, T, ldt, U, ldu, MB, st)) != SIGNTRI_OK) return rs;
     {
         ProfScope ps(SIGNTRI_KC_CONVERT, st);
-        diag_slices_kernel<<<nb, 256, 0, st>>>(n, U, ldu, c.Ur, c.Uc, S, (int)np, (int)np);
+        diag_slices_kernel<<<nb, 256, 0, st>>>(n, U, ldu, c.Ur, c.Uc, S, nb);
         SGT_LAUNCH_CHECK();
     }
     if ((rs = sweep<0>(c, T, ldt, U, ldu, c.Ur, c.Uc, nullptr, 0)) != SIGNTRI_OK) return rs;
@@ -1316,7 +1363,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
         }
         {
             ProfScope ps(SIGNTRI_KC_CONVERT, st);
-            diag_slices_kernel<<<nb, 256, 0, st>>>(n, c.E, n, c.Er, c.Ec, S, (int)np, (int)np);
+            diag_slices_kernel<<<nb, 256, 0, st>>>(n, c.E, n, c.Er, c.Ec, S, nb);
             SGT_LAUNCH_CHECK();
         }
         if ((rs = sweep<1>(c, T, ldt, c.E, n, c.Er, c.Ec, U, ldu)) != SIGNTRI_OK) return rs;

@@ -216,6 +216,20 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float a)
     lo = __fadd_rn(lo, err);
 }
 
+// TMA coordinates of K-block kb of rows [row, row + 64) of slice sl of a
+// source with `rows` rows: plain layout (x = K offset, y = stacked row) or
+// blocked layout (64 x 64 tiles, each a contiguous run of 64 rows).
+__device__ __forceinline__ void src_coord(int blk, int nkb, int rows, int sl, int row, int kb, int &x, int &y)
+{
+    if (blk) {
+        x = 0;
+        y = ((sl * (rows >> 6) + (row >> 6)) * nkb + kb) << 6;
+    } else {
+        x = kb * 64;
+        y = sl * rows + row;
+    }
+}
+
 // Units of one job: (K-chunk, pair) in pair mode, K-chunks in resident mode.
 __device__ __forceinline__ int job_units(const TcJob &job, int chunk_kb, int npairs, int resident)
 {
@@ -234,7 +248,8 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
                    int rowsA, int rowsB, const TcJob *__restrict__ jobs, const int *__restrict__ job_off,
                    const TcPairs *__restrict__ pairs_g, int chunk_kb, const float *__restrict__ sTop,
                    const float *__restrict__ sBot, const float *__restrict__ sLeft, const float *__restrict__ sRight,
-                   double *__restrict__ out, TcQuadOut qo, int *__restrict__ err, int resident, int nsl)
+                   double *__restrict__ out, TcQuadOut qo, int *__restrict__ err, int resident, int nsl, int blk,
+                   int nkb)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -304,28 +319,36 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
                         if (resident) {
                             // [A slice 0 | ... | A slice nsl-1 | B slice 0 | ...], 16 KB each
                             mbar_expect_tx(&full[stage], 2 * nsl * (kHalfBytes / 2));
-                            const int x = kb * 64;
                             for (int sl = 0; sl < nsl; sl++) {
                                 unsigned char *a = base + sl * (kHalfBytes / 2);
                                 unsigned char *b = base + (nsl + sl) * (kHalfBytes / 2);
-                                tma_load_2d(a, &mTop, &full[stage], x, sl * rowsA + job.rt);
-                                tma_load_2d(a + 8192, &mBot, &full[stage], x, sl * rowsA + job.rb);
-                                tma_load_2d(b, &mLeft, &full[stage], x, sl * rowsB + job.cl);
-                                tma_load_2d(b + 8192, &mRight, &full[stage], x, sl * rowsB + job.cr);
+                                int x, y;
+                                src_coord(blk, nkb, rowsA, sl, job.rt, kb, x, y);
+                                tma_load_2d(a, &mTop, &full[stage], x, y);
+                                src_coord(blk, nkb, rowsA, sl, job.rb, kb, x, y);
+                                tma_load_2d(a + 8192, &mBot, &full[stage], x, y);
+                                src_coord(blk, nkb, rowsB, sl, job.cl, kb, x, y);
+                                tma_load_2d(b, &mLeft, &full[stage], x, y);
+                                src_coord(blk, nkb, rowsB, sl, job.cr, kb, x, y);
+                                tma_load_2d(b + 8192, &mRight, &full[stage], x, y);
                             }
                         } else {
                             const int nk = min(kKPS, kbe - kb);
-                            const int ya = pairs.s[p] * rowsA, yb = pairs.t[p] * rowsB;
+                            const int sa = pairs.s[p], sb = pairs.t[p];
                             mbar_expect_tx(&full[stage], nk * kHalfBytes);
                             for (int h = 0; h < nk; h++) {
                                 // stage layout: A halves [h][top 8 KB | bottom 8 KB], then B halves
                                 unsigned char *a = base + h * (kHalfBytes / 2);
                                 unsigned char *b = base + kStageBytes / 2 + h * (kHalfBytes / 2);
-                                const int x = (kb + h) * 64;
-                                tma_load_2d(a, &mTop, &full[stage], x, ya + job.rt);
-                                tma_load_2d(a + 8192, &mBot, &full[stage], x, ya + job.rb);
-                                tma_load_2d(b, &mLeft, &full[stage], x, yb + job.cl);
-                                tma_load_2d(b + 8192, &mRight, &full[stage], x, yb + job.cr);
+                                int x, y;
+                                src_coord(blk, nkb, rowsA, sa, job.rt, kb + h, x, y);
+                                tma_load_2d(a, &mTop, &full[stage], x, y);
+                                src_coord(blk, nkb, rowsA, sa, job.rb, kb + h, x, y);
+                                tma_load_2d(a + 8192, &mBot, &full[stage], x, y);
+                                src_coord(blk, nkb, rowsB, sb, job.cl, kb + h, x, y);
+                                tma_load_2d(b, &mLeft, &full[stage], x, y);
+                                src_coord(blk, nkb, rowsB, sb, job.cr, kb + h, x, y);
+                                tma_load_2d(b + 8192, &mRight, &full[stage], x, y);
                             }
                         }
                         issued++;
@@ -583,12 +606,24 @@ signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSo
     if (pairs.n <= 0 || pairs.n > kTcMaxPairs || chunk_kb <= 0 || !d_pairs) return SIGNTRI_ERR_BAD_ARG;
     signtri_status rs = get_encoder();
     if (rs != SIGNTRI_OK) return rs;
+    // all four sources in one layout; a blocked layout needs whole tiles and
+    // one K-block count
+    const int blk = top.blocked ? 1 : 0;
+    if ((bot.blocked ? 1 : 0) != blk || (left.blocked ? 1 : 0) != blk || (right.blocked ? 1 : 0) != blk)
+        return SIGNTRI_ERR_BAD_ARG;
+    if (blk && (top.cols != bot.cols || top.cols != left.cols || top.cols != right.cols || (top.cols & 63) ||
+                (top.rows & 63) || (left.rows & 63)))
+        return SIGNTRI_ERR_BAD_ARG;
+    auto map_of = [&](CUtensorMap *m, const TcSource &src) {
+        if (src.blocked)
+            return make_map(m, src.base, (long long)src.nslices * src.rows * (src.cols / 64), 64, 64);
+        return make_map(m, src.base, (long long)src.nslices * src.rows, src.cols, src.ld);
+    };
     CUtensorMap mt, mb, ml, mr;
-    if ((rs = make_map(&mt, top.base, (long long)top.nslices * top.rows, top.cols, top.ld)) != SIGNTRI_OK) return rs;
-    if ((rs = make_map(&mb, bot.base, (long long)bot.nslices * bot.rows, bot.cols, bot.ld)) != SIGNTRI_OK) return rs;
-    if ((rs = make_map(&ml, left.base, (long long)left.nslices * left.rows, left.cols, left.ld)) != SIGNTRI_OK) return rs;
-    if ((rs = make_map(&mr, right.base, (long long)right.nslices * right.rows, right.cols, right.ld)) != SIGNTRI_OK)
-        return rs;
+    if ((rs = map_of(&mt, top)) != SIGNTRI_OK) return rs;
+    if ((rs = map_of(&mb, bot)) != SIGNTRI_OK) return rs;
+    if ((rs = map_of(&ml, left)) != SIGNTRI_OK) return rs;
+    if ((rs = map_of(&mr, right)) != SIGNTRI_OK) return rs;
     if (top.rows != bot.rows || left.rows != right.rows) return SIGNTRI_ERR_BAD_ARG;
     // resident mode when every pair has the same weight and at most 3 slices
     // per operand are involved (so that a stage of all slices fits twice)
@@ -606,7 +641,7 @@ signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSo
     ProfScope ps(kernel_class, st);
     tc_blocksum_kernel<<<d_job_off ? nctas : njobs, kTcThreads, smem, st>>>(
         mt, mb, ml, mr, top.rows, left.rows, d_jobs, d_job_off, d_pairs, chunk_kb, top.scale, bot.scale, left.scale,
-        right.scale, out, qo, d_err, resident, nsl);
+        right.scale, out, qo, d_err, resident, nsl, blk, top.cols / 64);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }

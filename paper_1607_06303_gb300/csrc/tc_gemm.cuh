@@ -38,6 +38,9 @@ struct TcPairs {
 // A bf16 operand source: nslices matrices of `rows` rows (a multiple of 64,
 // zero padded) by `cols` K-contiguous columns, pitch ld elements, stacked;
 // optional per-row scale (power of two) applied to the result rows/columns.
+// blocked = 1: each matrix is stored as 64 x 64 tiles, tile (row block R,
+// K-block K) of slice s contiguous (8 KB, row-major, K fastest) at element
+// ((s * rows/64 + R) * cols/64 + K) * 4096; ld is then unused.
 struct TcSource {
     const __nv_bfloat16 *base;
     int nslices;
@@ -45,6 +48,7 @@ struct TcSource {
     int cols;
     int ld;
     const float *scale;
+    int blocked;
 };
 
 // Alternative output: quadrant q of every job written into its own
