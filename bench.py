@@ -37,10 +37,15 @@ if ROOT not in sys.path:
 METRIC = "sign(T) seconds & useful GFLOP/s at n=16384: mixed+refine vs FP64, ≤1e-12 err"
 UNIT = "GFLOP/s"
 
-# DRAM bytes per launch of the dominant kernel from an ncu capture, keyed by
-# the sha256 of the source file it came from; reported only while the source
-# is unchanged (see profiles/).
-TRAFFIC = {}
+# ncu DRAM traffic of the dominant kernel, keyed by (class, sha256 of the
+# source file it came from) and reported only while that source is unchanged
+# (captures summarised under profiles/): for block_sums_tc the ratio of
+# dram__bytes_read.sum + dram__bytes_write.sum to the algorithmic operand
+# bytes of the same launches, for the other classes bytes per launch.
+TRAFFIC = {
+    # profiles/tc_blocksum_sweep_traffic_n4096.txt: 14.20 GB over 13.48 GB algorithmic
+    ("block_sums_tc", "d69735523bdaee2b6047162907f65a13aaf3f798d6ace4fb53b43bee14d7e064"): 1.054,
+}
 
 
 def parse_args():
@@ -384,20 +389,37 @@ def main():
                 "peak_source": "float64 FMA issue rate measured live by signtri_probe_fp64_peak (no FP64 entry "
                                "in MEASURED_PEAKS.json)",
                 "share_of_step": per_class[dom]["device_ms"] / ms_total}
-    elif dom in ("residual", "block_sums_tc"):
+    elif dom == "block_sums_tc":
+        # the sweeps' block sums stream every operand panel once: bound by HBM
+        peaks, src = measured_peaks()
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        launches_dom = per_class[dom]["launches"]
+        bytes_all = st.signtri_profile_read_bytes(st.signtri.KC_BLOCK_SUMS_TC)
+        flops_all = st.signtri_profile_read_flops(st.signtri.KC_BLOCK_SUMS_TC)
+        per_launch = bytes_all / launches_dom
+        avg_ms = per_class[dom]["device_ms"] / launches_dom
+        ach = per_launch / (avg_ms * 1e-3) / 1e9
+        sha = src_sha("paper_1607_06303_gb300/csrc/tc_gemm.cu")
+        traffic = TRAFFIC.get((dom, sha))
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None if traffic is None else traffic * per_launch,
+                "kernel": "tc_blocksum_kernel (tcgen05 bf16, sweep block sums, blocked slice layout)",
+                "algorithmic_bytes_per_launch": per_launch,
+                "tensor_tflops": flops_all / launches_dom / (avg_ms * 1e-3) / 1e12,
+                "peak_source": "hbm_gbs of %s (copy bandwidth)" % src,
+                "share_of_step": per_class[dom]["device_ms"] / ms_total}
+    elif dom == "residual":
         peaks, src = measured_peaks()
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
         launches_dom = per_class[dom]["launches"]
-        cls = st.signtri.KC_RESIDUAL if dom == "residual" else st.signtri.KC_BLOCK_SUMS_TC
-        flops_all = st.signtri_profile_read_flops(cls)
+        flops_all = st.signtri_profile_read_flops(st.signtri.KC_RESIDUAL)
         per_launch = flops_all / launches_dom
         avg_ms = per_class[dom]["device_ms"] / launches_dom
         ach = per_launch / (avg_ms * 1e-3) / 1e12
         sha = src_sha("paper_1607_06303_gb300/csrc/tc_gemm.cu")
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": TRAFFIC.get((dom, sha)),
-                "kernel": "tc_blocksum_kernel (tcgen05 bf16, %s)" % ("emulated-float64 residual products"
-                                                                     if dom == "residual" else "block sums"),
+                "kernel": "tc_blocksum_kernel (tcgen05 bf16, emulated-float64 residual products)",
                 "algorithmic_flops_per_launch": per_launch,
                 "peak_source": "bf16_tflops_sustained of %s (kernel timed inside a long step)" % src,
                 "share_of_step": per_class[dom]["device_ms"] / ms_total}

@@ -261,6 +261,12 @@ signtri_status signtri_profile_read(int cls, long long *launches, double *device
    last reset: 2*64*64*64 per (slice pair, K-block, used 64x64 quadrant) of
    every tensor-core job.  Zero for classes that do not use tensor cores. */
 signtri_status signtri_profile_read_flops(int cls, double *flops);
+/* Algorithmic operand bytes that launches of class `cls` read from device
+   memory since the last reset, where the class has a byte model: for the
+   tensor-core sweeps of the mixed variants (class block_sums_tc), 8 KB per
+   (bf16 slice, 64-row panel, 64-wide K-block) over the four panels of every
+   job's K range, each read once.  Zero for the other classes. */
+signtri_status signtri_profile_read_bytes(int cls, double *bytes);
 /* Name of a kernel class ("" when out of range). */
 const char *signtri_kernel_class_name(int cls);
 /* Self-test of the bounded device waits used by the tensor-core kernels:

@@ -11,5 +11,5 @@ from .signtri import (Info, SignTriError, Status, Variant, load, sign, sign_tri,
                       signtri_kernel_class_name, signtri_probe_fp64_peak, sign_tri_noalloc,
                       signtri_reorder_by_sign, signtri_sylvester, signtri_set_rates,
                       signtri_gemm_emulated, signtri_set_refinement, signtri_set_verification,
-                      signtri_profile_read_flops, sign_tri_batched, signtri_set_cutoff_table,
+                      signtri_profile_read_flops, signtri_profile_read_bytes, sign_tri_batched, signtri_set_cutoff_table,
                       signtri_get_cutoff_table, signtri_autotune, signtri_selftest_wait)

@@ -56,6 +56,7 @@ void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st);
 // Algorithmic tensor-core flops of a launch (counted on the host).
 void prof_add_flops(int cls, double flops);
+void prof_add_bytes(int cls, double bytes);
 // While paused (stream capture), launches are counted but not timed.
 void prof_pause(bool on);
 void prof_count(int cls, long long launches);

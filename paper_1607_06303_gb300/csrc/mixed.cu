@@ -833,6 +833,8 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
         const int *coff = c.d_cta_off + c.sc.cta_begin[d];
         const int G = c.sc.nctas[d];
         const long long sum_kb = (long long)ntiles * (d + 1);
+        // operand bytes of one launch: four 64-row panels of S bf16 slices per K-block
+        const double launch_bytes = (double)sum_kb * 4 * c.S * MB * MB * 2;
         signtri_status rs;
         if (njobs > 0) {
             if (MODE == 0) {
@@ -841,17 +843,20 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
                                   c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st,
                                   tc_flops(c.pairs_split.n, sum_kb, 3), coff, G);
                 if (rs != SIGNTRI_OK) return rs;
+                prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, launch_bytes);
             } else {
                 // X^E: [E_I.; T_I.] x [T_.J | E_.J]: TL = E T, BR = T E
                 rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
                                   c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st,
                                   tc_flops(c.pairs_split.n, sum_kb, 2), coff, G);
                 if (rs != SIGNTRI_OK) return rs;
+                prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, launch_bytes);
                 // Y^E: [U0_I.; E_I.] x [E_.J | U0_.J]: TL = U0 E, BR = E U0
                 rs = tc_blocksums(srcU_r, srcV_r, srcV_c, srcU_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
                                   c.PB, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st,
                                   tc_flops(c.pairs_split.n, sum_kb, 2), coff, G);
                 if (rs != SIGNTRI_OK) return rs;
+                prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, launch_bytes);
             }
         }
         ProfScope ps(MODE == 0 ? SIGNTRI_KC_OFFDIAG_LEAF_F32 : SIGNTRI_KC_CORRECTION, c.st);

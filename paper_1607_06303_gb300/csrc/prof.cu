@@ -24,6 +24,7 @@ bool p_enabled = false;
 long long p_launches[SIGNTRI_KC_COUNT] = {};
 double p_ms[SIGNTRI_KC_COUNT] = {};
 double p_flops[SIGNTRI_KC_COUNT] = {};
+double p_bytes[SIGNTRI_KC_COUNT] = {};
 std::vector<Pending> p_pending;
 std::vector<cudaEvent_t> p_free;
 thread_local int p_open_cls = -1;
@@ -79,6 +80,12 @@ void prof_add_flops(int cls, double flops)
     if (cls >= 0 && cls < SIGNTRI_KC_COUNT) p_flops[cls] += flops;
 }
 
+void prof_add_bytes(int cls, double bytes)
+{
+    std::lock_guard<std::mutex> lk(p_mu);
+    if (cls >= 0 && cls < SIGNTRI_KC_COUNT) p_bytes[cls] += bytes;
+}
+
 void prof_end(int cls, cudaStream_t st)
 {
     std::lock_guard<std::mutex> lk(p_mu);
@@ -132,7 +139,7 @@ signtri_status signtri_profile_reset(void)
     std::lock_guard<std::mutex> lk(p_mu);
     for (auto &p : p_pending) { p_free.push_back(p.a); p_free.push_back(p.b); }
     p_pending.clear();
-    for (int i = 0; i < SIGNTRI_KC_COUNT; i++) { p_launches[i] = 0; p_ms[i] = 0.0; p_flops[i] = 0.0; }
+    for (int i = 0; i < SIGNTRI_KC_COUNT; i++) { p_launches[i] = 0; p_ms[i] = 0.0; p_flops[i] = 0.0; p_bytes[i] = 0.0; }
     return SIGNTRI_OK;
 }
 
@@ -159,6 +166,14 @@ signtri_status signtri_profile_read_flops(int cls, double *flops)
     if (cls < 0 || cls >= SIGNTRI_KC_COUNT || !flops) return SIGNTRI_ERR_BAD_ARG;
     std::lock_guard<std::mutex> lk(p_mu);
     *flops = p_flops[cls];
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_profile_read_bytes(int cls, double *bytes)
+{
+    if (cls < 0 || cls >= SIGNTRI_KC_COUNT || !bytes) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(p_mu);
+    *bytes = p_bytes[cls];
     return SIGNTRI_OK;
 }
 

@@ -92,6 +92,7 @@ _SIGNATURES = {
     "signtri_set_refinement": (_I, [ctypes.c_double, _I]),
     "signtri_set_verification": (_I, [_I]),
     "signtri_profile_read_flops": (_I, [_I, ctypes.POINTER(ctypes.c_double)]),
+    "signtri_profile_read_bytes": (_I, [_I, ctypes.POINTER(ctypes.c_double)]),
     "sign_tri_batched": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_VP), ctypes.POINTER(_I),
                               ctypes.POINTER(_VP), ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _VP]),
     "signtri_set_cutoff_table": (_I, [ctypes.POINTER(_I), _I]),
@@ -259,6 +260,14 @@ def signtri_profile_read_flops(cls: int) -> float:
     if st != 0:
         raise SignTriError(st, "signtri_profile_read_flops")
     return f.value
+
+
+def signtri_profile_read_bytes(cls: int) -> float:
+    b = ctypes.c_double(0)
+    st = load().signtri_profile_read_bytes(cls, ctypes.byref(b))
+    if st != 0:
+        raise SignTriError(st, "signtri_profile_read_bytes")
+    return b.value
 
 
 def signtri_kernel_class_name(cls: int) -> str:
