@@ -713,6 +713,7 @@ struct MixedCtx {
     // (the last 64 all zero), pitch rows_g
     int ng, rows_g;
     int *gmap, *ginv;           // original -> gathered, gathered -> original (-1 padding)
+    int *sbbase;                // gathered start of each superblock (nsb + 1 entries)
     unsigned char *pos;         // diagonal sign flags
     __nv_bfloat16 *NTgr, *NTgc;         // T, gathered layout
     __nv_bfloat16 *NTr, *NTc;           // T, original layout
@@ -760,6 +761,7 @@ size_t bytes_for(int n, int S)
     b += 2 * (size_t)kOzakiSlices * (np + 64) * np * 2 + 2 * 256;      // exact slices: T original
     b += 4 * (np + 64) * 4 + 2 * (np + 64) * 8 + 7 * 256;               // scales, tmp
     b += 4 * ngr * 4 + 4 * 256 + 2 * ngr * 4 + np + 3 * 256;            // gathered scales, maps, signs
+    b += ((size_t)(n + kSuper - 1) / kSuper + 1) * 4 + 256;             // superblock starts
     b += 2 * ngr * ngr * 8 + 2 * 256;                                   // RA, RB
     const size_t maxjobs = (size_t)kSweepCtas + nb + 8;
     b += 2 * maxjobs * 16384 * 8 + 2 * 256;                             // partials
@@ -944,6 +946,8 @@ signtri_status setup_gathered(MixedCtx &c, const double *T, int ldt)
         SGT_CUDA_TRY(cudaMemcpyAsync(c.d_res_jobs, same.data(), same.size() * sizeof(TcJob), cudaMemcpyHostToDevice,
                                      c.st));
     SGT_CUDA_TRY(cudaMemcpyAsync(c.gmap, gmap.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, c.st));
+    SGT_CUDA_TRY(cudaMemcpyAsync(c.sbbase, base.data(), (size_t)(nsb + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                                 c.st));
     SGT_CUDA_TRY(cudaMemcpyAsync(c.ginv, ginv.data(), (size_t)c.rows_g * sizeof(int), cudaMemcpyHostToDevice, c.st));
     // the host tables are pageable and local
     SGT_CUDA_TRY(cudaStreamSynchronize(c.st));
@@ -959,8 +963,8 @@ signtri_status gathered_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bf
     if (!scaled &&
         (rs = make_scales_both(c.n, M, ldm, 1, c.np + 64, c.tmpmax, c.tmpmax2, sR, sC, c.st)) != SIGNTRI_OK)
         return rs;
-    return make_gathered_slices(c.n, M, ldm, c.ginv, c.ng, kOzakiSlices, kOzakiBits, sR, sC, gR, gC, R, C, c.rows_g,
-                                c.rows_g, c.st);
+    return make_gathered_slices(c.n, M, ldm, c.ginv, c.gmap, c.sbbase, kSuper, c.ng, kOzakiSlices, kOzakiBits, sR,
+                                sC, gR, gC, R, C, c.rows_g, c.rows_g, c.st);
 }
 
 // Exact slices of the strictly upper part of M in the original layout (scales
@@ -1177,6 +1181,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     c.sUr = take<float>(ws, np + 64); c.sUc = take<float>(ws, np + 64);
     c.gTr = take<float>(ws, ngr); c.gTc = take<float>(ws, ngr); c.gUr = take<float>(ws, ngr); c.gUc = take<float>(ws, ngr);
     c.gmap = take<int>(ws, ngr); c.ginv = take<int>(ws, ngr); c.pos = take<unsigned char>(ws, np);
+    c.sbbase = take<int>(ws, (size_t)(n + kSuper - 1) / kSuper + 1);
     c.tmpmax = take<unsigned long long>(ws, np + 64);
     c.tmpmax2 = take<unsigned long long>(ws, np + 64);
     const size_t maxjobs = (size_t)std::max(c.sc.max_jobs, 1);
@@ -1214,7 +1219,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
         !c.NUc || !c.d_full_jobs || !c.sTr ||
         !c.sTc || !c.sUr || !c.sUc || !c.gTr || !c.gTc || !c.gUr || !c.gUc || !c.gmap || !c.ginv || !c.pos ||
         !c.tmpmax || !c.tmpmax2 || !c.PA || !c.PB || !c.E || !c.R || !c.RA || !c.RB || !c.norms || !c.d_res_jobs || !c.d_jobs ||
-        !c.d_pairs_split || !c.d_pairs_oz || !c.d_cta_off || !c.d_tslot || !c.DT32 || !c.DA32)
+        !c.d_pairs_split || !c.d_pairs_oz || !c.d_cta_off || !c.d_tslot || !c.DT32 || !c.DA32 || !c.sbbase)
         return SIGNTRI_ERR_NO_WORKSPACE;
     c.pairs_split = split_pairs(S);
     c.pairs_oz = ozaki_pairs_impl(kOzakiSlices, kOzakiBits);

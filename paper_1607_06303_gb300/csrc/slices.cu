@@ -195,58 +195,97 @@ __global__ void col_slices_kernel(int k, int n, const double *__restrict__ M, in
 }
 
 // Gathered layout (residual products): position g of the gathered index
-// space holds original index inv[g] (-1 = zero padding).  Row slices
-// R[s][g][h] = slice s of M[inv[g], inv[h]] (strictly upper part), written
-// for every g < rows, h < ldr (padding and the lower part as zeros), with the
-// per-row scales already gathered (scale_g[g]).
-__global__ void row_slices_gathered_kernel(const double *__restrict__ M, int ldm, const int *__restrict__ inv,
+// space holds original index inv[g] (-1 = zero padding), gmap is the inverse
+// (original -> gathered), and superblock sb of `super` consecutive original
+// indices occupies gathered positions [sbbase[sb], sbbase[sb + 1]).
+// Row slices R[s][g][h] = slice s of M[inv[g], inv[h]] (strictly upper
+// part), pitch ldr, under the gathered row scales scale_g.  CTA (64 original
+// rows i0.., 64 gathered columns h0..): one coalesced read down each of the
+// 64 source columns inv[h], then each row's 64 entries are written to its
+// gathered row gmap[i] as whole 128-byte runs.  Column tiles wholly before
+// the gathered start of the rows' superblock lie outside every residual
+// job's K range and are not written; padding rows are zeroed separately.
+__global__ void row_slices_gathered_kernel(int n, const double *__restrict__ M, int ldm, const int *__restrict__ inv,
+                                           const int *__restrict__ gmap, const int *__restrict__ sbbase, int super,
                                            int ng, int S, int bits, const float *__restrict__ scale_g,
                                            __nv_bfloat16 *__restrict__ R, int rows, int ldr)
 {
-    __shared__ double tile[2 * TS][TS + 1];   // [column][row]
-    const int g0 = blockIdx.y * TS, h0 = blockIdx.x * 2 * TS;
-    for (int y = threadIdx.y; y < 2 * TS; y += blockDim.y) {     // y: column offset
-        const int h = h0 + y, g = g0 + threadIdx.x;
-        const int i = g < ng ? inv[g] : -1, kk = h < ng ? inv[h] : -1;
-        double v = 0.0;
-        if (i >= 0 && kk >= 0 && i < kk) v = SGT_AT(M, ldm, i, kk);
-        tile[y][threadIdx.x] = v;
+    __shared__ __align__(16) double tile[64][66];   // [row][column]
+    const int i0 = blockIdx.x * 64, h0 = blockIdx.y * 64;
+    if (h0 + 64 <= sbbase[i0 / super]) return;
+    const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;   // 256 threads
+    const int i = i0 + tx;
+    for (int cc = ty; cc < 64; cc += 4) {
+        const int h = h0 + cc;
+        const int kk = h < ng ? inv[h] : -1;
+        tile[tx][cc] = (kk >= 0 && i < kk && i < n) ? SGT_AT(M, ldm, i, kk) : 0.0;
     }
     __syncthreads();
-    for (int y = threadIdx.y; y < TS; y += blockDim.y) {         // y: row offset
-        const int g = g0 + y, h = h0 + 2 * threadIdx.x;
-        if (g >= rows || h >= ldr) continue;
-        const int e = g < ng ? ilogbf(scale_g[g]) : 0;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int r = warp; r < 64; r += 8) {
+        if (i0 + r >= n) break;
+        const int g = gmap[i0 + r];
+        const int e = ilogbf(scale_g[g]);
+        const double2 v = *reinterpret_cast<const double2 *>(&tile[r][2 * lane]);
         float q0[8], q1[8];
-        exact_slices(tile[2 * threadIdx.x][y], e, S, bits, q0);
-        exact_slices(tile[2 * threadIdx.x + 1][y], e, S, bits, q1);
+        exact_slices(v.x, e, S, bits, q0);
+        exact_slices(v.y, e, S, bits, q1);
         for (int s = 0; s < S; s++)
-            *reinterpret_cast<__nv_bfloat162 *>(&R[((size_t)s * rows + g) * ldr + h]) =
+            *reinterpret_cast<__nv_bfloat162 *>(&R[((size_t)s * rows + g) * ldr + h0 + 2 * lane]) =
                 __floats2bfloat162_rn(q0[s], q1[s]);
     }
 }
 
 // Column slices C[s][g][h] = slice s of M[inv[h], inv[g]] (column inv[g]),
-// two adjacent h per thread.
-__global__ void col_slices_gathered_kernel(const double *__restrict__ M, int ldm, const int *__restrict__ inv,
-                                           int ng, int S, int bits, const float *__restrict__ scale_g,
-                                           __nv_bfloat16 *__restrict__ C, int rows, int ldc)
+// pitch ldc, under the gathered column scales scale_g.  CTA (original column
+// j, row superblock sb): the superblock's rows of column j (one contiguous
+// read) are sliced into their gathered positions of a shared-memory copy of
+// the segment [sbbase[sb], sbbase[sb + 1]) of output row gmap[j], which is
+// then written in one pass.  Segments after j's superblock lie outside every
+// residual job's K range and are not written.
+__global__ void col_slices_gathered_kernel(int n, const double *__restrict__ M, int ldm, const int *__restrict__ gmap,
+                                           const int *__restrict__ sbbase, int super, int segmax, int S, int bits,
+                                           const float *__restrict__ scale_g, __nv_bfloat16 *__restrict__ C, int rows,
+                                           int ldc)
 {
-    const int g = blockIdx.y;
-    const int h = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    if (h >= ldc) return;
-    const int j = g < ng ? inv[g] : -1;
-    const int k0 = h < ng ? inv[h] : -1, k1 = h + 1 < ng ? inv[h + 1] : -1;
-    double v0 = 0.0, v1 = 0.0;
-    if (j >= 0 && k0 >= 0 && k0 < j) v0 = SGT_AT(M, ldm, k0, j);
-    if (j >= 0 && k1 >= 0 && k1 < j) v1 = SGT_AT(M, ldm, k1, j);
-    const int e = g < ng ? ilogbf(scale_g[g]) : 0;
-    float q0[8], q1[8];
-    exact_slices(v0, e, S, bits, q0);
-    exact_slices(v1, e, S, bits, q1);
+    extern __shared__ __align__(16) unsigned char seg_raw[];
+    __nv_bfloat16 *seg = reinterpret_cast<__nv_bfloat16 *>(seg_raw);   // [s][segmax]
+    const int j = blockIdx.x, sb = blockIdx.y;
+    if (sb > j / super) return;
+    const int b0 = sbbase[sb], len = sbbase[sb + 1] - b0;
+    for (int idx = threadIdx.x; idx < S * segmax; idx += blockDim.x) seg[idx] = __float2bfloat16_rn(0.f);
+    __syncthreads();
+    const int g = gmap[j];
+    const int e = ilogbf(scale_g[g]);
+    const int i1 = min(min(n, (sb + 1) * super), j);   // strictly upper: rows i < j
+    for (int i = sb * super + threadIdx.x; i < i1; i += blockDim.x) {
+        float q[8];
+        exact_slices(SGT_AT(M, ldm, i, j), e, S, bits, q);
+        const int h = gmap[i] - b0;
+        for (int s = 0; s < S; s++) seg[s * segmax + h] = __float2bfloat16_rn(q[s]);
+    }
+    __syncthreads();
+    // len and b0 are multiples of 64: bf16 pairs
+    for (int idx = threadIdx.x; idx < S * (len / 2); idx += blockDim.x) {
+        const int s = idx / (len / 2), h = 2 * (idx % (len / 2));
+        *reinterpret_cast<__nv_bfloat162 *>(&C[((size_t)s * rows + g) * ldc + b0 + h]) =
+            *reinterpret_cast<const __nv_bfloat162 *>(&seg[s * segmax + h]);
+    }
+}
+
+// Zero rows of R and C that hold no original index (padding inside the
+// superblocks and the zero block from ng on), every slice, full pitch.
+__global__ void zero_padding_rows_kernel(const int *__restrict__ inv, int ng, int S, __nv_bfloat16 *__restrict__ R,
+                                         __nv_bfloat16 *__restrict__ C, int rows, int ld)
+{
+    const int g = blockIdx.x;
+    if (g < ng && inv[g] >= 0) return;
+    const __nv_bfloat162 z = __floats2bfloat162_rn(0.f, 0.f);
     for (int s = 0; s < S; s++)
-        *reinterpret_cast<__nv_bfloat162 *>(&C[((size_t)s * rows + g) * ldc + h]) =
-            __floats2bfloat162_rn(q0[s], q1[s]);
+        for (int h = 2 * threadIdx.x; h < ld; h += 2 * blockDim.x) {
+            *reinterpret_cast<__nv_bfloat162 *>(&R[((size_t)s * rows + g) * ld + h]) = z;
+            *reinterpret_cast<__nv_bfloat162 *>(&C[((size_t)s * rows + g) * ld + h]) = z;
+        }
 }
 
 // scale_g[g] = scale[inv[g]], 1 for padding
@@ -332,23 +371,27 @@ signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, 
     return SIGNTRI_OK;
 }
 
-signtri_status make_gathered_slices(int n, const double *M, int ldm, const int *inv, int ng, int S, int bits,
-                                    const float *sR, const float *sC, float *sRg, float *sCg, __nv_bfloat16 *R,
-                                    __nv_bfloat16 *C, int rows, int ld, cudaStream_t st)
+signtri_status make_gathered_slices(int n, const double *M, int ldm, const int *inv, const int *gmap,
+                                    const int *sbbase, int super, int ng, int S, int bits, const float *sR,
+                                    const float *sC, float *sRg, float *sCg, __nv_bfloat16 *R, __nv_bfloat16 *C,
+                                    int rows, int ld, cudaStream_t st)
 {
-    if (S > 8 || S * bits > 64) return SIGNTRI_ERR_BAD_ARG;
-    (void)n;
+    if (S > 8 || S * bits > 64 || n <= 0) return SIGNTRI_ERR_BAD_ARG;
+    if ((ld & 63) || (rows & 63) || super <= 0 || (super & 63)) return SIGNTRI_ERR_BAD_ARG;
     ProfScope ps(SIGNTRI_KC_CONVERT, st);
     gather_scales_kernel<<<(rows + 255) / 256, 256, 0, st>>>(rows, ng, inv, sR, sRg);
     SGT_LAUNCH_CHECK();
     gather_scales_kernel<<<(rows + 255) / 256, 256, 0, st>>>(rows, ng, inv, sC, sCg);
     SGT_LAUNCH_CHECK();
-    if (ld & 1) return SIGNTRI_ERR_BAD_ARG;
-    dim3 grid((ld + 2 * TS - 1) / (2 * TS), (rows + TS - 1) / TS), block(TS, 8);
-    row_slices_gathered_kernel<<<grid, block, 0, st>>>(M, ldm, inv, ng, S, bits, sRg, R, rows, ld);
+    const int nsb = (n + super - 1) / super;
+    row_slices_gathered_kernel<<<dim3((n + 63) / 64, ld / 64), 256, 0, st>>>(n, M, ldm, inv, gmap, sbbase, super, ng,
+                                                                           S, bits, sRg, R, rows, ld);
     SGT_LAUNCH_CHECK();
-    col_slices_gathered_kernel<<<dim3((ld / 2 + 255) / 256, rows), 256, 0, st>>>(M, ldm, inv, ng, S, bits, sCg, C,
-                                                                                  rows, ld);
+    const int segmax = super + 128;   // a superblock's rows, each sign class padded to 64
+    col_slices_gathered_kernel<<<dim3(n, nsb), 256, (size_t)S * segmax * sizeof(__nv_bfloat16), st>>>(
+        n, M, ldm, gmap, sbbase, super, segmax, S, bits, sCg, C, rows, ld);
+    SGT_LAUNCH_CHECK();
+    zero_padding_rows_kernel<<<rows, 256, 0, st>>>(inv, ng, S, R, C, rows, ld);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }

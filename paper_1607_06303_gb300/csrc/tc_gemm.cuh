@@ -82,12 +82,17 @@ signtri_status make_scales_both(int n, const double *M, int ldm, int tri, int no
                                 unsigned long long *tmp_cols, float *scale_rows, float *scale_cols, cudaStream_t st);
 
 // Exact slices of the strictly upper part of the n x n matrix M in a gathered
-// index space (inv[g] = original index at position g, -1 = padding, ng
-// positions used, `rows` allocated, pitch ld): per-row and per-column scales
-// sR, sC (original indices) are gathered into sRg, sCg.
-signtri_status make_gathered_slices(int n, const double *M, int ldm, const int *inv, int ng, int S, int bits,
-                                    const float *sR, const float *sC, float *sRg, float *sCg, __nv_bfloat16 *R,
-                                    __nv_bfloat16 *C, int rows, int ld, cudaStream_t st);
+// index space (inv[g] = original index at position g, -1 = padding, gmap
+// its inverse, ng positions used, `rows` allocated, pitch ld; superblock sb
+// of `super` original indices at gathered positions [sbbase[sb],
+// sbbase[sb+1])): per-row and per-column scales sR, sC (original indices)
+// are gathered into sRg, sCg.  Only what a residual job's K range can reach
+// is written: row slices from the row's superblock on, column slices up to
+// the column's superblock, padding rows zero.
+signtri_status make_gathered_slices(int n, const double *M, int ldm, const int *inv, const int *gmap,
+                                    const int *sbbase, int super, int ng, int S, int bits, const float *sR,
+                                    const float *sC, float *sRg, float *sCg, __nv_bfloat16 *R, __nv_bfloat16 *C,
+                                    int rows, int ld, cudaStream_t st);
 
 // d_job_off (device, nctas + 1 entries): CTA b runs jobs [d_job_off[b],
 // d_job_off[b+1]) back to back; null: one CTA per job.
