@@ -976,10 +976,13 @@ signtri_status exact_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bfloa
     if (!scaled &&
         (rs = make_scales_both(c.n, M, ldm, 1, c.np + 64, c.tmpmax, c.tmpmax2, sR, sC, c.st)) != SIGNTRI_OK)
         return rs;
-    if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, kOzakiBits, sR, R, c.np + 64, c.np, c.st)) !=
+    // the probe and full-residual jobs pair 64-blocks (2i, 2i+1): they never
+    // read row slices left of a row's even block or column slices past a
+    // column's block pair
+    if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, kOzakiBits, sR, R, c.np + 64, c.np, c.st, 1)) !=
         SIGNTRI_OK)
         return rs;
-    return make_col_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, kOzakiBits, sC, C, c.np + 64, c.np, c.st);
+    return make_col_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, kOzakiBits, sC, C, c.np + 64, c.np, c.st, 1);
 }
 
 signtri_status read_norms(MixedCtx &c)
@@ -1081,7 +1084,7 @@ signtri_status probe_check(MixedCtx &c, const double *T, int ldt, const double *
     const int n = c.n, np = c.np;
     signtri_status rs;
     if ((rs = make_scales(n, n, U, ldu, 1, true, np + 64, c.tmpmax, c.sUr, c.st)) != SIGNTRI_OK) return rs;
-    if ((rs = make_row_slices(n, n, U, ldu, 1, kOzakiSlices, kOzakiBits, c.sUr, c.NUr, np + 64, np, c.st)) !=
+    if ((rs = make_row_slices(n, n, U, ldu, 1, kOzakiSlices, kOzakiBits, c.sUr, c.NUr, np + 64, np, c.st, 1)) !=
         SIGNTRI_OK)
         return rs;
     const size_t blk = (size_t)n * kProbes;

@@ -39,6 +39,7 @@ __global__ void absmax_kernel(int m, int k, const double *__restrict__ M, int ld
 {
     __shared__ double tile[TS][TS + 1];
     const int i0 = blockIdx.y * TS, j0 = blockIdx.x * TS;
+    if (tri && j0 + TS - 1 <= i0) return;   // wholly on or below the diagonal
     for (int y = threadIdx.y; y < TS; y += blockDim.y) {
         const int i = i0 + threadIdx.x, j = j0 + y;
         double v = 0.0;
@@ -55,28 +56,34 @@ __global__ void absmax_kernel(int m, int k, const double *__restrict__ M, int ld
     }
 }
 
-// Row and column maxima in one pass (square n x n, tri as above).
+// Row and column maxima in one pass (square n x n, tri as above), per
+// 64 x 64 tile: coalesced column reads into shared memory, then 64 threads
+// reduce the rows and 64 the columns (128 atomics per tile).  With tri = 1
+// tiles wholly on or below the diagonal hold nothing and return at once.
 __global__ void absmax_both_kernel(int n, const double *__restrict__ M, int ldm, int tri,
                                    unsigned long long *__restrict__ out_rows, unsigned long long *__restrict__ out_cols)
 {
-    __shared__ double tile[TS][TS + 1];
-    const int i0 = blockIdx.y * TS, j0 = blockIdx.x * TS;
-    for (int y = threadIdx.y; y < TS; y += blockDim.y) {
-        const int i = i0 + threadIdx.x, j = j0 + y;
+    __shared__ double tile[64][65];   // [column][row]
+    const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+    if (tri && j0 + 63 <= i0) return;
+    const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;   // 256 threads
+    for (int c = ty; c < 64; c += 4) {
+        const int i = i0 + tx, j = j0 + c;
         double v = 0.0;
         if (i < n && j < n && (tri == 0 || i < j)) v = fabs(SGT_AT(M, ldm, i, j));
-        tile[threadIdx.x][y] = v;
+        tile[c][tx] = v;
     }
     __syncthreads();
-    if (threadIdx.y == 0) {
+    if (threadIdx.x < 64) {
         double best = 0.0;
-        for (int t = 0; t < TS; t++) best = fmax(best, tile[threadIdx.x][t]);
+        for (int t = 0; t < 64; t++) best = fmax(best, tile[t][threadIdx.x]);
         const int g = i0 + threadIdx.x;
         if (best > 0.0 && g < n) atomicMax(&out_rows[g], (unsigned long long)__double_as_longlong(best));
-    } else if (threadIdx.y == 1) {
+    } else if (threadIdx.x < 128) {
+        const int c = threadIdx.x - 64;
         double best = 0.0;
-        for (int t = 0; t < TS; t++) best = fmax(best, tile[t][threadIdx.x]);
-        const int g = j0 + threadIdx.x;
+        for (int t = 0; t < 64; t++) best = fmax(best, tile[c][t]);
+        const int g = j0 + c;
         if (best > 0.0 && g < n) atomicMax(&out_cols[g], (unsigned long long)__double_as_longlong(best));
     }
 }
@@ -133,13 +140,15 @@ __device__ __forceinline__ void round_slices(double x, int S, float *q)
 // kk < k_pad (ldr even).  Tiled transpose through shared memory, tiles of 32
 // rows x 64 columns, two adjacent columns per thread (bf16x2 stores).
 // tri: 0 = all entries, 1 = strictly upper (i < kk) only.  scale == nullptr:
-// rounding split.
+// rounding split.  skip = 1: tiles left of the even 64-block at or below a
+// row's diagonal block are not written (no 2 x 2-block job reads them).
 __global__ void row_slices_kernel(int m, int k, const double *__restrict__ M, int ldm, int tri, int S, int bits,
                                   const float *__restrict__ scale, __nv_bfloat16 *__restrict__ R, int rows_pad,
-                                  int ldr)
+                                  int ldr, int skip)
 {
     __shared__ double tile[2 * TS][TS + 1];   // [column][row]
     const int i0 = blockIdx.y * TS, k0 = blockIdx.x * 2 * TS;
+    if (skip && k0 + 2 * TS <= 2 * ((i0 / 64) / 2) * 64) return;
     for (int y = threadIdx.y; y < 2 * TS; y += blockDim.y) {     // y: column offset
         const int kk = k0 + y, i = i0 + threadIdx.x;
         double v = 0.0;
@@ -167,14 +176,17 @@ __global__ void row_slices_kernel(int m, int k, const double *__restrict__ M, in
 
 // Column slices of a k x n column-major matrix: C[s][j][kk] (same order as
 // the source, no transpose), two adjacent kk per thread (ldc even).
-// tri: 1 = strictly upper (kk < j) only.
+// tri: 1 = strictly upper (kk < j) only.  skip = 1: entries past the end of
+// the column's even 64-block pair are not written (no 2 x 2-block job reads
+// them).
 __global__ void col_slices_kernel(int k, int n, const double *__restrict__ M, int ldm, int tri, int S, int bits,
                                   const float *__restrict__ scale, __nv_bfloat16 *__restrict__ C, int rows_pad,
-                                  int ldc)
+                                  int ldc, int skip)
 {
     const int j = blockIdx.y;
     const int kk = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (kk >= ldc) return;
+    if (skip && kk >= (2 * ((j / 64) / 2) + 2) * 64) return;
     double v0 = 0.0, v1 = 0.0;
     if (j < n) {
         if (kk < k && (tri == 0 || kk < j)) v0 = SGT_AT(M, ldm, kk, j);
@@ -337,8 +349,7 @@ signtri_status make_scales_both(int n, const double *M, int ldm, int tri, int no
     SGT_CUDA_TRY(cudaMemsetAsync(tmp_rows, 0, (size_t)nout * sizeof(unsigned long long), st));
     SGT_CUDA_TRY(cudaMemsetAsync(tmp_cols, 0, (size_t)nout * sizeof(unsigned long long), st));
     ProfScope ps(SIGNTRI_KC_CONVERT, st);
-    dim3 grid((n + TS - 1) / TS, (n + TS - 1) / TS), block(TS, 8);
-    absmax_both_kernel<<<grid, block, 0, st>>>(n, M, ldm, tri, tmp_rows, tmp_cols);
+    absmax_both_kernel<<<dim3((n + 63) / 64, (n + 63) / 64), 256, 0, st>>>(n, M, ldm, tri, tmp_rows, tmp_cols);
     SGT_LAUNCH_CHECK();
     pow2_scale_kernel<<<(nout + 255) / 256, 256, 0, st>>>(nout, tmp_rows, scale_rows);
     SGT_LAUNCH_CHECK();
@@ -348,25 +359,25 @@ signtri_status make_scales_both(int n, const double *M, int ldm, int tri, int no
 }
 
 signtri_status make_row_slices(int m, int k, const double *M, int ldm, int tri, int S, int bits, const float *scale,
-                               __nv_bfloat16 *R, int rows_pad, int ldr, cudaStream_t st)
+                               __nv_bfloat16 *R, int rows_pad, int ldr, cudaStream_t st, int skip)
 {
     if (S > 8 || S * bits > 64) return SIGNTRI_ERR_BAD_ARG;
     if (ldr & 1) return SIGNTRI_ERR_BAD_ARG;
     dim3 grid((ldr + 2 * TS - 1) / (2 * TS), (rows_pad + TS - 1) / TS), block(TS, 8);
     ProfScope ps(SIGNTRI_KC_CONVERT, st);
-    row_slices_kernel<<<grid, block, 0, st>>>(m, k, M, ldm, tri, S, bits, scale, R, rows_pad, ldr);
+    row_slices_kernel<<<grid, block, 0, st>>>(m, k, M, ldm, tri, S, bits, scale, R, rows_pad, ldr, skip);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }
 
 signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, int S, int bits, const float *scale,
-                               __nv_bfloat16 *C, int rows_pad, int ldc, cudaStream_t st)
+                               __nv_bfloat16 *C, int rows_pad, int ldc, cudaStream_t st, int skip)
 {
     if (S > 8 || S * bits > 64) return SIGNTRI_ERR_BAD_ARG;
     if (ldc & 1) return SIGNTRI_ERR_BAD_ARG;
     dim3 grid((ldc / 2 + 255) / 256, rows_pad);
     ProfScope ps(SIGNTRI_KC_CONVERT, st);
-    col_slices_kernel<<<grid, 256, 0, st>>>(k, n, M, ldm, tri, S, bits, scale, C, rows_pad, ldc);
+    col_slices_kernel<<<grid, 256, 0, st>>>(k, n, M, ldm, tri, S, bits, scale, C, rows_pad, ldc, skip);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }

@@ -71,10 +71,12 @@ TcPairs ozaki_pairs_impl(int S, int bits);
 TcPairs split_pairs(int S);
 // Row / column slices: exact integer slices of `bits` bits under the
 // power-of-two scales when scale != nullptr, else a rounding split.
+// skip = 1 (square upper triangular M, consumers whose jobs pair 64-blocks
+// 2i, 2i+1): the parts no such job reads are not written.
 signtri_status make_row_slices(int m, int k, const double *M, int ldm, int tri, int S, int bits, const float *scale,
-                               __nv_bfloat16 *R, int rows_pad, int ldr, cudaStream_t st);
+                               __nv_bfloat16 *R, int rows_pad, int ldr, cudaStream_t st, int skip = 0);
 signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, int S, int bits, const float *scale,
-                               __nv_bfloat16 *C, int rows_pad, int ldc, cudaStream_t st);
+                               __nv_bfloat16 *C, int rows_pad, int ldc, cudaStream_t st, int skip = 0);
 
 // Power-of-two row and column scales of the n x n matrix M (tri = 1: its
 // strictly upper part) in one pass; tmp_rows, tmp_cols, scale_* hold nout.
