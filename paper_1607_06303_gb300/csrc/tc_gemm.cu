@@ -555,6 +555,318 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
     }
 }
 
+// ---------------------------------------------------------------------------
+// Grouped pair mode: slice pairs (s, t0), (s, t1) with the same A slice run
+// as one N = 256 MMA, A_s x [B_t0 | B_t1]^T, the two 128-column halves of the
+// accumulator being the two pairs' unit sums (each exact, as in pair mode).
+// Per MMA the tensor core then reads 12 KB of operands for 2 x 128 x 128 x 16
+// products instead of 16 KB, and a K-block stage is written once for two
+// pairs: shared-memory traffic per product drops by a quarter, which is what
+// bounds pair mode.  A pair without a partner runs alone (N = 128).  Two TMEM
+// accumulators of 256 columns fill the TMEM, so the fp32 hi parts of the
+// result live in shared memory (thread-private columns) and the lo parts in
+// registers.  Warp roles, job lists and outputs as in tc_blocksum_kernel.
+
+constexpr int kP2Stages = 3;
+constexpr int kP2StageBytes = 3 * 16384;          // A | B_t0 | B_t1 for one K-block
+constexpr int kP2HiBytes = 512 * 32 * 4;           // 32 hi values per epilogue thread
+
+struct TcGroups {
+    int n;
+    int s[kTcMaxPairs], t0[kTcMaxPairs], t1[kTcMaxPairs];   // t1 < 0: single pair
+    float w0[kTcMaxPairs], w1[kTcMaxPairs];
+};
+
+__device__ __forceinline__ void mma_bf16_n(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+tc_pair2_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_constant__ CUtensorMap mBot,
+                const __grid_constant__ CUtensorMap mLeft, const __grid_constant__ CUtensorMap mRight, int rowsA,
+                int rowsB, const TcJob *__restrict__ jobs, const int *__restrict__ job_off,
+                const TcPairs *__restrict__ pairs_g, int chunk_kb, const float *__restrict__ sTop,
+                const float *__restrict__ sBot, const float *__restrict__ sLeft, const float *__restrict__ sRight,
+                double *__restrict__ out, TcQuadOut qo, int *__restrict__ err, int blk, int nkb)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    float *his = reinterpret_cast<float *>(smem + kP2Stages * kP2StageBytes);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kP2Stages * kP2StageBytes + kP2HiBytes);
+    uint64_t *empty = full + kP2Stages;
+    uint64_t *tfull = empty + kP2Stages;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *done_bar = tempty + 2;
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(done_bar + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+    TcGroups *grp_s = reinterpret_cast<TcGroups *>(smem + kP2Stages * kP2StageBytes + kP2HiBytes + 512);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int j0 = job_off ? job_off[blockIdx.x] : (int)blockIdx.x;
+    const int j1 = job_off ? job_off[blockIdx.x + 1] : (int)blockIdx.x + 1;
+    if (threadIdx.x == 0) {
+        // group the pairs by A slice, in list order: each pair takes the next
+        // unused pair with the same s as its partner
+        const TcPairs &pp = *pairs_g;
+        bool used[kTcMaxPairs];
+        for (int p = 0; p < pp.n; p++) used[p] = false;
+        int ng = 0;
+        for (int p = 0; p < pp.n; p++) {
+            if (used[p]) continue;
+            used[p] = true;
+            int q = -1;
+            for (int r = p + 1; r < pp.n && q < 0; r++)
+                if (!used[r] && pp.s[r] == pp.s[p]) q = r;
+            grp_s->s[ng] = pp.s[p];
+            grp_s->t0[ng] = pp.t[p];
+            grp_s->w0[ng] = pp.w[p];
+            if (q >= 0) {
+                used[q] = true;
+                grp_s->t1[ng] = pp.t[q];
+                grp_s->w1[ng] = pp.w[q];
+            } else {
+                grp_s->t1[ng] = -1;
+                grp_s->w1[ng] = 0.f;
+            }
+            ng++;
+        }
+        grp_s->n = ng;
+    }
+    __syncthreads();
+    const TcGroups &grp = *grp_s;
+    const int ngrp = grp.n;
+    long long total_units = 0;
+    for (int j = j0; j < j1; j++) total_units += job_units(jobs[j], chunk_kb, ngrp, 0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kP2Stages; s++) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < 2; b++) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 16); }
+        mbar_init(done_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_holder))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+
+    if (warp == 0) {
+        if (lane == 0 && total_units > 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&mTop) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&mBot) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&mLeft) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&mRight) : "memory");
+            int stage = 0;
+            uint32_t phase = 0;
+            long long issued = 0;
+            bool ok = true;
+            for (int j = j0; j < j1 && ok; j++) {
+                const TcJob job = jobs[j];
+                const int nu = job_units(job, chunk_kb, ngrp, 0);
+                for (int u = 0; u < nu && ok; u++) {
+                    // chunk-major: the groups of one K-chunk reuse its panels in L2
+                    const int c = u / ngrp, p = u % ngrp;
+                    const int sa = grp.s[p], tb0 = grp.t0[p], tb1 = grp.t1[p];
+                    const int kbs = job.kb0 + c * chunk_kb, kbe = min(kbs + chunk_kb, job.kb1);
+                    for (int kb = kbs; kb < kbe; kb++) {
+                        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) { ok = false; break; }
+                        unsigned char *base = smem + stage * kP2StageBytes;
+                        mbar_expect_tx(&full[stage], tb1 >= 0 ? 3 * 16384 : 2 * 16384);
+                        int x, y;
+                        src_coord(blk, nkb, rowsA, sa, job.rt, kb, x, y);
+                        tma_load_2d(base, &mTop, &full[stage], x, y);
+                        src_coord(blk, nkb, rowsA, sa, job.rb, kb, x, y);
+                        tma_load_2d(base + 8192, &mBot, &full[stage], x, y);
+                        src_coord(blk, nkb, rowsB, tb0, job.cl, kb, x, y);
+                        tma_load_2d(base + 16384, &mLeft, &full[stage], x, y);
+                        src_coord(blk, nkb, rowsB, tb0, job.cr, kb, x, y);
+                        tma_load_2d(base + 24576, &mRight, &full[stage], x, y);
+                        if (tb1 >= 0) {
+                            src_coord(blk, nkb, rowsB, tb1, job.cl, kb, x, y);
+                            tma_load_2d(base + 32768, &mLeft, &full[stage], x, y);
+                            src_coord(blk, nkb, rowsB, tb1, job.cr, kb, x, y);
+                            tma_load_2d(base + 40960, &mRight, &full[stage], x, y);
+                        }
+                        issued++;
+                        if (++stage == kP2Stages) { stage = 0; phase ^= 1; }
+                    }
+                }
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                atomicExch(err, 1);
+                const long long tail = issued < kP2Stages ? issued : kP2Stages;
+                for (long long i = 0; i < tail; i++) {
+                    if (stage == 0) { stage = kP2Stages - 1; phase ^= 1; } else stage--;
+                    const uint32_t a = smem_u32(&full[stage]);
+                    const long long t0 = clock64();
+                    while (clock64() - t0 < kWaitCycles) {
+                        uint32_t done;
+                        asm volatile(
+                            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                            " selp.u32 %0, 1, 0, p;\n}\n"
+                            : "=r"(done)
+                            : "r"(a), "r"(phase)
+                            : "memory");
+                        if (done) break;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && total_units > 0) {
+            const uint32_t idesc256 = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            int g = 0;
+            for (int j = j0; j < j1 && ok; j++) {
+                const TcJob job = jobs[j];
+                const int nu = job_units(job, chunk_kb, ngrp, 0);
+                for (int u = 0; u < nu && ok; u++, g++) {
+                    const int buf = g & 1;
+                    const uint32_t tphase = (uint32_t)((g >> 1) & 1);
+                    if (!mbar_wait(&tempty[buf], tphase ^ 1, abort_flag)) { ok = false; break; }
+                    fence_after();
+                    const uint32_t d = tmem_base + (uint32_t)(buf * 256);
+                    const int c = u / ngrp, p = u % ngrp;
+                    const uint32_t idesc = grp.t1[p] >= 0 ? idesc256 : kIdesc;
+                    const int kbs = job.kb0 + c * chunk_kb, kbe = min(kbs + chunk_kb, job.kb1);
+                    for (int kb = kbs; kb < kbe; kb++) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag)) { ok = false; break; }
+                        fence_after();
+                        unsigned char *base = smem + stage * kP2StageBytes;
+                        const uint64_t ad = smem_desc(base), bd = smem_desc(base + 16384);
+#pragma unroll
+                        for (int k = 0; k < 4; k++)
+                            mma_bf16_n(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc,
+                                       (kb > kbs || k > 0) ? 1u : 0u);
+                        mma_commit(&empty[stage]);
+                        if (++stage == kP2Stages) { stage = 0; phase ^= 1; }
+                    }
+                    if (!ok) break;
+                    mma_commit(&tfull[buf]);
+                }
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                atomicExch(err, 1);
+            }
+            mma_commit(done_bar);
+        }
+    } else {
+        const int q = warp & 3;                 // TMEM lane quadrant this warp may read
+        const int cg = (warp - 2) >> 2;         // 32-column group 0..3
+        const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
+        const int row = 32 * q + lane;
+        const int r = row & 63;
+        const bool bottom = row >= 64;
+        const int half = cg >> 1;
+        const int c0 = (cg & 1) * 32;
+        const int quad = (bottom ? 2 : 0) + half;
+        const bool quad_mode = qo.m[0] || qo.m[1] || qo.m[2] || qo.m[3];
+        float *hi = his + (threadIdx.x - 64);   // hi[i * 512]: this thread's column i
+        bool ok = true;
+        int g = 0;
+        for (int j = j0; j < j1 && ok; j++) {
+            const int nu = job_units(jobs[j], chunk_kb, ngrp, 0);
+            float lo[32];
+#pragma unroll
+            for (int i = 0; i < 32; i++) lo[i] = 0.f;
+            for (int u = 0; u < nu && ok; u++, g++) {
+                const int buf = g & 1;
+                const uint32_t tphase = (uint32_t)((g >> 1) & 1);
+                if (!mbar_wait(&tfull[buf], tphase, abort_flag)) { ok = false; break; }
+                fence_after();
+                const int p = u % ngrp;
+                const float w0 = grp.w0[p], w1 = grp.w1[p];
+                const bool two = grp.t1[p] >= 0;
+                const uint32_t taddr = lane_base + (uint32_t)(buf * 256 + cg * 32);
+#pragma unroll
+                for (int cc = 0; cc < 32; cc += 16) {
+                    uint32_t v0[16], v1[16];
+                    tmem_ld16_nowait(taddr + cc, v0);
+                    if (two) tmem_ld16_nowait(taddr + 128 + cc, v1);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        float h = (u == 0) ? __fmul_rn(__uint_as_float(v0[i]), w0) : hi[(cc + i) * 512];
+                        if (u > 0) df_add(h, lo[cc + i], __fmul_rn(__uint_as_float(v0[i]), w0));
+                        if (two) df_add(h, lo[cc + i], __fmul_rn(__uint_as_float(v1[i]), w1));
+                        hi[(cc + i) * 512] = h;
+                    }
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
+            }
+            if (!ok) break;
+            const TcJob job = jobs[j];
+            double srow = 1.0;
+            if (bottom) { if (sBot) srow = sBot[job.rb + r]; }
+            else if (sTop) srow = sTop[job.rt + r];
+            const float *scol = half ? sRight : sLeft;
+            const int cbase = (half ? job.cr : job.cl) + c0;
+            double *o = nullptr;
+            float2 *o2 = nullptr;
+            if (quad_mode) {
+                o = qo.m[quad];
+                const int grow = (bottom ? job.rb : job.rt) + r;
+                if (grow >= qo.nrows) o = nullptr;
+                if (o) o += (size_t)grow + (size_t)cbase * qo.ld + (size_t)job.slot * qo.slot_stride;
+            } else {
+                o2 = reinterpret_cast<float2 *>(out) + (size_t)job.slot * 16384 + (size_t)quad * 4096 +
+                     (size_t)c0 * 64 + r;
+            }
+            const float srow_f = (float)srow;
+#pragma unroll
+            for (int i = 0; i < 32; i++) {
+                const float h = nu > 0 ? hi[i * 512] : 0.f;
+                const float sc = __fmul_rn(srow_f, scol ? scol[cbase + i] : 1.f);
+                const float hs = __fmul_rn(h, sc), ls = __fmul_rn(lo[i], sc);
+                if (o2) o2[(size_t)i * 64] = make_float2(hs, ls);
+                else if (o && cbase + i < qo.ncols) o[(size_t)i * qo.ld] = (double)hs + (double)ls;
+            }
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicExch(err, 1);
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        if (total_units > 0) {
+            const uint32_t a = smem_u32(done_bar);
+            const long long t0 = clock64();
+            while (clock64() - t0 < kWaitCycles) {
+                uint32_t done;
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                    : "=r"(done)
+                    : "r"(a), "r"(0u)
+                    : "memory");
+                if (done) break;
+            }
+        }
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 signtri_status get_encoder()
@@ -596,6 +908,11 @@ signtri_status wait_selftest(int arrive, long long limit, int *d_err, cudaStream
 
 size_t tc_smem_bytes() { return (size_t)kStages * kStageBytes + 1024 + 512 + sizeof(TcPairs) + 64; }
 
+size_t tc_pair2_smem_bytes()
+{
+    return (size_t)kP2Stages * kP2StageBytes + kP2HiBytes + 1024 + 512 + sizeof(TcGroups) + 64;
+}
+
 signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSource &left, const TcSource &right,
                             const TcJob *d_jobs, int njobs, const TcPairs &pairs, const TcPairs *d_pairs, int chunk_kb,
                             double *out, const TcQuadOut &qo, int *d_err, int kernel_class, cudaStream_t st,
@@ -635,6 +952,21 @@ signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSo
     }
     const int resident = (same_w && pairs.n > 1 && nsl <= 3 && nsl <= top.nslices && nsl <= bot.nslices &&
                           nsl <= left.nslices && nsl <= right.nslices) ? 1 : 0;
+    // grouped pair mode when pairs with unequal weights share A slices
+    bool share = false;
+    for (int p = 0; p < pairs.n && !share; p++)
+        for (int q = p + 1; q < pairs.n && !share; q++) share = pairs.s[p] == pairs.s[q];
+    if (!resident && share) {
+        const size_t smem2 = tc_pair2_smem_bytes();
+        SGT_CUDA_TRY(cudaFuncSetAttribute(tc_pair2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+        prof_add_flops(kernel_class, useful_flops);
+        ProfScope ps(kernel_class, st);
+        tc_pair2_kernel<<<d_job_off ? nctas : njobs, kTcThreads, smem2, st>>>(
+            mt, mb, ml, mr, top.rows, left.rows, d_jobs, d_job_off, d_pairs, chunk_kb, top.scale, bot.scale,
+            left.scale, right.scale, out, qo, d_err, blk, top.cols / 64);
+        SGT_LAUNCH_CHECK();
+        return SIGNTRI_OK;
+    }
     const size_t smem = tc_smem_bytes();
     SGT_CUDA_TRY(cudaFuncSetAttribute(tc_blocksum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     prof_add_flops(kernel_class, useful_flops);
