@@ -52,7 +52,7 @@ struct Arena {
 };
 
 // Launch accounting (prof.cu): bracket every library launch.
-void prof_begin(int cls, cudaStream_t st);
+void prof_begin(int cls, cudaStream_t st, bool count = true);
 void prof_end(int cls, cudaStream_t st);
 // Algorithmic tensor-core flops of a launch (counted on the host).
 void prof_add_flops(int cls, double flops);
@@ -61,12 +61,21 @@ void prof_add_bytes(int cls, double bytes);
 void prof_pause(bool on);
 void prof_count(int cls, long long launches);
 
+// Brackets a launch (or, with count = false, a group of launches that count
+// themselves) with events on `s`; timed = false only counts the launch.
 struct ProfScope {
     int cls;
     cudaStream_t st;
-    ProfScope(int c, cudaStream_t s) : cls(c), st(s) { prof_begin(c, s); }
-    ~ProfScope() { prof_end(cls, st); }
+    bool timed;
+    ProfScope(int c, cudaStream_t s, bool t = true, bool count = true) : cls(c), st(s), timed(t)
+    {
+        if (timed) prof_begin(c, s, count);
+        else if (count) prof_count(c, 1);
+    }
+    ~ProfScope() { if (timed) prof_end(cls, st); }
 };
+// Kernel-class flag for launches inside an already timed group: counted, not timed.
+constexpr int kProfUntimed = 0x1000;
 
 // Scan / init kernels (scan.cu)
 signtri_status launch_inertia_scan(int n, const double *T, int ldt, ScanResult *d_out,

@@ -622,10 +622,14 @@ __global__ void zero_kernel(size_t count, double *__restrict__ p)
 
 // ------------------------------------------------------------ host side ---
 
-// Block sums of one anti-diagonal, split evenly over kSweepCtas persistent
-// CTAs (the tiles' K-blocks in a row, cut into equal ranges; a CTA's range
-// may cross tile boundaries): CTA c's partial for tile t goes to slot c + t,
-// and tile t's partials are the slots first(t)+t .. last(t)+t (in K order).
+// Block sums of one anti-diagonal, split evenly over G persistent CTAs (the
+// tiles' K-blocks in a row, cut into equal ranges; a CTA's range may cross
+// tile boundaries): CTA c's partial for tile t goes to slot c + t, and tile
+// t's partials are the slots first(t)+t .. last(t)+t (in K order).  The
+// initial sweep's single launch per anti-diagonal takes kSweepCtas CTAs; the
+// correction's two launches run side by side with half as many each, on the
+// same split, so that the CTA pairs that read the same E panels at the same
+// time share them through L2.
 constexpr int kSweepCtas = 152;
 
 struct Schedule {
@@ -640,7 +644,7 @@ struct Schedule {
     int max_jobs = 0;           // partial slots needed by one diagonal
 };
 
-void build_schedule(int n, Schedule &sc)
+void build_schedule(int n, int gmax, Schedule &sc)
 {
     const int nb = (n + MB - 1) / MB;
     sc.nb = nb;
@@ -664,7 +668,7 @@ void build_schedule(int n, Schedule &sc)
             for (int t = 0; t < ntiles; t++) sc.tslot.push_back(make_int2(0, 0));
             continue;
         }
-        const int G = (int)std::min<long long>(kSweepCtas, W);
+        const int G = (int)std::min<long long>(gmax, W);
         sc.nctas[d] = G;
         const int base = (int)sc.jobs.size();
         for (int c = 0; c < G; c++) {
@@ -698,10 +702,12 @@ struct MixedCtx {
     int n, np, S;
     cudaStream_t st;
     int *d_err;
-    Schedule sc;
-    TcJob *d_jobs;
-    int *d_cta_off;
-    int2 *d_tslot;
+    Schedule sc, sc2;           // initial sweep; correction (two launches side by side)
+    TcJob *d_jobs, *d_jobs2;
+    int *d_cta_off, *d_cta_off2;
+    int2 *d_tslot, *d_tslot2;
+    cudaStream_t side;          // second stream of the correction launches (null: one stream)
+    cudaEvent_t ev_fork, ev_join;
     TcPairs pairs_split, pairs_oz;
     TcPairs *d_pairs_split, *d_pairs_oz;
     // bf16 splits (S slices) of T and of the unknowns, row and column forms,
@@ -772,9 +778,9 @@ size_t bytes_for(int n, int S)
     b += pairs_max * pairs_max * sizeof(TcJob) + 256;                   // needed-residual jobs
     const size_t nbp = (nb + 1) / 2;
     b += nbp * (nbp + 1) / 2 * sizeof(TcJob) + 256;                     // full-residual jobs
-    b += nb * (size_t)(kSweepCtas + nb) * sizeof(TcJob) + 256;          // wavefront jobs (bound)
-    b += nb * (size_t)(kSweepCtas + 1) * sizeof(int) + 256;              // per-CTA job ranges
-    b += (size_t)nb * nb * sizeof(int2) + 256;                           // per-tile partial slots
+    b += 2 * (nb * (size_t)(kSweepCtas + nb) * sizeof(TcJob) + 256);     // wavefront jobs (bound), 2 schedules
+    b += 2 * (nb * (size_t)(kSweepCtas + 1) * sizeof(int) + 256);         // per-CTA job ranges
+    b += 2 * ((size_t)nb * nb * sizeof(int2) + 256);                      // per-tile partial slots
     b += 3 * sizeof(TcPairs) + 768;
     b += 13 * (size_t)n * kProbes * 8 + 4 * 256;                       // probe Z, W1, W2, product halves
     b += (1 + 2 * (size_t)kOzakiSlices) * kProbes * np * 2 + 3 * 256;  // their slices
@@ -828,15 +834,22 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
     // into one unit, so 2 K-blocks keep each fp32 accumulation short; a single
     // pair takes long units
     const int chunk = c.pairs_split.n > 1 ? 2 : 16;
+    // the correction's two launches per anti-diagonal run side by side on
+    // their own half-width schedule when a second stream is available
+    const bool pair = (MODE == 1) && c.side != nullptr;
+    const Schedule &sc = pair ? c.sc2 : c.sc;
+    const TcJob *d_jobs = pair ? c.d_jobs2 : c.d_jobs;
+    const int *d_coff = pair ? c.d_cta_off2 : c.d_cta_off;
+    const int2 *d_tslot = pair ? c.d_tslot2 : c.d_tslot;
     for (int d = 1; d < nb; d++) {
         const int ntiles = nb - d;
-        const int njobs = c.sc.job_off[d + 1] - c.sc.job_off[d];
-        const TcJob *jobs = c.d_jobs + c.sc.job_off[d];
-        const int *coff = c.d_cta_off + c.sc.cta_begin[d];
-        const int G = c.sc.nctas[d];
+        const int njobs = sc.job_off[d + 1] - sc.job_off[d];
+        const TcJob *jobs = d_jobs + sc.job_off[d];
+        const int *coff = d_coff + sc.cta_begin[d];
+        const int G = sc.nctas[d];
         const long long sum_kb = (long long)ntiles * (d + 1);
-        // operand bytes of one launch: four 64-row panels of S bf16 slices per K-block
-        const double launch_bytes = (double)sum_kb * 4 * c.S * MB * MB * 2;
+        // operand bytes: 64-row panels of S bf16 slices per K-block, each read once
+        const double panel_bytes = (double)sum_kb * c.S * MB * MB * 2;
         signtri_status rs;
         if (njobs > 0) {
             if (MODE == 0) {
@@ -845,25 +858,36 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
                                   c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st,
                                   tc_flops(c.pairs_split.n, sum_kb, 3), coff, G);
                 if (rs != SIGNTRI_OK) return rs;
-                prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, launch_bytes);
+                prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, 4 * panel_bytes);
             } else {
-                // X^E: [E_I.; T_I.] x [T_.J | E_.J]: TL = E T, BR = T E
+                // X^E: [E_I.; T_I.] x [T_.J | E_.J]: TL = E T, BR = T E, and
+                // Y^E: [U0_I.; E_I.] x [E_.J | U0_.J]: TL = U0 E, BR = E U0.  Side by side
+                // (same split, CTA c of each on the same tiles and K-blocks at the
+                // same time) they read the E panels once: six panels for both.
+                ProfScope pg(SIGNTRI_KC_BLOCK_SUMS_TC, c.st, pair, false);
+                const int cls = pair ? (SIGNTRI_KC_BLOCK_SUMS_TC | kProfUntimed) : SIGNTRI_KC_BLOCK_SUMS_TC;
+                cudaStream_t sy = c.st;
+                if (pair) {
+                    SGT_CUDA_TRY(cudaEventRecord(c.ev_fork, c.st));
+                    SGT_CUDA_TRY(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
+                    sy = c.side;
+                }
                 rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
-                                  c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st,
-                                  tc_flops(c.pairs_split.n, sum_kb, 2), coff, G);
+                                  c.PA, slots, c.d_err, cls, c.st, tc_flops(c.pairs_split.n, sum_kb, 2), coff, G);
                 if (rs != SIGNTRI_OK) return rs;
-                prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, launch_bytes);
-                // Y^E: [U0_I.; E_I.] x [E_.J | U0_.J]: TL = U0 E, BR = E U0
                 rs = tc_blocksums(srcU_r, srcV_r, srcV_c, srcU_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
-                                  c.PB, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st,
-                                  tc_flops(c.pairs_split.n, sum_kb, 2), coff, G);
+                                  c.PB, slots, c.d_err, cls, sy, tc_flops(c.pairs_split.n, sum_kb, 2), coff, G);
                 if (rs != SIGNTRI_OK) return rs;
-                prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, launch_bytes);
+                if (pair) {
+                    SGT_CUDA_TRY(cudaEventRecord(c.ev_join, c.side));
+                    SGT_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_join, 0));
+                }
+                prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, (pair ? 6 : 8) * panel_bytes);
             }
         }
         ProfScope ps(MODE == 0 ? SIGNTRI_KC_OFFDIAG_LEAF_F32 : SIGNTRI_KC_CORRECTION, c.st);
         mixed_leaf_kernel<MODE><<<ntiles, kLeafThreads, leaf_smem, c.st>>>(
-            n, T, ldt, V, ldv, c.DT32, c.DA32, c.res_c, c.res_s, n, d, c.d_tslot + c.sc.tile_begin[d], c.PA, c.PB,
+            n, T, ldt, V, ldv, c.DT32, c.DA32, c.res_c, c.res_s, n, d, d_tslot + sc.tile_begin[d], c.PA, c.PB,
             Vr, Vc, c.S, nb);
         SGT_LAUNCH_CHECK();
     }
@@ -1156,6 +1180,32 @@ signtri_status probe_check(MixedCtx &c, const double *T, int ldt, const double *
 
 }  // namespace
 
+// The correction's second stream and its fork / join events, one set per
+// device, created on first use (the library's calls are serialized).
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+SideStream g_side[64];
+
+signtri_status side_stream(MixedCtx &c)
+{
+    c.side = nullptr;
+    int dev = 0;
+    SGT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return SIGNTRI_OK;
+    SideStream &g = g_side[dev];
+    if (!g.s) {
+        SGT_CUDA_TRY(cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking));
+        SGT_CUDA_TRY(cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming));
+        SGT_CUDA_TRY(cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming));
+    }
+    c.side = g.s;
+    c.ev_fork = g.fork;
+    c.ev_join = g.join;
+    return SIGNTRI_OK;
+}
+
 size_t mixed_workspace_bytes(int n, int S) { return n > 0 ? bytes_for(n, S) + (64 << 10) : 0; }
 
 signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, int S, const MixedParams &prm,
@@ -1167,7 +1217,8 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     c.S = S;
     c.st = st;
     c.d_err = d_err;
-    build_schedule(n, c.sc);
+    build_schedule(n, kSweepCtas, c.sc);
+    build_schedule(n, kSweepCtas / 2, c.sc2);
     const int nb = c.sc.nb;
     const size_t np = c.np;
     const size_t split_elems = (size_t)S * np * np;
@@ -1201,6 +1252,9 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     c.d_jobs = take<TcJob>(ws, std::max<size_t>(c.sc.jobs.size(), 1));
     c.d_cta_off = take<int>(ws, std::max<size_t>(c.sc.cta_off.size(), 1));
     c.d_tslot = take<int2>(ws, std::max<size_t>(c.sc.tslot.size(), 1));
+    c.d_jobs2 = take<TcJob>(ws, std::max<size_t>(c.sc2.jobs.size(), 1));
+    c.d_cta_off2 = take<int>(ws, std::max<size_t>(c.sc2.cta_off.size(), 1));
+    c.d_tslot2 = take<int2>(ws, std::max<size_t>(c.sc2.tslot.size(), 1));
     c.d_pairs_split = take<TcPairs>(ws, 1);
     c.d_pairs_oz = take<TcPairs>(ws, 1);
     c.d_pairs_z = take<TcPairs>(ws, 1);
@@ -1222,7 +1276,8 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
         !c.NUc || !c.d_full_jobs || !c.sTr ||
         !c.sTc || !c.sUr || !c.sUc || !c.gTr || !c.gTc || !c.gUr || !c.gUc || !c.gmap || !c.ginv || !c.pos ||
         !c.tmpmax || !c.tmpmax2 || !c.PA || !c.PB || !c.E || !c.R || !c.RA || !c.RB || !c.norms || !c.d_res_jobs || !c.d_jobs ||
-        !c.d_pairs_split || !c.d_pairs_oz || !c.d_cta_off || !c.d_tslot || !c.DT32 || !c.DA32 || !c.sbbase)
+        !c.d_pairs_split || !c.d_pairs_oz || !c.d_cta_off || !c.d_tslot || !c.DT32 || !c.DA32 || !c.sbbase ||
+        !c.d_jobs2 || !c.d_cta_off2 || !c.d_tslot2)
         return SIGNTRI_ERR_NO_WORKSPACE;
     c.pairs_split = split_pairs(S);
     c.pairs_oz = ozaki_pairs_impl(kOzakiSlices, kOzakiBits);
@@ -1266,6 +1321,19 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     if (!c.sc.tslot.empty())
         SGT_CUDA_TRY(cudaMemcpyAsync(c.d_tslot, c.sc.tslot.data(), c.sc.tslot.size() * sizeof(int2),
                                      cudaMemcpyHostToDevice, st));
+    if (!c.sc2.jobs.empty())
+        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_jobs2, c.sc2.jobs.data(), c.sc2.jobs.size() * sizeof(TcJob),
+                                     cudaMemcpyHostToDevice, st));
+    if (!c.sc2.cta_off.empty())
+        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_cta_off2, c.sc2.cta_off.data(), c.sc2.cta_off.size() * sizeof(int),
+                                     cudaMemcpyHostToDevice, st));
+    if (!c.sc2.tslot.empty())
+        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_tslot2, c.sc2.tslot.data(), c.sc2.tslot.size() * sizeof(int2),
+                                     cudaMemcpyHostToDevice, st));
+    {
+        const signtri_status ss = side_stream(c);
+        if (ss != SIGNTRI_OK) return ss;
+    }
     SGT_CUDA_TRY(cudaMemcpyAsync(c.d_pairs_split, &c.pairs_split, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
     SGT_CUDA_TRY(cudaMemcpyAsync(c.d_pairs_oz, &c.pairs_oz, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
     {

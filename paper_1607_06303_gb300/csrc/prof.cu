@@ -64,10 +64,10 @@ void prof_count(int cls, long long launches)
     if (cls >= 0 && cls < SIGNTRI_KC_COUNT) p_launches[cls] += launches;
 }
 
-void prof_begin(int cls, cudaStream_t st)
+void prof_begin(int cls, cudaStream_t st, bool count)
 {
     std::lock_guard<std::mutex> lk(p_mu);
-    p_launches[cls]++;
+    if (count) p_launches[cls]++;
     if (!p_enabled || p_paused) return;
     p_open_cls = cls;
     p_open_ev = take_event();

@@ -952,6 +952,8 @@ signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSo
     }
     const int resident = (same_w && pairs.n > 1 && nsl <= 3 && nsl <= top.nslices && nsl <= bot.nslices &&
                           nsl <= left.nslices && nsl <= right.nslices) ? 1 : 0;
+    const bool timed = (kernel_class & kProfUntimed) == 0;
+    kernel_class &= ~kProfUntimed;
     // grouped pair mode when pairs with unequal weights share A slices
     bool share = false;
     for (int p = 0; p < pairs.n && !share; p++)
@@ -960,7 +962,7 @@ signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSo
         const size_t smem2 = tc_pair2_smem_bytes();
         SGT_CUDA_TRY(cudaFuncSetAttribute(tc_pair2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
         prof_add_flops(kernel_class, useful_flops);
-        ProfScope ps(kernel_class, st);
+        ProfScope ps(kernel_class, st, timed);
         tc_pair2_kernel<<<d_job_off ? nctas : njobs, kTcThreads, smem2, st>>>(
             mt, mb, ml, mr, top.rows, left.rows, d_jobs, d_job_off, d_pairs, chunk_kb, top.scale, bot.scale,
             left.scale, right.scale, out, qo, d_err, blk, top.cols / 64);
@@ -970,7 +972,7 @@ signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSo
     const size_t smem = tc_smem_bytes();
     SGT_CUDA_TRY(cudaFuncSetAttribute(tc_blocksum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     prof_add_flops(kernel_class, useful_flops);
-    ProfScope ps(kernel_class, st);
+    ProfScope ps(kernel_class, st, timed);
     tc_blocksum_kernel<<<d_job_off ? nctas : njobs, kTcThreads, smem, st>>>(
         mt, mb, ml, mr, top.rows, left.rows, d_jobs, d_job_off, d_pairs, chunk_kb, top.scale, bot.scale, left.scale,
         right.scale, out, qo, d_err, resident, nsl, blk, top.cols / 64);

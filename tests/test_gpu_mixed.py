@@ -108,3 +108,36 @@ def test_verification_modes(gpu_lib, oracle_mod):
         assert 0 < a <= 1e-13 and 0 < b <= 1e-13
         assert b / 3 <= a <= 3 * b, (a, b)
     assert gpu_lib.signtri_set_verification(2) == gpu_lib.Status.ERR_BAD_ARG
+
+
+@pytest.mark.parametrize("n", [700, 1000])
+def test_sweep_operand_byte_count(gpu_lib, n):
+    # the byte model behind the sweeps' HBM roofline: every anti-diagonal d
+    # of the nb = ceil(n/64) block partition reads, per tile (I, I+d), 64-row
+    # panels of three bf16 slices over its d+1 K-blocks once: four panels in
+    # the initial sweep, six for the correction's two launches side by side
+    # (they share the E panels); one refinement step
+    import torch
+    T = make_T(n, 0.5, seed=n)
+    Tt = gpu_lib.to_device(T)
+    Ut = torch.empty_like(Tt)
+    h = torch.cuda.current_stream().cuda_stream
+    gpu_lib.signtri_profile_reset()
+    gpu_lib.signtri_profile_enable(True)
+    try:
+        assert gpu_lib.sign_tri(n, Tt.data_ptr(), n, Ut.data_ptr(), n, gpu_lib.Variant.PH_MIXED_TF32, h) == 0
+        torch.cuda.synchronize()
+        got = gpu_lib.signtri_profile_read_bytes(gpu_lib.signtri.KC_BLOCK_SUMS_TC)
+        flops = gpu_lib.signtri_profile_read_flops(gpu_lib.signtri.KC_BLOCK_SUMS_TC)
+    finally:
+        gpu_lib.signtri_profile_enable(False)
+    info = gpu_lib.signtri_get_info()
+    assert info.variant == gpu_lib.Variant.PH_MIXED_TF32 and info.refine_steps == 1, info.as_dict()
+    nb = (n + 63) // 64
+    panel = sum((nb - d) * (d + 1) for d in range(1, nb)) * 3 * 64 * 64 * 2
+    assert got == (4 + 6) * panel, (got, panel)
+    # tensor work: 6 slice pairs x 2*64^3 per tile K-block and used quadrant (3 in the
+    # initial sweep, 2 in each correction launch)
+    kb = sum((nb - d) * (d + 1) for d in range(1, nb))
+    assert flops == pytest.approx(6 * 2 * 64 ** 3 * kb * (3 + 2 + 2), rel=1e-12)
+    assert gpu_lib.signtri_profile_read_bytes(gpu_lib.signtri.KC_RESIDUAL) == 0
