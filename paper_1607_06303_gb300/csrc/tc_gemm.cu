@@ -564,12 +564,15 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
 // pairs: shared-memory traffic per product drops by a quarter, which is what
 // bounds pair mode.  A pair without a partner runs alone (N = 128).  Two TMEM
 // accumulators of 256 columns fill the TMEM, so the fp32 hi parts of the
-// result live in shared memory (thread-private columns) and the lo parts in
-// registers.  Warp roles, job lists and outputs as in tc_blocksum_kernel.
+// result live half in registers, half in shared memory (thread-private
+// columns), and the lo parts in registers: the shared memory left over holds
+// a 4-stage ring, which the units' operand latency needs (3 stages ran the
+// tensor pipe ~10% slower despite a few registers spilled now).  Warp roles,
+// job lists and outputs as in tc_blocksum_kernel.
 
-constexpr int kP2Stages = 3;
+constexpr int kP2Stages = 4;
 constexpr int kP2StageBytes = 3 * 16384;          // A | B_t0 | B_t1 for one K-block
-constexpr int kP2HiBytes = 512 * 32 * 4;           // 32 hi values per epilogue thread
+constexpr int kP2HiBytes = 512 * 16 * 4;           // 16 of the 32 hi values per epilogue thread
 
 struct TcGroups {
     int n;
@@ -776,14 +779,16 @@ tc_pair2_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_constant_
         const int c0 = (cg & 1) * 32;
         const int quad = (bottom ? 2 : 0) + half;
         const bool quad_mode = qo.m[0] || qo.m[1] || qo.m[2] || qo.m[3];
-        float *hi = his + (threadIdx.x - 64);   // hi[i * 512]: this thread's column i
+        float *his_t = his + (threadIdx.x - 64);   // his_t[i * 512]: this thread's column 16 + i
         bool ok = true;
         int g = 0;
         for (int j = j0; j < j1 && ok; j++) {
             const int nu = job_units(jobs[j], chunk_kb, ngrp, 0);
-            float lo[32];
+            float lo[32], hr[16];
 #pragma unroll
             for (int i = 0; i < 32; i++) lo[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; i++) hr[i] = 0.f;
             for (int u = 0; u < nu && ok; u++, g++) {
                 const int buf = g & 1;
                 const uint32_t tphase = (uint32_t)((g >> 1) & 1);
@@ -801,10 +806,13 @@ tc_pair2_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_constant_
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int i = 0; i < 16; i++) {
-                        float h = (u == 0) ? __fmul_rn(__uint_as_float(v0[i]), w0) : hi[(cc + i) * 512];
+                        // hi of columns 0..15 in registers, 16..31 in shared memory
+                        float h = (u == 0) ? __fmul_rn(__uint_as_float(v0[i]), w0)
+                                           : (cc == 0 ? hr[i] : his_t[i * 512]);
                         if (u > 0) df_add(h, lo[cc + i], __fmul_rn(__uint_as_float(v0[i]), w0));
                         if (two) df_add(h, lo[cc + i], __fmul_rn(__uint_as_float(v1[i]), w1));
-                        hi[(cc + i) * 512] = h;
+                        if (cc == 0) hr[i] = h;
+                        else his_t[i * 512] = h;
                     }
                 }
                 fence_before();
@@ -832,7 +840,7 @@ tc_pair2_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_constant_
             const float srow_f = (float)srow;
 #pragma unroll
             for (int i = 0; i < 32; i++) {
-                const float h = nu > 0 ? hi[i * 512] : 0.f;
+                const float h = nu > 0 ? (i < 16 ? hr[i] : his_t[(i - 16) * 512]) : 0.f;
                 const float sc = __fmul_rn(srow_f, scol ? scol[cbase + i] : 1.f);
                 const float hs = __fmul_rn(h, sc), ls = __fmul_rn(lo[i], sc);
                 if (o2) o2[(size_t)i * 64] = make_float2(hs, ls);
