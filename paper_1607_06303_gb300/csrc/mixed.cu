@@ -361,8 +361,9 @@ corr_diag_leaf_kernel(int n, const double *__restrict__ T, int ldt, const double
 // Residual of entry (i < j) into R (column-major n x n): Rc_ij when the signs
 // of i and j differ, Rs_ij when they agree, from the gathered products
 // (RA: Y at equal-sign positions, N_T N_U at opposite-sign ones; RB: N_U N_T)
-// plus the diagonal terms; other entries 0.  Squared Frobenius norms of the
-// used Rc and Rs entries, of T and of U into norms[0..3].
+// plus the diagonal terms.  Only the strictly upper part of R is written: the
+// correction reads nothing else.  Squared Frobenius norms of the used Rc and
+// Rs entries, of T and of U into norms[0..3].
 __global__ void needed_finalize_kernel(int n, const double *__restrict__ T, int ldt, const double *__restrict__ U,
                                        int ldu, const int *__restrict__ gmap, const double *__restrict__ RA,
                                          const double *__restrict__ RB, int ldg, double *__restrict__ R,
@@ -372,26 +373,25 @@ __global__ void needed_finalize_kernel(int n, const double *__restrict__ T, int 
     double nc = 0.0, ns = 0.0, nt = 0.0, nu = 0.0;
     const double tjj = SGT_AT(T, ldt, j, j), ujj = SGT_AT(U, ldu, j, j);
     const size_t gj = (size_t)gmap[j] * ldg;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double r = 0.0;
-        if (i < j) {
-            const double tii = SGT_AT(T, ldt, i, i), uii = SGT_AT(U, ldu, i, i);
-            const double tij = SGT_AT(T, ldt, i, j), uij = SGT_AT(U, ldu, i, j);
-            const size_t g = (size_t)gmap[i] + gj;
-            if ((tii > 0.0) == (tjj > 0.0)) {
-                r = RA[g] + uii * uij + uij * ujj;
-                ns += r * r;
-            } else {
-                r = RA[g] - RB[g] + (tii * uij - uij * tjj) + (tij * ujj - uii * tij);
-                nc += r * r;
-            }
-            nt += tij * tij;
-            nu += uij * uij;
-        } else if (i == j) {
-            nt += tjj * tjj;
-            nu += ujj * ujj;
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        const double tii = SGT_AT(T, ldt, i, i), uii = SGT_AT(U, ldu, i, i);
+        const double tij = SGT_AT(T, ldt, i, j), uij = SGT_AT(U, ldu, i, j);
+        const size_t g = (size_t)gmap[i] + gj;
+        double r;
+        if ((tii > 0.0) == (tjj > 0.0)) {
+            r = RA[g] + uii * uij + uij * ujj;
+            ns += r * r;
+        } else {
+            r = RA[g] - RB[g] + (tii * uij - uij * tjj) + (tij * ujj - uii * tij);
+            nc += r * r;
         }
+        nt += tij * tij;
+        nu += uij * uij;
         SGT_AT(R, n, i, j) = r;
+    }
+    if (threadIdx.x == 0) {
+        nt += tjj * tjj;
+        nu += ujj * ujj;
     }
     __shared__ double red[4][256];
     red[0][threadIdx.x] = nc; red[1][threadIdx.x] = ns; red[2][threadIdx.x] = nt; red[3][threadIdx.x] = nu;

@@ -108,6 +108,7 @@ __global__ void pow2_scale_kernel(int n, const unsigned long long *__restrict__ 
 // [64 - b(s+1), 64 - bs) of F with the sign of x.  Same digits as repeated
 // q_s = trunc(2^b r), r <- 2^b r - q_s, without float64 arithmetic (slow on
 // this part).  S b <= 64.
+template <int SC>
 __device__ __forceinline__ void exact_slices(double x, int scale_exp, int S, int b, float *q)
 {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
@@ -122,14 +123,19 @@ __device__ __forceinline__ void exact_slices(double x, int scale_exp, int S, int
     }
     const float sgn = (bits >> 63) ? -1.f : 1.f;
     const unsigned long long mask = (1ull << b) - 1ull;
-    for (int s = 0; s < S; s++) q[s] = sgn * (float)((F >> (64 - b * (s + 1))) & mask);
+    const int ns = SC ? SC : S;   // SC > 0: slice count known at compile time (q in registers)
+#pragma unroll
+    for (int s = 0; s < ns; s++) q[s] = sgn * (float)((F >> (64 - b * (s + 1))) & mask);
 }
 
 // Rounding split of the fp32 value of x: x0 = bf16(x), x1 = bf16(x - x0), ...
+template <int SC>
 __device__ __forceinline__ void round_slices(double x, int S, float *q)
 {
     float r = (float)x;
-    for (int s = 0; s < S; s++) {
+    const int ns = SC ? SC : S;
+#pragma unroll
+    for (int s = 0; s < ns; s++) {
         const float b = __bfloat162float(__float2bfloat16_rn(r));
         q[s] = b;
         r = __fsub_rn(r, b);
@@ -142,6 +148,7 @@ __device__ __forceinline__ void round_slices(double x, int S, float *q)
 // tri: 0 = all entries, 1 = strictly upper (i < kk) only.  scale == nullptr:
 // rounding split.  skip = 1: tiles left of the even 64-block at or below a
 // row's diagonal block are not written (no 2 x 2-block job reads them).
+template <int SC>
 __global__ void row_slices_kernel(int m, int k, const double *__restrict__ M, int ldm, int tri, int S, int bits,
                                   const float *__restrict__ scale, __nv_bfloat16 *__restrict__ R, int rows_pad,
                                   int ldr, int skip)
@@ -162,13 +169,14 @@ __global__ void row_slices_kernel(int m, int k, const double *__restrict__ M, in
         float q0[8], q1[8];
         const int e = (scale && i < m) ? ilogbf(scale[i]) : 0;
         if (scale) {
-            exact_slices(tile[2 * threadIdx.x][y], e, S, bits, q0);
-            exact_slices(tile[2 * threadIdx.x + 1][y], e, S, bits, q1);
+            exact_slices<SC>(tile[2 * threadIdx.x][y], e, S, bits, q0);
+            exact_slices<SC>(tile[2 * threadIdx.x + 1][y], e, S, bits, q1);
         } else {
-            round_slices(tile[2 * threadIdx.x][y], S, q0);
-            round_slices(tile[2 * threadIdx.x + 1][y], S, q1);
+            round_slices<SC>(tile[2 * threadIdx.x][y], S, q0);
+            round_slices<SC>(tile[2 * threadIdx.x + 1][y], S, q1);
         }
-        for (int s = 0; s < S; s++)
+        #pragma unroll
+        for (int s = 0; s < (SC ? SC : S); s++)
             *reinterpret_cast<__nv_bfloat162 *>(&R[((size_t)s * rows_pad + i) * ldr + kk]) =
                 __floats2bfloat162_rn(q0[s], q1[s]);
     }
@@ -179,6 +187,7 @@ __global__ void row_slices_kernel(int m, int k, const double *__restrict__ M, in
 // tri: 1 = strictly upper (kk < j) only.  skip = 1: entries past the end of
 // the column's even 64-block pair are not written (no 2 x 2-block job reads
 // them).
+template <int SC>
 __global__ void col_slices_kernel(int k, int n, const double *__restrict__ M, int ldm, int tri, int S, int bits,
                                   const float *__restrict__ scale, __nv_bfloat16 *__restrict__ C, int rows_pad,
                                   int ldc, int skip)
@@ -195,13 +204,14 @@ __global__ void col_slices_kernel(int k, int n, const double *__restrict__ M, in
     float q0[8], q1[8];
     if (scale) {
         const int e = j < n ? ilogbf(scale[j]) : 0;
-        exact_slices(v0, e, S, bits, q0);
-        exact_slices(v1, e, S, bits, q1);
+        exact_slices<SC>(v0, e, S, bits, q0);
+        exact_slices<SC>(v1, e, S, bits, q1);
     } else {
-        round_slices(v0, S, q0);
-        round_slices(v1, S, q1);
+        round_slices<SC>(v0, S, q0);
+        round_slices<SC>(v1, S, q1);
     }
-    for (int s = 0; s < S; s++)
+    #pragma unroll
+    for (int s = 0; s < (SC ? SC : S); s++)
         *reinterpret_cast<__nv_bfloat162 *>(&C[((size_t)s * rows_pad + j) * ldc + kk]) =
             __floats2bfloat162_rn(q0[s], q1[s]);
 }
@@ -217,6 +227,7 @@ __global__ void col_slices_kernel(int k, int n, const double *__restrict__ M, in
 // gathered row gmap[i] as whole 128-byte runs.  Column tiles wholly before
 // the gathered start of the rows' superblock lie outside every residual
 // job's K range and are not written; padding rows are zeroed separately.
+template <int SC>
 __global__ void row_slices_gathered_kernel(int n, const double *__restrict__ M, int ldm, const int *__restrict__ inv,
                                            const int *__restrict__ gmap, const int *__restrict__ sbbase, int super,
                                            int ng, int S, int bits, const float *__restrict__ scale_g,
@@ -240,9 +251,10 @@ __global__ void row_slices_gathered_kernel(int n, const double *__restrict__ M, 
         const int e = ilogbf(scale_g[g]);
         const double2 v = *reinterpret_cast<const double2 *>(&tile[r][2 * lane]);
         float q0[8], q1[8];
-        exact_slices(v.x, e, S, bits, q0);
-        exact_slices(v.y, e, S, bits, q1);
-        for (int s = 0; s < S; s++)
+        exact_slices<SC>(v.x, e, S, bits, q0);
+        exact_slices<SC>(v.y, e, S, bits, q1);
+        #pragma unroll
+        for (int s = 0; s < (SC ? SC : S); s++)
             *reinterpret_cast<__nv_bfloat162 *>(&R[((size_t)s * rows + g) * ldr + h0 + 2 * lane]) =
                 __floats2bfloat162_rn(q0[s], q1[s]);
     }
@@ -255,6 +267,7 @@ __global__ void row_slices_gathered_kernel(int n, const double *__restrict__ M, 
 // the segment [sbbase[sb], sbbase[sb + 1]) of output row gmap[j], which is
 // then written in one pass.  Segments after j's superblock lie outside every
 // residual job's K range and are not written.
+template <int SC>
 __global__ void col_slices_gathered_kernel(int n, const double *__restrict__ M, int ldm, const int *__restrict__ gmap,
                                            const int *__restrict__ sbbase, int super, int segmax, int S, int bits,
                                            const float *__restrict__ scale_g, __nv_bfloat16 *__restrict__ C, int rows,
@@ -272,9 +285,10 @@ __global__ void col_slices_gathered_kernel(int n, const double *__restrict__ M, 
     const int i1 = min(min(n, (sb + 1) * super), j);   // strictly upper: rows i < j
     for (int i = sb * super + threadIdx.x; i < i1; i += blockDim.x) {
         float q[8];
-        exact_slices(SGT_AT(M, ldm, i, j), e, S, bits, q);
+        exact_slices<SC>(SGT_AT(M, ldm, i, j), e, S, bits, q);
         const int h = gmap[i] - b0;
-        for (int s = 0; s < S; s++) seg[s * segmax + h] = __float2bfloat16_rn(q[s]);
+        #pragma unroll
+        for (int s = 0; s < (SC ? SC : S); s++) seg[s * segmax + h] = __float2bfloat16_rn(q[s]);
     }
     __syncthreads();
     // len and b0 are multiples of 64: bf16 pairs
@@ -365,7 +379,11 @@ signtri_status make_row_slices(int m, int k, const double *M, int ldm, int tri, 
     if (ldr & 1) return SIGNTRI_ERR_BAD_ARG;
     dim3 grid((ldr + 2 * TS - 1) / (2 * TS), (rows_pad + TS - 1) / TS), block(TS, 8);
     ProfScope ps(SIGNTRI_KC_CONVERT, st);
-    row_slices_kernel<<<grid, block, 0, st>>>(m, k, M, ldm, tri, S, bits, scale, R, rows_pad, ldr, skip);
+    // compile-time slice counts for the exact residual slices (7) and the sweeps' splits (3)
+    if (S == 7) row_slices_kernel<7><<<grid, block, 0, st>>>(m, k, M, ldm, tri, S, bits, scale, R, rows_pad, ldr, skip);
+    else if (S == 3)
+        row_slices_kernel<3><<<grid, block, 0, st>>>(m, k, M, ldm, tri, S, bits, scale, R, rows_pad, ldr, skip);
+    else row_slices_kernel<0><<<grid, block, 0, st>>>(m, k, M, ldm, tri, S, bits, scale, R, rows_pad, ldr, skip);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }
@@ -377,7 +395,9 @@ signtri_status make_col_slices(int k, int n, const double *M, int ldm, int tri, 
     if (ldc & 1) return SIGNTRI_ERR_BAD_ARG;
     dim3 grid((ldc / 2 + 255) / 256, rows_pad);
     ProfScope ps(SIGNTRI_KC_CONVERT, st);
-    col_slices_kernel<<<grid, 256, 0, st>>>(k, n, M, ldm, tri, S, bits, scale, C, rows_pad, ldc, skip);
+    if (S == 7) col_slices_kernel<7><<<grid, 256, 0, st>>>(k, n, M, ldm, tri, S, bits, scale, C, rows_pad, ldc, skip);
+    else if (S == 3) col_slices_kernel<3><<<grid, 256, 0, st>>>(k, n, M, ldm, tri, S, bits, scale, C, rows_pad, ldc, skip);
+    else col_slices_kernel<0><<<grid, 256, 0, st>>>(k, n, M, ldm, tri, S, bits, scale, C, rows_pad, ldc, skip);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }
@@ -395,12 +415,22 @@ signtri_status make_gathered_slices(int n, const double *M, int ldm, const int *
     gather_scales_kernel<<<(rows + 255) / 256, 256, 0, st>>>(rows, ng, inv, sC, sCg);
     SGT_LAUNCH_CHECK();
     const int nsb = (n + super - 1) / super;
-    row_slices_gathered_kernel<<<dim3((n + 63) / 64, ld / 64), 256, 0, st>>>(n, M, ldm, inv, gmap, sbbase, super, ng,
-                                                                           S, bits, sRg, R, rows, ld);
+    const dim3 rgrid((n + 63) / 64, ld / 64);
+    if (S == 7)
+        row_slices_gathered_kernel<7><<<rgrid, 256, 0, st>>>(n, M, ldm, inv, gmap, sbbase, super, ng, S, bits, sRg, R,
+                                                             rows, ld);
+    else
+        row_slices_gathered_kernel<0><<<rgrid, 256, 0, st>>>(n, M, ldm, inv, gmap, sbbase, super, ng, S, bits, sRg, R,
+                                                             rows, ld);
     SGT_LAUNCH_CHECK();
     const int segmax = super + 128;   // a superblock's rows, each sign class padded to 64
-    col_slices_gathered_kernel<<<dim3(n, nsb), 256, (size_t)S * segmax * sizeof(__nv_bfloat16), st>>>(
-        n, M, ldm, gmap, sbbase, super, segmax, S, bits, sCg, C, rows, ld);
+    const size_t csm = (size_t)S * segmax * sizeof(__nv_bfloat16);
+    if (S == 7)
+        col_slices_gathered_kernel<7><<<dim3(n, nsb), 256, csm, st>>>(n, M, ldm, gmap, sbbase, super, segmax, S, bits,
+                                                                      sCg, C, rows, ld);
+    else
+        col_slices_gathered_kernel<0><<<dim3(n, nsb), 256, csm, st>>>(n, M, ldm, gmap, sbbase, super, segmax, S, bits,
+                                                                      sCg, C, rows, ld);
     SGT_LAUNCH_CHECK();
     zero_padding_rows_kernel<<<rows, 256, 0, st>>>(inv, ng, S, R, C, rows, ld);
     SGT_LAUNCH_CHECK();
