@@ -45,6 +45,7 @@
 //    to the float64 path when a step does not reduce the larger of the two by
 //    a factor 10, or after the step limit.
 #include <algorithm>
+#include <utility>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(kLeafThreads, 2)
 mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restrict__ V, int ldv,
                   const float *__restrict__ DT, const float *__restrict__ DA, const double *__restrict__ Rc,
                   const double *__restrict__ Rs, int ldr, int d, const int2 *__restrict__ tslot,
+                  const int2 *__restrict__ tslot2,
                   const double *__restrict__ PA, const double *__restrict__ PB, __nv_bfloat16 *__restrict__ Vr,
                   __nv_bfloat16 *__restrict__ Vc, int S, int nbk)
 {
@@ -123,6 +125,8 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
     // every global read that needs no sign first: the diagonal blocks, the
     // base terms of the seeds, this tile's partial slots
     const int2 ts = tslot[I];
+    // mode 0 with look-ahead pairing: a second set of partial slots in PB
+    const int2 ts2 = (MODE == 0 && tslot2) ? tslot2[I] : make_int2(0, 0);
     float base0[EPT], base1[EPT];
 #pragma unroll
     for (int m = 0; m < EPT; m++) {
@@ -175,8 +179,11 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
         float acc[EPT];
 #pragma unroll
         for (int m = 0; m < EPT; m++) acc[m] = 0.f;
-        for (int s = 0; s < ts.y; s++) {
-            const size_t sb = ((size_t)ts.x + s) * 16384 + p;
+        for (int s = 0; s < ts.y + ts2.y; s++) {
+            // mode 0: slots of PA, then (look-ahead pairing) slots of PB
+            const bool second = s >= ts.y;
+            const float2 *P0 = second ? PB2 : PA2;
+            const size_t sb = ((size_t)(second ? ts2.x + s - ts.y : ts.x + s)) * 16384 + p;
 #pragma unroll
             for (int m = 0; m < EPT; m++) {
                 const int q = q0 + m * QS;
@@ -184,7 +191,7 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
                     const bool opp = (srow[p] + scol[q] == 0.f);
                     // opposite signs: TL - BR of PA (X); equal signs: TR of PA
                     // (Y, mode 0) or TL + BR of PB (Y^E, mode 1)
-                    const float2 *src = opp ? PA2 : (MODE == 0 ? PA2 + 4096 : PB2);
+                    const float2 *src = opp ? P0 : (MODE == 0 ? P0 + 4096 : PB2);
                     const size_t e = sb + (size_t)q * 64;
                     const float2 l1 = src[e];
                     float2 l2 = make_float2(0.f, 0.f);
@@ -644,9 +651,8 @@ struct Schedule {
     int max_jobs = 0;           // partial slots needed by one diagonal
 };
 
-void build_schedule(int n, int gmax, Schedule &sc)
+void schedule_reset(int nb, Schedule &sc)
 {
-    const int nb = (n + MB - 1) / MB;
     sc.nb = nb;
     sc.job_off.assign(nb + 1, 0);
     sc.cta_begin.assign(nb + 1, 0);
@@ -656,47 +662,132 @@ void build_schedule(int n, int gmax, Schedule &sc)
     sc.tslot.clear();
     sc.jobs.clear();
     sc.max_jobs = 0;
-    for (int d = 0; d <= nb; d++) {
-        sc.job_off[d] = (int)sc.jobs.size();
-        sc.cta_begin[d] = (int)sc.cta_off.size();
-        sc.tile_begin[d] = (int)sc.tslot.size();
-        if (d < 1 || d >= nb) continue;
-        const int ntiles = nb - d;
-        // K-blocks I .. J: the diagonal blocks carry the known in-block terms
-        const long long kmax = d + 1, W = (long long)ntiles * kmax;
-        if (W == 0) {
-            for (int t = 0; t < ntiles; t++) sc.tslot.push_back(make_int2(0, 0));
-            continue;
-        }
-        const int G = (int)std::min<long long>(gmax, W);
-        sc.nctas[d] = G;
-        const int base = (int)sc.jobs.size();
-        for (int c = 0; c < G; c++) {
-            sc.cta_off.push_back((int)sc.jobs.size() - base);
-            const long long x1 = (long long)(c + 1) * W / G;
-            for (long long x = (long long)c * W / G; x < x1;) {
-                const int t = (int)(x / kmax);
-                const long long t0 = (long long)t * kmax, xe = std::min(x1, t0 + kmax);
-                TcJob j;
-                j.rt = t * MB; j.rb = t * MB; j.cl = (t + d) * MB; j.cr = (t + d) * MB;
-                j.kb0 = t + (int)(x - t0);
-                j.kb1 = t + (int)(xe - t0);
-                j.slot = c + t;
-                j.pad = 0;
-                sc.jobs.push_back(j);
-                x = xe;
-            }
-        }
+}
+
+// Marks where anti-diagonal d's entries begin (call for d = 0 .. nb in order).
+void schedule_open(Schedule &sc, int d)
+{
+    sc.job_off[d] = (int)sc.jobs.size();
+    sc.cta_begin[d] = (int)sc.cta_off.size();
+    sc.tile_begin[d] = (int)sc.tslot.size();
+}
+
+TcJob tile_job(int I, int J, int kb0, int kb1, int slot)
+{
+    TcJob j;
+    j.rt = I * MB; j.rb = I * MB; j.cl = J * MB; j.cr = J * MB;
+    j.kb0 = kb0; j.kb1 = kb1; j.slot = slot; j.pad = 0;
+    return j;
+}
+
+// The full block sums of anti-diagonal d (K-blocks I .. J: the diagonal
+// blocks carry the known in-block terms), split evenly over up to gmax CTAs.
+void add_even_split(Schedule &sc, int d, int nb, int gmax)
+{
+    const int ntiles = nb - d;
+    const long long kmax = d + 1, W = (long long)ntiles * kmax;
+    const int G = (int)std::min<long long>(gmax, W);
+    sc.nctas[d] = G;
+    const int base = (int)sc.jobs.size();
+    for (int c = 0; c < G; c++) {
         sc.cta_off.push_back((int)sc.jobs.size() - base);
-        for (int t = 0; t < ntiles; t++) {
-            // the CTA holding chunk x is ((x + 1) G - 1) / W (every CTA's range is non-empty)
-            const long long f = (((long long)t * kmax + 1) * G - 1) / W;
-            const long long l = (((long long)(t + 1) * kmax) * G - 1) / W;
-            sc.tslot.push_back(make_int2((int)(f + t), (int)(l - f + 1)));
+        const long long x1 = (long long)(c + 1) * W / G;
+        for (long long x = (long long)c * W / G; x < x1;) {
+            const int t = (int)(x / kmax);
+            const long long t0 = (long long)t * kmax, xe = std::min(x1, t0 + kmax);
+            sc.jobs.push_back(tile_job(t, t + d, t + (int)(x - t0), t + (int)(xe - t0), c + t));
+            x = xe;
         }
-        sc.max_jobs = std::max(sc.max_jobs, G + ntiles);
+    }
+    sc.cta_off.push_back((int)sc.jobs.size() - base);
+    for (int t = 0; t < ntiles; t++) {
+        // the CTA holding chunk x is ((x + 1) G - 1) / W (every CTA's range is non-empty)
+        const long long f = (((long long)t * kmax + 1) * G - 1) / W;
+        const long long l = (((long long)(t + 1) * kmax) * G - 1) / W;
+        sc.tslot.push_back(make_int2((int)(f + t), (int)(l - f + 1)));
+    }
+    sc.max_jobs = std::max(sc.max_jobs, G + ntiles);
+}
+
+void build_schedule(int n, int gmax, Schedule &sc)
+{
+    const int nb = (n + MB - 1) / MB;
+    schedule_reset(nb, sc);
+    for (int d = 0; d <= nb; d++) {
+        schedule_open(sc, d);
+        if (d >= 1 && d < nb) add_even_split(sc, d, nb, gmax);
     }
 }
+
+// Look-ahead pairing of the initial sweep: for a lead anti-diagonal d (odd,
+// >= 3, with d + 1 < nb), the tiles (I, I+d+1) of the next one take their
+// block sums over K-blocks I+2 .. I+d-1 -- all known before anti-diagonal d
+// is solved -- in a launch that runs beside d's own, on a split matched CTA
+// by CTA to d's: CTA c of both walks the same row panels I at the same
+// K-blocks, so the look-ahead reads them from L2.  The four K-blocks left,
+// I, I+1, I+d, I+d+1 (two of them involve anti-diagonal d), are summed
+// after d's leaves by a completion launch.
+bool look_lead(int d, int nb) { return d >= 3 && (d & 1) && d + 1 < nb; }
+bool look_follow(int d, int nb) { return d >= 4 && !(d & 1) && look_lead(d - 1, nb); }
+
+void build_look_schedules(int n, int gmax, Schedule &A, Schedule &B, Schedule &C)
+{
+    const int nb = (n + MB - 1) / MB;
+    schedule_reset(nb, A);
+    schedule_reset(nb, B);
+    schedule_reset(nb, C);
+    for (int d = 0; d <= nb; d++) {
+        schedule_open(A, d);
+        schedule_open(B, d);
+        schedule_open(C, d);
+        if (d < 1 || d >= nb) continue;
+        if (look_lead(d, nb)) add_even_split(A, d, nb, gmax);
+        if (!look_follow(d, nb)) continue;
+        // B: the look-ahead sums of anti-diagonal e = d, matched to A's split of d - 1
+        const int e = d, dl = d - 1, nl = nb - dl, ne = nb - e;
+        const long long kmax = dl + 1, W = (long long)nl * kmax;
+        const int G = (int)std::min<long long>(gmax, W);
+        B.nctas[e] = G;
+        const int base = (int)B.jobs.size();
+        for (int c = 0; c < G; c++) {
+            B.cta_off.push_back((int)B.jobs.size() - base);
+            const long long x0 = (long long)c * W / G, x1 = (long long)(c + 1) * W / G;
+            for (int t = (int)(x0 / kmax); t <= (int)((x1 - 1) / kmax) && t < ne; t++) {
+                const long long lo = std::max<long long>(x0 - (long long)t * kmax, 2);
+                const long long hi = std::min<long long>(x1 - (long long)t * kmax, dl);   // offsets 2 .. dl-1
+                if (lo < hi) B.jobs.push_back(tile_job(t, t + e, t + (int)lo, t + (int)hi, c + t));
+            }
+        }
+        B.cta_off.push_back((int)B.jobs.size() - base);
+        for (int t = 0; t < ne; t++) {
+            const long long f = (((long long)t * kmax + 2 + 1) * G - 1) / W;
+            const long long l = (((long long)t * kmax + dl - 1 + 1) * G - 1) / W;
+            B.tslot.push_back(make_int2((int)(f + t), (int)(l - f + 1)));
+        }
+        B.max_jobs = std::max(B.max_jobs, G + nl);
+        // C: the completion, K-blocks I, I+1 and I+e-1, I+e of every tile, two slots a tile
+        const int GC = std::min(kSweepCtas, ne);
+        C.nctas[e] = GC;
+        const int cbase = (int)C.jobs.size();
+        for (int c = 0; c < GC; c++) {
+            C.cta_off.push_back((int)C.jobs.size() - cbase);
+            for (int t = (int)((long long)c * ne / GC); t < (int)((long long)(c + 1) * ne / GC); t++) {
+                C.jobs.push_back(tile_job(t, t + e, t, t + 2, 2 * t));
+                C.jobs.push_back(tile_job(t, t + e, t + e - 1, t + e + 1, 2 * t + 1));
+            }
+        }
+        C.cta_off.push_back((int)C.jobs.size() - cbase);
+        for (int t = 0; t < ne; t++) C.tslot.push_back(make_int2(2 * t, 2));
+        C.max_jobs = std::max(C.max_jobs, 2 * ne);
+    }
+}
+
+// A schedule's device copy (job list, per-CTA job ranges, per-tile slots).
+struct DevSchedule {
+    TcJob *jobs = nullptr;
+    int *cta_off = nullptr;
+    int2 *tslot = nullptr;
+};
 
 struct MixedCtx {
     int n, np, S;
@@ -706,6 +797,8 @@ struct MixedCtx {
     TcJob *d_jobs, *d_jobs2;
     int *d_cta_off, *d_cta_off2;
     int2 *d_tslot, *d_tslot2;
+    Schedule scA, scB, scC;     // initial sweep's look-ahead pairs: lead, look-ahead, completion
+    DevSchedule dsA, dsB, dsC;
     cudaStream_t side;          // second stream of the correction launches (null: one stream)
     cudaEvent_t ev_fork, ev_join;
     TcPairs pairs_split, pairs_oz;
@@ -769,7 +862,7 @@ size_t bytes_for(int n, int S)
     b += 4 * ngr * 4 + 4 * 256 + 2 * ngr * 4 + np + 3 * 256;            // gathered scales, maps, signs
     b += ((size_t)(n + kSuper - 1) / kSuper + 1) * 4 + 256;             // superblock starts
     b += 2 * ngr * ngr * 8 + 2 * 256;                                   // RA, RB
-    const size_t maxjobs = (size_t)kSweepCtas + nb + 8;
+    const size_t maxjobs = (size_t)kSweepCtas + 2 * nb + 8;
     b += 2 * maxjobs * 16384 * 8 + 2 * 256;                             // partials
     b += 2 * (size_t)n * n * 8 + 2 * 256;                               // E, R (= Rs)
     b += 64 + 256;                                                      // norms
@@ -778,9 +871,9 @@ size_t bytes_for(int n, int S)
     b += pairs_max * pairs_max * sizeof(TcJob) + 256;                   // needed-residual jobs
     const size_t nbp = (nb + 1) / 2;
     b += nbp * (nbp + 1) / 2 * sizeof(TcJob) + 256;                     // full-residual jobs
-    b += 2 * (nb * (size_t)(kSweepCtas + nb) * sizeof(TcJob) + 256);     // wavefront jobs (bound), 2 schedules
-    b += 2 * (nb * (size_t)(kSweepCtas + 1) * sizeof(int) + 256);         // per-CTA job ranges
-    b += 2 * ((size_t)nb * nb * sizeof(int2) + 256);                      // per-tile partial slots
+    b += 5 * (nb * (size_t)(kSweepCtas + 2 * nb) * sizeof(TcJob) + 256); // wavefront jobs (bound), 5 schedules
+    b += 5 * (nb * (size_t)(kSweepCtas + 1) * sizeof(int) + 256);         // per-CTA job ranges
+    b += 5 * ((size_t)nb * nb * sizeof(int2) + 256);                      // per-tile partial slots
     b += 3 * sizeof(TcPairs) + 768;
     b += 13 * (size_t)n * kProbes * 8 + 4 * 256;                       // probe Z, W1, W2, product halves
     b += (1 + 2 * (size_t)kOzakiSlices) * kProbes * np * 2 + 3 * 256;  // their slices
@@ -835,60 +928,105 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
     // pair takes long units
     const int chunk = c.pairs_split.n > 1 ? 2 : 16;
     // the correction's two launches per anti-diagonal run side by side on
-    // their own half-width schedule when a second stream is available
+    // their own half-width schedule when a second stream is available; so do
+    // the initial sweep's look-ahead pairs
     const bool pair = (MODE == 1) && c.side != nullptr;
+    const bool look = (MODE == 0) && c.side != nullptr;
     const Schedule &sc = pair ? c.sc2 : c.sc;
     const TcJob *d_jobs = pair ? c.d_jobs2 : c.d_jobs;
     const int *d_coff = pair ? c.d_cta_off2 : c.d_cta_off;
     const int2 *d_tslot = pair ? c.d_tslot2 : c.d_tslot;
+    const double kb_bytes = (double)c.S * MB * MB * 2;   // one 64-row panel of S bf16 slices, one K-block
+    auto fork = [&]() -> signtri_status {
+        SGT_CUDA_TRY(cudaEventRecord(c.ev_fork, c.st));
+        SGT_CUDA_TRY(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
+        return SIGNTRI_OK;
+    };
+    auto join = [&]() -> signtri_status {
+        SGT_CUDA_TRY(cudaEventRecord(c.ev_join, c.side));
+        SGT_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_join, 0));
+        return SIGNTRI_OK;
+    };
     for (int d = 1; d < nb; d++) {
         const int ntiles = nb - d;
-        const int njobs = sc.job_off[d + 1] - sc.job_off[d];
-        const TcJob *jobs = d_jobs + sc.job_off[d];
-        const int *coff = d_coff + sc.cta_begin[d];
-        const int G = sc.nctas[d];
         const long long sum_kb = (long long)ntiles * (d + 1);
-        // operand bytes: 64-row panels of S bf16 slices per K-block, each read once
-        const double panel_bytes = (double)sum_kb * c.S * MB * MB * 2;
+        const int2 *leaf_slots = d_tslot + sc.tile_begin[d];
+        const int2 *leaf_slots2 = nullptr;
         signtri_status rs;
-        if (njobs > 0) {
-            if (MODE == 0) {
-                // [U_I.; T_I.] x [T_.J | U_.J]: TL = U T, TR = U U, BR = T U
-                rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
-                                  c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st,
-                                  tc_flops(c.pairs_split.n, sum_kb, 3), coff, G);
-                if (rs != SIGNTRI_OK) return rs;
-                prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, 4 * panel_bytes);
-            } else {
-                // X^E: [E_I.; T_I.] x [T_.J | E_.J]: TL = E T, BR = T E, and
-                // Y^E: [U0_I.; E_I.] x [E_.J | U0_.J]: TL = U0 E, BR = E U0.  Side by side
-                // (same split, CTA c of each on the same tiles and K-blocks at the
-                // same time) they read the E panels once: six panels for both.
-                ProfScope pg(SIGNTRI_KC_BLOCK_SUMS_TC, c.st, pair, false);
-                const int cls = pair ? (SIGNTRI_KC_BLOCK_SUMS_TC | kProfUntimed) : SIGNTRI_KC_BLOCK_SUMS_TC;
-                cudaStream_t sy = c.st;
-                if (pair) {
-                    SGT_CUDA_TRY(cudaEventRecord(c.ev_fork, c.st));
-                    SGT_CUDA_TRY(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
-                    sy = c.side;
+        if (MODE == 0 && look && look_lead(d, nb)) {
+            // lead: anti-diagonal d in full beside the look-ahead sums of d + 1
+            const Schedule &A = c.scA, &B = c.scB;
+            const int e = d + 1, ne = nb - e;
+            const long long look_kb = (long long)ne * (d - 2);
+            ProfScope pg(SIGNTRI_KC_BLOCK_SUMS_TC, c.st, true, false);
+            const int cls = SIGNTRI_KC_BLOCK_SUMS_TC | kProfUntimed;
+            if ((rs = fork()) != SIGNTRI_OK) return rs;
+            rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, c.dsA.jobs + A.job_off[d], A.job_off[d + 1] - A.job_off[d],
+                              c.pairs_split, c.d_pairs_split, chunk, c.PA, slots, c.d_err, cls, c.st,
+                              tc_flops(c.pairs_split.n, sum_kb, 3), c.dsA.cta_off + A.cta_begin[d], A.nctas[d]);
+            if (rs != SIGNTRI_OK) return rs;
+            rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, c.dsB.jobs + B.job_off[e], B.job_off[e + 1] - B.job_off[e],
+                              c.pairs_split, c.d_pairs_split, chunk, c.PB, slots, c.d_err, cls, c.side,
+                              tc_flops(c.pairs_split.n, look_kb, 3), c.dsB.cta_off + B.cta_begin[e], B.nctas[e]);
+            if (rs != SIGNTRI_OK) return rs;
+            if ((rs = join()) != SIGNTRI_OK) return rs;
+            // the look-ahead reads its row panels from L2: only its column panels are new
+            prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, (4.0 * sum_kb + 2.0 * look_kb) * kb_bytes);
+            leaf_slots = c.dsA.tslot + A.tile_begin[d];
+        } else if (MODE == 0 && look && look_follow(d, nb)) {
+            // follow: the four K-blocks per tile the look-ahead left, then the
+            // leaves sum both slot sets
+            const Schedule &B = c.scB, &C = c.scC;
+            rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, c.dsC.jobs + C.job_off[d], C.job_off[d + 1] - C.job_off[d],
+                              c.pairs_split, c.d_pairs_split, chunk, c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC,
+                              c.st, tc_flops(c.pairs_split.n, 4LL * ntiles, 3), c.dsC.cta_off + C.cta_begin[d],
+                              C.nctas[d]);
+            if (rs != SIGNTRI_OK) return rs;
+            prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, 4.0 * 4.0 * ntiles * kb_bytes);
+            leaf_slots = c.dsC.tslot + C.tile_begin[d];
+            leaf_slots2 = c.dsB.tslot + B.tile_begin[d];
+        } else {
+            const int njobs = sc.job_off[d + 1] - sc.job_off[d];
+            const TcJob *jobs = d_jobs + sc.job_off[d];
+            const int *coff = d_coff + sc.cta_begin[d];
+            const int G = sc.nctas[d];
+            if (njobs > 0) {
+                if (MODE == 0) {
+                    // [U_I.; T_I.] x [T_.J | U_.J]: TL = U T, TR = U U, BR = T U
+                    rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, jobs, njobs, c.pairs_split, c.d_pairs_split,
+                                      chunk, c.PA, slots, c.d_err, SIGNTRI_KC_BLOCK_SUMS_TC, c.st,
+                                      tc_flops(c.pairs_split.n, sum_kb, 3), coff, G);
+                    if (rs != SIGNTRI_OK) return rs;
+                    prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, 4.0 * sum_kb * kb_bytes);
+                } else {
+                    // X^E: [E_I.; T_I.] x [T_.J | E_.J]: TL = E T, BR = T E, and
+                    // Y^E: [U0_I.; E_I.] x [E_.J | U0_.J]: TL = U0 E, BR = E U0.  Side by side
+                    // (same split, CTA c of each on the same tiles and K-blocks at the
+                    // same time) they read the E panels once: six panels for both.
+                    ProfScope pg(SIGNTRI_KC_BLOCK_SUMS_TC, c.st, pair, false);
+                    const int cls = pair ? (SIGNTRI_KC_BLOCK_SUMS_TC | kProfUntimed) : SIGNTRI_KC_BLOCK_SUMS_TC;
+                    cudaStream_t sy = c.st;
+                    if (pair) {
+                        if ((rs = fork()) != SIGNTRI_OK) return rs;
+                        sy = c.side;
+                    }
+                    rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, jobs, njobs, c.pairs_split, c.d_pairs_split,
+                                      chunk, c.PA, slots, c.d_err, cls, c.st, tc_flops(c.pairs_split.n, sum_kb, 2),
+                                      coff, G);
+                    if (rs != SIGNTRI_OK) return rs;
+                    rs = tc_blocksums(srcU_r, srcV_r, srcV_c, srcU_c, jobs, njobs, c.pairs_split, c.d_pairs_split,
+                                      chunk, c.PB, slots, c.d_err, cls, sy, tc_flops(c.pairs_split.n, sum_kb, 2),
+                                      coff, G);
+                    if (rs != SIGNTRI_OK) return rs;
+                    if (pair && (rs = join()) != SIGNTRI_OK) return rs;
+                    prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, (pair ? 6.0 : 8.0) * sum_kb * kb_bytes);
                 }
-                rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
-                                  c.PA, slots, c.d_err, cls, c.st, tc_flops(c.pairs_split.n, sum_kb, 2), coff, G);
-                if (rs != SIGNTRI_OK) return rs;
-                rs = tc_blocksums(srcU_r, srcV_r, srcV_c, srcU_c, jobs, njobs, c.pairs_split, c.d_pairs_split, chunk,
-                                  c.PB, slots, c.d_err, cls, sy, tc_flops(c.pairs_split.n, sum_kb, 2), coff, G);
-                if (rs != SIGNTRI_OK) return rs;
-                if (pair) {
-                    SGT_CUDA_TRY(cudaEventRecord(c.ev_join, c.side));
-                    SGT_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_join, 0));
-                }
-                prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, (pair ? 6 : 8) * panel_bytes);
             }
         }
         ProfScope ps(MODE == 0 ? SIGNTRI_KC_OFFDIAG_LEAF_F32 : SIGNTRI_KC_CORRECTION, c.st);
         mixed_leaf_kernel<MODE><<<ntiles, kLeafThreads, leaf_smem, c.st>>>(
-            n, T, ldt, V, ldv, c.DT32, c.DA32, c.res_c, c.res_s, n, d, d_tslot + sc.tile_begin[d], c.PA, c.PB,
-            Vr, Vc, c.S, nb);
+            n, T, ldt, V, ldv, c.DT32, c.DA32, c.res_c, c.res_s, n, d, leaf_slots, leaf_slots2, c.PA, c.PB, Vr, Vc,
+            c.S, nb);
         SGT_LAUNCH_CHECK();
     }
     return SIGNTRI_OK;
@@ -1219,6 +1357,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     c.d_err = d_err;
     build_schedule(n, kSweepCtas, c.sc);
     build_schedule(n, kSweepCtas / 2, c.sc2);
+    build_look_schedules(n, kSweepCtas / 2, c.scA, c.scB, c.scC);
     const int nb = c.sc.nb;
     const size_t np = c.np;
     const size_t split_elems = (size_t)S * np * np;
@@ -1238,7 +1377,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     c.sbbase = take<int>(ws, (size_t)(n + kSuper - 1) / kSuper + 1);
     c.tmpmax = take<unsigned long long>(ws, np + 64);
     c.tmpmax2 = take<unsigned long long>(ws, np + 64);
-    const size_t maxjobs = (size_t)std::max(c.sc.max_jobs, 1);
+    const size_t maxjobs = (size_t)std::max({c.sc.max_jobs, c.scA.max_jobs, c.scB.max_jobs, c.scC.max_jobs, 1});
     c.PA = take<double>(ws, maxjobs * 16384); c.PB = take<double>(ws, maxjobs * 16384);
     c.E = take<double>(ws, (size_t)n * n); c.R = take<double>(ws, (size_t)n * n);
     c.DT32 = take<float>(ws, (size_t)nb * MB * MB); c.DA32 = take<float>(ws, (size_t)nb * MB * MB);
@@ -1255,6 +1394,12 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     c.d_jobs2 = take<TcJob>(ws, std::max<size_t>(c.sc2.jobs.size(), 1));
     c.d_cta_off2 = take<int>(ws, std::max<size_t>(c.sc2.cta_off.size(), 1));
     c.d_tslot2 = take<int2>(ws, std::max<size_t>(c.sc2.tslot.size(), 1));
+    for (auto pr : {std::make_pair(&c.scA, &c.dsA), std::make_pair(&c.scB, &c.dsB), std::make_pair(&c.scC, &c.dsC)}) {
+        pr.second->jobs = take<TcJob>(ws, std::max<size_t>(pr.first->jobs.size(), 1));
+        pr.second->cta_off = take<int>(ws, std::max<size_t>(pr.first->cta_off.size(), 1));
+        pr.second->tslot = take<int2>(ws, std::max<size_t>(pr.first->tslot.size(), 1));
+        if (!pr.second->jobs || !pr.second->cta_off || !pr.second->tslot) return SIGNTRI_ERR_NO_WORKSPACE;
+    }
     c.d_pairs_split = take<TcPairs>(ws, 1);
     c.d_pairs_oz = take<TcPairs>(ws, 1);
     c.d_pairs_z = take<TcPairs>(ws, 1);
@@ -1330,6 +1475,17 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     if (!c.sc2.tslot.empty())
         SGT_CUDA_TRY(cudaMemcpyAsync(c.d_tslot2, c.sc2.tslot.data(), c.sc2.tslot.size() * sizeof(int2),
                                      cudaMemcpyHostToDevice, st));
+    for (auto pr : {std::make_pair(&c.scA, &c.dsA), std::make_pair(&c.scB, &c.dsB), std::make_pair(&c.scC, &c.dsC)}) {
+        if (!pr.first->jobs.empty())
+            SGT_CUDA_TRY(cudaMemcpyAsync(pr.second->jobs, pr.first->jobs.data(), pr.first->jobs.size() * sizeof(TcJob),
+                                         cudaMemcpyHostToDevice, st));
+        if (!pr.first->cta_off.empty())
+            SGT_CUDA_TRY(cudaMemcpyAsync(pr.second->cta_off, pr.first->cta_off.data(),
+                                         pr.first->cta_off.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        if (!pr.first->tslot.empty())
+            SGT_CUDA_TRY(cudaMemcpyAsync(pr.second->tslot, pr.first->tslot.data(),
+                                         pr.first->tslot.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    }
     {
         const signtri_status ss = side_stream(c);
         if (ss != SIGNTRI_OK) return ss;

@@ -116,7 +116,10 @@ def test_sweep_operand_byte_count(gpu_lib, n):
     # of the nb = ceil(n/64) block partition reads, per tile (I, I+d), 64-row
     # panels of three bf16 slices over its d+1 K-blocks once: four panels in
     # the initial sweep, six for the correction's two launches side by side
-    # (they share the E panels); one refinement step
+    # (they share the E panels).  In the initial sweep a lead anti-diagonal d
+    # (odd, >= 3, d + 1 < nb) also sums d + 1's tiles over K-blocks
+    # I+2 .. I+d-1 reading only new column panels, and d + 1 then completes
+    # four K-blocks per tile.  One refinement step.
     import torch
     T = make_T(n, 0.5, seed=n)
     Tt = gpu_lib.to_device(T)
@@ -134,8 +137,17 @@ def test_sweep_operand_byte_count(gpu_lib, n):
     info = gpu_lib.signtri_get_info()
     assert info.variant == gpu_lib.Variant.PH_MIXED_TF32 and info.refine_steps == 1, info.as_dict()
     nb = (n + 63) // 64
-    panel = sum((nb - d) * (d + 1) for d in range(1, nb)) * 3 * 64 * 64 * 2
-    assert got == (4 + 6) * panel, (got, panel)
+    lead = lambda d: d >= 3 and d % 2 == 1 and d + 1 < nb
+    follow = lambda d: d >= 4 and d % 2 == 0 and lead(d - 1)
+    units = 0
+    for d in range(1, nb):
+        kb = (nb - d) * (d + 1)
+        if follow(d):
+            units += 4 * 4 * (nb - d)
+        else:
+            units += 4 * kb + (2 * (nb - d - 1) * (d - 2) if lead(d) else 0)
+        units += 6 * kb
+    assert got == units * 3 * 64 * 64 * 2, (got, units)
     # tensor work: 6 slice pairs x 2*64^3 per tile K-block and used quadrant (3 in the
     # initial sweep, 2 in each correction launch)
     kb = sum((nb - d) * (d + 1) for d in range(1, nb))
