@@ -424,6 +424,21 @@ def main():
                 "peak_source": "bf16_tflops_sustained of %s (kernel timed inside a long step)" % src,
                 "share_of_step": per_class[dom]["device_ms"] / ms_total}
 
+    # the residual products (second class of the mixed step) against the tensor roof
+    roof2 = None
+    if "residual" in per_class and dom != "residual":
+        peaks, src = measured_peaks()
+        fl = st.signtri_profile_read_flops(st.signtri.KC_RESIDUAL)
+        ms_r = per_class["residual"]["device_ms"]
+        if fl > 0 and ms_r > 0:
+            peak_t = float(peaks.get("bf16_tflops_sustained", 1700.0))
+            ach_t = fl / (ms_r * 1e-3) / 1e12
+            roof2 = {"class": "residual", "bound": "tensor", "achieved": ach_t, "peak": peak_t, "unit": "TFLOP/s",
+                     "frac": ach_t / peak_t,
+                     "kernel": "tc_pair2_kernel / tc_blocksum_kernel (emulated-float64 residual and probe products)",
+                     "peak_source": "bf16_tflops_sustained of %s" % src,
+                     "share_of_step": ms_r / ms_total}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step_max, "seconds_per_solve": ms_step_max / 1e3,
@@ -438,7 +453,8 @@ def main():
                    "l2": ("no flush: T and U are %.3g GB each, > 129 MB L2" % (8e-9 * n * n) if 8 * n * n > 129e6
                           else "T and U (%.3g MB each) fit in L2: warm-cache timing" % (8e-6 * n * n)),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "gpu_launches": launches, "kernel_time_ms": per_class, "roofline": roof, "clocks": clk,
+        "gpu_launches": launches, "kernel_time_ms": per_class, "roofline": roof, "roofline_second": roof2,
+        "clocks": clk,
         "refinement": {"steps": info.refine_steps, "resid_commute": info.resid_commute,
                        "resid_involution": info.resid_involution},
     }
