@@ -49,10 +49,16 @@ typedef enum {
        T11 X - X T22 = 2 T12, transform back. */
     SIGNTRI_PS_FP64 = 2,
     /* Parlett-Higham with TF32 tensor-core block updates, then float64
-       refinement of both defining equations. */
+       refinement of both defining equations.  Some of its tensor-core
+       launches run on side streams the library creates once per device;
+       they are forked from and joined back into the caller's stream with
+       events, so all of the call's work is ordered on `stream` as usual.
+       The host waits on `stream` a few times during the call (diagonal
+       signs, residual norms). */
     SIGNTRI_PH_MIXED_TF32 = 3,
     /* Parlett-Higham with BF16 tensor-core block updates, then float64
-       refinement of both defining equations. */
+       refinement of both defining equations (side streams and host waits as
+       above). */
     SIGNTRI_PH_MIXED_BF16 = 4,
     /* Arithmetic-efficient recursive Parlett-Higham (Section 5.3), float64:
        each entry's block sum is X (signs differ) or Y (signs agree) only,
