@@ -1078,13 +1078,38 @@ signtri_status setup_gathered(MixedCtx &c, const double *T, int ldt)
         for (int o = 0; o < len; o += 128) v.push_back({start + o, o + 64 < len ? start + o + 64 : c.ng});
         return v;
     };
+    // original indices of each superblock's positives and negatives, ascending
+    std::vector<std::vector<int>> porig(nsb), norig(nsb);
+    for (int i = 0; i < n; i++) (pos[i] ? porig : norig)[i / kSuper].push_back(i);
+    // K range of a job: the products vanish unless row < k < column, so in the
+    // rows' superblock the K-blocks before the first positive above the rows'
+    // smallest index are skipped (positives come first there) and in the
+    // columns' superblock those after the last negative below the columns'
+    // largest index (negatives come last); what lies between stays (zeros)
+    auto k_start = [&](int sr, int cr, int first) {
+        if (cr == 0) return first / 64;
+        const int rmin = ginv[first];
+        const int cp = (int)(std::upper_bound(porig[sr].begin(), porig[sr].end(), rmin) - porig[sr].begin());
+        return (base[sr] + cp) / 64;
+    };
+    auto k_end = [&](int sc, int cc, const std::pair<int, int> &cpair) {
+        int last = -1;   // gathered position of the pair's last real column
+        for (int gpos : {cpair.second, cpair.first})
+            if (gpos < c.ng && last < 0)
+                for (int q = gpos + 63; q >= gpos; q--)
+                    if (ginv[q] >= 0) { last = q; break; }
+        const int cmax = ginv[last];
+        const int cn = (int)(std::lower_bound(norig[sc].begin(), norig[sc].end(), cmax) - norig[sc].begin());
+        const int end = base[sc] + cls_len[0][sc] + cn;
+        return (end + 63) / 64;
+    };
     std::vector<TcJob> same, opp;
     double kb_same = 0.0, kb_opp = 0.0;
-    // longest K ranges first (load balance); one superblock pair's jobs together
+    // longest superblock spans first (load balance); one superblock pair's
+    // jobs together (they share operand panels in L2)
     for (int span = nsb - 1; span >= 0; span--)
         for (int sr = 0; sr + span < nsb; sr++) {
             const int sc = sr + span;
-            const int kb0 = base[sr] / 64, kb1 = base[sc + 1] / 64;
             for (int cr = 0; cr < 2; cr++)
                 for (int cc = 0; cc < 2; cc++) {
                     const auto rows = pairs_of(sr, cr), cols = pairs_of(sc, cc);
@@ -1092,13 +1117,16 @@ signtri_status setup_gathered(MixedCtx &c, const double *T, int ldt)
                         for (const auto &cp : cols) {
                             TcJob j;
                             j.rt = rp.first; j.rb = rp.second; j.cl = cp.first; j.cr = cp.second;
-                            j.kb0 = kb0; j.kb1 = kb1; j.slot = 0; j.pad = 0;
+                            j.kb0 = k_start(sr, cr, rp.first);
+                            j.kb1 = std::max(j.kb0, k_end(sc, cc, cp));
+                            j.slot = 0; j.pad = 0;
                             const double used = (double)((rp.second < c.ng) + 1) * ((cp.second < c.ng) + 1);
-                            if (cr == cc) { same.push_back(j); kb_same += used * (kb1 - kb0); }
-                            else { opp.push_back(j); kb_opp += used * (kb1 - kb0); }
+                            if (cr == cc) { same.push_back(j); kb_same += used * (j.kb1 - j.kb0); }
+                            else { opp.push_back(j); kb_opp += used * (j.kb1 - j.kb0); }
                         }
                 }
         }
+
     c.n_res_same = (int)same.size();
     c.n_res_opp = (int)opp.size();
     c.res_kb_same = kb_same;
