@@ -964,12 +964,15 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
             rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, c.dsA.jobs + A.job_off[d], A.job_off[d + 1] - A.job_off[d],
                               c.pairs_split, c.d_pairs_split, chunk, c.PA, slots, c.d_err, cls, c.st,
                               tc_flops(c.pairs_split.n, sum_kb, 3), c.dsA.cta_off + A.cta_begin[d], A.nctas[d]);
+            if (rs == SIGNTRI_OK)
+                rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, c.dsB.jobs + B.job_off[e],
+                                  B.job_off[e + 1] - B.job_off[e], c.pairs_split, c.d_pairs_split, chunk, c.PB, slots,
+                                  c.d_err, cls, c.side, tc_flops(c.pairs_split.n, look_kb, 3),
+                                  c.dsB.cta_off + B.cta_begin[e], B.nctas[e]);
+            // join even after a failed launch: nothing on the side stream outlives the call
+            const signtri_status rj = join();
             if (rs != SIGNTRI_OK) return rs;
-            rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, c.dsB.jobs + B.job_off[e], B.job_off[e + 1] - B.job_off[e],
-                              c.pairs_split, c.d_pairs_split, chunk, c.PB, slots, c.d_err, cls, c.side,
-                              tc_flops(c.pairs_split.n, look_kb, 3), c.dsB.cta_off + B.cta_begin[e], B.nctas[e]);
-            if (rs != SIGNTRI_OK) return rs;
-            if ((rs = join()) != SIGNTRI_OK) return rs;
+            if (rj != SIGNTRI_OK) return rj;
             // the look-ahead reads its row panels from L2: only its column panels are new
             prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, (4.0 * sum_kb + 2.0 * look_kb) * kb_bytes);
             leaf_slots = c.dsA.tslot + A.tile_begin[d];
@@ -1013,12 +1016,13 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
                     rs = tc_blocksums(srcV_r, srcT_r, srcT_c, srcV_c, jobs, njobs, c.pairs_split, c.d_pairs_split,
                                       chunk, c.PA, slots, c.d_err, cls, c.st, tc_flops(c.pairs_split.n, sum_kb, 2),
                                       coff, G);
+                    if (rs == SIGNTRI_OK)
+                        rs = tc_blocksums(srcU_r, srcV_r, srcV_c, srcU_c, jobs, njobs, c.pairs_split,
+                                          c.d_pairs_split, chunk, c.PB, slots, c.d_err, cls, sy,
+                                          tc_flops(c.pairs_split.n, sum_kb, 2), coff, G);
+                    const signtri_status rj = pair ? join() : SIGNTRI_OK;   // also after a failed launch
                     if (rs != SIGNTRI_OK) return rs;
-                    rs = tc_blocksums(srcU_r, srcV_r, srcV_c, srcU_c, jobs, njobs, c.pairs_split, c.d_pairs_split,
-                                      chunk, c.PB, slots, c.d_err, cls, sy, tc_flops(c.pairs_split.n, sum_kb, 2),
-                                      coff, G);
-                    if (rs != SIGNTRI_OK) return rs;
-                    if (pair && (rs = join()) != SIGNTRI_OK) return rs;
+                    if (rj != SIGNTRI_OK) return rj;
                     prof_add_bytes(SIGNTRI_KC_BLOCK_SUMS_TC, (pair ? 6.0 : 8.0) * sum_kb * kb_bytes);
                 }
             }
