@@ -38,12 +38,20 @@
 //    and one in its columns, and a tensor-core job computes four such blocks
 //    that all need the same product (Y = N_U N_U, or one of the two parts of
 //    X).  Block upper triangular structure survives at superblock level, so a
-//    job's K range is whole superblocks (the extra terms are structural zeros).
+//    job's K range lies within its superblocks, trimmed to where its rows and
+//    columns can have nonzero terms (the rest are structural zeros).
 //    The full residuals use the original layout and four-quadrant jobs
 //    [N_T I.; N_U I.] x [N_U .J | N_T .J].  Stop when ||Rc||_F / (||T||_F
 //    ||U||_F) and ||Rs||_F / ||U||_F^2 are both below the tolerance; fall back
 //    to the float64 path when a step does not reduce the larger of the two by
 //    a factor 10, or after the step limit.
+// 3. Memory traffic.  The sweeps stream each tile's operand panels once per
+//    anti-diagonal (bf16 slices stored as contiguous 64 x 64 tiles).  Launches
+//    that read the same panels run side by side on side streams with matched
+//    CTA splits, so the second read comes from L2: the correction's X^E and
+//    Y^E (shared E panels), and the initial sweep's look-ahead pairs, where an
+//    anti-diagonal's tiles sum the next one's interior K-blocks (shared row
+//    panels) and a short completion launch adds the four K-blocks left.
 #include <algorithm>
 #include <utility>
 #include <cmath>
@@ -794,9 +802,7 @@ struct MixedCtx {
     cudaStream_t st;
     int *d_err;
     Schedule sc, sc2;           // initial sweep; correction (two launches side by side)
-    TcJob *d_jobs, *d_jobs2;
-    int *d_cta_off, *d_cta_off2;
-    int2 *d_tslot, *d_tslot2;
+    DevSchedule ds, ds2;
     Schedule scA, scB, scC;     // initial sweep's look-ahead pairs: lead, look-ahead, completion
     DevSchedule dsA, dsB, dsC;
     cudaStream_t side;          // second stream of the correction launches (null: one stream)
@@ -933,9 +939,10 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
     const bool pair = (MODE == 1) && c.side != nullptr;
     const bool look = (MODE == 0) && c.side != nullptr;
     const Schedule &sc = pair ? c.sc2 : c.sc;
-    const TcJob *d_jobs = pair ? c.d_jobs2 : c.d_jobs;
-    const int *d_coff = pair ? c.d_cta_off2 : c.d_cta_off;
-    const int2 *d_tslot = pair ? c.d_tslot2 : c.d_tslot;
+    const DevSchedule &ds = pair ? c.ds2 : c.ds;
+    const TcJob *d_jobs = ds.jobs;
+    const int *d_coff = ds.cta_off;
+    const int2 *d_tslot = ds.tslot;
     const double kb_bytes = (double)c.S * MB * MB * 2;   // one 64-row panel of S bf16 slices, one K-block
     auto fork = [&]() -> signtri_status {
         SGT_CUDA_TRY(cudaEventRecord(c.ev_fork, c.st));
@@ -1420,13 +1427,8 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     c.norms = take<double>(ws, 8);
     const size_t pairs_max = ngr / 128 + 2 * (size_t)((n + kSuper - 1) / kSuper) + 2;
     c.d_res_jobs = take<TcJob>(ws, pairs_max * pairs_max);
-    c.d_jobs = take<TcJob>(ws, std::max<size_t>(c.sc.jobs.size(), 1));
-    c.d_cta_off = take<int>(ws, std::max<size_t>(c.sc.cta_off.size(), 1));
-    c.d_tslot = take<int2>(ws, std::max<size_t>(c.sc.tslot.size(), 1));
-    c.d_jobs2 = take<TcJob>(ws, std::max<size_t>(c.sc2.jobs.size(), 1));
-    c.d_cta_off2 = take<int>(ws, std::max<size_t>(c.sc2.cta_off.size(), 1));
-    c.d_tslot2 = take<int2>(ws, std::max<size_t>(c.sc2.tslot.size(), 1));
-    for (auto pr : {std::make_pair(&c.scA, &c.dsA), std::make_pair(&c.scB, &c.dsB), std::make_pair(&c.scC, &c.dsC)}) {
+    for (auto pr : {std::make_pair(&c.sc, &c.ds), std::make_pair(&c.sc2, &c.ds2), std::make_pair(&c.scA, &c.dsA),
+                    std::make_pair(&c.scB, &c.dsB), std::make_pair(&c.scC, &c.dsC)}) {
         pr.second->jobs = take<TcJob>(ws, std::max<size_t>(pr.first->jobs.size(), 1));
         pr.second->cta_off = take<int>(ws, std::max<size_t>(pr.first->cta_off.size(), 1));
         pr.second->tslot = take<int2>(ws, std::max<size_t>(pr.first->tslot.size(), 1));
@@ -1452,9 +1454,8 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     if (!c.Tr || !c.Tc || !c.Ur || !c.Uc || !c.Er || !c.Ec || !c.NTgr || !c.NTgc || !c.NTr || !c.NTc || !c.NUr ||
         !c.NUc || !c.d_full_jobs || !c.sTr ||
         !c.sTc || !c.sUr || !c.sUc || !c.gTr || !c.gTc || !c.gUr || !c.gUc || !c.gmap || !c.ginv || !c.pos ||
-        !c.tmpmax || !c.tmpmax2 || !c.PA || !c.PB || !c.E || !c.R || !c.RA || !c.RB || !c.norms || !c.d_res_jobs || !c.d_jobs ||
-        !c.d_pairs_split || !c.d_pairs_oz || !c.d_cta_off || !c.d_tslot || !c.DT32 || !c.DA32 || !c.sbbase ||
-        !c.d_jobs2 || !c.d_cta_off2 || !c.d_tslot2)
+        !c.tmpmax || !c.tmpmax2 || !c.PA || !c.PB || !c.E || !c.R || !c.RA || !c.RB || !c.norms || !c.d_res_jobs ||
+        !c.d_pairs_split || !c.d_pairs_oz || !c.DT32 || !c.DA32 || !c.sbbase)
         return SIGNTRI_ERR_NO_WORKSPACE;
     c.pairs_split = split_pairs(S);
     c.pairs_oz = ozaki_pairs_impl(kOzakiSlices, kOzakiBits);
@@ -1489,25 +1490,8 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
                                      st));
         SGT_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    if (!c.sc.jobs.empty())
-        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_jobs, c.sc.jobs.data(), c.sc.jobs.size() * sizeof(TcJob),
-                                     cudaMemcpyHostToDevice, st));
-    if (!c.sc.cta_off.empty())
-        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_cta_off, c.sc.cta_off.data(), c.sc.cta_off.size() * sizeof(int),
-                                     cudaMemcpyHostToDevice, st));
-    if (!c.sc.tslot.empty())
-        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_tslot, c.sc.tslot.data(), c.sc.tslot.size() * sizeof(int2),
-                                     cudaMemcpyHostToDevice, st));
-    if (!c.sc2.jobs.empty())
-        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_jobs2, c.sc2.jobs.data(), c.sc2.jobs.size() * sizeof(TcJob),
-                                     cudaMemcpyHostToDevice, st));
-    if (!c.sc2.cta_off.empty())
-        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_cta_off2, c.sc2.cta_off.data(), c.sc2.cta_off.size() * sizeof(int),
-                                     cudaMemcpyHostToDevice, st));
-    if (!c.sc2.tslot.empty())
-        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_tslot2, c.sc2.tslot.data(), c.sc2.tslot.size() * sizeof(int2),
-                                     cudaMemcpyHostToDevice, st));
-    for (auto pr : {std::make_pair(&c.scA, &c.dsA), std::make_pair(&c.scB, &c.dsB), std::make_pair(&c.scC, &c.dsC)}) {
+    for (auto pr : {std::make_pair(&c.sc, &c.ds), std::make_pair(&c.sc2, &c.ds2), std::make_pair(&c.scA, &c.dsA),
+                    std::make_pair(&c.scB, &c.dsB), std::make_pair(&c.scC, &c.dsC)}) {
         if (!pr.first->jobs.empty())
             SGT_CUDA_TRY(cudaMemcpyAsync(pr.second->jobs, pr.first->jobs.data(), pr.first->jobs.size() * sizeof(TcJob),
                                          cudaMemcpyHostToDevice, st));
