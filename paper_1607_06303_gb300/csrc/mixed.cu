@@ -1171,7 +1171,7 @@ signtri_status gathered_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bf
 // Exact slices of the strictly upper part of M in the original layout (scales
 // computed here unless `scaled`).
 signtri_status exact_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bfloat16 *R, __nv_bfloat16 *C, float *sR,
-                               float *sC, bool scaled = false)
+                               float *sC, bool scaled = false, bool cols = true)
 {
     signtri_status rs;
     if (!scaled &&
@@ -1183,6 +1183,7 @@ signtri_status exact_slices_of(MixedCtx &c, const double *M, int ldm, __nv_bfloa
     if ((rs = make_row_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, kOzakiBits, sR, R, c.np + 64, c.np, c.st, 1)) !=
         SIGNTRI_OK)
         return rs;
+    if (!cols) return SIGNTRI_OK;
     return make_col_slices(c.n, c.n, M, ldm, 1, kOzakiSlices, kOzakiBits, sC, C, c.np + 64, c.np, c.st, 1);
 }
 
@@ -1542,8 +1543,10 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     signtri_status rs;
     if ((rs = split_full(c, T, ldt, c.Tr, c.Tc)) != SIGNTRI_OK) return rs;
     if ((rs = gathered_slices_of(c, T, ldt, c.NTgr, c.NTgc, c.sTr, c.sTc, c.gTr, c.gTc)) != SIGNTRI_OK) return rs;
-    // T's scales serve both layouts
-    if ((rs = exact_slices_of(c, T, ldt, c.NTr, c.NTc, c.sTr, c.sTc, true)) != SIGNTRI_OK) return rs;
+    // T's scales serve both layouts; the probe check reads only T's row
+    // slices, the full residual also its column slices
+    if ((rs = exact_slices_of(c, T, ldt, c.NTr, c.NTc, c.sTr, c.sTc, true, prm.verify_full != 0)) != SIGNTRI_OK)
+        return rs;
 
     // 1. low-precision solve: diagonal blocks in float64, the rest by sweep
     if ((rs = launch_zero_strict_lower(n, U, ldu, st)) != SIGNTRI_OK) return rs;
