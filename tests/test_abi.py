@@ -66,3 +66,18 @@ def test_host_side_argument_checks(lib):
     assert lib.signtri_workspace_bytes(100, 1) >= 0
     info = lib.signtri_get_info()
     assert info.n == -3 and info.bad_index == -1
+
+
+def test_profile_counters_host_side(lib):
+    # counters are host state: readable and resettable without a GPU; bad
+    # classes are rejected
+    import ctypes
+    L = lib.load()
+    v = ctypes.c_double(-1.0)
+    assert L.signtri_profile_read_flops(99, ctypes.byref(v)) == lib.Status.ERR_BAD_ARG
+    assert L.signtri_profile_read_bytes(-1, ctypes.byref(v)) == lib.Status.ERR_BAD_ARG
+    assert L.signtri_profile_read_bytes(lib.signtri.KC_BLOCK_SUMS_TC, None) == lib.Status.ERR_BAD_ARG
+    assert lib.signtri_profile_reset() == lib.Status.OK
+    assert lib.signtri_profile_read_bytes(lib.signtri.KC_BLOCK_SUMS_TC) == 0.0
+    assert lib.signtri_profile_read_flops(lib.signtri.KC_RESIDUAL) == 0.0
+    assert lib.signtri_kernel_class_name(lib.signtri.KC_BLOCK_SUMS_TC) == "block_sums_tc"
