@@ -48,7 +48,7 @@ UNIT = "GFLOP/s"
 TRAFFIC = {}
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -68,7 +68,7 @@ def parse_args():
     ap.add_argument("--workload", choices=["single", "batched"], default="single",
                     help="batched: 2000 problems, n log-uniform in [32, 2048], p ~ U[0,1], random order")
     ap.add_argument("--batch", type=int, default=2000)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # ---------------------------------------------------------------- clocks ---
@@ -127,13 +127,13 @@ def run_reference(args, rank):
     leading principal window of the same input: a bounded sample of the
     workload with the same structure (u_ij of a window depends on the window
     only)."""
+    if rank != 0:
+        return None
     import numpy as np
 
     import oracle
     from paper_1607_06303_gb300 import workload
     from paper_1607_06303_gb300.inputs import make_T
-    if rank != 0:
-        return None
     m = min(args.cpu_sample if args.cpu_sample else 3072, args.n)
     T = make_T(args.n, args.p, seed=0, order=args.order)
     Tw = np.asfortranarray(T[:m, :m])
@@ -286,6 +286,17 @@ def run_batched(args):
     return 0
 
 
+def reduce_over_ranks(dist, x, op, device):
+    """x reduced over the replicas ("max" for times, "sum" for work done);
+    x itself when the bench runs as one process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def main():
     args = parse_args()
     if args.workload == "batched" and args.impl == "ours":
@@ -363,11 +374,11 @@ def main():
             per_class[st.signtri_kernel_class_name(c)] = {"launches": cnt, "device_ms": ms}
     info = st.signtri_get_info()
     ms_step = ms_total / max(args.steps, 1)
-    t_max = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_step_max = float(t_max.item())
-    value = world * useful / (ms_step_max * 1e-3) / 1e9
+    ms_step_max = reduce_over_ranks(dist, ms_step, "max", "cuda")
+    # each replica solves its own input (seed = rank): the job's work is the
+    # sum of the replicas' useful flops
+    useful_all = reduce_over_ranks(dist, useful, "sum", "cuda")
+    value = useful_all / (ms_step_max * 1e-3) / 1e9
 
     # roofline of the dominant kernel class
     dom = max(per_class.items(), key=lambda kv: kv[1]["device_ms"])[0] if per_class else None
@@ -478,13 +489,10 @@ def main():
                     raise st.SignTriError(s, "sign_tri_host")
             barrier()
             reps.append((time.perf_counter() - t0) / max(args.steps, 1))
-        e2e_s = statistics.median(reps)
-        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        line["e2e"] = {"value": world * useful / float(te.item()) / 1e9, "unit": UNIT,
+        e2e_s = reduce_over_ranks(dist, statistics.median(reps), "max", "cuda")
+        line["e2e"] = {"value": useful_all / e2e_s / 1e9, "unit": UNIT,
                        "h2d_bytes_per_step": Th.numel() * 8, "d2h_bytes_per_step": Uh.numel() * 8,
-                       "seconds_per_solve": float(te.item()), "repetitions_s": reps}
+                       "seconds_per_solve": e2e_s, "repetitions_s": reps}
         del Th, Uh
 
     # comparison variants on the same input (float64 forms), fewer steps
@@ -506,13 +514,9 @@ def main():
             cstep()
         c1.record(stream)
         barrier()
-        cms = c0.elapsed_time(c1) / ck
-        tc_ = torch.tensor([cms], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(tc_, op=dist.ReduceOp.MAX)
-        cms = float(tc_.item())
+        cms = reduce_over_ranks(dist, c0.elapsed_time(c1) / ck, "max", "cuda")
         compares.append(({"variant": cname, "steps": ck, "seconds_per_solve": cms / 1e3,
-                          "value": world * useful / (cms * 1e-3) / 1e9, "unit": UNIT,
+                          "value": useful_all / (cms * 1e-3) / 1e9, "unit": UNIT,
                           "speedup_of_headline": cms / ms_step_max}, Uc))
     if compares:
         line["compare"] = [c for c, _ in compares]

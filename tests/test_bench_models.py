@@ -44,3 +44,44 @@ def test_efficient_is_between_third_and_two_thirds_of_mm():
     alt = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
     e = bench.block_sum_flops_efficient(n, b, alt)
     assert bench.block_sum_flops(n, b) / 3 < e < 2 * bench.block_sum_flops(n, b) / 3 + 1
+
+
+def _replica_worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # rank r: a step of 10 + r ms over 1e12 (1 + r) useful flops
+        t = bench.reduce_over_ranks(dist, 10.0 + rank, "max", "cpu")
+        w = bench.reduce_over_ranks(dist, 1e12 * (1 + rank), "sum", "cpu")
+        with open(os.path.join(out_dir, "r%d.txt" % rank), "w") as f:
+            f.write("%r %r\n" % (t, w))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replica_aggregation_two_gloo_ranks(tmp_path):
+    """The N > 1 bench path: the time is the slowest replica's, the work the
+    sum of all replicas' (each rank solves its own seeded input)."""
+    import multiprocessing as mp
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_replica_worker, args=(r, 2, port, str(tmp_path))) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    for r in range(2):
+        t, w = map(float, (tmp_path / ("r%d.txt" % r)).read_text().split())
+        assert t == 11.0 and w == 3e12
+    assert bench.reduce_over_ranks(None, 7.5, "max", "cpu") == 7.5
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """Under torchrun only rank 0 times the oracle; the other ranks exit
+    without work."""
+    assert bench.run_reference(bench.parse_args(["--impl", "reference"]), 1) is None
