@@ -13,7 +13,7 @@ HEADER = os.path.join(ROOT, "include", "signtri.h")
 def declared_functions():
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\**\s*([a-z_]+)\s*\(", txt, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\**\s*([a-z_0-9]+)\s*\(", txt, flags=re.M)
     return sorted(set(names))
 
 
@@ -81,3 +81,71 @@ def test_profile_counters_host_side(lib):
     assert lib.signtri_profile_read_bytes(lib.signtri.KC_BLOCK_SUMS_TC) == 0.0
     assert lib.signtri_profile_read_flops(lib.signtri.KC_RESIDUAL) == 0.0
     assert lib.signtri_kernel_class_name(lib.signtri.KC_BLOCK_SUMS_TC) == "block_sums_tc"
+
+
+def _header_text():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return re.sub(r"//.*", "", txt)
+
+
+def _c_kind(decl):
+    """'ptr', or the base type of a C declaration without its name."""
+    decl = " ".join(decl.replace("const", " ").split())
+    if "*" in decl:
+        return "ptr"
+    words = decl.split()
+    base = " ".join(words[:-1]) if len(words) > 1 else words[0]
+    return {"signtri_variant": "int", "signtri_status": "int"}.get(base, base)
+
+
+def _ctypes_kind(t):
+    import ctypes
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return "ptr"
+    return {ctypes.c_int: "int", ctypes.c_size_t: "size_t", ctypes.c_double: "double",
+            ctypes.c_longlong: "long long"}[t]
+
+
+def test_binding_signatures_match_header():
+    """Every prototype of include/signtri.h against the ctypes signature the
+    binding installs: same arity, same kind (pointer, int, size_t, double,
+    long long) in every position and in the return type."""
+    from paper_1607_06303_gb300 import signtri
+    protos = re.findall(r"^\s*((?:const\s+)?[a-z_]+\s*\**)\s*([a-z_0-9]+)\s*\(([^)]*)\)\s*;", _header_text(),
+                        flags=re.M)
+    assert len(protos) == len(declared_functions())
+    for ret, name, params in protos:
+        res, args = signtri._SIGNATURES[name]
+        params = " ".join(params.split())
+        c_args = [] if params in ("", "void") else [_c_kind(p) for p in params.split(",")]
+        assert c_args == [_ctypes_kind(a) for a in args], name
+        assert _c_kind(ret + " r") == _ctypes_kind(res), name
+    assert set(signtri._SIGNATURES) == {p[1] for p in protos}
+
+
+def test_binding_constants_match_header():
+    """Variant and status codes, kernel classes and the signtri_info layout."""
+    import ctypes
+
+    from paper_1607_06303_gb300 import signtri
+    txt = _header_text()
+    enums = {k: int(v) for k, v in re.findall(r"\b(SIGNTRI_[A-Z0-9_]+)\s*=\s*(\d+)", txt)}
+    for v in signtri.Variant:
+        assert enums["SIGNTRI_" + v.name] == v.value
+    for s in signtri.Status:
+        assert enums["SIGNTRI_" + s.name] == s.value
+    alias = {"OFFDIAG_LEAF_F32": "OFFDIAG_LEAF_MIXED"}
+    kcs = {k[len("SIGNTRI_KC_"):]: v for k, v in enums.items() if k.startswith("SIGNTRI_KC_")}
+    for k, v in kcs.items():
+        assert getattr(signtri, "KC_" + alias.get(k, k)) == v, k
+    body = re.search(r"typedef struct \{(.*?)\}\s*signtri_info;", txt, flags=re.S).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        words = decl.split(" ", 1) if not decl.startswith("long long") else ["long long", decl[10:]]
+        fields += [(n.strip(), words[0]) for n in words[1].split(",")]
+    kinds = {"int": ctypes.c_int, "double": ctypes.c_double, "long long": ctypes.c_longlong}
+    assert [(f, kinds[t]) for f, t in fields] == [(f, t) for f, t in signtri.Info._fields_]
