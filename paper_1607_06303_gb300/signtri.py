@@ -290,17 +290,37 @@ def _stream_handle(stream=None):
     return s.cuda_stream
 
 
+def check_operands(Tt, Ut=None):
+    """The checks sign() makes before a pointer reaches the library: T (and
+    U, when given) square, contiguous float64 CUDA tensors; U with T's shape
+    and device and no byte in common with T (sign_tri writes all n*n entries
+    of U and reads T while it does)."""
+    import torch
+    for name, t in (("T", Tt), ("out", Ut)):
+        if t is None:
+            continue
+        if t.dtype != torch.float64 or not t.is_cuda or t.dim() != 2 or t.shape[0] != t.shape[1]:
+            raise ValueError("%s must be a square CUDA float64 tensor" % name)
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    if Ut is not None:
+        if tuple(Ut.shape) != tuple(Tt.shape) or Ut.device != Tt.device:
+            raise ValueError("out must have T's shape and device")
+        nbytes = 8 * Tt.numel()
+        if nbytes and Ut.data_ptr() < Tt.data_ptr() + nbytes and Tt.data_ptr() < Ut.data_ptr() + nbytes:
+            raise ValueError("out must not overlap T")
+
+
 def sign(Tt, variant=Variant.AUTO, out=None, stream=None, check=True):
     """U = sign(T) for a CUDA float64 tensor holding T column-major (see the
-    module docstring).  Returns the tensor holding U in the same layout."""
+    module docstring).  Returns the tensor holding U in the same layout.
+    Runs on T's device, on `stream` (default: that device's current stream)."""
     import torch
-    if Tt.dtype != torch.float64 or not Tt.is_cuda or Tt.dim() != 2 or Tt.shape[0] != Tt.shape[1]:
-        raise ValueError("T must be a square CUDA float64 tensor")
-    if not Tt.is_contiguous():
-        raise ValueError("T must be contiguous")
+    check_operands(Tt, out)
     n = Tt.shape[0]
     Ut = out if out is not None else torch.empty_like(Tt)
-    st = sign_tri(n, Tt.data_ptr(), max(n, 1), Ut.data_ptr(), max(n, 1), variant, _stream_handle(stream))
+    with torch.cuda.device(Tt.device):
+        st = sign_tri(n, Tt.data_ptr(), max(n, 1), Ut.data_ptr(), max(n, 1), variant, _stream_handle(stream))
     if check and st != 0:
         raise SignTriError(st, "sign_tri")
     return Ut

@@ -149,3 +149,55 @@ def test_binding_constants_match_header():
         fields += [(n.strip(), words[0]) for n in words[1].split(",")]
     kinds = {"int": ctypes.c_int, "double": ctypes.c_double, "long long": ctypes.c_longlong}
     assert [(f, kinds[t]) for f, t in fields] == [(f, t) for f, t in signtri.Info._fields_]
+
+
+class _FakeCudaTensor:
+    """Attributes sign()'s checks read, without a GPU."""
+
+    def __init__(self, n, ptr, dtype=None, cuda=True, contiguous=True, device="cuda:0", shape=None):
+        import torch
+        self.shape = shape or (n, n)
+        self.dtype = dtype or torch.float64
+        self.is_cuda = cuda
+        self._contig = contiguous
+        self.device = torch.device(device)
+        self._ptr = ptr
+
+    def dim(self):
+        return len(self.shape)
+
+    def is_contiguous(self):
+        return self._contig
+
+    def numel(self):
+        out = 1
+        for s in self.shape:
+            out *= s
+        return out
+
+    def data_ptr(self):
+        return self._ptr
+
+
+def test_sign_operand_checks():
+    """sign() rejects, before any library call, operands that would make the
+    kernels read or write outside a tensor: wrong dtype, shape, layout,
+    device, or an output overlapping T."""
+    import torch
+
+    from paper_1607_06303_gb300.signtri import check_operands
+    F = _FakeCudaTensor
+    T = F(8, 1 << 20)
+    check_operands(T)
+    check_operands(T, F(8, (1 << 20) + 512))                  # adjacent, not overlapping
+    check_operands(F(0, 4096), F(0, 4096))                    # empty: nothing to overlap
+    bad = [(F(8, 4096, dtype=torch.float32), None), (F(8, 4096, cuda=False), None),
+           (F(8, 4096, shape=(8, 9)), None), (F(8, 4096, contiguous=False), None),
+           (T, F(9, 4096)), (T, F(8, 4096, device="cuda:1")), (T, F(8, (1 << 20) + 504)),
+           (T, F(8, (1 << 20) - 8)), (T, F(8, 1 << 20)), (T, F(8, 4096, dtype=torch.float32))]
+    for t, u in bad:
+        with pytest.raises(ValueError):
+            check_operands(t, u)
+    with pytest.raises(ValueError):
+        from paper_1607_06303_gb300 import sign
+        sign(torch.zeros(4, 4, dtype=torch.float64))           # a CPU tensor never reaches the library
