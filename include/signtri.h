@@ -11,7 +11,10 @@
  *   - Matrices are float64, column-major: element (i,j) (0-based) of a matrix
  *     M with leading dimension ld is M[i + j*ld].  ld >= max(1, n).
  *   - Pointers named T, U are DEVICE pointers unless the name says _host.
- *     They are owned by the caller.  T and U must not overlap.
+ *     They are owned by the caller.  T and U must not share an element:
+ *     the device-pointer entry points compare the two blocks (exactly, so
+ *     disjoint blocks interleaved in one array through their leading
+ *     dimensions are fine) and return SIGNTRI_ERR_BAD_ARG before any work.
  *   - Only the upper triangle of T (i <= j) is read.  All of the n x n part of
  *     U is written; its strictly lower triangle is set to 0.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
@@ -71,7 +74,8 @@ typedef enum {
 
 typedef enum {
     SIGNTRI_OK = 0,
-    SIGNTRI_ERR_BAD_ARG = 1,          /* n < 0, ld too small, NULL pointer, bad variant */
+    SIGNTRI_ERR_BAD_ARG = 1,          /* n < 0, ld too small, NULL pointer, bad variant,
+                                         output sharing an element with an input */
     SIGNTRI_ERR_ZERO_EIGENVALUE = 2,  /* some t_ii == 0: sign(0) is undefined (Section 1) */
     SIGNTRI_ERR_NONFINITE = 3,        /* some t_ii is NaN or infinite */
     SIGNTRI_ERR_NO_CONVERGENCE = 4,   /* refinement did not reach the tolerance */
@@ -204,8 +208,9 @@ signtri_status signtri_get_info(signtri_info *out);
    in fp32 over K-chunks of at most 1024 (exact: every partial sum is an
    integer below 2^24) and summed in double-float (fp32 hi + lo).  Error
    below 2^-44 relative to |A| |B| entrywise (independent of k).  This is the product used for the refinement
-   residuals TU - UT and U^2 - I of the mixed variants.  Synchronous on
-   `stream`; SIGNTRI_ERR_TIMEOUT if a bounded device wait expired. */
+   residuals TU - UT and U^2 - I of the mixed variants.  C must not share an
+   element with A or B (SIGNTRI_ERR_BAD_ARG).  Synchronous on `stream`;
+   SIGNTRI_ERR_TIMEOUT if a bounded device wait expired. */
 signtri_status signtri_gemm_emulated(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
                                      double *C, int ldc, void *stream);
 
@@ -217,15 +222,16 @@ signtri_status signtri_gemm_emulated(int m, int n, int k, const double *A, int l
    Adjacent Givens swaps, *swaps of them (the number of pairs i<j with
    t_ii < 0 < t_jj, the minimum).  T, Tr, Q device pointers, n x n
    column-major; T is only read (its upper triangle), Tr's strictly lower part
-   is written as 0.  Synchronous on `stream` (the swap schedule is built on
-   the host from the diagonal signs).  swaps may be NULL. */
+   is written as 0.  Tr and Q share no element with T or with each other
+   (SIGNTRI_ERR_BAD_ARG).  Synchronous on `stream` (the swap schedule is
+   built on the host from the diagonal signs).  swaps may be NULL. */
 signtri_status signtri_reorder_by_sign(int n, const double *T, int ldt, double *Tr, int ldtr,
                                        double *Q, int ldq, long long *swaps, void *stream);
 
 /* Triangular Sylvester equation A X - X B = C for X (m x p): A (m x m) and
    B (p x p) upper triangular (only their upper triangles are read) with
    a_ii != b_jj for all i, j; C (m x p).  All device pointers, column-major;
-   X must not overlap A, B or C.  Enqueued on `stream`.  m == 0 or p == 0 is a
+   X must not share an element with A, B or C (SIGNTRI_ERR_BAD_ARG).  Enqueued on `stream`.  m == 0 or p == 0 is a
    no-op. */
 signtri_status signtri_sylvester(int m, int p, const double *A, int lda, const double *B, int ldb,
                                  const double *C, int ldc, double *X, int ldx, void *stream);

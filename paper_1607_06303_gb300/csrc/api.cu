@@ -345,7 +345,8 @@ signtri_status sign_tri_batched(int count, const int *n, const double *const *T,
     int nmax = 0;
     for (int m = 0; m < count; m++) {
         info[m] = SIGNTRI_OK;
-        if (n[m] < 0 || (n[m] > 0 && (!T[m] || !U[m] || ldt[m] < n[m] || ldu[m] < n[m]))) {
+        if (n[m] < 0 || (n[m] > 0 && (!T[m] || !U[m] || ldt[m] < n[m] || ldu[m] < n[m] ||
+                                      blocks_overlap(T[m], ldt[m], n[m], n[m], U[m], ldu[m], n[m], n[m])))) {
             info[m] = SIGNTRI_ERR_BAD_ARG;
             continue;
         }
@@ -534,6 +535,9 @@ signtri_status signtri_reorder_by_sign(int n, const double *T, int ldt, double *
     if (n < 0) return SIGNTRI_ERR_BAD_ARG;
     if (n == 0) return SIGNTRI_OK;
     if (!T || !Tr || !Q || ldt < n || ldtr < n || ldq < n) return SIGNTRI_ERR_BAD_ARG;
+    if (blocks_overlap(T, ldt, n, n, Tr, ldtr, n, n) || blocks_overlap(T, ldt, n, n, Q, ldq, n, n) ||
+        blocks_overlap(Tr, ldtr, n, n, Q, ldq, n, n))
+        return SIGNTRI_ERR_BAD_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
     DeviceState *s = nullptr;
     signtri_status rs = current_state(&s);
@@ -557,6 +561,8 @@ signtri_status signtri_gemm_emulated(int m, int n, int k, const double *A, int l
     if (m < 0 || n < 0 || k < 0) return SIGNTRI_ERR_BAD_ARG;
     if (m == 0 || n == 0) return SIGNTRI_OK;
     if (!A || !B || !C || lda < m || ldb < std::max(k, 1) || ldc < m) return SIGNTRI_ERR_BAD_ARG;
+    if (blocks_overlap(A, lda, m, k, C, ldc, m, n) || blocks_overlap(B, ldb, k, n, C, ldc, m, n))
+        return SIGNTRI_ERR_BAD_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
     DeviceState *s = nullptr;
     signtri_status rs = current_state(&s);
@@ -579,6 +585,9 @@ signtri_status signtri_sylvester(int m, int p, const double *A, int lda, const d
     if (m < 0 || p < 0) return SIGNTRI_ERR_BAD_ARG;
     if (m == 0 || p == 0) return SIGNTRI_OK;
     if (!A || !B || !C || !X || lda < m || ldb < p || ldc < m || ldx < m) return SIGNTRI_ERR_BAD_ARG;
+    if (blocks_overlap(A, lda, m, m, X, ldx, m, p) || blocks_overlap(B, ldb, p, p, X, ldx, m, p) ||
+        blocks_overlap(C, ldc, m, p, X, ldx, m, p))
+        return SIGNTRI_ERR_BAD_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
     DeviceState *s = nullptr;
     signtri_status rs = current_state(&s);
@@ -617,6 +626,7 @@ signtri_status sign_tri(int n, const double *T, int ldt, double *U, int ldu, sig
     if (n < 0 || !valid_variant(v)) return SIGNTRI_ERR_BAD_ARG;
     if (n == 0) return SIGNTRI_OK;
     if (!T || !U || ldt < n || ldu < n) return SIGNTRI_ERR_BAD_ARG;
+    if (blocks_overlap(T, ldt, n, n, U, ldu, n, n)) return SIGNTRI_ERR_BAD_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
     DeviceState *s = nullptr;
     signtri_status rs = current_state(&s);

@@ -21,6 +21,37 @@ namespace signtri {
 
 #define SGT_LAUNCH_CHECK() SGT_CUDA_TRY(cudaGetLastError())
 
+// True when the column-major blocks A (rowsA x colsA, leading dimension lda)
+// and B (rowsB x colsB, ldb) share an element; rowsA <= lda.  Exact for
+// blocks interleaved within one array: each column of B is a contiguous run
+// compared with the runs of A that its span reaches.  Pointers whose distance
+// is not a whole number of doubles count as overlapping once their byte
+// extents meet.  Host only, O(colsB) when the extents meet, O(1) otherwise.
+inline bool blocks_overlap(const double *A, int lda, int rowsA, int colsA, const double *B, int ldb, int rowsB,
+                           int colsB)
+{
+    if (rowsA <= 0 || colsA <= 0 || rowsB <= 0 || colsB <= 0) return false;
+    const long long pa = (long long)(uintptr_t)A, pb = (long long)(uintptr_t)B;
+    const long long lenA = ((long long)(colsA - 1) * lda + rowsA) * 8;
+    const long long lenB = ((long long)(colsB - 1) * ldb + rowsB) * 8;
+    if (pb >= pa + lenA || pa >= pb + lenB) return false;
+    if ((pb - pa) % 8 != 0) return true;
+    const long long d = (pb - pa) / 8;               // B's first element, in doubles from A's
+    for (int cb = 0; cb < colsB; cb++) {
+        const long long s = d + (long long)cb * ldb;  // column cb of B: elements [s, e] from A's start
+        const long long e = s + rowsB - 1;
+        if (e < 0) continue;
+        const long long lo = s < 0 ? 0 : s / lda;     // first column of A that can reach [s, e]
+        long long hi = e / lda;                       // last column of A starting at or before e
+        if (hi > colsA - 1) hi = colsA - 1;
+        if (lo > hi) continue;
+        if (hi > lo) return true;                     // column lo+1 of A starts inside [s, e]
+        const long long a0 = lo * lda;                // column lo of A: [a0, a0 + rowsA - 1]
+        if (a0 <= e && a0 + rowsA - 1 >= s) return true;
+    }
+    return false;
+}
+
 // Result of the inertia scan (written by the device, read by the host).
 struct ScanResult {
     int n_pos;

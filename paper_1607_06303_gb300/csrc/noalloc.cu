@@ -39,6 +39,7 @@ extern "C" signtri_status sign_tri_noalloc(int n, const double *T, int ldt, doub
     if (n < 0) return SIGNTRI_ERR_BAD_ARG;
     if (n == 0) return SIGNTRI_OK;
     if (!T || !U || ldt < n || ldu < n) return SIGNTRI_ERR_BAD_ARG;
+    if (blocks_overlap(T, ldt, n, n, U, ldu, n, n)) return SIGNTRI_ERR_BAD_ARG;
     if (n > kNoallocMaxN) return SIGNTRI_ERR_NO_WORKSPACE;
     int dev = 0;
     SGT_CUDA_TRY(cudaGetDevice(&dev));

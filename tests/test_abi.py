@@ -201,3 +201,59 @@ def test_sign_operand_checks():
     with pytest.raises(ValueError):
         from paper_1607_06303_gb300 import sign
         sign(torch.zeros(4, 4, dtype=torch.float64))           # a CPU tensor never reaches the library
+
+
+def _elements(base, ld, rows, cols):
+    """Byte offsets of the doubles of a column-major block."""
+    return {base + 8 * (i + j * ld) for j in range(cols) for i in range(rows)}
+
+
+def _bytes(base, ld, rows, cols):
+    return {b + q for b in _elements(base, ld, rows, cols) for q in range(8)}
+
+
+def _cuda_visible():
+    import torch
+    return torch.cuda.is_available()
+
+
+@pytest.mark.skipif(_cuda_visible(), reason="accepted calls would launch kernels on made-up pointers")
+def test_overlapping_operands_rejected(lib):
+    """Output blocks that share an element with an input block are rejected
+    with SIGNTRI_ERR_BAD_ARG before any CUDA call; disjoint blocks (also when
+    interleaved in one array through their leading dimensions) pass the check
+    and, with no GPU here, stop at the first CUDA call.  Checked against a
+    brute-force intersection of the blocks' elements."""
+    import random
+    BAD, CUDA = lib.Status.ERR_BAD_ARG, lib.Status.ERR_CUDA
+    rng = random.Random(7)
+    base = 1 << 32
+    cases = 0
+    for _ in range(400):
+        n = rng.randint(1, 9)
+        ldt, ldu = n + rng.choice([0, 0, 1, 3, n]), n + rng.choice([0, 0, 2, n])
+        off = 8 * rng.randint(-3 * n * ldu, 3 * n * ldt) + (rng.choice([1, 4]) if rng.random() < 0.1 else 0)
+        pT, pU = base, base + off
+        expect = BAD if _bytes(pT, ldt, n, n) & _bytes(pU, ldu, n, n) else CUDA
+        assert lib.sign_tri(n, pT, ldt, pU, ldu, 1, 0) == expect, (n, ldt, ldu, off)
+        assert lib.sign_tri_noalloc(n, pT, ldt, pU, ldu, 0) == expect, (n, ldt, ldu, off)
+        cases += expect == BAD
+    assert 50 < cases < 350          # both outcomes exercised
+    # rectangular blocks: X (m x p) of the Sylvester solve against C (m x p)
+    # in one array, interleaved by the leading dimension
+    for _ in range(300):
+        m, p_ = rng.randint(1, 6), rng.randint(1, 6)
+        ldc, ldx = m + rng.choice([0, 1, m]), m + rng.choice([0, 2, m])
+        off = 8 * rng.randint(-2 * p_ * ldx, 2 * p_ * ldc)
+        pA, pB, pC, pX = base + (1 << 24), base + (1 << 25), base, base + off
+        expect = BAD if _elements(pC, ldc, m, p_) & _elements(pX, ldx, m, p_) else CUDA
+        assert lib.signtri_sylvester(m, p_, pA, m, pB, p_, pC, ldc, pX, ldx, 0) == expect, (m, p_, ldc, ldx, off)
+        # the same pair as C = A B with A (m x k) in C's place
+        assert lib.signtri_gemm_emulated(m, p_, p_, pC, ldc, pB, p_, pX, ldx, 0) == \
+            (BAD if _elements(pC, ldc, m, p_) & _elements(pX, ldx, m, p_) else CUDA)
+    # the Parlett-Sylvester reorder: Tr and Q each against T and each other
+    n = 5
+    assert lib.signtri_reorder_by_sign(n, base, n, base + 8 * n * n, n, base + 16 * n * n, n)[0] == CUDA
+    assert lib.signtri_reorder_by_sign(n, base, n, base + 8 * n * n, n, base + 8 * (n * n + 3), n)[0] == BAD
+    assert lib.signtri_reorder_by_sign(n, base, 2 * n, base + 8 * n, 2 * n, base + 16 * n * n, n)[0] == CUDA
+    assert lib.signtri_reorder_by_sign(n, base, 2 * n, base + 8 * (n - 1), 2 * n, base + 16 * n * n, n)[0] == BAD

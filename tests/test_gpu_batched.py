@@ -93,3 +93,27 @@ def test_batched_mixed_variant(gpu_lib, oracle_mod):
     assert st == 0 and info == [0, 0, 0]
     for T, U in zip(Ts, Us):
         assert relerr(U, oracle_mod.sign_tri(T)) <= 1e-12
+
+
+def test_batched_overlapping_operands(gpu_lib, oracle_mod):
+    """A matrix whose U shares elements with its T is rejected with
+    SIGNTRI_ERR_BAD_ARG and left alone; the others are solved.  T and the
+    overlapping U sit in one buffer large enough for both, so every access
+    stays inside it whatever the check decides."""
+    import torch
+    T0, T1 = make_T(60, 0.5, seed=5), make_T(50, 0.5, seed=6)
+    n1 = 50
+    dT0 = gpu_lib.to_device(T0)
+    dU0 = torch.full_like(dT0, np.nan)
+    buf = torch.zeros(2 * n1 * n1, dtype=torch.float64, device="cuda")
+    buf[:n1 * n1] = gpu_lib.to_device(T1).reshape(-1)
+    pT1 = buf.data_ptr()
+    pU1 = pT1 + 8 * n1 * 10                     # U starts at column 10 of T
+    st, info = gpu_lib.sign_tri_batched([60, n1], [dT0.data_ptr(), pT1], [60, n1], [dU0.data_ptr(), pU1],
+                                        [60, n1], gpu_lib.Variant.PH_FP64, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert st == 0
+    assert info == [0, gpu_lib.Status.ERR_BAD_ARG]
+    assert relerr(gpu_lib.to_numpy(dU0), oracle_mod.sign_tri(T0)) <= TOL_FP64
+    np.testing.assert_array_equal(gpu_lib.to_numpy(buf[:n1 * n1].reshape(n1, n1)), T1)
+    assert bool(torch.all(buf[n1 * n1:] == 0))
