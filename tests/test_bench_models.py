@@ -85,3 +85,37 @@ def test_reference_arm_runs_on_rank_zero_only():
     """Under torchrun only rank 0 times the oracle; the other ranks exit
     without work."""
     assert bench.run_reference(bench.parse_args(["--impl", "reference"]), 1) is None
+
+
+def _cited_bench_commands():
+    """The bench.py argument lists cited by the summaries under profiles/
+    (continuation lines joined; commands with placeholders skipped)."""
+    import glob
+    import shlex
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = []
+    for path in sorted(glob.glob(os.path.join(root, "profiles", "*.txt"))):
+        text = open(path).read().replace("\\\n", " ")
+        for line in text.splitlines():
+            if "python bench.py" not in line or "[" in line:
+                continue
+            rest = line.split("python bench.py", 1)[1]
+            toks = []
+            for t in shlex.split(rest.replace(">", " > ").replace("&&", " && ").replace("|", " | ")):
+                if t in (">", "&&", "|", ")") or t.endswith(")"):
+                    break
+                toks.append(t)
+            out.append((os.path.basename(path), toks))
+    return out
+
+
+def test_profile_commands_parse():
+    """Every bench command a profile summary cites still parses (no flag it
+    uses was renamed or dropped)."""
+    cmds = _cited_bench_commands()
+    assert len(cmds) >= 10
+    for name, toks in cmds:
+        try:
+            bench.parse_args(toks)
+        except SystemExit:
+            pytest.fail("%s cites an invalid bench command: %s" % (name, " ".join(toks)))
