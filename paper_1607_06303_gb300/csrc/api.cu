@@ -33,6 +33,7 @@ struct DeviceState {
     double *stage_T = nullptr;     // device staging for sign_tri_host
     double *stage_U = nullptr;
     size_t stage_elems = 0;
+    bool ready = false;            // every per-device buffer above the workspace allocated
 };
 
 std::mutex g_mu;
@@ -61,13 +62,32 @@ signtri_status current_state(DeviceState **out)
     SGT_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return SIGNTRI_ERR_CUDA;
     DeviceState &s = g_dev[dev];
-    if (!s.scan_dev) {
-        SGT_CUDA_TRY(cudaMalloc(&s.scan_dev, sizeof(ScanResult)));
-        SGT_CUDA_TRY(cudaMallocHost(&s.scan_host, sizeof(ScanResult)));
-        SGT_CUDA_TRY(cudaMalloc(&s.err_dev, sizeof(int)));
+    if (!s.ready) {
+        // a piece is stored only once allocated, so a call after a failed
+        // attempt allocates what is still missing instead of using a NULL
+        void *p = nullptr;
+        if (!s.scan_dev) {
+            SGT_CUDA_TRY(cudaMalloc(&p, sizeof(ScanResult)));
+            s.scan_dev = static_cast<ScanResult *>(p);
+        }
+        if (!s.scan_host) {
+            SGT_CUDA_TRY(cudaMallocHost(&p, sizeof(ScanResult)));
+            s.scan_host = static_cast<ScanResult *>(p);
+        }
+        if (!s.err_dev) {
+            SGT_CUDA_TRY(cudaMalloc(&p, sizeof(int)));
+            s.err_dev = static_cast<int *>(p);
+        }
+        if (!s.err_host) {
+            SGT_CUDA_TRY(cudaMallocHost(&p, sizeof(int)));
+            s.err_host = static_cast<int *>(p);
+        }
+        if (!s.norms_host) {
+            SGT_CUDA_TRY(cudaMallocHost(&p, 8 * sizeof(double)));
+            s.norms_host = static_cast<double *>(p);
+        }
         SGT_CUDA_TRY(cudaMemset(s.err_dev, 0, sizeof(int)));
-        SGT_CUDA_TRY(cudaMallocHost(&s.err_host, sizeof(int)));
-        SGT_CUDA_TRY(cudaMallocHost(&s.norms_host, 8 * sizeof(double)));
+        s.ready = true;
     }
     *out = &s;
     return SIGNTRI_OK;
@@ -663,7 +683,11 @@ signtri_status sign_tri_host(int n, const double *T_host, int ldt, double *U_hos
     SGT_CUDA_TRY(cudaMemcpy2DAsync(s->stage_T, (size_t)n * sizeof(double), T_host, (size_t)ldt * sizeof(double),
                                    (size_t)n * sizeof(double), n, cudaMemcpyHostToDevice, st));
     rs = sign_tri_locked(n, s->stage_T, n, s->stage_U, n, v, st, *s);
-    if (rs != SIGNTRI_OK) return rs;
+    if (rs != SIGNTRI_OK) {
+        // no copy from the caller's T_host may still be in flight on return
+        cudaStreamSynchronize(st);
+        return rs;
+    }
     SGT_CUDA_TRY(cudaMemcpy2DAsync(U_host, (size_t)ldu * sizeof(double), s->stage_U, (size_t)n * sizeof(double),
                                    (size_t)n * sizeof(double), n, cudaMemcpyDeviceToHost, st));
     SGT_CUDA_TRY(cudaStreamSynchronize(st));
