@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
+#include "tc_job.h"
 
 namespace signtri {
 
@@ -13,19 +14,6 @@ constexpr int kTcMaxPairs = 36;
 // the fp32 accumulator
 constexpr int kExactChunkKb8 = 4;
 constexpr int kExactChunkKb7 = 16;
-
-// One CTA's work: rows [rt, rt+64) of the top source and [rb, rb+64) of the
-// bottom source form A; rows [cl, cl+64) of the left and [cr, cr+64) of the
-// right source form B; K = 64-blocks [kb0, kb1).  The four 64 x 64 quadrants
-// of A B^T go to out + slot * 16384 float2 (hi, lo) pairs, quadrant q
-// (0 top-left, 1 top-right, 2 bottom-left, 3 bottom-right) at + q * 4096,
-// column-major; the value is hi + lo.
-struct TcJob {
-    int rt, rb, cl, cr;
-    int kb0, kb1;
-    int slot;
-    int pad;
-};
 
 // Slice pairs (s, t) and their weights (the kernel reads a device copy).
 struct TcPairs {
