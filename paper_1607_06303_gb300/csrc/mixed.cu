@@ -61,6 +61,7 @@
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
+#include "gathered_layout.h"
 #include "sweep_schedule.h"
 #include "tc_gemm.cuh"
 
@@ -908,97 +909,22 @@ signtri_status setup_gathered(MixedCtx &c, const double *T, int ldt)
     std::vector<unsigned char> pos(n);
     SGT_CUDA_TRY(cudaMemcpyAsync(pos.data(), c.pos, n, cudaMemcpyDeviceToHost, c.st));
     SGT_CUDA_TRY(cudaStreamSynchronize(c.st));
-    const int nsb = (n + kSuper - 1) / kSuper;
-    std::vector<int> gmap(n), base(nsb + 1, 0), cnt_pos(nsb, 0), cls_len[2];
-    cls_len[0].assign(nsb, 0);
-    cls_len[1].assign(nsb, 0);
-    int g = 0;
-    for (int sb = 0; sb < nsb; sb++) {
-        const int i0 = sb * kSuper, i1 = std::min(n, i0 + kSuper);
-        int np_ = 0;
-        for (int i = i0; i < i1; i++) np_ += pos[i];
-        const int A = pad64(np_), Bn = pad64(i1 - i0 - np_);
-        base[sb] = g;
-        cls_len[0][sb] = A;
-        cls_len[1][sb] = Bn;
-        int rp = 0, rn = 0;
-        for (int i = i0; i < i1; i++) gmap[i] = pos[i] ? g + rp++ : g + A + rn++;
-        g += A + Bn;
-    }
-    base[nsb] = g;
-    c.ng = g;
-    c.rows_g = g + 64;
+    GatheredLayout L;
+    build_gathered_layout(n, pos.data(), kSuper, L);
+    c.ng = L.ng;
+    c.rows_g = L.rows_g;
     if (c.rows_g > gathered_bound(n) + 64) return SIGNTRI_ERR_NO_WORKSPACE;
-    std::vector<int> ginv(c.rows_g, -1);
-    for (int i = 0; i < n; i++) ginv[gmap[i]] = i;
-    // block pairs per (superblock, class): row offsets, lone block with the zero block
-    auto pairs_of = [&](int sb, int cls) {
-        std::vector<std::pair<int, int>> v;
-        const int start = base[sb] + (cls ? cls_len[0][sb] : 0), len = cls_len[cls][sb];
-        for (int o = 0; o < len; o += 128) v.push_back({start + o, o + 64 < len ? start + o + 64 : c.ng});
-        return v;
-    };
-    // original indices of each superblock's positives and negatives, ascending
-    std::vector<std::vector<int>> porig(nsb), norig(nsb);
-    for (int i = 0; i < n; i++) (pos[i] ? porig : norig)[i / kSuper].push_back(i);
-    // K range of a job: the products vanish unless row < k < column, so in the
-    // rows' superblock the K-blocks before the first positive above the rows'
-    // smallest index are skipped (positives come first there) and in the
-    // columns' superblock those after the last negative below the columns'
-    // largest index (negatives come last); what lies between stays (zeros)
-    auto k_start = [&](int sr, int cr, int first) {
-        if (cr == 0) return first / 64;
-        const int rmin = ginv[first];
-        const int cp = (int)(std::upper_bound(porig[sr].begin(), porig[sr].end(), rmin) - porig[sr].begin());
-        return (base[sr] + cp) / 64;
-    };
-    auto k_end = [&](int sc, int cc, const std::pair<int, int> &cpair) {
-        int last = -1;   // gathered position of the pair's last real column
-        for (int gpos : {cpair.second, cpair.first})
-            if (gpos < c.ng && last < 0)
-                for (int q = gpos + 63; q >= gpos; q--)
-                    if (ginv[q] >= 0) { last = q; break; }
-        const int cmax = ginv[last];
-        const int cn = (int)(std::lower_bound(norig[sc].begin(), norig[sc].end(), cmax) - norig[sc].begin());
-        const int end = base[sc] + cls_len[0][sc] + cn;
-        return (end + 63) / 64;
-    };
-    std::vector<TcJob> same, opp;
-    double kb_same = 0.0, kb_opp = 0.0;
-    // longest superblock spans first (load balance); one superblock pair's
-    // jobs together (they share operand panels in L2)
-    for (int span = nsb - 1; span >= 0; span--)
-        for (int sr = 0; sr + span < nsb; sr++) {
-            const int sc = sr + span;
-            for (int cr = 0; cr < 2; cr++)
-                for (int cc = 0; cc < 2; cc++) {
-                    const auto rows = pairs_of(sr, cr), cols = pairs_of(sc, cc);
-                    for (const auto &rp : rows)
-                        for (const auto &cp : cols) {
-                            TcJob j;
-                            j.rt = rp.first; j.rb = rp.second; j.cl = cp.first; j.cr = cp.second;
-                            j.kb0 = k_start(sr, cr, rp.first);
-                            j.kb1 = std::max(j.kb0, k_end(sc, cc, cp));
-                            j.slot = 0; j.pad = 0;
-                            const double used = (double)((rp.second < c.ng) + 1) * ((cp.second < c.ng) + 1);
-                            if (cr == cc) { same.push_back(j); kb_same += used * (j.kb1 - j.kb0); }
-                            else { opp.push_back(j); kb_opp += used * (j.kb1 - j.kb0); }
-                        }
-                }
-        }
-
-    c.n_res_same = (int)same.size();
-    c.n_res_opp = (int)opp.size();
-    c.res_kb_same = kb_same;
-    c.res_kb_opp = kb_opp;
-    same.insert(same.end(), opp.begin(), opp.end());
-    if (!same.empty())
-        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_res_jobs, same.data(), same.size() * sizeof(TcJob), cudaMemcpyHostToDevice,
-                                     c.st));
-    SGT_CUDA_TRY(cudaMemcpyAsync(c.gmap, gmap.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, c.st));
-    SGT_CUDA_TRY(cudaMemcpyAsync(c.sbbase, base.data(), (size_t)(nsb + 1) * sizeof(int), cudaMemcpyHostToDevice,
+    c.n_res_same = L.n_same;
+    c.n_res_opp = L.n_opp;
+    c.res_kb_same = L.kb_same;
+    c.res_kb_opp = L.kb_opp;
+    if (!L.jobs.empty())
+        SGT_CUDA_TRY(cudaMemcpyAsync(c.d_res_jobs, L.jobs.data(), L.jobs.size() * sizeof(TcJob),
+                                     cudaMemcpyHostToDevice, c.st));
+    SGT_CUDA_TRY(cudaMemcpyAsync(c.gmap, L.gmap.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, c.st));
+    SGT_CUDA_TRY(cudaMemcpyAsync(c.sbbase, L.base.data(), L.base.size() * sizeof(int), cudaMemcpyHostToDevice,
                                  c.st));
-    SGT_CUDA_TRY(cudaMemcpyAsync(c.ginv, ginv.data(), (size_t)c.rows_g * sizeof(int), cudaMemcpyHostToDevice, c.st));
+    SGT_CUDA_TRY(cudaMemcpyAsync(c.ginv, L.ginv.data(), (size_t)c.rows_g * sizeof(int), cudaMemcpyHostToDevice, c.st));
     // the host tables are pageable and local
     SGT_CUDA_TRY(cudaStreamSynchronize(c.st));
     return SIGNTRI_OK;
