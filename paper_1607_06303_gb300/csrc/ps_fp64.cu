@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "reorder_schedule.h"
 
 namespace signtri {
 
@@ -129,35 +130,6 @@ __global__ void copy_upper_identity_kernel(int n, const double *__restrict__ src
         SGT_AT(dst, ldd, i, j) = (i <= j) ? SGT_AT(src, lds, i, j) : 0.0;
         SGT_AT(Q, ldq, i, j) = (i == j) ? 1.0 : 0.0;
     }
-}
-
-// Odd-even transposition rounds of the stable partition, from the signs:
-// flat list of the upper index k of each swapped pair, and round offsets.
-void schedule_rounds(const std::vector<double> &diag, std::vector<int> &pairs, std::vector<int> &offsets)
-{
-    const int n = (int)diag.size();
-    std::vector<signed char> s(n);
-    for (int i = 0; i < n; i++) s[i] = diag[i] > 0.0 ? 1 : -1;
-    pairs.clear();
-    offsets.assign(1, 0);
-    int lo = 0, hi = n - 1;                       // unsorted window
-    int idle = 0;
-    for (int r = 0; idle < 2; r++) {
-        while (lo < n && s[lo] > 0) lo++;         // leading positives are final
-        while (hi >= 0 && s[hi] < 0) hi--;        // trailing negatives are final
-        bool any = false;
-        const int start = std::max(0, lo - 1);
-        for (int k = start + ((start & 1) != (r & 1) ? 1 : 0); k + 1 <= hi; k += 2) {
-            if (s[k] < 0 && s[k + 1] > 0) {
-                std::swap(s[k], s[k + 1]);
-                pairs.push_back(k);
-                any = true;
-            }
-        }
-        offsets.push_back((int)pairs.size());
-        idle = any ? 0 : idle + 1;
-    }
-    while (offsets.size() > 1 && offsets[offsets.size() - 1] == offsets[offsets.size() - 2]) offsets.pop_back();
 }
 
 // ------------------------------------------------------------- Sylvester ---

@@ -1,4 +1,4 @@
-"""Host logic of the mixed variants, compiled here with the host compiler and
+"""Host logic of the GPU variants, compiled here with the host compiler and
 checked without a GPU:
   - the tensor-core sweeps' work lists (csrc/sweep_schedule.h: which CTA sums
     which K-blocks of which tile into which partial slot, and which slots each
@@ -7,7 +7,11 @@ checked without a GPU:
   - the needed residual's gathered layout and job lists
     (csrc/gathered_layout.h: index order, block coverage, K trimming that
     drops no term, workspace bounds), for seeded sign patterns of many sizes,
-    by tests/gathered_layout_check.cpp."""
+    by tests/gathered_layout_check.cpp;
+  - the Parlett-Sylvester reorder's rounds of Givens swaps
+    (csrc/reorder_schedule.h: a stable partition by sign in the minimum
+    number of swaps, disjoint pairs of the round's parity), by
+    tests/reorder_schedule_check.cpp."""
 import os
 import shutil
 import subprocess
@@ -45,3 +49,8 @@ def test_sweep_work_lists(tmp_path):
 @pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
 def test_gathered_layout_and_residual_jobs(tmp_path):
     _compile_and_run(tmp_path, "gathered_layout_check.cpp")
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
+def test_reorder_rounds(tmp_path):
+    _compile_and_run(tmp_path, "reorder_schedule_check.cpp")
