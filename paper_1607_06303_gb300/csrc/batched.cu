@@ -15,6 +15,7 @@
 
 #include "internal.cuh"
 #include "ph_bodies.cuh"
+#include "batched_plan.h"
 
 namespace signtri {
 
@@ -22,15 +23,8 @@ using namespace ph;
 
 namespace {
 
-struct GemmTask {
-    int m, I, J, kb0, kb1, slot;
-};
-struct LeafTask {
-    int m, I, J, nsplit, slot0, pad;
-};
-struct DiagTask {
-    int m, blk;
-};
+static_assert(kBatchSplitMax == kSplitMax && kBatchTargetCtas == kTargetCtas,
+              "the batched plan and the float64 kernels share their split limits");
 
 template <int B>
 __global__ void __launch_bounds__(kThreads)
@@ -87,74 +81,6 @@ batched_leaf_kernel(const BatchDesc *__restrict__ mats, const int *__restrict__ 
     const BatchDesc M = mats[members[t.m]];
     offdiag_leaf_body<B>(M.n, M.T, M.ldt, M.U, M.ldu, t.I, t.J, t.nsplit, PX + (size_t)t.slot0 * B * B,
                          PY + (size_t)t.slot0 * B * B, (size_t)B * B);
-}
-
-struct Plan {
-    std::vector<DiagTask> diag;
-    std::vector<GemmTask> gemm;
-    std::vector<LeafTask> leaf;
-    std::vector<int> gemm_off, leaf_off;   // per level d (size nbmax + 1)
-    std::vector<int> poff, noff;           // per member: sign permutation and count offsets
-    int nbmax = 0;
-    size_t max_slots = 0;
-    size_t perm_len = 0, npos_len = 0;
-};
-
-// members: indices (into the batch) of the matrices of this group
-void make_plan(const std::vector<int> &ns, int B, Plan &p)
-{
-    const int cnt = (int)ns.size();
-    std::vector<int> nb(cnt);
-    p.nbmax = 0;
-    p.poff.assign(cnt, 0);
-    p.noff.assign(cnt, 0);
-    for (int k = 0; k < cnt; k++) {
-        nb[k] = (ns[k] + B - 1) / B;
-        p.nbmax = std::max(p.nbmax, nb[k]);
-        for (int b = 0; b < nb[k]; b++) p.diag.push_back({k, b});
-        p.poff[k] = (int)p.perm_len;
-        p.noff[k] = (int)p.npos_len;
-        p.perm_len += (size_t)nb[k] * B;
-        p.npos_len += (size_t)nb[k];
-    }
-    p.gemm_off.assign(p.nbmax + 1, 0);
-    p.leaf_off.assign(p.nbmax + 1, 0);
-    for (int d = 0; d <= p.nbmax; d++) {
-        p.gemm_off[d] = (int)p.gemm.size();
-        p.leaf_off[d] = (int)p.leaf.size();
-        if (d < 1 || d >= p.nbmax) continue;
-        long long tiles = 0;
-        for (int k = 0; k < cnt; k++) tiles += std::max(0, nb[k] - d);
-        const int kmax = d - 1;
-        int ns = 0, kc = 1;
-        if (kmax > 0 && tiles > 0) {
-            ns = (int)std::max(1LL, std::min<long long>(kmax, (kTargetCtas + tiles - 1) / tiles));
-            ns = std::min(ns, kSplitMax);
-            kc = (kmax + ns - 1) / ns;
-            ns = (kmax + kc - 1) / kc;
-        }
-        int slot = 0;
-        for (int k = 0; k < cnt; k++)
-            for (int I = 0; I + d < nb[k]; I++) {
-                const int J = I + d;
-                p.leaf.push_back({k, I, J, ns, slot, 0});
-                for (int s = 0; s < ns; s++) {
-                    const int kb0 = I + 1 + s * kc;
-                    p.gemm.push_back({k, I, J, kb0, std::min(kb0 + kc, J), slot + s});
-                }
-                slot += ns;
-            }
-        p.max_slots = std::max(p.max_slots, (size_t)slot);
-    }
-    p.gemm_off[p.nbmax] = (int)p.gemm.size();
-    p.leaf_off[p.nbmax] = (int)p.leaf.size();
-}
-
-size_t plan_bytes(const Plan &p, int B)
-{
-    return p.diag.size() * sizeof(DiagTask) + p.gemm.size() * sizeof(GemmTask) + p.leaf.size() * sizeof(LeafTask) +
-           2 * std::max<size_t>(p.max_slots, 1) * B * B * sizeof(double) + p.perm_len * sizeof(short) +
-           p.npos_len * sizeof(int) + 2 * p.poff.size() * sizeof(int) + 12 * 256;
 }
 
 template <int B>
@@ -250,7 +176,7 @@ size_t batched_workspace_bytes(int count, const int *n, int B)
     std::vector<int> ns(n, n + count);
     Plan p;
     make_plan(ns, B, p);
-    return plan_bytes(p, B) + (size_t)count * sizeof(int) + 4096;
+    return std::max(plan_bytes(p, B), plan_bytes_bound(ns, B)) + (size_t)count * sizeof(int) + 4096;
 }
 
 // bs[m]: leaf size of matrix m (16, 32 or 64); matrices with bs[m] == 0 are

@@ -11,7 +11,11 @@ checked without a GPU:
   - the Parlett-Sylvester reorder's rounds of Givens swaps
     (csrc/reorder_schedule.h: a stable partition by sign in the minimum
     number of swaps, disjoint pairs of the round's parity), by
-    tests/reorder_schedule_check.cpp."""
+    tests/reorder_schedule_check.cpp;
+  - the batched path's per-level task tables (csrc/batched_plan.h: every
+    tile's block sums once, slots disjoint) and its workspace bound, which
+    must hold for every subset of a batch's matrices, by
+    tests/batched_plan_check.cpp."""
 import os
 import shutil
 import subprocess
@@ -54,3 +58,8 @@ def test_gathered_layout_and_residual_jobs(tmp_path):
 @pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
 def test_reorder_rounds(tmp_path):
     _compile_and_run(tmp_path, "reorder_schedule_check.cpp")
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
+def test_batched_plan_and_workspace_bound(tmp_path):
+    _compile_and_run(tmp_path, "batched_plan_check.cpp")
