@@ -1148,10 +1148,23 @@ signtri_status side_stream(MixedCtx &c)
     SGT_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return SIGNTRI_OK;
     SideStream &g = g_side[dev];
+    // a piece is stored only once created, so a call after a failed attempt
+    // creates what is still missing; the side stream is used only with both
+    // of its events
     if (!g.s) {
-        SGT_CUDA_TRY(cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking));
-        SGT_CUDA_TRY(cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming));
-        SGT_CUDA_TRY(cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming));
+        cudaStream_t s = nullptr;
+        SGT_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        g.s = s;
+    }
+    if (!g.fork) {
+        cudaEvent_t e = nullptr;
+        SGT_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        g.fork = e;
+    }
+    if (!g.join) {
+        cudaEvent_t e = nullptr;
+        SGT_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        g.join = e;
     }
     c.side = g.s;
     c.ev_fork = g.fork;
