@@ -42,15 +42,38 @@ def _compile(src, extra):
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep and not extra:
         return obj, None
-    cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj]
+    # written under a private name and renamed when complete, so an
+    # interrupted or concurrent build never leaves a truncated object that
+    # looks up to date
+    tmp = "%s.tmp%d" % (obj, os.getpid())
+    cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(extra) + ["-c", src, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
+        if os.path.exists(tmp):
+            os.remove(tmp)
         return obj, "%s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr)
+    os.replace(tmp, obj)
     return obj, None
+
+
+def _flags_changed():
+    """True (and the stamp updated) when the compiler flags differ from
+    those the objects in _lib were built with."""
+    stamp = os.path.join(OUT, "flags.txt")
+    want = " ".join(ARCH + NVCC_FLAGS)
+    have = open(stamp).read() if os.path.exists(stamp) else None
+    if have == want:
+        return False
+    with open(stamp + ".tmp%d" % os.getpid(), "w") as f:
+        f.write(want)
+    os.replace(stamp + ".tmp%d" % os.getpid(), stamp)
+    return True
 
 
 def build(force: bool = False, extra=()) -> str:
     os.makedirs(OUT, exist_ok=True)
+    if _flags_changed():
+        force = True
     if force:
         for f in os.listdir(OUT):
             if f.endswith(".o"):
