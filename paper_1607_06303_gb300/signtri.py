@@ -173,6 +173,8 @@ def signtri_gemm_emulated(m, n, k, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, stream=No
 def sign_tri_batched(ns, T_ptrs, ldts, U_ptrs, ldus, v, stream=None):
     """Batched call on host lists; returns (status, per-matrix info list)."""
     cnt = len(ns)
+    if not (len(T_ptrs) == len(ldts) == len(U_ptrs) == len(ldus) == cnt):
+        raise ValueError("sign_tri_batched: n, T, ldt, U and ldu must have the same length")
     arr = lambda t, xs: (t * max(cnt, 1))(*xs)
     info = (_I * max(cnt, 1))()
     st = load().sign_tri_batched(cnt, arr(_I, ns), arr(_VP, T_ptrs), arr(_I, ldts), arr(_VP, U_ptrs),

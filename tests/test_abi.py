@@ -257,3 +257,10 @@ def test_overlapping_operands_rejected(lib):
     assert lib.signtri_reorder_by_sign(n, base, n, base + 8 * n * n, n, base + 8 * (n * n + 3), n)[0] == BAD
     assert lib.signtri_reorder_by_sign(n, base, 2 * n, base + 8 * n, 2 * n, base + 16 * n * n, n)[0] == CUDA
     assert lib.signtri_reorder_by_sign(n, base, 2 * n, base + 8 * (n - 1), 2 * n, base + 16 * n * n, n)[0] == BAD
+
+
+def test_batched_binding_rejects_ragged_lists(lib):
+    with pytest.raises(ValueError):
+        lib.sign_tri_batched([4, 4], [0], [4, 4], [0, 0], [4, 4], 1)
+    # an empty batch is a no-op that needs no GPU
+    assert lib.sign_tri_batched([], [], [], [], [], 1) == (lib.Status.OK, [])
