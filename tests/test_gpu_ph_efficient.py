@@ -34,7 +34,7 @@ def run_gpu(p, T, variant, cutoff=None):
         p.signtri_set_cutoff(0)
 
 
-SIZES = [1, 2, 17, 33, 64, 65, 127, 129, 200, 257, 300]
+SIZES = [1, 2, 17, 33, 48, 64, 65, 96, 127, 129, 192, 200, 255, 257, 300]
 
 
 @pytest.mark.parametrize("cutoff", [16, 32, 64])

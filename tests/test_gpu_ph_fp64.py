@@ -35,7 +35,9 @@ def check_structure(U, T):
     assert np.all(np.tril(U, -1) == 0.0)
 
 
-SIZES = [1, 2, 3, 5, 15, 16, 17, 31, 32, 33, 63, 64, 65, 100, 127, 129, 200, 257, 300]
+# every cutoff b in {16, 32, 64} meets n = 2b+1, 3b and 4b-1 (recursion
+# bookkeeping at uneven splits) besides the tile-edge sizes
+SIZES = [1, 2, 3, 5, 15, 16, 17, 31, 32, 33, 48, 63, 64, 65, 96, 100, 127, 129, 192, 200, 255, 257, 300]
 
 
 @pytest.mark.parametrize("cutoff", [16, 32, 64])
