@@ -203,12 +203,17 @@ signtri_status signtri_get_info(signtri_info *out);
 /* ---- Emulated float64 product on the tensor cores --------------------------
    C = A B (A m x k, B k x n, C m x n; device pointers, column-major) with
    float64-level accuracy from bf16 tensor-core products: each row of A and
-   column of B is split exactly into 8 integer slices of 7 bits under a
-   power-of-two scale; the 36 slice products with s + t <= 7 are accumulated
-   in fp32 over K-chunks of at most 1024 (exact: every partial sum is an
-   integer below 2^24) and summed in double-float (fp32 hi + lo).  Error
-   below 2^-44 relative to |A| |B| entrywise (independent of k).  This is the product used for the refinement
-   residuals TU - UT and U^2 - I of the mixed variants.  C must not share an
+   column of B is cut into 8 integer slices of 7 bits under its own
+   power-of-two scale (every entry kept to 2^-56 of that scale); the 36 slice
+   products with s + t <= 7 are accumulated in fp32 over K-chunks of at most
+   1024 (exact: every partial sum is an integer below 2^24) and summed in
+   double-float (fp32 hi + lo).  The error is therefore relative to the
+   scales, not to each entry: when the entries of each row of A and each
+   column of B are of similar magnitude (as in the tests, k up to 4100) it
+   stays below 2^-44 (|A| |B|)_ij; an entry far below its row's or column's
+   largest keeps correspondingly fewer bits.  The mixed variants' refinement
+   residuals TU - UT and U^2 - I use this product on the strictly upper parts
+   (the diagonal terms in float64).  C must not share an
    element with A or B (SIGNTRI_ERR_BAD_ARG).  Synchronous on `stream`;
    SIGNTRI_ERR_TIMEOUT if a bounded device wait expired. */
 signtri_status signtri_gemm_emulated(int m, int n, int k, const double *A, int lda, const double *B, int ldb,

@@ -26,7 +26,9 @@
 //    before the other equation).  The residuals
 //    come from exact 7-bit integer slices of the strictly upper parts of T and
 //    U0 (seven slices, 28 pairs over K-chunks of 1024: emulated float64
-//    products, about 2^-45 relative to |T||U|; 8-bit slices would need 21
+//    products, about 2^-45 relative to |T||U| -- the slices are scaled per
+//    row and column of the strictly upper parts, whose entries are of similar
+//    magnitude, the diagonals being taken apart; 8-bit slices would need 21
 //    pairs but K-chunks of 256, and the fourfold epilogue work costs more than
 //    the pairs save) plus the
 //    diagonal terms in float64:

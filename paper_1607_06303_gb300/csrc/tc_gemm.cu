@@ -15,8 +15,10 @@
 // (fp32 hi + fp32 lo) accumulator in the epilogue registers.  With integer
 // slices of 7 bits and K-chunks of at most 1024 (8 bits, 256), every fp32
 // unit sum is an integer below 2^24 and therefore exact, which makes the
-// emulated product accurate to the split (about 2^-48 relative to |A||B|
-// with 7 slices of 7 bits or 6 of 8).
+// emulated product accurate to the split: each entry is kept to 2^-49 of its
+// row's (column's) power-of-two scale with 7 slices of 7 bits (or 6 of 8), so
+// the product is within about 2^-48 of |A||B| where the entries of each row
+// of A and column of B are of similar magnitude.
 //
 // Warp roles (576 threads): warp 0 issues TMA loads into a 3-stage ring of
 // two K-blocks per stage,
