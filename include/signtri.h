@@ -51,8 +51,12 @@ typedef enum {
        Section 5.1): reorder by sign with adjacent Givens swaps, solve
        T11 X - X T22 = 2 T12, transform back. */
     SIGNTRI_PS_FP64 = 2,
-    /* Parlett-Higham with TF32 tensor-core block updates, then float64
-       refinement of both defining equations.  Some of its tensor-core
+    /* Parlett-Higham with tensor-core block updates of about fp32 accuracy,
+       then float64 refinement of both defining equations.  tcgen05 has no
+       fp32 product and tf32 keeps 10 mantissa bits, so each operand is split
+       into three bf16 terms (hi + mid + lo) and the six products with
+       s + t <= 2 are summed (about 2^-24 relative); the name is the
+       interface's.  Some of its tensor-core
        launches run on side streams the library creates once per device;
        they are forked from and joined back into the caller's stream with
        events, so all of the call's work is ordered on `stream` as usual.
@@ -78,7 +82,8 @@ typedef enum {
                                          output sharing an element with an input */
     SIGNTRI_ERR_ZERO_EIGENVALUE = 2,  /* some t_ii == 0: sign(0) is undefined (Section 1) */
     SIGNTRI_ERR_NONFINITE = 3,        /* some t_ii is NaN or infinite */
-    SIGNTRI_ERR_NO_CONVERGENCE = 4,   /* refinement did not reach the tolerance */
+    SIGNTRI_ERR_NO_CONVERGENCE = 4,   /* reserved: a mixed variant whose refinement
+                                         stalls falls back to SIGNTRI_PH_FP64 instead */
     SIGNTRI_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up */
     SIGNTRI_ERR_CUDA = 6,             /* a CUDA runtime call or launch failed */
     SIGNTRI_ERR_NO_WORKSPACE = 7,     /* workspace could not be allocated / too small */
@@ -150,9 +155,12 @@ signtri_status signtri_set_verification(int full);
 signtri_status signtri_set_cutoff(int b);
 
 /* U = sign(T).  T, U device pointers (see conventions).  Enqueued on
-   `stream`; the host waits once, after the inertia scan, to read three
-   integers (n_pos, n_neg, swaps) and the error flags, then enqueues the
-   chosen variant and returns without waiting for it.
+   `stream`; the host waits after the inertia scan to read three integers
+   (n_pos, n_neg, swaps) and the error flags.  The float64 Parlett-Higham
+   forms then enqueue their launches and return without waiting for them;
+   Parlett-Sylvester also waits while it builds its swap schedule from the
+   diagonal, and the mixed variants wait a few times (diagonal signs,
+   residual norms) and return after U is written.
    n == 0 is a no-op returning SIGNTRI_OK.  n == 1 writes sign(t_11).
    If all t_ii > 0 (all < 0) U = I (U = -I) exactly (Section 3). */
 signtri_status sign_tri(int n, const double *T, int ldt, double *U, int ldu,
