@@ -273,14 +273,16 @@ enum {
 };
 
 /* on != 0: bracket every library kernel launch with CUDA events on its
-   stream from now on (adds two event records per launch).  Launch counts
-   are kept either way. */
+   stream from now on (adds two event records per launch; launches that run
+   side by side on the caller's and a side stream are bracketed together, as
+   one interval on the caller's stream).  Launch counts are kept either way
+   (launches inside a captured graph are counted, not timed). */
 signtri_status signtri_profile_enable(int on);
 /* Zero the launch counters and timers. */
 signtri_status signtri_profile_reset(void);
 /* Launches of class `cls` since the last reset and their summed device time
-   in milliseconds (waits for the recorded events).  Either pointer may be
-   NULL. */
+   in milliseconds (waits for the recorded events; a side-by-side group adds
+   its one interval).  Either pointer may be NULL. */
 signtri_status signtri_profile_read(int cls, long long *launches, double *device_ms);
 /* Algorithmic tensor-core flops issued by launches of class `cls` since the
    last reset: 2*64*64*64 per (slice pair, K-block, used 64x64 quadrant) of
@@ -289,8 +291,13 @@ signtri_status signtri_profile_read_flops(int cls, double *flops);
 /* Algorithmic operand bytes that launches of class `cls` read from device
    memory since the last reset, where the class has a byte model: for the
    tensor-core sweeps of the mixed variants (class block_sums_tc), 8 KB per
-   (bf16 slice, 64-row panel, 64-wide K-block) over the four panels of every
-   job's K range, each read once.  Zero for the other classes. */
+   (bf16 slice, 64-row panel, 64-wide K-block) of the panels each tile
+   K-block needs, each read once: four in the initial sweep (a look-ahead
+   launch adds only its two column panels, its row panels being its partner
+   launch's; a completion launch four panels over four K-blocks per tile),
+   six for the correction's two side-by-side launches, which share the
+   correction's panels (eight when they run one after the other).  Zero for
+   the other classes. */
 signtri_status signtri_profile_read_bytes(int cls, double *bytes);
 /* Name of a kernel class ("" when out of range). */
 const char *signtri_kernel_class_name(int cls);
