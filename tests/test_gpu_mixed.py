@@ -24,9 +24,10 @@ def solve(p, T, variant):
 
 
 @pytest.mark.parametrize("variant", ["PH_MIXED_TF32", "PH_MIXED_BF16"])
-@pytest.mark.parametrize("n,pr,order", [(50, 0.5, "random"), (64, 0.5, "random"), (65, 0.4, "random"),
-                                        (130, 0.5, "random"), (257, 0.3, "random"), (300, 0.5, "sorted"),
-                                        (700, 0.5, "random"), (1000, 0.1, "random")])
+@pytest.mark.parametrize("n,pr,order", [(3, 0.5, "random"), (50, 0.5, "random"), (64, 0.5, "random"),
+                                        (65, 0.4, "random"), (130, 0.5, "random"), (257, 0.3, "random"),
+                                        (300, 0.5, "sorted"), (700, 0.5, "random"), (1000, 0.1, "random"),
+                                        (1025, 0.5, "random")])   # 1025: a superblock of one index
 def test_mixed_vs_oracle(gpu_lib, oracle_mod, variant, n, pr, order):
     T = make_T(n, pr, seed=41, order=order)
     U, info = solve(gpu_lib, T, gpu_lib.Variant[variant])
