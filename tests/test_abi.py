@@ -264,3 +264,23 @@ def test_batched_binding_rejects_ragged_lists(lib):
         lib.sign_tri_batched([4, 4], [0], [4, 4], [0, 0], [4, 4], 1)
     # an empty batch is a no-op that needs no GPU
     assert lib.sign_tri_batched([], [], [], [], [], 1) == (lib.Status.OK, [])
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without libsigntri.so every entry point raises: there is no CPU or
+    eager fallback behind the binding."""
+    code = (
+        "import paper_1607_06303_gb300 as p\n"
+        "from paper_1607_06303_gb300 import signtri as s\n"
+        "s.load.__defaults__ = (%r,)\n"
+        "for call in (lambda: s.load(), lambda: p.sign_tri(4, 16, 4, 4096, 4, 1, 0),\n"
+        "             lambda: p.signtri_status_string(0)):\n"
+        "    try:\n"
+        "        call()\n"
+        "    except RuntimeError as e:\n"
+        "        assert 'not built' in str(e), e\n"
+        "    else:\n"
+        "        raise SystemExit('no error without the library')\n"
+        "print('raised')\n" % str(tmp_path / "missing" / "libsigntri.so"))
+    out = subprocess.run([os.sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT)
+    assert out.returncode == 0 and out.stdout.strip() == "raised", out.stdout + out.stderr
