@@ -1,12 +1,15 @@
 """bench.py's output line, checked without a GPU: the keys and types of the
 JSON line that the benchmark contract fixes (value, e2e, roofline, clocks,
-launch count, ...), for the tensor-core step and for the reference arm.
+launch count, ...), for the tensor-core step, the batched workload and the
+reference arm.
 
-The GPU step runs against stand-ins for the CUDA calls and for the library
-binding that do no computation at all (U is never read: the window parity
-check belongs to the CPU-baseline leg, switched off here); only the line's
-shape is under test.  The reference arm runs the oracle, as it does on the
-GPU machine, on a small window."""
+The GPU steps run against stand-ins for the CUDA calls and for the library
+binding that do no computation at all, so only the line's shape is under
+test: the single-problem step runs without its CPU-baseline leg, and the
+batched workload's leg times the oracle and compares outputs the stand-ins
+never wrote (the parity figure it reports here means nothing).  The
+reference arm runs the oracle, as it does on the GPU machine, on a small
+window."""
 import json
 import os
 import sys
@@ -50,6 +53,10 @@ def no_gpu_step(monkeypatch):
         calls["solves"] += 1
         return 0
 
+    def solve_batch(ns, *args):
+        calls["solves"] += 1
+        return 0, [0] * len(ns)
+
     classes = {sm.KC_BLOCK_SUMS_TC: ("block_sums_tc", 120, 6.0), sm.KC_RESIDUAL: ("residual", 9, 4.0),
                sm.KC_OFFDIAG_LEAF_MIXED: ("offdiag_leaf_mixed", 30, 1.5)}
 
@@ -69,6 +76,9 @@ def no_gpu_step(monkeypatch):
         "signtri_profile_read_flops": lambda c: 3e12,
         "signtri_kernel_class_name": lambda c: classes[c][0] if c in classes else "class%d" % c,
         "signtri_get_info": info,
+        "signtri_autotune": lambda n_max, h=None: 0,
+        "signtri_get_cutoff_table": lambda length=32: [0] * length,
+        "sign_tri_batched": solve_batch,
     }.items():
         monkeypatch.setattr(st, name, fn)
     return calls
@@ -130,3 +140,16 @@ def test_reference_line(capsys, monkeypatch):
 def test_defaults_meet_the_timing_rules():
     a = bench.parse_args([])
     assert a.warmup >= 3 and a.steps >= 1 and a.gpus == 1 and a.n == 16384
+
+
+def test_batched_line(no_gpu_step, capsys, monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "batched", "--batch", "6", "--steps", "3",
+                                      "--warmup", "3"])
+    assert bench.main() == 0
+    line = _last_json(capsys)
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "dtype", "data", "config", "gpu_launches", "clocks", "cpu_baseline"):
+        assert key in line, key
+    assert line["steps"] == 3 and line["warmup"] == 3 and no_gpu_step["solves"] == 6
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] > 0 and line["sample_size"] == 6
