@@ -321,8 +321,9 @@ signtri_status signtri_probe_fp64_peak(double *gflops, void *stream);
 
    Same result as sign_tri with SIGNTRI_PH_FP64 (the same kernels and the
    process-wide cutoff), but the scratch lives in a file-scope device array of
-   32 MiB + 4 KiB inside the library: every GPU that loads the library holds it
-   until the process exits.  Limits and behaviour:
+   16 MiB inside the library (the block-sum slabs of n = 1024 at the largest
+   cutoff, 64, need 15.7 MB): every GPU that loads the library holds it until
+   the process exits.  Limits and behaviour:
      - n <= SIGNTRI_NOALLOC_MAX_N (1024); larger n returns
        SIGNTRI_ERR_NO_WORKSPACE without launching anything.
      - Calls no cudaMalloc, cudaFree or allocating library routine.  (With
@@ -330,7 +331,8 @@ signtri_status signtri_probe_fp64_peak(double *gflops, void *stream);
        profiling off on such paths.)
      - The first call on a device looks up the array's device address with
        cudaGetSymbolAddress (the device must be current); make that first call
-       before any stream capture.
+       before any stream capture.  The address is kept for the life of the
+       process: do not reset the device (cudaDeviceReset) between calls.
      - All calls share the one array, which keeps the last call's contents;
        nothing in it needs to start at zero.  Calls that overlap on the GPU
        (different streams, or different host threads) race on it: serialize

@@ -60,8 +60,9 @@ def _ptr(a):
 
 
 def sign_tri(T, *, threads=None, schedule="paper"):
-    """sign(T) by Algorithm 3.  schedule='paper' runs the printed loop order;
-    'antidiag' runs the anti-diagonal order (OpenMP, bit-identical)."""
+    """sign(T) by the Parlett-Higham substitution (Eqs. 1 and 2 entry by
+    entry).  schedule='paper' visits columns left to right, each bottom to
+    top; 'antidiag' visits by anti-diagonal (OpenMP, bit-identical)."""
     T = _colmajor(T)
     n = T.shape[0]
     U = np.zeros((n, n), dtype=np.float64, order="F")

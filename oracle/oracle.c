@@ -12,9 +12,13 @@
  * oracle is then fixed by the order written here.
  *
  * Functions
- *   oracle_sign_tri        Parlett-Higham substitution, Algorithm 3 of the
- *                          paper (Higham's Algorithm 5.5), loops in the order
- *                          printed there: j = 2..n outer, i = j-1..1 inner.
+ *   oracle_sign_tri        Parlett-Higham substitution (the method of the
+ *                          paper's Section 3; Higham's Algorithm 5.5), derived
+ *                          below from entry (i,j) of TU = UT (Eq. 1) and of
+ *                          U^2 = I (Eq. 2).  Entry (i,j) needs the entries
+ *                          (i,k) and (k,j) with i < k < j, so columns are
+ *                          visited left to right and each column bottom to
+ *                          top: j = 2..n outer, i = j-1..1 inner.
  *   oracle_sign_tri_count  Same, and counts the floating-point operations that
  *                          the inner sums execute (the useful-flop count).
  *   oracle_sign_tri_antidiag
@@ -62,11 +66,19 @@ static int check_args(int n, const double *T, int ldt, const double *U, int ldu)
 }
 
 /*
- * Algorithm 3 (Parlett-Higham).  For i < j:
- *   if u_ii + u_jj = 0 (signs differ), from TU = UT (Eq. 1):
+ * Parlett-Higham substitution.  For i < j, entry (i,j) of TU = UT (Eq. 1),
+ * with U and T upper triangular, reads
+ *       t_ii u_ij + t_ij u_jj + sum_{i<k<j} t_ik u_kj
+ *     = u_ii t_ij + u_ij t_jj + sum_{i<k<j} u_ik t_kj,
+ * and entry (i,j) of U^2 = I (Eq. 2) reads
+ *       u_ii u_ij + u_ij u_jj + sum_{i<k<j} u_ik u_kj = 0.
+ * The second fixes u_ij whenever u_ii + u_jj != 0 (equal signs, |u_ii +
+ * u_jj| = 2); when the signs differ it is empty and the first is used, its
+ * divisor t_ii - t_jj being nonzero then:
+ *   if u_ii + u_jj = 0 (signs differ), from Eq. 1:
  *       u_ij = t_ij (u_ii - u_jj)/(t_ii - t_jj)
  *              + [sum_{k=i+1}^{j-1} (u_ik t_kj - t_ik u_kj)] / (t_ii - t_jj)
- *   else, from U^2 = I (Eq. 2):
+ *   else, from Eq. 2:
  *       u_ij = -[sum_{k=i+1}^{j-1} u_ik u_kj] / (u_ii + u_jj)
  * The strictly lower triangle of U is set to zero.
  * inner_flops, when not NULL, receives the number of floating-point

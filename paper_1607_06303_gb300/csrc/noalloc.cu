@@ -11,17 +11,31 @@
 #include <mutex>
 
 #include "internal.cuh"
+#include "ph_bodies.cuh"
 
 namespace signtri {
 
 namespace {
 
 constexpr int kNoallocMaxN = 1024;
-// Largest need at n <= 1024 over the cutoffs 16, 32, 64 is at cutoff 64:
-// two block-sum slab sets of 32 splits x 16 blocks x 64 x 64 doubles
-// (32 MiB), plus alignment.  The first 256 bytes hold the scan result.
+// The first 256 bytes hold the scan result; the rest is the float64 path's
+// block-sum slabs.  Their size grows with n, so n = 1024 bounds every smaller
+// problem; at n = 1024 the cutoffs need 15.7 MB (b = 64: 240 slabs of 64 x 64
+// doubles per set), 8.4 MB (b = 32: 512 slabs) and 2.8 MB (b = 16: 672), two
+// sets each.  The array is sized from that bound, checked at compile time.
 constexpr size_t kScanSlot = 256;
-constexpr size_t kNoallocBytes = ((size_t)32 << 20) + 4096;
+constexpr size_t noalloc_need()
+{
+    size_t m = 0;
+    for (int b = 16; b <= 64; b *= 2)
+        if (ph::mm_form_workspace_bytes(kNoallocMaxN, b) > m) m = ph::mm_form_workspace_bytes(kNoallocMaxN, b);
+    return m;
+}
+constexpr size_t kNoallocBytes = ((kScanSlot + noalloc_need() + 4095) / 4096) * 4096;
+static_assert(ph::mm_form_workspace_bytes(kNoallocMaxN, 64) <= kNoallocBytes - kScanSlot, "b = 64 at the maximum n");
+static_assert(ph::mm_form_workspace_bytes(kNoallocMaxN, 32) <= kNoallocBytes - kScanSlot, "b = 32 at the maximum n");
+static_assert(ph::mm_form_workspace_bytes(kNoallocMaxN, 16) <= kNoallocBytes - kScanSlot, "b = 16 at the maximum n");
+static_assert(kNoallocBytes <= ((size_t)16 << 20), "the array stays modest");
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
@@ -47,7 +61,10 @@ extern "C" signtri_status sign_tri_noalloc(int n, const double *T, int ldt, doub
     std::lock_guard<std::mutex> lk(na_mu);
     if (!na_base[dev]) {
         // once per device, with that device current: the host-side symbol is
-        // only a stand-in, the kernels need the device address
+        // only a stand-in, the kernels need the device address.  The address
+        // is kept for the life of the process, so the device must not be
+        // reset (cudaDeviceReset) between calls: a reset unloads the module
+        // and a reloaded one may place the array elsewhere
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || p == nullptr) return SIGNTRI_ERR_CUDA;

@@ -23,10 +23,30 @@ constexpr int kTargetCtas = 4 * 152;   // two resident CTAs per SM, two waves
 // the GPU.
 constexpr int kStreamCtas = 4 * 152;
 
-__host__ __device__ __forceinline__ long long sk_chunks_per_tile(int d, int B) { return (long long)(d - 1) * (B / 16); }
-__host__ __device__ __forceinline__ int sk_ctas(long long W) { return (int)(W < kStreamCtas ? W : kStreamCtas); }
+__host__ __device__ constexpr long long sk_chunks_per_tile(int d, int B) { return (long long)(d - 1) * (B / 16); }
+__host__ __device__ constexpr int sk_ctas(long long W) { return (int)(W < kStreamCtas ? W : kStreamCtas); }
 // the CTA whose range holds chunk x (every CTA's range is non-empty)
 __host__ __device__ __forceinline__ long long sk_owner(long long x, long long W, int G) { return ((x + 1) * G - 1) / W; }
+
+// Partial slabs one anti-diagonal needs at most, over all anti-diagonals of
+// an n x n problem with leaf size B (slab c + I for CTA c and tile I).
+constexpr size_t max_slabs(int n, int B)
+{
+    const long long nb = (n + B - 1) / B;
+    long long wmax = 0;
+    for (long long d = 2; d < nb; d++) {
+        const long long w = (nb - d) * sk_chunks_per_tile((int)d, B);
+        if (w > wmax) wmax = w;
+    }
+    return wmax == 0 ? 0 : (size_t)(sk_ctas(wmax) + nb);
+}
+
+// Workspace of the matrix-multiply form: the X and Y slab sets, each
+// 256-byte aligned by the arena.
+constexpr size_t mm_form_workspace_bytes(int n, int B)
+{
+    return max_slabs(n, B) == 0 ? 0 : 2 * (max_slabs(n, B) * B * B * sizeof(double) + 256);
+}
 
 __device__ __forceinline__ double sgn(double t) { return t > 0.0 ? 1.0 : -1.0; }
 

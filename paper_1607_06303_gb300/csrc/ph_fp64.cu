@@ -110,15 +110,6 @@ __global__ void sign_perm_kernel(int n, const double *__restrict__ T, int ldt, s
     sign_perm_body<B>(n, T, ldt, blockIdx.x, perm, npos);
 }
 
-// Partial slabs one anti-diagonal needs at most, over all anti-diagonals.
-size_t max_slabs(int n, int B)
-{
-    const long long nb = (n + B - 1) / B;
-    long long wmax = 0;
-    for (long long d = 2; d < nb; d++) wmax = std::max(wmax, (nb - d) * sk_chunks_per_tile((int)d, B));
-    return wmax == 0 ? 0 : (size_t)(sk_ctas(wmax) + nb);
-}
-
 // One schedule for both forms: per anti-diagonal d, the block sums (if any
 // K-block lies between) then the in-block leaves.  split = true runs the
 // arithmetic-efficient form (one sum per entry, X or Y by the sign pair).
@@ -210,8 +201,7 @@ signtri_status diag_leaves_f64(int n, const double *T, int ldt, double *U, int l
 size_t ph_fp64_workspace_bytes(int n, int b)
 {
     if (n <= 0 || (b != 16 && b != 32 && b != 64)) return 0;
-    const size_t slabs = max_slabs(n, b);
-    return slabs == 0 ? 0 : 2 * (slabs * b * b * sizeof(double) + 256);
+    return mm_form_workspace_bytes(n, b);
 }
 
 size_t ph_fp64_split_workspace_bytes(int n, int b)
