@@ -73,7 +73,6 @@ namespace {
 
 constexpr int MB = 64;
 static_assert(MB == kSweepTile, "the sweep work lists and the kernels share the tile size");
-constexpr int kLeafThreads = 512;
 
 constexpr int kOzakiSlices = 7;   // exact slices of kOzakiBits bits: 49 bits, 28 pairs
 constexpr int kOzakiBits = 7;
@@ -83,36 +82,133 @@ __device__ __forceinline__ float fsgn(double t) { return t > 0.0 ? 1.f : -1.f; }
 
 // --------------------------------------------------------------- leaves ---
 
-// MODE 0: V = U (initial solve).  MODE 1: V = E (correction), with U0, Rc, Rs.
-// Shared memory (fp32, 64 x 68 each): T_II, T_JJ, the same-sign wavefront
-// blocks A_II, A_JJ (U in mode 0, U0 in mode 1), V and the seeds C.
-template <int MODE>
-constexpr int leaf_buffers() { return 6; }
-
+constexpr int kLeafThreads = 256;
 constexpr int kSub = 16;             // sub-block edge of the in-tile solve
-constexpr int kLeafLD = MB + 4;      // leaf smem pitch: columns stay 16-byte aligned for float4 reads
+constexpr int kLeafLD = MB + 4;      // leaf smem pitch: rows / columns stay 16-byte aligned for float4 reads
 constexpr int kNSub = MB / kSub;     // sub-blocks per tile edge
+constexpr int kLeafBufs = 6;         // M+, M-, N+, N-, V by columns, V by rows
 
-// fp32 copies of the diagonal blocks a leaf reads: DT[I] = the upper
-// triangle of T_II, DA[I] = the strictly upper triangle of A_II, each 64 x 64
-// column-major, zero outside the matrix.
-__global__ void diag32_kernel(int n, const double *__restrict__ T, int ldt, const double *__restrict__ A, int lda,
-                              float *__restrict__ DT, float *__restrict__ DA)
+// Per-sign operators of the in-block recurrences.  Entry (p, q) of a tile
+// (I, J) is fixed by
+//   signs differ:  v_pq (t_pp - t_qq) = c_pq + sum_k v_pk T_kq - sum_k T_pk v_kq
+//   signs agree:   v_pq (s_p + s_q)   = c_pq - sum_k v_pk A_kq - sum_k A_pk v_kq
+// (k over the tile's own rows and columns; A = U in the initial solve, U0 in
+// the correction).  So the column part is - sum_k M^{s_q}_pk v_kq, where row
+// r of M^+ is A's row r if s_r = +, else T's, and M^- the other way round,
+// and the row part is + sum_k v_pk N^{s_p}_kq, where column c of N^+ is -A's
+// column c if s_c = +, else +T's, and N^- the other way round.  Per diagonal
+// block I, fp32, 64 x 64, zero on and below the diagonal (the diagonal terms
+// of T sit in the divisor t_pp - t_qq):
+//   OPS[(4 I + 0) 4096 ..]  M^+ row-major      OPS[(4 I + 1) 4096 ..]  M^- row-major
+//   OPS[(4 I + 2) 4096 ..]  N^+ column-major   OPS[(4 I + 3) 4096 ..]  N^- column-major
+// and DIAG[i] = (float) t_ii (0 beyond n).
+__global__ void leaf_ops_kernel(int n, const double *__restrict__ T, int ldt, const double *__restrict__ A, int lda,
+                                float *__restrict__ OPS, float *__restrict__ DIAG)
 {
     const int r0 = blockIdx.x * MB;
-    float *dt = DT + (size_t)blockIdx.x * MB * MB, *da = DA + (size_t)blockIdx.x * MB * MB;
+    __shared__ float sg[MB];
+    for (int i = threadIdx.x; i < MB; i += blockDim.x) {
+        const bool in = r0 + i < n;
+        const double t = in ? SGT_AT(T, ldt, r0 + i, r0 + i) : 0.0;
+        sg[i] = (in && t > 0.0) ? 1.f : -1.f;
+        DIAG[r0 + i] = (float)t;
+    }
+    __syncthreads();
+    float *mp = OPS + (size_t)(4 * blockIdx.x) * MB * MB;
     for (int idx = threadIdx.x; idx < MB * MB; idx += blockDim.x) {
-        const int i = idx % MB, j = idx / MB;
-        const bool in = r0 + j < n;
-        dt[idx] = (in && i <= j) ? (float)SGT_AT(T, ldt, r0 + i, r0 + j) : 0.f;
-        da[idx] = (in && i < j) ? (float)SGT_AT(A, lda, r0 + i, r0 + j) : 0.f;
+        const int i = idx % MB, j = idx / MB;   // element (i, j) of the block, i fastest
+        const bool in = r0 + j < n && i < j;
+        const float t = in ? (float)SGT_AT(T, ldt, r0 + i, r0 + j) : 0.f;
+        const float a = in ? (float)SGT_AT(A, lda, r0 + i, r0 + j) : 0.f;
+        // row-major M: row i picks by the sign of i; column-major N: column j by the sign of j
+        mp[0 * MB * MB + i * MB + j] = sg[i] > 0.f ? a : t;
+        mp[1 * MB * MB + i * MB + j] = sg[i] > 0.f ? t : a;
+        mp[2 * MB * MB + j * MB + i] = sg[j] > 0.f ? -a : t;
+        mp[3 * MB * MB + j * MB + i] = sg[j] > 0.f ? t : -a;
     }
 }
 
+// One warp solves the 16 x 16 sub-block with rows R0.. and columns C0.. of a
+// leaf tile (the recurrences above restricted to it; the terms of the other,
+// already solved, sub-blocks are in VR and VC).  Lane p (and its mirror p +
+// 16, which writes nothing) owns row R0 + p: its pending values c[q] start as
+// seed + row parts - column parts of the solved sub-blocks, entry (p, q) is
+// solved at step t = 15 - p + q, and each solved value is pushed at once into
+// the entries that depend on it -- into the row's later entries by the lane
+// itself (+ v N~), into the entries above it in its column by the other
+// lanes, which receive it by shuffle (- M v).  A step thus waits only for
+// one shuffle and one multiply-add; the step loop is unrolled so that every
+// register index is a constant.
+__device__ __forceinline__ void subblock_solve(const float *__restrict__ Mp, const float *__restrict__ Mm,
+                                               const float *__restrict__ Np, const float *__restrict__ Nm,
+                                               float *__restrict__ VC, float *__restrict__ VR,
+                                               const float *__restrict__ srow, const float *__restrict__ scol,
+                                               const float *__restrict__ drow, const float *__restrict__ dcol, int R0,
+                                               int C0, int lane)
+{
+    constexpr int LD = kLeafLD;
+    const int p = lane & (kSub - 1);
+    const int P = R0 + p;
+    // column signs of the sub-block, bit q for column C0 + q
+    const unsigned colmask = __ballot_sync(0xffffffffu, lane < kSub && scol[C0 + p] > 0.f) & 0xffffu;
+    const float sp = srow[P], dp = drow[P];
+    float c[kSub], mp[kSub], mm[kSub];
+#pragma unroll
+    for (int q = 0; q < kSub; q++) c[q] = VR[P * LD + C0 + q] - VC[(C0 + q) * LD + P];
+#pragma unroll
+    for (int k = 0; k < kSub; k += 4) {
+        const float4 x = *reinterpret_cast<const float4 *>(Mp + P * LD + R0 + k);
+        const float4 y = *reinterpret_cast<const float4 *>(Mm + P * LD + R0 + k);
+        mp[k] = x.x; mp[k + 1] = x.y; mp[k + 2] = x.z; mp[k + 3] = x.w;
+        mm[k] = y.x; mm[k + 1] = y.y; mm[k + 2] = y.z; mm[k + 3] = y.w;
+    }
+    const float *Nt = (sp > 0.f ? Np : Nm) + C0 * LD + C0;   // N~^{s_p}, this sub-block
+    float vprev = 0.f;
+#pragma unroll
+    for (int t = 0; t < 2 * kSub - 1; t++) {
+        // column parts: row k solved column t - 16 + k at the previous step
+#pragma unroll
+        for (int k = 0; k < kSub; k++) {
+            const int qk = t - kSub + k;
+            if (t > 0 && qk >= 0 && qk < kSub) {
+                const float vk = __shfl_sync(0xffffffffu, vprev, k);
+                c[qk] = fmaf((colmask >> qk) & 1u ? -mp[k] : -mm[k], vk, c[qk]);
+            }
+        }
+        const int qp = t - (kSub - 1) + p;
+        const bool act = lane < kSub && qp >= 0 && qp < kSub;
+        const int qc = min(max(qp, 0), kSub - 1);
+        float x = 0.f;
+#pragma unroll
+        for (int q = 0; q < kSub; q++)
+            if (q >= t - (kSub - 1) && q <= t && q == qc) x = c[q];
+        const bool sq = (colmask >> qc) & 1u;
+        const bool opp = (sp > 0.f) != sq;
+        const float den = opp ? dp - dcol[C0 + qc] : sp + (sq ? 1.f : -1.f);
+        const float v = act ? __fdividef(x, den) : 0.f;
+        // row part into the row's later entries (N~ vanishes for q <= qc)
+        if (t < 2 * kSub - 2) {
+#pragma unroll
+            for (int q = 0; q < kSub; q++) c[q] = fmaf(Nt[q * LD + qc], v, c[q]);
+        }
+        if (act) {
+            VC[(C0 + qc) * LD + P] = v;
+            VR[P * LD + C0 + qc] = v;
+        }
+        vprev = v;
+    }
+}
+
+// MODE 0: V = U (initial solve).  MODE 1: V = E (correction), with Rc, Rs.
+// Shared memory (fp32, pitch kLeafLD): the operators M^+, M^- of block I
+// (row-major) and N^+, N^- of block J (column-major), V by columns (VC) and
+// by rows (VR).  Until entry (p, q) is solved, VR[p][q] holds its seed (base
+// terms, block sums and the row parts of the solved sub-blocks) and VC[q][p]
+// the column parts of the solved sub-blocks.
 template <int MODE>
 __global__ void __launch_bounds__(kLeafThreads, 2)
 mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restrict__ V, int ldv,
-                  const float *__restrict__ DT, const float *__restrict__ DA, const double *__restrict__ Rc,
+                  const float *__restrict__ OPS, const float *__restrict__ DIAG, const double *__restrict__ Rc,
                   const double *__restrict__ Rs, int ldr, int d, const int2 *__restrict__ tslot,
                   const int2 *__restrict__ tslot2,
                   const double *__restrict__ PA, const double *__restrict__ PB, __nv_bfloat16 *__restrict__ Vr,
@@ -120,63 +216,58 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
 {
     constexpr int LD = kLeafLD;
     constexpr int EPT = MB * MB / kLeafThreads;   // tile entries per thread
+    constexpr int QS = kLeafThreads / MB;
     extern __shared__ float4 fsm4[];
-    float *TI = reinterpret_cast<float *>(fsm4);
-    float *TJ = TI + MB * LD;
-    float *AI = TJ + MB * LD;
-    float *AJ = AI + MB * LD;
-    float *Vs = AJ + MB * LD + 16;   // 16 banks off T and A: the sub-block updates read both at once
-    float *Cs = Vs + MB * LD;
-    __shared__ float srow[MB], scol[MB];
+    float *Mp = reinterpret_cast<float *>(fsm4);
+    float *Mm = Mp + MB * LD;
+    float *Np = Mm + MB * LD;
+    float *Nm = Np + MB * LD;
+    float *VC = Nm + MB * LD;
+    float *VR = VC + MB * LD;
+    __shared__ float srow[MB], scol[MB], drow[MB], dcol[MB];
     const int I = blockIdx.x, J = I + d;
     const int r0 = I * MB, c0 = J * MB;
     const int bj = min(MB, n - c0);
-    // thread's entries: row p, columns q0 + m * (kLeafThreads / MB)
     const int p = threadIdx.x % MB, q0 = threadIdx.x / MB;
-    constexpr int QS = kLeafThreads / MB;
 
-    // every global read that needs no sign first: the diagonal blocks, the
-    // base terms of the seeds, this tile's partial slots
+    // every global read that needs no sign first: the operators, the base
+    // terms of the seeds, this tile's partial slots
     const int2 ts = tslot[I];
-    // mode 0 with look-ahead pairing: a second set of partial slots in PB
     const int2 ts2 = (MODE == 0 && tslot2) ? tslot2[I] : make_int2(0, 0);
-    float base0[EPT], base1[EPT];
-#pragma unroll
+    // base terms staged in VR (t_pq, or Rc_pq) and VC (Rs_pq) at the thread's
+    // own entries until the seeds replace them
+#pragma unroll 4
     for (int m = 0; m < EPT; m++) {
         const int q = q0 + m * QS;
         const bool ok = q < bj;
-        if (MODE == 0) {
-            base0[m] = ok ? (float)SGT_AT(T, ldt, r0 + p, c0 + q) : 0.f;
-            base1[m] = 0.f;
-        } else {
-            base0[m] = ok ? (float)SGT_AT(Rc, ldr, r0 + p, c0 + q) : 0.f;
-            base1[m] = ok ? (float)SGT_AT(Rs, ldr, r0 + p, c0 + q) : 0.f;
-        }
+        VR[p * LD + q] = ok ? (float)SGT_AT(MODE == 0 ? T : Rc, MODE == 0 ? ldt : ldr, r0 + p, c0 + q) : 0.f;
+        VC[q * LD + p] = (MODE == 1 && ok) ? (float)SGT_AT(Rs, ldr, r0 + p, c0 + q) : 0.f;
     }
     {
-        const float4 *src[4] = {reinterpret_cast<const float4 *>(DT + (size_t)I * MB * MB),
-                                reinterpret_cast<const float4 *>(DT + (size_t)J * MB * MB),
-                                reinterpret_cast<const float4 *>(DA + (size_t)I * MB * MB),
-                                reinterpret_cast<const float4 *>(DA + (size_t)J * MB * MB)};
-        float *dst[4] = {TI, TJ, AI, AJ};
-        float4 v[4][EPT / 4];
+        const float4 *src[4] = {reinterpret_cast<const float4 *>(OPS + (size_t)(4 * I + 0) * MB * MB),
+                                reinterpret_cast<const float4 *>(OPS + (size_t)(4 * I + 1) * MB * MB),
+                                reinterpret_cast<const float4 *>(OPS + (size_t)(4 * J + 2) * MB * MB),
+                                reinterpret_cast<const float4 *>(OPS + (size_t)(4 * J + 3) * MB * MB)};
+        float *dst[4] = {Mp, Mm, Np, Nm};
 #pragma unroll
-        for (int a = 0; a < 4; a++)
+        for (int a = 0; a < 4; a++) {
+            float4 v[MB * MB / 4 / kLeafThreads];
 #pragma unroll
-            for (int m = 0; m < EPT / 4; m++) v[a][m] = src[a][threadIdx.x + m * kLeafThreads];
+            for (int m = 0; m < MB * MB / 4 / kLeafThreads; m++) v[m] = src[a][threadIdx.x + m * kLeafThreads];
 #pragma unroll
-        for (int a = 0; a < 4; a++)
-#pragma unroll
-            for (int m = 0; m < EPT / 4; m++) {
+            for (int m = 0; m < MB * MB / 4 / kLeafThreads; m++) {
                 const int e = 4 * (threadIdx.x + m * kLeafThreads);
-                // four rows of one column
-                *reinterpret_cast<float4 *>(dst[a] + e % MB + (e / MB) * LD) = v[a][m];
+                // four consecutive entries of one row (M) or column (N)
+                *reinterpret_cast<float4 *>(dst[a] + (e / MB) * LD + e % MB) = v[m];
             }
-        for (int idx = threadIdx.x; idx < MB * LD; idx += kLeafThreads) Vs[idx] = 0.f;
+        }
     }
     for (int i = threadIdx.x; i < MB; i += kLeafThreads) {
-        srow[i] = fsgn(SGT_AT(T, ldt, r0 + i, r0 + i));
-        scol[i] = (i < bj) ? fsgn(SGT_AT(T, ldt, c0 + i, c0 + i)) : 1.f;
+        const float dr = DIAG[r0 + i], dc = DIAG[c0 + i];
+        drow[i] = dr;
+        dcol[i] = dc;
+        srow[i] = dr > 0.f ? 1.f : -1.f;
+        scol[i] = (i < bj) ? (dc > 0.f ? 1.f : -1.f) : 1.f;
     }
     __syncthreads();
 
@@ -190,8 +281,13 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
         const float2 *PA2 = reinterpret_cast<const float2 *>(PA);
         const float2 *PB2 = reinterpret_cast<const float2 *>(PB);
         float acc[EPT];
+        bool opp[EPT];
 #pragma unroll
-        for (int m = 0; m < EPT; m++) acc[m] = 0.f;
+        for (int m = 0; m < EPT; m++) {
+            acc[m] = 0.f;
+            opp[m] = srow[p] + scol[q0 + m * QS] == 0.f;
+        }
+#pragma unroll 2
         for (int s = 0; s < ts.y + ts2.y; s++) {
             // mode 0: slots of PA, then (look-ahead pairing) slots of PB
             const bool second = s >= ts.y;
@@ -200,29 +296,28 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
 #pragma unroll
             for (int m = 0; m < EPT; m++) {
                 const int q = q0 + m * QS;
-                if (q < bj) {
-                    const bool opp = (srow[p] + scol[q] == 0.f);
-                    // opposite signs: TL - BR of PA (X); equal signs: TR of PA
-                    // (Y, mode 0) or TL + BR of PB (Y^E, mode 1)
-                    const float2 *src = opp ? P0 : (MODE == 0 ? P0 + 4096 : PB2);
-                    const size_t e = sb + (size_t)q * 64;
-                    const float2 l1 = src[e];
-                    float2 l2 = make_float2(0.f, 0.f);
-                    if (MODE == 1 || opp) l2 = src[e + 3 * 4096];
-                    const float sg = opp ? -1.f : 1.f;
-                    acc[m] += (l1.x + sg * l2.x) + (l1.y + sg * l2.y);
-                }
+                // opposite signs: TL - BR of PA (X); equal signs: TR of PA
+                // (Y, mode 0) or TL + BR of PB (Y^E, mode 1)
+                const float2 *src = opp[m] ? P0 : (MODE == 0 ? P0 + 4096 : PB2);
+                const size_t e = sb + (size_t)q * 64;
+                const float2 l1 = src[e];
+                float2 l2 = make_float2(0.f, 0.f);
+                if (MODE == 1 || opp[m]) l2 = src[e + 3 * 4096];
+                const float sg = opp[m] ? -1.f : 1.f;
+                acc[m] += (l1.x + sg * l2.x) + (l1.y + sg * l2.y);
             }
         }
 #pragma unroll
         for (int m = 0; m < EPT; m++) {
             const int q = q0 + m * QS;
+            const float b0 = VR[p * LD + q], b1 = VC[q * LD + p];
             float c = 0.f;
             if (q < bj) {
-                if (srow[p] + scol[q] == 0.f) c = (MODE == 0 ? base0[m] * (srow[p] - scol[q]) : -base0[m]) + acc[m];
-                else c = (MODE == 0) ? -acc[m] : -base1[m] - acc[m];
+                if (opp[m]) c = (MODE == 0 ? b0 * (srow[p] - scol[q]) : -b0) + acc[m];
+                else c = (MODE == 0) ? -acc[m] : -b1 - acc[m];
             }
-            Cs[p + q * LD] = c;
+            VR[p * LD + q] = c;
+            VC[q * LD + p] = 0.f;
         }
     }
     __syncthreads();
@@ -231,75 +326,73 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
     // (p, q) needs the entries below it in its column and left of it in its
     // row, so sub-block (a, b) (rows 16a.., columns 16b..) needs the
     // sub-blocks below and left of it, and phase s = (3 - a) + b holds up to
-    // four independent sub-blocks.  A phase first adds to its seeds the sums
-    // over the solved sub-blocks (two threads per entry: the column part and
-    // the row part), then one warp per sub-block runs the 31-step
-    // anti-diagonal wavefront inside it (two lanes per entry, warp-synchronous).
+    // four independent sub-blocks.  A phase first adds the sums over the solved
+    // sub-blocks -- the column parts into VC, the row parts into the seeds in
+    // VR, register-blocked 4 x 2 and 2 x 4 -- then one warp per sub-block
+    // solves it (subblock_solve).
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     for (int s = 0; s < 2 * kNSub - 1; s++) {
         const int blo = max(0, s - (kNSub - 1)), nblk = min(kNSub - 1, s) - blo + 1;
         if (s > 0) {
-            const int items = nblk * kSub * kSub * 2;   // a multiple of kLeafThreads: same trip count everywhere
-            for (int it = threadIdx.x; it < items; it += kLeafThreads) {
-                const int part = it & 1, e = it >> 1;
-                const int b = blo + e / (kSub * kSub), pq = e % (kSub * kSub);
-                const int a = kNSub - 1 - s + b;
-                const int P = a * kSub + pq % kSub, Q = b * kSub + pq / kSub;
-                const bool opp = (srow[P] + scol[Q] == 0.f);
-                // part 0: sum_{k >= 16(a+1)} M_Pk V_kQ; part 1: sum_{k < 16b} V_Pk N_kQ
-                const float *X = part == 0 ? (opp ? TI : AI) + P : Vs + P;
-                const float *Y = part == 0 ? Vs + Q * LD : (opp ? TJ : AJ) + Q * LD;
-                const int klo = part == 0 ? (a + 1) * kSub : 0, khi = part == 0 ? MB : b * kSub;
-                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-                for (int k = klo; k < khi; k += 4) {   // lengths are multiples of 16
-                    const float4 y = *reinterpret_cast<const float4 *>(Y + k);
-                    a0 = fmaf(X[k * LD], y.x, a0);
-                    a1 = fmaf(X[(k + 1) * LD], y.y, a1);
-                    a2 = fmaf(X[(k + 2) * LD], y.z, a2);
-                    a3 = fmaf(X[(k + 3) * LD], y.w, a3);
+            for (int it = threadIdx.x; it < 64 * nblk; it += kLeafThreads) {
+                const int b = blo + it / 64, w = it % 64, a = kNSub - 1 - s + b;
+                const int R0 = a * kSub, C0 = b * kSub;
+                if (w < 32) {
+                    // column parts of rows R0+4mr.. x columns C0+2mc..: sum over k >= 16(a+1)
+                    const int P = R0 + 4 * (w % 4), Q = C0 + 2 * (w / 4);
+                    float acc[4][2] = {};
+                    const float *mrow[4][2];
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+#pragma unroll
+                        for (int j = 0; j < 2; j++) mrow[i][j] = (scol[Q + j] > 0.f ? Mp : Mm) + (P + i) * LD;
+                    for (int k = R0 + kSub; k < MB; k += 4) {
+                        const float4 v0 = *reinterpret_cast<const float4 *>(VC + Q * LD + k);
+                        const float4 v1 = *reinterpret_cast<const float4 *>(VC + (Q + 1) * LD + k);
+#pragma unroll
+                        for (int i = 0; i < 4; i++) {
+                            const float4 x0 = *reinterpret_cast<const float4 *>(mrow[i][0] + k);
+                            const float4 x1 = *reinterpret_cast<const float4 *>(mrow[i][1] + k);
+                            acc[i][0] = fmaf(x0.x, v0.x, fmaf(x0.y, v0.y, fmaf(x0.z, v0.z, fmaf(x0.w, v0.w, acc[i][0]))));
+                            acc[i][1] = fmaf(x1.x, v1.x, fmaf(x1.y, v1.y, fmaf(x1.z, v1.z, fmaf(x1.w, v1.w, acc[i][1]))));
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+#pragma unroll
+                        for (int j = 0; j < 2; j++) VC[(Q + j) * LD + P + i] = acc[i][j];
+                } else {
+                    // row parts of rows R0+2mr.. x columns C0+4mc..: sum over k < 16b
+                    const int m = w - 32;
+                    const int P = R0 + 2 * (m % 8), Q = C0 + 4 * (m / 8);
+                    float acc[2][4] = {};
+                    const float *ncol[2][4];
+#pragma unroll
+                    for (int i = 0; i < 2; i++)
+#pragma unroll
+                        for (int j = 0; j < 4; j++) ncol[i][j] = (srow[P + i] > 0.f ? Np : Nm) + (Q + j) * LD;
+                    for (int k = 0; k < C0; k += 4) {
+                        const float4 v0 = *reinterpret_cast<const float4 *>(VR + P * LD + k);
+                        const float4 v1 = *reinterpret_cast<const float4 *>(VR + (P + 1) * LD + k);
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            const float4 y0 = *reinterpret_cast<const float4 *>(ncol[0][j] + k);
+                            const float4 y1 = *reinterpret_cast<const float4 *>(ncol[1][j] + k);
+                            acc[0][j] = fmaf(v0.x, y0.x, fmaf(v0.y, y0.y, fmaf(v0.z, y0.z, fmaf(v0.w, y0.w, acc[0][j]))));
+                            acc[1][j] = fmaf(v1.x, y1.x, fmaf(v1.y, y1.y, fmaf(v1.z, y1.z, fmaf(v1.w, y1.w, acc[1][j]))));
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 2; i++)
+#pragma unroll
+                        for (int j = 0; j < 4; j++) VR[(P + i) * LD + Q + j] += acc[i][j];
                 }
-                const float mine = (a0 + a1) + (a2 + a3);
-                const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-                if (part == 0) Cs[P + Q * LD] += opp ? (other - mine) : (-mine - other);
             }
             __syncthreads();
         }
         if (warp < nblk) {
             const int b = blo + warp, a = kNSub - 1 - s + b;
-            const int R0 = a * kSub, C0 = b * kSub;
-            if (C0 < bj) {
-                // lane pair el: entry el of anti-diagonal t of the sub-block;
-                // role 0 sums M_Pk V_kQ, role 1 V_Pk N_kQ, both over all 16 k
-                // of the sub-block: M and N are zero below their diagonals
-                // and V_PQ is still zero, so the terms outside (P, R0 + 16)
-                // and [C0, Q) vanish and no lane needs a predicate
-                const int el = lane >> 1, role = lane & 1;
-                for (int t = 0; t < 2 * kSub - 1; t++) {
-                    const int qlo = max(0, t - (kSub - 1)), qhi = min(kSub - 1, t);
-                    const bool act = qlo + el <= qhi;
-                    const int qq = act ? qlo + el : qhi;
-                    const int pp = kSub - 1 - t + qq;
-                    const int P = R0 + pp, Q = C0 + qq;
-                    const bool opp = (srow[P] + scol[Q] == 0.f);
-                    const float *X = role == 0 ? (opp ? TI : AI) + P + R0 * LD : Vs + P + C0 * LD;
-                    const float *Y = role == 0 ? Vs + R0 + Q * LD : (opp ? TJ : AJ) + C0 + Q * LD;
-                    const float rden = __frcp_rn(opp ? (TI[P + P * LD] - TJ[Q + Q * LD]) : (srow[P] + scol[Q]));
-                    const float cv = Cs[P + Q * LD];
-                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-                    for (int i = 0; i < kSub; i += 4) {
-                        const float4 y = *reinterpret_cast<const float4 *>(Y + i);
-                        a0 = fmaf(X[i * LD], y.x, a0);
-                        a1 = fmaf(X[(i + 1) * LD], y.y, a1);
-                        a2 = fmaf(X[(i + 2) * LD], y.z, a2);
-                        a3 = fmaf(X[(i + 3) * LD], y.w, a3);
-                    }
-                    const float mine = (a0 + a1) + (a2 + a3);
-                    const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-                    if (role == 0 && act && Q < bj) Vs[P + Q * LD] = (cv - mine + (opp ? other : -other)) * rden;
-                    __syncwarp();
-                }
-            }
+            if (b * kSub < bj) subblock_solve(Mp, Mm, Np, Nm, VC, VR, srow, scol, drow, dcol, a * kSub, b * kSub, lane);
         }
         __syncthreads();
     }
@@ -310,23 +403,42 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
     // exact (V is an fp32 value and a bf16 rounding removes its leading bits)
     const size_t tr = ((size_t)I * nbk + J) * MB * MB, tc = ((size_t)J * nbk + I) * MB * MB;
     const size_t sstride = (size_t)nbk * nbk * MB * MB;
-    for (int idx = threadIdx.x; idx < MB * bj; idx += kLeafThreads) {
-        const int pr = idx % MB, q = idx / MB;
-        float r = Vs[pr + q * LD];
-        SGT_AT(V, ldv, r0 + pr, c0 + q) = (double)r;
-        for (int s = 0; s < S; s++) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(r);
-            Vc[s * sstride + tc + q * MB + pr] = h;
-            r -= __bfloat162float(h);
+    // four consecutive entries per thread and store: column form (and V) from
+    // VC, row form from VR
+    for (int idx = threadIdx.x; idx < MB * MB / 4; idx += kLeafThreads) {
+        const int pr = 4 * (idx % (MB / 4)), q = idx / (MB / 4);
+        if (q < bj) {
+            float4 r = *reinterpret_cast<const float4 *>(VC + q * LD + pr);
+            double *vo = &SGT_AT(V, ldv, r0 + pr, c0 + q);
+            vo[0] = r.x; vo[1] = r.y; vo[2] = r.z; vo[3] = r.w;
+            for (int s = 0; s < S; s++) {
+                const __nv_bfloat162 h01 = __floats2bfloat162_rn(r.x, r.y), h23 = __floats2bfloat162_rn(r.z, r.w);
+                uint2 pk;
+                pk.x = *reinterpret_cast<const unsigned *>(&h01);
+                pk.y = *reinterpret_cast<const unsigned *>(&h23);
+                *reinterpret_cast<uint2 *>(Vc + s * sstride + tc + q * MB + pr) = pk;
+                const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+                r.x -= f01.x; r.y -= f01.y; r.z -= f23.x; r.w -= f23.y;
+            }
         }
     }
-    for (int idx = threadIdx.x; idx < MB * bj; idx += kLeafThreads) {
-        const int q = idx % bj, pr = idx / bj;
-        float r = Vs[pr + q * LD];
-        for (int s = 0; s < S; s++) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(r);
-            Vr[s * sstride + tr + pr * MB + q] = h;
-            r -= __bfloat162float(h);
+    for (int idx = threadIdx.x; idx < MB * MB / 4; idx += kLeafThreads) {
+        const int q = 4 * (idx % (MB / 4)), pr = idx / (MB / 4);
+        if (q < bj) {
+            // columns at or beyond bj stay zero: a partial group keeps them so
+            float4 r = *reinterpret_cast<const float4 *>(VR + pr * LD + q);
+            if (q + 1 >= bj) r.y = 0.f;
+            if (q + 2 >= bj) r.z = 0.f;
+            if (q + 3 >= bj) r.w = 0.f;
+            for (int s = 0; s < S; s++) {
+                const __nv_bfloat162 h01 = __floats2bfloat162_rn(r.x, r.y), h23 = __floats2bfloat162_rn(r.z, r.w);
+                uint2 pk;
+                pk.x = *reinterpret_cast<const unsigned *>(&h01);
+                pk.y = *reinterpret_cast<const unsigned *>(&h23);
+                *reinterpret_cast<uint2 *>(Vr + s * sstride + tr + pr * MB + q) = pk;
+                const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+                r.x -= f01.x; r.y -= f01.y; r.z -= f23.x; r.w -= f23.y;
+            }
         }
     }
 }
@@ -664,7 +776,7 @@ struct MixedCtx {
     // bf16 splits (S slices) of T and of the unknowns, row and column forms,
     // blocked layout (each 64 x 64 tile contiguous)
     __nv_bfloat16 *Tr, *Tc, *Ur, *Uc, *Er, *Ec;
-    float *DT32, *DA32;         // fp32 diagonal blocks for the leaves (64 x 64 each)
+    float *OPS, *DIAG;          // per-sign fp32 operators of the diagonal blocks for the leaves, fp32 diagonal
     // exact slices of the strictly upper parts of T and U in the gathered
     // layout (residual products): ng gathered positions, rows_g allocated
     // (the last 64 all zero), pitch rows_g
@@ -724,7 +836,7 @@ size_t bytes_for(int n, int S)
     b += 2 * maxjobs * 16384 * 8 + 2 * 256;                             // partials
     b += 2 * (size_t)n * n * 8 + 2 * 256;                               // E, R (= Rs)
     b += 64 + 256;                                                      // norms
-    b += 2 * nb * MB * MB * sizeof(float) + 2 * 256;                    // fp32 diagonal blocks
+    b += 4 * nb * MB * MB * sizeof(float) + nb * MB * sizeof(float) + 2 * 256;   // leaf operators, diagonal
     const size_t pairs_max = ngr / 128 + 2 * (size_t)((n + kSuper - 1) / kSuper) + 2;
     b += pairs_max * pairs_max * sizeof(TcJob) + 256;                   // needed-residual jobs
     const size_t nbp = (nb + 1) / 2;
@@ -763,16 +875,17 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
                      __nv_bfloat16 *Vc, const double *U0, int ldu0)
 {
     const int n = c.n, nb = c.sc.nb;
-    const size_t leaf_smem = ((size_t)leaf_buffers<MODE>() * MB * kLeafLD + 16) * sizeof(float);
+    const size_t leaf_smem = (size_t)kLeafBufs * MB * kLeafLD * sizeof(float);
     SGT_CUDA_TRY(cudaFuncSetAttribute(mixed_leaf_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)leaf_smem));
     SGT_CUDA_TRY(cudaFuncSetAttribute(mixed_leaf_kernel<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       cudaSharedmemCarveoutMaxShared));   // two leaves per SM
     {
-        // fp32 copies of the diagonal blocks of T and of the known blocks
-        // the same-sign recurrences use (U in mode 0, U0 in mode 1)
+        // the leaves' per-sign fp32 operators of the diagonal blocks, built
+        // from T and the known blocks the same-sign recurrences use (U in
+        // mode 0, U0 in mode 1)
         ProfScope ps(MODE == 0 ? SIGNTRI_KC_OFFDIAG_LEAF_F32 : SIGNTRI_KC_CORRECTION, c.st);
-        diag32_kernel<<<nb, 256, 0, c.st>>>(n, T, ldt, MODE == 0 ? V : U0, MODE == 0 ? ldv : ldu0, c.DT32, c.DA32);
+        leaf_ops_kernel<<<nb, 256, 0, c.st>>>(n, T, ldt, MODE == 0 ? V : U0, MODE == 0 ? ldv : ldu0, c.OPS, c.DIAG);
         SGT_LAUNCH_CHECK();
     }
     // slices in the blocked layout: every 64 x 64 tile one contiguous 8 KB run
@@ -888,7 +1001,7 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
         }
         ProfScope ps(MODE == 0 ? SIGNTRI_KC_OFFDIAG_LEAF_F32 : SIGNTRI_KC_CORRECTION, c.st);
         mixed_leaf_kernel<MODE><<<ntiles, kLeafThreads, leaf_smem, c.st>>>(
-            n, T, ldt, V, ldv, c.DT32, c.DA32, c.res_c, c.res_s, n, d, leaf_slots, leaf_slots2, c.PA, c.PB, Vr, Vc,
+            n, T, ldt, V, ldv, c.OPS, c.DIAG, c.res_c, c.res_s, n, d, leaf_slots, leaf_slots2, c.PA, c.PB, Vr, Vc,
             c.S, nb);
         SGT_LAUNCH_CHECK();
     }
@@ -1210,7 +1323,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     const size_t maxjobs = (size_t)std::max({c.sc.max_jobs, c.scA.max_jobs, c.scB.max_jobs, c.scC.max_jobs, 1});
     c.PA = take<double>(ws, maxjobs * 16384); c.PB = take<double>(ws, maxjobs * 16384);
     c.E = take<double>(ws, (size_t)n * n); c.R = take<double>(ws, (size_t)n * n);
-    c.DT32 = take<float>(ws, (size_t)nb * MB * MB); c.DA32 = take<float>(ws, (size_t)nb * MB * MB);
+    c.OPS = take<float>(ws, (size_t)4 * nb * MB * MB); c.DIAG = take<float>(ws, (size_t)nb * MB);
     const int nbp = (nb + 1) / 2;
     c.n_full_jobs = nbp * (nbp + 1) / 2;
     c.d_full_jobs = take<TcJob>(ws, (size_t)c.n_full_jobs);
@@ -1246,7 +1359,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
         !c.NUc || !c.d_full_jobs || !c.sTr ||
         !c.sTc || !c.sUr || !c.sUc || !c.gTr || !c.gTc || !c.gUr || !c.gUc || !c.gmap || !c.ginv || !c.pos ||
         !c.tmpmax || !c.tmpmax2 || !c.PA || !c.PB || !c.E || !c.R || !c.RA || !c.RB || !c.norms || !c.d_res_jobs ||
-        !c.d_pairs_split || !c.d_pairs_oz || !c.DT32 || !c.DA32 || !c.sbbase)
+        !c.d_pairs_split || !c.d_pairs_oz || !c.OPS || !c.DIAG || !c.sbbase)
         return SIGNTRI_ERR_NO_WORKSPACE;
     c.pairs_split = split_pairs(S);
     c.pairs_oz = ozaki_pairs_impl(kOzakiSlices, kOzakiBits);

@@ -27,6 +27,15 @@ constexpr int kSweepTile = 64;
 // same split, so that the CTA pairs that read the same E panels at the same
 // time share them through L2.
 constexpr int kSweepCtas = 152;
+// At most this many CTAs (partial slots) per tile: the leaf adds a tile's
+// slots one after another, so on the last anti-diagonals, where few tiles
+// would share all CTAs, a longer K range per CTA costs less than the slots.
+constexpr int kMaxSlotsPerTile = 16;
+
+inline int sweep_ctas(int gmax, int ntiles, long long W)
+{
+    return (int)std::min<long long>(std::min<long long>(gmax, W), (long long)ntiles * kMaxSlotsPerTile);
+}
 
 struct Schedule {
     int nb = 0;
@@ -75,7 +84,7 @@ inline void add_even_split(Schedule &sc, int d, int nb, int gmax)
 {
     const int ntiles = nb - d;
     const long long kmax = d + 1, W = (long long)ntiles * kmax;
-    const int G = (int)std::min<long long>(gmax, W);
+    const int G = sweep_ctas(gmax, ntiles, W);
     sc.nctas[d] = G;
     const int base = (int)sc.jobs.size();
     for (int c = 0; c < G; c++) {
@@ -135,7 +144,7 @@ inline void build_look_schedules(int n, int gmax, Schedule &A, Schedule &B, Sche
         // B: the look-ahead sums of anti-diagonal e = d, matched to A's split of d - 1
         const int e = d, dl = d - 1, nl = nb - dl, ne = nb - e;
         const long long kmax = dl + 1, W = (long long)nl * kmax;
-        const int G = (int)std::min<long long>(gmax, W);
+        const int G = sweep_ctas(gmax, nl, W);   // the lead's split
         B.nctas[e] = G;
         const int base = (int)B.jobs.size();
         for (int c = 0; c < G; c++) {

@@ -126,6 +126,9 @@ static void check_list(const Schedule &sc, int d, bool completion, bool nonempty
             prev = slot_k0[q];
         }
         listed += ts.y;
+        // a full split (one sweep launch) gives a tile at most kMaxSlotsPerTile
+        // CTAs, so at most that many slots plus one per CTA-range boundary
+        CHECK(ts.y <= kMaxSlotsPerTile + 1, "d=%d tile %d: %d slots", d, t, ts.y);
     }
     CHECK(listed == s.j1 - s.j0, "d=%d: %d slots listed for %d jobs", d, listed, s.j1 - s.j0);
 }
