@@ -7,11 +7,12 @@ One step = one sign_tri call on a resident input: inertia scan, variant
 choice, and the chosen variant's kernels.  The input (2.1 GB) and output are
 each larger than L2 (129 MB), so no flush is needed between steps.
 
-The headline is the mixed-precision form with refinement (PH_MIXED_TF32:
-tensor-core block sums, fp32 leaves, float64 defect correction with
-emulated-float64 residuals); the plain float64 form (PH_FP64) is timed on the
-same input for the comparison the metric names, and both are checked against
-the oracle on the leading and trailing 4096 principal windows.
+The headline is the mixed-precision form with refinement (PH_MIXED_FP16:
+tensor-core block sums on a two-term fp16 split, fp32 leaves, float64 defect
+correction with emulated-float64 residuals); the three-term bf16 split
+(PH_MIXED_TF32) and the float64 forms (PH_FP64_EFFICIENT, PH_FP64) are timed
+on the same input for the comparison the metric names, and all are checked
+against the oracle on the leading and trailing 4096 principal windows.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--variant V]
     python bench.py --impl reference      # the CPU oracle, the reference arm
@@ -57,8 +58,8 @@ def parse_args(argv=None):
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--p", type=float, default=0.5)
     ap.add_argument("--order", default="random")
-    ap.add_argument("--variant", default="PH_MIXED_TF32")
-    ap.add_argument("--compare", default="PH_FP64,PH_FP64_EFFICIENT",
+    ap.add_argument("--variant", default="PH_MIXED_FP16")
+    ap.add_argument("--compare", default="PH_MIXED_TF32,PH_FP64_EFFICIENT,PH_FP64",
                     help="comma-separated variants timed beside the headline on the same input ('' to skip)")
     ap.add_argument("--cutoff", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -410,23 +411,38 @@ def main():
                                "in MEASURED_PEAKS.json)",
                 "share_of_step": per_class[dom]["device_ms"] / ms_total}
     elif dom == "block_sums_tc":
-        # the sweeps' block sums stream every operand panel once: bound by HBM
+        # the sweeps' block sums against the tensor roof on the method's own
+        # work: the initial sweep's useful flops (the oracle's count) and, per
+        # refinement step, one sum per entry of the correction (4 flops per
+        # (i, k, j) term of X^E = ET - TE or Y^E = U0 E + E U0: 4 C(n, 3)).
+        # Beside it: the executed tensor rate (every slice pair and quadrant
+        # issued) and the operand bytes against the copy bandwidth.
         peaks, src = measured_peaks()
-        peak = float(peaks.get("hbm_gbs", 6800.0))
+        peak_t = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        peak_b = float(peaks.get("hbm_gbs", 6800.0))
         launches_dom = per_class[dom]["launches"]
         bytes_all = st.signtri_profile_read_bytes(st.signtri.KC_BLOCK_SUMS_TC)
         flops_all = st.signtri_profile_read_flops(st.signtri.KC_BLOCK_SUMS_TC)
-        per_launch = bytes_all / launches_dom
         avg_ms = per_class[dom]["device_ms"] / launches_dom
-        ach = per_launch / (avg_ms * 1e-3) / 1e9
+        method_step = useful + 4.0 * math.comb(n, 3) * max(info.refine_steps, 0)
+        per_launch = method_step * args.steps / launches_dom
+        ach = per_launch / (avg_ms * 1e-3) / 1e12
+        bytes_launch = bytes_all / launches_dom
+        ach_b = bytes_launch / (avg_ms * 1e-3) / 1e9
         sha = src_sha("paper_1607_06303_gb300/csrc/tc_gemm.cu")
         traffic = TRAFFIC.get((dom, sha))
-        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": None if traffic is None else traffic * per_launch,
-                "kernel": "tc_blocksum_kernel (tcgen05 bf16, sweep block sums, blocked slice layout)",
-                "algorithmic_bytes_per_launch": per_launch,
-                "tensor_tflops": flops_all / launches_dom / (avg_ms * 1e-3) / 1e12,
-                "peak_source": "hbm_gbs of %s (copy bandwidth)" % src,
+        fp16 = variant == st.Variant.PH_MIXED_FP16
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak_t, "unit": "TFLOP/s", "frac": ach / peak_t,
+                "traffic": None if traffic is None else traffic * bytes_launch,
+                "kernel": "tc_blocksum_kernel (tcgen05 %s, sweep block sums, blocked slice layout)"
+                          % ("fp16, two-term split" if fp16 else "bf16 split"),
+                "algorithmic_flops_per_launch": per_launch,
+                "peak_source": "bf16_tflops_sustained of %s (fp16 runs at the bf16 rate; kernel timed inside "
+                               "a long step)" % src,
+                "executed_tflops": flops_all / launches_dom / (avg_ms * 1e-3) / 1e12,
+                "executed_frac": flops_all / launches_dom / (avg_ms * 1e-3) / 1e12 / peak_t,
+                "hbm_view": {"operand_bytes_per_launch": bytes_launch, "achieved_gbs": ach_b, "peak_gbs": peak_b,
+                             "frac": ach_b / peak_b, "peak_source": "hbm_gbs of %s (copy bandwidth)" % src},
                 "share_of_step": per_class[dom]["device_ms"] / ms_total}
     elif dom == "residual":
         peaks, src = measured_peaks()
@@ -463,7 +479,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step_max, "seconds_per_solve": ms_step_max / 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if variant in (st.Variant.PH_FP64, st.Variant.PS_FP64) else "bf16+f32+f64",
+        "dtype": ("f64" if variant in (st.Variant.PH_FP64, st.Variant.PS_FP64, st.Variant.PH_FP64_EFFICIENT)
+                  else "fp16+f32+f64" if variant == st.Variant.PH_MIXED_FP16 else "bf16+f32+f64"),
         "data": "synthetic",
         "config": {"workload": "sign(T) n=%d p=%g %s diagonal, |t_ii|~U[0.5,2], t_ij~N(0,1/n), seed=rank"
                                % (n, args.p, args.order),
@@ -504,7 +521,7 @@ def main():
                        "seconds_per_solve": e2e_s, "repetitions_s": reps}
         del Th, Uh
 
-    # comparison variants on the same input (float64 forms), fewer steps
+    # comparison variants on the same input, fewer steps
     compares = []
     for cname in [c for c in (args.compare or "").split(",") if c and c != args.variant]:
         cv = st.Variant[cname]

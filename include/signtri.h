@@ -73,7 +73,19 @@ typedef enum {
        terms in the same order as in SIGNTRI_PH_FP64, so the two results
        agree bit for bit (up to the sign of zero).  Workspace: see
        signtri_workspace_bytes. */
-    SIGNTRI_PH_FP64_EFFICIENT = 5
+    SIGNTRI_PH_FP64_EFFICIENT = 5,
+    /* As SIGNTRI_PH_MIXED_TF32, with each block-update operand split into
+       two fp16 terms (hi + lo, 22 significant bits) and the three products
+       with s + t <= 1 summed: half the tensor-core products and two thirds of
+       the operand bytes of the three-term bf16 split, about 2^-21 relative
+       instead of 2^-24.  fp16 spans 2^-24 .. 65504, so T, U and each
+       correction are scaled by powers of two (from the largest strictly
+       upper entry of T, of the diagonal blocks of U, and of the correction's
+       first-order terms Rc_ij / (t_ii - t_jj) and Rs_ij / 2); a problem
+       whose values leave that range shows up as a residual that does not
+       contract, and the call then falls back to SIGNTRI_PH_FP64 like the
+       other mixed variants. */
+    SIGNTRI_PH_MIXED_FP16 = 6
 } signtri_variant;
 
 typedef enum {

@@ -54,7 +54,7 @@ int g_mixed_max_steps = -1;   // < 0: per-variant default
 int g_mixed_verify_full = 0;  // 1: accept on the full residuals, 0: on their probe estimate
 thread_local signtri_info g_info;
 
-bool valid_variant(int v) { return v >= SIGNTRI_AUTO && v <= SIGNTRI_PH_FP64_EFFICIENT; }
+bool valid_variant(int v) { return v >= SIGNTRI_AUTO && v <= SIGNTRI_PH_MIXED_FP16; }
 
 signtri_status current_state(DeviceState **out)
 {
@@ -134,8 +134,9 @@ size_t workspace_need(int n, signtri_variant v, int cutoff, long long swaps)
         return ph_fp64_split_workspace_bytes(n, cutoff);
     case SIGNTRI_PH_MIXED_TF32:
     case SIGNTRI_PH_MIXED_BF16:
+    case SIGNTRI_PH_MIXED_FP16:
         // the float64 fallback reuses the same memory
-        return std::max(mixed_workspace_bytes(n, v == SIGNTRI_PH_MIXED_TF32 ? 3 : 1),
+        return std::max(mixed_workspace_bytes(n, v == SIGNTRI_PH_MIXED_TF32 ? 3 : (v == SIGNTRI_PH_MIXED_FP16 ? 2 : 1)),
                         ph_fp64_workspace_bytes(n, cutoff));
     case SIGNTRI_PS_FP64:
         return ps_workspace_bytes(n, swaps);
@@ -207,9 +208,11 @@ signtri_status run_variant(int n, const double *T, int ldt, double *U, int ldu, 
     case SIGNTRI_PS_FP64:
         return ps_fp64_run(n, T, ldt, U, ldu, r.n_pos, r.swaps, ws, st);
     case SIGNTRI_PH_MIXED_TF32:
-    case SIGNTRI_PH_MIXED_BF16: {
-        const int S = (v == SIGNTRI_PH_MIXED_TF32) ? 3 : 1;
-        MixedParams prm{g_mixed_tol, g_mixed_max_steps >= 0 ? g_mixed_max_steps : (S == 3 ? 3 : 8), 10.0,
+    case SIGNTRI_PH_MIXED_BF16:
+    case SIGNTRI_PH_MIXED_FP16: {
+        // S split terms per operand; a negative S marks the fp16 split
+        const int S = (v == SIGNTRI_PH_MIXED_TF32) ? 3 : (v == SIGNTRI_PH_MIXED_FP16 ? -2 : 1);
+        MixedParams prm{g_mixed_tol, g_mixed_max_steps >= 0 ? g_mixed_max_steps : (S == 1 ? 8 : 3), 10.0,
                         g_mixed_verify_full};
         MixedReport rep{};
         SGT_CUDA_TRY(cudaMemsetAsync(s.err_dev, 0, sizeof(int), st));

@@ -61,6 +61,7 @@
 #include <vector>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "internal.cuh"
 #include "gathered_layout.h"
@@ -79,6 +80,30 @@ constexpr int kOzakiBits = 7;
 constexpr int kSuper = 1024;   // superblock of the gathered residual layout
 
 __device__ __forceinline__ float fsgn(double t) { return t > 0.0 ? 1.f : -1.f; }
+
+// One term of a rounding split: the 16-bit rounding of x (bf16, or fp16 when
+// f16), x left holding the remainder (exact in fp32).
+__device__ __forceinline__ unsigned short split_term(float &x, bool f16)
+{
+    if (f16) {
+        const __half h = __float2half_rn(x);
+        x -= __half2float(h);
+        return __half_as_ushort(h);
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    x -= __bfloat162float(h);
+    return __bfloat16_as_ushort(h);
+}
+
+// Four consecutive entries, S terms each, slice s at dst + s * sstride.
+__device__ __forceinline__ void split_store4(float4 r, int S, bool f16, __nv_bfloat16 *dst, size_t sstride)
+{
+    for (int s = 0; s < S; s++) {
+        const unsigned a = split_term(r.x, f16), b = split_term(r.y, f16);
+        const unsigned c = split_term(r.z, f16), d = split_term(r.w, f16);
+        *reinterpret_cast<uint2 *>(dst + s * sstride) = make_uint2(a | (b << 16), c | (d << 16));
+    }
+}
 
 // --------------------------------------------------------------- leaves ---
 
@@ -212,7 +237,7 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
                   const double *__restrict__ Rs, int ldr, int d, const int2 *__restrict__ tslot,
                   const int2 *__restrict__ tslot2,
                   const double *__restrict__ PA, const double *__restrict__ PB, __nv_bfloat16 *__restrict__ Vr,
-                  __nv_bfloat16 *__restrict__ Vc, int S, int nbk)
+                  __nv_bfloat16 *__restrict__ Vc, int S, int nbk, float sigma)
 {
     constexpr int LD = kLeafLD;
     constexpr int EPT = MB * MB / kLeafThreads;   // tile entries per thread
@@ -397,10 +422,12 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
         __syncthreads();
     }
 
-    // V (float64) and its bf16 splits in the blocked slice layout: row
+    // V (float64) and its 16-bit splits in the blocked slice layout: row
     // slices tile (I, J) of Vr[s] (row-major), column slices tile (J, I) of
-    // Vc[s] (V^T, row-major).  The split runs in fp32: each remainder is
-    // exact (V is an fp32 value and a bf16 rounding removes its leading bits)
+    // Vc[s] (V^T, row-major).  The split runs in fp32, of V (bf16 terms) or
+    // of sigma V (fp16 terms, sigma a power of two): each remainder is exact
+    const bool f16 = sigma > 0.f;
+    const float sc = f16 ? sigma : 1.f;
     const size_t tr = ((size_t)I * nbk + J) * MB * MB, tc = ((size_t)J * nbk + I) * MB * MB;
     const size_t sstride = (size_t)nbk * nbk * MB * MB;
     // four consecutive entries per thread and store: column form (and V) from
@@ -408,18 +435,10 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
     for (int idx = threadIdx.x; idx < MB * MB / 4; idx += kLeafThreads) {
         const int pr = 4 * (idx % (MB / 4)), q = idx / (MB / 4);
         if (q < bj) {
-            float4 r = *reinterpret_cast<const float4 *>(VC + q * LD + pr);
+            const float4 r = *reinterpret_cast<const float4 *>(VC + q * LD + pr);
             double *vo = &SGT_AT(V, ldv, r0 + pr, c0 + q);
             vo[0] = r.x; vo[1] = r.y; vo[2] = r.z; vo[3] = r.w;
-            for (int s = 0; s < S; s++) {
-                const __nv_bfloat162 h01 = __floats2bfloat162_rn(r.x, r.y), h23 = __floats2bfloat162_rn(r.z, r.w);
-                uint2 pk;
-                pk.x = *reinterpret_cast<const unsigned *>(&h01);
-                pk.y = *reinterpret_cast<const unsigned *>(&h23);
-                *reinterpret_cast<uint2 *>(Vc + s * sstride + tc + q * MB + pr) = pk;
-                const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-                r.x -= f01.x; r.y -= f01.y; r.z -= f23.x; r.w -= f23.y;
-            }
+            split_store4(make_float4(r.x * sc, r.y * sc, r.z * sc, r.w * sc), S, f16, Vc + tc + q * MB + pr, sstride);
         }
     }
     for (int idx = threadIdx.x; idx < MB * MB / 4; idx += kLeafThreads) {
@@ -430,15 +449,7 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
             if (q + 1 >= bj) r.y = 0.f;
             if (q + 2 >= bj) r.z = 0.f;
             if (q + 3 >= bj) r.w = 0.f;
-            for (int s = 0; s < S; s++) {
-                const __nv_bfloat162 h01 = __floats2bfloat162_rn(r.x, r.y), h23 = __floats2bfloat162_rn(r.z, r.w);
-                uint2 pk;
-                pk.x = *reinterpret_cast<const unsigned *>(&h01);
-                pk.y = *reinterpret_cast<const unsigned *>(&h23);
-                *reinterpret_cast<uint2 *>(Vr + s * sstride + tr + pr * MB + q) = pk;
-                const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-                r.x -= f01.x; r.y -= f01.y; r.z -= f23.x; r.w -= f23.y;
-            }
+            split_store4(make_float4(r.x * sc, r.y * sc, r.z * sc, r.w * sc), S, f16, Vr + tr + pr * MB + q, sstride);
         }
     }
 }
@@ -605,12 +616,14 @@ __global__ void apply_correction_kernel(int n, double *__restrict__ U, int ldu, 
     if (threadIdx.x == 0) atomicAdd(&norms[4], red[0]);
 }
 
-// Rounding-split bf16 slices of the strictly upper part of the diagonal
-// blocks of V (U after the float64 diagonal leaves, E after the corrections'
+// Rounding-split slices of the strictly upper part of the diagonal blocks
+// of V (U after the float64 diagonal leaves, E after the corrections'
 // diagonal leaves), in the blocked layout the leaves write: tile (I, I) of
-// Vr[s] (row-major) and of Vc[s] (transposed).  One CTA per block.
+// Vr[s] (row-major) and of Vc[s] (transposed).  bf16 terms of V (split in
+// float64), or fp16 terms of sigma V (sigma > 0, split in fp32: two terms
+// keep 22 bits).  One CTA per block.
 __global__ void diag_slices_kernel(int n, const double *__restrict__ V, int ldv, __nv_bfloat16 *__restrict__ Vr,
-                                   __nv_bfloat16 *__restrict__ Vc, int S, int nbk)
+                                   __nv_bfloat16 *__restrict__ Vc, int S, int nbk, float sigma)
 {
     const int I = blockIdx.x, r0 = I * MB;
     const int bs = min(MB, n - r0);
@@ -618,6 +631,15 @@ __global__ void diag_slices_kernel(int n, const double *__restrict__ V, int ldv,
     for (int idx = threadIdx.x; idx < bs * bs; idx += blockDim.x) {
         const int i = idx % bs, j = idx / bs;
         double r = (i < j) ? SGT_AT(V, ldv, r0 + i, r0 + j) : 0.0;
+        if (sigma > 0.f) {
+            float x = (float)(r * (double)sigma);
+            for (int s = 0; s < S; s++) {
+                const unsigned short h = split_term(x, true);
+                Vr[s * sstride + t + i * MB + j] = __ushort_as_bfloat16(h);
+                Vc[s * sstride + t + j * MB + i] = __ushort_as_bfloat16(h);
+            }
+            continue;
+        }
         for (int s = 0; s < S; s++) {
             const __nv_bfloat16 h = __double2bfloat16(r);
             Vr[s * sstride + t + i * MB + j] = h;
@@ -627,40 +649,78 @@ __global__ void diag_slices_kernel(int n, const double *__restrict__ V, int ldv,
     }
 }
 
-// Rounding-split bf16 slices (of the fp32 value, as the leaves split) of the
-// strictly upper part of the n x n matrix M in the blocked layout: tile
-// (I, K) of R[s] (row-major) and tile (K, I) of C[s] (transposed) for every
-// block K >= I; the blocks below are never read and not written.
+// Rounding-split slices (of the fp32 value, as the leaves split: bf16 terms,
+// or fp16 terms of sigma M when sigma > 0) of the strictly upper part of the
+// n x n matrix M in the blocked layout: tile (I, K) of R[s] (row-major) and
+// tile (K, I) of C[s] (transposed) for every block K >= I; the blocks below
+// are never read and not written.
 __global__ void blocked_split_kernel(int n, const double *__restrict__ M, int ldm, int S, int nbk,
-                                     __nv_bfloat16 *__restrict__ R, __nv_bfloat16 *__restrict__ C)
+                                     __nv_bfloat16 *__restrict__ R, __nv_bfloat16 *__restrict__ C, float sigma)
 {
     __shared__ float tile[MB][MB + 1];   // [column][row]
     const int K = blockIdx.x, I = blockIdx.y;
     if (K < I) return;
+    const bool f16 = sigma > 0.f;
+    const double sc = f16 ? (double)sigma : 1.0;
     const size_t sstride = (size_t)nbk * nbk * MB * MB;
     const size_t tr = ((size_t)I * nbk + K) * MB * MB, tc = ((size_t)K * nbk + I) * MB * MB;
     for (int idx = threadIdx.x; idx < MB * MB; idx += blockDim.x) {
         const int r = idx % MB, k = idx / MB;
         const int gi = I * MB + r, gk = K * MB + k;
-        const float v = (gi < gk && gk < n) ? (float)SGT_AT(M, ldm, gi, gk) : 0.f;
+        const float v = (gi < gk && gk < n) ? (float)(SGT_AT(M, ldm, gi, gk) * sc) : 0.f;
         tile[k][r] = v;
         float x = v;
-        for (int s = 0; s < S; s++) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(x);
-            C[s * sstride + tc + k * MB + r] = h;
-            x -= __bfloat162float(h);
-        }
+        for (int s = 0; s < S; s++) C[s * sstride + tc + k * MB + r] = __ushort_as_bfloat16(split_term(x, f16));
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < MB * MB; idx += blockDim.x) {
         const int k = idx % MB, r = idx / MB;
         float x = tile[k][r];
-        for (int s = 0; s < S; s++) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(x);
-            R[s * sstride + tr + r * MB + k] = h;
-            x -= __bfloat162float(h);
-        }
+        for (int s = 0; s < S; s++) R[s * sstride + tr + r * MB + k] = __ushort_as_bfloat16(split_term(x, f16));
     }
+}
+
+// Largest |entry| of the strictly upper part of the n x n matrix M (all of it,
+// or only its 64 x 64 diagonal blocks), as the bits of a non-negative float
+// (ordered like the values) max-ed into *out.
+__global__ void absmax_upper_kernel(int n, const double *__restrict__ M, int ldm, int diag_only,
+                                    unsigned *__restrict__ out)
+{
+    float m = 0.f;
+    const long long total = (long long)n * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        if (i < j && (!diag_only || i / MB == j / MB)) m = fmaxf(m, fabsf((float)SGT_AT(M, ldm, i, j)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// Largest first-order correction term |e_ij| ~ |Rc_ij| / |t_ii - t_jj|
+// (signs differ) or |Rs_ij| / 2 (signs agree) over the strictly upper
+// entries, max-ed into *out as float bits (see absmax_upper_kernel).
+__global__ void corr_magnitude_kernel(int n, const double *__restrict__ T, int ldt, const double *__restrict__ Rc,
+                                      const double *__restrict__ Rs, int ldr, unsigned *__restrict__ out)
+{
+    float m = 0.f;
+    const long long total = (long long)n * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        if (i >= j) continue;
+        const double ti = SGT_AT(T, ldt, i, i), tj = SGT_AT(T, ldt, j, j);
+        const double v = ((ti > 0.0) != (tj > 0.0)) ? fabs(SGT_AT(Rc, ldr, i, j)) / fabs(ti - tj)
+                                                   : 0.5 * fabs(SGT_AT(Rs, ldr, i, j));
+        m = fmaxf(m, (float)v);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+__global__ void fill_float_kernel(int count, float v, float *__restrict__ p)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) p[i] = v;
 }
 
 // ---------------------------------------------------------- probe check ---
@@ -763,6 +823,13 @@ struct DevSchedule {
 
 struct MixedCtx {
     int n, np, S;
+    // fp16 split (S = 2): T, U and E are split as sT T, sU U, sE E (powers of
+    // two), and the products' rows and columns scaled back by invT, invU,
+    // invE (np + 64 entries, constant); sT = sU = sE = 0 for the bf16 splits
+    bool f16;
+    float sT, sU, sE;
+    float *invT, *invU, *invE;
+    unsigned *amax;             // scratch of absmax_upper_kernel
     cudaStream_t st;
     int *d_err;
     Schedule sc, sc2;           // initial sweep; correction (two launches side by side)
@@ -837,6 +904,7 @@ size_t bytes_for(int n, int S)
     b += 2 * (size_t)n * n * 8 + 2 * 256;                               // E, R (= Rs)
     b += 64 + 256;                                                      // norms
     b += 4 * nb * MB * MB * sizeof(float) + nb * MB * sizeof(float) + 2 * 256;   // leaf operators, diagonal
+    b += 3 * (np + 64) * sizeof(float) + 64 + 4 * 256;                  // fp16 split scales, max slot
     const size_t pairs_max = ngr / 128 + 2 * (size_t)((n + kSuper - 1) / kSuper) + 2;
     b += pairs_max * pairs_max * sizeof(TcJob) + 256;                   // needed-residual jobs
     const size_t nbp = (nb + 1) / 2;
@@ -857,14 +925,49 @@ P *take(Arena &ws, size_t count)
     return static_cast<P *>(ws.take(count * sizeof(P)));
 }
 
+// 2^(target - floor(log2 m)) for m > 0: scales m into [2^target, 2^(target+1)).
+float pow2_scale(float m, int target)
+{
+    int e = 0;
+    std::frexp(m, &e);   // m = f 2^e, f in [0.5, 1)
+    return std::ldexp(1.f, std::max(-120, std::min(120, target - (e - 1))));
+}
+
+// Largest |entry| of the strictly upper part of M (diag_only: of its 64 x 64
+// diagonal blocks) into m; the host waits for it.
+signtri_status upper_absmax(MixedCtx &c, const double *M, int ldm, int diag_only, float &m)
+{
+    SGT_CUDA_TRY(cudaMemsetAsync(c.amax, 0, sizeof(unsigned), c.st));
+    {
+        ProfScope ps(SIGNTRI_KC_CONVERT, c.st);
+        absmax_upper_kernel<<<608, 256, 0, c.st>>>(c.n, M, ldm, diag_only, c.amax);
+        SGT_LAUNCH_CHECK();
+    }
+    unsigned bits = 0;
+    SGT_CUDA_TRY(cudaMemcpyAsync(&bits, c.amax, sizeof(unsigned), cudaMemcpyDeviceToHost, c.st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(c.st));
+    std::memcpy(&m, &bits, sizeof(float));
+    return SIGNTRI_OK;
+}
+
+// inv[0 .. np + 64) = 1 / sigma: the engine's row / column scales of a product
+// whose operand was split as sigma M
+signtri_status fill_inverse(MixedCtx &c, float *inv, float sigma)
+{
+    ProfScope ps(SIGNTRI_KC_FILL, c.st);
+    fill_float_kernel<<<8, 256, 0, c.st>>>(c.np + 64, 1.f / sigma, inv);
+    SGT_LAUNCH_CHECK();
+    return SIGNTRI_OK;
+}
+
 // Blocked-layout rounding splits of the strictly upper part of M (row and
 // column forms) for the sweeps.
-signtri_status split_full(MixedCtx &c, const double *M, int ldm, __nv_bfloat16 *R, __nv_bfloat16 *C)
+signtri_status split_full(MixedCtx &c, const double *M, int ldm, __nv_bfloat16 *R, __nv_bfloat16 *C, float sigma)
 {
     if (c.S > 8) return SIGNTRI_ERR_BAD_ARG;
     const int nbk = c.np / MB;
     ProfScope ps(SIGNTRI_KC_CONVERT, c.st);
-    blocked_split_kernel<<<dim3(nbk, nbk), 256, 0, c.st>>>(c.n, M, ldm, c.S, nbk, R, C);
+    blocked_split_kernel<<<dim3(nbk, nbk), 256, 0, c.st>>>(c.n, M, ldm, c.S, nbk, R, C, sigma);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }
@@ -889,9 +992,13 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
         SGT_LAUNCH_CHECK();
     }
     // slices in the blocked layout: every 64 x 64 tile one contiguous 8 KB run
-    const TcSource srcT_r{c.Tr, c.S, c.np, c.np, c.np, nullptr, 1}, srcT_c{c.Tc, c.S, c.np, c.np, c.np, nullptr, 1};
-    const TcSource srcV_r{Vr, c.S, c.np, c.np, c.np, nullptr, 1}, srcV_c{Vc, c.S, c.np, c.np, c.np, nullptr, 1};
-    const TcSource srcU_r{c.Ur, c.S, c.np, c.np, c.np, nullptr, 1}, srcU_c{c.Uc, c.S, c.np, c.np, c.np, nullptr, 1};
+    // fp16 splits carry their scales: the engine scales the products back
+    const int h = c.f16 ? 1 : 0;
+    const float *iT = c.f16 ? c.invT : nullptr, *iU = c.f16 ? c.invU : nullptr;
+    const float *iV = c.f16 ? (MODE == 0 ? c.invU : c.invE) : nullptr;
+    const TcSource srcT_r{c.Tr, c.S, c.np, c.np, c.np, iT, 1, h}, srcT_c{c.Tc, c.S, c.np, c.np, c.np, iT, 1, h};
+    const TcSource srcV_r{Vr, c.S, c.np, c.np, c.np, iV, 1, h}, srcV_c{Vc, c.S, c.np, c.np, c.np, iV, 1, h};
+    const TcSource srcU_r{c.Ur, c.S, c.np, c.np, c.np, iU, 1, h}, srcU_c{c.Uc, c.S, c.np, c.np, c.np, iU, 1, h};
     const TcQuadOut slots{{nullptr, nullptr, nullptr, nullptr}, 0, 0, 0};
     // K-blocks per tensor-core unit: with several unit-weight slice pairs the
     // engine keeps every slice of a K-block resident and accumulates all pairs
@@ -1002,7 +1109,7 @@ signtri_status sweep(MixedCtx &c, const double *T, int ldt, double *V, int ldv, 
         ProfScope ps(MODE == 0 ? SIGNTRI_KC_OFFDIAG_LEAF_F32 : SIGNTRI_KC_CORRECTION, c.st);
         mixed_leaf_kernel<MODE><<<ntiles, kLeafThreads, leaf_smem, c.st>>>(
             n, T, ldt, V, ldv, c.OPS, c.DIAG, c.res_c, c.res_s, n, d, leaf_slots, leaf_slots2, c.PA, c.PB, Vr, Vc,
-            c.S, nb);
+            c.S, nb, c.f16 ? (MODE == 0 ? c.sU : c.sE) : 0.f);
         SGT_LAUNCH_CHECK();
     }
     return SIGNTRI_OK;
@@ -1295,6 +1402,8 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     MixedCtx c{};
     c.n = n;
     c.np = pad64(n);
+    c.f16 = S < 0;   // a negative S asks for the fp16 split of -S terms
+    if (S < 0) S = -S;
     c.S = S;
     c.st = st;
     c.d_err = d_err;
@@ -1324,6 +1433,9 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     c.PA = take<double>(ws, maxjobs * 16384); c.PB = take<double>(ws, maxjobs * 16384);
     c.E = take<double>(ws, (size_t)n * n); c.R = take<double>(ws, (size_t)n * n);
     c.OPS = take<float>(ws, (size_t)4 * nb * MB * MB); c.DIAG = take<float>(ws, (size_t)nb * MB);
+    c.invT = take<float>(ws, np + 64); c.invU = take<float>(ws, np + 64); c.invE = take<float>(ws, np + 64);
+    c.amax = take<unsigned>(ws, 16);
+    if (!c.invT || !c.invU || !c.invE || !c.amax) return SIGNTRI_ERR_NO_WORKSPACE;
     const int nbp = (nb + 1) / 2;
     c.n_full_jobs = nbp * (nbp + 1) / 2;
     c.d_full_jobs = take<TcJob>(ws, (size_t)c.n_full_jobs);
@@ -1444,7 +1556,14 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     SGT_CUDA_TRY(cudaMemsetAsync(c.Er, 0, split_elems * 2, st));
     SGT_CUDA_TRY(cudaMemsetAsync(c.Ec, 0, split_elems * 2, st));
     signtri_status rs;
-    if ((rs = split_full(c, T, ldt, c.Tr, c.Tc)) != SIGNTRI_OK) return rs;
+    if (c.f16) {
+        // T's largest strictly upper entry to 2^13 .. 2^14 (fp16 stops at 65504)
+        float m = 0.f;
+        if ((rs = upper_absmax(c, T, ldt, 0, m)) != SIGNTRI_OK) return rs;
+        c.sT = m > 0.f ? pow2_scale(m, 13) : 1.f;
+        if ((rs = fill_inverse(c, c.invT, c.sT)) != SIGNTRI_OK) return rs;
+    }
+    if ((rs = split_full(c, T, ldt, c.Tr, c.Tc, c.f16 ? c.sT : 0.f)) != SIGNTRI_OK) return rs;
     if ((rs = gathered_slices_of(c, T, ldt, c.NTgr, c.NTgc, c.sTr, c.sTc, c.gTr, c.gTc)) != SIGNTRI_OK) return rs;
     // T's scales serve both layouts; the probe check reads only T's row
     // slices, the full residual also its column slices
@@ -1454,9 +1573,17 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     // 1. low-precision solve: diagonal blocks in float64, the rest by sweep
     if ((rs = launch_zero_strict_lower(n, U, ldu, st)) != SIGNTRI_OK) return rs;
     if ((rs = diag_leaves_f64(n, T, ldt, U, ldu, MB, st)) != SIGNTRI_OK) return rs;
+    if (c.f16) {
+        // U's scale from its diagonal blocks, largest entry to 2^12 .. 2^13:
+        // room for off-diagonal entries up to 8x larger
+        float m = 0.f;
+        if ((rs = upper_absmax(c, U, ldu, 1, m)) != SIGNTRI_OK) return rs;
+        c.sU = m > 0.f ? pow2_scale(m, 12) : c.sT;
+        if ((rs = fill_inverse(c, c.invU, c.sU)) != SIGNTRI_OK) return rs;
+    }
     {
         ProfScope ps(SIGNTRI_KC_CONVERT, st);
-        diag_slices_kernel<<<nb, 256, 0, st>>>(n, U, ldu, c.Ur, c.Uc, S, nb);
+        diag_slices_kernel<<<nb, 256, 0, st>>>(n, U, ldu, c.Ur, c.Uc, S, nb, c.f16 ? c.sU : 0.f);
         SGT_LAUNCH_CHECK();
     }
     if ((rs = sweep<0>(c, T, ldt, U, ldu, c.Ur, c.Uc, nullptr, 0)) != SIGNTRI_OK) return rs;
@@ -1511,7 +1638,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
         // U0's slices: after the initial sweep they are already in Ur / Uc
         // (off-diagonal blocks from the leaves, diagonal blocks from
         // diag_slices_kernel); after a correction U has moved
-        if (step > 0 && (rs = split_full(c, U, ldu, c.Ur, c.Uc)) != SIGNTRI_OK) return rs;
+        if (step > 0 && (rs = split_full(c, U, ldu, c.Ur, c.Uc, c.f16 ? c.sU : 0.f)) != SIGNTRI_OK) return rs;
         {
             const size_t dsm = 3 * (size_t)MB * (MB + 1) * sizeof(double);
             SGT_CUDA_TRY(cudaFuncSetAttribute(corr_diag_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1520,9 +1647,28 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
             corr_diag_leaf_kernel<<<nb, kLeafThreads, dsm, st>>>(n, T, ldt, U, ldu, c.res_c, c.res_s, n, c.E, n);
             SGT_LAUNCH_CHECK();
         }
+        if (c.f16) {
+            // the correction's scale from its first-order terms, Rc_ij /
+            // (t_ii - t_jj) or Rs_ij / 2 (its diagonal blocks are no guide,
+            // U0's being float64-exact), largest to 2^10 .. 2^11: room for
+            // entries of E up to 32x larger
+            float m = 0.f;
+            SGT_CUDA_TRY(cudaMemsetAsync(c.amax, 0, sizeof(unsigned), st));
+            {
+                ProfScope ps(SIGNTRI_KC_CONVERT, st);
+                corr_magnitude_kernel<<<608, 256, 0, st>>>(n, T, ldt, c.res_c, c.res_s, n, c.amax);
+                SGT_LAUNCH_CHECK();
+            }
+            unsigned bits = 0;
+            SGT_CUDA_TRY(cudaMemcpyAsync(&bits, c.amax, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+            SGT_CUDA_TRY(cudaStreamSynchronize(st));
+            std::memcpy(&m, &bits, sizeof(float));
+            c.sE = m > 0.f ? pow2_scale(m, 10) : c.sU;
+            if ((rs = fill_inverse(c, c.invE, c.sE)) != SIGNTRI_OK) return rs;
+        }
         {
             ProfScope ps(SIGNTRI_KC_CONVERT, st);
-            diag_slices_kernel<<<nb, 256, 0, st>>>(n, c.E, n, c.Er, c.Ec, S, nb);
+            diag_slices_kernel<<<nb, 256, 0, st>>>(n, c.E, n, c.Er, c.Ec, S, nb, c.f16 ? c.sE : 0.f);
             SGT_LAUNCH_CHECK();
         }
         if ((rs = sweep<1>(c, T, ldt, c.E, n, c.Er, c.Ec, U, ldu)) != SIGNTRI_OK) return rs;

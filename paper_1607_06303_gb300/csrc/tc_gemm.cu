@@ -50,8 +50,10 @@ constexpr int kBufs = 3;                    // TMEM accumulator buffers of 128 c
 constexpr long long kWaitCycles = 4000000000LL;   // about 2 s at 2 GHz
 
 // Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A and B bf16
-// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+// (bits 7-9, 10-12 = 1) or fp16 (0), both K-major, N >> 3 at bit 17, M >> 4
+// at bit 24.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdescF16 = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -132,12 +134,13 @@ __device__ __forceinline__ uint64_t smem_desc(const void *p)
     return a | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
 {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -228,8 +231,9 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
                    const TcPairs *__restrict__ pairs_g, int chunk_kb, const float *__restrict__ sTop,
                    const float *__restrict__ sBot, const float *__restrict__ sLeft, const float *__restrict__ sRight,
                    double *__restrict__ out, TcQuadOut qo, int *__restrict__ err, int resident, int nsl, int blk,
-                   int nkb)
+                   int nkb, int f16)
 {
+    const uint32_t idesc = f16 ? kIdescF16 : kIdesc;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
@@ -385,7 +389,7 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
                                 const uint64_t bd = smem_desc(base + (nsl + pairs.t[p]) * (kHalfBytes / 2));
 #pragma unroll
                                 for (int k = 0; k < 4; k++)
-                                    mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k),
+                                    mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc,
                                              (kb > kbs || p > 0 || k > 0) ? 1u : 0u);
                             }
                         } else {
@@ -396,7 +400,7 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
                                 const uint64_t ad = smem_desc(a), bd = smem_desc(b);
 #pragma unroll
                                 for (int k = 0; k < 4; k++)
-                                    mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k),
+                                    mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc,
                                              (kb > kbs || h > 0 || k > 0) ? 1u : 0u);
                             }
                         }
@@ -915,6 +919,10 @@ signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSo
     const int blk = top.blocked ? 1 : 0;
     if ((bot.blocked ? 1 : 0) != blk || (left.blocked ? 1 : 0) != blk || (right.blocked ? 1 : 0) != blk)
         return SIGNTRI_ERR_BAD_ARG;
+    // one operand type for A and B (kind::f16 takes both bf16 or both fp16)
+    const int f16 = top.f16 ? 1 : 0;
+    if ((bot.f16 ? 1 : 0) != f16 || (left.f16 ? 1 : 0) != f16 || (right.f16 ? 1 : 0) != f16)
+        return SIGNTRI_ERR_BAD_ARG;
     if (blk && (top.cols != bot.cols || top.cols != left.cols || top.cols != right.cols || (top.cols & 63) ||
                 (top.rows & 63) || (left.rows & 63)))
         return SIGNTRI_ERR_BAD_ARG;
@@ -946,6 +954,7 @@ signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSo
     for (int p = 0; p < pairs.n && !share; p++)
         for (int q = p + 1; q < pairs.n && !share; q++) share = pairs.s[p] == pairs.s[q];
     if (!resident && share) {
+        if (f16) return SIGNTRI_ERR_BAD_ARG;   // grouped pair mode serves the bf16 exact slices only
         const size_t smem2 = tc_pair2_smem_bytes();
         SGT_CUDA_TRY(cudaFuncSetAttribute(tc_pair2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
         prof_add_flops(kernel_class, useful_flops);
@@ -962,7 +971,7 @@ signtri_status tc_blocksums(const TcSource &top, const TcSource &bot, const TcSo
     ProfScope ps(kernel_class, st, timed);
     tc_blocksum_kernel<<<d_job_off ? nctas : njobs, kTcThreads, smem, st>>>(
         mt, mb, ml, mr, top.rows, left.rows, d_jobs, d_job_off, d_pairs, chunk_kb, top.scale, bot.scale, left.scale,
-        right.scale, out, qo, d_err, resident, nsl, blk, top.cols / 64);
+        right.scale, out, qo, d_err, resident, nsl, blk, top.cols / 64, f16);
     SGT_LAUNCH_CHECK();
     return SIGNTRI_OK;
 }

@@ -29,6 +29,8 @@ struct TcPairs {
 // blocked = 1: each matrix is stored as 64 x 64 tiles, tile (row block R,
 // K-block K) of slice s contiguous (8 KB, row-major, K fastest) at element
 // ((s * rows/64 + R) * cols/64 + K) * 4096; ld is then unused.
+// f16 = 1: the 16-bit elements are IEEE fp16 instead of bf16 (all four
+// sources of a product have the same type).
 struct TcSource {
     const __nv_bfloat16 *base;
     int nslices;
@@ -37,6 +39,7 @@ struct TcSource {
     int ld;
     const float *scale;
     int blocked;
+    int f16;
 };
 
 // Alternative output: quadrant q of every job written into its own

@@ -23,6 +23,7 @@ class Variant(enum.IntEnum):
     PH_MIXED_TF32 = 3
     PH_MIXED_BF16 = 4
     PH_FP64_EFFICIENT = 5
+    PH_MIXED_FP16 = 6
 
 
 class Status(enum.IntEnum):

@@ -62,7 +62,7 @@ def no_gpu_step(monkeypatch):
 
     def info():
         i = st.Info()
-        i.variant = int(st.Variant.PH_MIXED_TF32)
+        i.variant = int(st.Variant.PH_MIXED_FP16)
         i.cutoff = 64
         i.refine_steps = 1
         return i
@@ -106,19 +106,30 @@ def test_step_line(no_gpu_step, capsys, monkeypatch):
     roof = line["roofline"]
     for key in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
         assert key in roof, key
-    assert roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    assert roof["bound"] == "tensor" and roof["unit"] == "TFLOP/s"
     assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
-    # 5e9 operand bytes over 120 launches of 6 ms in all: 5e9/120 / (6e-3/120) B/s
-    assert roof["achieved"] == pytest.approx(5e9 / 6e-3 / 1e9)
+    # the method's work of the 3 timed steps (per step the oracle's useful
+    # flops of the initial sweep, 4 C(n,3) for the one correction) over 120
+    # launches of 6 ms in all
+    import math
+    import numpy as np
+    from paper_1607_06303_gb300 import workload
+    from paper_1607_06303_gb300.inputs import make_T
+    useful = workload.useful_flops(np.sign(np.diag(make_T(192, 0.5, seed=0))))
+    assert roof["achieved"] == pytest.approx(3 * (useful + 4 * math.comb(192, 3)) / 6e-3 / 1e12)
+    # beside it: 5e9 operand bytes over 120 launches of 6 ms in all against the copy bandwidth
+    assert roof["hbm_view"]["achieved_gbs"] == pytest.approx(5e9 / 6e-3 / 1e9)
+    assert roof["executed_tflops"] == pytest.approx(3e12 / 6e-3 / 1e12)
+    assert line["dtype"] == "fp16+f32+f64"
     assert line["roofline_second"]["bound"] == "tensor"
     e2e = line["e2e"]
     assert e2e["unit"] == line["unit"] and e2e["value"] > 0
     assert e2e["h2d_bytes_per_step"] == e2e["d2h_bytes_per_step"] == 8 * 192 * 192
     for key in ("sm_mhz", "sm_max_mhz", "reasons"):
         assert key in line["clocks"], key
-    assert [c["variant"] for c in line["compare"]] == ["PH_FP64", "PH_FP64_EFFICIENT"]
+    assert [c["variant"] for c in line["compare"]] == ["PH_MIXED_TF32", "PH_FP64_EFFICIENT", "PH_FP64"]
     # warm-up, timed steps, e2e (one warm call + three repetitions), comparisons
-    assert no_gpu_step["solves"] == 3 + 3 + 1 + 3 * 3 + 2 * (1 + 2)
+    assert no_gpu_step["solves"] == 3 + 3 + 1 + 3 * 3 + 3 * (1 + 2)
 
 
 def test_reference_line(capsys, monkeypatch):

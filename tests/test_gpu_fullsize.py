@@ -29,7 +29,7 @@ def T16384():
     return make_T(16384, 0.5, seed=0)
 
 
-@pytest.mark.parametrize("variant,tol", [("PH_MIXED_TF32", 1e-12), ("PH_FP64", 1e-11)])
+@pytest.mark.parametrize("variant,tol", [("PH_MIXED_TF32", 1e-12), ("PH_MIXED_FP16", 1e-12), ("PH_FP64", 1e-11)])
 def test_n16384(gpu_lib, oracle_mod, T16384, variant, tol):
     import torch
     Tt = gpu_lib.to_device(T16384)
@@ -42,7 +42,8 @@ def test_n16384(gpu_lib, oracle_mod, T16384, variant, tol):
     d = torch.diagonal(Ut)
     assert bool(torch.all(d == torch.sign(torch.diagonal(Tt))))
     assert bool(torch.all(torch.triu(Ut, 1) == 0))          # strictly lower part of U (transposed storage)
-    if variant == "PH_MIXED_TF32":
+    if variant.startswith("PH_MIXED"):
+        assert info.refine_steps == 1
         assert max(info.resid_commute, info.resid_involution) <= 1e-13
 
 

@@ -23,7 +23,7 @@ def solve(p, T, variant):
     return p.to_numpy(Ut), p.signtri_get_info()
 
 
-@pytest.mark.parametrize("variant", ["PH_MIXED_TF32", "PH_MIXED_BF16"])
+@pytest.mark.parametrize("variant", ["PH_MIXED_TF32", "PH_MIXED_BF16", "PH_MIXED_FP16"])
 @pytest.mark.parametrize("n,pr,order", [(3, 0.5, "random"), (50, 0.5, "random"), (64, 0.5, "random"),
                                         (65, 0.4, "random"), (130, 0.5, "random"), (257, 0.3, "random"),
                                         (300, 0.5, "sorted"), (700, 0.5, "random"), (1000, 0.1, "random"),
@@ -44,7 +44,7 @@ def test_mixed_vs_oracle(gpu_lib, oracle_mod, variant, n, pr, order):
 def test_mixed_medium(gpu_lib, oracle_mod, n):
     T = make_T(n, 0.5, seed=42)
     Uo = oracle_mod.sign_tri(T, schedule="antidiag")
-    for variant in ("PH_MIXED_TF32", "PH_MIXED_BF16"):
+    for variant in ("PH_MIXED_TF32", "PH_MIXED_BF16", "PH_MIXED_FP16"):
         U, info = solve(gpu_lib, T, gpu_lib.Variant[variant])
         assert relerr(U, Uo) <= TOL_MIXED, (variant, relerr(U, Uo), info.as_dict())
 
@@ -62,8 +62,9 @@ def test_mixed_fallback_to_fp64(gpu_lib, oracle_mod):
     assert relerr(U, oracle_mod.sign_tri(T)) <= 1e-11
 
 
+@pytest.mark.parametrize("variant", ["PH_MIXED_TF32", "PH_MIXED_FP16"])
 @pytest.mark.parametrize("pattern", ["blocks_of_one_sign", "alternating", "one_negative", "ragged_tail"])
-def test_mixed_gathered_residual_patterns(gpu_lib, oracle_mod, pattern):
+def test_mixed_gathered_residual_patterns(gpu_lib, oracle_mod, pattern, variant):
     # the first residual gathers indices per 1024-index superblock by sign;
     # cover superblocks of one sign, every class boundary inside 64-blocks,
     # a single negative index, and a ragged last superblock
@@ -83,11 +84,37 @@ def test_mixed_gathered_residual_patterns(gpu_lib, oracle_mod, pattern):
         s = np.where(rng.random(n) < 0.3, -1.0, 1.0)
     T[idx, idx] = s * rng.uniform(0.5, 2.0, n)
     T = np.asfortranarray(T)
-    U, info = solve(gpu_lib, T, gpu_lib.Variant.PH_MIXED_TF32)
+    U, info = solve(gpu_lib, T, gpu_lib.Variant[variant])
     Uo = oracle_mod.sign_tri(T, schedule="antidiag")
     assert relerr(U, Uo) <= TOL_MIXED, (pattern, relerr(U, Uo), info.as_dict())
-    assert info.variant == gpu_lib.Variant.PH_MIXED_TF32, info.as_dict()
+    assert info.variant == gpu_lib.Variant[variant], info.as_dict()
     assert max(info.resid_commute, info.resid_involution) <= 1e-13
+
+
+@pytest.mark.parametrize("scale", [1e-20, 1e20])
+def test_fp16_split_scales_with_the_input(gpu_lib, oracle_mod, scale):
+    # sign(cT) = sign(T) for c > 0: the fp16 split's power-of-two scales
+    # follow T, U and the residual, so the variant runs without fallback at
+    # magnitudes far outside fp16's range
+    T = make_T(700, 0.5, seed=46)
+    U, info = solve(gpu_lib, np.asfortranarray(T * scale), gpu_lib.Variant.PH_MIXED_FP16)
+    assert info.variant == gpu_lib.Variant.PH_MIXED_FP16, info.as_dict()
+    assert relerr(U, oracle_mod.sign_tri(T)) <= TOL_MIXED
+
+
+def test_fp16_split_out_of_range_falls_back(gpu_lib, oracle_mod):
+    # U's scale comes from its 64 x 64 diagonal blocks; with the strictly
+    # upper entries inside those blocks a million times smaller than the
+    # rest, the off-diagonal entries of U overflow fp16 after scaling, the
+    # residual is not finite, and the call falls back to float64
+    n = 500
+    T = make_T(n, 0.5, seed=47)
+    idx = np.arange(n)
+    same_block = (idx[:, None] // 64) == (idx[None, :] // 64)
+    T = np.asfortranarray(np.where(same_block & (idx[:, None] < idx[None, :]), T * 1e-6, T))
+    U, info = solve(gpu_lib, T, gpu_lib.Variant.PH_MIXED_FP16)
+    assert info.variant == gpu_lib.Variant.PH_FP64, info.as_dict()
+    assert relerr(U, oracle_mod.sign_tri(T)) <= 1e-11
 
 
 def test_verification_modes(gpu_lib, oracle_mod):
@@ -111,11 +138,12 @@ def test_verification_modes(gpu_lib, oracle_mod):
     assert gpu_lib.signtri_set_verification(2) == gpu_lib.Status.ERR_BAD_ARG
 
 
+@pytest.mark.parametrize("variant,slices,pairs", [("PH_MIXED_TF32", 3, 6), ("PH_MIXED_FP16", 2, 3)])
 @pytest.mark.parametrize("n", [700, 1000])
-def test_sweep_operand_byte_count(gpu_lib, n):
+def test_sweep_operand_byte_count(gpu_lib, n, variant, slices, pairs):
     # the byte model behind the sweeps' HBM roofline: every anti-diagonal d
     # of the nb = ceil(n/64) block partition reads, per tile (I, I+d), 64-row
-    # panels of three bf16 slices over its d+1 K-blocks once: four panels in
+    # panels of S 16-bit slices (three bf16 or two fp16) over its d+1 K-blocks once: four panels in
     # the initial sweep, six for the correction's two launches side by side
     # (they share the E panels).  In the initial sweep a lead anti-diagonal d
     # (odd, >= 3, d + 1 < nb) also sums d + 1's tiles over K-blocks
@@ -129,14 +157,14 @@ def test_sweep_operand_byte_count(gpu_lib, n):
     gpu_lib.signtri_profile_reset()
     gpu_lib.signtri_profile_enable(True)
     try:
-        assert gpu_lib.sign_tri(n, Tt.data_ptr(), n, Ut.data_ptr(), n, gpu_lib.Variant.PH_MIXED_TF32, h) == 0
+        assert gpu_lib.sign_tri(n, Tt.data_ptr(), n, Ut.data_ptr(), n, gpu_lib.Variant[variant], h) == 0
         torch.cuda.synchronize()
         got = gpu_lib.signtri_profile_read_bytes(gpu_lib.signtri.KC_BLOCK_SUMS_TC)
         flops = gpu_lib.signtri_profile_read_flops(gpu_lib.signtri.KC_BLOCK_SUMS_TC)
     finally:
         gpu_lib.signtri_profile_enable(False)
     info = gpu_lib.signtri_get_info()
-    assert info.variant == gpu_lib.Variant.PH_MIXED_TF32 and info.refine_steps == 1, info.as_dict()
+    assert info.variant == gpu_lib.Variant[variant] and info.refine_steps == 1, info.as_dict()
     nb = (n + 63) // 64
     lead = lambda d: d >= 3 and d % 2 == 1 and d + 1 < nb
     follow = lambda d: d >= 4 and d % 2 == 0 and lead(d - 1)
@@ -148,9 +176,9 @@ def test_sweep_operand_byte_count(gpu_lib, n):
         else:
             units += 4 * kb + (2 * (nb - d - 1) * (d - 2) if lead(d) else 0)
         units += 6 * kb
-    assert got == units * 3 * 64 * 64 * 2, (got, units)
-    # tensor work: 6 slice pairs x 2*64^3 per tile K-block and used quadrant (3 in the
+    assert got == units * slices * 64 * 64 * 2, (got, units)
+    # tensor work: slice pairs x 2*64^3 per tile K-block and used quadrant (3 in the
     # initial sweep, 2 in each correction launch)
     kb = sum((nb - d) * (d + 1) for d in range(1, nb))
-    assert flops == pytest.approx(6 * 2 * 64 ** 3 * kb * (3 + 2 + 2), rel=1e-12)
+    assert flops == pytest.approx(pairs * 2 * 64 ** 3 * kb * (3 + 2 + 2), rel=1e-12)
     assert gpu_lib.signtri_profile_read_bytes(gpu_lib.signtri.KC_RESIDUAL) == 0

@@ -19,7 +19,7 @@ def relerr(A, B):
 
 
 @pytest.mark.parametrize("n,n_neg", [(50, None), (200, None), (400, None), (400, 3), (657, None)])
-@pytest.mark.parametrize("variant", ["PH_FP64", "PS_FP64", "AUTO", "PH_MIXED_TF32"])
+@pytest.mark.parametrize("variant", ["PH_FP64", "PS_FP64", "AUTO", "PH_MIXED_TF32", "PH_MIXED_FP16"])
 def test_schur_workload(gpu_lib, oracle_mod, n, n_neg, variant):
     import torch
     T = make_T_schur(n, seed=n, n_neg=n_neg)
