@@ -205,6 +205,12 @@ def measured_peaks():
         return {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0}, "fallback"
 
 
+def h2d_bytes(n, panel=128):
+    """Bytes sign_tri_host copies to the device: T's upper triangle by column
+    panels of `panel` columns, each from row 0 to its last column."""
+    return sum(8 * min(panel, n - j0) * min(n, j0 + panel) for j0 in range(0, n, panel))
+
+
 def src_sha(rel):
     with open(os.path.join(ROOT, rel), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()
@@ -234,6 +240,7 @@ def run_batched(args):
     ptrT, ptrU = [t.data_ptr() for t in dT], [u.data_ptr() for u in dU]
     assert st.signtri_autotune(2048, h) == 0
     table = st.signtri_get_cutoff_table()
+    vtable = st.signtri_get_variant_table()
     variant = st.Variant[args.variant] if args.variant in ("AUTO", "PH_FP64") else st.Variant.AUTO
 
     def step():
@@ -263,6 +270,22 @@ def run_batched(args):
         launches += cnt
         if cnt:
             per_class[st.signtri_kernel_class_name(c)] = {"launches": cnt, "device_ms": dms}
+    # a check that needs no oracle, on every problem: with random +-1 probes
+    # z, ||U (U z) - z|| / ||z|| and ||U (T z) - T (U z)|| / (||T|| ||U|| ||z||)
+    # on the device (U^2 = I and TU = UT hold for sign(T) exactly)
+    dev = dT[0].device if dT else torch.device("cuda")
+    gen = torch.Generator(device=dev).manual_seed(7)
+    inv_worst = com_worst = 0.0
+    for t, u in zip(dT, dU):
+        # the tensors hold M^T (column-major storage): M z = (M^T)^T z
+        z = torch.randint(0, 2, (t.shape[0], 4), generator=gen, device=dev, dtype=torch.float64) * 2 - 1
+        Ut, Tt_ = u.T, t.T
+        inv = torch.linalg.norm(Ut @ (Ut @ z) - z) / torch.linalg.norm(z)
+        com = torch.linalg.norm(Ut @ (Tt_ @ z) - Tt_ @ (Ut @ z)) / (
+            torch.linalg.norm(t) * torch.linalg.norm(u) * torch.linalg.norm(z))
+        inv_worst = max(inv_worst, float(inv))
+        com_worst = max(com_worst, float(com))
+    hits, builds = st.signtri_batched_cache_stats()
     line = {
         "metric": "batched sign(T): useful GFLOP/s over %d problems" % len(Ts), "value": useful / (ms * 1e-3) / 1e9,
         "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -270,8 +293,14 @@ def run_batched(args):
         "config": {"workload": "batched: %d problems, n log-uniform [32, 2048], p ~ U[0,1], random order, seed 0"
                                % len(Ts), "sum_n2": int(sum(n * n for n in ns)), "useful_flops": useful,
                    "variant": variant.name, "cutoff_table": {str(1 << k): table[k] for k in range(5, 12)},
+                   "variant_table": {str(1 << k): (st.Variant(vtable[k]).name if vtable[k] else "batched")
+                                     for k in range(5, 12)},
                    "host_generation_s": gen_s},
         "gpu_launches": launches, "kernel_time_ms": per_class, "clocks": clk,
+        "probe_residuals": {"involution_max": inv_worst, "commutation_max": com_worst,
+                            "what": "max over problems of ||U(Uz)-z||/||z|| and ||U(Tz)-T(Uz)||/(||T|| ||U|| ||z||), "
+                                    "4 random +-1 probes each, float64 on the device"},
+        "graph_cache": {"hits": hits, "builds": builds},
     }
     if not args.no_cpu_baseline:
         # CPU baseline on a bounded sample (the largest problem and 20 more):
@@ -390,90 +419,89 @@ def main():
     useful_all = reduce_over_ranks(dist, useful, "sum", "cuda")
     value = useful_all / (ms_step_max * 1e-3) / 1e9
 
-    # roofline of the dominant kernel class
-    dom = max(per_class.items(), key=lambda kv: kv[1]["device_ms"])[0] if per_class else None
-    roof = None
-    if dom == "block_sums_f64":
-        b = info.cutoff
-        efficient = info.variant == st.Variant.PH_FP64_EFFICIENT
-        flops_step = block_sum_flops_efficient(n, b, signs) if efficient else block_sum_flops(n, b)
-        launches_dom = per_class[dom]["launches"]
-        per_launch = flops_step * args.steps / launches_dom
-        avg_ms = per_class[dom]["device_ms"] / launches_dom
-        ach = per_launch / (avg_ms * 1e-3) / 1e12
-        peak = fp64_peak / 1e3
-        sha = src_sha("paper_1607_06303_gb300/csrc/ph_fp64.cu")
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": TRAFFIC.get(("block_sums_f64", sha)),
-                "kernel": ("ph_gemm_split_kernel (float64 DFMA, one sum per entry)" if efficient
-                           else "ph_gemm_kernel (float64 DFMA block sums)"),
-                "peak_source": "float64 FMA issue rate measured live by signtri_probe_fp64_peak (no FP64 entry "
-                               "in MEASURED_PEAKS.json)",
-                "share_of_step": per_class[dom]["device_ms"] / ms_total}
-    elif dom == "block_sums_tc":
-        # the sweeps' block sums against the tensor roof on the method's own
-        # work: the initial sweep's useful flops (the oracle's count) and, per
-        # refinement step, one sum per entry of the correction (4 flops per
-        # (i, k, j) term of X^E = ET - TE or Y^E = U0 E + E U0: 4 C(n, 3)).
-        # Beside it: the executed tensor rate (every slice pair and quadrant
-        # issued) and the operand bytes against the copy bandwidth.
-        peaks, src = measured_peaks()
-        peak_t = float(peaks.get("bf16_tflops_sustained", 1700.0))
-        peak_b = float(peaks.get("hbm_gbs", 6800.0))
-        launches_dom = per_class[dom]["launches"]
-        bytes_all = st.signtri_profile_read_bytes(st.signtri.KC_BLOCK_SUMS_TC)
-        flops_all = st.signtri_profile_read_flops(st.signtri.KC_BLOCK_SUMS_TC)
-        avg_ms = per_class[dom]["device_ms"] / launches_dom
-        method_step = useful + 4.0 * math.comb(n, 3) * max(info.refine_steps, 0)
-        per_launch = method_step * args.steps / launches_dom
-        ach = per_launch / (avg_ms * 1e-3) / 1e12
-        bytes_launch = bytes_all / launches_dom
-        ach_b = bytes_launch / (avg_ms * 1e-3) / 1e9
-        sha = src_sha("paper_1607_06303_gb300/csrc/tc_gemm.cu")
-        traffic = TRAFFIC.get((dom, sha))
-        fp16 = variant == st.Variant.PH_MIXED_FP16
-        roof = {"bound": "tensor", "achieved": ach, "peak": peak_t, "unit": "TFLOP/s", "frac": ach / peak_t,
-                "traffic": None if traffic is None else traffic * bytes_launch,
-                "kernel": "tc_blocksum_kernel (tcgen05 %s, sweep block sums, blocked slice layout)"
-                          % ("fp16, two-term split" if fp16 else "bf16 split"),
-                "algorithmic_flops_per_launch": per_launch,
-                "peak_source": "bf16_tflops_sustained of %s (fp16 runs at the bf16 rate; kernel timed inside "
-                               "a long step)" % src,
-                "executed_tflops": flops_all / launches_dom / (avg_ms * 1e-3) / 1e12,
-                "executed_frac": flops_all / launches_dom / (avg_ms * 1e-3) / 1e12 / peak_t,
-                "hbm_view": {"operand_bytes_per_launch": bytes_launch, "achieved_gbs": ach_b, "peak_gbs": peak_b,
-                             "frac": ach_b / peak_b, "peak_source": "hbm_gbs of %s (copy bandwidth)" % src},
-                "share_of_step": per_class[dom]["device_ms"] / ms_total}
-    elif dom == "residual":
-        peaks, src = measured_peaks()
-        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
-        launches_dom = per_class[dom]["launches"]
-        flops_all = st.signtri_profile_read_flops(st.signtri.KC_RESIDUAL)
-        per_launch = flops_all / launches_dom
-        avg_ms = per_class[dom]["device_ms"] / launches_dom
-        ach = per_launch / (avg_ms * 1e-3) / 1e12
-        sha = src_sha("paper_1607_06303_gb300/csrc/tc_gemm.cu")
-        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": TRAFFIC.get((dom, sha)),
-                "kernel": "tc_blocksum_kernel (tcgen05 bf16, emulated-float64 residual products)",
-                "algorithmic_flops_per_launch": per_launch,
-                "peak_source": "bf16_tflops_sustained of %s (kernel timed inside a long step)" % src,
-                "share_of_step": per_class[dom]["device_ms"] / ms_total}
-
-    # the residual products (second class of the mixed step) against the tensor roof
-    roof2 = None
-    if "residual" in per_class and dom != "residual":
-        peaks, src = measured_peaks()
-        fl = st.signtri_profile_read_flops(st.signtri.KC_RESIDUAL)
-        ms_r = per_class["residual"]["device_ms"]
-        if fl > 0 and ms_r > 0:
+    # roofline of the dominant kernel class, and of the runner-up among the
+    # tensor-core classes (the mixed step's sweeps and residual products are
+    # close in time)
+    def class_roofline(cls):
+        if cls == "block_sums_f64":
+            b = info.cutoff
+            efficient = info.variant == st.Variant.PH_FP64_EFFICIENT
+            flops_step = block_sum_flops_efficient(n, b, signs) if efficient else block_sum_flops(n, b)
+            launches_c = per_class[cls]["launches"]
+            per_launch = flops_step * args.steps / launches_c
+            avg_ms = per_class[cls]["device_ms"] / launches_c
+            ach = per_launch / (avg_ms * 1e-3) / 1e12
+            peak = fp64_peak / 1e3
+            sha = src_sha("paper_1607_06303_gb300/csrc/ph_fp64.cu")
+            return {"class": cls, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": TRAFFIC.get(("block_sums_f64", sha)),
+                    "kernel": ("ph_gemm_split_kernel (float64 DFMA, one sum per entry)" if efficient
+                               else "ph_gemm_kernel (float64 DFMA block sums)"),
+                    "peak_source": "float64 FMA issue rate measured live by signtri_probe_fp64_peak (no FP64 "
+                                   "entry in MEASURED_PEAKS.json)",
+                    "share_of_step": per_class[cls]["device_ms"] / ms_total}
+        if cls == "block_sums_tc":
+            # the sweeps' block sums against the tensor roof on the method's
+            # own work: the initial sweep's useful flops (the oracle's count)
+            # and, per refinement step, one sum per entry of the correction (4
+            # flops per (i, k, j) term of X^E = ET - TE or Y^E = U0 E + E U0:
+            # 4 C(n, 3)).  Beside it: the executed tensor rate (every slice
+            # pair and quadrant issued) and the operand bytes against the copy
+            # bandwidth.
+            peaks, src = measured_peaks()
             peak_t = float(peaks.get("bf16_tflops_sustained", 1700.0))
-            ach_t = fl / (ms_r * 1e-3) / 1e12
-            roof2 = {"class": "residual", "bound": "tensor", "achieved": ach_t, "peak": peak_t, "unit": "TFLOP/s",
-                     "frac": ach_t / peak_t,
-                     "kernel": "tc_pair2_kernel / tc_blocksum_kernel (emulated-float64 residual and probe products)",
-                     "peak_source": "bf16_tflops_sustained of %s" % src,
-                     "share_of_step": ms_r / ms_total}
+            peak_b = float(peaks.get("hbm_gbs", 6800.0))
+            launches_c = per_class[cls]["launches"]
+            bytes_all = st.signtri_profile_read_bytes(st.signtri.KC_BLOCK_SUMS_TC)
+            flops_all = st.signtri_profile_read_flops(st.signtri.KC_BLOCK_SUMS_TC)
+            avg_ms = per_class[cls]["device_ms"] / launches_c
+            method_step = useful + 4.0 * math.comb(n, 3) * max(info.refine_steps, 0)
+            per_launch = method_step * args.steps / launches_c
+            ach = per_launch / (avg_ms * 1e-3) / 1e12
+            bytes_launch = bytes_all / launches_c
+            ach_b = bytes_launch / (avg_ms * 1e-3) / 1e9
+            sha = src_sha("paper_1607_06303_gb300/csrc/tc_gemm.cu")
+            traffic = TRAFFIC.get((cls, sha))
+            fp16 = variant == st.Variant.PH_MIXED_FP16
+            return {"class": cls, "bound": "tensor", "achieved": ach, "peak": peak_t, "unit": "TFLOP/s",
+                    "frac": ach / peak_t, "traffic": None if traffic is None else traffic * bytes_launch,
+                    "kernel": "tc_blocksum_kernel (tcgen05 %s, sweep block sums, blocked slice layout)"
+                              % ("fp16, two-term split" if fp16 else "bf16 split"),
+                    "algorithmic_flops_per_launch": per_launch,
+                    "peak_source": "bf16_tflops_sustained of %s (fp16 runs at the bf16 rate; kernel timed "
+                                   "inside a long step)" % src,
+                    "executed_tflops": flops_all / launches_c / (avg_ms * 1e-3) / 1e12,
+                    "executed_frac": flops_all / launches_c / (avg_ms * 1e-3) / 1e12 / peak_t,
+                    "hbm_view": {"operand_bytes_per_launch": bytes_launch, "achieved_gbs": ach_b,
+                                 "peak_gbs": peak_b, "frac": ach_b / peak_b,
+                                 "peak_source": "hbm_gbs of %s (copy bandwidth)" % src},
+                    "share_of_step": per_class[cls]["device_ms"] / ms_total}
+        if cls == "residual":
+            # emulated-float64 residual and probe products: every slice pair
+            # product is needed (exact integer slices), so the executed
+            # products are the algorithmic work of the emulation
+            peaks, src = measured_peaks()
+            peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+            launches_c = per_class[cls]["launches"]
+            flops_all = st.signtri_profile_read_flops(st.signtri.KC_RESIDUAL)
+            per_launch = flops_all / launches_c
+            avg_ms = per_class[cls]["device_ms"] / launches_c
+            ach = per_launch / (avg_ms * 1e-3) / 1e12
+            sha = src_sha("paper_1607_06303_gb300/csrc/tc_gemm.cu")
+            return {"class": cls, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": TRAFFIC.get((cls, sha)),
+                    "kernel": "tc_pair2_kernel / tc_blocksum_kernel (tcgen05 bf16, emulated-float64 residual "
+                              "and probe products)",
+                    "algorithmic_flops_per_launch": per_launch,
+                    "peak_source": "bf16_tflops_sustained of %s (kernel timed inside a long step)" % src,
+                    "share_of_step": per_class[cls]["device_ms"] / ms_total}
+        return None
+
+    ranked = sorted(per_class, key=lambda c: -per_class[c]["device_ms"])
+    dom = ranked[0] if ranked else None
+    roof = class_roofline(dom) if dom else None
+    second = next((c for c in ranked[1:] if c in ("block_sums_tc", "residual")), None)
+    roof2 = class_roofline(second) if second else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -517,7 +545,7 @@ def main():
             reps.append((time.perf_counter() - t0) / max(args.steps, 1))
         e2e_s = reduce_over_ranks(dist, statistics.median(reps), "max", "cuda")
         line["e2e"] = {"value": useful_all / e2e_s / 1e9, "unit": UNIT,
-                       "h2d_bytes_per_step": Th.numel() * 8, "d2h_bytes_per_step": Uh.numel() * 8,
+                       "h2d_bytes_per_step": h2d_bytes(n), "d2h_bytes_per_step": Uh.numel() * 8,
                        "seconds_per_solve": e2e_s, "repetitions_s": reps}
         del Th, Uh
 

@@ -179,8 +179,9 @@ signtri_status sign_tri(int n, const double *T, int ldt, double *U, int ldu,
                         signtri_variant v, void *stream);
 
 /* Same as sign_tri, with T_host and U_host in host memory (pinned memory
-   gives full copy bandwidth).  Copies T to the device, computes, copies U
-   back, and returns after U_host is written (synchronous). */
+   gives full copy bandwidth).  Copies T's upper triangle to the device (by
+   column panels, about n^2/2 doubles), computes, copies all of U back, and
+   returns after U_host is written (synchronous). */
 signtri_status sign_tri_host(int n, const double *T_host, int ldt, double *U_host, int ldu,
                              signtri_variant v, void *stream);
 
@@ -192,8 +193,11 @@ signtri_status sign_tri_host(int n, const double *T_host, int ldt, double *U_hos
    Parlett-Sylvester when the diagonal is already grouped by sign, i.e. no
    swaps, else Parlett-Higham, which shares its launches across the batch).  All
    Parlett-Higham float64 problems run together as one CUDA graph of
-   level-synchronous launches (leaf size per problem from the cutoff table);
-   the others run one after another.  Returns after all U[m] are written.
+   level-synchronous launches (leaf size per problem from the cutoff table;
+   the graph is built once per group shape and relaunched by later calls, see
+   signtri_batched_cache_stats); the others run one after another (under
+   AUTO also the size buckets the variant table sends to a mixed variant).
+   Returns after all U[m] are written.
    The return value reports failures of the call itself. */
 signtri_status sign_tri_batched(int count, const int *n, const double *const *T, const int *ldt,
                                 double *const *U, const int *ldu, signtri_variant v, int *info,
@@ -204,11 +208,27 @@ signtri_status sign_tri_batched(int count, const int *n, const double *const *T,
 signtri_status signtri_set_cutoff_table(const int *b, int len);
 signtri_status signtri_get_cutoff_table(int *b, int len);
 
-/* Autotuner: for n = 32, 64, ..., up to n_max (<= 32768), time the float64
-   Parlett-Higham path AUTO takes (the arithmetic-efficient form) on a
-   synthetic problem with each leaf size and store the fastest in the cutoff
-   table.  Allocates two n_max x n_max matrices. */
+/* Autotuner of the batched path (the paper's closing suggestion of
+   choosing by auto-tuning): for each size bucket n = 32, 64, ..., up to
+   n_max (<= 32768), time sign_tri_batched's float64 Parlett-Higham on a
+   synthetic batch of min(1024, 2^27 / n^2) problems of order n with each
+   leaf size 16, 32, 64, store the fastest in the cutoff table, and for n >=
+   1024 also time SIGNTRI_PH_MIXED_FP16 on one problem: when it beats the
+   batch's time per problem, the variant table sends that bucket's problems
+   there under AUTO.  Allocates an n_max x n_max T and 2^27 doubles of U. */
 signtri_status signtri_autotune(int n_max, void *stream);
+/* Variant table of the batched path under AUTO: v[k] (0 = batched
+   Parlett-Higham, or Parlett-Sylvester when no swaps are needed; else a
+   variant other than AUTO, run problem by problem) for problems with
+   floor(log2 n) == k, k < len <= 32. */
+signtri_status signtri_get_variant_table(int *v, int len);
+signtri_status signtri_set_variant_table(const int *v, int len);
+/* The batched path keeps, per device and leaf size, the task tables and the
+   instantiated CUDA graph of the last group of problems it ran, and relaunches
+   that graph when a call brings a group of the same shape (member sizes and
+   order, descriptor and scratch addresses).  hits: launches of a kept graph;
+   builds: graphs built, since the library was loaded. */
+signtri_status signtri_batched_cache_stats(long long *hits, long long *builds);
 
 /* Inertia scan alone (Section 3): counts of positive and negative diagonal
    entries and the number of adjacent swaps that group positives first.

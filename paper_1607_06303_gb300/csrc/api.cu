@@ -41,6 +41,9 @@ DeviceState g_dev[kMaxDevices];
 int g_cutoff = kDefaultCutoff;
 // leaf size per size bucket floor(log2 n) for the batched path; 0 = g_cutoff
 int g_cutoff_table[32] = {};
+// variant AUTO runs per size bucket in the batched path; 0 = the batched
+// Parlett-Higham (or Parlett-Sylvester when no swaps are needed)
+int g_variant_table[32] = {};
 // flops/s used by the AUTO choice (float64 block products; Givens rounds)
 constexpr double kDefaultGemmRate = 1.0e12;
 constexpr double kDefaultGivensRate = 0.35e12;
@@ -277,10 +280,16 @@ void reset_info(int n)
     g_info.variant = -1;
 }
 
-int cutoff_for(int n)
+int size_bucket(int n)
 {
     int k = 0;
     while ((2 << k) <= n && k < 31) k++;
+    return k;
+}
+
+int cutoff_for(int n)
+{
+    const int k = size_bucket(n);
     return g_cutoff_table[k] ? g_cutoff_table[k] : g_cutoff;
 }
 
@@ -424,8 +433,12 @@ signtri_status sign_tri_batched(int count, const int *n, const double *const *T,
         signtri_variant run = v;
         // in a batch Parlett-Higham shares its launches with every other
         // problem, so Parlett-Sylvester (run on its own) is taken only when
-        // no swaps are needed
-        if (v == SIGNTRI_AUTO) run = (r.swaps == 0) ? SIGNTRI_PS_FP64 : SIGNTRI_PH_FP64_EFFICIENT;
+        // no swaps are needed; a size bucket the autotuner found faster on
+        // its own (a mixed variant) runs that way
+        if (v == SIGNTRI_AUTO) {
+            const int tv = g_variant_table[size_bucket(sizes[k])];
+            run = tv ? (signtri_variant)tv : (r.swaps == 0) ? SIGNTRI_PS_FP64 : SIGNTRI_PH_FP64_EFFICIENT;
+        }
         if (run == SIGNTRI_PH_FP64 || run == SIGNTRI_PH_FP64_EFFICIENT) {
             ph_bs[k] = bs[k];
             which.push_back(k);
@@ -478,45 +491,101 @@ signtri_status signtri_autotune(int n_max, void *stream)
     signtri_status rs = current_state(&s);
     if (rs != SIGNTRI_OK) return rs;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int saved = g_cutoff;
+    // per size bucket n = 2^k: a batch of c = 2^27 / n^2 problems (at most
+    // 1024) sharing one synthetic T, each with its own U
+    const size_t elems = (size_t)1 << 27;
     double *T = nullptr, *U = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaMalloc(&T, (size_t)n_max * n_max * 8) != cudaSuccess ||
-        cudaMalloc(&U, (size_t)n_max * n_max * 8) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaMalloc(&U, std::max(elems, (size_t)n_max * n_max) * 8) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
         cudaEventCreate(&e1) != cudaSuccess)
         rs = SIGNTRI_ERR_CUDA;
+    auto timed = [&](auto &&run, float &ms) -> signtri_status {
+        // the second of two runs (the first builds what later calls reuse)
+        signtri_status r2 = SIGNTRI_OK;
+        for (int rep = 0; rep < 2 && r2 == SIGNTRI_OK; rep++) {
+            cudaEventRecord(e0, st);
+            r2 = run();
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) r2 = SIGNTRI_ERR_CUDA;
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        return r2;
+    };
     for (int k = 5; rs == SIGNTRI_OK && (1 << k) <= n_max; k++) {
         const int nn = 1 << k;
+        const int c = (int)std::max<size_t>(1, std::min<size_t>(1024, elems / ((size_t)nn * nn)));
         synth_kernel<<<nn, 256, 0, st>>>(nn, T, 0x5eed0000ull + k);
         if (cudaGetLastError() != cudaSuccess) { rs = SIGNTRI_ERR_CUDA; break; }
-        ScanResult r{};
-        rs = launch_inertia_scan(nn, T, nn, s->scan_dev, st);
-        if (rs != SIGNTRI_OK) break;
-        SGT_CUDA_TRY(cudaMemcpyAsync(&r, s->scan_dev, sizeof(ScanResult), cudaMemcpyDeviceToHost, st));
-        SGT_CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<BatchDesc> h(c);
+        for (int m = 0; m < c; m++) h[m] = {T, U + (size_t)m * nn * nn, nn, nn, nn, 0};
+        // leaf size: the batched path, per problem
+        size_t need = 0;
+        std::vector<int> ns(c, nn);
+        for (int b : {16, 32, 64}) need = std::max(need, batched_workspace_bytes(c, ns.data(), b));
+        Arena ws;
+        if ((rs = get_workspace(*s, need + c * sizeof(BatchDesc) + 512, ws)) != SIGNTRI_OK) break;
+        auto *d_h = static_cast<BatchDesc *>(ws.take(c * sizeof(BatchDesc)));
+        SGT_CUDA_TRY(cudaMemcpyAsync(d_h, h.data(), c * sizeof(BatchDesc), cudaMemcpyHostToDevice, st));
         float best = 1e30f;
-        int best_b = saved;
+        int best_b = 16;
         for (int b : {16, 32, 64}) {
-            g_cutoff = b;
+            std::vector<int> bs(c, b);
             float ms = 0.f;
-            for (int rep = 0; rep < 2 && rs == SIGNTRI_OK; rep++) {
-                cudaEventRecord(e0, st);
-                rs = run_variant(nn, T, nn, U, nn, SIGNTRI_PH_FP64_EFFICIENT, r, st, *s);
-                cudaEventRecord(e1, st);
-                if (cudaEventSynchronize(e1) != cudaSuccess) rs = SIGNTRI_ERR_CUDA;
-                cudaEventElapsedTime(&ms, e0, e1);
-            }
+            Arena sub = ws;
+            rs = timed([&]() { return batched_ph_run(c, h.data(), d_h, bs.data(), true, sub, st); }, ms);
             if (rs != SIGNTRI_OK) break;
             if (ms < best) { best = ms; best_b = b; }
         }
+        if (rs != SIGNTRI_OK) break;
         g_cutoff_table[k] = best_b;
+        // variant: the mixed fp16 form on its own, against the batched
+        // float64 time per problem (only where one problem is large enough
+        // for the tensor-core sweeps to pay)
+        g_variant_table[k] = 0;
+        if (nn >= 1024) {
+            ScanResult r{};
+            rs = launch_inertia_scan(nn, T, nn, s->scan_dev, st);
+            if (rs != SIGNTRI_OK) break;
+            SGT_CUDA_TRY(cudaMemcpyAsync(&r, s->scan_dev, sizeof(ScanResult), cudaMemcpyDeviceToHost, st));
+            SGT_CUDA_TRY(cudaStreamSynchronize(st));
+            float ms = 0.f;
+            rs = timed([&]() { return run_variant(nn, T, nn, U, nn, SIGNTRI_PH_MIXED_FP16, r, st, *s); }, ms);
+            if (rs != SIGNTRI_OK) break;
+            if (ms < best / c) g_variant_table[k] = SIGNTRI_PH_MIXED_FP16;
+        }
     }
-    g_cutoff = saved;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(T);
     cudaFree(U);
     return rs;
+}
+
+signtri_status signtri_get_variant_table(int *v, int len)
+{
+    if (len < 0 || len > 32 || (len > 0 && !v)) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int k = 0; k < len; k++) v[k] = g_variant_table[k];
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_set_variant_table(const int *v, int len)
+{
+    if (len < 0 || len > 32 || (len > 0 && !v)) return SIGNTRI_ERR_BAD_ARG;
+    for (int k = 0; k < len; k++)
+        if (v[k] != 0 && !(valid_variant(v[k]) && v[k] != SIGNTRI_AUTO)) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int k = 0; k < 32; k++) g_variant_table[k] = k < len ? v[k] : 0;
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_batched_cache_stats(long long *hits, long long *builds)
+{
+    if (!hits || !builds) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    batched_cache_stats(hits, builds);
+    return SIGNTRI_OK;
 }
 
 signtri_status signtri_selftest_wait(int arrive, long long limit_cycles, void *stream)
@@ -683,8 +752,15 @@ signtri_status sign_tri_host(int n, const double *T_host, int ldt, double *U_hos
         }
         s->stage_elems = elems;
     }
-    SGT_CUDA_TRY(cudaMemcpy2DAsync(s->stage_T, (size_t)n * sizeof(double), T_host, (size_t)ldt * sizeof(double),
-                                   (size_t)n * sizeof(double), n, cudaMemcpyHostToDevice, st));
+    // only T's upper triangle is read: copy it by column panels, each from
+    // row 0 to its last column's diagonal (about half of T's bytes)
+    constexpr int kPanel = 128;
+    for (int j0 = 0; j0 < n; j0 += kPanel) {
+        const int cols = std::min(kPanel, n - j0), rows = std::min(n, j0 + kPanel);
+        SGT_CUDA_TRY(cudaMemcpy2DAsync(s->stage_T + (size_t)j0 * n, (size_t)n * sizeof(double),
+                                       T_host + (size_t)j0 * ldt, (size_t)ldt * sizeof(double),
+                                       (size_t)rows * sizeof(double), cols, cudaMemcpyHostToDevice, st));
+    }
     rs = sign_tri_locked(n, s->stage_T, n, s->stage_U, n, v, st, *s);
     if (rs != SIGNTRI_OK) {
         // no copy from the caller's T_host may still be in flight on return

@@ -159,6 +159,9 @@ signtri_status emulated_gemm_run(int m, int n, int k, const double *A, int lda, 
 size_t batched_workspace_bytes(int count, const int *n, int cutoff_for_all);
 signtri_status batched_ph_run(int count, const BatchDesc *h_mats, const BatchDesc *d_mats, const int *bs,
                               bool split, Arena &ws, cudaStream_t st);
+// Graph-cache counters of the batched path: launches of a cached graph, and
+// graphs built (tables, capture, instantiation), over all devices.
+void batched_cache_stats(long long *hits, long long *builds);
 
 // Bounded-wait self-test (tc_gemm.cu)
 signtri_status wait_selftest(int arrive, long long limit, int *d_err, cudaStream_t st);

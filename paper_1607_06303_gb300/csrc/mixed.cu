@@ -680,39 +680,51 @@ __global__ void blocked_split_kernel(int n, const double *__restrict__ M, int ld
     }
 }
 
-// Largest |entry| of the strictly upper part of the n x n matrix M (all of it,
-// or only its 64 x 64 diagonal blocks), as the bits of a non-negative float
-// (ordered like the values) max-ed into *out.
-__global__ void absmax_upper_kernel(int n, const double *__restrict__ M, int ldm, int diag_only,
-                                    unsigned *__restrict__ out)
+// Largest |entry| of the strictly upper parts of the 64 x 64 diagonal blocks
+// of the n x n matrix M, as the bits of a non-negative float (ordered like
+// the values) max-ed into *out.
+__global__ void absmax_diag_blocks_kernel(int n, const double *__restrict__ M, int ldm, unsigned *__restrict__ out)
 {
     float m = 0.f;
-    const long long total = (long long)n * n;
+    const long long total = (long long)((n + MB - 1) / MB) * MB * MB;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e % n), j = (int)(e / n);
-        if (i < j && (!diag_only || i / MB == j / MB)) m = fmaxf(m, fabsf((float)SGT_AT(M, ldm, i, j)));
+        const int b = (int)(e / (MB * MB)), w = (int)(e % (MB * MB));
+        const int i = b * MB + w % MB, j = b * MB + w / MB;
+        if (i < j && j < n) m = fmaxf(m, fabsf((float)SGT_AT(M, ldm, i, j)));
     }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// Largest of `count` non-negative float64 values held as their bits (the
+// per-row maxima the exact slices' scales come from), as float bits max-ed
+// into *out.
+__global__ void max_of_maxima_kernel(int count, const unsigned long long *__restrict__ bits, unsigned *__restrict__ out)
+{
+    float m = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        m = fmaxf(m, (float)__longlong_as_double((long long)bits[i]));
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
 // Largest first-order correction term |e_ij| ~ |Rc_ij| / |t_ii - t_jj|
 // (signs differ) or |Rs_ij| / 2 (signs agree) over the strictly upper
-// entries, max-ed into *out as float bits (see absmax_upper_kernel).
-__global__ void corr_magnitude_kernel(int n, const double *__restrict__ T, int ldt, const double *__restrict__ Rc,
+// entries, max-ed into *out as float bits (see absmax_diag_blocks_kernel).
+// D: t_ii in fp32.  One column per CTA step: coalesced reads of R and D.
+__global__ void corr_magnitude_kernel(int n, const float *__restrict__ D, const double *__restrict__ Rc,
                                       const double *__restrict__ Rs, int ldr, unsigned *__restrict__ out)
 {
     float m = 0.f;
-    const long long total = (long long)n * n;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e % n), j = (int)(e / n);
-        if (i >= j) continue;
-        const double ti = SGT_AT(T, ldt, i, i), tj = SGT_AT(T, ldt, j, j);
-        const double v = ((ti > 0.0) != (tj > 0.0)) ? fabs(SGT_AT(Rc, ldr, i, j)) / fabs(ti - tj)
-                                                   : 0.5 * fabs(SGT_AT(Rs, ldr, i, j));
-        m = fmaxf(m, (float)v);
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        const float tj = D[j];
+        for (int i = threadIdx.x; i < j; i += blockDim.x) {
+            const float ti = D[i];
+            const float v = ((ti > 0.f) != (tj > 0.f)) ? (float)fabs(SGT_AT(Rc, ldr, i, j)) / fabsf(ti - tj)
+                                                       : 0.5f * (float)fabs(SGT_AT(Rs, ldr, i, j));
+            m = fmaxf(m, v);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
@@ -829,7 +841,7 @@ struct MixedCtx {
     bool f16;
     float sT, sU, sE;
     float *invT, *invU, *invE;
-    unsigned *amax;             // scratch of absmax_upper_kernel
+    unsigned *amax;             // float bits of a maximum the fp16 scales come from
     cudaStream_t st;
     int *d_err;
     Schedule sc, sc2;           // initial sweep; correction (two launches side by side)
@@ -933,21 +945,38 @@ float pow2_scale(float m, int target)
     return std::ldexp(1.f, std::max(-120, std::min(120, target - (e - 1))));
 }
 
-// Largest |entry| of the strictly upper part of M (diag_only: of its 64 x 64
-// diagonal blocks) into m; the host waits for it.
-signtri_status upper_absmax(MixedCtx &c, const double *M, int ldm, int diag_only, float &m)
+// Reads back the float max-ed into c.amax (the host waits for it).
+signtri_status read_amax(MixedCtx &c, float &m)
 {
-    SGT_CUDA_TRY(cudaMemsetAsync(c.amax, 0, sizeof(unsigned), c.st));
-    {
-        ProfScope ps(SIGNTRI_KC_CONVERT, c.st);
-        absmax_upper_kernel<<<608, 256, 0, c.st>>>(c.n, M, ldm, diag_only, c.amax);
-        SGT_LAUNCH_CHECK();
-    }
     unsigned bits = 0;
     SGT_CUDA_TRY(cudaMemcpyAsync(&bits, c.amax, sizeof(unsigned), cudaMemcpyDeviceToHost, c.st));
     SGT_CUDA_TRY(cudaStreamSynchronize(c.st));
     std::memcpy(&m, &bits, sizeof(float));
     return SIGNTRI_OK;
+}
+
+// Largest |entry| of the strictly upper parts of M's diagonal blocks into m.
+signtri_status diag_blocks_absmax(MixedCtx &c, const double *M, int ldm, float &m)
+{
+    SGT_CUDA_TRY(cudaMemsetAsync(c.amax, 0, sizeof(unsigned), c.st));
+    {
+        ProfScope ps(SIGNTRI_KC_CONVERT, c.st);
+        absmax_diag_blocks_kernel<<<152, 256, 0, c.st>>>(c.n, M, ldm, c.amax);
+        SGT_LAUNCH_CHECK();
+    }
+    return read_amax(c, m);
+}
+
+// Largest of the per-row maxima in c.tmpmax (np + 64 entries) into m.
+signtri_status row_maxima_max(MixedCtx &c, float &m)
+{
+    SGT_CUDA_TRY(cudaMemsetAsync(c.amax, 0, sizeof(unsigned), c.st));
+    {
+        ProfScope ps(SIGNTRI_KC_CONVERT, c.st);
+        max_of_maxima_kernel<<<32, 256, 0, c.st>>>(c.np + 64, c.tmpmax, c.amax);
+        SGT_LAUNCH_CHECK();
+    }
+    return read_amax(c, m);
 }
 
 // inv[0 .. np + 64) = 1 / sigma: the engine's row / column scales of a product
@@ -1556,15 +1585,17 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
     SGT_CUDA_TRY(cudaMemsetAsync(c.Er, 0, split_elems * 2, st));
     SGT_CUDA_TRY(cudaMemsetAsync(c.Ec, 0, split_elems * 2, st));
     signtri_status rs;
+    if ((rs = gathered_slices_of(c, T, ldt, c.NTgr, c.NTgc, c.sTr, c.sTc, c.gTr, c.gTc)) != SIGNTRI_OK) return rs;
     if (c.f16) {
-        // T's largest strictly upper entry to 2^13 .. 2^14 (fp16 stops at 65504)
+        // T's largest strictly upper entry (from the row maxima the exact
+        // slices' scales were just taken from) to 2^13 .. 2^14 (fp16 stops
+        // at 65504)
         float m = 0.f;
-        if ((rs = upper_absmax(c, T, ldt, 0, m)) != SIGNTRI_OK) return rs;
+        if ((rs = row_maxima_max(c, m)) != SIGNTRI_OK) return rs;
         c.sT = m > 0.f ? pow2_scale(m, 13) : 1.f;
         if ((rs = fill_inverse(c, c.invT, c.sT)) != SIGNTRI_OK) return rs;
     }
     if ((rs = split_full(c, T, ldt, c.Tr, c.Tc, c.f16 ? c.sT : 0.f)) != SIGNTRI_OK) return rs;
-    if ((rs = gathered_slices_of(c, T, ldt, c.NTgr, c.NTgc, c.sTr, c.sTc, c.gTr, c.gTc)) != SIGNTRI_OK) return rs;
     // T's scales serve both layouts; the probe check reads only T's row
     // slices, the full residual also its column slices
     if ((rs = exact_slices_of(c, T, ldt, c.NTr, c.NTc, c.sTr, c.sTc, true, prm.verify_full != 0)) != SIGNTRI_OK)
@@ -1577,7 +1608,7 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
         // U's scale from its diagonal blocks, largest entry to 2^12 .. 2^13:
         // room for off-diagonal entries up to 8x larger
         float m = 0.f;
-        if ((rs = upper_absmax(c, U, ldu, 1, m)) != SIGNTRI_OK) return rs;
+        if ((rs = diag_blocks_absmax(c, U, ldu, m)) != SIGNTRI_OK) return rs;
         c.sU = m > 0.f ? pow2_scale(m, 12) : c.sT;
         if ((rs = fill_inverse(c, c.invU, c.sU)) != SIGNTRI_OK) return rs;
     }
@@ -1656,13 +1687,11 @@ signtri_status mixed_run(int n, const double *T, int ldt, double *U, int ldu, in
             SGT_CUDA_TRY(cudaMemsetAsync(c.amax, 0, sizeof(unsigned), st));
             {
                 ProfScope ps(SIGNTRI_KC_CONVERT, st);
-                corr_magnitude_kernel<<<608, 256, 0, st>>>(n, T, ldt, c.res_c, c.res_s, n, c.amax);
+                // c.DIAG: t_ii in fp32, from the initial sweep (same T)
+                corr_magnitude_kernel<<<1216, 256, 0, st>>>(n, c.DIAG, c.res_c, c.res_s, n, c.amax);
                 SGT_LAUNCH_CHECK();
             }
-            unsigned bits = 0;
-            SGT_CUDA_TRY(cudaMemcpyAsync(&bits, c.amax, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-            SGT_CUDA_TRY(cudaStreamSynchronize(st));
-            std::memcpy(&m, &bits, sizeof(float));
+            if ((rs = read_amax(c, m)) != SIGNTRI_OK) return rs;
             c.sE = m > 0.f ? pow2_scale(m, 10) : c.sU;
             if ((rs = fill_inverse(c, c.invE, c.sE)) != SIGNTRI_OK) return rs;
         }

@@ -99,6 +99,9 @@ _SIGNATURES = {
     "signtri_set_cutoff_table": (_I, [ctypes.POINTER(_I), _I]),
     "signtri_get_cutoff_table": (_I, [ctypes.POINTER(_I), _I]),
     "signtri_autotune": (_I, [_I, _VP]),
+    "signtri_get_variant_table": (_I, [ctypes.POINTER(_I), _I]),
+    "signtri_set_variant_table": (_I, [ctypes.POINTER(_I), _I]),
+    "signtri_batched_cache_stats": (_I, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "signtri_selftest_wait": (_I, [_I, ctypes.c_longlong, _VP]),
 }
 
@@ -198,6 +201,28 @@ def signtri_get_cutoff_table(length: int = 32):
 
 def signtri_autotune(n_max: int, stream=None) -> int:
     return load().signtri_autotune(int(n_max), stream or None)
+
+
+def signtri_set_variant_table(table) -> int:
+    arr = (_I * max(len(table), 1))(*[int(v) for v in table])
+    return load().signtri_set_variant_table(arr, len(table))
+
+
+def signtri_get_variant_table(length: int = 32):
+    arr = (_I * length)()
+    st = load().signtri_get_variant_table(arr, length)
+    if st != 0:
+        raise SignTriError(st, "signtri_get_variant_table")
+    return list(arr)
+
+
+def signtri_batched_cache_stats():
+    """(launches of a kept batch graph, graphs built) since the library was loaded."""
+    h, b = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    st = load().signtri_batched_cache_stats(ctypes.byref(h), ctypes.byref(b))
+    if st != 0:
+        raise SignTriError(st, "signtri_batched_cache_stats")
+    return h.value, b.value
 
 
 def signtri_selftest_wait(arrive: bool, limit_cycles: int, stream=None) -> int:

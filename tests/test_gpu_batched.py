@@ -78,18 +78,74 @@ def test_cutoff_table_and_autotune(gpu_lib, oracle_mod):
             for T, U in zip(Ts, Us):
                 assert relerr(U, oracle_mod.sign_tri(T)) <= TOL_FP64
         assert gpu_lib.signtri_set_cutoff_table([48]) == gpu_lib.Status.ERR_BAD_ARG
-        assert gpu_lib.signtri_autotune(512, torch.cuda.current_stream().cuda_stream) == 0
+        # the autotuner times the batched path per size bucket (leaf size) and,
+        # from n = 1024 on, the fp16 mixed form on its own (variant)
+        assert gpu_lib.signtri_autotune(1024, torch.cuda.current_stream().cuda_stream) == 0
         table = gpu_lib.signtri_get_cutoff_table()
-        assert all(table[k] in (16, 32, 64) for k in range(5, 10))
+        assert all(table[k] in (16, 32, 64) for k in range(5, 11))
+        vt = gpu_lib.signtri_get_variant_table()
+        assert all(vt[k] == 0 for k in range(5, 10))          # below 1024: never the single mixed path
+        assert vt[10] in (0, int(gpu_lib.Variant.PH_MIXED_FP16))
+        # a batch under the tuned tables
+        Ts = [make_T(n, 0.5, seed=n + 1) for n in (40, 333, 1024)]
+        st, info, Us = run_batch(gpu_lib, Ts, gpu_lib.Variant.AUTO)
+        assert st == 0 and info == [0, 0, 0]
+        for T, U in zip(Ts, Us):
+            assert relerr(U, oracle_mod.sign_tri(T)) <= 1e-12
     finally:
         gpu_lib.signtri_set_cutoff_table(old)
+        gpu_lib.signtri_set_variant_table([])
 
 
-def test_batched_mixed_variant(gpu_lib, oracle_mod):
+def test_variant_table_routes_auto(gpu_lib, oracle_mod):
+    # under AUTO, the size buckets the variant table names run through that
+    # variant one by one, the rest through the batched float64 path
+    Ts = [make_T(n, 0.5, seed=300 + n) for n in (90, 300, 600)]
+    vt = [0] * 32
+    vt[8] = int(gpu_lib.Variant.PH_MIXED_FP16)      # 256 <= n < 512
+    try:
+        assert gpu_lib.signtri_set_variant_table(vt) == 0
+        assert gpu_lib.signtri_get_variant_table()[8] == int(gpu_lib.Variant.PH_MIXED_FP16)
+        st, info, Us = run_batch(gpu_lib, Ts, gpu_lib.Variant.AUTO)
+    finally:
+        gpu_lib.signtri_set_variant_table([])
+    assert st == 0 and info == [0, 0, 0]
+    for T, U in zip(Ts, Us):
+        assert relerr(U, oracle_mod.sign_tri(T)) <= 1e-12
+    # 0 (AUTO's value) keeps a bucket on the batched path; no such variant: refused
+    assert gpu_lib.signtri_set_variant_table([0, 0]) == 0
+    assert gpu_lib.signtri_set_variant_table([77]) == gpu_lib.Status.ERR_BAD_ARG
+    assert gpu_lib.signtri_set_variant_table([-1]) == gpu_lib.Status.ERR_BAD_ARG
+    gpu_lib.signtri_set_variant_table([])
+
+
+def test_batched_graph_is_kept(gpu_lib, oracle_mod):
+    # a second call with a batch of the same shape relaunches the graph built
+    # by the first (its tables kept); a batch of another shape builds anew;
+    # every result meets the bar
+    Ts = [make_T(n, 0.4, seed=400 + n) for n in (70, 130, 257, 400)]
+    h0, b0 = gpu_lib.signtri_batched_cache_stats()
+    for rep in range(2):
+        st, info, Us = run_batch(gpu_lib, Ts, gpu_lib.Variant.PH_FP64_EFFICIENT)
+        assert st == 0 and info == [0] * len(Ts)
+        for T, U in zip(Ts, Us):
+            assert relerr(U, oracle_mod.sign_tri(T)) <= TOL_FP64
+    h1, b1 = gpu_lib.signtri_batched_cache_stats()
+    assert h1 >= h0 + 1 and b1 >= b0 + 1
+    Ts2 = Ts[:3] + [make_T(401, 0.4, seed=9)]
+    st, info, Us = run_batch(gpu_lib, Ts2, gpu_lib.Variant.PH_FP64_EFFICIENT)
+    assert st == 0 and info == [0] * len(Ts2)
+    assert relerr(Us[3], oracle_mod.sign_tri(Ts2[3])) <= TOL_FP64
+    h2, b2 = gpu_lib.signtri_batched_cache_stats()
+    assert b2 >= b1 + 1
+
+
+@pytest.mark.parametrize("variant", ["PH_MIXED_TF32", "PH_MIXED_FP16"])
+def test_batched_mixed_variant(gpu_lib, oracle_mod, variant):
     # mixed-precision problems in a batch run one after another through the
     # single-matrix path; each meets the mixed bar
     Ts = [make_T(n, 0.5, seed=200 + n) for n in (70, 200, 513)]
-    st, info, Us = run_batch(gpu_lib, Ts, gpu_lib.Variant.PH_MIXED_TF32)
+    st, info, Us = run_batch(gpu_lib, Ts, gpu_lib.Variant[variant])
     assert st == 0 and info == [0, 0, 0]
     for T, U in zip(Ts, Us):
         assert relerr(U, oracle_mod.sign_tri(T)) <= 1e-12

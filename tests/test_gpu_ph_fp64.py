@@ -123,6 +123,22 @@ def test_inertia_scan(gpu_lib):
         assert k == workload.swaps(s)
 
 
+@pytest.mark.parametrize("variant", ["PH_FP64", "PH_MIXED_FP16"])
+def test_host_entry_point_reads_upper_triangle_only(gpu_lib, oracle_mod, variant):
+    # T_host as the leading n x n block of an (n + 7) x n array whose strictly
+    # lower part holds NaN: only the upper triangle is copied and read; all of
+    # U_host (NaN beforehand) is written, zeros below the diagonal
+    n, ld = 300, 307
+    T = make_T(n, 0.5, seed=5)
+    big = np.full((ld, n), np.nan, order="F")
+    big[:n, :n] = np.where(np.triu(np.ones((n, n), bool)), T, np.nan)
+    U = np.full((n, n), np.nan, order="F")
+    st = gpu_lib.sign_tri_host(n, big.ctypes.data, ld, U.ctypes.data, n, gpu_lib.Variant[variant], 0)
+    assert st == 0
+    assert np.all(np.isfinite(U)) and np.all(np.tril(U, -1) == 0.0)
+    assert relerr(U, oracle_mod.sign_tri(T)) <= (1e-12 if "MIXED" in variant else TOL_FP64)
+
+
 def test_host_entry_point(gpu_lib, oracle_mod):
     import ctypes
     n = 333
