@@ -208,8 +208,18 @@ signtri_status run_variant(int n, const double *T, int ldt, double *U, int ldu, 
     case SIGNTRI_PH_FP64_EFFICIENT:
         g_info.cutoff = b;
         return ph_fp64_split_run(n, T, ldt, U, ldu, b, ws, st);
-    case SIGNTRI_PS_FP64:
-        return ps_fp64_run(n, T, ldt, U, ldu, r.n_pos, r.swaps, ws, st);
+    case SIGNTRI_PS_FP64: {
+        SGT_CUDA_TRY(cudaMemsetAsync(s.err_dev, 0, sizeof(int), st));
+        rs = ps_fp64_run(n, T, ldt, U, ldu, r.n_pos, r.swaps, ws, s.err_dev, st);
+        if (rs != SIGNTRI_OK) return rs;
+        if (r.swaps > 0 && n >= kBlockedReorderMin) {
+            // the blocked reorder's tensor-core products wait with a bound
+            SGT_CUDA_TRY(cudaMemcpyAsync(s.err_host, s.err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SGT_CUDA_TRY(cudaStreamSynchronize(st));
+            if (*s.err_host) return SIGNTRI_ERR_TIMEOUT;
+        }
+        return SIGNTRI_OK;
+    }
     case SIGNTRI_PH_MIXED_TF32:
     case SIGNTRI_PH_MIXED_BF16:
     case SIGNTRI_PH_MIXED_FP16: {
@@ -642,9 +652,14 @@ signtri_status signtri_reorder_by_sign(int n, const double *T, int ldt, double *
     const ScanResult r = *s->scan_host;
     if (r.bad_key != INT_MAX) return (signtri_status)(r.bad_key % 4);
     Arena ws;
-    rs = get_workspace(s[0], reorder_workspace_bytes(n) + (size_t)r.swaps * sizeof(int) + 256, ws);
+    rs = get_workspace(s[0], reorder_any_workspace_bytes(n, r.swaps), ws);
     if (rs != SIGNTRI_OK) return rs;
-    return reorder_run(n, T, ldt, Tr, ldtr, Q, ldq, swaps, ws, st);
+    SGT_CUDA_TRY(cudaMemsetAsync(s->err_dev, 0, sizeof(int), st));
+    rs = reorder_any_run(n, T, ldt, Tr, ldtr, Q, ldq, swaps, ws, s->err_dev, st);
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaMemcpyAsync(s->err_host, s->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    return *s->err_host ? SIGNTRI_ERR_TIMEOUT : SIGNTRI_OK;
 }
 
 signtri_status signtri_gemm_emulated(int m, int n, int k, const double *A, int lda, const double *B, int ldb,

@@ -140,12 +140,25 @@ signtri_status gemm_f64(bool transA, bool transB, int m, int n, int k, double al
 size_t sylvester_workspace_bytes(int m, int p);
 signtri_status sylvester_run(int m, int p, const double *A, int lda, const double *Bm, int ldb, const double *C,
                              int ldc, double cscale, double *X, int ldx, Arena &ws, cudaStream_t st);
+signtri_status copy_upper_identity(int n, const double *T, int ldt, double *Tr, int ldtr, double *Q, int ldq,
+                                   cudaStream_t st);
+// the odd-even rounds, float64 rotations applied one by one
 size_t reorder_workspace_bytes(int n);
 signtri_status reorder_run(int n, const double *T, int ldt, double *Tr, int ldtr, double *Q, int ldq,
                            long long *swaps_out, Arena &ws, cudaStream_t st);
+// the windowed form, each window's rotations applied by emulated-float64
+// tensor-core products (reorder_tc.cu); from this order on
+constexpr int kBlockedReorderMin = 512;
+size_t reorder_blocked_workspace_bytes(int n);
+signtri_status reorder_blocked_run(int n, const double *T, int ldt, double *Tr, int ldtr, double *Q, int ldq,
+                                   long long *swaps_out, Arena &ws, int *d_err, cudaStream_t st);
+// whichever of the two the order selects
+size_t reorder_any_workspace_bytes(int n, long long swaps);
+signtri_status reorder_any_run(int n, const double *T, int ldt, double *Tr, int ldtr, double *Q, int ldq,
+                               long long *swaps_out, Arena &ws, int *d_err, cudaStream_t st);
 size_t ps_workspace_bytes(int n, long long swaps);
 signtri_status ps_fp64_run(int n, const double *T, int ldt, double *U, int ldu, int npos, long long swaps,
-                           Arena &ws, cudaStream_t st);
+                           Arena &ws, int *d_err, cudaStream_t st);
 
 // bf16 slices and the emulated-float64 GEMM (slices.cu)
 int pad64(int x);

@@ -322,6 +322,15 @@ signtri_status sylvester_run(int m, int p, const double *A, int lda, const doubl
     return SIGNTRI_OK;
 }
 
+signtri_status copy_upper_identity(int n, const double *T, int ldt, double *Tr, int ldtr, double *Q, int ldq,
+                                   cudaStream_t st)
+{
+    ProfScope ps(SIGNTRI_KC_FILL, st);
+    copy_upper_identity_kernel<<<n, 256, 0, st>>>(n, T, ldt, Tr, ldtr, Q, ldq);
+    SGT_LAUNCH_CHECK();
+    return SIGNTRI_OK;
+}
+
 size_t reorder_workspace_bytes(int n)
 {
     if (n <= 0) return 0;
@@ -370,17 +379,30 @@ signtri_status reorder_run(int n, const double *T, int ldt, double *Tr, int ldtr
     return SIGNTRI_OK;
 }
 
+size_t reorder_any_workspace_bytes(int n, long long swaps)
+{
+    return n >= kBlockedReorderMin ? reorder_blocked_workspace_bytes(n)
+                                   : reorder_workspace_bytes(n) + (size_t)std::max(swaps, 0LL) * sizeof(int) + 256;
+}
+
+signtri_status reorder_any_run(int n, const double *T, int ldt, double *Tr, int ldtr, double *Q, int ldq,
+                               long long *swaps_out, Arena &ws, int *d_err, cudaStream_t st)
+{
+    return n >= kBlockedReorderMin ? reorder_blocked_run(n, T, ldt, Tr, ldtr, Q, ldq, swaps_out, ws, d_err, st)
+                                   : reorder_run(n, T, ldt, Tr, ldtr, Q, ldq, swaps_out, ws, st);
+}
+
 size_t ps_workspace_bytes(int n, long long swaps)
 {
     if (n <= 0) return 0;
     const size_t nn = (size_t)n * n * sizeof(double) + 256;
     size_t b = sylvester_workspace_bytes(n, n) + nn /* X */;
-    if (swaps > 0) b += 2 * nn /* T~, Q */ + nn /* W */ + reorder_workspace_bytes(n) + (size_t)swaps * sizeof(int) + 256;
+    if (swaps > 0) b += 2 * nn /* T~, Q */ + nn /* W */ + reorder_any_workspace_bytes(n, swaps);
     return b;
 }
 
 signtri_status ps_fp64_run(int n, const double *T, int ldt, double *U, int ldu, int npos, long long swaps,
-                           Arena &ws, cudaStream_t st)
+                           Arena &ws, int *d_err, cudaStream_t st)
 {
     const int nneg = n - npos;
     if (swaps == 0) {
@@ -399,7 +421,7 @@ signtri_status ps_fp64_run(int n, const double *T, int ldt, double *U, int ldu, 
     double *W = static_cast<double *>(ws.take((size_t)n * n * sizeof(double)));
     if (!Tr || !Q || !X || !W) return SIGNTRI_ERR_NO_WORKSPACE;
     long long done = 0;
-    signtri_status rs = reorder_run(n, T, ldt, Tr, n, Q, n, &done, ws, st);
+    signtri_status rs = reorder_any_run(n, T, ldt, Tr, n, Q, n, &done, ws, d_err, st);
     if (rs != SIGNTRI_OK) return rs;
     rs = sylvester_run(npos, nneg, Tr, n, &SGT_AT(Tr, n, npos, npos), n, &SGT_AT(Tr, n, 0, npos), n, 2.0, X, npos,
                        ws, st);

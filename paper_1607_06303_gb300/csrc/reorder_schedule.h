@@ -5,6 +5,8 @@
 // tests compile it on its own to check the schedule.
 #pragma once
 
+#include <vector_types.h>
+
 #include <algorithm>
 #include <utility>
 #include <vector>
@@ -43,6 +45,49 @@ inline void schedule_rounds(const std::vector<double> &diag, std::vector<int> &p
         idle = any ? 0 : idle + 1;
     }
     while (offsets.size() > 1 && offsets[offsets.size() - 1] == offsets[offsets.size() - 2]) offsets.pop_back();
+}
+
+// Windowed form of the same stable partition (blocked reorder): sweeps over
+// windows of w consecutive indices (w a multiple of 64, at most 128), their
+// boundaries at offset 0 in even sweeps and w / 2 in odd ones (a first window
+// of w / 2 then); in a sweep every window holding a negative above a positive
+// is stable-partitioned on its own (positives first), by adjacent swaps.
+// Output: per sweep the active windows (start, width); the total swap count
+// (the same minimum k).  Ends when the whole sequence is partitioned.
+inline void schedule_window_sweeps(const std::vector<double> &diag, int w, std::vector<std::vector<int2>> &sweeps,
+                                   long long &swaps)
+{
+    const int n = (int)diag.size();
+    std::vector<signed char> s(n);
+    for (int i = 0; i < n; i++) s[i] = diag[i] > 0.0 ? 1 : -1;
+    sweeps.clear();
+    swaps = 0;
+    auto sorted = [&]() {
+        int i = 0;
+        while (i < n && s[i] > 0) i++;
+        while (i < n && s[i] < 0) i++;
+        return i == n;
+    };
+    for (int t = 0; !sorted(); t++) {
+        const int off = (t & 1) ? w / 2 : 0;
+        std::vector<int2> act;
+        for (int a = 0; a < n;) {
+            const int b = std::min(n, a == 0 && off > 0 ? off : a + w);
+            // inversions inside [a, b): pairs (negative, later positive)
+            long long inv = 0, neg = 0;
+            for (int i = a; i < b; i++) {
+                if (s[i] < 0) neg++;
+                else inv += neg;
+            }
+            if (inv > 0) {
+                act.push_back(int2{a, b - a});
+                swaps += inv;
+                std::stable_partition(s.begin() + a, s.begin() + b, [](signed char x) { return x > 0; });
+            }
+            a = b;
+        }
+        sweeps.push_back(act);
+    }
 }
 
 }  // namespace signtri

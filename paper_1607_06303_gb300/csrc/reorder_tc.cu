@@ -1,0 +1,338 @@
+// reorder_tc.cu -- blocked reorder by sign for Parlett-Sylvester (Section 2,
+// Section 3; Section 4.1's blocking applied to the swaps).
+//
+// The same stable partition as the odd-even rounds of ps_fp64.cu, done by
+// windows (reorder_schedule.h, schedule_window_sweeps): in each sweep every
+// window W = [a, a + w) (w <= 128) that still holds a negative above a
+// positive is partitioned on its own by adjacent Givens swaps.  One CTA per
+// window keeps the diagonal block T[W, W] in shared memory, runs the swaps as
+// odd-even rounds there (each rotation as in ps_fp64.cu: G's first column the
+// eigenvector of the entry moving up, the 2 x 2 diagonal block swapped
+// exactly) and logs them; it then forms the window's orthogonal factor Z_W =
+// G_1 G_2 ... by applying the logged rotations to the identity.  The rest of
+// T and Q receive the window's rotations at once, as products:
+//   T[W, right of W] <- Z_W^T T[W, right of W]
+//   T[above W, W]    <- T[above W, W] Z_W
+//   Q[:, W]          <- Q[:, W] Z_W
+// (left and right factors commute, so all row products of a sweep come
+// first, then all column products).  GB300 has no fast float64 product, so
+// these run on the tensor cores as emulated-float64 products of exact 7-bit
+// slices (tc_gemm.cu), written straight back into T and Q: each product
+// reads the slices, snapshots taken before it, never the matrix it writes.
+#include <algorithm>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "exact_slices.cuh"
+#include "internal.cuh"
+#include "reorder_schedule.h"
+#include "tc_gemm.cuh"
+
+namespace signtri {
+
+namespace {
+
+constexpr int kWin = 128;                  // window width (two 64-row panels)
+constexpr int kWinLD = kWin + 1;
+constexpr int kMaxRot = (kWin / 2) * (kWin / 2);   // swaps of a window at most
+constexpr int kWinThreads = 512;
+constexpr int kSlices = 7;                 // exact slices of 7 bits: float64 products to about 2^-45
+
+size_t window_smem_bytes()
+{
+    return (size_t)kWin * kWinLD * sizeof(double) + 2 * (size_t)kMaxRot * sizeof(double) +
+           (size_t)kMaxRot * sizeof(short) + 2 * (size_t)kWin * sizeof(double);
+}
+
+// One window per CTA: stable partition of T[W, W] by swaps, then Z_W as the
+// exact column slices the products read -- ZC[s][a + j][a + i] = slice s of
+// Z_W[i][j] under the column's power-of-two scale sZ[a + j] (rp rows of
+// pitch kp per slice).  Entries of ZC outside the windows' blocks are never
+// read (the products' K ranges stay inside the window).
+__global__ void __launch_bounds__(kWinThreads)
+window_sort_kernel(double *__restrict__ Tr, int ldt, const int2 *__restrict__ wins, __nv_bfloat16 *__restrict__ ZC,
+                   float *__restrict__ sZ, int rp, int kp)
+{
+    extern __shared__ double wsm[];
+    double *B = wsm;                                   // B[i + j * kWinLD] = T[a + i, a + j]
+    double *lc = B + kWin * kWinLD;                    // logged rotations (cs, sn, k), round by round
+    double *ls = lc + kMaxRot;
+    short *lk = reinterpret_cast<short *>(ls + kMaxRot);
+    double *rc = reinterpret_cast<double *>(lk + kMaxRot);   // this round's rotation at position k
+    double *rsn = rc + kWin;
+    __shared__ signed char sg[kWin], act[kWin];
+    __shared__ int roff[2 * kWin + 4];
+    __shared__ int nlog, nround, quiet;
+    const int a = wins[blockIdx.x].x, w = wins[blockIdx.x].y;
+    for (int idx = threadIdx.x; idx < kWin * kWin; idx += kWinThreads) {
+        const int i = idx % kWin, j = idx / kWin;
+        B[i + j * kWinLD] = (i <= j && j < w) ? SGT_AT(Tr, ldt, a + i, a + j) : 0.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kWin; i += kWinThreads) sg[i] = (i < w && B[i + i * kWinLD] > 0.0) ? 1 : -1;
+    if (threadIdx.x == 0) {
+        nlog = 0;
+        nround = 0;
+        quiet = 0;
+    }
+    __syncthreads();
+    // odd-even rounds until two in a row swap nothing (at most w + 1 rounds)
+    for (int r = 0; quiet < 2 && r < 2 * kWin + 2; r++) {
+        if (threadIdx.x == 0) roff[r] = nlog;
+        for (int k = threadIdx.x; k < kWin; k += kWinThreads) {
+            const bool on = (k & 1) == (r & 1) && k + 1 < w && sg[k] < 0 && sg[k + 1] > 0;
+            act[k] = on ? 1 : 0;
+            if (on) {
+                const double aa = B[k + k * kWinLD], cc = B[(k + 1) + (k + 1) * kWinLD], bb = B[k + (k + 1) * kWinLD];
+                const double d = cc - aa, h = hypot(bb, d);
+                rc[k] = bb / h;
+                rsn[k] = d / h;
+            }
+        }
+        __syncthreads();
+        // log this round's rotations in position order
+        if (threadIdx.x < 32) {
+            // warp 0: positions k = 4 lane .. 4 lane + 3, a prefix count by ballots
+            int c = 0, mine[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int k = 4 * threadIdx.x + q;
+                mine[q] = k < w && act[k];
+                c += mine[q];
+            }
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)threadIdx.x >= o) incl += t;
+            }
+            int e = nlog + incl - c;
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (mine[q]) {
+                    const int k = 4 * threadIdx.x + q;
+                    lc[e] = rc[k];
+                    ls[e] = rsn[k];
+                    lk[e] = (short)k;
+                    e++;
+                }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            __syncwarp();
+            if (threadIdx.x == 0) {
+                nlog += total;
+                quiet = total ? 0 : quiet + 1;
+                nround = r + 1;
+            }
+        }
+        // G^T on rows k, k+1 (columns past the pair), then G on columns k, k+1
+        // (rows above the pair); the pairs of a round are disjoint and the
+        // two sides commute
+        for (int idx = threadIdx.x; idx < kWin * kWin; idx += kWinThreads) {
+            const int k = idx % kWin, j = idx / kWin;
+            if (!act[k] || j < k + 2 || j >= w) continue;
+            double *x0 = &B[k + j * kWinLD], *x1 = &B[(k + 1) + j * kWinLD];
+            const double u = *x0, v = *x1, c1 = rc[k], s1 = rsn[k];
+            *x0 = c1 * u + s1 * v;
+            *x1 = -s1 * u + c1 * v;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kWin * kWin; idx += kWinThreads) {
+            const int i = idx % kWin, k = idx / kWin;
+            if (!act[k] || i >= k) continue;
+            double *x0 = &B[i + k * kWinLD], *x1 = &B[i + (k + 1) * kWinLD];
+            const double u = *x0, v = *x1, c1 = rc[k], s1 = rsn[k];
+            *x0 = u * c1 + v * s1;
+            *x1 = -u * s1 + v * c1;
+        }
+        __syncthreads();
+        // the exact swap of the 2 x 2 diagonal block (its coupling unchanged)
+        for (int k = threadIdx.x; k < kWin; k += kWinThreads)
+            if (act[k]) {
+                const double t0 = B[k + k * kWinLD];
+                B[k + k * kWinLD] = B[(k + 1) + (k + 1) * kWinLD];
+                B[(k + 1) + (k + 1) * kWinLD] = t0;
+                sg[k] = 1;
+                sg[k + 1] = -1;
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) roff[nround] = nlog;
+    for (int idx = threadIdx.x; idx < kWin * kWin; idx += kWinThreads) {
+        const int i = idx % kWin, j = idx / kWin;
+        if (i <= j && j < w) SGT_AT(Tr, ldt, a + i, a + j) = B[i + j * kWinLD];
+    }
+    __syncthreads();
+    // Z = I G_1 G_2 ..., round by round (a round's rotations act on disjoint columns)
+    for (int idx = threadIdx.x; idx < kWin * kWin; idx += kWinThreads) {
+        const int i = idx % kWin, j = idx / kWin;
+        B[i + j * kWinLD] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int r = 0; r < nround; r++) {
+        const int e0 = roff[r], e1 = roff[r + 1];
+        for (int idx = threadIdx.x; idx < (e1 - e0) * kWin; idx += kWinThreads) {
+            const int e = e0 + idx / kWin, i = idx % kWin;
+            const int k = lk[e];
+            double *x0 = &B[i + k * kWinLD], *x1 = &B[i + (k + 1) * kWinLD];
+            const double u = *x0, v = *x1, c1 = lc[e], s1 = ls[e];
+            *x0 = u * c1 + v * s1;
+            *x1 = -u * s1 + v * c1;
+        }
+        __syncthreads();
+    }
+    // per column of Z: the power-of-two scale above its largest entry (an
+    // orthogonal column: between 1 / sqrt(w) and 1), then its exact slices
+    __shared__ int cexp[kWin];
+    for (int j = threadIdx.x; j < w; j += kWinThreads) {
+        double mx = 0.0;
+        for (int i = 0; i < w; i++) mx = fmax(mx, fabs(B[i + j * kWinLD]));
+        int e = 0;
+        frexp(mx, &e);
+        cexp[j] = e;
+        sZ[a + j] = ldexpf(1.f, e);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < w * w; idx += kWinThreads) {
+        const int i = idx % w, j = idx / w;
+        float q[kSlices];
+        exact_slices<kSlices>(B[i + j * kWinLD], cexp[j], kSlices, 7, q);
+#pragma unroll
+        for (int sl = 0; sl < kSlices; sl++)
+            ZC[((size_t)sl * rp + a + j) * kp + a + i] = __float2bfloat16_rn(q[sl]);
+    }
+}
+
+}  // namespace
+
+size_t reorder_blocked_workspace_bytes(int n)
+{
+    if (n <= 0) return 0;
+    const size_t rp = (size_t)pad64(n) + 64, kp = (size_t)pad64(n);
+    size_t b = 4 * (kSlices * rp * kp * 2 + 256);                    // slices: Z, T (two forms), Q
+    b += 4 * (rp * sizeof(float) + 256) + rp * 8 + 256;               // scales, max buffer
+    b += sizeof(TcPairs) + 256;
+    // the window and job lists of every sweep go to memory of their own
+    return b;
+}
+
+signtri_status reorder_blocked_run(int n, const double *T, int ldt, double *Tr, int ldtr, double *Q, int ldq,
+                                   long long *swaps_out, Arena &ws, int *d_err, cudaStream_t st)
+{
+    if (n <= 0) return SIGNTRI_OK;
+    const int np = pad64(n), rp = np + 64, kp = np, zero = np;   // rows [np, np + 64) of every slice array are zero
+    auto slices = [&]() { return static_cast<__nv_bfloat16 *>(ws.take((size_t)kSlices * rp * kp * 2)); };
+    __nv_bfloat16 *ZC = slices(), *TC = slices(), *TR = slices(), *QR = slices();
+    float *sZ = static_cast<float *>(ws.take(rp * sizeof(float)));
+    float *sTc = static_cast<float *>(ws.take(rp * sizeof(float)));
+    float *sTr = static_cast<float *>(ws.take(rp * sizeof(float)));
+    float *sQ = static_cast<float *>(ws.take(rp * sizeof(float)));
+    auto *tmp = static_cast<unsigned long long *>(ws.take(rp * sizeof(unsigned long long)));
+    auto *d_pairs = static_cast<TcPairs *>(ws.take(sizeof(TcPairs)));
+    if (!ZC || !TC || !TR || !QR || !sZ || !sTc || !sTr || !sQ || !tmp || !d_pairs) return SIGNTRI_ERR_NO_WORKSPACE;
+    signtri_status rs = copy_upper_identity(n, T, ldt, Tr, ldtr, Q, ldq, st);   // T~ = upper part of T, Q = I
+    if (rs != SIGNTRI_OK) return rs;
+    std::vector<double> diag(n);
+    SGT_CUDA_TRY(cudaMemcpy2DAsync(diag.data(), sizeof(double), T, ((size_t)ldt + 1) * sizeof(double), sizeof(double),
+                                   n, cudaMemcpyDeviceToHost, st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<std::vector<int2>> sweeps;
+    long long swaps = 0;
+    schedule_window_sweeps(diag, kWin, sweeps, swaps);
+    if (swaps_out) *swaps_out = swaps;
+    if (swaps == 0) return SIGNTRI_OK;
+    // every sweep's windows and the jobs of its three products, built here
+    // and uploaded once
+    auto job = [](int rt, int rb, int cl, int cr, int kb0, int kb1) {
+        TcJob j;
+        j.rt = rt; j.rb = rb; j.cl = cl; j.cr = cr; j.kb0 = kb0; j.kb1 = kb1; j.slot = 0; j.pad = 0;
+        return j;
+    };
+    std::vector<int2> wins_all;
+    std::vector<TcJob> jobs_all;
+    struct Sweep { int w0, nw; int j[4]; double kb[3]; };
+    std::vector<Sweep> plan;
+    for (const std::vector<int2> &sw : sweeps) {
+        if (sw.empty()) continue;
+        Sweep p{(int)wins_all.size(), (int)sw.size(), {0, 0, 0, 0}, {0, 0, 0}};
+        wins_all.insert(wins_all.end(), sw.begin(), sw.end());
+        for (int phase = 0; phase < 3; phase++) {
+            p.j[phase] = (int)jobs_all.size();
+            for (const int2 &win : sw) {
+                const int a = win.x, e = win.x + win.y, kb0 = a / 64, kb1 = (e + 63) / 64;
+                const int second = win.y > 64 ? a + 64 : zero;
+                if (phase == 0) {
+                    // rows: T[W, c..c+128) <- Z^T T[W, c..c+128) for the columns right of W
+                    for (int c = e; c < n; c += 128) jobs_all.push_back(job(a, second, c, c + 64 < n ? c + 64 : zero, kb0, kb1));
+                } else {
+                    // columns: T[r..r+128, W] <- T[r..r+128, W] Z above W; Q[r..r+128, W] <- Q[..] Z for all rows
+                    const int rows = phase == 1 ? a : n;
+                    for (int r = 0; r < rows; r += 128)
+                        jobs_all.push_back(job(r, r + 64 < rows ? r + 64 : zero, a, second, kb0, kb1));
+                }
+            }
+            for (int q = p.j[phase]; q < (int)jobs_all.size(); q++) p.kb[phase] += 4.0 * (jobs_all[q].kb1 - jobs_all[q].kb0);
+        }
+        p.j[3] = (int)jobs_all.size();
+        plan.push_back(p);
+    }
+    int2 *d_wins = nullptr;
+    TcJob *d_jobs = nullptr;
+    if (cudaMalloc(&d_wins, std::max<size_t>(wins_all.size(), 1) * sizeof(int2)) != cudaSuccess ||
+        cudaMalloc(&d_jobs, std::max<size_t>(jobs_all.size(), 1) * sizeof(TcJob)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d_wins);
+        return SIGNTRI_ERR_NO_WORKSPACE;
+    }
+    auto body = [&]() -> signtri_status {
+        SGT_CUDA_TRY(cudaMemcpyAsync(d_wins, wins_all.data(), wins_all.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+        SGT_CUDA_TRY(cudaMemcpyAsync(d_jobs, jobs_all.data(), jobs_all.size() * sizeof(TcJob), cudaMemcpyHostToDevice, st));
+        const TcPairs pairs = ozaki_pairs_impl(kSlices, 7);
+        SGT_CUDA_TRY(cudaMemcpyAsync(d_pairs, &pairs, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
+        // the zero rows past the matrix, read by the half-empty jobs
+        SGT_CUDA_TRY(cudaMemsetAsync(ZC, 0, (size_t)kSlices * rp * kp * 2, st));
+        const size_t smem = window_smem_bytes();
+        SGT_CUDA_TRY(cudaFuncSetAttribute(window_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const TcSource srcZ{ZC, kSlices, rp, kp, kp, sZ}, srcTc{TC, kSlices, rp, kp, kp, sTc};
+        const TcSource srcTr{TR, kSlices, rp, kp, kp, sTr}, srcQ{QR, kSlices, rp, kp, kp, sQ};
+        const TcQuadOut toT{{Tr, Tr, Tr, Tr}, ldtr, n, n, 0}, toQ{{Q, Q, Q, Q}, ldq, n, n, 0};
+        const double fl = tc_flops(pairs.n, 1, 1);
+        auto product = [&](const Sweep &p, int phase, const TcSource &top, const TcSource &left,
+                           const TcQuadOut &out) -> signtri_status {
+            const int cnt = p.j[phase + 1] - p.j[phase];
+            if (cnt == 0) return SIGNTRI_OK;
+            return tc_blocksums(top, top, left, left, d_jobs + p.j[phase], cnt, pairs, d_pairs, kExactChunkKb7, nullptr,
+                                out, d_err, SIGNTRI_KC_GIVENS, st, fl * p.kb[phase]);
+        };
+        signtri_status r2;
+        for (const Sweep &p : plan) {
+            {
+                ProfScope ps(SIGNTRI_KC_GIVENS, st);
+                window_sort_kernel<<<p.nw, kWinThreads, smem, st>>>(Tr, ldtr, d_wins + p.w0, ZC, sZ, rp, kp);
+                SGT_LAUNCH_CHECK();
+            }
+            // rows of T (column slices of its strictly upper part: K = rows of W)
+            if ((r2 = make_scales(n, n, Tr, ldtr, 1, false, rp, tmp, sTc, st)) != SIGNTRI_OK) return r2;
+            if ((r2 = make_col_slices(n, n, Tr, ldtr, 1, kSlices, 7, sTc, TC, rp, kp, st)) != SIGNTRI_OK) return r2;
+            if ((r2 = product(p, 0, srcZ, srcTc, toT)) != SIGNTRI_OK) return r2;
+            // columns of T (row slices after the row products) and of Q
+            if ((r2 = make_scales(n, n, Tr, ldtr, 1, true, rp, tmp, sTr, st)) != SIGNTRI_OK) return r2;
+            if ((r2 = make_row_slices(n, n, Tr, ldtr, 1, kSlices, 7, sTr, TR, rp, kp, st)) != SIGNTRI_OK) return r2;
+            if ((r2 = product(p, 1, srcTr, srcZ, toT)) != SIGNTRI_OK) return r2;
+            if ((r2 = make_scales(n, n, Q, ldq, 0, true, rp, tmp, sQ, st)) != SIGNTRI_OK) return r2;
+            if ((r2 = make_row_slices(n, n, Q, ldq, 0, kSlices, 7, sQ, QR, rp, kp, st)) != SIGNTRI_OK) return r2;
+            if ((r2 = product(p, 2, srcQ, srcZ, toQ)) != SIGNTRI_OK) return r2;
+        }
+        // the host lists stay alive until the copies above are done; so do the
+        // device lists until the last product
+        SGT_CUDA_TRY(cudaStreamSynchronize(st));
+        return SIGNTRI_OK;
+    };
+    rs = body();
+    if (rs != SIGNTRI_OK) cudaStreamSynchronize(st);
+    cudaFree(d_wins);
+    cudaFree(d_jobs);
+    return rs;
+}
+
+}  // namespace signtri

@@ -21,6 +21,7 @@
 
 #include <cuda_bf16.h>
 
+#include "exact_slices.cuh"
 #include "internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -100,32 +101,6 @@ __global__ void pow2_scale_kernel(int n, const unsigned long long *__restrict__ 
         e = max(e, -120);
     }
     scale[i] = ldexpf(1.0f, e);
-}
-
-// Exact slices by integer arithmetic: |x| / scale < 1 written as the 64-bit
-// fixed-point integer F = trunc(|x| / scale * 2^64) (from the float64
-// significand and exponent, no rounding), digits q_s = bits
-// [64 - b(s+1), 64 - bs) of F with the sign of x.  Same digits as repeated
-// q_s = trunc(2^b r), r <- 2^b r - q_s, without float64 arithmetic (slow on
-// this part).  S b <= 64.
-template <int SC>
-__device__ __forceinline__ void exact_slices(double x, int scale_exp, int S, int b, float *q)
-{
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    const int bexp = (int)((bits >> 52) & 0x7ff);
-    unsigned long long F = 0;
-    if (bexp != 0) {   // zero and subnormals (far below any scale used here) give 0
-        const unsigned long long mant = (bits & 0xfffffffffffffull) | (1ull << 52);
-        // |x| = mant * 2^(bexp - 1075); F = |x| * 2^(64 - scale_exp)
-        const int sh = bexp - 1075 + 64 - scale_exp;   // <= 11 since |x| < 2^scale_exp
-        if (sh >= 0) F = mant << sh;
-        else if (sh > -64) F = mant >> (-sh);
-    }
-    const float sgn = (bits >> 63) ? -1.f : 1.f;
-    const unsigned long long mask = (1ull << b) - 1ull;
-    const int ns = SC ? SC : S;   // SC > 0: slice count known at compile time (q in registers)
-#pragma unroll
-    for (int s = 0; s < ns; s++) q[s] = sgn * (float)((F >> (64 - b * (s + 1))) & mask);
 }
 
 // Rounding split of the fp32 value of x: x0 = bf16(x), x1 = bf16(x - x0), ...

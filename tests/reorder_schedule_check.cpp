@@ -9,7 +9,13 @@
 //   - after the last round the positives come first, each sign group in its
 //     original order (a stable partition);
 //   - the number of swaps is #{i<j : s_i < 0 < s_j} (Section 3, the minimum);
-//   - at most n + 1 rounds, offsets consistent, no trailing empty round.
+//   - at most n + 1 rounds, offsets consistent, no trailing empty round;
+// and of the windowed form (blocked reorder), by replaying its sweeps:
+//   - windows disjoint, ascending, inside [0, n), starting on multiples of
+//     w / 2 (the 64-row panels of the products that apply them), at most w
+//     wide, each holding an inversion when its sweep comes;
+//   - after the last sweep the same stable partition, with the same total
+//     swap count; at most 2 n / (w / 2) + 2 sweeps.
 // Prints "ok <swaps checked>" and exits 0, or the first violations and exit
 // code 1.  Test infrastructure: compiled and run by the CPU tests.
 #include <cstdio>
@@ -75,6 +81,44 @@ static void check(const std::vector<int> &sign)
     for (int i = 0; i < n; i++) CHECK((s[i] > 0) == (i < npos), "position %d holds sign %d after the rounds", i, s[i]);
     for (int i = 0; i + 1 < n; i++)
         if ((i + 1 < npos) || (i >= npos)) CHECK(orig[i] < orig[i + 1], "positions %d, %d out of original order", i, i + 1);
+
+    // windowed sweeps
+    constexpr int w = 128;
+    std::vector<std::vector<int2>> sweeps;
+    long long wswaps = 0;
+    schedule_window_sweeps(diag, w, sweeps, wswaps);
+    CHECK(wswaps == inversions, "windowed: %lld swaps, %lld inversions", wswaps, inversions);
+    CHECK((long long)sweeps.size() <= 2LL * n / (w / 2) + 2, "windowed: %zu sweeps", sweeps.size());
+    std::vector<int> ws = sign, worig(n);
+    for (int i = 0; i < n; i++) worig[i] = i;
+    for (size_t t = 0; t < sweeps.size(); t++) {
+        int end = 0;
+        for (const int2 &win : sweeps[t]) {
+            const int a = win.x, b = win.x + win.y;
+            CHECK(a >= end && win.y > 0 && win.y <= w && b <= n, "sweep %zu: window (%d, %d)", t, a, win.y);
+            CHECK(a % (w / 2) == 0, "sweep %zu: window start %d", t, a);
+            if (a < end || a < 0 || b > n || win.y <= 0) return;
+            end = b;
+            long long inv = 0, neg = 0;
+            for (int i = a; i < b; i++) {
+                if (ws[i] < 0) neg++;
+                else inv += neg;
+            }
+            CHECK(inv > 0, "sweep %zu: window (%d, %d) already partitioned", t, a, win.y);
+            std::vector<int> pos_s, neg_s, pos_o, neg_o;
+            for (int i = a; i < b; i++) {
+                (ws[i] > 0 ? pos_s : neg_s).push_back(ws[i]);
+                (ws[i] > 0 ? pos_o : neg_o).push_back(worig[i]);
+            }
+            int i = a;
+            for (size_t q = 0; q < pos_s.size(); q++, i++) { ws[i] = pos_s[q]; worig[i] = pos_o[q]; }
+            for (size_t q = 0; q < neg_s.size(); q++, i++) { ws[i] = neg_s[q]; worig[i] = neg_o[q]; }
+        }
+    }
+    for (int i = 0; i < n; i++) CHECK((ws[i] > 0) == (i < npos), "windowed: position %d holds sign %d", i, ws[i]);
+    for (int i = 0; i + 1 < n; i++)
+        if ((i + 1 < npos) || (i >= npos))
+            CHECK(worig[i] < worig[i + 1], "windowed: positions %d, %d out of original order", i, i + 1);
 }
 
 int main()

@@ -27,10 +27,20 @@ def stream():
 
 @pytest.mark.parametrize("n,p,order", [(2, 0.5, "random"), (7, 0.3, "random"), (64, 0.5, "random"),
                                        (65, 0.2, "random"), (200, 0.1, "random"), (333, 0.5, "random"),
-                                       (300, 0.25, "sorted"), (129, 0.9, "random")])
+                                       (300, 0.25, "sorted"), (129, 0.9, "random"),
+                                       # from n = 512 on the blocked reorder: windows of 128 sorted in
+                                       # shared memory, their rotations applied by tensor-core products
+                                       (512, 0.5, "random"), (700, 0.1, "random"), (1111, 0.3, "random"),
+                                       (640, 0.5, "negatives_first")])
 def test_reorder_by_sign(gpu_lib, n, p, order):
     import torch
-    T = make_T(n, p, seed=31, order=order)
+    if order == "negatives_first":
+        # every negative above every positive: the most swaps, every window active
+        T = make_T(n, p, seed=31, order="sorted")
+        d = np.diag(T).copy()
+        T[np.arange(n), np.arange(n)] = np.concatenate([d[d < 0], d[d > 0]])
+    else:
+        T = make_T(n, p, seed=31, order=order)
     Tt = dev(gpu_lib, T)
     Tr = torch.full_like(Tt, 9.0)
     Qt = torch.empty_like(Tt)
