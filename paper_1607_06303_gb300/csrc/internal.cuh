@@ -167,6 +167,12 @@ signtri_status make_scales(int m, int k, const double *M, int ldm, int tri, bool
 size_t emulated_gemm_workspace_bytes(int m, int n, int k, int S);
 signtri_status emulated_gemm_run(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C,
                                  int ldc, int S, Arena &ws, int *d_err, cudaStream_t st);
+// C = A op(B) (op(B) = B or B^T) written straight into C; upper: only the
+// 128 x 128 tiles that meet the upper triangle
+size_t emulated_product_workspace_bytes(int m, int n, int k);
+signtri_status emulated_product(int m, int n, int k, const double *A, int lda, const double *B, int ldb, bool transB,
+                                double *C, int ldc, bool upper, int kernel_class, Arena &ws, int *d_err,
+                                cudaStream_t st);
 
 // Batched float64 Parlett-Higham (batched.cu)
 size_t batched_workspace_bytes(int count, const int *n, int cutoff_for_all);

@@ -250,12 +250,13 @@ sylv_leaf_kernel(int m, int p, const double *__restrict__ A, int lda, const doub
 
 // ---------------------------------------------------------- back-transform ---
 
-__global__ void scale_copy_kernel(int rows, int cols, const double *__restrict__ src, int lds, double alpha,
+// dst += alpha op(src) (rows x cols; op = transpose when asked), a CTA per column.
+__global__ void add_scaled_kernel(int rows, int cols, const double *__restrict__ src, int lds, double alpha,
                                   bool transpose, double *__restrict__ dst, int ldd)
 {
     const int j = blockIdx.x;
     for (int i = threadIdx.x; i < rows; i += blockDim.x)
-        SGT_AT(dst, ldd, i, j) = alpha * (transpose ? SGT_AT(src, lds, j, i) : SGT_AT(src, lds, i, j));
+        SGT_AT(dst, ldd, i, j) += alpha * (transpose ? SGT_AT(src, lds, j, i) : SGT_AT(src, lds, i, j));
 }
 
 // Diagonal of U set to sign(t_ii) of the input, strictly lower part to 0.
@@ -392,12 +393,29 @@ signtri_status reorder_any_run(int n, const double *T, int ldt, double *Tr, int 
                                    : reorder_run(n, T, ldt, Tr, ldtr, Q, ldq, swaps_out, ws, st);
 }
 
+// the back-transform's two products, one after the other in the same space
+static size_t back_transform_workspace_bytes(int n, int npos)
+{
+    const int nneg = n - npos;
+    if (nneg <= npos)
+        return std::max(emulated_product_workspace_bytes(n, nneg, npos), emulated_product_workspace_bytes(n, n, nneg));
+    return std::max(emulated_product_workspace_bytes(npos, n, nneg), emulated_product_workspace_bytes(n, n, npos));
+}
+
 size_t ps_workspace_bytes(int n, long long swaps)
 {
     if (n <= 0) return 0;
     const size_t nn = (size_t)n * n * sizeof(double) + 256;
     size_t b = sylvester_workspace_bytes(n, n) + nn /* X */;
-    if (swaps > 0) b += 2 * nn /* T~, Q */ + nn /* W */ + reorder_any_workspace_bytes(n, swaps);
+    if (swaps > 0) {
+        // T~, Q, W; then the reorder's space, reused by the Sylvester solve and
+        // the back-transform (bounded over every inertia)
+        size_t bt = 0;
+        for (int npos = 1; npos < n; npos = npos < 128 ? npos + 1 : npos + 64)
+            bt = std::max(bt, back_transform_workspace_bytes(n, npos));
+        bt = std::max(bt, back_transform_workspace_bytes(n, n - 1));
+        b += 3 * nn + std::max(reorder_any_workspace_bytes(n, swaps), bt) + 256;
+    }
     return b;
 }
 
@@ -420,34 +438,41 @@ signtri_status ps_fp64_run(int n, const double *T, int ldt, double *U, int ldu, 
     double *X = static_cast<double *>(ws.take((size_t)n * n * sizeof(double)));
     double *W = static_cast<double *>(ws.take((size_t)n * n * sizeof(double)));
     if (!Tr || !Q || !X || !W) return SIGNTRI_ERR_NO_WORKSPACE;
+    const size_t mark = ws.used;
     long long done = 0;
     signtri_status rs = reorder_any_run(n, T, ldt, Tr, n, Q, n, &done, ws, d_err, st);
     if (rs != SIGNTRI_OK) return rs;
+    ws.used = mark;   // the reorder's scratch is free again (stream order)
     rs = sylvester_run(npos, nneg, Tr, n, &SGT_AT(Tr, n, npos, npos), n, &SGT_AT(Tr, n, 0, npos), n, 2.0, X, npos,
                        ws, st);
     if (rs != SIGNTRI_OK) return rs;
+    ws.used = mark;
     const double *Q1 = Q;
     const double *Q2 = &SGT_AT(Q, n, 0, npos);
+    // the back-transform U = Q sign(T~) Q^T, as emulated-float64 tensor-core
+    // products, in the form whose inner dimension is the smaller block
     if (nneg <= npos) {
         // W = Q1 X - 2 Q2 (n x n_-),  U = I + W Q2^T
+        rs = emulated_product(n, nneg, npos, Q1, n, X, npos, false, W, n, false, SIGNTRI_KC_GEMM_F64, ws, d_err, st);
+        if (rs != SIGNTRI_OK) return rs;
+        ws.used = mark;
         {
             ProfScope ps(SIGNTRI_KC_FILL, st);
-            scale_copy_kernel<<<nneg, 256, 0, st>>>(n, nneg, Q2, n, -2.0, false, W, n);
+            add_scaled_kernel<<<nneg, 256, 0, st>>>(n, nneg, Q2, n, -2.0, false, W, n);
             SGT_LAUNCH_CHECK();
         }
-        rs = gemm_f64(false, false, n, nneg, npos, 1.0, Q1, n, X, npos, 1.0, W, n, false, st);
-        if (rs != SIGNTRI_OK) return rs;
-        rs = gemm_f64(false, true, n, n, nneg, 1.0, W, n, Q2, n, 0.0, U, ldu, true, st);
+        rs = emulated_product(n, n, nneg, W, n, Q2, n, true, U, ldu, true, SIGNTRI_KC_GEMM_F64, ws, d_err, st);
     } else {
         // W = 2 Q1^T + X Q2^T (n_+ x n),  U = -I + Q1 W
+        rs = emulated_product(npos, n, nneg, X, npos, Q2, n, true, W, npos, false, SIGNTRI_KC_GEMM_F64, ws, d_err, st);
+        if (rs != SIGNTRI_OK) return rs;
+        ws.used = mark;
         {
             ProfScope ps(SIGNTRI_KC_FILL, st);
-            scale_copy_kernel<<<n, 256, 0, st>>>(npos, n, Q1, n, 2.0, true, W, npos);
+            add_scaled_kernel<<<n, 256, 0, st>>>(npos, n, Q1, n, 2.0, true, W, npos);
             SGT_LAUNCH_CHECK();
         }
-        rs = gemm_f64(false, true, npos, n, nneg, 1.0, X, npos, Q2, n, 1.0, W, npos, false, st);
-        if (rs != SIGNTRI_OK) return rs;
-        rs = gemm_f64(false, false, n, n, npos, 1.0, Q1, n, W, npos, 0.0, U, ldu, true, st);
+        rs = emulated_product(n, n, npos, Q1, n, W, npos, false, U, ldu, true, SIGNTRI_KC_GEMM_F64, ws, d_err, st);
     }
     if (rs != SIGNTRI_OK) return rs;
     ProfScope ps(SIGNTRI_KC_FILL, st);

@@ -203,6 +203,133 @@ window_sort_kernel(double *__restrict__ Tr, int ldt, const int2 *__restrict__ wi
     }
 }
 
+// The slices the products of one sweep read, for the active 64-blocks of K
+// only (kbl: the sweep's window blocks, ascending).  Three kinds of lines:
+//   kColsT: column j of T, K = rows kk < j (row products: tiles kb < jb);
+//   kRowsT: row r of T, K = columns kk > r (column products: tiles rb < kb,
+//           plus the zero rows [np, np + 64));
+//   kRowsQ: row r of Q, K = every active column.
+// Every entry a tile holds is then strictly upper for T.  The scale of a line
+// is the power of two above its largest entry in the tiles it reads (1 for
+// none); lines outside every tile are not outputs of the sweep's products.
+constexpr int kColsT = 0, kRowsT = 1, kRowsQ = 2;
+
+template <int MODE>
+__device__ __forceinline__ bool tile_used(int kb, int lb, int zero_lb)
+{
+    if (MODE == kColsT) return lb > kb;
+    if (MODE == kRowsT) return lb < kb || lb == zero_lb;
+    return true;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256)
+masked_absmax_kernel(int n, const double *__restrict__ M, int ldm, const int *__restrict__ kbl, int zero_lb,
+                     unsigned long long *__restrict__ mx)
+{
+    const int kb = kbl[blockIdx.x], lb = blockIdx.y;
+    if (!tile_used<MODE>(kb, lb, zero_lb) || lb == zero_lb) return;
+    const int k0 = kb * 64, l0 = lb * 64;
+    if (MODE == kColsT) {
+        // a warp per column: two rows per lane, reduced by shuffles
+        const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+        for (int c = wp; c < 64; c += 8) {
+            const int j = l0 + c;
+            double v = 0.0;
+            if (j < n) {
+                if (k0 + lane < n) v = fabs(SGT_AT(M, ldm, k0 + lane, j));
+                if (k0 + lane + 32 < n) v = fmax(v, fabs(SGT_AT(M, ldm, k0 + lane + 32, j)));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0 && v > 0.0) atomicMax(&mx[j], (unsigned long long)__double_as_longlong(v));
+        }
+    } else {
+        // a thread per row and quarter of the columns, then the quarters reduced
+        __shared__ double part[4][64];
+        const int t = threadIdx.x & 63, q = threadIdx.x >> 6, r = l0 + t;
+        double v = 0.0;
+        if (r < n)
+            for (int c = q * 16; c < q * 16 + 16; c++)
+                if (k0 + c < n) v = fmax(v, fabs(SGT_AT(M, ldm, r, k0 + c)));
+        part[q][t] = v;
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            v = fmax(fmax(part[0][t], part[1][t]), fmax(part[2][t], part[3][t]));
+            if (v > 0.0) atomicMax(&mx[r], (unsigned long long)__double_as_longlong(v));
+        }
+    }
+}
+
+__device__ __forceinline__ int line_exp(const unsigned long long *mx, int line, int n)
+{
+    if (line >= n) return 0;
+    const double m = __longlong_as_double((long long)mx[line]);
+    int e = 0;
+    if (m > 0.0) {
+        frexp(m, &e);
+        e = max(e, -120);
+    }
+    return e;
+}
+
+// Exact 7-bit slices of the used tiles (S = kSlices), K-contiguous lines of
+// pitch kp, rp lines per slice; the line scales go to `scale` (written once
+// per line, by the CTA of the first (kColsT, kRowsQ) or last (kRowsT) block).
+template <int MODE>
+__global__ void __launch_bounds__(256)
+masked_slices_kernel(int n, const double *__restrict__ M, int ldm, const int *__restrict__ kbl, int zero_lb,
+                     const unsigned long long *__restrict__ mx, __nv_bfloat16 *__restrict__ out, float *__restrict__ scale,
+                     int rp, int kp)
+{
+    const int kb = kbl[blockIdx.x], lb = blockIdx.y;
+    if (!tile_used<MODE>(kb, lb, zero_lb)) return;
+    const int k0 = kb * 64, l0 = lb * 64;
+    const bool zero = lb == zero_lb;
+    const bool writes_scale = !zero && (int)blockIdx.x == (MODE == kRowsT ? (int)gridDim.x - 1 : 0);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (MODE == kColsT) {
+        // column j's K run is contiguous in M: lane reads rows k0 + 2 lane, + 1
+        for (int c = wp; c < 64; c += 8) {
+            const int j = l0 + c, kk = k0 + 2 * lane;
+            double v0 = 0.0, v1 = 0.0;
+            if (j < n) {
+                if (kk < n) v0 = SGT_AT(M, ldm, kk, j);
+                if (kk + 1 < n) v1 = SGT_AT(M, ldm, kk + 1, j);
+            }
+            const int e = line_exp(mx, j, n);
+            float q0[kSlices], q1[kSlices];
+            exact_slices<kSlices>(v0, e, kSlices, 7, q0);
+            exact_slices<kSlices>(v1, e, kSlices, 7, q1);
+#pragma unroll
+            for (int sl = 0; sl < kSlices; sl++)
+                *reinterpret_cast<__nv_bfloat162 *>(&out[((size_t)sl * rp + j) * kp + kk]) =
+                    __floats2bfloat162_rn(q0[sl], q1[sl]);
+            if (writes_scale && lane == 0 && j < n) scale[j] = ldexpf(1.f, e);
+        }
+    } else {
+        // rows: transposed through shared memory (tile[kk][r])
+        __shared__ double tile[64][65];
+        for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
+            const int t = idx & 63, c = idx >> 6, r = l0 + t, kk = k0 + c;
+            tile[c][t] = (!zero && r < n && kk < n) ? SGT_AT(M, ldm, r, kk) : 0.0;
+        }
+        __syncthreads();
+        for (int t = wp; t < 64; t += 8) {
+            const int r = l0 + t, kk = k0 + 2 * lane;
+            const int e = zero ? 0 : line_exp(mx, r, n);
+            float q0[kSlices], q1[kSlices];
+            exact_slices<kSlices>(tile[2 * lane][t], e, kSlices, 7, q0);
+            exact_slices<kSlices>(tile[2 * lane + 1][t], e, kSlices, 7, q1);
+#pragma unroll
+            for (int sl = 0; sl < kSlices; sl++)
+                *reinterpret_cast<__nv_bfloat162 *>(&out[((size_t)sl * rp + r) * kp + kk]) =
+                    __floats2bfloat162_rn(q0[sl], q1[sl]);
+            if (writes_scale && lane == 0 && r < n) scale[r] = ldexpf(1.f, e);
+        }
+    }
+}
+
 }  // namespace
 
 size_t reorder_blocked_workspace_bytes(int n)
@@ -210,7 +337,7 @@ size_t reorder_blocked_workspace_bytes(int n)
     if (n <= 0) return 0;
     const size_t rp = (size_t)pad64(n) + 64, kp = (size_t)pad64(n);
     size_t b = 4 * (kSlices * rp * kp * 2 + 256);                    // slices: Z, T (two forms), Q
-    b += 4 * (rp * sizeof(float) + 256) + rp * 8 + 256;               // scales, max buffer
+    b += 4 * (rp * sizeof(float) + 256) + 3 * rp * 8 + 256;           // scales, line maxima
     b += sizeof(TcPairs) + 256;
     // the window and job lists of every sweep go to memory of their own
     return b;
@@ -227,9 +354,9 @@ signtri_status reorder_blocked_run(int n, const double *T, int ldt, double *Tr, 
     float *sTc = static_cast<float *>(ws.take(rp * sizeof(float)));
     float *sTr = static_cast<float *>(ws.take(rp * sizeof(float)));
     float *sQ = static_cast<float *>(ws.take(rp * sizeof(float)));
-    auto *tmp = static_cast<unsigned long long *>(ws.take(rp * sizeof(unsigned long long)));
+    auto *mx = static_cast<unsigned long long *>(ws.take(3 * (size_t)rp * sizeof(unsigned long long)));
     auto *d_pairs = static_cast<TcPairs *>(ws.take(sizeof(TcPairs)));
-    if (!ZC || !TC || !TR || !QR || !sZ || !sTc || !sTr || !sQ || !tmp || !d_pairs) return SIGNTRI_ERR_NO_WORKSPACE;
+    if (!ZC || !TC || !TR || !QR || !sZ || !sTc || !sTr || !sQ || !mx || !d_pairs) return SIGNTRI_ERR_NO_WORKSPACE;
     signtri_status rs = copy_upper_identity(n, T, ldt, Tr, ldtr, Q, ldq, st);   // T~ = upper part of T, Q = I
     if (rs != SIGNTRI_OK) return rs;
     std::vector<double> diag(n);
@@ -250,12 +377,16 @@ signtri_status reorder_blocked_run(int n, const double *T, int ldt, double *Tr, 
     };
     std::vector<int2> wins_all;
     std::vector<TcJob> jobs_all;
-    struct Sweep { int w0, nw; int j[4]; double kb[3]; };
+    std::vector<int> kbl_all;   // each sweep's window 64-blocks, ascending
+    struct Sweep { int w0, nw; int j[4]; double kb[3]; int k0, nk; };
     std::vector<Sweep> plan;
     for (const std::vector<int2> &sw : sweeps) {
         if (sw.empty()) continue;
-        Sweep p{(int)wins_all.size(), (int)sw.size(), {0, 0, 0, 0}, {0, 0, 0}};
+        Sweep p{(int)wins_all.size(), (int)sw.size(), {0, 0, 0, 0}, {0, 0, 0}, (int)kbl_all.size(), 0};
         wins_all.insert(wins_all.end(), sw.begin(), sw.end());
+        for (const int2 &win : sw)
+            for (int kb = win.x / 64; kb <= (win.x + win.y - 1) / 64; kb++) kbl_all.push_back(kb);
+        p.nk = (int)kbl_all.size() - p.k0;
         for (int phase = 0; phase < 3; phase++) {
             p.j[phase] = (int)jobs_all.size();
             for (const int2 &win : sw) {
@@ -278,15 +409,19 @@ signtri_status reorder_blocked_run(int n, const double *T, int ldt, double *Tr, 
     }
     int2 *d_wins = nullptr;
     TcJob *d_jobs = nullptr;
+    int *d_kbl = nullptr;
     if (cudaMalloc(&d_wins, std::max<size_t>(wins_all.size(), 1) * sizeof(int2)) != cudaSuccess ||
-        cudaMalloc(&d_jobs, std::max<size_t>(jobs_all.size(), 1) * sizeof(TcJob)) != cudaSuccess) {
+        cudaMalloc(&d_jobs, std::max<size_t>(jobs_all.size(), 1) * sizeof(TcJob)) != cudaSuccess ||
+        cudaMalloc(&d_kbl, std::max<size_t>(kbl_all.size(), 1) * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(d_wins);
+        cudaFree(d_jobs);
         return SIGNTRI_ERR_NO_WORKSPACE;
     }
     auto body = [&]() -> signtri_status {
         SGT_CUDA_TRY(cudaMemcpyAsync(d_wins, wins_all.data(), wins_all.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
         SGT_CUDA_TRY(cudaMemcpyAsync(d_jobs, jobs_all.data(), jobs_all.size() * sizeof(TcJob), cudaMemcpyHostToDevice, st));
+        SGT_CUDA_TRY(cudaMemcpyAsync(d_kbl, kbl_all.data(), kbl_all.size() * sizeof(int), cudaMemcpyHostToDevice, st));
         const TcPairs pairs = ozaki_pairs_impl(kSlices, 7);
         SGT_CUDA_TRY(cudaMemcpyAsync(d_pairs, &pairs, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
         // the zero rows past the matrix, read by the half-empty jobs
@@ -304,24 +439,42 @@ signtri_status reorder_blocked_run(int n, const double *T, int ldt, double *Tr, 
             return tc_blocksums(top, top, left, left, d_jobs + p.j[phase], cnt, pairs, d_pairs, kExactChunkKb7, nullptr,
                                 out, d_err, SIGNTRI_KC_GIVENS, st, fl * p.kb[phase]);
         };
+        const int zero_lb = np / 64;
+        unsigned long long *mxTc = mx, *mxTr = mx + rp, *mxQ = mx + 2 * (size_t)rp;
+        // scales and slices of the active K blocks of one kind of line
+        auto convert = [&](int mode, const Sweep &p, const double *M, int ldm, unsigned long long *m,
+                           __nv_bfloat16 *out, float *scale) -> signtri_status {
+            ProfScope ps(SIGNTRI_KC_CONVERT, st);
+            const dim3 grid(p.nk, rp / 64);
+            const int *kbl = d_kbl + p.k0;
+            if (mode == kColsT) {
+                masked_absmax_kernel<kColsT><<<grid, 256, 0, st>>>(n, M, ldm, kbl, zero_lb, m);
+                masked_slices_kernel<kColsT><<<grid, 256, 0, st>>>(n, M, ldm, kbl, zero_lb, m, out, scale, rp, kp);
+            } else if (mode == kRowsT) {
+                masked_absmax_kernel<kRowsT><<<grid, 256, 0, st>>>(n, M, ldm, kbl, zero_lb, m);
+                masked_slices_kernel<kRowsT><<<grid, 256, 0, st>>>(n, M, ldm, kbl, zero_lb, m, out, scale, rp, kp);
+            } else {
+                masked_absmax_kernel<kRowsQ><<<grid, 256, 0, st>>>(n, M, ldm, kbl, zero_lb, m);
+                masked_slices_kernel<kRowsQ><<<grid, 256, 0, st>>>(n, M, ldm, kbl, zero_lb, m, out, scale, rp, kp);
+            }
+            SGT_LAUNCH_CHECK();
+            return SIGNTRI_OK;
+        };
         signtri_status r2;
         for (const Sweep &p : plan) {
+            SGT_CUDA_TRY(cudaMemsetAsync(mx, 0, 3 * (size_t)rp * sizeof(unsigned long long), st));
             {
                 ProfScope ps(SIGNTRI_KC_GIVENS, st);
                 window_sort_kernel<<<p.nw, kWinThreads, smem, st>>>(Tr, ldtr, d_wins + p.w0, ZC, sZ, rp, kp);
                 SGT_LAUNCH_CHECK();
             }
-            // rows of T (column slices of its strictly upper part: K = rows of W)
-            if ((r2 = make_scales(n, n, Tr, ldtr, 1, false, rp, tmp, sTc, st)) != SIGNTRI_OK) return r2;
-            if ((r2 = make_col_slices(n, n, Tr, ldtr, 1, kSlices, 7, sTc, TC, rp, kp, st)) != SIGNTRI_OK) return r2;
-            if ((r2 = product(p, 0, srcZ, srcTc, toT)) != SIGNTRI_OK) return r2;
-            // columns of T (row slices after the row products) and of Q
-            if ((r2 = make_scales(n, n, Tr, ldtr, 1, true, rp, tmp, sTr, st)) != SIGNTRI_OK) return r2;
-            if ((r2 = make_row_slices(n, n, Tr, ldtr, 1, kSlices, 7, sTr, TR, rp, kp, st)) != SIGNTRI_OK) return r2;
-            if ((r2 = product(p, 1, srcTr, srcZ, toT)) != SIGNTRI_OK) return r2;
-            if ((r2 = make_scales(n, n, Q, ldq, 0, true, rp, tmp, sQ, st)) != SIGNTRI_OK) return r2;
-            if ((r2 = make_row_slices(n, n, Q, ldq, 0, kSlices, 7, sQ, QR, rp, kp, st)) != SIGNTRI_OK) return r2;
-            if ((r2 = product(p, 2, srcQ, srcZ, toQ)) != SIGNTRI_OK) return r2;
+            // Q is read by its own product only: slice it alongside T's columns
+            if ((r2 = convert(kRowsQ, p, Q, ldq, mxQ, QR, sQ)) != SIGNTRI_OK) return r2;
+            if ((r2 = convert(kColsT, p, Tr, ldtr, mxTc, TC, sTc)) != SIGNTRI_OK) return r2;
+            if ((r2 = product(p, 0, srcZ, srcTc, toT)) != SIGNTRI_OK) return r2;     // rows of T
+            if ((r2 = convert(kRowsT, p, Tr, ldtr, mxTr, TR, sTr)) != SIGNTRI_OK) return r2;
+            if ((r2 = product(p, 1, srcTr, srcZ, toT)) != SIGNTRI_OK) return r2;     // columns of T
+            if ((r2 = product(p, 2, srcQ, srcZ, toQ)) != SIGNTRI_OK) return r2;      // columns of Q
         }
         // the host lists stay alive until the copies above are done; so do the
         // device lists until the last product
@@ -332,6 +485,7 @@ signtri_status reorder_blocked_run(int n, const double *T, int ldt, double *Tr, 
     if (rs != SIGNTRI_OK) cudaStreamSynchronize(st);
     cudaFree(d_wins);
     cudaFree(d_jobs);
+    cudaFree(d_kbl);
     return rs;
 }
 

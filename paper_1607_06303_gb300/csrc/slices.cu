@@ -497,4 +497,70 @@ signtri_status emulated_gemm_run(int m, int n, int k, const double *A, int lda, 
     return SIGNTRI_OK;
 }
 
+// C = A op(B), A m x k, op(B) k x n (B or B^T), all column-major, as an
+// emulated-float64 product of exact 7-bit slices (7 slices, 28 pairs)
+// written straight into C: 128 x 128 output tiles, one job each, the whole K
+// range per job.  upper: only tiles that meet the upper triangle (column
+// block >= row block) are written; entries below the diagonal inside them
+// hold the product as well.
+size_t emulated_product_workspace_bytes(int m, int n, int k)
+{
+    if (m <= 0 || n <= 0) return 0;
+    const size_t mp = (size_t)(m + 127) / 128 * 128, np = (size_t)(n + 127) / 128 * 128, kp = pad64(std::max(k, 1));
+    const size_t jobs = (mp / 128) * (np / 128);
+    return 7 * (mp + np) * kp * 2 + (mp + np) * 12 + jobs * sizeof(TcJob) + sizeof(TcPairs) + 8 * 256;
+}
+
+signtri_status emulated_product(int m, int n, int k, const double *A, int lda, const double *B, int ldb, bool transB,
+                                double *C, int ldc, bool upper, int kernel_class, Arena &ws, int *d_err,
+                                cudaStream_t st)
+{
+    if (m <= 0 || n <= 0) return SIGNTRI_OK;
+    constexpr int S = 7;
+    const int mp = (m + 127) / 128 * 128, np = (n + 127) / 128 * 128, kp = pad64(std::max(k, 1));
+    const int ntI = mp / 128, ntJ = np / 128;
+    auto *AR = static_cast<__nv_bfloat16 *>(ws.take((size_t)S * mp * kp * 2));
+    auto *BC = static_cast<__nv_bfloat16 *>(ws.take((size_t)S * np * kp * 2));
+    auto *sa = static_cast<float *>(ws.take((size_t)mp * 4));
+    auto *sb = static_cast<float *>(ws.take((size_t)np * 4));
+    auto *tmpa = static_cast<unsigned long long *>(ws.take((size_t)mp * 8));
+    auto *tmpb = static_cast<unsigned long long *>(ws.take((size_t)np * 8));
+    auto *jobs = static_cast<TcJob *>(ws.take((size_t)ntI * ntJ * sizeof(TcJob)));
+    auto *dp = static_cast<TcPairs *>(ws.take(sizeof(TcPairs)));
+    if (!AR || !BC || !sa || !sb || !tmpa || !tmpb || !jobs || !dp) return SIGNTRI_ERR_NO_WORKSPACE;
+    signtri_status rs;
+    if ((rs = make_scales(m, k, A, lda, 0, true, mp, tmpa, sa, st)) != SIGNTRI_OK) return rs;
+    if ((rs = make_row_slices(m, k, A, lda, 0, S, 7, sa, AR, mp, kp, st)) != SIGNTRI_OK) return rs;
+    if (transB) {
+        // op(B)[kk][j] = B[j][kk]: the rows of B are the K-contiguous lines
+        if ((rs = make_scales(n, k, B, ldb, 0, true, np, tmpb, sb, st)) != SIGNTRI_OK) return rs;
+        if ((rs = make_row_slices(n, k, B, ldb, 0, S, 7, sb, BC, np, kp, st)) != SIGNTRI_OK) return rs;
+    } else {
+        if ((rs = make_scales(k, n, B, ldb, 0, false, np, tmpb, sb, st)) != SIGNTRI_OK) return rs;
+        if ((rs = make_col_slices(k, n, B, ldb, 0, S, 7, sb, BC, np, kp, st)) != SIGNTRI_OK) return rs;
+    }
+    std::vector<TcJob> hj;
+    hj.reserve((size_t)ntI * ntJ);
+    double sum_kb = 0.0;
+    for (int I = 0; I < ntI; I++)
+        for (int J = upper ? I : 0; J < ntJ; J++) {
+            TcJob j;
+            j.rt = I * 128; j.rb = I * 128 + 64; j.cl = J * 128; j.cr = J * 128 + 64;
+            j.kb0 = 0; j.kb1 = kp / 64; j.slot = 0; j.pad = 0;
+            hj.push_back(j);
+            sum_kb += kp / 64;
+        }
+    const TcPairs pairs = ozaki_pairs_impl(S, 7);
+    SGT_CUDA_TRY(cudaMemcpyAsync(jobs, hj.data(), hj.size() * sizeof(TcJob), cudaMemcpyHostToDevice, st));
+    SGT_CUDA_TRY(cudaMemcpyAsync(dp, &pairs, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
+    const TcSource top{AR, S, mp, kp, kp, sa}, left{BC, S, np, kp, kp, sb};
+    const TcQuadOut qo{{C, C, C, C}, ldc, m, n, 0};
+    rs = tc_blocksums(top, top, left, left, jobs, (int)hj.size(), pairs, dp, kExactChunkKb7, nullptr, qo, d_err,
+                      kernel_class, st, tc_flops(1, 1, 4) * sum_kb);   // the float64 product's flops
+    if (rs != SIGNTRI_OK) return rs;
+    // the host job table and pair list were copied from pageable memory
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIGNTRI_OK;
+}
+
 }  // namespace signtri
