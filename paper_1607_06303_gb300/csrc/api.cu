@@ -167,15 +167,35 @@ void work_estimates(int n, const ScanResult &r, double *w_ph, double *w_ps)
     *w_ps = w;
 }
 
-// Times predicted from the Section 3 work of what each variant executes:
-// Parlett-Higham runs the arithmetic-efficient form (Section 5.3: only the
-// sum each entry needs, exactly the useful count w_ph); Parlett-Sylvester
-// runs 12 n k flops of Givens rounds, n_- n_+ n of Sylvester solve and, when
-// k > 0, the back-transform products.
-// Plus launch latency: Parlett-Higham issues two launches per block
-// anti-diagonal; Parlett-Sylvester two per Givens round (at most n rounds
-// when swaps are needed) and two per Sylvester anti-diagonal.
+// Times predicted from the Section 3 work of what each variant executes,
+// plus the latency-bound parts, with constants measured on GB300 (float64
+// leaves and the windowed reorder, whose cost is not in the flop counts):
+//  * Parlett-Higham runs the arithmetic-efficient form (Section 5.3: only the
+//    sum each entry needs, exactly the useful count w_ph) at the float64
+//    product rate, and one off-diagonal leaf step per block column (about
+//    0.55 ms at b = 64, shorter for smaller leaves);
+//  * Parlett-Sylvester runs the Sylvester block sums (n_- n_+ n flops) and
+//    one in-block step per block anti-diagonal (about 0.4 ms); when k > 0,
+//    the reorder and the back-transform (emulated-float64 tensor-core
+//    products, about 6e13 float64 flop/s).  The windowed reorder (n >= 512)
+//    runs sweeps of windows of 128 at offsets 0 / 64: a negative moves at
+//    most 64 places a sweep, so there are about d / 64 sweeps, d = n_+ -
+//    (index of the first negative) the longest distance one travels.  A
+//    sweep costs its window launch (rounds and float64 rotations, growing
+//    with the swaps per window) plus the products and slicing of its about
+//    min(n_-, n / 256) active windows, each about 1.1e-8 n seconds.  The
+//    unblocked rounds (n < 512) cost 12 n k flops at the Givens rate and two
+//    launches per round.
 constexpr double kLaunchSeconds = 5e-6;
+constexpr double kPhLeafStepSeconds = 0.55e-3;
+constexpr double kSylvStepSeconds = 0.40e-3;
+constexpr double kEmulatedRate = 6e13;
+constexpr double kWindowProductSeconds = 1.1e-8;
+
+double window_launch_seconds(double kw)
+{
+    return std::fmin(0.95e-3, 3e-5 + 1.2e-6 * kw) + 6e-7 * std::fmax(0.0, kw - 770.0);
+}
 
 signtri_variant choose_variant(int n, const ScanResult &r)
 {
@@ -183,14 +203,22 @@ signtri_variant choose_variant(int n, const ScanResult &r)
     const double nb = std::ceil(nd / g_cutoff);
     double w_ph = 0.0, w_ps = 0.0;
     work_estimates(n, r, &w_ph, &w_ps);
-    const double t_ph = w_ph / g_rate_gemm + 2.0 * nb * kLaunchSeconds;
+    const double t_ph = w_ph / g_rate_gemm + nb * kPhLeafStepSeconds * g_cutoff / 64.0 + 2.0 * nb * kLaunchSeconds;
     const double np = r.n_pos, nm = r.n_neg, k = (double)r.swaps;
-    double bt = 0.0;
-    if (r.swaps > 0) bt = 2.0 * nd * std::fmin(np, nm) * (nd + std::fmax(np, nm));
-    const double rounds = r.swaps > 0 ? nd : 0.0;
-    const double sylv_steps = std::ceil(np / 64.0) + std::ceil(nm / 64.0);
-    const double t_ps = 12.0 * nd * k / g_rate_givens + (np * nm * nd + bt) / g_rate_gemm +
-                        2.0 * (rounds + sylv_steps) * kLaunchSeconds;
+    const double sylv_steps = std::ceil(np / 64.0) + std::ceil(nm / 64.0) - 1.0;
+    double t_ps = np * nm * nd / g_rate_gemm + sylv_steps * kSylvStepSeconds;
+    if (r.swaps > 0) {
+        t_ps += 2.0 * nd * std::fmin(np, nm) * (nd + std::fmax(np, nm)) / kEmulatedRate;
+        if (n >= kBlockedReorderMin) {
+            const double d = std::fmax(1.0, np - (double)r.first_neg);
+            const double sweeps = std::ceil(d / 64.0) + 1.0;
+            const double active = std::fmax(1.0, std::fmin(nm, nd / 256.0));
+            const double kw = std::fmin(4096.0, k / (sweeps * active));
+            t_ps += sweeps * (window_launch_seconds(kw) + kWindowProductSeconds * active * nd);
+        } else {
+            t_ps += 12.0 * nd * k / g_rate_givens + 2.0 * nd * kLaunchSeconds;
+        }
+    }
     return t_ps < t_ph ? SIGNTRI_PS_FP64 : SIGNTRI_PH_FP64_EFFICIENT;
 }
 

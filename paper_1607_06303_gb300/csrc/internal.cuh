@@ -59,7 +59,7 @@ struct ScanResult {
     long long swaps;       // #{i<j : t_ii < 0 < t_jj}
     long long same_terms;  // sum over equal-sign pairs i<j of (j-i-1)
     int bad_key;       // min over bad i of (4*i + kind), INT_MAX when none
-    int pad;
+    int first_neg;     // index of the first negative diagonal entry, n when none
 };
 
 // One matrix of a batch (device copy).

@@ -439,19 +439,36 @@ __device__ __forceinline__ void offdiag_leaf_body(int n, const double *__restric
     }
     __syncthreads();
 
+    // each entry's two in-block sums are split over four consecutive lanes
+    // (terms k = part mod 4) and reduced by shuffles, so that every warp
+    // shares the float64 work of an anti-diagonal step
+    static_assert(kThreads == 4 * 64 && B <= 64, "one entry slot per four lanes");
     const int nsteps = B + bj - 1;
+    const int part = threadIdx.x & 3, slot = threadIdx.x >> 2;
     for (int s = 0; s < nsteps; s++) {
         const int plo = max(0, B - 1 - s);
         const int phi = min(B - 1, B - 1 - s + bj - 1);
-        for (int p = plo + threadIdx.x; p <= phi; p += kThreads) {
-            const int q = s - (B - 1 - p);
-            const double up = srow[p], uq = scol[q];
-            const bool opp = (up + uq == 0.0);
+        const int p = plo + slot;
+        const bool live = p <= phi;
+        const int q = s - (B - 1 - p);
+        double up = 1.0, uq = 1.0;
+        if (live) {
+            up = srow[p];
+            uq = scol[q];
+        }
+        const bool opp = (up + uq == 0.0);
+        double a = 0.0, b = 0.0;
+        if (live) {
             const double *A = opp ? TI : UI;
             const double *Bm = opp ? TJ : UJ;
-            double a = 0.0, b = 0.0;
-            for (int k = p + 1; k < B; k++) a = fma(A[p + k * LD], V[k + q * LD], a);
-            for (int k = 0; k < q; k++) b = fma(V[p + k * LD], Bm[k + q * LD], b);
+            for (int k = p + 1 + part; k < B; k += 4) a = fma(A[p + k * LD], V[k + q * LD], a);
+            for (int k = part; k < q; k += 4) b = fma(V[p + k * LD], Bm[k + q * LD], b);
+        }
+        a += __shfl_xor_sync(0xffffffffu, a, 1);
+        b += __shfl_xor_sync(0xffffffffu, b, 1);
+        a += __shfl_xor_sync(0xffffffffu, a, 2);
+        b += __shfl_xor_sync(0xffffffffu, b, 2);
+        if (live && part == 0) {
             double v;
             if (opp) v = (C[p + q * LD] - a + b) / (TI[p + p * LD] - TJ[q + q * LD]);
             else     v = (C[p + q * LD] - a - b) / (up + uq);

@@ -229,17 +229,25 @@ sylv_leaf_kernel(int m, int p, const double *__restrict__ A, int lda, const doub
         Xs[i + j * LD] = c;
     }
     __syncthreads();
+    // anti-diagonal steps inside the block; each entry's two sums are split
+    // over four consecutive lanes (terms k = part mod 4) and reduced by
+    // shuffles, so that all warps share the float64 work of a step
     const int nsteps = bi + bj - 1;
+    const int part = threadIdx.x & 3, slot = threadIdx.x >> 2;   // 64 entry slots
     for (int st = 0; st < nsteps; st++) {
         const int plo = max(0, bi - 1 - st);
         const int phi = min(bi - 1, bi - 1 - st + bj - 1);
-        for (int pp = plo + threadIdx.x; pp <= phi; pp += kThreads) {
-            const int q = st - (bi - 1 - pp);
-            double a = 0.0, b = 0.0;
-            for (int k = pp + 1; k < bi; k++) a = fma(As[pp + k * LD], Xs[k + q * LD], a);
-            for (int k = 0; k < q; k++) b = fma(Xs[pp + k * LD], Bs[k + q * LD], b);
-            Xs[pp + q * LD] = (Xs[pp + q * LD] - a + b) / (As[pp + pp * LD] - Bs[q + q * LD]);
+        const int pp = plo + slot;
+        const bool live = pp <= phi;
+        const int q = st - (bi - 1 - pp);
+        double acc = 0.0;
+        if (live) {
+            for (int k = pp + 1 + part; k < bi; k += 4) acc = fma(-As[pp + k * LD], Xs[k + q * LD], acc);
+            for (int k = part; k < q; k += 4) acc = fma(Xs[pp + k * LD], Bs[k + q * LD], acc);
         }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (live && part == 0) Xs[pp + q * LD] = (Xs[pp + q * LD] + acc) / (As[pp + pp * LD] - Bs[q + q * LD]);
         __syncthreads();
     }
     for (int idx = threadIdx.x; idx < bi * bj; idx += kThreads) {

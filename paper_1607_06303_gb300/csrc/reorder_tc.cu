@@ -42,7 +42,7 @@ constexpr int kSlices = 7;                 // exact slices of 7 bits: float64 pr
 size_t window_smem_bytes()
 {
     return (size_t)kWin * kWinLD * sizeof(double) + 2 * (size_t)kMaxRot * sizeof(double) +
-           (size_t)kMaxRot * sizeof(short) + 2 * (size_t)kWin * sizeof(double);
+           (size_t)kMaxRot * sizeof(short);
 }
 
 // One window per CTA: stable partition of T[W, W] by swaps, then Z_W as the
@@ -59,11 +59,10 @@ window_sort_kernel(double *__restrict__ Tr, int ldt, const int2 *__restrict__ wi
     double *lc = B + kWin * kWinLD;                    // logged rotations (cs, sn, k), round by round
     double *ls = lc + kMaxRot;
     short *lk = reinterpret_cast<short *>(ls + kMaxRot);
-    double *rc = reinterpret_cast<double *>(lk + kMaxRot);   // this round's rotation at position k
-    double *rsn = rc + kWin;
-    __shared__ signed char sg[kWin], act[kWin];
+    __shared__ signed char sg[kWin];
+    __shared__ short pm[kWin];                        // log index of the round's pair holding position i, or -1
     __shared__ int roff[2 * kWin + 4];
-    __shared__ int nlog, nround, quiet;
+    __shared__ int nlog, nround, quiet[2];
     const int a = wins[blockIdx.x].x, w = wins[blockIdx.x].y;
     for (int idx = threadIdx.x; idx < kWin * kWin; idx += kWinThreads) {
         const int i = idx % kWin, j = idx / kWin;
@@ -74,87 +73,108 @@ window_sort_kernel(double *__restrict__ Tr, int ldt, const int2 *__restrict__ wi
     if (threadIdx.x == 0) {
         nlog = 0;
         nround = 0;
-        quiet = 0;
+        quiet[0] = quiet[1] = 0;
     }
     __syncthreads();
-    // odd-even rounds until two in a row swap nothing (at most w + 1 rounds)
-    for (int r = 0; quiet < 2 && r < 2 * kWin + 2; r++) {
-        if (threadIdx.x == 0) roff[r] = nlog;
-        for (int k = threadIdx.x; k < kWin; k += kWinThreads) {
-            const bool on = (k & 1) == (r & 1) && k + 1 < w && sg[k] < 0 && sg[k + 1] > 0;
-            act[k] = on ? 1 : 0;
-            if (on) {
-                const double aa = B[k + k * kWinLD], cc = B[(k + 1) + (k + 1) * kWinLD], bb = B[k + (k + 1) * kWinLD];
-                const double d = cc - aa, h = hypot(bb, d);
-                rc[k] = bb / h;
-                rsn[k] = d / h;
-            }
-        }
-        __syncthreads();
-        // log this round's rotations in position order
+    // odd-even rounds until two in a row swap nothing (at most w + 1 rounds).
+    // The count of quiet rounds is double-buffered: round r writes slot
+    // r & 1 while the loop test of round r reads slot (r - 1) & 1.
+    for (int r = 0; r < 2 * kWin + 2; r++) {
+        if (r > 0 && quiet[(r - 1) & 1] >= 2) break;
         if (threadIdx.x < 32) {
-            // warp 0: positions k = 4 lane .. 4 lane + 3, a prefix count by ballots
-            int c = 0, mine[4];
+            // warp 0 finds the round's pairs (positions 4 lane .. 4 lane + 3),
+            // logs their rotations in position order (a prefix count by
+            // shuffles) and marks both positions of each pair in pm
+            const int lane = threadIdx.x, base = nlog;
+            bool on[4];
+            int c = 0;
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                const int k = 4 * threadIdx.x + q;
-                mine[q] = k < w && act[k];
-                c += mine[q];
+                const int k = 4 * lane + q;
+                on[q] = (k & 1) == (r & 1) && k + 1 < w && sg[k] < 0 && sg[k + 1] > 0;
+                c += on[q];
             }
             int incl = c;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                if ((int)threadIdx.x >= o) incl += t;
+                if (lane >= o) incl += t;
             }
-            int e = nlog + incl - c;
+            int e = base + incl - c, mine[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++)
-                if (mine[q]) {
-                    const int k = 4 * threadIdx.x + q;
-                    lc[e] = rc[k];
-                    ls[e] = rsn[k];
+            for (int q = 0; q < 4; q++) {
+                mine[q] = -1;
+                if (on[q]) {
+                    // G's first column: the eigenvector of the entry moving up
+                    const int k = 4 * lane + q;
+                    const double aa = B[k + k * kWinLD], cc = B[(k + 1) + (k + 1) * kWinLD], bb = B[k + (k + 1) * kWinLD];
+                    const double d = cc - aa, h = hypot(bb, d);
+                    lc[e] = bb / h;
+                    ls[e] = d / h;
                     lk[e] = (short)k;
-                    e++;
+                    mine[q] = e++;
                 }
+            }
+            const int prev = __shfl_up_sync(0xffffffffu, mine[3], 1);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int left = q > 0 ? mine[q - 1] : (lane > 0 ? prev : -1);
+                pm[4 * lane + q] = (short)(mine[q] >= 0 ? mine[q] : left);
+            }
             const int total = __shfl_sync(0xffffffffu, incl, 31);
-            __syncwarp();
-            if (threadIdx.x == 0) {
-                nlog += total;
-                quiet = total ? 0 : quiet + 1;
+            if (lane == 0) {
+                roff[r] = base;
+                nlog = base + total;
+                quiet[r & 1] = total ? 0 : (r > 0 ? quiet[(r - 1) & 1] : 0) + 1;
                 nround = r + 1;
             }
         }
-        // G^T on rows k, k+1 (columns past the pair), then G on columns k, k+1
-        // (rows above the pair); the pairs of a round are disjoint and the
-        // two sides commute
-        for (int idx = threadIdx.x; idx < kWin * kWin; idx += kWinThreads) {
-            const int k = idx % kWin, j = idx / kWin;
-            if (!act[k] || j < k + 2 || j >= w) continue;
-            double *x0 = &B[k + j * kWinLD], *x1 = &B[(k + 1) + j * kWinLD];
-            const double u = *x0, v = *x1, c1 = rc[k], s1 = rsn[k];
-            *x0 = c1 * u + s1 * v;
-            *x1 = -s1 * u + c1 * v;
-        }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < kWin * kWin; idx += kWinThreads) {
-            const int i = idx % kWin, k = idx / kWin;
-            if (!act[k] || i >= k) continue;
-            double *x0 = &B[i + k * kWinLD], *x1 = &B[i + (k + 1) * kWinLD];
-            const double u = *x0, v = *x1, c1 = rc[k], s1 = rsn[k];
-            *x0 = u * c1 + v * s1;
-            *x1 = -u * s1 + v * c1;
-        }
-        __syncthreads();
-        // the exact swap of the 2 x 2 diagonal block (its coupling unchanged)
-        for (int k = threadIdx.x; k < kWin; k += kWinThreads)
-            if (act[k]) {
-                const double t0 = B[k + k * kWinLD];
-                B[k + k * kWinLD] = B[(k + 1) + (k + 1) * kWinLD];
-                B[(k + 1) + (k + 1) * kWinLD] = t0;
+        // the round's rotations, one item per (pair, position x): x right of
+        // the pair -- G^T on rows k, k+1 of column x (with G_q on columns x,
+        // x+1 as well when x starts pair q); x left of the pair -- G on
+        // columns k, k+1 of row x (rows inside a pair are done from that
+        // pair's side); x = k -- the exact swap of the 2 x 2 diagonal block,
+        // whose coupling is unchanged.  No two items touch the same entry.
+        const int e0 = roff[r], P = nlog - e0;
+        for (int idx = threadIdx.x; idx < P * kWin; idx += kWinThreads) {
+            const int e = e0 + idx / kWin, x = idx % kWin, k = lk[e];
+            if (x >= w) continue;
+            const double c1 = lc[e], s1 = ls[e];
+            if (x >= k + 2) {
+                const int q = pm[x];
+                if (q < 0) {
+                    double *x0 = &B[k + x * kWinLD], *x1 = &B[(k + 1) + x * kWinLD];
+                    const double u = *x0, v = *x1;
+                    *x0 = c1 * u + s1 * v;
+                    *x1 = -s1 * u + c1 * v;
+                } else if (lk[q] == x) {
+                    const double c2 = lc[q], s2 = ls[q];
+                    double *p00 = &B[k + x * kWinLD], *p10 = p00 + 1, *p01 = p00 + kWinLD, *p11 = p01 + 1;
+                    const double b00 = *p00, b10 = *p10, b01 = *p01, b11 = *p11;
+                    const double r00 = c1 * b00 + s1 * b10, r10 = -s1 * b00 + c1 * b10;
+                    const double r01 = c1 * b01 + s1 * b11, r11 = -s1 * b01 + c1 * b11;
+                    *p00 = r00 * c2 + r01 * s2;
+                    *p01 = -r00 * s2 + r01 * c2;
+                    *p10 = r10 * c2 + r11 * s2;
+                    *p11 = -r10 * s2 + r11 * c2;
+                }
+            } else if (x < k) {
+                if (pm[x] < 0) {
+                    double *x0 = &B[x + k * kWinLD], *x1 = &B[x + (k + 1) * kWinLD];
+                    const double u = *x0, v = *x1;
+                    *x0 = u * c1 + v * s1;
+                    *x1 = -u * s1 + v * c1;
+                }
+            } else if (x == k) {
+                double *d0 = &B[k + k * kWinLD], *d1 = &B[(k + 1) + (k + 1) * kWinLD];
+                const double t0 = *d0;
+                *d0 = *d1;
+                *d1 = t0;
                 sg[k] = 1;
                 sg[k + 1] = -1;
             }
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0) roff[nround] = nlog;

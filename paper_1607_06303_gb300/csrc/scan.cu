@@ -25,17 +25,17 @@ constexpr int kScanThreads = 1024;
 __device__ __forceinline__ void inertia_scan_body(int n, const double *__restrict__ T, int ldt, ScanResult *out)
 {
     __shared__ long long s_a[kScanThreads], s_b[kScanThreads], s_c[kScanThreads], s_d[kScanThreads];
-    __shared__ int s_bad[kScanThreads];
+    __shared__ int s_bad[kScanThreads], s_fneg[kScanThreads];
     const int tid = threadIdx.x;
     const int per = (n + kScanThreads - 1) / kScanThreads;
     const int lo = min(n, tid * per), hi = min(n, lo + per);
     long long cneg = 0, cpos = 0, sneg = 0, spos = 0;
-    int bad = INT_MAX;
+    int bad = INT_MAX, fneg = INT_MAX;
     for (int i = lo; i < hi; i++) {
         const double t = SGT_AT(T, ldt, i, i);
         if (!isfinite(t)) { if (bad == INT_MAX) bad = 4 * i + SIGNTRI_ERR_NONFINITE; }
         else if (t == 0.0) { if (bad == INT_MAX) bad = 4 * i + SIGNTRI_ERR_ZERO_EIGENVALUE; }
-        else if (t < 0.0) { cneg++; sneg += i; }
+        else if (t < 0.0) { cneg++; sneg += i; fneg = min(fneg, i); }
         else { cpos++; spos += i; }
     }
     s_a[tid] = cneg; s_b[tid] = cpos; s_c[tid] = sneg; s_d[tid] = spos;
@@ -56,13 +56,14 @@ __device__ __forceinline__ void inertia_scan_body(int n, const double *__restric
         else if (t > 0.0) { swaps += cn; same += cp * (long long)(i - 1) - sp; cp++; sp += i; }
     }
     __syncthreads();
-    s_a[tid] = swaps; s_b[tid] = same; s_bad[tid] = bad;
+    s_a[tid] = swaps; s_b[tid] = same; s_bad[tid] = bad; s_fneg[tid] = fneg;
     __syncthreads();
     for (int off = kScanThreads / 2; off > 0; off >>= 1) {
         if (tid < off) {
             s_a[tid] += s_a[tid + off];
             s_b[tid] += s_b[tid + off];
             s_bad[tid] = min(s_bad[tid], s_bad[tid + off]);
+            s_fneg[tid] = min(s_fneg[tid], s_fneg[tid + off]);
         }
         __syncthreads();
     }
@@ -72,7 +73,7 @@ __device__ __forceinline__ void inertia_scan_body(int n, const double *__restric
         out->swaps = s_a[0];
         out->same_terms = s_b[0];
         out->bad_key = s_bad[0];
-        out->pad = 0;
+        out->first_neg = s_fneg[0] == INT_MAX ? n : s_fneg[0];
     }
 }
 
