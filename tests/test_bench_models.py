@@ -89,7 +89,8 @@ def test_reference_arm_runs_on_rank_zero_only():
 
 def _cited_bench_commands():
     """The bench.py argument lists cited by the summaries under profiles/
-    (continuation lines joined; commands with placeholders skipped)."""
+    (continuation lines joined; commands with placeholders -- [optional]
+    parts or shell variables -- skipped)."""
     import glob
     import shlex
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -97,7 +98,7 @@ def _cited_bench_commands():
     for path in sorted(glob.glob(os.path.join(root, "profiles", "*.txt"))):
         text = open(path).read().replace("\\\n", " ")
         for line in text.splitlines():
-            if "python bench.py" not in line or "[" in line:
+            if "python bench.py" not in line or "[" in line or "$" in line:
                 continue
             rest = line.split("python bench.py", 1)[1]
             toks = []
