@@ -240,6 +240,27 @@ signtri_status signtri_inertia(int n, const double *T, int ldt, int *n_pos, int 
    calling host thread. */
 signtri_status signtri_get_info(signtri_info *out);
 
+/* ---- sign(A) from a real Schur form (Section 1; Algorithm 3's first step) --
+   The paper computes sign(A) of a general A as Q sign(T) Q^* from a Schur
+   decomposition A = Q T Q^*.  This call does the part after the
+   decomposition for a real Schur pair whose T is upper triangular (A with
+   real eigenvalues, none zero; e.g. the real Schur form of such an A from a
+   host LAPACK): S = Q U Q^T with U = sign(T) by `variant` (as sign_tri), then
+   W = U Q^T and S = Q W as emulated-float64 tensor-core products (7 exact
+   slices of 7 bits per row or column under power-of-two scales, error about
+   2^-45 of the product of the scales).  Q, T, S: n x n device pointers,
+   column-major, leading dimensions >= n; Q orthogonal is the caller's
+   promise (not checked); only T's upper triangle is read.  S must not share
+   an element with Q or T (SIGNTRI_ERR_BAD_ARG).  The Schur decomposition
+   itself, and complex Schur forms, are not provided.  Statuses as
+   sign_tri (SIGNTRI_ERR_ZERO_EIGENVALUE / NONFINITE for t_ii);
+   signtri_get_info reports the variant that ran.  Synchronous on `stream`;
+   with a caller workspace (signtri_set_workspace) it needs
+   signtri_sign_schur_workspace_bytes(n, variant) bytes. */
+signtri_status signtri_sign_schur(int n, const double *Q, int ldq, const double *T, int ldt, double *S, int lds,
+                                  signtri_variant variant, void *stream);
+size_t signtri_sign_schur_workspace_bytes(int n, signtri_variant variant);
+
 /* ---- Emulated float64 product on the tensor cores --------------------------
    C = A B (A m x k, B k x n, C m x n; device pointers, column-major) with
    float64-level accuracy from bf16 tensor-core products: each row of A and

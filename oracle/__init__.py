@@ -36,6 +36,9 @@ def lib():
         L.oracle_sign_tri_antidiag.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int,
                                                ctypes.c_int]
         L.oracle_sign_tri_antidiag.restype = ctypes.c_int
+        L.oracle_sign_schur.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int,
+                                        ctypes.c_int]
+        L.oracle_sign_schur.restype = ctypes.c_int
         L.oracle_max_threads.argtypes = []
         L.oracle_max_threads.restype = ctypes.c_int
         _lib = L
@@ -107,6 +110,21 @@ def sign_spectral(T):
     if st != OK:
         raise OracleError(st)
     return U
+
+
+def sign_schur(Q, T, *, threads=None):
+    """sign(A) = Q sign(T) Q^T for the real Schur pair A = Q T Q^T (Section 1:
+    the route through a Schur decomposition; Algorithm 3's first step)."""
+    Q = _colmajor(Q)
+    T = _colmajor(T)
+    if Q.shape != T.shape:
+        raise ValueError("Q and T must have the same shape")
+    n = T.shape[0]
+    S = np.zeros((n, n), dtype=np.float64, order="F")
+    st = lib().oracle_sign_schur(n, _ptr(Q), max(n, 1), _ptr(T), max(n, 1), _ptr(S), max(n, 1), int(threads or 0))
+    if st != OK:
+        raise OracleError(st)
+    return S
 
 
 def max_threads():

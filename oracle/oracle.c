@@ -28,6 +28,12 @@
  *                          entries of one anti-diagonal may run in parallel
  *                          (OpenMP).  The result is bit-identical to
  *                          oracle_sign_tri (a test checks this).
+ *   oracle_sign_schur      The Schur route of Section 1 (and Algorithm 3's
+ *                          first step) for a real Schur pair: with
+ *                          A = Q T Q^T, Q orthogonal, T upper triangular,
+ *                          sign(A) = Q U Q^T where U = sign(T) from
+ *                          oracle_sign_tri_antidiag; then W = U Q^T and
+ *                          S = Q W, each entry one plain sum over k ascending.
  *   oracle_sign_spectral   Brute force from the definition in Section 1:
  *                          sign(T) = Z sign(D) Z^{-1}, with Z the (unit upper
  *                          triangular) eigenvector matrix of T, in long double.
@@ -237,6 +243,47 @@ int oracle_sign_spectral(int n, const double *T, int ldt, double *U, int ldu)
             AT(U, ldu, i, j) = (i <= j) ? (double)s : 0.0;
         }
     return ORACLE_OK;
+}
+
+int oracle_sign_schur(int n, const double *Q, int ldq, const double *T, int ldt, double *S, int lds, int nthreads)
+{
+    if (n < 0 || ldq < (n > 1 ? n : 1) || lds < (n > 1 ? n : 1)) return ORACLE_BAD_ARG;
+    if (n > 0 && (Q == NULL || S == NULL)) return ORACLE_BAD_ARG;
+    size_t nn = (size_t)n * (size_t)n;
+    double *U = (double *)calloc(nn > 0 ? nn : 1, sizeof(double));
+    double *W = (double *)calloc(nn > 0 ? nn : 1, sizeof(double));
+    if (!U || !W) { free(U); free(W); return ORACLE_BAD_ARG; }
+    int st = oracle_sign_tri_antidiag(n, T, ldt, U, n > 1 ? n : 1, nthreads);
+    if (st == ORACLE_OK) {
+        /* W(:, j) = sum_k U(:, k) Q(j, k)  (W = U Q^T) */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+        for (int j = 0; j < n; j++) {
+            double *w = W + (size_t)j * n;
+            for (int k = 0; k < n; k++) {
+                const double q = AT(Q, ldq, j, k);
+                const double *u = U + (size_t)k * n;
+                for (int i = 0; i < n; i++) w[i] = w[i] + u[i] * q;
+            }
+        }
+        /* S(:, j) = sum_k Q(:, k) W(k, j)  (S = Q W) */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+        for (int j = 0; j < n; j++) {
+            double *sc = &AT(S, lds, 0, j);
+            for (int i = 0; i < n; i++) sc[i] = 0.0;
+            for (int k = 0; k < n; k++) {
+                const double wkj = W[(size_t)j * n + k];
+                const double *q = &AT(Q, ldq, 0, k);
+                for (int i = 0; i < n; i++) sc[i] = sc[i] + q[i] * wkj;
+            }
+        }
+    }
+    free(U);
+    free(W);
+    return st;
 }
 
 int oracle_max_threads(void)

@@ -714,6 +714,58 @@ signtri_status signtri_gemm_emulated(int m, int n, int k, const double *A, int l
     return *s->err_host ? SIGNTRI_ERR_TIMEOUT : SIGNTRI_OK;
 }
 
+// W = U Q^T (n x n) then S = Q W, after U = sign(T) was written into S
+static size_t schur_products_bytes(int n)
+{
+    return (size_t)n * n * sizeof(double) + 256 + emulated_product_workspace_bytes(n, n, n);
+}
+
+size_t signtri_sign_schur_workspace_bytes(int n, signtri_variant v)
+{
+    if (n < 0 || !valid_variant(v)) return 0;
+    std::lock_guard<std::mutex> lk(g_mu);
+    return std::max(workspace_need(n, v, g_cutoff, -1), schur_products_bytes(n));
+}
+
+signtri_status signtri_sign_schur(int n, const double *Q, int ldq, const double *T, int ldt, double *S, int lds,
+                                  signtri_variant v, void *stream)
+{
+    reset_info(n);
+    if (n < 0 || !valid_variant(v)) return SIGNTRI_ERR_BAD_ARG;
+    if (n == 0) return SIGNTRI_OK;
+    if (!Q || !T || !S || ldq < n || ldt < n || lds < n) return SIGNTRI_ERR_BAD_ARG;
+    if (blocks_overlap(T, ldt, n, n, S, lds, n, n) || blocks_overlap(Q, ldq, n, n, S, lds, n, n))
+        return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // U = sign(T), held in S until the second product overwrites it
+    rs = sign_tri_locked(n, T, ldt, S, lds, v, st, *s);
+    if (rs != SIGNTRI_OK) return rs;
+    if (g_info.n_neg == 0 || g_info.n_pos == 0) {
+        // U = +-I, so S = +-Q Q^T = +-I for orthogonal Q: left exact
+        SGT_CUDA_TRY(cudaStreamSynchronize(st));
+        return SIGNTRI_OK;
+    }
+    Arena ws;
+    rs = get_workspace(*s, schur_products_bytes(n), ws);
+    if (rs != SIGNTRI_OK) return rs;
+    double *W = static_cast<double *>(ws.take((size_t)n * n * sizeof(double)));
+    if (!W) return SIGNTRI_ERR_NO_WORKSPACE;
+    const size_t mark = ws.used;
+    SGT_CUDA_TRY(cudaMemsetAsync(s->err_dev, 0, sizeof(int), st));
+    rs = emulated_product(n, n, n, S, lds, Q, ldq, true, W, n, false, SIGNTRI_KC_GEMM_F64, ws, s->err_dev, st);
+    if (rs != SIGNTRI_OK) return rs;
+    ws.used = mark;
+    rs = emulated_product(n, n, n, Q, ldq, W, n, false, S, lds, false, SIGNTRI_KC_GEMM_F64, ws, s->err_dev, st);
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaMemcpyAsync(s->err_host, s->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    return *s->err_host ? SIGNTRI_ERR_TIMEOUT : SIGNTRI_OK;
+}
+
 signtri_status signtri_sylvester(int m, int p, const double *A, int lda, const double *B, int ldb, const double *C,
                                  int ldc, double *X, int ldx, void *stream)
 {

@@ -59,6 +59,28 @@ def make_T(n: int, p: float = 0.5, seed: int = 0, order: str = "random",
     return T
 
 
+def make_orthogonal(n: int, seed: int = 0) -> np.ndarray:
+    """Seeded n x n orthogonal matrix (column-major float64): the Q factor of
+    a standard normal matrix, columns signed so that R's diagonal is
+    positive (Haar-distributed)."""
+    if n < 0:
+        raise ValueError("n must be >= 0")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    G = rng.standard_normal((n, n))
+    if n == 0:
+        return np.zeros((0, 0), order="F")
+    Q, R = np.linalg.qr(G)
+    d = np.sign(np.diag(R))
+    d[d == 0] = 1.0
+    return np.asfortranarray(Q * d)
+
+
+def make_schur_pair(n: int, p: float = 0.5, seed: int = 0, order: str = "random"):
+    """A real Schur pair (Q, T): T from make_T, Q from make_orthogonal, so
+    that A = Q T Q^T has T's (real) eigenvalues."""
+    return make_orthogonal(n, seed + 7919), make_T(n, p, seed=seed, order=order)
+
+
 def make_T_schur(n: int, seed: int = 0, n_neg: int = None) -> np.ndarray:
     """The paper's workload (Section 6): the real part of the complex Schur
     form of a random n x n matrix with entries uniform in [-50, 50]; inertia

@@ -103,6 +103,8 @@ _SIGNATURES = {
     "signtri_set_variant_table": (_I, [ctypes.POINTER(_I), _I]),
     "signtri_batched_cache_stats": (_I, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "signtri_selftest_wait": (_I, [_I, ctypes.c_longlong, _VP]),
+    "signtri_sign_schur": (_I, [_I, _VP, _I, _VP, _I, _VP, _I, _I, _VP]),
+    "signtri_sign_schur_workspace_bytes": (_SZ, [_I, _I]),
 }
 
 SIGNTRI_NOALLOC_MAX_N = 1024
@@ -352,6 +354,33 @@ def sign(Tt, variant=Variant.AUTO, out=None, stream=None, check=True):
     if check and st != 0:
         raise SignTriError(st, "sign_tri")
     return Ut
+
+
+def signtri_sign_schur(n, Q_ptr, ldq, T_ptr, ldt, S_ptr, lds, variant=Variant.AUTO, stream=None) -> int:
+    return load().signtri_sign_schur(n, Q_ptr or None, ldq, T_ptr or None, ldt, S_ptr or None, lds, int(variant),
+                                     stream or None)
+
+
+def signtri_sign_schur_workspace_bytes(n, variant=Variant.AUTO) -> int:
+    return load().signtri_sign_schur_workspace_bytes(n, int(variant))
+
+
+def sign_schur(Qt, Tt, variant=Variant.AUTO, out=None, stream=None, check=True):
+    """S = Q sign(T) Q^T from a real Schur pair (CUDA float64 tensors in the
+    layout above, Q orthogonal, T upper triangular).  Returns S."""
+    import torch
+    check_operands(Tt, out)
+    check_operands(Qt, out)
+    n = Tt.shape[0]
+    if tuple(Qt.shape) != tuple(Tt.shape) or Qt.device != Tt.device:
+        raise ValueError("Q and T must be n x n on the same device")
+    St = out if out is not None else torch.empty_like(Tt)
+    with torch.cuda.device(Tt.device):
+        st = signtri_sign_schur(n, Qt.data_ptr(), max(n, 1), Tt.data_ptr(), max(n, 1), St.data_ptr(), max(n, 1),
+                                variant, _stream_handle(stream))
+    if check and st != 0:
+        raise SignTriError(st, "signtri_sign_schur")
+    return St
 
 
 def to_device(T_colmajor, device="cuda"):

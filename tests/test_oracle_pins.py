@@ -187,3 +187,50 @@ def test_flop_count_closed_forms(oracle_mod, n):
     Ta = np.diag(d) + np.triu(np.ones((n, n)), 1)
     expect = sum((n - g) * (g - 1) * (4 if g % 2 else 2) for g in range(1, n))
     assert oracle_mod.useful_flops(Ta) == expect
+
+
+# ---- the Schur route (Section 1; Algorithm 3's first step) ----------------
+
+@pytest.mark.parametrize("n,p", [(5, 0.4), (20, 0.5), (60, 0.3)])
+def test_sign_schur_vs_signm(oracle_mod, n, p):
+    # A = Q T Q^T with orthogonal Q: sign(A) from scipy's own routine on A,
+    # which knows nothing of the Schur pair (a transposed Q, or U applied on
+    # the wrong side, fails this)
+    sl = pytest.importorskip("scipy.linalg")
+    from paper_1607_06303_gb300.inputs import make_schur_pair
+    Q, T = make_schur_pair(n, p, seed=n)
+    A = Q @ T @ Q.T
+    S = oracle_mod.sign_schur(Q, T)
+    ref = sl.signm(A)
+    assert np.linalg.norm(S - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_sign_schur_real_schur_of_A(oracle_mod):
+    # the use the route is for: A with real eigenvalues, its real Schur form
+    # from LAPACK, against the spectral definition V sign(L) V^{-1}
+    sl = pytest.importorskip("scipy.linalg")
+    rng = np.random.Generator(np.random.PCG64(5))
+    n = 40
+    V = np.eye(n) + 0.3 * rng.standard_normal((n, n)) / math.sqrt(n)
+    lam = rng.uniform(0.5, 2.0, n) * np.where(rng.random(n) < 0.4, -1.0, 1.0)
+    A = V @ np.diag(lam) @ np.linalg.inv(V)
+    T, Z = sl.schur(A, output="real")
+    assert np.allclose(np.tril(T, -1), 0.0, atol=1e-12)   # real spectrum: T triangular
+    S = oracle_mod.sign_schur(Z, np.triu(T))
+    ref = V @ np.diag(np.sign(lam)) @ np.linalg.inv(V)
+    assert np.linalg.norm(S - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("n,p", [(1, 0.0), (2, 0.5), (33, 0.5), (64, 0.1)])
+def test_sign_schur_invariants(oracle_mod, n, p):
+    from paper_1607_06303_gb300.inputs import make_schur_pair
+    Q, T = make_schur_pair(n, p, seed=3 * n + 1)
+    A = Q @ T @ Q.T
+    S = oracle_mod.sign_schur(Q, T)
+    I = np.eye(n)
+    assert np.linalg.norm(S @ S - I) <= 1e-12 * max(1.0, np.linalg.norm(S) ** 2)
+    assert np.linalg.norm(A @ S - S @ A) <= 1e-12 * np.linalg.norm(A) * np.linalg.norm(S)
+    npos = int(np.sum(np.diag(T) > 0))
+    assert abs(np.trace(S) - (npos - (n - npos))) <= 1e-10 * n
+    # Q = I reduces to the triangular oracle exactly
+    assert np.array_equal(oracle_mod.sign_schur(np.eye(n), T), oracle_mod.sign_tri(T))
