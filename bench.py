@@ -38,15 +38,29 @@ if ROOT not in sys.path:
 METRIC = "sign(T) seconds & useful GFLOP/s at n=16384: mixed+refine vs FP64, ≤1e-12 err"
 UNIT = "GFLOP/s"
 
-# ncu DRAM traffic of the dominant kernel, keyed by (class, sha256 of the
-# source file it came from) and reported only while that source is unchanged
-# (captures summarised under profiles/): for block_sums_tc the ratio of
-# dram__bytes_read.sum + dram__bytes_write.sum to the algorithmic operand
-# bytes of the same launches, for the other classes bytes per launch.
-# The sweeps' launches that share panels side by side cannot be measured this
-# way (ncu serialises them); the unpaired launches' ratio, 1.054, is in
-# profiles/tc_blocksum_sweep_traffic_n4096.txt.
-TRAFFIC = {}
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch
+# of a kernel class, averaged over the class's launches of one solve, from
+# one capture of this script's workload (summarised under profiles/),
+# keyed by (class, sha256 of the kernel and job-list sources, n, p, order,
+# variant): reported only while those sources are unchanged and for that
+# workload, else null.  The capture serialises launches, so classes whose
+# launches run side by side in the timed solve (the sweeps' look-ahead
+# pairs, which share operand panels through L2) read more there than here.
+TRAFFIC_SOURCES = ("paper_1607_06303_gb300/csrc/tc_gemm.cu", "paper_1607_06303_gb300/csrc/mixed.cu")
+TRAFFIC = {
+    # n = 16384, p = 0.5 random, PH_MIXED_FP16 (profiles/launches_mixed_n16384.txt)
+    ("residual", "59f76311a78493eb"): 34.876e9,
+    ("block_sums_tc", "59f76311a78493eb"): 639.0e6,
+}
+
+
+def traffic_key(cls, n, p, order, variant):
+    h = hashlib.sha256()
+    for rel in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    h.update(("%d %g %s %s" % (n, p, order, variant)).encode())
+    return (cls, h.hexdigest()[:16])
 
 
 def parse_args(argv=None):
@@ -209,11 +223,6 @@ def h2d_bytes(n, panel=128):
     """Bytes sign_tri_host copies to the device: T's upper triangle by column
     panels of `panel` columns, each from row 0 to its last column."""
     return sum(8 * min(panel, n - j0) * min(n, j0 + panel) for j0 in range(0, n, panel))
-
-
-def src_sha(rel):
-    with open(os.path.join(ROOT, rel), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
 
 
 def run_batched(args):
@@ -432,9 +441,8 @@ def main():
             avg_ms = per_class[cls]["device_ms"] / launches_c
             ach = per_launch / (avg_ms * 1e-3) / 1e12
             peak = fp64_peak / 1e3
-            sha = src_sha("paper_1607_06303_gb300/csrc/ph_fp64.cu")
             return {"class": cls, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": TRAFFIC.get(("block_sums_f64", sha)),
+                    "frac": ach / peak, "traffic": TRAFFIC.get(traffic_key(cls, n, args.p, args.order, variant.name)),
                     "kernel": ("ph_gemm_split_kernel (float64 DFMA, one sum per entry)" if efficient
                                else "ph_gemm_kernel (float64 DFMA block sums)"),
                     "peak_source": "float64 FMA issue rate measured live by signtri_probe_fp64_peak (no FP64 "
@@ -460,11 +468,10 @@ def main():
             ach = per_launch / (avg_ms * 1e-3) / 1e12
             bytes_launch = bytes_all / launches_c
             ach_b = bytes_launch / (avg_ms * 1e-3) / 1e9
-            sha = src_sha("paper_1607_06303_gb300/csrc/tc_gemm.cu")
-            traffic = TRAFFIC.get((cls, sha))
             fp16 = variant == st.Variant.PH_MIXED_FP16
             return {"class": cls, "bound": "tensor", "achieved": ach, "peak": peak_t, "unit": "TFLOP/s",
-                    "frac": ach / peak_t, "traffic": None if traffic is None else traffic * bytes_launch,
+                    "frac": ach / peak_t,
+                    "traffic": TRAFFIC.get(traffic_key(cls, n, args.p, args.order, variant.name)),
                     "kernel": "tc_blocksum_kernel (tcgen05 %s, sweep block sums, blocked slice layout)"
                               % ("fp16, two-term split" if fp16 else "bf16 split"),
                     "algorithmic_flops_per_launch": per_launch,
@@ -487,9 +494,8 @@ def main():
             per_launch = flops_all / launches_c
             avg_ms = per_class[cls]["device_ms"] / launches_c
             ach = per_launch / (avg_ms * 1e-3) / 1e12
-            sha = src_sha("paper_1607_06303_gb300/csrc/tc_gemm.cu")
             return {"class": cls, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": TRAFFIC.get((cls, sha)),
+                    "frac": ach / peak, "traffic": TRAFFIC.get(traffic_key(cls, n, args.p, args.order, variant.name)),
                     "kernel": "tc_pair2_kernel / tc_blocksum_kernel (tcgen05 bf16, emulated-float64 residual "
                               "and probe products)",
                     "algorithmic_flops_per_launch": per_launch,
