@@ -40,16 +40,25 @@ extern "C" {
 typedef enum {
     /* Choose Parlett-Higham (its arithmetic-efficient form,
        SIGNTRI_PH_FP64_EFFICIENT) or Parlett-Sylvester per input from the
-       work estimates of Section 3 (inertia and swap count).  In
-       sign_tri_batched, AUTO picks Parlett-Sylvester when no swaps are
-       needed and the batched Parlett-Higham (efficient form) otherwise. */
+       work estimates of Section 3 (inertia, swap count, and the index of
+       the first negative, which bounds the reorder's sweeps) turned into
+       times with rates and latencies measured on GB300.  In
+       sign_tri_batched, AUTO follows the variant table (signtri_autotune):
+       by default Parlett-Sylvester when no swaps are needed and the batched
+       Parlett-Higham (efficient form) otherwise. */
     SIGNTRI_AUTO = 0,
     /* Recursive Parlett-Higham (Algorithms 3-6), float64 throughout; block
        sums in matrix-multiply form (both X and Y for every entry). */
     SIGNTRI_PH_FP64 = 1,
     /* Parlett-Sylvester for the sign function (Section 2, Section 3,
        Section 5.1): reorder by sign with adjacent Givens swaps, solve
-       T11 X - X T22 = 2 T12, transform back. */
+       T11 X - X T22 = 2 T12, transform back.  From n = 512 on the swaps run
+       by windows of 128 (each window's rotations accumulated into one
+       orthogonal factor and applied to the rest of T and Q as
+       emulated-float64 tensor-core products); the back-transform's two
+       products are emulated-float64 too (7 exact slices of 7 bits per row
+       or column, about 2^-45 of the product of the scales).  Float64
+       accuracy in the normwise sense; the diagonal of U is exact. */
     SIGNTRI_PS_FP64 = 2,
     /* Parlett-Higham with tensor-core block updates of about fp32 accuracy,
        then float64 refinement of both defining equations.  tcgen05 has no
@@ -290,7 +299,11 @@ signtri_status signtri_gemm_emulated(int m, int n, int k, const double *A, int l
    column-major; T is only read (its upper triangle), Tr's strictly lower part
    is written as 0.  Tr and Q share no element with T or with each other
    (SIGNTRI_ERR_BAD_ARG).  Synchronous on `stream` (the swap schedule is
-   built on the host from the diagonal signs).  swaps may be NULL. */
+   built on the host from the diagonal signs).  swaps may be NULL.  For
+   n < 512 the swaps run as odd-even rounds applied in float64; from 512 on
+   as sweeps of windows of 128 (offsets 0 and 64), each window partitioned in
+   shared memory by the same swaps and its accumulated factor applied to the
+   rest of T and Q by emulated-float64 tensor-core products. */
 signtri_status signtri_reorder_by_sign(int n, const double *T, int ldt, double *Tr, int ldtr,
                                        double *Q, int ldq, long long *swaps, void *stream);
 

@@ -4,10 +4,13 @@
 // 1. Low-precision solve.  The block anti-diagonal schedule of the float64
 //    path (Algorithms 4-6 reordered, blocks of 64), with the block sums
 //      X_IJ = sum_K U_IK T_KJ - T_IK U_KJ,   Y_IJ = sum_K U_IK U_KJ
-//    formed on the tensor cores (tc_gemm.cu) from bf16 splits of U and T:
-//    one bf16 term (BF16 variant) or a three-term split hi + mid + lo with the
-//    six products of s + t <= 2 (about fp32 accuracy, the "FP32" variant);
-//    in-block recurrences (Algorithm 6, 1x1 case) in fp32.
+//    formed on the tensor cores (tc_gemm.cu) from 16-bit splits of U and T:
+//    one bf16 term (BF16 variant), a three-term bf16 split hi + mid + lo with
+//    the six products of s + t <= 2 (about fp32 accuracy, the "FP32"
+//    variant), or a two-term fp16 split hi + lo with the three products of
+//    s + t <= 1 (about 2^-21; T, U and the correction scaled by powers of two
+//    into fp16's range, the FP16 variant); in-block recurrences (Algorithm 6,
+//    1x1 case) in fp32, a 64-row tile solved by 16 x 16 sub-blocks.
 // 2. Refinement.  With U = U0 + E and E strictly upper triangular, UT = TU
 //    and U^2 = I become, entry by entry (i < j):
 //      signs differ: (t_ii - t_jj) e_ij = -Rc_ij + sum_{i<k<j} (e_ik t_kj - t_ik e_kj)

@@ -16,7 +16,8 @@
 //     multiplications commute), so the stable partition runs as odd-even
 //     transposition rounds: in round r every pair (k, k+1), k = r mod 2, with
 //     a negative above a positive is swapped at once.  The total number of
-//     swaps is k = #{i<j : t_ii < 0 < t_jj}, the minimum (Section 3).
+//     swaps is k = #{i<j : t_ii < 0 < t_jj}, the minimum (Section 3).  From
+//     n = 512 on the same swaps run by windows instead (reorder_tc.cu).
 //  2. Triangular Sylvester solve A X - X B = C by the element recurrence
 //     (a_ii - b_jj) x_ij = c_ij - sum_{k>i} a_ik x_kj + sum_{k<j} x_ik b_kj,
 //     blocked: b x b blocks by anti-diagonal (bottom-left first), float64 block
@@ -24,8 +25,10 @@
 //     the recurrence inside each block.
 //  3. Back-transform: with Q = [Q1 Q2] (n x n_+, n x n_-),
 //     Q U~ Q^T = I + (Q1 X - 2 Q2) Q2^T = -I + Q1 (2 Q1^T + X Q2^T);
-//     the form with the smaller inner dimension is used, only the upper
-//     triangle is formed, the diagonal is set to sign(t_ii) exactly.
+//     the form with the smaller inner dimension is used, as two
+//     emulated-float64 tensor-core products (slices.cu), only the tiles that
+//     meet the upper triangle of U are formed, and the diagonal is set to
+//     sign(t_ii) exactly.
 #include <algorithm>
 #include <vector>
 
