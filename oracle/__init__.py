@@ -39,6 +39,10 @@ def lib():
         L.oracle_sign_schur.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int,
                                         ctypes.c_int]
         L.oracle_sign_schur.restype = ctypes.c_int
+        L.oracle_sign_tri_complex.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int]
+        L.oracle_sign_tri_complex.restype = ctypes.c_int
+        L.oracle_sign_schur_complex.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int]
+        L.oracle_sign_schur_complex.restype = ctypes.c_int
         L.oracle_max_threads.argtypes = []
         L.oracle_max_threads.restype = ctypes.c_int
         _lib = L
@@ -122,6 +126,40 @@ def sign_schur(Q, T, *, threads=None):
     n = T.shape[0]
     S = np.zeros((n, n), dtype=np.float64, order="F")
     st = lib().oracle_sign_schur(n, _ptr(Q), max(n, 1), _ptr(T), max(n, 1), _ptr(S), max(n, 1), int(threads or 0))
+    if st != OK:
+        raise OracleError(st)
+    return S
+
+
+def _ccolmajor(M):
+    M = np.asarray(M, dtype=np.complex128)
+    if M.ndim != 2 or M.shape[0] != M.shape[1]:
+        raise ValueError("matrix must be square")
+    return np.asfortranarray(M)
+
+
+def sign_tri_complex(T):
+    """sign(T) of a complex upper triangular T (complex128): u_ii =
+    sign(Re t_ii), then Eqs. 1 and 2 entry by entry (Algorithm 3)."""
+    T = _ccolmajor(T)
+    n = T.shape[0]
+    U = np.zeros((n, n), dtype=np.complex128, order="F")
+    st = lib().oracle_sign_tri_complex(n, _ptr(T), max(n, 1), _ptr(U), max(n, 1))
+    if st != OK:
+        raise OracleError(st)
+    return U
+
+
+def sign_schur_complex(Q, T):
+    """sign(A) = Q sign(T) Q^H for a complex Schur pair A = Q T Q^H (Section
+    1's route; Algorithm 3's first step)."""
+    Q = _ccolmajor(Q)
+    T = _ccolmajor(T)
+    if Q.shape != T.shape:
+        raise ValueError("Q and T must have the same shape")
+    n = T.shape[0]
+    S = np.zeros((n, n), dtype=np.complex128, order="F")
+    st = lib().oracle_sign_schur_complex(n, _ptr(Q), max(n, 1), _ptr(T), max(n, 1), _ptr(S), max(n, 1))
     if st != OK:
         raise OracleError(st)
     return S

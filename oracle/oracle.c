@@ -34,6 +34,15 @@
  *                          sign(A) = Q U Q^T where U = sign(T) from
  *                          oracle_sign_tri_antidiag; then W = U Q^T and
  *                          S = Q W, each entry one plain sum over k ascending.
+ *   oracle_sign_tri_complex, oracle_sign_schur_complex
+ *                          The same substitution and route for a complex
+ *                          upper triangular T (the paper's Schur form is
+ *                          complex in general, Algorithm 3's first step):
+ *                          u_ii = sign(Re t_ii) (Section 1: sign is defined
+ *                          off the imaginary axis), then Eq. 1 / Eq. 2 entry
+ *                          by entry in the order of oracle_sign_tri, in C99
+ *                          complex arithmetic; S = Q U Q^H for unitary Q.
+ *                          Matrices interleaved (re, im) column-major.
  *   oracle_sign_spectral   Brute force from the definition in Section 1:
  *                          sign(T) = Z sign(D) Z^{-1}, with Z the (unit upper
  *                          triangular) eigenvector matrix of T, in long double.
@@ -42,6 +51,7 @@
  * Status codes: 0 ok, 1 bad argument, 2 a diagonal entry is zero (sign(0) is
  * undefined, Section 1), 3 a diagonal entry is NaN or infinite.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -277,6 +287,90 @@ int oracle_sign_schur(int n, const double *Q, int ldq, const double *T, int ldt,
             for (int k = 0; k < n; k++) {
                 const double wkj = W[(size_t)j * n + k];
                 const double *q = &AT(Q, ldq, 0, k);
+                for (int i = 0; i < n; i++) sc[i] = sc[i] + q[i] * wkj;
+            }
+        }
+    }
+    free(U);
+    free(W);
+    return st;
+}
+
+/*
+ * Complex T (interleaved re, im; element (i,j) at 2 (i + j ld)).  Status 2
+ * when some Re t_ii == 0 (sign undefined on the imaginary axis, Section 1),
+ * 3 when some t_ii is not finite.  Per entry the arithmetic of
+ * oracle_sign_tri with complex operands: for differing signs the divisor
+ * t_ii - t_jj has real parts of opposite sign, hence is nonzero.
+ */
+#define CAT(M, ld, i, j) (((double complex *)(M))[(size_t)(i) + (size_t)(j) * (size_t)(ld)])
+
+int oracle_sign_tri_complex(int n, const double *T, int ldt, double *U, int ldu)
+{
+    if (n < 0 || ldt < (n > 1 ? n : 1) || ldu < (n > 1 ? n : 1)) return ORACLE_BAD_ARG;
+    if (n > 0 && (T == NULL || U == NULL)) return ORACLE_BAD_ARG;
+    for (int i = 0; i < n; i++) {
+        double complex t = CAT(T, ldt, i, i);
+        if (!isfinite(creal(t)) || !isfinite(cimag(t))) return ORACLE_NONFINITE;
+        if (creal(t) == 0.0) return ORACLE_ZERO_EIGENVALUE;
+    }
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) CAT(U, ldu, i, j) = 0.0;
+    for (int i = 0; i < n; i++) CAT(U, ldu, i, i) = scalar_sign(creal(CAT(T, ldt, i, i)));
+    for (int j = 1; j < n; j++) {
+        for (int i = j - 1; i >= 0; i--) {
+            double complex uii = CAT(U, ldu, i, i), ujj = CAT(U, ldu, j, j);
+            if (uii + ujj == 0.0) {
+                double complex s = 0.0;
+                for (int k = i + 1; k <= j - 1; k++) {
+                    double complex a = CAT(U, ldu, i, k) * CAT(T, ldt, k, j);
+                    double complex b = CAT(T, ldt, i, k) * CAT(U, ldu, k, j);
+                    s = s + (a - b);
+                }
+                double complex den = CAT(T, ldt, i, i) - CAT(T, ldt, j, j);
+                CAT(U, ldu, i, j) = CAT(T, ldt, i, j) * (uii - ujj) / den + s / den;
+            } else {
+                double complex s = 0.0;
+                for (int k = i + 1; k <= j - 1; k++) s = s + CAT(U, ldu, i, k) * CAT(U, ldu, k, j);
+                CAT(U, ldu, i, j) = -s / (uii + ujj);
+            }
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* S = Q U Q^H, U = sign(T), Q unitary: W = U Q^H, then S = Q W, each entry
+   one plain sum over k ascending. */
+int oracle_sign_schur_complex(int n, const double *Q, int ldq, const double *T, int ldt, double *S, int lds)
+{
+    if (n < 0 || ldq < (n > 1 ? n : 1) || lds < (n > 1 ? n : 1)) return ORACLE_BAD_ARG;
+    if (n > 0 && (Q == NULL || S == NULL)) return ORACLE_BAD_ARG;
+    size_t nn = (size_t)n * (size_t)n;
+    double complex *U = (double complex *)calloc(nn > 0 ? nn : 1, sizeof(double complex));
+    double complex *W = (double complex *)calloc(nn > 0 ? nn : 1, sizeof(double complex));
+    if (!U || !W) { free(U); free(W); return ORACLE_BAD_ARG; }
+    int st = oracle_sign_tri_complex(n, T, ldt, (double *)U, n > 1 ? n : 1);
+    if (st == ORACLE_OK) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+        for (int j = 0; j < n; j++) {
+            double complex *w = W + (size_t)j * n;
+            for (int k = 0; k < n; k++) {
+                const double complex q = conj(CAT(Q, ldq, j, k));
+                const double complex *u = U + (size_t)k * n;
+                for (int i = 0; i < n; i++) w[i] = w[i] + u[i] * q;
+            }
+        }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+        for (int j = 0; j < n; j++) {
+            double complex *sc = &CAT(S, lds, 0, j);
+            for (int i = 0; i < n; i++) sc[i] = 0.0;
+            for (int k = 0; k < n; k++) {
+                const double complex wkj = W[(size_t)j * n + k];
+                const double complex *q = &CAT(Q, ldq, 0, k);
                 for (int i = 0; i < n; i++) sc[i] = sc[i] + q[i] * wkj;
             }
         }

@@ -234,3 +234,71 @@ def test_sign_schur_invariants(oracle_mod, n, p):
     assert abs(np.trace(S) - (npos - (n - npos))) <= 1e-10 * n
     # Q = I reduces to the triangular oracle exactly
     assert np.array_equal(oracle_mod.sign_schur(np.eye(n), T), oracle_mod.sign_tri(T))
+
+
+# ---- complex T (the Schur form of a general matrix is complex) ------------
+
+def _paper_matrix(n, seed):
+    # Section 6's workload: entries uniform in [-50, 50]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(-50.0, 50.0, size=(n, n))
+
+
+@pytest.mark.parametrize("n,seed", [(8, 1), (30, 2), (60, 3)])
+def test_complex_schur_route_vs_signm(oracle_mod, n, seed):
+    # a general real A through its complex Schur form (LAPACK), against
+    # scipy's signm of A itself; sign(A) of a real A is real
+    sl = pytest.importorskip("scipy.linalg")
+    A = _paper_matrix(n, seed)
+    T, Z = sl.schur(A, output="complex")
+    S = oracle_mod.sign_schur_complex(Z, T)
+    ref = sl.signm(A)
+    assert np.linalg.norm(S - ref) <= 1e-11 * np.linalg.norm(ref)
+    assert np.abs(S.imag).max() <= 1e-11 * np.abs(S).max()
+
+
+def test_complex_spectral_definition(oracle_mod):
+    # complex triangular T with distinct eigenvalues: V sign(Re L) V^{-1}
+    rng = np.random.Generator(np.random.PCG64(11))
+    n = 12
+    T = np.triu(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / 3.0
+    d = (rng.uniform(0.5, 2.0, n) * np.where(rng.random(n) < 0.5, -1.0, 1.0)
+         + 1j * rng.uniform(-2.0, 2.0, n))
+    T[np.arange(n), np.arange(n)] = d
+    lam, V = np.linalg.eig(T)
+    ref = V @ np.diag(np.sign(lam.real)) @ np.linalg.inv(V)
+    U = oracle_mod.sign_tri_complex(T)
+    assert np.linalg.norm(U - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert np.array_equal(np.diag(U), np.sign(d.real).astype(complex))
+    assert np.all(np.tril(U, -1) == 0)
+
+
+def test_complex_2x2_and_invariants(oracle_mod):
+    t11, t12, t22 = 1.5 - 0.5j, 0.3 + 2.0j, -0.7 + 1.1j
+    U = oracle_mod.sign_tri_complex(np.array([[t11, t12], [0, t22]]))
+    assert U[0, 0] == 1 and U[1, 1] == -1
+    assert abs(U[0, 1] - t12 * 2 / (t11 - t22)) <= 1e-15 * abs(U[0, 1])
+    rng = np.random.Generator(np.random.PCG64(12))
+    n = 40
+    T = np.triu(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / math.sqrt(n)
+    T[np.arange(n), np.arange(n)] = (rng.uniform(0.5, 2.0, n) * np.where(rng.random(n) < 0.5, -1.0, 1.0)
+                                     + 1j * rng.standard_normal(n))
+    U = oracle_mod.sign_tri_complex(T)
+    assert np.linalg.norm(U @ U - np.eye(n)) <= 1e-12 * np.linalg.norm(U) ** 2
+    assert np.linalg.norm(U @ T - T @ U) <= 1e-12 * np.linalg.norm(U) * np.linalg.norm(T)
+
+
+def test_complex_reduces_to_real(oracle_mod):
+    # a real T in complex form gives the real oracle's U bit for bit
+    T = make_T(50, 0.4, seed=7)
+    U = oracle_mod.sign_tri_complex(T.astype(complex))
+    assert np.array_equal(U.real, oracle_mod.sign_tri(T))
+    assert np.all(U.imag == 0)
+
+
+def test_complex_imaginary_axis_is_an_error(oracle_mod):
+    # sign is undefined on the imaginary axis (Section 1)
+    T = np.array([[1.0 + 1j, 0.5], [0, 2.0j]])
+    with pytest.raises(oracle_mod.OracleError) as e:
+        oracle_mod.sign_tri_complex(T)
+    assert e.value.status == oracle_mod.ZERO_EIGENVALUE
