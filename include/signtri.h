@@ -270,6 +270,28 @@ signtri_status signtri_sign_schur(int n, const double *Q, int ldq, const double 
                                   signtri_variant variant, void *stream);
 size_t signtri_sign_schur_workspace_bytes(int n, signtri_variant variant);
 
+/* ---- Complex T and the complex Schur route (Section 1; Algorithm 3) -------
+   The Schur form of a general A is complex.  Complex matrices here are
+   interleaved (re, im) float64 pairs, column-major, leading dimensions
+   counted in complex elements (LAPACK's COMPLEX*16 / cuDoubleComplex).
+   signtri_sign_tri_complex: U = sign(T) for complex upper triangular T,
+   u_ii = sign(Re t_ii) and Eqs. 1 and 2 entry by entry in complex float64
+   (one launch per anti-diagonal, a warp per entry; float64 rate).  A
+   diagonal entry with Re t_ii == 0 (the sign is undefined on the imaginary
+   axis) gives SIGNTRI_ERR_ZERO_EIGENVALUE, a non-finite one
+   SIGNTRI_ERR_NONFINITE, the first such index in signtri_get_info.  Only
+   T's upper triangle is read; U's strictly lower part is written as 0.
+   signtri_sign_schur_complex: S = Q U Q^H for a caller's complex Schur pair
+   (A = Q T Q^H, Q unitary -- not checked), the products as four real
+   emulated-float64 tensor-core products each (about 2^-45 of the product
+   of the row and column scales).  Outputs must not share an element with
+   the inputs (SIGNTRI_ERR_BAD_ARG).  Both synchronous on `stream`; with a
+   caller workspace they need signtri_complex_workspace_bytes(n). */
+signtri_status signtri_sign_tri_complex(int n, const double *T, int ldt, double *U, int ldu, void *stream);
+signtri_status signtri_sign_schur_complex(int n, const double *Q, int ldq, const double *T, int ldt, double *S,
+                                          int lds, void *stream);
+size_t signtri_complex_workspace_bytes(int n);
+
 /* ---- Emulated float64 product on the tensor cores --------------------------
    C = A B (A m x k, B k x n, C m x n; device pointers, column-major) with
    float64-level accuracy from bf16 tensor-core products: each row of A and

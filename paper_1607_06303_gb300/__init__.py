@@ -14,4 +14,6 @@ from .signtri import (Info, SignTriError, Status, Variant, load, sign, sign_tri,
                       signtri_profile_read_flops, signtri_profile_read_bytes, sign_tri_batched, signtri_set_cutoff_table,
                       signtri_get_cutoff_table, signtri_autotune, signtri_selftest_wait,
                       signtri_get_variant_table, signtri_set_variant_table, signtri_batched_cache_stats,
-                      signtri_sign_schur, signtri_sign_schur_workspace_bytes, sign_schur)
+                      signtri_sign_schur, signtri_sign_schur_workspace_bytes, sign_schur,
+                      signtri_sign_tri_complex, signtri_sign_schur_complex, signtri_complex_workspace_bytes,
+                      sign_complex, sign_schur_complex, to_device_complex)

@@ -766,6 +766,67 @@ signtri_status signtri_sign_schur(int n, const double *Q, int ldq, const double 
     return *s->err_host ? SIGNTRI_ERR_TIMEOUT : SIGNTRI_OK;
 }
 
+size_t signtri_complex_workspace_bytes(int n)
+{
+    if (n < 0) return 0;
+    return complex_schur_workspace_bytes(n);
+}
+
+// the complex blocks [A] (rows x cols, ld in complex elements) as double runs
+static bool cblocks_overlap(const double *A, int lda, const double *B, int ldb, int n)
+{
+    return blocks_overlap(A, 2 * lda, 2 * n, n, B, 2 * ldb, 2 * n, n);
+}
+
+signtri_status signtri_sign_tri_complex(int n, const double *T, int ldt, double *U, int ldu, void *stream)
+{
+    reset_info(n);
+    if (n < 0) return SIGNTRI_ERR_BAD_ARG;
+    if (n == 0) return SIGNTRI_OK;
+    if (!T || !U || ldt < n || ldu < n) return SIGNTRI_ERR_BAD_ARG;
+    if (cblocks_overlap(T, ldt, U, ldu, n)) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    Arena ws;
+    rs = get_workspace(*s, complex_workspace_bytes(n), ws);
+    if (rs != SIGNTRI_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int bad = -1;
+    rs = complex_sign_run(n, T, ldt, U, ldu, ws, &bad, st);
+    if (rs == SIGNTRI_ERR_ZERO_EIGENVALUE || rs == SIGNTRI_ERR_NONFINITE) g_info.bad_index = bad;
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_sign_schur_complex(int n, const double *Q, int ldq, const double *T, int ldt, double *S,
+                                          int lds, void *stream)
+{
+    reset_info(n);
+    if (n < 0) return SIGNTRI_ERR_BAD_ARG;
+    if (n == 0) return SIGNTRI_OK;
+    if (!Q || !T || !S || ldq < n || ldt < n || lds < n) return SIGNTRI_ERR_BAD_ARG;
+    if (cblocks_overlap(T, ldt, S, lds, n) || cblocks_overlap(Q, ldq, S, lds, n)) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    Arena ws;
+    rs = get_workspace(*s, complex_schur_workspace_bytes(n), ws);
+    if (rs != SIGNTRI_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SGT_CUDA_TRY(cudaMemsetAsync(s->err_dev, 0, sizeof(int), st));
+    int bad = -1;
+    rs = complex_schur_run(n, Q, ldq, T, ldt, S, lds, ws, s->err_dev, &bad, st);
+    if (rs == SIGNTRI_ERR_ZERO_EIGENVALUE || rs == SIGNTRI_ERR_NONFINITE) g_info.bad_index = bad;
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaMemcpyAsync(s->err_host, s->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    return *s->err_host ? SIGNTRI_ERR_TIMEOUT : SIGNTRI_OK;
+}
+
 signtri_status signtri_sylvester(int m, int p, const double *A, int lda, const double *B, int ldb, const double *C,
                                  int ldc, double *X, int ldx, void *stream)
 {

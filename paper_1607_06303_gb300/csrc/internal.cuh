@@ -185,6 +185,16 @@ void batched_cache_stats(long long *hits, long long *builds);
 // Bounded-wait self-test (tc_gemm.cu)
 signtri_status wait_selftest(int arrive, long long limit, int *d_err, cudaStream_t st);
 
+// Complex T (complex.cu): interleaved (re, im) column-major, ld in complex
+// elements.  bad_index receives the first bad diagonal index on a status
+// other than OK that concerns the diagonal.
+size_t complex_workspace_bytes(int n);
+signtri_status complex_sign_run(int n, const double *T, int ldt, double *U, int ldu, Arena &ws, int *bad_index,
+                                cudaStream_t st);
+size_t complex_schur_workspace_bytes(int n);
+signtri_status complex_schur_run(int n, const double *Q, int ldq, const double *T, int ldt, double *S, int lds,
+                                 Arena &ws, int *d_err, int *bad_index, cudaStream_t st);
+
 // Mixed precision with refinement (mixed.cu)
 struct MixedParams {
     double tol;              // stopping test on both relative residuals

@@ -81,6 +81,32 @@ def make_schur_pair(n: int, p: float = 0.5, seed: int = 0, order: str = "random"
     return make_orthogonal(n, seed + 7919), make_T(n, p, seed=seed, order=order)
 
 
+def make_T_complex(n: int, p: float = 0.5, seed: int = 0, order: str = "random") -> np.ndarray:
+    """Complex upper-triangular T (column-major complex128): the real recipe's
+    sign pattern and |Re t_ii| ~ U[0.5, 2], Im t_ii ~ N(0, 1); strictly upper
+    re and im parts each N(0, 1/(2n)) (so |t_ij|^2 has mean 1/n)."""
+    if n < 0:
+        raise ValueError("n must be >= 0")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = n_negative(n, p)
+    s = sign_pattern(rng, n, k, order)
+    mags = rng.uniform(0.5, 2.0, size=n)
+    ims = rng.standard_normal(n)
+    T = np.zeros((n, n), dtype=np.complex128, order="F")
+    if n == 0:
+        return T
+    m = n * (n - 1) // 2
+    sd = 1.0 / math.sqrt(2.0 * n)
+    re = rng.standard_normal(m) * sd
+    im = rng.standard_normal(m) * sd
+    o = 0
+    for j in range(1, n):
+        T[:j, j] = re[o:o + j] + 1j * im[o:o + j]
+        o += j
+    T[np.arange(n), np.arange(n)] = s * mags + 1j * ims
+    return T
+
+
 def make_T_schur(n: int, seed: int = 0, n_neg: int = None) -> np.ndarray:
     """The paper's workload (Section 6): the real part of the complex Schur
     form of a random n x n matrix with entries uniform in [-50, 50]; inertia

@@ -105,6 +105,9 @@ _SIGNATURES = {
     "signtri_selftest_wait": (_I, [_I, ctypes.c_longlong, _VP]),
     "signtri_sign_schur": (_I, [_I, _VP, _I, _VP, _I, _VP, _I, _I, _VP]),
     "signtri_sign_schur_workspace_bytes": (_SZ, [_I, _I]),
+    "signtri_sign_tri_complex": (_I, [_I, _VP, _I, _VP, _I, _VP]),
+    "signtri_sign_schur_complex": (_I, [_I, _VP, _I, _VP, _I, _VP, _I, _VP]),
+    "signtri_complex_workspace_bytes": (_SZ, [_I]),
 }
 
 SIGNTRI_NOALLOC_MAX_N = 1024
@@ -381,6 +384,70 @@ def sign_schur(Qt, Tt, variant=Variant.AUTO, out=None, stream=None, check=True):
     if check and st != 0:
         raise SignTriError(st, "signtri_sign_schur")
     return St
+
+
+def signtri_sign_tri_complex(n, T_ptr, ldt, U_ptr, ldu, stream=None) -> int:
+    return load().signtri_sign_tri_complex(n, T_ptr or None, ldt, U_ptr or None, ldu, stream or None)
+
+
+def signtri_sign_schur_complex(n, Q_ptr, ldq, T_ptr, ldt, S_ptr, lds, stream=None) -> int:
+    return load().signtri_sign_schur_complex(n, Q_ptr or None, ldq, T_ptr or None, ldt, S_ptr or None, lds,
+                                             stream or None)
+
+
+def signtri_complex_workspace_bytes(n) -> int:
+    return load().signtri_complex_workspace_bytes(n)
+
+
+def _check_complex(name, t):
+    import torch
+    if t.dtype != torch.complex128 or not t.is_cuda or t.dim() != 2 or t.shape[0] != t.shape[1]:
+        raise ValueError("%s must be a square CUDA complex128 tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
+def sign_complex(Tt, out=None, stream=None, check=True):
+    """U = sign(T) for a CUDA complex128 tensor holding complex upper
+    triangular T column-major (to_device_complex's layout)."""
+    import torch
+    _check_complex("T", Tt)
+    Ut = out if out is not None else torch.empty_like(Tt)
+    _check_complex("out", Ut)
+    n = Tt.shape[0]
+    with torch.cuda.device(Tt.device):
+        st = signtri_sign_tri_complex(n, Tt.data_ptr(), max(n, 1), Ut.data_ptr(), max(n, 1), _stream_handle(stream))
+    if check and st != 0:
+        raise SignTriError(st, "signtri_sign_tri_complex")
+    return Ut
+
+
+def sign_schur_complex(Qt, Tt, out=None, stream=None, check=True):
+    """S = Q sign(T) Q^H from a complex Schur pair (CUDA complex128 tensors,
+    column-major as to_device_complex makes them)."""
+    import torch
+    _check_complex("T", Tt)
+    _check_complex("Q", Qt)
+    if tuple(Qt.shape) != tuple(Tt.shape) or Qt.device != Tt.device:
+        raise ValueError("Q and T must be n x n on the same device")
+    St = out if out is not None else torch.empty_like(Tt)
+    _check_complex("out", St)
+    n = Tt.shape[0]
+    with torch.cuda.device(Tt.device):
+        st = signtri_sign_schur_complex(n, Qt.data_ptr(), max(n, 1), Tt.data_ptr(), max(n, 1), St.data_ptr(),
+                                        max(n, 1), _stream_handle(stream))
+    if check and st != 0:
+        raise SignTriError(st, "signtri_sign_schur_complex")
+    return St
+
+
+def to_device_complex(M_colmajor, device="cuda"):
+    """numpy complex n x n matrix -> CUDA complex128 tensor holding it
+    column-major (interleaved re, im; the tensor is the transpose)."""
+    import numpy as np
+    import torch
+    a = np.asfortranarray(np.asarray(M_colmajor, dtype=np.complex128))
+    return torch.from_numpy(np.ascontiguousarray(a.T)).to(device)
 
 
 def to_device(T_colmajor, device="cuda"):
