@@ -143,8 +143,9 @@ size_t signtri_workspace_bytes(int n, signtri_variant v);
 signtri_status signtri_set_workspace(void *dev_ptr, size_t bytes);
 
 /* Per-variant throughput used by SIGNTRI_AUTO to turn the Section 3 work
-   estimates into times: flops/s of the float64 block products and of the
-   Givens reorder rounds.  Values <= 0 restore the defaults. */
+   estimates into times: flops/s of the float64 block products (default
+   1.2e12, GB300's measured float64 rate) and of the unblocked Givens
+   rounds (default 0.35e12).  Values <= 0 restore the defaults. */
 signtri_status signtri_set_rates(double gemm_flops_per_s, double givens_flops_per_s);
 
 /* Refinement of the mixed variants: stop when ||TU-UT||_F/(||T||_F||U||_F)
@@ -170,9 +171,13 @@ signtri_status signtri_set_refinement(double tol, int max_steps);
    return SIGNTRI_ERR_BAD_ARG. */
 signtri_status signtri_set_verification(int full);
 
-/* Leaf (recursion cutoff) size b of Parlett-Higham: the order of the diagonal
-   and off-diagonal blocks solved element by element (Section 6 uses 16).
-   b in {16, 32, 64}; 0 restores the default.  Process-wide setting. */
+/* Leaf (recursion cutoff) size b of the float64 Parlett-Higham forms: the
+   order of the diagonal and off-diagonal blocks solved element by element
+   (Section 6 uses 16).  b in {16, 32, 64}, or 0 (the default): by size, the
+   fastest measured on GB300 -- the efficient form 16 below n = 4096, 32
+   below 8192, then 64; the matrix-multiply form 16 up to n = 4096, then 32.
+   The mixed variants' tensor-core tiles are 64 whatever b.  signtri_info
+   reports the b a call used.  Process-wide setting. */
 signtri_status signtri_set_cutoff(int b);
 
 /* U = sign(T).  T, U device pointers (see conventions).  Enqueued on
@@ -213,7 +218,8 @@ signtri_status sign_tri_batched(int count, const int *n, const double *const *T,
                                 void *stream);
 
 /* Leaf-size table of the batched path: b[k] (16, 32, 64, or 0 = the
-   process-wide cutoff) for problems with floor(log2 n) == k, k < len <= 32. */
+   process-wide cutoff, by size when that is 0) for problems with
+   floor(log2 n) == k, k < len <= 32. */
 signtri_status signtri_set_cutoff_table(const int *b, int len);
 signtri_status signtri_get_cutoff_table(int *b, int len);
 

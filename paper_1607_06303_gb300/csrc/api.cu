@@ -18,7 +18,6 @@ using namespace signtri;
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr int kDefaultCutoff = 64;
 
 struct DeviceState {
     void *lib_ptr = nullptr;       // library-owned workspace (cudaMalloc)
@@ -38,14 +37,15 @@ struct DeviceState {
 
 std::mutex g_mu;
 DeviceState g_dev[kMaxDevices];
-int g_cutoff = kDefaultCutoff;
+// 0: by size (default_cutoff); else the leaf size set by signtri_set_cutoff
+int g_cutoff = 0;
 // leaf size per size bucket floor(log2 n) for the batched path; 0 = g_cutoff
 int g_cutoff_table[32] = {};
 // variant AUTO runs per size bucket in the batched path; 0 = the batched
 // Parlett-Higham (or Parlett-Sylvester when no swaps are needed)
 int g_variant_table[32] = {};
 // flops/s used by the AUTO choice (float64 block products; Givens rounds)
-constexpr double kDefaultGemmRate = 1.0e12;
+constexpr double kDefaultGemmRate = 1.2e12;   // the measured float64 FMA rate of a GB300
 constexpr double kDefaultGivensRate = 0.35e12;
 double g_rate_gemm = kDefaultGemmRate;
 double g_rate_givens = kDefaultGivensRate;
@@ -127,9 +127,27 @@ signtri_status get_workspace(DeviceState &s, size_t need, Arena &a)
 }
 
 // swaps < 0: the worst case over inertia (n^2/4 swaps).
-size_t workspace_need(int n, signtri_variant v, int cutoff, long long swaps)
+// Leaf size of the float64 forms when none is set: measured on GB300 (p = 0.5
+// random), the fastest of 16, 32, 64 per size -- small leaves while the leaf
+// latency dominates, larger ones once the block sums do: the efficient form
+// 16 below n = 4096, 32 below 8192, then 64; the matrix-multiply form 16 up
+// to 4096, then 32.
+int default_cutoff(int n, signtri_variant v)
+{
+    if (v == SIGNTRI_PH_FP64_EFFICIENT || v == SIGNTRI_AUTO) return n < 4096 ? 16 : (n < 8192 ? 32 : 64);
+    return n <= 4096 ? 16 : 32;
+}
+
+// the leaf size a float64 form runs with (callers hold g_mu)
+int cutoff_of(int n, signtri_variant v)
+{
+    return g_cutoff ? g_cutoff : default_cutoff(n, v);
+}
+
+size_t workspace_need(int n, signtri_variant v, long long swaps)
 {
     if (swaps < 0) swaps = (long long)n * n / 4;
+    const int cutoff = cutoff_of(n, v == SIGNTRI_PH_FP64_EFFICIENT || v == SIGNTRI_AUTO ? v : SIGNTRI_PH_FP64);
     switch (v) {
     case SIGNTRI_PH_FP64:
         return ph_fp64_workspace_bytes(n, cutoff);
@@ -173,7 +191,7 @@ void work_estimates(int n, const ScanResult &r, double *w_ph, double *w_ps)
 //  * Parlett-Higham runs the arithmetic-efficient form (Section 5.3: only the
 //    sum each entry needs, exactly the useful count w_ph) at the float64
 //    product rate, and one off-diagonal leaf step per block column (about
-//    0.55 ms at b = 64, shorter for smaller leaves);
+//    0.075, 0.21, 0.65 ms at b = 16, 32, 64);
 //  * Parlett-Sylvester runs the Sylvester block sums (n_- n_+ n flops) and
 //    one in-block step per block anti-diagonal (about 0.4 ms); when k > 0,
 //    the reorder and the back-transform (emulated-float64 tensor-core
@@ -182,28 +200,34 @@ void work_estimates(int n, const ScanResult &r, double *w_ph, double *w_ps)
 //    most 64 places a sweep, so there are about d / 64 sweeps, d = n_+ -
 //    (index of the first negative) the longest distance one travels.  A
 //    sweep costs its window launch (rounds and float64 rotations, growing
-//    with the swaps per window) plus the products and slicing of its about
-//    min(n_-, n / 256) active windows, each about 1.1e-8 n seconds.  The
+//    with the swaps per window) and about 0.1 ms of launches, plus the
+//    products and slicing of its about min(n_-, n / 256) active windows,
+//    each about 1.1e-8 n seconds.  The
 //    unblocked rounds (n < 512) cost 12 n k flops at the Givens rate and two
 //    launches per round.
 constexpr double kLaunchSeconds = 5e-6;
-constexpr double kPhLeafStepSeconds = 0.55e-3;
+double ph_leaf_step_seconds(int b)
+{
+    return b <= 16 ? 0.075e-3 : (b <= 32 ? 0.21e-3 : 0.65e-3);
+}
+constexpr double kSweepLaunchSeconds = 1e-4;
 constexpr double kSylvStepSeconds = 0.40e-3;
 constexpr double kEmulatedRate = 6e13;
 constexpr double kWindowProductSeconds = 1.1e-8;
 
 double window_launch_seconds(double kw)
 {
-    return std::fmin(0.95e-3, 3e-5 + 1.2e-6 * kw) + 6e-7 * std::fmax(0.0, kw - 770.0);
+    return std::fmin(0.95e-3, 1.5e-4 + 1.0e-6 * kw) + 6e-7 * std::fmax(0.0, kw - 800.0);
 }
 
 signtri_variant choose_variant(int n, const ScanResult &r)
 {
     const double nd = n;
-    const double nb = std::ceil(nd / g_cutoff);
+    const int b = cutoff_of(n, SIGNTRI_PH_FP64_EFFICIENT);
+    const double nb = std::ceil(nd / b);
     double w_ph = 0.0, w_ps = 0.0;
     work_estimates(n, r, &w_ph, &w_ps);
-    const double t_ph = w_ph / g_rate_gemm + nb * kPhLeafStepSeconds * g_cutoff / 64.0 + 2.0 * nb * kLaunchSeconds;
+    const double t_ph = w_ph / g_rate_gemm + nb * ph_leaf_step_seconds(b) + 2.0 * nb * kLaunchSeconds;
     const double np = r.n_pos, nm = r.n_neg, k = (double)r.swaps;
     const double sylv_steps = std::ceil(np / 64.0) + std::ceil(nm / 64.0) - 1.0;
     double t_ps = np * nm * nd / g_rate_gemm + sylv_steps * kSylvStepSeconds;
@@ -214,7 +238,7 @@ signtri_variant choose_variant(int n, const ScanResult &r)
             const double sweeps = std::ceil(d / 64.0) + 1.0;
             const double active = std::fmax(1.0, std::fmin(nm, nd / 256.0));
             const double kw = std::fmin(4096.0, k / (sweeps * active));
-            t_ps += sweeps * (window_launch_seconds(kw) + kWindowProductSeconds * active * nd);
+            t_ps += sweeps * (kSweepLaunchSeconds + window_launch_seconds(kw) + kWindowProductSeconds * active * nd);
         } else {
             t_ps += 12.0 * nd * k / g_rate_givens + 2.0 * nd * kLaunchSeconds;
         }
@@ -226,8 +250,8 @@ signtri_status run_variant(int n, const double *T, int ldt, double *U, int ldu, 
                            const ScanResult &r, cudaStream_t st, DeviceState &s)
 {
     Arena ws;
-    const int b = g_cutoff;
-    signtri_status rs = get_workspace(s, workspace_need(n, v, b, r.swaps), ws);
+    const int b = cutoff_of(n, v == SIGNTRI_PH_FP64_EFFICIENT ? v : SIGNTRI_PH_FP64);
+    signtri_status rs = get_workspace(s, workspace_need(n, v, r.swaps), ws);
     if (rs != SIGNTRI_OK) return rs;
     switch (v) {
     case SIGNTRI_PH_FP64:
@@ -328,7 +352,7 @@ int size_bucket(int n)
 int cutoff_for(int n)
 {
     const int k = size_bucket(n);
-    return g_cutoff_table[k] ? g_cutoff_table[k] : g_cutoff;
+    return g_cutoff_table[k] ? g_cutoff_table[k] : cutoff_of(n, SIGNTRI_PH_FP64_EFFICIENT);
 }
 
 // Synthetic upper-triangular T for the autotuner: counter-based hash
@@ -359,10 +383,10 @@ __global__ void synth_kernel(int n, double *T, unsigned long long seed)
 
 }  // namespace
 
-int signtri::current_cutoff()
+int signtri::current_cutoff(int n)
 {
     std::lock_guard<std::mutex> lk(g_mu);
-    return g_cutoff;
+    return cutoff_of(n, SIGNTRI_PH_FP64);
 }
 
 extern "C" {
@@ -387,7 +411,7 @@ size_t signtri_workspace_bytes(int n, signtri_variant v)
 {
     if (n < 0 || !valid_variant(v)) return 0;
     std::lock_guard<std::mutex> lk(g_mu);
-    return workspace_need(n, v, g_cutoff, -1);
+    return workspace_need(n, v, -1);
 }
 
 signtri_status signtri_set_rates(double gemm_flops_per_s, double givens_flops_per_s)
@@ -724,7 +748,7 @@ size_t signtri_sign_schur_workspace_bytes(int n, signtri_variant v)
 {
     if (n < 0 || !valid_variant(v)) return 0;
     std::lock_guard<std::mutex> lk(g_mu);
-    return std::max(workspace_need(n, v, g_cutoff, -1), schur_products_bytes(n));
+    return std::max(workspace_need(n, v, -1), schur_products_bytes(n));
 }
 
 signtri_status signtri_sign_schur(int n, const double *Q, int ldq, const double *T, int ldt, double *S, int lds,
@@ -860,8 +884,7 @@ signtri_status signtri_set_workspace(void *dev_ptr, size_t bytes)
 
 signtri_status signtri_set_cutoff(int b)
 {
-    if (b == 0) b = kDefaultCutoff;
-    if (b != 16 && b != 32 && b != 64) return SIGNTRI_ERR_BAD_ARG;
+    if (b != 0 && b != 16 && b != 32 && b != 64) return SIGNTRI_ERR_BAD_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
     g_cutoff = b;
     return SIGNTRI_OK;

@@ -118,8 +118,8 @@ signtri_status launch_fill_batched(int count, const BatchDesc *d_mats, const int
                                    cudaStream_t st);
 signtri_status launch_zero_strict_lower(int n, double *U, int ldu, cudaStream_t st);
 
-// Process-wide leaf size of Parlett-Higham (api.cu).
-int current_cutoff();
+// Leaf size the float64 matrix-multiply form runs with at order n (api.cu).
+int current_cutoff(int n);
 
 // Recursive Parlett-Higham, float64 (ph_fp64.cu)
 size_t ph_fp64_workspace_bytes(int n, int b);

