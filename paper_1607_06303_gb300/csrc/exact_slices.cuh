@@ -29,7 +29,9 @@ __device__ __forceinline__ void exact_slices(double x, int scale_exp, int S, int
     const unsigned long long mask = (1ull << b) - 1ull;
     const int ns = SC ? SC : S;   // SC > 0: slice count known at compile time (q in registers)
 #pragma unroll
-    for (int s = 0; s < ns; s++) q[s] = sgn * (float)((F >> (64 - b * (s + 1))) & mask);
+    // each digit fits in 32 bits: convert it as a 32-bit integer (a 64-bit
+    // integer conversion would issue on the float64 pipe, slow on this part)
+    for (int s = 0; s < ns; s++) q[s] = sgn * (float)(unsigned)((F >> (64 - b * (s + 1))) & mask);
 }
 
 }  // namespace signtri
