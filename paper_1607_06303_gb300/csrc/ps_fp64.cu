@@ -137,17 +137,73 @@ __global__ void copy_upper_identity_kernel(int n, const double *__restrict__ src
 
 // ------------------------------------------------------------- Sylvester ---
 
+// Double-float (fp32 hi + lo) arithmetic for the Sylvester block sums.
+// GB300 issues float64 at about 1/64 of its fp32 rate, so the sums run as
+// double-float products on the fp32 pipes: each float64 operand is cut
+// exactly into hi (its leading 24 significand bits) and lo (the next 29,
+// rounded to 24) with integer operations only; a product term is
+// a_h b_h (Dekker's exact product by FMA) + a_h b_l + a_l b_h, accumulated
+// with Knuth's two-sum.  About 2^-47 relative per term, summed in a fixed
+// order; values beyond fp32's exponent range (below 2^-126 or from 2^127)
+// are not represented (the first flush to 0; inputs and solutions here stay
+// far inside the range).
+__device__ __forceinline__ void split_df(double x, float &hi, float &lo)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7ff) - 1023;          // unbiased exponent
+    if (e < -126 || e > 127) {                                  // zero, tiny, or out of fp32's range
+        hi = (e > 127) ? __int_as_float(((unsigned)(bits >> 32) & 0x80000000u) | 0x7f800000u) : 0.f;
+        lo = 0.f;
+        return;
+    }
+    const unsigned sign = (unsigned)(bits >> 32) & 0x80000000u;
+    const unsigned long long mant = bits & 0xfffffffffffffull;  // 52 fraction bits
+    // hi: the implicit 1 and the top 23 fraction bits
+    hi = __int_as_float((int)(sign | ((unsigned)(e + 127) << 23) | (unsigned)(mant >> 29)));
+    // lo: the remaining 29 fraction bits, value mant_lo 2^(e - 52)
+    const unsigned mlo = (unsigned)(mant & 0x1fffffffull);
+    float l = __uint2float_rn(mlo);                             // < 2^29, rounded to 24 bits
+    const int el = e - 52;                                      // l * 2^el; el >= -178
+    l = (el >= -126) ? __fmul_rn(l, __int_as_float((el + 127) << 23))
+                     : __fmul_rn(__fmul_rn(l, __int_as_float((el + 127 + 64) << 23)), __int_as_float((127 - 64) << 23));
+    lo = sign ? -l : l;
+}
+
+// acc += a b in double-float (acc_h, acc_l unnormalised between renormalisations)
+__device__ __forceinline__ void df_mac(float &ah_acc, float &al_acc, float a_h, float a_l, float b_h, float b_l)
+{
+    const float p = __fmul_rn(a_h, b_h);
+    float e = __fmaf_rn(a_h, b_h, -p);
+    e = __fmaf_rn(a_h, b_l, e);
+    e = __fmaf_rn(a_l, b_h, e);
+    const float s = __fadd_rn(ah_acc, p);
+    const float bb = __fsub_rn(s, ah_acc);
+    const float err = __fadd_rn(__fsub_rn(ah_acc, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    ah_acc = s;
+    al_acc = __fadd_rn(al_acc, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ void df_renorm(float &h, float &l)
+{
+    const float s = __fadd_rn(h, l);
+    l = __fsub_rn(l, __fsub_rn(s, h));
+    h = s;
+}
+
 // Block sums of anti-diagonal s for A X - X B = C (m x p), block (I, J) with
 // I = nbr - 1 - s + J:  P = -sum_{I'>I} A[I, I'] X[I', J] + sum_{J'<J} X[I, J'] B[J', J].
 // The s K-blocks of a tile are numbered v = 0..s-1: first the row blocks
 // I' = I+1.. (the last may be partial), then the column blocks J' = 0..J-1.
+// Operands staged in shared memory as double-float pairs; each thread keeps
+// a 4 x 4 set of double-float accumulators, renormalised after every chunk
+// of KT terms; the float64 partial written is hi + lo.
 __global__ void __launch_bounds__(kThreads)
 sylv_sums_kernel(int m, int p, const double *__restrict__ A, int lda, const double *__restrict__ Bm, int ldb,
                  const double *__restrict__ X, int ldx, int s, int nbr, int j_lo, int kc, double *__restrict__ P,
                  size_t split_stride)
 {
     constexpr int KT = 16;
-    __shared__ double As[KT][SB], Bs[KT][SB];
+    __shared__ float Ah[KT][SB], Al[KT][SB], Bh[KT][SB], Bl[KT][SB];
     const int J = j_lo + blockIdx.x;
     const int I = nbr - 1 - s + J;
     const int split = blockIdx.y;
@@ -156,11 +212,11 @@ sylv_sums_kernel(int m, int p, const double *__restrict__ A, int lda, const doub
     const int bi = min(SB, m - r0), bj = min(SB, p - c0);
     const int nrow_blocks = nbr - 1 - I;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    double acc[4][4];
+    float acc_h[4][4], acc_l[4][4];
 #pragma unroll
     for (int a = 0; a < 4; a++)
 #pragma unroll
-        for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
+        for (int b = 0; b < 4; b++) acc_h[a][b] = acc_l[a][b] = 0.f;
     for (int v = v0; v < v1; v++) {
         const bool phase1 = v < nrow_blocks;
         const int kb = phase1 ? (I + 1 + v) : (v - nrow_blocks);
@@ -173,7 +229,7 @@ sylv_sums_kernel(int m, int p, const double *__restrict__ A, int lda, const doub
                 double av = 0.0;
                 if (r < bi && gk < kext)
                     av = phase1 ? -SGT_AT(A, lda, r0 + r, k_base + gk) : SGT_AT(X, ldx, r0 + r, k_base + gk);
-                As[kk][r] = av;
+                split_df(av, Ah[kk][r], Al[kk][r]);
             }
             for (int idx = threadIdx.x; idx < SB * KT; idx += kThreads) {
                 const int kk = idx % KT, c = idx / KT;
@@ -181,19 +237,28 @@ sylv_sums_kernel(int m, int p, const double *__restrict__ A, int lda, const doub
                 double bv = 0.0;
                 if (c < bj && gk < kext)
                     bv = phase1 ? SGT_AT(X, ldx, k_base + gk, c0 + c) : SGT_AT(Bm, ldb, k_base + gk, c0 + c);
-                Bs[kk][c] = bv;
+                split_df(bv, Bh[kk][c], Bl[kk][c]);
             }
             __syncthreads();
-#pragma unroll
+#pragma unroll 4
             for (int kk = 0; kk < KT; kk++) {
-                double a[4], b[4];
+                float ah[4], al[4], bh[4], bl[4];
 #pragma unroll
-                for (int q = 0; q < 4; q++) { a[q] = As[kk][tx + 16 * q]; b[q] = Bs[kk][ty + 16 * q]; }
+                for (int q = 0; q < 4; q++) {
+                    ah[q] = Ah[kk][tx + 16 * q];
+                    al[q] = Al[kk][tx + 16 * q];
+                    bh[q] = Bh[kk][ty + 16 * q];
+                    bl[q] = Bl[kk][ty + 16 * q];
+                }
 #pragma unroll
                 for (int pp = 0; pp < 4; pp++)
 #pragma unroll
-                    for (int q = 0; q < 4; q++) acc[pp][q] = fma(a[pp], b[q], acc[pp][q]);
+                    for (int q = 0; q < 4; q++) df_mac(acc_h[pp][q], acc_l[pp][q], ah[pp], al[pp], bh[q], bl[q]);
             }
+#pragma unroll
+            for (int pp = 0; pp < 4; pp++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) df_renorm(acc_h[pp][q], acc_l[pp][q]);
             __syncthreads();
         }
     }
@@ -201,40 +266,66 @@ sylv_sums_kernel(int m, int p, const double *__restrict__ A, int lda, const doub
 #pragma unroll
     for (int pp = 0; pp < 4; pp++)
 #pragma unroll
-        for (int q = 0; q < 4; q++) out[(tx + 16 * pp) + (ty + 16 * q) * SB] = acc[pp][q];
+        for (int q = 0; q < 4; q++)
+            out[(tx + 16 * pp) + (ty + 16 * q) * SB] = (double)acc_h[pp][q] + (double)acc_l[pp][q];
 }
 
 // In-block recurrence for block (I, J) of anti-diagonal s:
 //   (a_pp - b_qq) x_pq = cscale*c_pq + sums_pq - sum_{p'>p} A[p,p'] x_p'q + sum_{q'<q} x_pq' B[q',q]
+// The in-block sums run in double-float on the fp32 pipes (as the block
+// sums above), each entry's terms split over four consecutive lanes and
+// reduced by shuffles; the seed, the division and x_pq itself stay float64
+// (x_pq is kept in both forms: float64 for the output, double-float for
+// the sums of later entries).
+__device__ __forceinline__ void df_add_df(float &h, float &l, float oh, float ol)
+{
+    const float s = __fadd_rn(h, oh);
+    const float bb = __fsub_rn(s, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(oh, bb));
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(ol, err));
+}
+
+constexpr int kLeafLD = SB + 1;
+constexpr size_t kLeafSmem = 6 * (size_t)SB * kLeafLD * sizeof(float) + (size_t)SB * kLeafLD * sizeof(double) +
+                             2 * (size_t)SB * sizeof(double);
+
 __global__ void __launch_bounds__(kThreads)
 sylv_leaf_kernel(int m, int p, const double *__restrict__ A, int lda, const double *__restrict__ Bm, int ldb,
                  const double *__restrict__ C, int ldc, double cscale, double *__restrict__ X, int ldx, int s,
                  int nbr, int j_lo, int nsplit, const double *__restrict__ P, size_t split_stride)
 {
-    constexpr int LD = SB + 1;
+    constexpr int LD = kLeafLD;
     extern __shared__ double sm[];
-    double *As = sm;
-    double *Bs = As + SB * LD;
-    double *Xs = Bs + SB * LD;
+    double *Xs = sm;                                   // float64 x (seeds, then results)
+    double *ad = Xs + SB * LD, *bd = ad + SB;          // diagonals of the blocks of A and B
+    float *Ah = reinterpret_cast<float *>(bd + SB), *Al = Ah + SB * LD;
+    float *Bh = Al + SB * LD, *Bl = Bh + SB * LD;
+    float *Xh = Bl + SB * LD, *Xl = Xh + SB * LD;
     const int J = j_lo + blockIdx.x;
     const int I = nbr - 1 - s + J;
     const int r0 = I * SB, c0 = J * SB;
     const int bi = min(SB, m - r0), bj = min(SB, p - c0);
     for (int idx = threadIdx.x; idx < SB * SB; idx += kThreads) {
         const int i = idx % SB, j = idx / SB;
-        As[i + j * LD] = (i <= j && j < bi) ? SGT_AT(A, lda, r0 + i, r0 + j) : 0.0;
-        Bs[i + j * LD] = (i <= j && j < bj) ? SGT_AT(Bm, ldb, c0 + i, c0 + j) : 0.0;
+        const double a = (i <= j && j < bi) ? SGT_AT(A, lda, r0 + i, r0 + j) : 0.0;
+        const double b = (i <= j && j < bj) ? SGT_AT(Bm, ldb, c0 + i, c0 + j) : 0.0;
+        split_df(a, Ah[i + j * LD], Al[i + j * LD]);
+        split_df(b, Bh[i + j * LD], Bl[i + j * LD]);
+        if (i == j) {
+            ad[i] = a;
+            bd[i] = b;
+        }
         double c = 0.0;
         if (i < bi && j < bj) {
             c = cscale * SGT_AT(C, ldc, r0 + i, c0 + j);
             for (int t = 0; t < nsplit; t++) c += P[(size_t)t * split_stride + (size_t)blockIdx.x * SB * SB + i + j * SB];
         }
         Xs[i + j * LD] = c;
+        Xh[i + j * LD] = 0.f;
+        Xl[i + j * LD] = 0.f;
     }
     __syncthreads();
-    // anti-diagonal steps inside the block; each entry's two sums are split
-    // over four consecutive lanes (terms k = part mod 4) and reduced by
-    // shuffles, so that all warps share the float64 work of a step
     const int nsteps = bi + bj - 1;
     const int part = threadIdx.x & 3, slot = threadIdx.x >> 2;   // 64 entry slots
     for (int st = 0; st < nsteps; st++) {
@@ -243,14 +334,20 @@ sylv_leaf_kernel(int m, int p, const double *__restrict__ A, int lda, const doub
         const int pp = plo + slot;
         const bool live = pp <= phi;
         const int q = st - (bi - 1 - pp);
-        double acc = 0.0;
+        float h = 0.f, l = 0.f;
         if (live) {
-            for (int k = pp + 1 + part; k < bi; k += 4) acc = fma(-As[pp + k * LD], Xs[k + q * LD], acc);
-            for (int k = part; k < q; k += 4) acc = fma(Xs[pp + k * LD], Bs[k + q * LD], acc);
+            for (int k = pp + 1 + part; k < bi; k += 4)
+                df_mac(h, l, -Ah[pp + k * LD], -Al[pp + k * LD], Xh[k + q * LD], Xl[k + q * LD]);
+            for (int k = part; k < q; k += 4)
+                df_mac(h, l, Xh[pp + k * LD], Xl[pp + k * LD], Bh[k + q * LD], Bl[k + q * LD]);
         }
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        if (live && part == 0) Xs[pp + q * LD] = (Xs[pp + q * LD] + acc) / (As[pp + pp * LD] - Bs[q + q * LD]);
+        df_add_df(h, l, __shfl_xor_sync(0xffffffffu, h, 1), __shfl_xor_sync(0xffffffffu, l, 1));
+        df_add_df(h, l, __shfl_xor_sync(0xffffffffu, h, 2), __shfl_xor_sync(0xffffffffu, l, 2));
+        if (live && part == 0) {
+            const double x = (Xs[pp + q * LD] + ((double)h + (double)l)) / (ad[pp] - bd[q]);
+            Xs[pp + q * LD] = x;
+            split_df(x, Xh[pp + q * LD], Xl[pp + q * LD]);
+        }
         __syncthreads();
     }
     for (int idx = threadIdx.x; idx < bi * bj; idx += kThreads) {
@@ -308,7 +405,7 @@ signtri_status sylvester_run(int m, int p, const double *A, int lda, const doubl
     const size_t split_stride = (size_t)std::min(nbr, nbc) * SB * SB;
     double *P = static_cast<double *>(ws.take(split_stride * kSplitMax * sizeof(double)));
     if (!P) return SIGNTRI_ERR_NO_WORKSPACE;
-    const size_t leaf_smem = 3 * (size_t)SB * (SB + 1) * sizeof(double);
+    const size_t leaf_smem = kLeafSmem;
     SGT_CUDA_TRY(cudaFuncSetAttribute(sylv_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem));
     const int nsteps = nbr + nbc - 1;
     for (int s = 0; s < nsteps; s++) {
