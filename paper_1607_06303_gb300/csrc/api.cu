@@ -192,8 +192,9 @@ void work_estimates(int n, const ScanResult &r, double *w_ph, double *w_ps)
 //    sum each entry needs, exactly the useful count w_ph) at the float64
 //    product rate, and one off-diagonal leaf step per block column (about
 //    0.075, 0.21, 0.65 ms at b = 16, 32, 64);
-//  * Parlett-Sylvester runs the Sylvester block sums (n_- n_+ n flops) and
-//    one in-block step per block anti-diagonal (about 0.4 ms); when k > 0,
+//  * Parlett-Sylvester runs the Sylvester block sums (n_- n_+ n flops, in
+//    double-float at about 4e12 flop/s) and one in-block step per block
+//    anti-diagonal (about 0.29 ms); when k > 0,
 //    the reorder and the back-transform (emulated-float64 tensor-core
 //    products, about 6e13 float64 flop/s).  The windowed reorder (n >= 512)
 //    runs sweeps of windows of 128 at offsets 0 / 64: a negative moves at
@@ -202,7 +203,7 @@ void work_estimates(int n, const ScanResult &r, double *w_ph, double *w_ps)
 //    sweep costs its window launch (rounds and float64 rotations, growing
 //    with the swaps per window) and about 0.1 ms of launches, plus the
 //    products and slicing of its about min(n_-, n / 256) active windows,
-//    each about 1.1e-8 n seconds.  The
+//    each about 0.9e-8 n seconds.  The
 //    unblocked rounds (n < 512) cost 12 n k flops at the Givens rate and two
 //    launches per round.
 constexpr double kLaunchSeconds = 5e-6;
@@ -211,9 +212,10 @@ double ph_leaf_step_seconds(int b)
     return b <= 16 ? 0.075e-3 : (b <= 32 ? 0.21e-3 : 0.65e-3);
 }
 constexpr double kSweepLaunchSeconds = 1e-4;
-constexpr double kSylvStepSeconds = 0.40e-3;
+constexpr double kSylvStepSeconds = 0.29e-3;
+constexpr double kSylvRate = 4e12;
 constexpr double kEmulatedRate = 6e13;
-constexpr double kWindowProductSeconds = 1.1e-8;
+constexpr double kWindowProductSeconds = 0.9e-8;
 
 double window_launch_seconds(double kw)
 {
@@ -230,7 +232,7 @@ signtri_variant choose_variant(int n, const ScanResult &r)
     const double t_ph = w_ph / g_rate_gemm + nb * ph_leaf_step_seconds(b) + 2.0 * nb * kLaunchSeconds;
     const double np = r.n_pos, nm = r.n_neg, k = (double)r.swaps;
     const double sylv_steps = std::ceil(np / 64.0) + std::ceil(nm / 64.0) - 1.0;
-    double t_ps = np * nm * nd / g_rate_gemm + sylv_steps * kSylvStepSeconds;
+    double t_ps = np * nm * nd / kSylvRate + sylv_steps * kSylvStepSeconds;
     if (r.swaps > 0) {
         t_ps += 2.0 * nd * std::fmin(np, nm) * (nd + std::fmax(np, nm)) / kEmulatedRate;
         if (n >= kBlockedReorderMin) {

@@ -133,9 +133,9 @@ def test_auto_choice(gpu_lib):
     # Parlett-Sylvester, balanced random order favours Parlett-Higham (run in
     # its arithmetic-efficient form, whose work is the useful count).  The
     # cases are ones where the measured times on GB300 differ clearly:
-    # n = 4096, p = 0.1 sorted: PS 30.8 ms against PH 48.9 ms; n = 2000, 3
-    # negatives: PH 11.0 ms against PS 15.9 ms (a small PH with leaves of 16
-    # beats about 32 window sweeps); n = 8192, 3 negatives: PS 101 ms against
+    # n = 4096, p = 0.1 sorted: PS 20.6 ms against PH 48.8 ms; n = 2000, 3
+    # negatives: PH 11.0 ms against PS 13.5 ms (a small PH with leaves of 16
+    # beats about 32 window sweeps); n = 8192, 3 negatives: PS 77 ms against
     # PH 223 ms.
     import torch
     cases = [(4096, 0.1, "sorted", gpu_lib.Variant.PS_FP64),
