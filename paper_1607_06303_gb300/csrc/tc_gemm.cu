@@ -188,6 +188,29 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
         : "r"(taddr));
 }
 
+// The float64 value of a normal fp32 x, assembled from its bits (sign,
+// exponent rebiased from 127 to 1023, significand moved up 29 places):
+// exact, and without the float64 pipe a conversion instruction would use
+// (slow on this part).  Zeros and fp32 subnormals (below 2^-126) give 0;
+// infinities and NaNs stay infinities and NaNs.
+__device__ __forceinline__ double f32_to_f64_bits(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0) return 0.0;
+    const unsigned long long de = (e == 0xffu) ? 0x7ffull : (unsigned long long)(e - 127 + 1023);
+    const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) | (de << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
+// hi + lo in float64 with one float64 addition (the operands converted by
+// bits)
+__device__ __forceinline__ double df_to_double(float hi, float lo)
+{
+    return __dadd_rn(f32_to_f64_bits(hi), f32_to_f64_bits(lo));
+}
+
 // Error-free addition of a into (hi, lo): Knuth's two-sum.
 __device__ __forceinline__ void df_add(float &hi, float &lo, float a)
 {
@@ -505,7 +528,7 @@ tc_blocksum_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_consta
                     const float sc = __fmul_rn(srow_f, scol ? scol[cbase + cc + i] : 1.f);
                     const float hs = __fmul_rn(h[i], sc), ls = __fmul_rn(lo[cc + i], sc);
                     if (o2) o2[(size_t)(cc + i) * 64] = make_float2(hs, ls);
-                    else if (o && cbase + cc + i < qo.ncols) o[(size_t)(cc + i) * qo.ld] = (double)hs + (double)ls;
+                    else if (o && cbase + cc + i < qo.ncols) o[(size_t)(cc + i) * qo.ld] = df_to_double(hs, ls);
                 }
             }
         }
@@ -827,7 +850,7 @@ tc_pair2_kernel(const __grid_constant__ CUtensorMap mTop, const __grid_constant_
                 const float sc = __fmul_rn(srow_f, scol ? scol[cbase + i] : 1.f);
                 const float hs = __fmul_rn(h, sc), ls = __fmul_rn(lo[i], sc);
                 if (o2) o2[(size_t)i * 64] = make_float2(hs, ls);
-                else if (o && cbase + i < qo.ncols) o[(size_t)i * qo.ld] = (double)hs + (double)ls;
+                else if (o && cbase + i < qo.ncols) o[(size_t)i * qo.ld] = df_to_double(hs, ls);
             }
         }
         if (!ok) {
