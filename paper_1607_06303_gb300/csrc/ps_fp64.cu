@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "df_arith.cuh"
 #include "internal.cuh"
 #include "reorder_schedule.h"
 
@@ -139,35 +140,14 @@ __global__ void copy_upper_identity_kernel(int n, const double *__restrict__ src
 
 // Double-float (fp32 hi + lo) arithmetic for the Sylvester block sums.
 // GB300 issues float64 at about 1/64 of its fp32 rate, so the sums run as
-// double-float products on the fp32 pipes: each float64 operand is cut
-// exactly into hi (its leading 24 significand bits) and lo (the next 29,
-// rounded to 24) with integer operations only; a product term is
+// double-float products on the fp32 pipes: each float64 operand is cut into
+// hi (its leading 24 significand bits) and lo (the next 29, rounded to 24)
+// by split_df (df_arith.cuh, integer operations only); a product term is
 // a_h b_h (Dekker's exact product by FMA) + a_h b_l + a_l b_h, accumulated
 // with Knuth's two-sum.  About 2^-47 relative per term, summed in a fixed
-// order; values beyond fp32's exponent range (below 2^-126 or from 2^127)
+// order; values beyond fp32's exponent range (below 2^-126 or from 2^128)
 // are not represented (the first flush to 0; inputs and solutions here stay
 // far inside the range).
-__device__ __forceinline__ void split_df(double x, float &hi, float &lo)
-{
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((bits >> 52) & 0x7ff) - 1023;          // unbiased exponent
-    if (e < -126 || e > 127) {                                  // zero, tiny, or out of fp32's range
-        hi = (e > 127) ? __int_as_float(((unsigned)(bits >> 32) & 0x80000000u) | 0x7f800000u) : 0.f;
-        lo = 0.f;
-        return;
-    }
-    const unsigned sign = (unsigned)(bits >> 32) & 0x80000000u;
-    const unsigned long long mant = bits & 0xfffffffffffffull;  // 52 fraction bits
-    // hi: the implicit 1 and the top 23 fraction bits
-    hi = __int_as_float((int)(sign | ((unsigned)(e + 127) << 23) | (unsigned)(mant >> 29)));
-    // lo: the remaining 29 fraction bits, value mant_lo 2^(e - 52)
-    const unsigned mlo = (unsigned)(mant & 0x1fffffffull);
-    float l = __uint2float_rn(mlo);                             // < 2^29, rounded to 24 bits
-    const int el = e - 52;                                      // l * 2^el; el >= -178
-    l = (el >= -126) ? __fmul_rn(l, __int_as_float((el + 127) << 23))
-                     : __fmul_rn(__fmul_rn(l, __int_as_float((el + 127 + 64) << 23)), __int_as_float((127 - 64) << 23));
-    lo = sign ? -l : l;
-}
 
 // acc += a b in double-float (acc_h, acc_l unnormalised between renormalisations)
 __device__ __forceinline__ void df_mac(float &ah_acc, float &al_acc, float a_h, float a_l, float b_h, float b_l)

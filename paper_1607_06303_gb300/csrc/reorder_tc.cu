@@ -24,6 +24,7 @@
 
 #include <cuda_bf16.h>
 
+#include "df_arith.cuh"
 #include "exact_slices.cuh"
 #include "internal.cuh"
 #include "reorder_schedule.h"
@@ -39,10 +40,12 @@ constexpr int kMaxRot = (kWin / 2) * (kWin / 2);   // swaps of a window at most
 constexpr int kWinThreads = 512;
 constexpr int kSlices = 7;                 // exact slices of 7 bits: float64 products to about 2^-45
 
+// Shared memory of a window: its block as double-float planes (hi, lo), the
+// logged rotations (c, s as double-float pairs, and k), the exact diagonal.
 size_t window_smem_bytes()
 {
-    return (size_t)kWin * kWinLD * sizeof(double) + 2 * (size_t)kMaxRot * sizeof(double) +
-           (size_t)kMaxRot * sizeof(short);
+    return 2 * (size_t)kWin * kWinLD * sizeof(float) + 4 * (size_t)kMaxRot * sizeof(float) +
+           (size_t)kWin * sizeof(double) + (size_t)kMaxRot * sizeof(short);
 }
 
 // One window per CTA: stable partition of T[W, W] by swaps, then Z_W as the
@@ -50,15 +53,22 @@ size_t window_smem_bytes()
 // Z_W[i][j] under the column's power-of-two scale sZ[a + j] (rp rows of
 // pitch kp per slice).  Entries of ZC outside the windows' blocks are never
 // read (the products' K ranges stay inside the window).
+// GB300's float64 rate is about 1/64 of its fp32 rate, and a window is one
+// SM's work, so the rotations are applied in double-float (df_arith.cuh:
+// about 2^-47 per operation) to the block held as hi/lo planes; the
+// diagonal stays float64 (swapped exactly) and each rotation's (c, s) is
+// computed in float64 from it and the coupling, one thread per pair.
 __global__ void __launch_bounds__(kWinThreads)
 window_sort_kernel(double *__restrict__ Tr, int ldt, const int2 *__restrict__ wins, __nv_bfloat16 *__restrict__ ZC,
                    float *__restrict__ sZ, int rp, int kp)
 {
     extern __shared__ double wsm[];
-    double *B = wsm;                                   // B[i + j * kWinLD] = T[a + i, a + j]
-    double *lc = B + kWin * kWinLD;                    // logged rotations (cs, sn, k), round by round
-    double *ls = lc + kMaxRot;
-    short *lk = reinterpret_cast<short *>(ls + kMaxRot);
+    double *dg = wsm;                                        // dg[i] = T[a + i, a + i]
+    float *Bh = reinterpret_cast<float *>(dg + kWin);        // Bh/Bl[i + j * kWinLD]: T[a + i, a + j], i < j
+    float *Bl = Bh + kWin * kWinLD;
+    float *lch = Bl + kWin * kWinLD, *lcl = lch + kMaxRot;   // logged rotations, round by round
+    float *lsh = lcl + kMaxRot, *lsl = lsh + kMaxRot;
+    short *lk = reinterpret_cast<short *>(lsl + kMaxRot);
     __shared__ signed char sg[kWin];
     __shared__ short pm[kWin];                        // log index of the round's pair holding position i, or -1
     __shared__ int roff[2 * kWin + 4];
@@ -66,10 +76,12 @@ window_sort_kernel(double *__restrict__ Tr, int ldt, const int2 *__restrict__ wi
     const int a = wins[blockIdx.x].x, w = wins[blockIdx.x].y;
     for (int idx = threadIdx.x; idx < kWin * kWin; idx += kWinThreads) {
         const int i = idx % kWin, j = idx / kWin;
-        B[i + j * kWinLD] = (i <= j && j < w) ? SGT_AT(Tr, ldt, a + i, a + j) : 0.0;
+        const double v = (i < j && j < w) ? SGT_AT(Tr, ldt, a + i, a + j) : 0.0;
+        split_df(v, Bh[i + j * kWinLD], Bl[i + j * kWinLD]);
+        if (i == j) dg[i] = (j < w) ? SGT_AT(Tr, ldt, a + i, a + i) : 1.0;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kWin; i += kWinThreads) sg[i] = (i < w && B[i + i * kWinLD] > 0.0) ? 1 : -1;
+    for (int i = threadIdx.x; i < kWin; i += kWinThreads) sg[i] = (i < w && dg[i] > 0.0) ? 1 : -1;
     if (threadIdx.x == 0) {
         nlog = 0;
         nround = 0;
@@ -83,8 +95,8 @@ window_sort_kernel(double *__restrict__ Tr, int ldt, const int2 *__restrict__ wi
         if (r > 0 && quiet[(r - 1) & 1] >= 2) break;
         if (threadIdx.x < 32) {
             // warp 0 finds the round's pairs (positions 4 lane .. 4 lane + 3),
-            // logs their rotations in position order (a prefix count by
-            // shuffles) and marks both positions of each pair in pm
+            // logs them in position order (a prefix count by shuffles) and
+            // marks both positions of each pair in pm
             const int lane = threadIdx.x, base = nlog;
             bool on[4];
             int c = 0;
@@ -105,13 +117,7 @@ window_sort_kernel(double *__restrict__ Tr, int ldt, const int2 *__restrict__ wi
             for (int q = 0; q < 4; q++) {
                 mine[q] = -1;
                 if (on[q]) {
-                    // G's first column: the eigenvector of the entry moving up
-                    const int k = 4 * lane + q;
-                    const double aa = B[k + k * kWinLD], cc = B[(k + 1) + (k + 1) * kWinLD], bb = B[k + (k + 1) * kWinLD];
-                    const double d = cc - aa, h = hypot(bb, d);
-                    lc[e] = bb / h;
-                    ls[e] = d / h;
-                    lk[e] = (short)k;
+                    lk[e] = (short)(4 * lane + q);
                     mine[q] = e++;
                 }
             }
@@ -130,47 +136,59 @@ window_sort_kernel(double *__restrict__ Tr, int ldt, const int2 *__restrict__ wi
             }
         }
         __syncthreads();
+        const int e0 = roff[r], P = nlog - e0;
+        // each pair's rotation, in float64 from the exact diagonal and the
+        // coupling: G's first column is the eigenvector of the entry moving up
+        for (int t = threadIdx.x; t < P; t += kWinThreads) {
+            const int e = e0 + t, k = lk[e];
+            const double aa = dg[k], cc = dg[k + 1];
+            const double bb = df_to_double(Bh[k + (k + 1) * kWinLD], Bl[k + (k + 1) * kWinLD]);
+            const double d = cc - aa, h = hypot(bb, d);
+            split_df(bb / h, lch[e], lcl[e]);
+            split_df(d / h, lsh[e], lsl[e]);
+        }
+        __syncthreads();
         // the round's rotations, one item per (pair, position x): x right of
         // the pair -- G^T on rows k, k+1 of column x (with G_q on columns x,
         // x+1 as well when x starts pair q); x left of the pair -- G on
         // columns k, k+1 of row x (rows inside a pair are done from that
         // pair's side); x = k -- the exact swap of the 2 x 2 diagonal block,
         // whose coupling is unchanged.  No two items touch the same entry.
-        const int e0 = roff[r], P = nlog - e0;
         for (int idx = threadIdx.x; idx < P * kWin; idx += kWinThreads) {
             const int e = e0 + idx / kWin, x = idx % kWin, k = lk[e];
             if (x >= w) continue;
-            const double c1 = lc[e], s1 = ls[e];
+            const float ch = lch[e], cl = lcl[e], sh = lsh[e], sl = lsl[e];
             if (x >= k + 2) {
                 const int q = pm[x];
                 if (q < 0) {
-                    double *x0 = &B[k + x * kWinLD], *x1 = &B[(k + 1) + x * kWinLD];
-                    const double u = *x0, v = *x1;
-                    *x0 = c1 * u + s1 * v;
-                    *x1 = -s1 * u + c1 * v;
+                    const int i0 = k + x * kWinLD, i1 = i0 + 1;
+                    const float uh = Bh[i0], ul = Bl[i0], vh = Bh[i1], vl = Bl[i1];
+                    df_rot(ch, cl, uh, ul, sh, sl, vh, vl, Bh[i0], Bl[i0]);          // c u + s v
+                    df_rot(-sh, -sl, uh, ul, ch, cl, vh, vl, Bh[i1], Bl[i1]);        // -s u + c v
                 } else if (lk[q] == x) {
-                    const double c2 = lc[q], s2 = ls[q];
-                    double *p00 = &B[k + x * kWinLD], *p10 = p00 + 1, *p01 = p00 + kWinLD, *p11 = p01 + 1;
-                    const double b00 = *p00, b10 = *p10, b01 = *p01, b11 = *p11;
-                    const double r00 = c1 * b00 + s1 * b10, r10 = -s1 * b00 + c1 * b10;
-                    const double r01 = c1 * b01 + s1 * b11, r11 = -s1 * b01 + c1 * b11;
-                    *p00 = r00 * c2 + r01 * s2;
-                    *p01 = -r00 * s2 + r01 * c2;
-                    *p10 = r10 * c2 + r11 * s2;
-                    *p11 = -r10 * s2 + r11 * c2;
+                    const float c2h = lch[q], c2l = lcl[q], s2h = lsh[q], s2l = lsl[q];
+                    const int i00 = k + x * kWinLD, i10 = i00 + 1, i01 = i00 + kWinLD, i11 = i01 + 1;
+                    float r00h, r00l, r10h, r10l, r01h, r01l, r11h, r11l;
+                    df_rot(ch, cl, Bh[i00], Bl[i00], sh, sl, Bh[i10], Bl[i10], r00h, r00l);
+                    df_rot(-sh, -sl, Bh[i00], Bl[i00], ch, cl, Bh[i10], Bl[i10], r10h, r10l);
+                    df_rot(ch, cl, Bh[i01], Bl[i01], sh, sl, Bh[i11], Bl[i11], r01h, r01l);
+                    df_rot(-sh, -sl, Bh[i01], Bl[i01], ch, cl, Bh[i11], Bl[i11], r11h, r11l);
+                    df_rot(c2h, c2l, r00h, r00l, s2h, s2l, r01h, r01l, Bh[i00], Bl[i00]);    // u c + v s
+                    df_rot(-s2h, -s2l, r00h, r00l, c2h, c2l, r01h, r01l, Bh[i01], Bl[i01]);  // -u s + v c
+                    df_rot(c2h, c2l, r10h, r10l, s2h, s2l, r11h, r11l, Bh[i10], Bl[i10]);
+                    df_rot(-s2h, -s2l, r10h, r10l, c2h, c2l, r11h, r11l, Bh[i11], Bl[i11]);
                 }
             } else if (x < k) {
                 if (pm[x] < 0) {
-                    double *x0 = &B[x + k * kWinLD], *x1 = &B[x + (k + 1) * kWinLD];
-                    const double u = *x0, v = *x1;
-                    *x0 = u * c1 + v * s1;
-                    *x1 = -u * s1 + v * c1;
+                    const int i0 = x + k * kWinLD, i1 = i0 + kWinLD;
+                    const float uh = Bh[i0], ul = Bl[i0], vh = Bh[i1], vl = Bl[i1];
+                    df_rot(ch, cl, uh, ul, sh, sl, vh, vl, Bh[i0], Bl[i0]);          // u c + v s
+                    df_rot(-sh, -sl, uh, ul, ch, cl, vh, vl, Bh[i1], Bl[i1]);        // -u s + v c
                 }
             } else if (x == k) {
-                double *d0 = &B[k + k * kWinLD], *d1 = &B[(k + 1) + (k + 1) * kWinLD];
-                const double t0 = *d0;
-                *d0 = *d1;
-                *d1 = t0;
+                const double t0 = dg[k];
+                dg[k] = dg[k + 1];
+                dg[k + 1] = t0;
                 sg[k] = 1;
                 sg[k + 1] = -1;
             }
@@ -180,13 +198,15 @@ window_sort_kernel(double *__restrict__ Tr, int ldt, const int2 *__restrict__ wi
     if (threadIdx.x == 0) roff[nround] = nlog;
     for (int idx = threadIdx.x; idx < kWin * kWin; idx += kWinThreads) {
         const int i = idx % kWin, j = idx / kWin;
-        if (i <= j && j < w) SGT_AT(Tr, ldt, a + i, a + j) = B[i + j * kWinLD];
+        if (j < w && i < j) SGT_AT(Tr, ldt, a + i, a + j) = df_to_double(Bh[i + j * kWinLD], Bl[i + j * kWinLD]);
+        else if (j < w && i == j) SGT_AT(Tr, ldt, a + i, a + i) = dg[i];
     }
     __syncthreads();
     // Z = I G_1 G_2 ..., round by round (a round's rotations act on disjoint columns)
     for (int idx = threadIdx.x; idx < kWin * kWin; idx += kWinThreads) {
         const int i = idx % kWin, j = idx / kWin;
-        B[i + j * kWinLD] = (i == j) ? 1.0 : 0.0;
+        Bh[i + j * kWinLD] = (i == j) ? 1.f : 0.f;
+        Bl[i + j * kWinLD] = 0.f;
     }
     __syncthreads();
     for (int r = 0; r < nround; r++) {
@@ -194,21 +214,22 @@ window_sort_kernel(double *__restrict__ Tr, int ldt, const int2 *__restrict__ wi
         for (int idx = threadIdx.x; idx < (e1 - e0) * kWin; idx += kWinThreads) {
             const int e = e0 + idx / kWin, i = idx % kWin;
             const int k = lk[e];
-            double *x0 = &B[i + k * kWinLD], *x1 = &B[i + (k + 1) * kWinLD];
-            const double u = *x0, v = *x1, c1 = lc[e], s1 = ls[e];
-            *x0 = u * c1 + v * s1;
-            *x1 = -u * s1 + v * c1;
+            const int i0 = i + k * kWinLD, i1 = i0 + kWinLD;
+            const float uh = Bh[i0], ul = Bl[i0], vh = Bh[i1], vl = Bl[i1];
+            df_rot(lch[e], lcl[e], uh, ul, lsh[e], lsl[e], vh, vl, Bh[i0], Bl[i0]);
+            df_rot(-lsh[e], -lsl[e], uh, ul, lch[e], lcl[e], vh, vl, Bh[i1], Bl[i1]);
         }
         __syncthreads();
     }
     // per column of Z: the power-of-two scale above its largest entry (an
-    // orthogonal column: between 1 / sqrt(w) and 1), then its exact slices
+    // orthogonal column: between 1 / sqrt(w) and 1; |hi + lo| < 2^e whenever
+    // |hi| < 2^e, lo being at most half an ulp of hi), then its exact slices
     __shared__ int cexp[kWin];
     for (int j = threadIdx.x; j < w; j += kWinThreads) {
-        double mx = 0.0;
-        for (int i = 0; i < w; i++) mx = fmax(mx, fabs(B[i + j * kWinLD]));
+        float mx = 0.f;
+        for (int i = 0; i < w; i++) mx = fmaxf(mx, fabsf(Bh[i + j * kWinLD]));
         int e = 0;
-        frexp(mx, &e);
+        frexpf(mx, &e);
         cexp[j] = e;
         sZ[a + j] = ldexpf(1.f, e);
     }
@@ -216,7 +237,7 @@ window_sort_kernel(double *__restrict__ Tr, int ldt, const int2 *__restrict__ wi
     for (int idx = threadIdx.x; idx < w * w; idx += kWinThreads) {
         const int i = idx % w, j = idx / w;
         float q[kSlices];
-        exact_slices<kSlices>(B[i + j * kWinLD], cexp[j], kSlices, 7, q);
+        exact_slices<kSlices>(df_to_double(Bh[i + j * kWinLD], Bl[i + j * kWinLD]), cexp[j], kSlices, 7, q);
 #pragma unroll
         for (int sl = 0; sl < kSlices; sl++)
             ZC[((size_t)sl * rp + a + j) * kp + a + i] = __float2bfloat16_rn(q[sl]);

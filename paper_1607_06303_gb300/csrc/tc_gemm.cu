@@ -34,6 +34,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include "df_arith.cuh"
 #include "internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -186,29 +187,6 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-}
-
-// The float64 value of a normal fp32 x, assembled from its bits (sign,
-// exponent rebiased from 127 to 1023, significand moved up 29 places):
-// exact, and without the float64 pipe a conversion instruction would use
-// (slow on this part).  Zeros and fp32 subnormals (below 2^-126) give 0;
-// infinities and NaNs stay infinities and NaNs.
-__device__ __forceinline__ double f32_to_f64_bits(float x)
-{
-    const unsigned u = __float_as_uint(x);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0) return 0.0;
-    const unsigned long long de = (e == 0xffu) ? 0x7ffull : (unsigned long long)(e - 127 + 1023);
-    const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) | (de << 52) |
-                                 ((unsigned long long)(u & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)d);
-}
-
-// hi + lo in float64 with one float64 addition (the operands converted by
-// bits)
-__device__ __forceinline__ double df_to_double(float hi, float lo)
-{
-    return __dadd_rn(f32_to_f64_bits(hi), f32_to_f64_bits(lo));
 }
 
 // Error-free addition of a into (hi, lo): Knuth's two-sum.
