@@ -133,15 +133,14 @@ def test_auto_choice(gpu_lib):
     # Parlett-Sylvester, balanced random order favours Parlett-Higham (run in
     # its arithmetic-efficient form, whose work is the useful count).  The
     # cases are ones where the measured times on GB300 differ clearly:
-    # n = 4096, p = 0.1 sorted: PS 20.6 ms against PH 48.8 ms; n = 2000, 3
-    # negatives: PH 11.0 ms against PS 13.5 ms (a small PH with leaves of 16
-    # beats about 32 window sweeps); n = 8192, 3 negatives: PS 77 ms against
-    # PH 223 ms.
+    # n = 4096, p = 0.1 sorted: PS 20.4 ms against PH 48.8 ms; n = 2000,
+    # p = 0.1 random: PH 13.2 ms against PS 29.7 ms; n = 4096 and 8192 with 3
+    # negatives in random order: PS 33 and 75 ms against PH 42 and 223 ms.
     import torch
     cases = [(4096, 0.1, "sorted", gpu_lib.Variant.PS_FP64),
              (2000, 0.5, "random", gpu_lib.Variant.PH_FP64_EFFICIENT),
-             (1024, 0.1, "random", gpu_lib.Variant.PH_FP64_EFFICIENT),
-             (2000, 3 / 2000, "random", gpu_lib.Variant.PH_FP64_EFFICIENT),
+             (2000, 0.1, "random", gpu_lib.Variant.PH_FP64_EFFICIENT),
+             (4096, 3 / 4096, "random", gpu_lib.Variant.PS_FP64),
              (8192, 3 / 8192, "random", gpu_lib.Variant.PS_FP64)]
     for n, p, order, expect in cases:
         T = make_T(n, p, seed=35, order=order)
