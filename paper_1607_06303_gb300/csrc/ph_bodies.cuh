@@ -457,6 +457,10 @@ __device__ __forceinline__ void offdiag_leaf_body(int n, const double *__restric
             uq = scol[q];
         }
         const bool opp = (up + uq == 0.0);
+        // the entry's reciprocal divisor, on the group's fourth lane while
+        // the sums run (it does not depend on them)
+        double rinv = 0.0;
+        if (live && part == 3) rinv = opp ? 1.0 / (TI[p + p * LD] - TJ[q + q * LD]) : 1.0 / (up + uq);
         double a = 0.0, b = 0.0;
         if (live) {
             const double *A = opp ? TI : UI;
@@ -468,12 +472,8 @@ __device__ __forceinline__ void offdiag_leaf_body(int n, const double *__restric
         b += __shfl_xor_sync(0xffffffffu, b, 1);
         a += __shfl_xor_sync(0xffffffffu, a, 2);
         b += __shfl_xor_sync(0xffffffffu, b, 2);
-        if (live && part == 0) {
-            double v;
-            if (opp) v = (C[p + q * LD] - a + b) / (TI[p + p * LD] - TJ[q + q * LD]);
-            else     v = (C[p + q * LD] - a - b) / (up + uq);
-            V[p + q * LD] = v;
-        }
+        rinv = __shfl_sync(0xffffffffu, rinv, (threadIdx.x & 31) | 3);
+        if (live && part == 0) V[p + q * LD] = (opp ? C[p + q * LD] - a + b : C[p + q * LD] - a - b) * rinv;
         __syncthreads();
     }
     for (int idx = threadIdx.x; idx < B * bj; idx += kThreads) {

@@ -314,6 +314,10 @@ sylv_leaf_kernel(int m, int p, const double *__restrict__ A, int lda, const doub
         const int pp = plo + slot;
         const bool live = pp <= phi;
         const int q = st - (bi - 1 - pp);
+        // the entry's reciprocal divisor, on the group's fourth lane while
+        // the sums run (it does not depend on them)
+        double rinv = 0.0;
+        if (live && part == 3) rinv = 1.0 / (ad[pp] - bd[q]);
         float h = 0.f, l = 0.f;
         if (live) {
             for (int k = pp + 1 + part; k < bi; k += 4)
@@ -323,8 +327,9 @@ sylv_leaf_kernel(int m, int p, const double *__restrict__ A, int lda, const doub
         }
         df_add_df(h, l, __shfl_xor_sync(0xffffffffu, h, 1), __shfl_xor_sync(0xffffffffu, l, 1));
         df_add_df(h, l, __shfl_xor_sync(0xffffffffu, h, 2), __shfl_xor_sync(0xffffffffu, l, 2));
+        rinv = __shfl_sync(0xffffffffu, rinv, (threadIdx.x & 31) | 3);
         if (live && part == 0) {
-            const double x = (Xs[pp + q * LD] + ((double)h + (double)l)) / (ad[pp] - bd[q]);
+            const double x = (Xs[pp + q * LD] + ((double)h + (double)l)) * rinv;
             Xs[pp + q * LD] = x;
             split_df(x, Xh[pp + q * LD], Xl[pp + q * LD]);
         }
