@@ -16,7 +16,7 @@
 //   Q[:, W]          <- Q[:, W] Z_W
 // (left and right factors commute, so all row products of a sweep come
 // first, then all column products).  GB300 has no fast float64 product, so
-// these run on the tensor cores as emulated-float64 products of exact 7-bit
+// these run on the tensor cores as emulated-float64 products of exact 8-bit
 // slices (tc_gemm.cu), written straight back into T and Q: each product
 // reads the slices, snapshots taken before it, never the matrix it writes.
 #include <algorithm>
@@ -38,7 +38,12 @@ constexpr int kWin = 128;                  // window width (two 64-row panels)
 constexpr int kWinLD = kWin + 1;
 constexpr int kMaxRot = (kWin / 2) * (kWin / 2);   // swaps of a window at most
 constexpr int kWinThreads = 512;
-constexpr int kSlices = 7;                 // exact slices of 7 bits: float64 products to about 2^-45
+// Exact slices of 8 bits, 6 of them (48 bits, the 21 pairs with s + t <= 5):
+// a window product's K range is one window (128 <= 256), so every fp32 unit
+// sum of products below 2^16 stays exact, and 8-bit slices take a quarter
+// fewer pairs, and so a quarter fewer epilogue drains, than 7-bit ones.
+constexpr int kSlices = 6;
+constexpr int kBits = 8;
 
 // Shared memory of a window: its block as double-float planes (hi, lo), the
 // logged rotations (c, s as double-float pairs, and k), the exact diagonal.
@@ -237,7 +242,7 @@ window_sort_kernel(double *__restrict__ Tr, int ldt, const int2 *__restrict__ wi
     for (int idx = threadIdx.x; idx < w * w; idx += kWinThreads) {
         const int i = idx % w, j = idx / w;
         float q[kSlices];
-        exact_slices<kSlices>(df_to_double(Bh[i + j * kWinLD], Bl[i + j * kWinLD]), cexp[j], kSlices, 7, q);
+        exact_slices<kSlices>(df_to_double(Bh[i + j * kWinLD], Bl[i + j * kWinLD]), cexp[j], kSlices, kBits, q);
 #pragma unroll
         for (int sl = 0; sl < kSlices; sl++)
             ZC[((size_t)sl * rp + a + j) * kp + a + i] = __float2bfloat16_rn(q[sl]);
@@ -314,7 +319,7 @@ __device__ __forceinline__ int line_exp(const unsigned long long *mx, int line, 
     return e;
 }
 
-// Exact 7-bit slices of the used tiles (S = kSlices), K-contiguous lines of
+// Exact slices (kSlices of kBits bits) of the used tiles, K-contiguous lines of
 // pitch kp, rp lines per slice; the line scales go to `scale` (written once
 // per line, by the CTA of the first (kColsT, kRowsQ) or last (kRowsT) block).
 template <int MODE>
@@ -340,8 +345,8 @@ masked_slices_kernel(int n, const double *__restrict__ M, int ldm, const int *__
             }
             const int e = line_exp(mx, j, n);
             float q0[kSlices], q1[kSlices];
-            exact_slices<kSlices>(v0, e, kSlices, 7, q0);
-            exact_slices<kSlices>(v1, e, kSlices, 7, q1);
+            exact_slices<kSlices>(v0, e, kSlices, kBits, q0);
+            exact_slices<kSlices>(v1, e, kSlices, kBits, q1);
 #pragma unroll
             for (int sl = 0; sl < kSlices; sl++)
                 *reinterpret_cast<__nv_bfloat162 *>(&out[((size_t)sl * rp + j) * kp + kk]) =
@@ -360,8 +365,8 @@ masked_slices_kernel(int n, const double *__restrict__ M, int ldm, const int *__
             const int r = l0 + t, kk = k0 + 2 * lane;
             const int e = zero ? 0 : line_exp(mx, r, n);
             float q0[kSlices], q1[kSlices];
-            exact_slices<kSlices>(tile[2 * lane][t], e, kSlices, 7, q0);
-            exact_slices<kSlices>(tile[2 * lane + 1][t], e, kSlices, 7, q1);
+            exact_slices<kSlices>(tile[2 * lane][t], e, kSlices, kBits, q0);
+            exact_slices<kSlices>(tile[2 * lane + 1][t], e, kSlices, kBits, q1);
 #pragma unroll
             for (int sl = 0; sl < kSlices; sl++)
                 *reinterpret_cast<__nv_bfloat162 *>(&out[((size_t)sl * rp + r) * kp + kk]) =
@@ -463,7 +468,7 @@ signtri_status reorder_blocked_run(int n, const double *T, int ldt, double *Tr, 
         SGT_CUDA_TRY(cudaMemcpyAsync(d_wins, wins_all.data(), wins_all.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
         SGT_CUDA_TRY(cudaMemcpyAsync(d_jobs, jobs_all.data(), jobs_all.size() * sizeof(TcJob), cudaMemcpyHostToDevice, st));
         SGT_CUDA_TRY(cudaMemcpyAsync(d_kbl, kbl_all.data(), kbl_all.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-        const TcPairs pairs = ozaki_pairs_impl(kSlices, 7);
+        const TcPairs pairs = ozaki_pairs_impl(kSlices, kBits);
         SGT_CUDA_TRY(cudaMemcpyAsync(d_pairs, &pairs, sizeof(TcPairs), cudaMemcpyHostToDevice, st));
         // the zero rows past the matrix, read by the half-empty jobs
         SGT_CUDA_TRY(cudaMemsetAsync(ZC, 0, (size_t)kSlices * rp * kp * 2, st));
@@ -477,7 +482,7 @@ signtri_status reorder_blocked_run(int n, const double *T, int ldt, double *Tr, 
                            const TcQuadOut &out) -> signtri_status {
             const int cnt = p.j[phase + 1] - p.j[phase];
             if (cnt == 0) return SIGNTRI_OK;
-            return tc_blocksums(top, top, left, left, d_jobs + p.j[phase], cnt, pairs, d_pairs, kExactChunkKb7, nullptr,
+            return tc_blocksums(top, top, left, left, d_jobs + p.j[phase], cnt, pairs, d_pairs, kExactChunkKb8, nullptr,
                                 out, d_err, SIGNTRI_KC_GIVENS, st, fl * p.kb[phase]);
         };
         const int zero_lb = np / 64;
