@@ -34,6 +34,30 @@ __device__ __forceinline__ void split_df(double x, float &hi, float &lo)
     lo = sign ? -l : l;
 }
 
+// x truncated to fp32 (its leading 24 significand bits; 0 below 2^-126,
+// infinity from 2^128), from its bits
+__device__ __forceinline__ float f64_to_f32_trunc(double x)
+{
+    float hi, lo;
+    split_df(x, hi, lo);
+    return hi;
+}
+
+// |x| as the bits of a non-negative float64: they order like the values,
+// so maxima can be taken as integers
+__device__ __forceinline__ unsigned long long abs_bits(double x)
+{
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// The exponent e of frexp for a non-negative float64 given by its bits
+// (m = f 2^e, f in [0.5, 1)); subnormals give -1022, zero gives 0
+__device__ __forceinline__ int frexp_exp_of_bits(unsigned long long b)
+{
+    const int ef = (int)(b >> 52);
+    return ef ? ef - 1022 : (b ? -1022 : 0);
+}
+
 // The float64 value of an fp32 x, assembled from its bits (exact).  Zeros
 // and fp32 subnormals give 0; infinities and NaNs stay so.
 __device__ __forceinline__ double f32_to_f64_bits(float x)

@@ -66,6 +66,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "df_arith.cuh"
 #include "internal.cuh"
 #include "gathered_layout.h"
 #include "sweep_schedule.h"
@@ -694,7 +695,7 @@ __global__ void absmax_diag_blocks_kernel(int n, const double *__restrict__ M, i
          e += (long long)gridDim.x * blockDim.x) {
         const int b = (int)(e / (MB * MB)), w = (int)(e % (MB * MB));
         const int i = b * MB + w % MB, j = b * MB + w / MB;
-        if (i < j && j < n) m = fmaxf(m, fabsf((float)SGT_AT(M, ldm, i, j)));
+        if (i < j && j < n) m = fmaxf(m, fabsf(f64_to_f32_trunc(SGT_AT(M, ldm, i, j))));
     }
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
@@ -724,8 +725,9 @@ __global__ void corr_magnitude_kernel(int n, const float *__restrict__ D, const 
         const float tj = D[j];
         for (int i = threadIdx.x; i < j; i += blockDim.x) {
             const float ti = D[i];
-            const float v = ((ti > 0.f) != (tj > 0.f)) ? (float)fabs(SGT_AT(Rc, ldr, i, j)) / fabsf(ti - tj)
-                                                       : 0.5f * (float)fabs(SGT_AT(Rs, ldr, i, j));
+            // fp32 magnitudes truncated from the bits (no float64 conversion)
+            const float v = ((ti > 0.f) != (tj > 0.f)) ? fabsf(f64_to_f32_trunc(SGT_AT(Rc, ldr, i, j))) / fabsf(ti - tj)
+                                                       : 0.5f * fabsf(f64_to_f32_trunc(SGT_AT(Rs, ldr, i, j)));
             m = fmaxf(m, v);
         }
     }

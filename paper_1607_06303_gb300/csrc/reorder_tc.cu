@@ -281,28 +281,28 @@ masked_absmax_kernel(int n, const double *__restrict__ M, int ldm, const int *__
         const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
         for (int c = wp; c < 64; c += 8) {
             const int j = l0 + c;
-            double v = 0.0;
+            unsigned long long v = 0;   // maxima on the bits of |x| (integer pipes)
             if (j < n) {
-                if (k0 + lane < n) v = fabs(SGT_AT(M, ldm, k0 + lane, j));
-                if (k0 + lane + 32 < n) v = fmax(v, fabs(SGT_AT(M, ldm, k0 + lane + 32, j)));
+                if (k0 + lane < n) v = abs_bits(SGT_AT(M, ldm, k0 + lane, j));
+                if (k0 + lane + 32 < n) v = max(v, abs_bits(SGT_AT(M, ldm, k0 + lane + 32, j)));
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-            if (lane == 0 && v > 0.0) atomicMax(&mx[j], (unsigned long long)__double_as_longlong(v));
+            for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0 && v > 0) atomicMax(&mx[j], v);
         }
     } else {
         // a thread per row and quarter of the columns, then the quarters reduced
-        __shared__ double part[4][64];
+        __shared__ unsigned long long part[4][64];
         const int t = threadIdx.x & 63, q = threadIdx.x >> 6, r = l0 + t;
-        double v = 0.0;
+        unsigned long long v = 0;
         if (r < n)
             for (int c = q * 16; c < q * 16 + 16; c++)
-                if (k0 + c < n) v = fmax(v, fabs(SGT_AT(M, ldm, r, k0 + c)));
+                if (k0 + c < n) v = max(v, abs_bits(SGT_AT(M, ldm, r, k0 + c)));
         part[q][t] = v;
         __syncthreads();
         if (threadIdx.x < 64) {
-            v = fmax(fmax(part[0][t], part[1][t]), fmax(part[2][t], part[3][t]));
-            if (v > 0.0) atomicMax(&mx[r], (unsigned long long)__double_as_longlong(v));
+            v = max(max(part[0][t], part[1][t]), max(part[2][t], part[3][t]));
+            if (v > 0) atomicMax(&mx[r], v);
         }
     }
 }
@@ -310,13 +310,8 @@ masked_absmax_kernel(int n, const double *__restrict__ M, int ldm, const int *__
 __device__ __forceinline__ int line_exp(const unsigned long long *mx, int line, int n)
 {
     if (line >= n) return 0;
-    const double m = __longlong_as_double((long long)mx[line]);
-    int e = 0;
-    if (m > 0.0) {
-        frexp(m, &e);
-        e = max(e, -120);
-    }
-    return e;
+    const unsigned long long m = mx[line];
+    return m ? max(frexp_exp_of_bits(m), -120) : 0;
 }
 
 // Exact slices (kSlices of kBits bits) of the used tiles, K-contiguous lines of

@@ -21,6 +21,7 @@
 
 #include <cuda_bf16.h>
 
+#include "df_arith.cuh"
 #include "exact_slices.cuh"
 #include "internal.cuh"
 #include "tc_gemm.cuh"
@@ -38,22 +39,22 @@ constexpr int TS = 32;   // transpose tile
 __global__ void absmax_kernel(int m, int k, const double *__restrict__ M, int ldm, int tri, bool rows,
                               unsigned long long *__restrict__ out)
 {
-    __shared__ double tile[TS][TS + 1];
+    __shared__ unsigned long long tile[TS][TS + 1];   // bits of |m_ij|: maxima on the integer pipes
     const int i0 = blockIdx.y * TS, j0 = blockIdx.x * TS;
     if (tri && j0 + TS - 1 <= i0) return;   // wholly on or below the diagonal
     for (int y = threadIdx.y; y < TS; y += blockDim.y) {
         const int i = i0 + threadIdx.x, j = j0 + y;
-        double v = 0.0;
-        if (i < m && j < k && (tri == 0 || i < j)) v = fabs(SGT_AT(M, ldm, i, j));
+        unsigned long long v = 0;
+        if (i < m && j < k && (tri == 0 || i < j)) v = abs_bits(SGT_AT(M, ldm, i, j));
         tile[threadIdx.x][y] = v;
     }
     __syncthreads();
     if (threadIdx.y == 0) {
-        double best = 0.0;
+        unsigned long long best = 0;
         const int line = threadIdx.x;
-        for (int t = 0; t < TS; t++) best = fmax(best, rows ? tile[line][t] : tile[t][line]);
+        for (int t = 0; t < TS; t++) best = max(best, rows ? tile[line][t] : tile[t][line]);
         const int g = (rows ? i0 : j0) + line;
-        if (best > 0.0 && g < (rows ? m : k)) atomicMax(&out[g], (unsigned long long)__double_as_longlong(best));
+        if (best > 0 && g < (rows ? m : k)) atomicMax(&out[g], best);
     }
 }
 
@@ -64,28 +65,28 @@ __global__ void absmax_kernel(int m, int k, const double *__restrict__ M, int ld
 __global__ void absmax_both_kernel(int n, const double *__restrict__ M, int ldm, int tri,
                                    unsigned long long *__restrict__ out_rows, unsigned long long *__restrict__ out_cols)
 {
-    __shared__ double tile[64][65];   // [column][row]
+    __shared__ unsigned long long tile[64][65];   // [column][row], bits of |m_ij|
     const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
     if (tri && j0 + 63 <= i0) return;
     const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;   // 256 threads
     for (int c = ty; c < 64; c += 4) {
         const int i = i0 + tx, j = j0 + c;
-        double v = 0.0;
-        if (i < n && j < n && (tri == 0 || i < j)) v = fabs(SGT_AT(M, ldm, i, j));
+        unsigned long long v = 0;
+        if (i < n && j < n && (tri == 0 || i < j)) v = abs_bits(SGT_AT(M, ldm, i, j));
         tile[c][tx] = v;
     }
     __syncthreads();
     if (threadIdx.x < 64) {
-        double best = 0.0;
-        for (int t = 0; t < 64; t++) best = fmax(best, tile[t][threadIdx.x]);
+        unsigned long long best = 0;
+        for (int t = 0; t < 64; t++) best = max(best, tile[t][threadIdx.x]);
         const int g = i0 + threadIdx.x;
-        if (best > 0.0 && g < n) atomicMax(&out_rows[g], (unsigned long long)__double_as_longlong(best));
+        if (best > 0 && g < n) atomicMax(&out_rows[g], best);
     } else if (threadIdx.x < 128) {
         const int c = threadIdx.x - 64;
-        double best = 0.0;
-        for (int t = 0; t < 64; t++) best = fmax(best, tile[c][t]);
+        unsigned long long best = 0;
+        for (int t = 0; t < 64; t++) best = max(best, tile[c][t]);
         const int g = j0 + c;
-        if (best > 0.0 && g < n) atomicMax(&out_cols[g], (unsigned long long)__double_as_longlong(best));
+        if (best > 0 && g < n) atomicMax(&out_cols[g], best);
     }
 }
 
@@ -94,12 +95,8 @@ __global__ void pow2_scale_kernel(int n, const unsigned long long *__restrict__ 
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double mx = __longlong_as_double((long long)maxbits[i]);
-    int e = 0;
-    if (mx > 0.0) {
-        frexp(mx, &e);
-        e = max(e, -120);
-    }
+    const unsigned long long mb = maxbits[i];
+    const int e = mb ? max(frexp_exp_of_bits(mb), -120) : 0;
     scale[i] = ldexpf(1.0f, e);
 }
 
