@@ -191,7 +191,7 @@ void work_estimates(int n, const ScanResult &r, double *w_ph, double *w_ps)
 //  * Parlett-Higham runs the arithmetic-efficient form (Section 5.3: only the
 //    sum each entry needs, exactly the useful count w_ph) at the float64
 //    product rate, and one off-diagonal leaf step per block column (about
-//    0.075, 0.21, 0.7 ms at b = 16, 32, 64);
+//    0.06, 0.21, 0.7 ms at b = 16, 32, 64);
 //  * Parlett-Sylvester runs the Sylvester block sums (n_- n_+ n flops, in
 //    double-float at about 4e12 flop/s) and one in-block step per block
 //    anti-diagonal (about 0.29 ms); when k > 0,
@@ -203,18 +203,18 @@ void work_estimates(int n, const ScanResult &r, double *w_ph, double *w_ps)
 //    sweep costs its window launch (rounds and float64 rotations, growing
 //    with the swaps per window, about 0.1 ms with a few and 0.5 ms with
 //    ~770), plus the products and slicing of its about min(n_-, n / 256)
-//    active windows, each about 0.87e-8 n seconds.  The
+//    active windows, each about 0.7e-8 n seconds.  The
 //    unblocked rounds (n < 512) cost 12 n k flops at the Givens rate and two
 //    launches per round.
 constexpr double kLaunchSeconds = 5e-6;
 double ph_leaf_step_seconds(int b)
 {
-    return b <= 16 ? 0.075e-3 : (b <= 32 ? 0.21e-3 : 0.7e-3);
+    return b <= 16 ? 0.06e-3 : (b <= 32 ? 0.21e-3 : 0.7e-3);
 }
 constexpr double kSylvStepSeconds = 0.29e-3;
 constexpr double kSylvRate = 4e12;
 constexpr double kEmulatedRate = 6e13;
-constexpr double kWindowProductSeconds = 0.87e-8;
+constexpr double kWindowProductSeconds = 0.7e-8;
 
 double window_launch_seconds(double kw)
 {
