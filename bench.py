@@ -49,8 +49,8 @@ UNIT = "GFLOP/s"
 TRAFFIC_SOURCES = ("paper_1607_06303_gb300/csrc/tc_gemm.cu", "paper_1607_06303_gb300/csrc/mixed.cu")
 TRAFFIC = {
     # n = 16384, p = 0.5 random, PH_MIXED_FP16 (profiles/launches_mixed_n16384.txt)
-    ("residual", "59f76311a78493eb"): 34.876e9,
-    ("block_sums_tc", "59f76311a78493eb"): 639.0e6,
+    ("residual", "4fd781973f172d7d"): 35.946e9,
+    ("block_sums_tc", "4fd781973f172d7d"): 638.9e6,
 }
 
 
