@@ -170,6 +170,11 @@ def run_reference(args, rank):
                    "n": args.n, "p": args.p, "order": args.order},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        # the two arms run different sizes: their rates compare, their seconds
+        # do not; a full-size time at the sample's rate is given for context
+        "comparison": "useful-GFLOP/s rates (the oracle on a %d-window sample, the GPU on n=%d); "
+                      "seconds are not comparable" % (m, args.n),
+        "extrapolated_seconds_per_solve": workload.useful_flops(np.sign(np.diag(T))) / (val * 1e9),
     }
     return line
 
