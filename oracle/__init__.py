@@ -43,6 +43,8 @@ def lib():
         L.oracle_sign_tri_complex.restype = ctypes.c_int
         L.oracle_sign_schur_complex.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int]
         L.oracle_sign_schur_complex.restype = ctypes.c_int
+        L.oracle_funm.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int]
+        L.oracle_funm.restype = ctypes.c_int
         L.oracle_max_threads.argtypes = []
         L.oracle_max_threads.restype = ctypes.c_int
         _lib = L
@@ -163,6 +165,23 @@ def sign_schur_complex(Q, T):
     if st != OK:
         raise OracleError(st)
     return S
+
+
+PHI = {"exp": 1, "log": 2, "sqrt": 3, "sign": 4}
+
+
+def funm(T, phi):
+    """phi(T) of an upper triangular T with distinct diagonal entries by
+    Parlett's substitution (Section 2, Algorithm 1): f_ii = phi(t_ii), then
+    each f_ij from entry (i, j) of TF = FT.  phi: "exp", "log", "sqrt"
+    (principal branches, t_ii > 0 for the last two) or "sign"."""
+    T = _colmajor(T)
+    n = T.shape[0]
+    F = np.zeros((n, n), dtype=np.float64, order="F")
+    st = lib().oracle_funm(n, _ptr(T), max(n, 1), _ptr(F), max(n, 1), PHI[phi])
+    if st != OK:
+        raise OracleError(st)
+    return F
 
 
 def max_threads():

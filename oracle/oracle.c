@@ -43,6 +43,15 @@
  *                          by entry in the order of oracle_sign_tri, in C99
  *                          complex arithmetic; S = Q U Q^H for unitary Q.
  *                          Matrices interleaved (re, im) column-major.
+ *   oracle_funm            Parlett's substitution for a general function
+ *                          phi (Section 2, Algorithm 1): f_ii = phi(t_ii),
+ *                          then entry (i,j) of TF = FT solved for f_ij,
+ *                          (t_ii - t_jj) f_ij = t_ij (f_ii - f_jj)
+ *                                + sum_{i<k<j} (f_ik t_kj - t_ik f_kj),
+ *                          in the order of oracle_sign_tri.  phi: 1 exp,
+ *                          2 log (t_ii > 0), 3 sqrt (t_ii > 0), 4 sign
+ *                          (the sign function through Eq. 1 alone).  Needs
+ *                          distinct diagonal entries.
  *   oracle_sign_spectral   Brute force from the definition in Section 1:
  *                          sign(T) = Z sign(D) Z^{-1}, with Z the (unit upper
  *                          triangular) eigenvector matrix of T, in long double.
@@ -378,6 +387,48 @@ int oracle_sign_schur_complex(int n, const double *Q, int ldq, const double *T, 
     free(U);
     free(W);
     return st;
+}
+
+/*
+ * Status 1 also for a repeated diagonal entry (Algorithm 1 divides by
+ * t_ii - t_jj) and for a phi outside its domain (log, sqrt of t_ii <= 0).
+ */
+static double scalar_phi(int phi, double x)
+{
+    switch (phi) {
+    case 1: return exp(x);
+    case 2: return log(x);
+    case 3: return sqrt(x);
+    default: return scalar_sign(x);
+    }
+}
+
+int oracle_funm(int n, const double *T, int ldt, double *F, int ldf, int phi)
+{
+    int st = check_args(n, T, ldt, F, ldf);
+    if (st != ORACLE_OK) return st;
+    if (phi < 1 || phi > 4) return ORACLE_BAD_ARG;
+    for (int i = 0; i < n; i++) {
+        if ((phi == 2 || phi == 3) && !(AT(T, ldt, i, i) > 0.0)) return ORACLE_BAD_ARG;
+        for (int j = i + 1; j < n; j++)
+            if (AT(T, ldt, i, i) == AT(T, ldt, j, j)) return ORACLE_BAD_ARG;
+    }
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) AT(F, ldf, i, j) = 0.0;
+    for (int i = 0; i < n; i++) AT(F, ldf, i, i) = scalar_phi(phi, AT(T, ldt, i, i));
+    for (int j = 1; j < n; j++) {
+        for (int i = j - 1; i >= 0; i--) {
+            double s = 0.0;
+            for (int k = i + 1; k <= j - 1; k++) {
+                double a = AT(F, ldf, i, k) * AT(T, ldt, k, j);
+                double b = AT(T, ldt, i, k) * AT(F, ldf, k, j);
+                s = s + (a - b);
+            }
+            double den = AT(T, ldt, i, i) - AT(T, ldt, j, j);
+            AT(F, ldf, i, j) = (AT(T, ldt, i, j) * (AT(F, ldf, i, i) - AT(F, ldf, j, j)) + s) / den;
+        }
+    }
+    return ORACLE_OK;
 }
 
 int oracle_max_threads(void)

@@ -302,3 +302,60 @@ def test_complex_imaginary_axis_is_an_error(oracle_mod):
     with pytest.raises(oracle_mod.OracleError) as e:
         oracle_mod.sign_tri_complex(T)
     assert e.value.status == oracle_mod.ZERO_EIGENVALUE
+
+
+# ---- general phi: Parlett's substitution (Section 2, Algorithm 1) ----------
+
+def _spread_T(n, seed, lo=1.0, hi=3.0):
+    # distinct, well separated diagonal entries in random order
+    rng = np.random.Generator(np.random.PCG64(seed))
+    T = np.triu(rng.standard_normal((n, n))) / math.sqrt(n)
+    T[np.arange(n), np.arange(n)] = rng.permutation(np.linspace(lo, hi, n))
+    return np.asfortranarray(T)
+
+
+@pytest.mark.parametrize("n", [5, 20, 40])
+def test_funm_vs_scipy(oracle_mod, n):
+    sl = pytest.importorskip("scipy.linalg")
+    T = _spread_T(n, n)
+    for phi, ref in (("exp", sl.expm(T)), ("log", sl.logm(T)), ("sqrt", sl.sqrtm(T))):
+        F = oracle_mod.funm(T, phi)
+        assert np.linalg.norm(F - ref) <= 1e-12 * np.linalg.norm(ref), phi
+        assert np.all(np.tril(F, -1) == 0)
+
+
+def test_funm_identities(oracle_mod):
+    sl = pytest.importorskip("scipy.linalg")
+    T = _spread_T(30, 3)
+    S = oracle_mod.funm(T, "sqrt")
+    assert np.linalg.norm(S @ S - T) <= 1e-13 * np.linalg.norm(T)
+    L = oracle_mod.funm(T, "log")
+    assert np.linalg.norm(sl.expm(L) - T) <= 1e-12 * np.linalg.norm(T)
+    E, Em = oracle_mod.funm(T, "exp"), oracle_mod.funm(-T, "exp")
+    assert np.linalg.norm(E @ Em - np.eye(30)) <= 1e-12 * np.linalg.norm(E) * np.linalg.norm(Em)
+    for F in (S, L, E):
+        assert np.linalg.norm(F @ T - T @ F) <= 1e-13 * np.linalg.norm(F) * np.linalg.norm(T)
+
+
+def test_funm_2x2_and_sign(oracle_mod):
+    T = np.array([[1.5, 0.7], [0.0, 0.4]])
+    F = oracle_mod.funm(T, "exp")
+    assert F[0, 0] == math.exp(1.5) and F[1, 1] == math.exp(0.4)
+    assert abs(F[0, 1] - 0.7 * (math.exp(1.5) - math.exp(0.4)) / 1.1) <= 1e-15 * abs(F[0, 1])
+    # the sign function through Eq. 1 alone agrees with Algorithm 3's mix of
+    # Eqs. 1 and 2 when the diagonal entries are well separated (with close
+    # equal-sign entries Eq. 1 divides by their small difference, which is
+    # why Algorithm 3 takes Eq. 2 there)
+    T = _spread_T(60, 8)
+    T[np.arange(60), np.arange(60)] *= np.where(np.arange(60) % 3 == 0, -1.0, 1.0)
+    U = oracle_mod.sign_tri(T)
+    assert np.linalg.norm(oracle_mod.funm(T, "sign") - U) <= 1e-12 * np.linalg.norm(U)
+
+
+def test_funm_errors(oracle_mod):
+    T = np.array([[1.0, 0.5], [0.0, 1.0]])       # repeated eigenvalue
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.funm(T, "exp")
+    T = np.array([[-1.0, 0.5], [0.0, 2.0]])      # log of a negative eigenvalue
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.funm(T, "log")
