@@ -108,7 +108,10 @@ typedef enum {
     SIGNTRI_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up */
     SIGNTRI_ERR_CUDA = 6,             /* a CUDA runtime call or launch failed */
     SIGNTRI_ERR_NO_WORKSPACE = 7,     /* workspace could not be allocated / too small */
-    SIGNTRI_ERR_UNSUPPORTED = 8       /* option not available in this build */
+    SIGNTRI_ERR_UNSUPPORTED = 8,      /* option not available in this build */
+    SIGNTRI_ERR_DOMAIN = 9            /* signtri_funm: a diagonal entry outside phi's domain,
+                                         not finite, or repeated (Parlett's substitution
+                                         divides by t_ii - t_jj) */
 } signtri_status;
 
 /* What the last sign_tri call on the calling host thread did. */
@@ -297,6 +300,30 @@ signtri_status signtri_sign_tri_complex(int n, const double *T, int ldt, double 
 signtri_status signtri_sign_schur_complex(int n, const double *Q, int ldq, const double *T, int ldt, double *S,
                                           int lds, void *stream);
 size_t signtri_complex_workspace_bytes(int n);
+
+/* ---- A general function of T (Section 2: Algorithms 1 and 2) --------------
+   F = phi(T) for real upper triangular T with distinct diagonal entries, by
+   Parlett's substitution: f_ii = phi(t_ii), and entry (i, j) of TF = FT,
+   (t_ii - t_jj) f_ij = t_ij (f_ii - f_jj) + sum_{i<k<j} (f_ik t_kj - t_ik f_kj),
+   blocked as Algorithm 2 with the float64 Parlett-Higham partition (the
+   off-diagonal blocks' Sylvester equations solved by the element recurrence
+   inside each block, their right-hand sums by the float64 block-sum kernels;
+   leaf size as signtri_set_cutoff).  phi: exp, the principal log and sqrt
+   (t_ii > 0), or sign (every entry through TU = UT; sign_tri's Algorithm 3
+   is the better-conditioned route for that one).  Divisions by
+   t_ii - t_jj amplify rounding when eigenvalues are close (the paper's
+   caveat); there is no cluster-based blocking.  Only T's upper triangle is
+   read; F's strictly lower part is written as 0.  SIGNTRI_ERR_DOMAIN with
+   the first offending index in signtri_get_info's bad_index when a diagonal
+   entry is outside phi's domain, not finite, or repeated.  F must not share
+   an element with T.  Synchronous on `stream`. */
+typedef enum {
+    SIGNTRI_PHI_EXP = 1,
+    SIGNTRI_PHI_LOG = 2,
+    SIGNTRI_PHI_SQRT = 3,
+    SIGNTRI_PHI_SIGN = 4
+} signtri_phi;
+signtri_status signtri_funm(int n, const double *T, int ldt, double *F, int ldf, signtri_phi phi, void *stream);
 
 /* ---- Emulated float64 product on the tensor cores --------------------------
    C = A B (A m x k, B k x n, C m x n; device pointers, column-major) with

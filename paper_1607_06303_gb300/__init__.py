@@ -16,4 +16,5 @@ from .signtri import (Info, SignTriError, Status, Variant, load, sign, sign_tri,
                       signtri_get_variant_table, signtri_set_variant_table, signtri_batched_cache_stats,
                       signtri_sign_schur, signtri_sign_schur_workspace_bytes, sign_schur,
                       signtri_sign_tri_complex, signtri_sign_schur_complex, signtri_complex_workspace_bytes,
-                      sign_complex, sign_schur_complex, to_device_complex)
+                      sign_complex, sign_schur_complex, to_device_complex,
+                      Phi, signtri_funm, funm)

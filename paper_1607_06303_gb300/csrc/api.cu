@@ -404,6 +404,7 @@ const char *signtri_status_string(signtri_status s)
     case SIGNTRI_ERR_CUDA: return "SIGNTRI_ERR_CUDA";
     case SIGNTRI_ERR_NO_WORKSPACE: return "SIGNTRI_ERR_NO_WORKSPACE";
     case SIGNTRI_ERR_UNSUPPORTED: return "SIGNTRI_ERR_UNSUPPORTED";
+    case SIGNTRI_ERR_DOMAIN: return "SIGNTRI_ERR_DOMAIN";
     }
     return "SIGNTRI_ERR_UNKNOWN";
 }
@@ -850,6 +851,31 @@ signtri_status signtri_sign_schur_complex(int n, const double *Q, int ldq, const
     SGT_CUDA_TRY(cudaMemcpyAsync(s->err_host, s->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
     SGT_CUDA_TRY(cudaStreamSynchronize(st));
     return *s->err_host ? SIGNTRI_ERR_TIMEOUT : SIGNTRI_OK;
+}
+
+signtri_status signtri_funm(int n, const double *T, int ldt, double *F, int ldf, signtri_phi phi, void *stream)
+{
+    reset_info(n);
+    if (n < 0 || phi < SIGNTRI_PHI_EXP || phi > SIGNTRI_PHI_SIGN) return SIGNTRI_ERR_BAD_ARG;
+    if (n == 0) return SIGNTRI_OK;
+    if (!T || !F || ldt < n || ldf < n) return SIGNTRI_ERR_BAD_ARG;
+    if (blocks_overlap(T, ldt, n, n, F, ldf, n, n)) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    const int b = cutoff_of(n, SIGNTRI_PH_FP64);
+    Arena ws;
+    rs = get_workspace(*s, funm_workspace_bytes(n, b), ws);
+    if (rs != SIGNTRI_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int bad = -1;
+    rs = funm_run(n, T, ldt, F, ldf, (int)phi, b, ws, &bad, st);
+    g_info.cutoff = b;
+    if (rs == SIGNTRI_ERR_DOMAIN) g_info.bad_index = bad;
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIGNTRI_OK;
 }
 
 signtri_status signtri_sylvester(int m, int p, const double *A, int lda, const double *B, int ldb, const double *C,

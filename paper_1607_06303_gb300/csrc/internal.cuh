@@ -185,6 +185,11 @@ void batched_cache_stats(long long *hits, long long *builds);
 // Bounded-wait self-test (tc_gemm.cu)
 signtri_status wait_selftest(int arrive, long long limit, int *d_err, cudaStream_t st);
 
+// General phi (funm.cu): Algorithms 1 and 2 on the float64 partition
+size_t funm_workspace_bytes(int n, int b);
+signtri_status funm_run(int n, const double *T, int ldt, double *F, int ldf, int phi, int b, Arena &ws,
+                        int *bad_index, cudaStream_t st);
+
 // Complex T (complex.cu): interleaved (re, im) column-major, ld in complex
 // elements.  bad_index receives the first bad diagonal index on a status
 // other than OK that concerns the diagonal.

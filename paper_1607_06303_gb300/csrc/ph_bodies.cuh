@@ -385,11 +385,15 @@ __device__ __forceinline__ void sign_perm_body(int n, const double *__restrict__
 // is computed by anti-diagonal s = (B-1-p) + q, since v_pq depends on V
 // entries below it in its column and left of it in its row only.
 // ---------------------------------------------------------------------------
+// general = true: U is phi(T) for a general function phi (Algorithm 2 with
+// this partition, the blocks' Sylvester equations solved by the same
+// element recurrence): every entry comes from TU = UT, with u_pp - u_qq the
+// difference of the diagonal values of phi already in U, and py0 is unused.
 template <int B>
 __device__ __forceinline__ void offdiag_leaf_body(int n, const double *__restrict__ T, int ldt,
                                                   double *__restrict__ U, int ldu, int I, int J, int nsplit,
                                                   const double *__restrict__ px0, const double *__restrict__ py0,
-                                                  size_t split_stride)
+                                                  size_t split_stride, bool general = false)
 {
     constexpr int LD = B + 1;
     extern __shared__ double sm[];
@@ -414,8 +418,8 @@ __device__ __forceinline__ void offdiag_leaf_body(int n, const double *__restric
         V[i + j * LD] = (j < bj) ? SGT_AT(T, ldt, r0 + i, c0 + j) : 0.0;   // T_IJ for now
     }
     for (int i = threadIdx.x; i < B; i += kThreads) {
-        srow[i] = sgn(SGT_AT(T, ldt, r0 + i, r0 + i));
-        scol[i] = (i < bj) ? sgn(SGT_AT(T, ldt, c0 + i, c0 + i)) : 1.0;
+        srow[i] = general ? SGT_AT(U, ldu, r0 + i, r0 + i) : sgn(SGT_AT(T, ldt, r0 + i, r0 + i));
+        scol[i] = (i < bj) ? (general ? SGT_AT(U, ldu, c0 + i, c0 + i) : sgn(SGT_AT(T, ldt, c0 + i, c0 + i))) : 1.0;
     }
     __syncthreads();
 
@@ -423,7 +427,7 @@ __device__ __forceinline__ void offdiag_leaf_body(int n, const double *__restric
         const int p = idx % B, q = idx / B;
         const double up = srow[p], uq = scol[q];
         double c;
-        if (up + uq == 0.0) {
+        if (general || up + uq == 0.0) {
             double x = 0.0;
             for (int s = 0; s < nsplit; s++) x += px0[(size_t)s * split_stride + p + q * B];
             double a = 0.0, b = 0.0;
@@ -456,7 +460,7 @@ __device__ __forceinline__ void offdiag_leaf_body(int n, const double *__restric
             up = srow[p];
             uq = scol[q];
         }
-        const bool opp = (up + uq == 0.0);
+        const bool opp = general || (up + uq == 0.0);
         // the entry's reciprocal divisor, on the group's fourth lane while
         // the sums run (it does not depend on them)
         double rinv = 0.0;

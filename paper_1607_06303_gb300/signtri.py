@@ -36,6 +36,14 @@ class Status(enum.IntEnum):
     ERR_CUDA = 6
     ERR_NO_WORKSPACE = 7
     ERR_UNSUPPORTED = 8
+    ERR_DOMAIN = 9
+
+
+class Phi(enum.IntEnum):
+    EXP = 1
+    LOG = 2
+    SQRT = 3
+    SIGN = 4
 
 
 class Info(ctypes.Structure):
@@ -108,6 +116,7 @@ _SIGNATURES = {
     "signtri_sign_tri_complex": (_I, [_I, _VP, _I, _VP, _I, _VP]),
     "signtri_sign_schur_complex": (_I, [_I, _VP, _I, _VP, _I, _VP, _I, _VP]),
     "signtri_complex_workspace_bytes": (_SZ, [_I]),
+    "signtri_funm": (_I, [_I, _VP, _I, _VP, _I, _I, _VP]),
 }
 
 SIGNTRI_NOALLOC_MAX_N = 1024
@@ -448,6 +457,25 @@ def to_device_complex(M_colmajor, device="cuda"):
     import torch
     a = np.asfortranarray(np.asarray(M_colmajor, dtype=np.complex128))
     return torch.from_numpy(np.ascontiguousarray(a.T)).to(device)
+
+
+def signtri_funm(n, T_ptr, ldt, F_ptr, ldf, phi, stream=None) -> int:
+    return load().signtri_funm(n, T_ptr or None, ldt, F_ptr or None, ldf, int(phi), stream or None)
+
+
+def funm(Tt, phi, out=None, stream=None, check=True):
+    """F = phi(T) (Phi.EXP, LOG, SQRT, SIGN) for a CUDA float64 tensor holding
+    upper triangular T column-major, by Parlett's substitution (distinct
+    diagonal entries)."""
+    import torch
+    check_operands(Tt, out)
+    n = Tt.shape[0]
+    Ft = out if out is not None else torch.empty_like(Tt)
+    with torch.cuda.device(Tt.device):
+        st = signtri_funm(n, Tt.data_ptr(), max(n, 1), Ft.data_ptr(), max(n, 1), Phi(phi), _stream_handle(stream))
+    if check and st != 0:
+        raise SignTriError(st, "signtri_funm")
+    return Ft
 
 
 def to_device(T_colmajor, device="cuda"):

@@ -96,7 +96,7 @@ def _c_kind(decl):
         return "ptr"
     words = decl.split()
     base = " ".join(words[:-1]) if len(words) > 1 else words[0]
-    return {"signtri_variant": "int", "signtri_status": "int"}.get(base, base)
+    return {"signtri_variant": "int", "signtri_status": "int", "signtri_phi": "int"}.get(base, base)
 
 
 def _ctypes_kind(t):
