@@ -103,8 +103,9 @@ typedef enum {
                                          output sharing an element with an input */
     SIGNTRI_ERR_ZERO_EIGENVALUE = 2,  /* some t_ii == 0: sign(0) is undefined (Section 1) */
     SIGNTRI_ERR_NONFINITE = 3,        /* some t_ii is NaN or infinite */
-    SIGNTRI_ERR_NO_CONVERGENCE = 4,   /* reserved: a mixed variant whose refinement
-                                         stalls falls back to SIGNTRI_PH_FP64 instead */
+    SIGNTRI_ERR_NO_CONVERGENCE = 4,   /* signtri_schur's QR iteration did not converge
+                                         (a mixed variant whose refinement stalls falls
+                                         back to SIGNTRI_PH_FP64 instead) */
     SIGNTRI_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up */
     SIGNTRI_ERR_CUDA = 6,             /* a CUDA runtime call or launch failed */
     SIGNTRI_ERR_NO_WORKSPACE = 7,     /* workspace could not be allocated / too small */
@@ -301,6 +302,35 @@ signtri_status signtri_sign_schur_complex(int n, const double *Q, int ldq, const
                                           int lds, void *stream);
 size_t signtri_complex_workspace_bytes(int n);
 
+/* ---- The Schur decomposition, and sign(A) of a general real A (Section 1) --
+   The paper's route for a general A: a complex Schur decomposition
+   A = Q T Q^H, then sign(A) = Q sign(T) Q^H.  signtri_schur computes the
+   decomposition on the GPU for a real n x n A (column-major, device):
+   Householder reduction to Hessenberg form, then the implicitly shifted QR
+   iteration in complex float64 (Wilkinson shifts, deflation at negligible
+   subdiagonal entries).  Outputs: Q unitary and T upper triangular
+   (strictly lower part written 0), both complex as above (interleaved
+   (re, im) float64, column-major, ld in complex elements); the diagonal of
+   T holds the eigenvalues in no particular order.  The QR sweeps run on
+   one CTA (a barrier per plane rotation): the front end for a general A,
+   not a tuned path.  signtri_sign_general: S = sign(A) for real A, real
+   n x n (device, column-major): signtri_schur, the complex sign of T
+   (signtri_sign_tri_complex), Q U Q^H (as signtri_sign_schur_complex), and
+   the real part (A real makes sign(A) real; the imaginary part left is
+   rounding).  Statuses: SIGNTRI_ERR_NONFINITE when A holds a non-finite
+   entry (signtri_get_info's bad_index: the first such column),
+   SIGNTRI_ERR_NO_CONVERGENCE when an eigenvalue takes more than 100 QR
+   sweeps, and for sign_general SIGNTRI_ERR_ZERO_EIGENVALUE when a computed
+   eigenvalue has real part exactly 0 (bad_index: its position on T's
+   diagonal).  Outputs must not share an element with A or with each other
+   (SIGNTRI_ERR_BAD_ARG).  Synchronous on `stream`; with a caller workspace
+   they need signtri_schur_workspace_bytes(n) and
+   signtri_sign_general_workspace_bytes(n) bytes. */
+signtri_status signtri_schur(int n, const double *A, int lda, double *Q, int ldq, double *T, int ldt, void *stream);
+size_t signtri_schur_workspace_bytes(int n);
+signtri_status signtri_sign_general(int n, const double *A, int lda, double *S, int lds, void *stream);
+size_t signtri_sign_general_workspace_bytes(int n);
+
 /* ---- A general function of T (Section 2: Algorithms 1 and 2) --------------
    F = phi(T) for real upper triangular T with distinct diagonal entries, by
    Parlett's substitution: f_ii = phi(t_ii), and entry (i, j) of TF = FT,
@@ -390,7 +420,8 @@ enum {
     SIGNTRI_KC_OTHER = 14,
     SIGNTRI_KC_RESIDUAL_SUM = 15, /* residual assembly and norms */
     SIGNTRI_KC_BATCH_GRAPH = 16,  /* one launch of the captured batch graph */
-    SIGNTRI_KC_COUNT = 17
+    SIGNTRI_KC_SCHUR = 17,        /* Schur decomposition (Hessenberg, QR sweeps) */
+    SIGNTRI_KC_COUNT = 18
 };
 
 /* on != 0: bracket every library kernel launch with CUDA events on its

@@ -167,6 +167,21 @@ def sign_schur_complex(Q, T):
     return S
 
 
+def sign_general(A):
+    """sign(A) of a general real A by the paper's route (Section 1): the
+    complex Schur form A = Q T Q^H from LAPACK (scipy.linalg.schur, a library
+    step), then sign_schur_complex; returns the real part (A real makes
+    sign(A) real; the imaginary part left is rounding)."""
+    import scipy.linalg
+    A = np.asarray(A, dtype=np.float64)
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("A must be square")
+    if A.shape[0] == 0:
+        return np.zeros((0, 0), order="F")
+    T, Z = scipy.linalg.schur(A, output="complex")
+    return np.asfortranarray(sign_schur_complex(Z, np.triu(T)).real)
+
+
 PHI = {"exp": 1, "log": 2, "sqrt": 3, "sign": 4}
 
 

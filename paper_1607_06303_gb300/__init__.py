@@ -17,4 +17,5 @@ from .signtri import (Info, SignTriError, Status, Variant, load, sign, sign_tri,
                       signtri_sign_schur, signtri_sign_schur_workspace_bytes, sign_schur,
                       signtri_sign_tri_complex, signtri_sign_schur_complex, signtri_complex_workspace_bytes,
                       sign_complex, sign_schur_complex, to_device_complex,
-                      Phi, signtri_funm, funm)
+                      Phi, signtri_funm, funm, signtri_schur, signtri_schur_workspace_bytes, schur,
+                      signtri_sign_general, signtri_sign_general_workspace_bytes, sign_general)

@@ -853,6 +853,71 @@ signtri_status signtri_sign_schur_complex(int n, const double *Q, int ldq, const
     return *s->err_host ? SIGNTRI_ERR_TIMEOUT : SIGNTRI_OK;
 }
 
+size_t signtri_schur_workspace_bytes(int n)
+{
+    if (n < 0) return 0;
+    return schur_workspace_bytes(n);
+}
+
+size_t signtri_sign_general_workspace_bytes(int n)
+{
+    if (n < 0) return 0;
+    return sign_general_workspace_bytes(n);
+}
+
+signtri_status signtri_schur(int n, const double *A, int lda, double *Q, int ldq, double *T, int ldt, void *stream)
+{
+    reset_info(n);
+    if (n < 0) return SIGNTRI_ERR_BAD_ARG;
+    if (n == 0) return SIGNTRI_OK;
+    if (!A || !Q || !T || lda < n || ldq < n || ldt < n) return SIGNTRI_ERR_BAD_ARG;
+    // A's block as doubles against the complex blocks of Q and T
+    if (blocks_overlap(A, lda, n, n, Q, 2 * ldq, 2 * n, n) || blocks_overlap(A, lda, n, n, T, 2 * ldt, 2 * n, n) ||
+        cblocks_overlap(Q, ldq, T, ldt, n))
+        return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    Arena ws;
+    rs = get_workspace(*s, schur_workspace_bytes(n), ws);
+    if (rs != SIGNTRI_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int bad = -1;
+    long long sweeps = 0;
+    rs = schur_run(n, A, lda, Q, ldq, T, ldt, ws, &bad, &sweeps, st);
+    if (rs == SIGNTRI_ERR_NONFINITE) g_info.bad_index = bad;
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIGNTRI_OK;
+}
+
+signtri_status signtri_sign_general(int n, const double *A, int lda, double *S, int lds, void *stream)
+{
+    reset_info(n);
+    if (n < 0) return SIGNTRI_ERR_BAD_ARG;
+    if (n == 0) return SIGNTRI_OK;
+    if (!A || !S || lda < n || lds < n) return SIGNTRI_ERR_BAD_ARG;
+    if (blocks_overlap(A, lda, n, n, S, lds, n, n)) return SIGNTRI_ERR_BAD_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState *s = nullptr;
+    signtri_status rs = current_state(&s);
+    if (rs != SIGNTRI_OK) return rs;
+    Arena ws;
+    rs = get_workspace(*s, sign_general_workspace_bytes(n), ws);
+    if (rs != SIGNTRI_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SGT_CUDA_TRY(cudaMemsetAsync(s->err_dev, 0, sizeof(int), st));
+    int bad = -1;
+    long long sweeps = 0;
+    rs = sign_general_run(n, A, lda, S, lds, ws, s->err_dev, &bad, &sweeps, st);
+    if (rs == SIGNTRI_ERR_ZERO_EIGENVALUE || rs == SIGNTRI_ERR_NONFINITE) g_info.bad_index = bad;
+    if (rs != SIGNTRI_OK) return rs;
+    SGT_CUDA_TRY(cudaMemcpyAsync(s->err_host, s->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SGT_CUDA_TRY(cudaStreamSynchronize(st));
+    return *s->err_host ? SIGNTRI_ERR_TIMEOUT : SIGNTRI_OK;
+}
+
 signtri_status signtri_funm(int n, const double *T, int ldt, double *F, int ldf, signtri_phi phi, void *stream)
 {
     reset_info(n);

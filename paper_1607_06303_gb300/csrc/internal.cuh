@@ -200,6 +200,17 @@ size_t complex_schur_workspace_bytes(int n);
 signtri_status complex_schur_run(int n, const double *Q, int ldq, const double *T, int ldt, double *S, int lds,
                                  Arena &ws, int *d_err, int *bad_index, cudaStream_t st);
 
+// Complex Schur decomposition of a real A and sign(A) through it (schur.cu).
+// Q, T complex as above; bad_index: the first column of A holding a
+// non-finite entry (NONFINITE), or as complex_sign_run; sweeps_out: QR
+// sweeps run.
+size_t schur_workspace_bytes(int n);
+signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, double *T, int ldt, Arena &ws,
+                         int *bad_index, long long *sweeps_out, cudaStream_t st);
+size_t sign_general_workspace_bytes(int n);
+signtri_status sign_general_run(int n, const double *A, int lda, double *S, int lds, Arena &ws, int *d_err,
+                                int *bad_index, long long *sweeps_out, cudaStream_t st);
+
 // Mixed precision with refinement (mixed.cu)
 struct MixedParams {
     double tol;              // stopping test on both relative residuals

@@ -107,6 +107,14 @@ def make_T_complex(n: int, p: float = 0.5, seed: int = 0, order: str = "random")
     return T
 
 
+def make_A(n: int, seed: int = 0) -> np.ndarray:
+    """A general real n x n matrix with entries uniform in [-50, 50] (the
+    matrices whose Schur forms make the paper's Section 6 workload);
+    column-major float64."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.asfortranarray(rng.uniform(-50.0, 50.0, size=(n, n)))
+
+
 def make_T_schur(n: int, seed: int = 0, n_neg: int = None) -> np.ndarray:
     """The paper's workload (Section 6): the real part of the complex Schur
     form of a random n x n matrix with entries uniform in [-50, 50]; inertia

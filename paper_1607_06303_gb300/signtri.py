@@ -116,6 +116,10 @@ _SIGNATURES = {
     "signtri_sign_tri_complex": (_I, [_I, _VP, _I, _VP, _I, _VP]),
     "signtri_sign_schur_complex": (_I, [_I, _VP, _I, _VP, _I, _VP, _I, _VP]),
     "signtri_complex_workspace_bytes": (_SZ, [_I]),
+    "signtri_schur": (_I, [_I, _VP, _I, _VP, _I, _VP, _I, _VP]),
+    "signtri_schur_workspace_bytes": (_SZ, [_I]),
+    "signtri_sign_general": (_I, [_I, _VP, _I, _VP, _I, _VP]),
+    "signtri_sign_general_workspace_bytes": (_SZ, [_I]),
     "signtri_funm": (_I, [_I, _VP, _I, _VP, _I, _I, _VP]),
 }
 
@@ -126,7 +130,8 @@ KC_SCAN, KC_FILL, KC_DIAG_LEAF, KC_BLOCK_SUMS_F64, KC_OFFDIAG_LEAF = 0, 1, 2, 3,
 KC_BLOCK_SUMS_TC, KC_OFFDIAG_LEAF_MIXED, KC_CONVERT, KC_RESIDUAL, KC_CORRECTION = 5, 6, 7, 8, 9
 KC_GIVENS, KC_SYLV_SUMS, KC_SYLV_LEAF, KC_GEMM_F64, KC_OTHER, KC_RESIDUAL_SUM = 10, 11, 12, 13, 14, 15
 KC_BATCH_GRAPH = 16
-KC_COUNT = 17
+KC_SCHUR = 17
+KC_COUNT = 18
 
 
 def load(path: str = LIB_PATH):
@@ -457,6 +462,54 @@ def to_device_complex(M_colmajor, device="cuda"):
     import torch
     a = np.asfortranarray(np.asarray(M_colmajor, dtype=np.complex128))
     return torch.from_numpy(np.ascontiguousarray(a.T)).to(device)
+
+
+def signtri_schur(n, A_ptr, lda, Q_ptr, ldq, T_ptr, ldt, stream=None) -> int:
+    return load().signtri_schur(n, A_ptr or None, lda, Q_ptr or None, ldq, T_ptr or None, ldt, stream or None)
+
+
+def signtri_schur_workspace_bytes(n) -> int:
+    return load().signtri_schur_workspace_bytes(n)
+
+
+def signtri_sign_general(n, A_ptr, lda, S_ptr, lds, stream=None) -> int:
+    return load().signtri_sign_general(n, A_ptr or None, lda, S_ptr or None, lds, stream or None)
+
+
+def signtri_sign_general_workspace_bytes(n) -> int:
+    return load().signtri_sign_general_workspace_bytes(n)
+
+
+def schur(At, stream=None, check=True):
+    """Complex Schur decomposition A = Q T Q^H of a real A (a CUDA float64
+    tensor in the layout above), on the GPU.  Returns (Q, T) as CUDA
+    complex128 tensors in to_device_complex's layout."""
+    import torch
+    check_operands(At)
+    n = At.shape[0]
+    Qt = torch.empty((n, n), dtype=torch.complex128, device=At.device)
+    Tt = torch.empty((n, n), dtype=torch.complex128, device=At.device)
+    with torch.cuda.device(At.device):
+        st = signtri_schur(n, At.data_ptr(), max(n, 1), Qt.data_ptr(), max(n, 1), Tt.data_ptr(), max(n, 1),
+                           _stream_handle(stream))
+    if check and st != 0:
+        raise SignTriError(st, "signtri_schur")
+    return Qt, Tt
+
+
+def sign_general(At, out=None, stream=None, check=True):
+    """S = sign(A) of a general real A (CUDA float64 tensor, layout above):
+    the Schur decomposition, the complex sign of T and Q U Q^H, all on the
+    GPU.  Returns S (real)."""
+    import torch
+    check_operands(At, out)
+    n = At.shape[0]
+    St = out if out is not None else torch.empty_like(At)
+    with torch.cuda.device(At.device):
+        st = signtri_sign_general(n, At.data_ptr(), max(n, 1), St.data_ptr(), max(n, 1), _stream_handle(stream))
+    if check and st != 0:
+        raise SignTriError(st, "signtri_sign_general")
+    return St
 
 
 def signtri_funm(n, T_ptr, ldt, F_ptr, ldf, phi, stream=None) -> int:

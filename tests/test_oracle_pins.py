@@ -359,3 +359,56 @@ def test_funm_errors(oracle_mod):
     T = np.array([[-1.0, 0.5], [0.0, 2.0]])      # log of a negative eigenvalue
     with pytest.raises(oracle_mod.OracleError):
         oracle_mod.funm(T, "log")
+
+
+@pytest.mark.parametrize("n,seed", [(1, 4), (8, 5), (30, 6), (60, 7)])
+def test_sign_general_vs_signm(oracle_mod, n, seed):
+    # the oracle's general route (LAPACK's complex Schur form, then the
+    # complex sign and Q U Q^H) against scipy's signm of A itself
+    sl = pytest.importorskip("scipy.linalg")
+    A = _paper_matrix(n, seed)
+    S = oracle_mod.sign_general(A)
+    ref = sl.signm(A)
+    assert S.dtype == np.float64
+    assert np.linalg.norm(S - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_sign_general_closed_form(oracle_mod):
+    # A = P B P^{-1} with B block diagonal: 2 x 2 blocks [a b; -b a]
+    # (eigenvalues a +- ib, sign = sign(a) I) and 1 x 1 blocks d; so
+    # sign(A) = P sign(B) P^{-1} with sign(B) diagonal +-1, no Schur form
+    # involved.  Also S^2 = I, AS = SA, trace S = n_+ - n_-.
+    pytest.importorskip("scipy.linalg")
+    rng = np.random.Generator(np.random.PCG64(21))
+    n = 40
+    B = np.zeros((n, n))
+    sB = np.zeros(n)
+    i = 0
+    while i < n:
+        a = rng.uniform(0.5, 3.0) * (1.0 if rng.random() < 0.5 else -1.0)
+        if i + 1 < n and rng.random() < 0.6:
+            b = rng.uniform(0.5, 3.0)
+            B[i:i + 2, i:i + 2] = [[a, b], [-b, a]]
+            sB[i:i + 2] = np.sign(a)
+            i += 2
+        else:
+            B[i, i] = a
+            sB[i] = np.sign(a)
+            i += 1
+    P = np.eye(n) + 0.3 * rng.standard_normal((n, n)) / math.sqrt(n)
+    Pi = np.linalg.inv(P)
+    A = P @ B @ Pi
+    ref = P @ np.diag(sB) @ Pi
+    S = oracle_mod.sign_general(A)
+    assert np.linalg.norm(S - ref) <= 1e-11 * np.linalg.norm(ref)
+    assert np.linalg.norm(S @ S - np.eye(n)) <= 1e-11 * np.linalg.norm(S) ** 2
+    assert np.linalg.norm(A @ S - S @ A) <= 1e-11 * np.linalg.norm(A) * np.linalg.norm(S)
+    assert abs(np.trace(S) - sB.sum()) <= 1e-9
+
+
+def test_sign_general_of_triangular(oracle_mod):
+    # an upper triangular A is its own Schur form: the real oracle's U
+    pytest.importorskip("scipy.linalg")
+    T = make_T(50, 0.5, seed=8)
+    assert np.linalg.norm(oracle_mod.sign_general(T) - oracle_mod.sign_tri(T)) <= \
+        1e-12 * np.linalg.norm(oracle_mod.sign_tri(T))
