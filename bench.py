@@ -80,8 +80,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="order of the leading principal window the oracle solves")
-    ap.add_argument("--workload", choices=["single", "batched"], default="single",
-                    help="batched: 2000 problems, n log-uniform in [32, 2048], p ~ U[0,1], random order")
+    ap.add_argument("--workload", choices=["single", "batched", "general"], default="single",
+                    help="batched: 2000 problems, n log-uniform in [32, 2048], p ~ U[0,1], random order; "
+                         "general: sign(A) of a general real A (--n), through the GPU Schur decomposition")
     ap.add_argument("--batch", type=int, default=2000)
     return ap.parse_args(argv)
 
@@ -339,6 +340,72 @@ def run_batched(args):
     return 0
 
 
+def run_general(args):
+    """sign(A) of a general real A (Section 1's route, all on the GPU): the
+    complex Schur decomposition, the complex sign of T and Q U Q^H, through
+    signtri_sign_general.  A: `--n` x `--n`, entries uniform in [-50, 50]
+    (the matrices of the paper's Section 6), seed 0."""
+    import numpy as np
+    import torch
+
+    import paper_1607_06303_gb300 as st
+    from paper_1607_06303_gb300.inputs import make_A
+
+    st.load()
+    torch.cuda.set_device(0)
+    n = args.n
+    A = make_A(n, seed=0)
+    At = st.to_device(A)
+    St = torch.empty_like(At)
+
+    def step():
+        st.sign_general(At, out=St)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    st.signtri_profile_reset()
+    st.signtri_profile_enable(True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    st.signtri_profile_enable(False)
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    per_class, launches = {}, 0
+    for c in range(st.signtri.KC_COUNT):
+        cnt, dms = st.signtri_profile_read(c)
+        launches += cnt
+        if cnt:
+            per_class[st.signtri_kernel_class_name(c)] = {"launches": cnt, "device_ms": dms / max(args.steps, 1)}
+    S = st.to_numpy(St)
+    line = {
+        "metric": "sign(A) of a general real A: solves per second", "value": 1e3 / ms, "unit": "solves/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "sign(A), A %d x %d, entries uniform in [-50, 50], seed 0" % (n, n)},
+        "gpu_launches": launches, "kernel_time_ms_per_solve": per_class, "clocks": clk,
+        "involution_residual": float(np.linalg.norm(S @ S - np.eye(n)) / np.linalg.norm(S) ** 2),
+    }
+    if not args.no_cpu_baseline:
+        # the oracle's route (LAPACK's Schur form, the oracle's complex sign and
+        # products) on the same A, one solve, and this run's result against it
+        import oracle
+        t0 = time.perf_counter()
+        ref = oracle.sign_general(A)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                "sample": "the same A, one solve (%.2f s)" % dt}
+        line["rel_err_vs_oracle"] = float(np.linalg.norm(S - ref) / np.linalg.norm(ref))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def reduce_over_ranks(dist, x, op, device):
     """x reduced over the replicas ("max" for times, "sum" for work done);
     x itself when the bench runs as one process."""
@@ -354,6 +421,8 @@ def main():
     args = parse_args()
     if args.workload == "batched" and args.impl == "ours":
         return run_batched(args)
+    if args.workload == "general" and args.impl == "ours":
+        return run_general(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -420,8 +420,9 @@ enum {
     SIGNTRI_KC_OTHER = 14,
     SIGNTRI_KC_RESIDUAL_SUM = 15, /* residual assembly and norms */
     SIGNTRI_KC_BATCH_GRAPH = 16,  /* one launch of the captured batch graph */
-    SIGNTRI_KC_SCHUR = 17,        /* Schur decomposition (Hessenberg, QR sweeps) */
-    SIGNTRI_KC_COUNT = 18
+    SIGNTRI_KC_SCHUR = 17,        /* Schur decomposition: QR sweeps and their rotations */
+    SIGNTRI_KC_HESSENBERG = 18,   /* Schur decomposition: Householder reduction */
+    SIGNTRI_KC_COUNT = 19
 };
 
 /* on != 0: bracket every library kernel launch with CUDA events on its

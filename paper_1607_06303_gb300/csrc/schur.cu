@@ -9,8 +9,9 @@
 //     For column k a reflector P = I - tau v v^T (v_0 = 1) maps A[k+1:, k]
 //     onto beta e_1; it is applied from the left to the columns right of k
 //     (one CTA per column: the column's dot product with v, then the
-//     update) and from the right to the rows of A and of Q0 (one thread per
-//     row).  Three launches per column.
+//     update) and from the right to the rows of A and of Q0 (the products
+//     with v, 32 rows per CTA, then the rank-1 update).  Four launches per
+//     column.
 //  2. Implicitly shifted QR iteration on H in complex float64.  A complex
 //     shift needs no double-shift pairing, so every sweep over the active
 //     window [l, i] is a chain of plane rotations: the first from
@@ -25,17 +26,23 @@
 //     Deflation takes the window's last row when its subdiagonal entry is
 //     negligible.  The rotations of a sweep depend on one another (each reads
 //     what the one before wrote), so one CTA runs the sweeps with a barrier
-//     per rotation; a launch runs sweeps until a rotation budget is spent and
-//     the host relaunches until the window is empty.  This stage is bound by
-//     that chain (about one L2 round trip per rotation, ~1.25 n^2 rotations
-//     for n eigenvalues), not by arithmetic: the decomposition is the
-//     general-matrix front end, not a tuned hot path.
+//     per rotation, applying each to the active window only; a launch runs
+//     sweeps until a rotation budget is spent and logs them, then a kernel on
+//     every SM applies the logged rotations to the columns right of each
+//     sweep's window and to Q, and the host relaunches until the window is
+//     empty.  The window part bounds the stage: about 3.4 sweeps per
+//     eigenvalue, sum over sweeps of (window)^2 ~ 1.1 n^3 entry updates of
+//     ~14 float64 operations on one SM, whose float64 rate is ~2 per cycle
+//     on GB300 -- the decomposition is the general-matrix front end, not a
+//     tuned hot path.
 //
 // Layout: A real column-major; Q, T complex interleaved (re, im) float64
 // pairs, column-major, leading dimensions counted in complex elements.
 #include <algorithm>
 #include <cfloat>
 #include <climits>
+
+#include <cooperative_groups.h>
 
 #include "internal.cuh"
 
@@ -77,26 +84,36 @@ __device__ __forceinline__ double2 csqrt_p(double2 z)
 }
 
 // The rotation G = [c s; -conj(s) c] (c real >= 0, c^2 + |s|^2 = 1) with
-// G [x; y] = [r; 0].
+// G [x; y] = [r; 0]: c = |x| / nrm, s = (x / |x|) conj(y) / nrm,
+// nrm^2 = |x|^2 + |y|^2.  x and y are first scaled by the power of two that
+// brings their largest component into [1, 2) (exact), so the squares
+// neither overflow nor lose range (below 2^-1000 the scale stops at 2^1000);
+// then two reciprocal square roots and
+// products (the rotation sits on the QR sweep's serial chain, where each
+// float64 division or hypot costs a long dependent sequence).
 __device__ __forceinline__ void make_rotation(double2 x, double2 y, double &c, double2 &s)
 {
-    const double ay = hypot(y.x, y.y);
-    if (ay == 0.0) {
+    const double my = fmax(fabs(y.x), fabs(y.y));
+    if (my == 0.0) {
         c = 1.0;
         s = make_double2(0.0, 0.0);
         return;
     }
-    const double ax = hypot(x.x, x.y);
-    if (ax == 0.0) {
+    const double m = fmax(my, fmax(fabs(x.x), fabs(x.y)));
+    const double sc = ldexp(1.0, -max(ilogb(m), -1000));   // 2^1000 at most (m subnormal)
+    const double2 xs = make_double2(x.x * sc, x.y * sc), ys = make_double2(y.x * sc, y.y * sc);
+    const double ax2 = fma(xs.x, xs.x, xs.y * xs.y), ay2 = fma(ys.x, ys.x, ys.y * ys.y);
+    if (ax2 == 0.0) {
+        const double r = rsqrt(ay2);
         c = 0.0;
-        s = make_double2(y.x / ay, -y.y / ay);
+        s = make_double2(ys.x * r, -ys.y * r);
         return;
     }
-    const double nrm = hypot(ax, ay);
-    c = ax / nrm;
-    const double2 u = make_double2(x.x / ax, x.y / ax);   // x / |x|
-    const double2 t = cmul(u, cconj(y));
-    s = make_double2(t.x / nrm, t.y / nrm);
+    const double inv_n = rsqrt(ax2 + ay2), inv_ax = rsqrt(ax2);
+    c = ax2 * inv_ax * inv_n;
+    const double2 t = cmul(xs, cconj(ys));
+    const double f = inv_ax * inv_n;
+    s = make_double2(t.x * f, t.y * f);
 }
 
 // (a, b) of rows k, k+1 in one column -> G (a, b)
@@ -213,22 +230,49 @@ __global__ void house_left_kernel(int n, int k, double *__restrict__ H, const do
     for (int i = threadIdx.x; i < m; i += blockDim.x) col[i] = fma(-v[i], w, col[i]);
 }
 
-// Row r of H (r < n) or of Q0 (r >= n): M[r, k+1:] -= tau (M[r, k+1:] v) v^T.
-__global__ void house_right_kernel(int n, int k, double *__restrict__ H, double *__restrict__ Q0,
-                                   const double *__restrict__ v, const double *__restrict__ tau)
+// The right application M[r, k+1:] -= tau (M[r, k+1:] v) v^T to the rows of
+// H (r < n) and of Q0 (r >= n), in two launches: y_r = tau M[r, k+1:] v with
+// 32 rows per CTA (lane = row, so each column's 32 entries are one
+// coalesced read) and the columns split over the 8 warps, then the rank-1
+// update with a CTA per column.
+constexpr int kGemvWarps = 8;
+__global__ void __launch_bounds__(32 * kGemvWarps)
+house_gemv_kernel(int n, int k, const double *__restrict__ H, const double *__restrict__ Q0,
+                  const double *__restrict__ v, const double *__restrict__ tau, double *__restrict__ y)
 {
+    __shared__ double part[kGemvWarps][32];
     const double t = *tau;
     if (t == 0.0) return;
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= 2 * n) return;
-    double *M = g < n ? H : Q0;
-    const int r = g < n ? g : g - n;
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    const int g = blockIdx.x * 32 + lane;
     const int m = n - k - 1;
-    double *row = &SGT_A(M, n, r, k + 1);
-    double y = 0.0;
-    for (int j = 0; j < m; j++) y = fma(row[(size_t)j * n], v[j], y);
-    y *= t;
-    for (int j = 0; j < m; j++) row[(size_t)j * n] = fma(-y, v[j], row[(size_t)j * n]);
+    double acc = 0.0;
+    if (g < 2 * n) {
+        const double *M = g < n ? H : Q0;
+        const int r = g < n ? g : g - n;
+        for (int j = w; j < m; j += kGemvWarps) acc = fma(SGT_A(M, n, r, k + 1 + j), v[j], acc);
+    }
+    part[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && g < 2 * n) {
+        double sum = 0.0;
+        for (int q = 0; q < kGemvWarps; q++) sum += part[q][lane];
+        y[g] = t * sum;
+    }
+}
+
+__global__ void house_rank1_kernel(int n, int k, double *__restrict__ H, double *__restrict__ Q0,
+                                   const double *__restrict__ v, const double *__restrict__ tau,
+                                   const double *__restrict__ y)
+{
+    if (*tau == 0.0) return;
+    const int j = k + 1 + blockIdx.x;
+    const double vj = v[blockIdx.x];
+    for (int g = threadIdx.x; g < 2 * n; g += blockDim.x) {
+        double *M = g < n ? H : Q0;
+        const int r = g < n ? g : g - n;
+        SGT_A(M, n, r, j) = fma(-y[g], vj, SGT_A(M, n, r, j));
+    }
 }
 
 // complex T = H with its entries below the subdiagonal exactly 0; complex Q = Q0
@@ -248,9 +292,16 @@ struct QrState {
     int ihi;          // last row of the active window (-1: all converged)
     int its;          // sweeps since the last deflation
     int status;       // 0 running, 1 converged, 2 no convergence
-    int pad;
+    int logged;       // sweeps in the log of the last launch
     long long sweeps;
     long long rotations;
+};
+
+// A sweep of the last launch: its window [l, i] and where its i - l
+// rotations start in the rotation log.
+struct SweepRec {
+    int l, i;
+    long long off;
 };
 
 __global__ void qr_state_init_kernel(int n, QrState *st)
@@ -258,160 +309,359 @@ __global__ void qr_state_init_kernel(int n, QrState *st)
     st->ihi = n - 1;
     st->its = 0;
     st->status = 0;
-    st->pad = 0;
+    st->logged = 0;
     st->sweeps = 0;
     st->rotations = 0;
 }
 
-// One CTA.  Thread 0 owns the 2 x 2 block at (k, k) and row k+2 of columns
-// k, k+1, where the next rotation's inputs (h_{k+1,k}, h_{k+2,k}) are
-// formed, so it computes that rotation too and hands it over in shared
-// memory (two slots, alternating): one barrier per rotation, and no entry is
-// written by one thread while another reads it.
-__global__ void __launch_bounds__(kQrThreads)
-schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, double2 *__restrict__ Q, int ldq, QrState *__restrict__ st,
-                long long budget)
+// One cluster of kQrCluster CTAs runs the sweeps.  On GB300 a float64 warp
+// instruction holds its SM sub-partition's float64 pipe for ~64 cycles
+// whatever the number of active lanes (and rsqrt or a division for ~430),
+// so the kernel is laid out around float64 instruction counts:
+//  * CTA 0's warp 0 (the chief warp) runs the chase's serial part alone on
+//    its sub-partition: the 2 x 2 block at (k, k) and row k+2 of columns
+//    k, k+1, where the next rotation's inputs (h_{k+1,k}, h_{k+2,k}) are
+//    formed, lane-parallel (lanes 0 and 1 hold the block's two columns for
+//    G's row action, lanes 0-2 its three rows for G^H's column action), kept
+//    in registers from step to step; then the next rotation, its two
+//    reciprocal square roots in lanes 0 and 1 at once, stored into every
+//    CTA's shared memory (two slots, alternating).  The one entry of the next
+//    block that another thread writes, h_{k+1,k+2} (row op of column k+2),
+//    comes through shared memory too, and the entries no step touches before
+//    (h_{k+2,k+2}, h_{k+3,k+2}) are loaded a step ahead.
+//  * CTAs 1.. do the rest of every rotation (rows k, k+1 across the window,
+//    columns k, k+1 above the block), entry e to warp e / 32 of a sequence
+//    that alternates CTAs and sub-partitions, so the work fills whole warps
+//    spread over the cluster.
+// One cluster barrier per rotation; no entry is written by one thread while
+// another reads it.  CTA 0 alone takes every decision (deflation, shift,
+// stop) and broadcasts it, so all CTAs run the same barriers.  T is read with
+// L2-only loads (another CTA may have written it since).  The rotations'
+// action on the columns right of the window (rows there are never read by a
+// later sweep: the window only shrinks) and on Q is left to
+// apply_rotations_kernel, which runs on every SM: this kernel logs each sweep
+// and its rotations instead.
+constexpr int kQrCluster = 8;
+constexpr int kQrWorkers = kQrCluster - 1;                       // CTAs 1..
+constexpr int kQrWorkerThreads = kQrWorkers * kQrThreads;
+enum { kActSweep = 0, kActDeflate = 1, kActStop = 2 };
+
+__device__ __forceinline__ double2 ldT(const double2 *p) { return __ldcg(p); }
+__device__ __forceinline__ double2 shfl2(double2 v, int src)
 {
+    return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+// the unbiased exponent field of |x| (integer operations only)
+__device__ __forceinline__ int exp_field(double x)
+{
+    return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+}
+
+// make_rotation for the chief warp: every lane gets (c, s) for (x, y); the
+// power-of-two scaling is skipped (decided by integer compares) when every
+// component's exponent lies in [-400, 400], and the reciprocal square roots
+// of |x|^2 + |y|^2 and |x|^2 run in lanes 0 and 1 of one instruction stream.
+__device__ __forceinline__ void make_rotation_warp(double2 x, double2 y, int lane, double &c, double2 &s)
+{
+    const int ey = max(exp_field(y.x), exp_field(y.y));
+    if (y.x == 0.0 && y.y == 0.0) {
+        c = 1.0;
+        s = make_double2(0.0, 0.0);
+        return;
+    }
+    const int em = max(ey, max(exp_field(x.x), exp_field(x.y)));
+    if (em > 400 || em < -400) {
+        make_rotation(x, y, c, s);
+        return;
+    }
+    const double ax2 = fma(x.x, x.x, x.y * x.y), ay2 = fma(y.x, y.x, y.y * y.y);
+    if (ax2 == 0.0) {
+        make_rotation(x, y, c, s);
+        return;
+    }
+    const double r = rsqrt(lane == 0 ? ax2 + ay2 : ax2);
+    const double inv_n = __shfl_sync(0xffffffffu, r, 0), inv_ax = __shfl_sync(0xffffffffu, r, 1);
+    const double f = inv_ax * inv_n;
+    c = ax2 * f;
+    const double2 t = cmul(x, cconj(y));
+    s = make_double2(t.x * f, t.y * f);
+}
+
+__global__ void __cluster_dims__(kQrCluster, 1, 1) __launch_bounds__(kQrThreads)
+schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ st, long long budget,
+                SweepRec *__restrict__ sweeplog, double *__restrict__ rclog, double2 *__restrict__ rslog)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
     __shared__ int redi[kQrThreads / 32];
     __shared__ double rc[2];
     __shared__ double2 rs[2];
-    const int tid = threadIdx.x;
+    __shared__ double2 bslot[2];   // CTA 0: h_{k+1,k+2} after step k, for step k+1
+    __shared__ int ctl[3];         // action, l, i (CTA 0's decision)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned crank = cl.block_rank();
+    const bool chiefw = crank == 0 && warp == 0;   // the chief warp
+    const bool chief = chiefw && lane == 0;
+    // this worker thread's first entry and the stride (CTAs 1.. only)
+    const int e0 = ((warp * kQrWorkers + ((int)crank - 1)) << 5) + lane;
     int i = st->ihi, its = st->its, status = st->status;
     long long sweeps = 0, rot = 0;
     const double eps = DBL_EPSILON;
     const double tiny = DBL_MIN * ((double)n / DBL_EPSILON);
-    while (status == 0) {
-        if (i <= 0) {
-            status = 1;
-            i = -1;
-            break;
+    const double2 zero = make_double2(0.0, 0.0);
+    // the chief warp's registers (lanes 0-2): lane 0 column k of the block
+    // (h_kk, h_{k+1,k}), lane 1 column k+1 (h_{k,k+1}, h_{k+1,k+1}), lane 2
+    // row k+2 (0, h_{k+2,k+1})
+    double2 p0 = zero, p1 = zero;
+    auto put_rotation = [&](int slot, double c, double2 s) {
+        // lanes 0..kQrCluster-1 of the chief warp store into CTA `lane`
+        if (lane < kQrCluster) {
+            *cl.map_shared_rank(&rc[slot], lane) = c;
+            *cl.map_shared_rank(&rs[slot], lane) = s;
         }
-        // l: the largest k in [1, i] whose h_{k,k-1} is negligible, else 0
-        int lk = 0;
-        for (int k = 1 + tid; k <= i; k += kQrThreads) {
-            const double sub = cabs1(SGT_A(T, ldt, k, k - 1));
-            const double ref = cabs1(SGT_A(T, ldt, k - 1, k - 1)) + cabs1(SGT_A(T, ldt, k, k));
-            if (sub <= fmax(eps * ref, tiny)) lk = k;
+    };
+    for (;;) {
+        if (crank == 0) {
+            // l: the largest k in [1, i] whose h_{k,k-1} is negligible, else 0
+            int lk = 0;
+            for (int k = 1 + tid; k <= i; k += kQrThreads) {
+                const double sub = cabs1(ldT(&SGT_A(T, ldt, k, k - 1)));
+                const double ref = cabs1(ldT(&SGT_A(T, ldt, k - 1, k - 1))) + cabs1(ldT(&SGT_A(T, ldt, k, k)));
+                if (sub <= fmax(eps * ref, tiny)) lk = k;
+            }
+            for (int o = 16; o > 0; o >>= 1) lk = max(lk, __shfl_xor_sync(0xffffffffu, lk, o));
+            if (lane == 0) redi[warp] = lk;
+            __syncthreads();
+            if (chiefw) {
+                int l = 0;
+                for (int w = 0; w < kQrThreads / 32; w++) l = max(l, redi[w]);
+                int act;
+                if (status != 0 || i <= 0) {
+                    act = kActStop;
+                    if (status == 0) {
+                        status = 1;
+                        i = -1;
+                    }
+                } else if (l == i) {
+                    act = kActDeflate;   // the window's last row has converged
+                    if (lane == 0) SGT_A(T, ldt, i, i - 1) = zero;
+                } else if (rot >= budget) {
+                    act = kActStop;
+                } else if (its >= kMaxSweepsPerEigenvalue) {
+                    act = kActStop;
+                    status = 2;
+                } else {
+                    act = kActSweep;
+                    if (l > 0 && lane == 0) SGT_A(T, ldt, l, l - 1) = zero;
+                    const int sw_its = its + 1;
+                    double2 sigma;
+                    if (sw_its % 10 == 0) {
+                        // ad hoc shift: off the window's top (sweeps 10, 30, ..)
+                        // or bottom corner (20, 40, ..) by 3/4 of a subdiagonal
+                        // entry's real part
+                        const bool top = (sw_its / 10) % 2 == 1;
+                        const double2 d = top ? ldT(&SGT_A(T, ldt, l, l)) : ldT(&SGT_A(T, ldt, i, i));
+                        const double e = top ? ldT(&SGT_A(T, ldt, l + 1, l)).x : ldT(&SGT_A(T, ldt, i, i - 1)).x;
+                        sigma = make_double2(d.x + 0.75 * fabs(e), d.y);
+                    } else {
+                        // Wilkinson: with x = (a - d) / 2 and y = sqrt(x^2 + bc)
+                        // signed so that |x + y| is the larger, the eigenvalue
+                        // of [a b; c d] nearer d is d - bc / (x + y)
+                        const double2 a = ldT(&SGT_A(T, ldt, i - 1, i - 1)), b = ldT(&SGT_A(T, ldt, i - 1, i));
+                        const double2 cc = ldT(&SGT_A(T, ldt, i, i - 1)), d = ldT(&SGT_A(T, ldt, i, i));
+                        const double2 x = make_double2(0.5 * (a.x - d.x), 0.5 * (a.y - d.y));
+                        const double2 bc = cmul(b, cc);
+                        const double2 xx = cmul(x, x);
+                        double2 y = csqrt_p(make_double2(xx.x + bc.x, xx.y + bc.y));
+                        if (x.x * y.x + x.y * y.y < 0.0) y = make_double2(-y.x, -y.y);
+                        const double2 xy = make_double2(x.x + y.x, x.y + y.y);
+                        if (xy.x == 0.0 && xy.y == 0.0) {
+                            sigma = d;
+                        } else {
+                            const double2 q = cdiv(bc, xy);
+                            sigma = make_double2(d.x - q.x, d.y - q.y);
+                        }
+                    }
+                    // lane 0: (h_ll, h_{l+1,l}); lane 1: (h_{l,l+1}, h_{l+1,l+1});
+                    // lane 2: (0, h_{l+2,l+1})
+                    if (lane == 0) {
+                        p0 = ldT(&SGT_A(T, ldt, l, l));
+                        p1 = ldT(&SGT_A(T, ldt, l + 1, l));
+                    } else if (lane == 1) {
+                        p0 = ldT(&SGT_A(T, ldt, l, l + 1));
+                        p1 = ldT(&SGT_A(T, ldt, l + 1, l + 1));
+                    } else if (lane == 2) {
+                        p0 = zero;
+                        p1 = (l + 2 <= i) ? ldT(&SGT_A(T, ldt, l + 2, l + 1)) : zero;
+                    }
+                    const double2 a0 = shfl2(p0, 0), e0v = shfl2(p1, 0);
+                    double c;
+                    double2 s;
+                    make_rotation_warp(make_double2(a0.x - sigma.x, a0.y - sigma.y), e0v, lane, c, s);
+                    put_rotation(l & 1, c, s);
+                    if (lane == 0) {
+                        sweeplog[sweeps] = SweepRec{l, i, rot};
+                        rclog[rot] = c;
+                        rslog[rot] = s;
+                    }
+                }
+                if (lane < kQrCluster) {
+                    int *rem = cl.map_shared_rank(ctl, lane);
+                    rem[0] = act;
+                    rem[1] = l;
+                    rem[2] = i;
+                }
+            }
         }
-        for (int o = 16; o > 0; o >>= 1) lk = max(lk, __shfl_xor_sync(0xffffffffu, lk, o));
-        __syncthreads();   // the previous pass's reads of redi are done
-        if ((tid & 31) == 0) redi[tid / 32] = lk;
-        __syncthreads();
-        int l = 0;
-        for (int w = 0; w < kQrThreads / 32; w++) l = max(l, redi[w]);
-        if (l == i) {   // the window's last row has converged
-            if (tid == 0) SGT_A(T, ldt, i, i - 1) = make_double2(0.0, 0.0);
+        cl.sync();
+        const int act = ctl[0], l = ctl[1];
+        i = ctl[2];
+        if (act == kActStop) break;
+        if (act == kActDeflate) {
             i--;
             its = 0;
             continue;
         }
-        if (rot >= budget) break;
-        if (its >= kMaxSweepsPerEigenvalue) {
-            status = 2;
-            break;
-        }
         its++;
         sweeps++;
-        if (tid == 0) {
-            if (l > 0) SGT_A(T, ldt, l, l - 1) = make_double2(0.0, 0.0);
-            double2 sigma;
-            if (its % 10 == 0) {
-                // ad hoc shift: off the window's top (sweeps 10, 30, ..) or
-                // bottom corner (20, 40, ..) by 3/4 of a subdiagonal entry's
-                // real part
-                const bool top = (its / 10) % 2 == 1;
-                const double2 d = top ? SGT_A(T, ldt, l, l) : SGT_A(T, ldt, i, i);
-                const double e = top ? SGT_A(T, ldt, l + 1, l).x : SGT_A(T, ldt, i, i - 1).x;
-                sigma = make_double2(d.x + 0.75 * fabs(e), d.y);
-            } else {
-                // Wilkinson: with x = (a - d) / 2 and y = sqrt(x^2 + bc) signed
-                // so that |x + y| is the larger, the eigenvalue of
-                // [a b; c d] nearer d is d - bc / (x + y)
-                const double2 a = SGT_A(T, ldt, i - 1, i - 1), b = SGT_A(T, ldt, i - 1, i);
-                const double2 cc = SGT_A(T, ldt, i, i - 1), d = SGT_A(T, ldt, i, i);
-                const double2 x = make_double2(0.5 * (a.x - d.x), 0.5 * (a.y - d.y));
-                const double2 bc = cmul(b, cc);
-                const double2 xx = cmul(x, x);
-                double2 y = csqrt_p(make_double2(xx.x + bc.x, xx.y + bc.y));
-                if (x.x * y.x + x.y * y.y < 0.0) y = make_double2(-y.x, -y.y);
-                const double2 xy = make_double2(x.x + y.x, x.y + y.y);
-                if (xy.x == 0.0 && xy.y == 0.0) {
-                    sigma = d;
-                } else {
-                    const double2 q = cdiv(bc, xy);
-                    sigma = make_double2(d.x - q.x, d.y - q.y);
-                }
-            }
-            double2 x = SGT_A(T, ldt, l, l);
-            x.x -= sigma.x;
-            x.y -= sigma.y;
-            double c;
-            double2 s;
-            make_rotation(x, SGT_A(T, ldt, l + 1, l), c, s);
-            rc[l & 1] = c;
-            rs[l & 1] = s;
-        }
-        __syncthreads();
         for (int k = l; k < i; k++) {
             const double c = rc[k & 1];
             const double2 s = rs[k & 1];
-            // rows k, k+1 from column jlo on, apart from the 2 x 2 block
-            const int jlo = (k == l) ? l : k - 1;
-            for (int j = jlo + tid; j < n; j += kQrThreads) {
-                if (j == k || j == k + 1) continue;
-                double2 a = SGT_A(T, ldt, k, j), b = SGT_A(T, ldt, k + 1, j);
-                rot_rows(c, s, a, b);
-                SGT_A(T, ldt, k, j) = a;
-                SGT_A(T, ldt, k + 1, j) = (j == k - 1) ? make_double2(0.0, 0.0) : b;   // the old bulge, zeroed
-            }
-            // columns k, k+1 in the rows above the block
-            for (int r = tid; r < k; r += kQrThreads) {
-                double2 a = SGT_A(T, ldt, r, k), b = SGT_A(T, ldt, r, k + 1);
-                rot_cols(c, s, a, b);
-                SGT_A(T, ldt, r, k) = a;
-                SGT_A(T, ldt, r, k + 1) = b;
-            }
-            if (tid == 0) {
-                double2 a = SGT_A(T, ldt, k, k), b = SGT_A(T, ldt, k, k + 1);
-                double2 e = SGT_A(T, ldt, k + 1, k), f = SGT_A(T, ldt, k + 1, k + 1);
-                rot_rows(c, s, a, e);
-                rot_rows(c, s, b, f);
-                rot_cols(c, s, a, b);
-                rot_cols(c, s, e, f);
-                SGT_A(T, ldt, k, k) = a;
-                SGT_A(T, ldt, k, k + 1) = b;
-                SGT_A(T, ldt, k + 1, k) = e;
-                SGT_A(T, ldt, k + 1, k + 1) = f;
+            if (crank > 0) {
+                // entries: the row op's columns jlo..i (the block's two
+                // apart), then the column op's rows 0..k-1; h_{k+1,k+2} also
+                // to the chief warp
+                const int jlo = (k == l) ? l : k - 1;
+                const int wr = i - jlo + 1, wtot = wr + k;
+                for (int e = e0; e < wtot; e += kQrWorkerThreads) {
+                    if (e < wr) {
+                        const int j = jlo + e;
+                        if (j == k || j == k + 1) continue;
+                        double2 a = ldT(&SGT_A(T, ldt, k, j)), b = ldT(&SGT_A(T, ldt, k + 1, j));
+                        rot_rows(c, s, a, b);
+                        SGT_A(T, ldt, k, j) = a;
+                        SGT_A(T, ldt, k + 1, j) = (j == k - 1) ? zero : b;   // the old bulge, zeroed
+                        if (j == k + 2) *cl.map_shared_rank(&bslot[(k + 1) & 1], 0) = b;
+                    } else {
+                        const int r = e - wr;
+                        double2 a = ldT(&SGT_A(T, ldt, r, k)), b = ldT(&SGT_A(T, ldt, r, k + 1));
+                        rot_cols(c, s, a, b);
+                        SGT_A(T, ldt, r, k) = a;
+                        SGT_A(T, ldt, r, k + 1) = b;
+                    }
+                }
+            } else if (chiefw) {
+                // entries no step writes before step k+1 reads them: lane 1
+                // h_{k+2,k+2}, lane 2 h_{k+3,k+2}
+                double2 nxt = zero;
+                if (lane == 1 && k + 2 <= i) nxt = ldT(&SGT_A(T, ldt, k + 2, k + 2));
+                if (lane == 2 && k + 3 <= i) nxt = ldT(&SGT_A(T, ldt, k + 3, k + 2));
+                // G on the block's columns (lanes 0, 1); lane 2's row is
+                // kept aside
+                const double2 keep = p1;
+                rot_rows(c, s, p0, p1);
+                // the block's rows: lane 0 (h_kk, h_{k,k+1}), lane 1
+                // (h_{k+1,k}, h_{k+1,k+1}), lane 2 (0, h_{k+2,k+1})
+                const double2 x01 = shfl2(p0, 1), x10 = shfl2(p1, 0);
+                double2 q0 = p0, q1 = p1;
+                if (lane == 0) q1 = x01;
+                if (lane == 1) q0 = x10;
+                if (lane == 2) {
+                    q0 = zero;
+                    q1 = keep;   // h_{k+2,k+1}, untouched by G's row action
+                }
+                rot_cols(c, s, q0, q1);
+                if (lane < 2 || (lane == 2 && k + 2 <= i)) {
+                    const int rr = k + lane;
+                    SGT_A(T, ldt, rr, k) = q0;
+                    SGT_A(T, ldt, rr, k + 1) = q1;
+                }
                 if (k + 2 <= i) {
-                    // row k+2: h_{k+2,k} = 0 before, the new bulge after
-                    double2 g = SGT_A(T, ldt, k + 2, k), h = SGT_A(T, ldt, k + 2, k + 1);
-                    rot_cols(c, s, g, h);
-                    SGT_A(T, ldt, k + 2, k) = g;
-                    SGT_A(T, ldt, k + 2, k + 1) = h;
-                    // the next rotation zeroes the bulge
+                    // the next rotation zeroes the bulge h_{k+2,k} (lane 2's
+                    // q0) against h_{k+1,k} (lane 1's q0)
+                    const double2 x = shfl2(q0, 1), y = shfl2(q0, 2);
                     double cn;
                     double2 sn;
-                    make_rotation(e, g, cn, sn);
-                    rc[(k + 1) & 1] = cn;
-                    rs[(k + 1) & 1] = sn;
+                    make_rotation_warp(x, y, lane, cn, sn);
+                    put_rotation((k + 1) & 1, cn, sn);
+                    if (lane == 0) {
+                        rclog[rot + (k + 1 - l)] = cn;
+                        rslog[rot + (k + 1 - l)] = sn;
+                    }
+                    // the block at (k+1, k+1): lane 0 (h_{k+1,k+1}, h_{k+2,k+1})
+                    // = (lane 1's q1, lane 2's q1); lane 1 (h_{k+1,k+2} from
+                    // bslot after the barrier, h_{k+2,k+2}); lane 2 (0, h_{k+3,k+2})
+                    const double2 f1 = shfl2(q1, 1), h2 = shfl2(q1, 2);
+                    if (lane == 0) {
+                        p0 = f1;
+                        p1 = h2;
+                    } else if (lane == 1) {
+                        p1 = nxt;
+                    } else if (lane == 2) {
+                        p0 = zero;
+                        p1 = nxt;
+                    }
                 }
             }
-            for (int r = tid; r < n; r += kQrThreads) {
-                double2 a = SGT_A(Q, ldq, r, k), b = SGT_A(Q, ldq, r, k + 1);
-                rot_cols(c, s, a, b);
-                SGT_A(Q, ldq, r, k) = a;
-                SGT_A(Q, ldq, r, k + 1) = b;
-            }
-            __syncthreads();
+            cl.sync();
+            if (chiefw && lane == 1 && k + 1 < i) p0 = bslot[(k + 1) & 1];
         }
         rot += i - l;
     }
-    if (tid == 0) {
+    if (chief) {
         st->ihi = i;
         st->its = its;
         st->status = status;
+        st->logged = (int)sweeps;
         st->sweeps += sweeps;
         st->rotations += rot;
+    }
+}
+
+// The logged sweeps' rotations where schur_qr_kernel left them out: thread g
+// < n takes column g of T and applies the row rotations of every sweep
+// whose window ends above it (g > i), down the column with the carried row;
+// thread g >= n takes row g - n of Q and applies every sweep's column
+// rotations along the row.  In log order, so each entry sees its rotations
+// in the order of the QR iteration.
+__global__ void apply_rotations_kernel(int n, double2 *__restrict__ T, int ldt, double2 *__restrict__ Q, int ldq,
+                                       const QrState *__restrict__ st, const SweepRec *__restrict__ sweeplog,
+                                       const double *__restrict__ rclog, const double2 *__restrict__ rslog)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= 2 * n) return;
+    const int logged = st->logged;
+    if (g < n) {
+        const int j = g;
+        for (int w = 0; w < logged; w++) {
+            const SweepRec sr = sweeplog[w];
+            if (j <= sr.i) continue;
+            double2 carry = SGT_A(T, ldt, sr.l, j);
+            for (int k = sr.l; k < sr.i; k++) {
+                const double c = rclog[sr.off + (k - sr.l)];
+                const double2 s = rslog[sr.off + (k - sr.l)];
+                double2 a = carry, b = SGT_A(T, ldt, k + 1, j);
+                rot_rows(c, s, a, b);
+                SGT_A(T, ldt, k, j) = a;
+                carry = b;
+            }
+            SGT_A(T, ldt, sr.i, j) = carry;
+        }
+    } else {
+        const int r = g - n;
+        for (int w = 0; w < logged; w++) {
+            const SweepRec sr = sweeplog[w];
+            double2 carry = SGT_A(Q, ldq, r, sr.l);
+            for (int k = sr.l; k < sr.i; k++) {
+                const double c = rclog[sr.off + (k - sr.l)];
+                const double2 s = rslog[sr.off + (k - sr.l)];
+                double2 a = carry, b = SGT_A(Q, ldq, r, k + 1);
+                rot_cols(c, s, a, b);
+                SGT_A(Q, ldq, r, k) = a;
+                carry = b;
+            }
+            SGT_A(Q, ldq, r, sr.i) = carry;
+        }
     }
 }
 
@@ -433,10 +683,11 @@ __global__ void real_part_kernel(int n, const double2 *__restrict__ Sc, double *
 size_t schur_workspace_bytes(int n)
 {
     if (n <= 0) return 0;
-    // six takes, each rounded up to 256 bytes
+    // ten takes, each rounded up to 256 bytes; the logs hold one launch
     const size_t nn = (size_t)n * n;
-    return 2 * nn * sizeof(double) + (size_t)n * sizeof(double) + sizeof(double) + sizeof(int) + sizeof(QrState) +
-           6 * 256;
+    const size_t nlog = (size_t)kRotationBudget + (size_t)n + 1;
+    return 2 * nn * sizeof(double) + 3 * (size_t)n * sizeof(double) + sizeof(double) + sizeof(int) + sizeof(QrState) +
+           nlog * (sizeof(SweepRec) + sizeof(double) + sizeof(double2)) + 10 * 256;
 }
 
 signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, double *T, int ldt, Arena &ws,
@@ -447,10 +698,17 @@ signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, do
     auto *H = static_cast<double *>(ws.take(nn * sizeof(double)));
     auto *Q0 = static_cast<double *>(ws.take(nn * sizeof(double)));
     auto *v = static_cast<double *>(ws.take((size_t)n * sizeof(double)));
+    auto *y = static_cast<double *>(ws.take((size_t)2 * n * sizeof(double)));
     auto *tau = static_cast<double *>(ws.take(sizeof(double)));
     auto *bad = static_cast<int *>(ws.take(sizeof(int)));
     auto *qs = static_cast<QrState *>(ws.take(sizeof(QrState)));
-    if (!H || !Q0 || !v || !tau || !bad || !qs) return SIGNTRI_ERR_NO_WORKSPACE;
+    // a launch logs fewer than budget + n rotations (it starts a sweep only
+    // below the budget, a sweep has at most n - 1) and no more sweeps
+    const size_t nlog = (size_t)kRotationBudget + (size_t)n + 1;
+    auto *sweeplog = static_cast<SweepRec *>(ws.take(nlog * sizeof(SweepRec)));
+    auto *rclog = static_cast<double *>(ws.take(nlog * sizeof(double)));
+    auto *rslog = static_cast<double2 *>(ws.take(nlog * sizeof(double2)));
+    if (!H || !Q0 || !v || !y || !tau || !bad || !qs || !sweeplog || !rclog || !rslog) return SIGNTRI_ERR_NO_WORKSPACE;
     const int big = INT_MAX;
     SGT_CUDA_TRY(cudaMemcpyAsync(bad, &big, sizeof(int), cudaMemcpyHostToDevice, st));
     {
@@ -471,13 +729,15 @@ signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, do
         SGT_LAUNCH_CHECK();
     }
     for (int k = 0; k + 2 < n; k++) {
-        ProfScope ps(SIGNTRI_KC_SCHUR, st, true, false);
-        prof_count(SIGNTRI_KC_SCHUR, 3);
+        ProfScope ps(SIGNTRI_KC_HESSENBERG, st, true, false);
+        prof_count(SIGNTRI_KC_HESSENBERG, 4);
         house_kernel<<<1, 1024, 0, st>>>(n, k, H, v, tau);
         SGT_LAUNCH_CHECK();
         house_left_kernel<<<n - k - 1, kThreads, 0, st>>>(n, k, H, v, tau);
         SGT_LAUNCH_CHECK();
-        house_right_kernel<<<(2 * n + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, k, H, Q0, v, tau);
+        house_gemv_kernel<<<(2 * n + 31) / 32, 32 * kGemvWarps, 0, st>>>(n, k, H, Q0, v, tau, y);
+        SGT_LAUNCH_CHECK();
+        house_rank1_kernel<<<n - k - 1, kThreads, 0, st>>>(n, k, H, Q0, v, tau, y);
         SGT_LAUNCH_CHECK();
     }
     auto *Tc = reinterpret_cast<double2 *>(T);
@@ -496,8 +756,13 @@ signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, do
     for (long long it = 0;; it++) {
         if (it >= max_launches) return SIGNTRI_ERR_NO_CONVERGENCE;
         {
-            ProfScope ps(SIGNTRI_KC_SCHUR, st);
-            schur_qr_kernel<<<1, kQrThreads, 0, st>>>(n, Tc, ldt, Qc, ldq, qs, kRotationBudget);
+            ProfScope ps(SIGNTRI_KC_SCHUR, st, true, false);
+            prof_count(SIGNTRI_KC_SCHUR, 2);
+            schur_qr_kernel<<<kQrCluster, kQrThreads, 0, st>>>(n, Tc, ldt, qs, kRotationBudget, sweeplog, rclog,
+                                                                rslog);
+            SGT_LAUNCH_CHECK();
+            apply_rotations_kernel<<<(2 * n + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, Tc, ldt, Qc, ldq, qs,
+                                                                                        sweeplog, rclog, rslog);
             SGT_LAUNCH_CHECK();
         }
         SGT_CUDA_TRY(cudaMemcpyAsync(&h, qs, sizeof(QrState), cudaMemcpyDeviceToHost, st));

@@ -131,7 +131,8 @@ KC_BLOCK_SUMS_TC, KC_OFFDIAG_LEAF_MIXED, KC_CONVERT, KC_RESIDUAL, KC_CORRECTION 
 KC_GIVENS, KC_SYLV_SUMS, KC_SYLV_LEAF, KC_GEMM_F64, KC_OTHER, KC_RESIDUAL_SUM = 10, 11, 12, 13, 14, 15
 KC_BATCH_GRAPH = 16
 KC_SCHUR = 17
-KC_COUNT = 18
+KC_HESSENBERG = 18
+KC_COUNT = 19
 
 
 def load(path: str = LIB_PATH):
