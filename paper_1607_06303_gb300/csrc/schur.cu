@@ -51,7 +51,7 @@ namespace signtri {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kQrThreads = 1024;
+constexpr int kQrThreads = 512;
 constexpr int kMaxSweepsPerEigenvalue = 100;
 constexpr long long kRotationBudget = 1LL << 15;   // rotations per launch of the QR kernel (then a sweep's end)
 
@@ -321,14 +321,15 @@ __global__ void qr_state_init_kernel(int n, QrState *st)
 //  * CTA 0's warp 0 (the chief warp) runs the chase's serial part alone on
 //    its sub-partition: the 2 x 2 block at (k, k) and row k+2 of columns
 //    k, k+1, where the next rotation's inputs (h_{k+1,k}, h_{k+2,k}) are
-//    formed, lane-parallel (lanes 0 and 1 hold the block's two columns for
-//    G's row action, lanes 0-2 its three rows for G^H's column action), kept
-//    in registers from step to step; then the next rotation, its two
-//    reciprocal square roots in lanes 0 and 1 at once, stored into every
+//    formed, lane-parallel (one real output per lane: 8 lanes for G's action
+//    on the block's two columns, 12 for G^H's on its three rows, 3 float64
+//    instructions each), kept in registers from step to step; then the next
+//    rotation, its two reciprocal square roots in lanes 0 and 1 at once,
+//    stored into every
 //    CTA's shared memory (two slots, alternating).  The one entry of the next
 //    block that another thread writes, h_{k+1,k+2} (row op of column k+2),
 //    comes through shared memory too, and the entries no step touches before
-//    (h_{k+2,k+2}, h_{k+3,k+2}) are loaded a step ahead.
+//    (h_{k+2,k+2}, h_{k+3,k+2}) are loaded two steps ahead.
 //  * CTAs 1.. do the rest of every rotation (rows k, k+1 across the window,
 //    columns k, k+1 above the block), entry e to warp e / 32 of a sequence
 //    that alternates CTAs and sub-partitions, so the work fills whole warps
@@ -357,34 +358,49 @@ __device__ __forceinline__ int exp_field(double x)
     return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
 }
 
-// make_rotation for the chief warp: every lane gets (c, s) for (x, y); the
-// power-of-two scaling is skipped (decided by integer compares) when every
-// component's exponent lies in [-400, 400], and the reciprocal square roots
-// of |x|^2 + |y|^2 and |x|^2 run in lanes 0 and 1 of one instruction stream.
+__device__ __forceinline__ bool is_zero2(double2 v)
+{
+    return (((unsigned long long)__double_as_longlong(v.x) | (unsigned long long)__double_as_longlong(v.y)) << 1) == 0;
+}
+
+// make_rotation for the chief warp (x, y the same in every lane; every lane
+// gets (c, s)): zero tests and the exponent-range test by integer operations
+// on the bits; without scaling when every component's exponent lies in
+// [-400, 400] (else make_rotation); |x|^2 and |y|^2, the two reciprocal
+// square roots, and the two parts of x conj(y) f each in lanes 0 and 1 of
+// one instruction stream.
 __device__ __forceinline__ void make_rotation_warp(double2 x, double2 y, int lane, double &c, double2 &s)
 {
-    const int ey = max(exp_field(y.x), exp_field(y.y));
-    if (y.x == 0.0 && y.y == 0.0) {
+    if (is_zero2(y)) {
         c = 1.0;
         s = make_double2(0.0, 0.0);
         return;
     }
-    const int em = max(ey, max(exp_field(x.x), exp_field(x.y)));
-    if (em > 400 || em < -400) {
+    const int em = max(max(exp_field(y.x), exp_field(y.y)), max(exp_field(x.x), exp_field(x.y)));
+    if (em > 400 || em < -400 || is_zero2(x)) {
         make_rotation(x, y, c, s);
         return;
     }
-    const double ax2 = fma(x.x, x.x, x.y * x.y), ay2 = fma(y.x, y.x, y.y * y.y);
-    if (ax2 == 0.0) {
-        make_rotation(x, y, c, s);
-        return;
-    }
-    const double r = rsqrt(lane == 0 ? ax2 + ay2 : ax2);
+    const bool l1 = lane & 1;
+    const double2 v = l1 ? y : x;
+    const double sq = fma(v.x, v.x, v.y * v.y);   // lane 0 |x|^2, lane 1 |y|^2
+    const double ax2 = __shfl_sync(0xffffffffu, sq, 0), ay2 = __shfl_sync(0xffffffffu, sq, 1);
+    // lane 0: Re(x conj(y)) = x.x y.x + x.y y.y; lane 1: Im = x.y y.x - x.x y.y
+    const double tt = fma(l1 ? x.y : x.x, y.x, (l1 ? -x.x : x.y) * y.y);
+    const double r = rsqrt(l1 ? ax2 : ax2 + ay2);   // lane 0 1/nrm, lane 1 1/|x|
     const double inv_n = __shfl_sync(0xffffffffu, r, 0), inv_ax = __shfl_sync(0xffffffffu, r, 1);
     const double f = inv_ax * inv_n;
     c = ax2 * f;
-    const double2 t = cmul(x, cconj(y));
-    s = make_double2(t.x * f, t.y * f);
+    const double sp = tt * f;
+    s = make_double2(__shfl_sync(0xffffffffu, sp, 0), __shfl_sync(0xffffffffu, sp, 1));
+}
+
+// One real output of G or G^H acting on a pair, in one of the chief warp's
+// lanes: out = c alpha + beta gamma + delta epsilon (3 float64 instructions).
+__device__ __forceinline__ double pair_part(double c, double alpha, double beta, double gamma, double delta,
+                                            double epsilon)
+{
+    return fma(c, alpha, fma(beta, gamma, delta * epsilon));
 }
 
 __global__ void __cluster_dims__(kQrCluster, 1, 1) __launch_bounds__(kQrThreads)
@@ -409,10 +425,10 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
     const double eps = DBL_EPSILON;
     const double tiny = DBL_MIN * ((double)n / DBL_EPSILON);
     const double2 zero = make_double2(0.0, 0.0);
-    // the chief warp's registers (lanes 0-2): lane 0 column k of the block
-    // (h_kk, h_{k+1,k}), lane 1 column k+1 (h_{k,k+1}, h_{k+1,k+1}), lane 2
-    // row k+2 (0, h_{k+2,k+1})
-    double2 p0 = zero, p1 = zero;
+    // the chief warp's registers, the same in every lane: the block
+    // (A B; E F) at (k, k) and Hh = h_{k+2,k+1}
+    double2 A = zero, B = zero, E = zero, F = zero, Hh = zero;
+    double2 pf_f = zero, pf_h = zero;   // h_{k+2,k+2}, h_{k+3,k+2} for step k+1, loaded a step early
     auto put_rotation = [&](int slot, double c, double2 s) {
         // lanes 0..kQrCluster-1 of the chief warp store into CTA `lane`
         if (lane < kQrCluster) {
@@ -482,22 +498,16 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
                             sigma = make_double2(d.x - q.x, d.y - q.y);
                         }
                     }
-                    // lane 0: (h_ll, h_{l+1,l}); lane 1: (h_{l,l+1}, h_{l+1,l+1});
-                    // lane 2: (0, h_{l+2,l+1})
-                    if (lane == 0) {
-                        p0 = ldT(&SGT_A(T, ldt, l, l));
-                        p1 = ldT(&SGT_A(T, ldt, l + 1, l));
-                    } else if (lane == 1) {
-                        p0 = ldT(&SGT_A(T, ldt, l, l + 1));
-                        p1 = ldT(&SGT_A(T, ldt, l + 1, l + 1));
-                    } else if (lane == 2) {
-                        p0 = zero;
-                        p1 = (l + 2 <= i) ? ldT(&SGT_A(T, ldt, l + 2, l + 1)) : zero;
-                    }
-                    const double2 a0 = shfl2(p0, 0), e0v = shfl2(p1, 0);
+                    A = ldT(&SGT_A(T, ldt, l, l));
+                    B = ldT(&SGT_A(T, ldt, l, l + 1));
+                    E = ldT(&SGT_A(T, ldt, l + 1, l));
+                    F = ldT(&SGT_A(T, ldt, l + 1, l + 1));
+                    Hh = (l + 2 <= i) ? ldT(&SGT_A(T, ldt, l + 2, l + 1)) : zero;
+                    pf_f = (l + 2 <= i) ? ldT(&SGT_A(T, ldt, l + 2, l + 2)) : zero;
+                    pf_h = (l + 3 <= i) ? ldT(&SGT_A(T, ldt, l + 3, l + 2)) : zero;
                     double c;
                     double2 s;
-                    make_rotation_warp(make_double2(a0.x - sigma.x, a0.y - sigma.y), e0v, lane, c, s);
+                    make_rotation_warp(make_double2(A.x - sigma.x, A.y - sigma.y), E, lane, c, s);
                     put_rotation(l & 1, c, s);
                     if (lane == 0) {
                         sweeplog[sweeps] = SweepRec{l, i, rot};
@@ -551,35 +561,46 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
                     }
                 }
             } else if (chiefw) {
-                // entries no step writes before step k+1 reads them: lane 1
-                // h_{k+2,k+2}, lane 2 h_{k+3,k+2}
-                double2 nxt = zero;
-                if (lane == 1 && k + 2 <= i) nxt = ldT(&SGT_A(T, ldt, k + 2, k + 2));
-                if (lane == 2 && k + 3 <= i) nxt = ldT(&SGT_A(T, ldt, k + 3, k + 2));
-                // G on the block's columns (lanes 0, 1); lane 2's row is
-                // kept aside
-                const double2 keep = p1;
-                rot_rows(c, s, p0, p1);
-                // the block's rows: lane 0 (h_kk, h_{k,k+1}), lane 1
-                // (h_{k+1,k}, h_{k+1,k+1}), lane 2 (0, h_{k+2,k+1})
-                const double2 x01 = shfl2(p0, 1), x10 = shfl2(p1, 0);
-                double2 q0 = p0, q1 = p1;
-                if (lane == 0) q1 = x01;
-                if (lane == 1) q0 = x10;
-                if (lane == 2) {
-                    q0 = zero;
-                    q1 = keep;   // h_{k+2,k+1}, untouched by G's row action
-                }
-                rot_cols(c, s, q0, q1);
-                if (lane < 2 || (lane == 2 && k + 2 <= i)) {
-                    const int rr = k + lane;
-                    SGT_A(T, ldt, rr, k) = q0;
-                    SGT_A(T, ldt, rr, k + 1) = q1;
-                }
+                // entries no step writes before step k+1 reads them
+                // (h_{k+2,k+2}, h_{k+3,k+2}), loaded at step k-1; and those
+                // of step k+2
+                const double2 F2 = pf_f, H2 = pf_h;
+                pf_f = (k + 3 <= i) ? ldT(&SGT_A(T, ldt, k + 3, k + 3)) : zero;
+                pf_h = (k + 4 <= i) ? ldT(&SGT_A(T, ldt, k + 4, k + 3)) : zero;
+                // G on the block's columns: lane 4 col + part holds part
+                // (0 top.x, 1 top.y, 2 bottom.x, 3 bottom.y) of column col
+                // (0: (A, E), 1: (B, F)) -- one real output per lane
+                // (operands picked by selects, no branches: all lanes run the
+                // same three float64 instructions)
+                const int part = lane & 3;
+                const bool odd = part & 1, hi = part >= 2;
+                const bool cl1 = (lane >> 2) & 1;
+                const double2 tp = cl1 ? B : A, bt = cl1 ? F : E;
+                const double2 u1 = hi ? bt : tp, v1 = hi ? tp : bt;
+                const double r1 = pair_part(c, odd ? u1.y : u1.x, hi ? -s.x : s.x, odd ? v1.y : v1.x,
+                                            odd ? s.y : -s.y, odd ? v1.x : v1.y);
+                const double2 A1 = make_double2(__shfl_sync(0xffffffffu, r1, 0), __shfl_sync(0xffffffffu, r1, 1));
+                const double2 E1 = make_double2(__shfl_sync(0xffffffffu, r1, 2), __shfl_sync(0xffffffffu, r1, 3));
+                const double2 B1 = make_double2(__shfl_sync(0xffffffffu, r1, 4), __shfl_sync(0xffffffffu, r1, 5));
+                const double2 F1 = make_double2(__shfl_sync(0xffffffffu, r1, 6), __shfl_sync(0xffffffffu, r1, 7));
+                // G^H on the rows k, k+1, k+2: lane 4 row + part holds part
+                // (0 p.x, 1 p.y, 2 q.x, 3 q.y) of row (p, q): (A1, B1),
+                // (E1, F1), (0, Hh)
+                const int row = min(lane >> 2, 2);
+                const double2 pp = row == 0 ? A1 : (row == 1 ? E1 : zero);
+                const double2 qq = row == 0 ? B1 : (row == 1 ? F1 : Hh);
+                const double2 u2 = hi ? qq : pp, v2 = hi ? pp : qq;
+                const double r2 = pair_part(c, odd ? u2.y : u2.x, hi ? -s.x : s.x, odd ? v2.y : v2.x,
+                                            odd ? -s.y : s.y, odd ? v2.x : v2.y);
+                if (lane < 8 || (lane < 12 && k + 2 <= i))
+                    reinterpret_cast<double *>(&SGT_A(T, ldt, k + (lane >> 2), k + (part >> 1)))[part & 1] = r2;
                 if (k + 2 <= i) {
-                    // the next rotation zeroes the bulge h_{k+2,k} (lane 2's
-                    // q0) against h_{k+1,k} (lane 1's q0)
-                    const double2 x = shfl2(q0, 1), y = shfl2(q0, 2);
+                    // the next rotation zeroes the bulge h_{k+2,k} (lanes 8, 9)
+                    // against h_{k+1,k} (lanes 4, 5)
+                    const double2 x = make_double2(__shfl_sync(0xffffffffu, r2, 4), __shfl_sync(0xffffffffu, r2, 5));
+                    const double2 y = make_double2(__shfl_sync(0xffffffffu, r2, 8), __shfl_sync(0xffffffffu, r2, 9));
+                    const double2 f1 = make_double2(__shfl_sync(0xffffffffu, r2, 6), __shfl_sync(0xffffffffu, r2, 7));
+                    const double2 h1 = make_double2(__shfl_sync(0xffffffffu, r2, 10), __shfl_sync(0xffffffffu, r2, 11));
                     double cn;
                     double2 sn;
                     make_rotation_warp(x, y, lane, cn, sn);
@@ -588,23 +609,17 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
                         rclog[rot + (k + 1 - l)] = cn;
                         rslog[rot + (k + 1 - l)] = sn;
                     }
-                    // the block at (k+1, k+1): lane 0 (h_{k+1,k+1}, h_{k+2,k+1})
-                    // = (lane 1's q1, lane 2's q1); lane 1 (h_{k+1,k+2} from
-                    // bslot after the barrier, h_{k+2,k+2}); lane 2 (0, h_{k+3,k+2})
-                    const double2 f1 = shfl2(q1, 1), h2 = shfl2(q1, 2);
-                    if (lane == 0) {
-                        p0 = f1;
-                        p1 = h2;
-                    } else if (lane == 1) {
-                        p1 = nxt;
-                    } else if (lane == 2) {
-                        p0 = zero;
-                        p1 = nxt;
-                    }
+                    // the block at (k+1, k+1): (h_{k+1,k+1}, h_{k+1,k+2};
+                    // h_{k+2,k+1}, h_{k+2,k+2}), h_{k+1,k+2} from bslot after
+                    // the barrier
+                    A = f1;
+                    E = h1;
+                    F = F2;
+                    Hh = H2;
                 }
             }
             cl.sync();
-            if (chiefw && lane == 1 && k + 1 < i) p0 = bslot[(k + 1) & 1];
+            if (chiefw && k + 1 < i) B = bslot[(k + 1) & 1];
         }
         rot += i - l;
     }
@@ -618,50 +633,48 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
     }
 }
 
-// The logged sweeps' rotations where schur_qr_kernel left them out: thread g
-// < n takes column g of T and applies the row rotations of every sweep
-// whose window ends above it (g > i), down the column with the carried row;
-// thread g >= n takes row g - n of Q and applies every sweep's column
-// rotations along the row.  In log order, so each entry sees its rotations
-// in the order of the QR iteration.
+// The logged sweeps' rotations where schur_qr_kernel left them out: unit u
+// < n is column u of T, which takes the row rotations of every sweep whose
+// window ends above it (u > i), down the column with the carried row; unit
+// u >= n is row u - n of Q, which takes every sweep's column rotations along
+// the row.  In log order, so each entry sees its rotations in the order of
+// the QR iteration.  Four lanes per unit, each computing one real output of
+// a rotation (3 float64 instructions, where GB300's float64 pipe, not the
+// memory, bounds this kernel), the carried entry passed by shuffles; the
+// next entry is loaded an iteration ahead.
 __global__ void apply_rotations_kernel(int n, double2 *__restrict__ T, int ldt, double2 *__restrict__ Q, int ldq,
                                        const QrState *__restrict__ st, const SweepRec *__restrict__ sweeplog,
                                        const double *__restrict__ rclog, const double2 *__restrict__ rslog)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= 2 * n) return;
+    const int unit = g >> 2, part = g & 3;
+    if (unit >= 2 * n) return;   // the four lanes of a unit leave together
+    const unsigned gmask = 0xFu << (threadIdx.x & 28);
+    const bool odd = part & 1, hi = part >= 2;
+    const bool isT = unit < n;
+    // entry k of the unit's line: T(k, j) (stride 1) or Q(r, k) (stride ldq)
+    double2 *line = isT ? &SGT_A(T, ldt, 0, unit) : &SGT_A(Q, ldq, unit - n, 0);
+    const size_t stride = isT ? 1 : (size_t)ldq;
     const int logged = st->logged;
-    if (g < n) {
-        const int j = g;
-        for (int w = 0; w < logged; w++) {
-            const SweepRec sr = sweeplog[w];
-            if (j <= sr.i) continue;
-            double2 carry = SGT_A(T, ldt, sr.l, j);
-            for (int k = sr.l; k < sr.i; k++) {
-                const double c = rclog[sr.off + (k - sr.l)];
-                const double2 s = rslog[sr.off + (k - sr.l)];
-                double2 a = carry, b = SGT_A(T, ldt, k + 1, j);
-                rot_rows(c, s, a, b);
-                SGT_A(T, ldt, k, j) = a;
-                carry = b;
-            }
-            SGT_A(T, ldt, sr.i, j) = carry;
+    for (int w = 0; w < logged; w++) {
+        const SweepRec sr = sweeplog[w];
+        if (isT && unit <= sr.i) continue;
+        double2 a = line[(size_t)sr.l * stride];
+        double2 b = line[(size_t)(sr.l + 1) * stride];
+        for (int k = sr.l; k < sr.i; k++) {
+            const double c = rclog[sr.off + (k - sr.l)];
+            const double2 s = rslog[sr.off + (k - sr.l)];
+            const double2 bn = (k + 2 <= sr.i) ? line[(size_t)(k + 2) * stride] : b;
+            // G (T's rows) or G^H (Q's columns) on (a, b): lane part gives
+            // part 0 a'.x, 1 a'.y, 2 b'.x, 3 b'.y
+            const double2 u = hi ? b : a, v = hi ? a : b;
+            const double sy = isT ? (odd ? s.y : -s.y) : (odd ? -s.y : s.y);
+            const double r = pair_part(c, odd ? u.y : u.x, hi ? -s.x : s.x, odd ? v.y : v.x, sy, odd ? v.x : v.y);
+            if (!hi) reinterpret_cast<double *>(&line[(size_t)k * stride])[part] = r;
+            a = make_double2(__shfl_sync(gmask, r, 2, 4), __shfl_sync(gmask, r, 3, 4));
+            b = bn;
         }
-    } else {
-        const int r = g - n;
-        for (int w = 0; w < logged; w++) {
-            const SweepRec sr = sweeplog[w];
-            double2 carry = SGT_A(Q, ldq, r, sr.l);
-            for (int k = sr.l; k < sr.i; k++) {
-                const double c = rclog[sr.off + (k - sr.l)];
-                const double2 s = rslog[sr.off + (k - sr.l)];
-                double2 a = carry, b = SGT_A(Q, ldq, r, k + 1);
-                rot_cols(c, s, a, b);
-                SGT_A(Q, ldq, r, k) = a;
-                carry = b;
-            }
-            SGT_A(Q, ldq, r, sr.i) = carry;
-        }
+        if (part == 0) line[(size_t)sr.i * stride] = a;
     }
 }
 
@@ -761,7 +774,7 @@ signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, do
             schur_qr_kernel<<<kQrCluster, kQrThreads, 0, st>>>(n, Tc, ldt, qs, kRotationBudget, sweeplog, rclog,
                                                                 rslog);
             SGT_LAUNCH_CHECK();
-            apply_rotations_kernel<<<(2 * n + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, Tc, ldt, Qc, ldq, qs,
+            apply_rotations_kernel<<<(8 * n + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, Tc, ldt, Qc, ldq, qs,
                                                                                         sweeplog, rclog, rslog);
             SGT_LAUNCH_CHECK();
         }
