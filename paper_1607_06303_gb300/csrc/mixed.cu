@@ -259,64 +259,28 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
     const int bj = min(MB, n - c0);
     const int p = threadIdx.x % MB, q0 = threadIdx.x / MB;
 
-    // every global read that needs no sign first: the operators, the base
-    // terms of the seeds, this tile's partial slots
+    // every global read before the first barrier: this tile's partial slots,
+    // the base terms of the seeds, the operators
     const int2 ts = tslot[I];
     const int2 ts2 = (MODE == 0 && tslot2) ? tslot2[I] : make_int2(0, 0);
-    // base terms staged in VR (t_pq, or Rc_pq) and VC (Rs_pq) at the thread's
-    // own entries until the seeds replace them
-#pragma unroll 4
-    for (int m = 0; m < EPT; m++) {
-        const int q = q0 + m * QS;
-        const bool ok = q < bj;
-        VR[p * LD + q] = ok ? (float)SGT_AT(MODE == 0 ? T : Rc, MODE == 0 ? ldt : ldr, r0 + p, c0 + q) : 0.f;
-        VC[q * LD + p] = (MODE == 1 && ok) ? (float)SGT_AT(Rs, ldr, r0 + p, c0 + q) : 0.f;
-    }
+    // the partial block sums first (the largest read), with the signs of the
+    // thread's own row and columns taken from DIAG, so that they are in
+    // flight with the reads below: float2 (hi, lo) per element, summed in
+    // fp32 over the slots
+    float acc[EPT];
+    bool opp[EPT];
     {
-        const float4 *src[4] = {reinterpret_cast<const float4 *>(OPS + (size_t)(4 * I + 0) * MB * MB),
-                                reinterpret_cast<const float4 *>(OPS + (size_t)(4 * I + 1) * MB * MB),
-                                reinterpret_cast<const float4 *>(OPS + (size_t)(4 * J + 2) * MB * MB),
-                                reinterpret_cast<const float4 *>(OPS + (size_t)(4 * J + 3) * MB * MB)};
-        float *dst[4] = {Mp, Mm, Np, Nm};
-#pragma unroll
-        for (int a = 0; a < 4; a++) {
-            float4 v[MB * MB / 4 / kLeafThreads];
-#pragma unroll
-            for (int m = 0; m < MB * MB / 4 / kLeafThreads; m++) v[m] = src[a][threadIdx.x + m * kLeafThreads];
-#pragma unroll
-            for (int m = 0; m < MB * MB / 4 / kLeafThreads; m++) {
-                const int e = 4 * (threadIdx.x + m * kLeafThreads);
-                // four consecutive entries of one row (M) or column (N)
-                *reinterpret_cast<float4 *>(dst[a] + (e / MB) * LD + e % MB) = v[m];
-            }
-        }
-    }
-    for (int i = threadIdx.x; i < MB; i += kLeafThreads) {
-        const float dr = DIAG[r0 + i], dc = DIAG[c0 + i];
-        drow[i] = dr;
-        dcol[i] = dc;
-        srow[i] = dr > 0.f ? 1.f : -1.f;
-        scol[i] = (i < bj) ? (dc > 0.f ? 1.f : -1.f) : 1.f;
-    }
-    __syncthreads();
-
-    // seeds: block sums (their K range includes the diagonal blocks K = I
-    // and K = J, so they already hold the in-block products of the known
-    // blocks: U_II T_IJ - T_IJ U_JJ for opposite signs in mode 0, E_II T_IJ -
-    // T_IJ E_JJ and E_II U0_IJ + U0_IJ E_JJ in mode 1; terms with the unknown
-    // V_IJ vanish, its slices being still zero) and the base terms.  Partial
-    // block sums: float2 (hi, lo) per element, summed in fp32 over the slots.
-    {
-        const float2 *PA2 = reinterpret_cast<const float2 *>(PA);
-        const float2 *PB2 = reinterpret_cast<const float2 *>(PB);
-        float acc[EPT];
-        bool opp[EPT];
+        const float sgp = DIAG[r0 + p] > 0.f ? 1.f : -1.f;
 #pragma unroll
         for (int m = 0; m < EPT; m++) {
+            const int q = q0 + m * QS;
+            const float sgq = (q < bj) ? (DIAG[c0 + q] > 0.f ? 1.f : -1.f) : 1.f;
             acc[m] = 0.f;
-            opp[m] = srow[p] + scol[q0 + m * QS] == 0.f;
+            opp[m] = sgp + sgq == 0.f;
         }
-#pragma unroll 2
+        const float2 *PA2 = reinterpret_cast<const float2 *>(PA);
+        const float2 *PB2 = reinterpret_cast<const float2 *>(PB);
+        #pragma unroll 2
         for (int s = 0; s < ts.y + ts2.y; s++) {
             // mode 0: slots of PA, then (look-ahead pairing) slots of PB
             const bool second = s >= ts.y;
@@ -336,6 +300,54 @@ mixed_leaf_kernel(int n, const double *__restrict__ T, int ldt, double *__restri
                 acc[m] += (l1.x + sg * l2.x) + (l1.y + sg * l2.y);
             }
         }
+    }
+    // base terms staged in VR (t_pq, or Rc_pq) and VC (Rs_pq) at the thread's
+    // own entries until the seeds replace them
+#pragma unroll 4
+    for (int m = 0; m < EPT; m++) {
+        const int q = q0 + m * QS;
+        const bool ok = q < bj;
+        VR[p * LD + q] = ok ? (float)SGT_AT(MODE == 0 ? T : Rc, MODE == 0 ? ldt : ldr, r0 + p, c0 + q) : 0.f;
+        VC[q * LD + p] = (MODE == 1 && ok) ? (float)SGT_AT(Rs, ldr, r0 + p, c0 + q) : 0.f;
+    }
+    {
+        const float4 *src[4] = {reinterpret_cast<const float4 *>(OPS + (size_t)(4 * I + 0) * MB * MB),
+                                reinterpret_cast<const float4 *>(OPS + (size_t)(4 * I + 1) * MB * MB),
+                                reinterpret_cast<const float4 *>(OPS + (size_t)(4 * J + 2) * MB * MB),
+                                reinterpret_cast<const float4 *>(OPS + (size_t)(4 * J + 3) * MB * MB)};
+        float *dst[4] = {Mp, Mm, Np, Nm};
+        // all four operators' loads in flight before the first store
+        constexpr int V4 = MB * MB / 4 / kLeafThreads;
+        float4 v[4][V4];
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int m = 0; m < V4; m++) v[a][m] = src[a][threadIdx.x + m * kLeafThreads];
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int m = 0; m < V4; m++) {
+                const int e = 4 * (threadIdx.x + m * kLeafThreads);
+                // four consecutive entries of one row (M) or column (N)
+                *reinterpret_cast<float4 *>(dst[a] + (e / MB) * LD + e % MB) = v[a][m];
+            }
+    }
+    for (int i = threadIdx.x; i < MB; i += kLeafThreads) {
+        const float dr = DIAG[r0 + i], dc = DIAG[c0 + i];
+        drow[i] = dr;
+        dcol[i] = dc;
+        srow[i] = dr > 0.f ? 1.f : -1.f;
+        scol[i] = (i < bj) ? (dc > 0.f ? 1.f : -1.f) : 1.f;
+    }
+    __syncthreads();
+
+    // seeds: block sums (their K range includes the diagonal blocks K = I
+    // and K = J, so they already hold the in-block products of the known
+    // blocks: U_II T_IJ - T_IJ U_JJ for opposite signs in mode 0, E_II T_IJ -
+    // T_IJ E_JJ and E_II U0_IJ + U0_IJ E_JJ in mode 1; terms with the unknown
+    // V_IJ vanish, its slices being still zero), summed into acc above, and
+    // the base terms.
+    {
 #pragma unroll
         for (int m = 0; m < EPT; m++) {
             const int q = q0 + m * QS;
