@@ -152,3 +152,28 @@ def test_schur_errors_and_arguments(gpu_lib):
     assert p.signtri_sign_general(0, 0, 1, 0, 1, h) == p.Status.OK
     assert p.signtri_schur_workspace_bytes(n) > 0 and p.signtri_sign_general_workspace_bytes(n) > 0
     torch.cuda.synchronize()
+
+
+def test_schur_block_triangular_large(gpu_lib):
+    # n beyond one pass of the sweep kernel's worker threads (7 x 512 entries
+    # per rotation): a block upper triangular A with 2 x 2 diagonal blocks
+    # [a b; -b a] (eigenvalues a +- ib) is already Hessenberg and splits at
+    # every block, so the QR sweeps are short while the column work above
+    # each block spans up to n rows; the eigenvalues are known exactly
+    rng = np.random.Generator(np.random.PCG64(41))
+    n = 3700
+    A = np.triu(rng.uniform(-1.0, 1.0, (n, n)), 2)
+    ev = []
+    for i in range(0, n, 2):
+        a, b = rng.uniform(0.5, 2.0) * rng.choice([-1.0, 1.0]), rng.uniform(0.5, 2.0)
+        A[i:i + 2, i:i + 2] = [[a, b], [-b, a]]
+        ev += [a + 1j * b, a - 1j * b]
+    A = np.asfortranarray(A)
+    Q, T = _schur(gpu_lib, A)
+    assert np.all(np.tril(T, -1) == 0)
+    eps = np.finfo(float).eps
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(n)) <= 50 * n * eps
+    assert _rel(Q @ T @ Q.conj().T, A) <= 50 * n * eps
+    got = np.sort_complex(np.diag(T))
+    want = np.sort_complex(np.array(ev))
+    assert np.abs(got - want).max() <= 1e-12 * 4.0
