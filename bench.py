@@ -49,8 +49,8 @@ UNIT = "GFLOP/s"
 TRAFFIC_SOURCES = ("paper_1607_06303_gb300/csrc/tc_gemm.cu", "paper_1607_06303_gb300/csrc/mixed.cu")
 TRAFFIC = {
     # n = 16384, p = 0.5 random, PH_MIXED_FP16 (profiles/launches_mixed_n16384.txt)
-    ("residual", "4fd781973f172d7d"): 35.946e9,
-    ("block_sums_tc", "4fd781973f172d7d"): 638.9e6,
+    ("residual", "4db3e3eba6679ba8"): 35.737e9,
+    ("block_sums_tc", "4db3e3eba6679ba8"): 638.9e6,
 }
 
 
@@ -629,6 +629,28 @@ def main():
         line["e2e"] = {"value": useful_all / e2e_s / 1e9, "unit": UNIT,
                        "h2d_bytes_per_step": h2d_bytes(n), "d2h_bytes_per_step": Uh.numel() * 8,
                        "seconds_per_solve": e2e_s, "repetitions_s": reps}
+        # where one call's time goes, after (outside) the timed repetitions:
+        # the two copies and the kernels by CUDA events, the rest host-side
+        st.signtri_profile_reset()
+        st.signtri_profile_enable(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = st.sign_tri_host(n, Th.data_ptr(), n, Uh.data_ptr(), n, variant, h)
+        wall_ms = (time.perf_counter() - t0) * 1e3
+        st.signtri_profile_enable(False)
+        if s != 0:
+            raise st.SignTriError(s, "sign_tri_host")
+        copy_ms = kern_ms = 0.0
+        for c in range(st.signtri.KC_COUNT):
+            cnt, dms = st.signtri_profile_read(c)
+            if c == st.signtri.KC_HOST_COPY:
+                copy_ms = dms
+            else:
+                kern_ms += dms
+        line["e2e"]["one_call_ms"] = {"wall": wall_ms, "copies": copy_ms, "kernels": kern_ms,
+                                      "rest": wall_ms - copy_ms - kern_ms,
+                                      "what": "one extra sign_tri_host call with the library's CUDA-event "
+                                              "profiling on; rest = host work, launch gaps and waits"}
         del Th, Uh
 
     # comparison variants on the same input, fewer steps

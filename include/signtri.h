@@ -422,7 +422,8 @@ enum {
     SIGNTRI_KC_BATCH_GRAPH = 16,  /* one launch of the captured batch graph */
     SIGNTRI_KC_SCHUR = 17,        /* Schur decomposition: QR sweeps and their rotations */
     SIGNTRI_KC_HESSENBERG = 18,   /* Schur decomposition: Householder reduction */
-    SIGNTRI_KC_COUNT = 19
+    SIGNTRI_KC_HOST_COPY = 19,    /* sign_tri_host's host <-> device copies (counted as calls) */
+    SIGNTRI_KC_COUNT = 20
 };
 
 /* on != 0: bracket every library kernel launch with CUDA events on its

@@ -1026,11 +1026,14 @@ signtri_status sign_tri_host(int n, const double *T_host, int ldt, double *U_hos
     // only T's upper triangle is read: copy it by column panels, each from
     // row 0 to its last column's diagonal (about half of T's bytes)
     constexpr int kPanel = 128;
-    for (int j0 = 0; j0 < n; j0 += kPanel) {
-        const int cols = std::min(kPanel, n - j0), rows = std::min(n, j0 + kPanel);
-        SGT_CUDA_TRY(cudaMemcpy2DAsync(s->stage_T + (size_t)j0 * n, (size_t)n * sizeof(double),
-                                       T_host + (size_t)j0 * ldt, (size_t)ldt * sizeof(double),
-                                       (size_t)rows * sizeof(double), cols, cudaMemcpyHostToDevice, st));
+    {
+        ProfScope ps(SIGNTRI_KC_HOST_COPY, st);
+        for (int j0 = 0; j0 < n; j0 += kPanel) {
+            const int cols = std::min(kPanel, n - j0), rows = std::min(n, j0 + kPanel);
+            SGT_CUDA_TRY(cudaMemcpy2DAsync(s->stage_T + (size_t)j0 * n, (size_t)n * sizeof(double),
+                                           T_host + (size_t)j0 * ldt, (size_t)ldt * sizeof(double),
+                                           (size_t)rows * sizeof(double), cols, cudaMemcpyHostToDevice, st));
+        }
     }
     rs = sign_tri_locked(n, s->stage_T, n, s->stage_U, n, v, st, *s);
     if (rs != SIGNTRI_OK) {
@@ -1038,8 +1041,11 @@ signtri_status sign_tri_host(int n, const double *T_host, int ldt, double *U_hos
         cudaStreamSynchronize(st);
         return rs;
     }
-    SGT_CUDA_TRY(cudaMemcpy2DAsync(U_host, (size_t)ldu * sizeof(double), s->stage_U, (size_t)n * sizeof(double),
-                                   (size_t)n * sizeof(double), n, cudaMemcpyDeviceToHost, st));
+    {
+        ProfScope ps(SIGNTRI_KC_HOST_COPY, st);
+        SGT_CUDA_TRY(cudaMemcpy2DAsync(U_host, (size_t)ldu * sizeof(double), s->stage_U, (size_t)n * sizeof(double),
+                                       (size_t)n * sizeof(double), n, cudaMemcpyDeviceToHost, st));
+    }
     SGT_CUDA_TRY(cudaStreamSynchronize(st));
     return SIGNTRI_OK;
 }

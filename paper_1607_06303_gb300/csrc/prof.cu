@@ -46,7 +46,7 @@ const char *kClassNames[SIGNTRI_KC_COUNT] = {
     "inertia_scan", "fill", "diag_leaf_f64", "block_sums_f64", "offdiag_leaf_f64",
     "block_sums_tc", "offdiag_leaf_mixed", "convert", "residual", "correction",
     "givens_rounds", "sylvester_sums", "sylvester_leaf", "gemm_f64", "other", "residual_sum", "batch_graph", "schur",
-    "hessenberg",
+    "hessenberg", "host_copies",
 };
 
 bool p_paused = false;

@@ -132,7 +132,8 @@ KC_GIVENS, KC_SYLV_SUMS, KC_SYLV_LEAF, KC_GEMM_F64, KC_OTHER, KC_RESIDUAL_SUM = 
 KC_BATCH_GRAPH = 16
 KC_SCHUR = 17
 KC_HESSENBERG = 18
-KC_COUNT = 19
+KC_HOST_COPY = 19
+KC_COUNT = 20
 
 
 def load(path: str = LIB_PATH):
