@@ -132,8 +132,11 @@ def test_step_line(no_gpu_step, capsys, monkeypatch):
     for key in ("sm_mhz", "sm_max_mhz", "reasons"):
         assert key in line["clocks"], key
     assert [c["variant"] for c in line["compare"]] == ["PH_MIXED_TF32", "PH_FP64_EFFICIENT", "PH_FP64"]
-    # warm-up, timed steps, e2e (one warm call + three repetitions), comparisons
-    assert no_gpu_step["solves"] == 3 + 3 + 1 + 3 * 3 + 3 * (1 + 2)
+    for key in ("wall", "copies", "kernels", "rest"):
+        assert key in e2e["one_call_ms"], key
+    # warm-up, timed steps, e2e (one warm call + three repetitions + one
+    # profiled call for the breakdown), comparisons
+    assert no_gpu_step["solves"] == 3 + 3 + 1 + 3 * 3 + 1 + 3 * (1 + 2)
 
 
 def test_reference_line(capsys, monkeypatch):
