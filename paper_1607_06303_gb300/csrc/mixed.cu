@@ -159,15 +159,20 @@ __global__ void leaf_ops_kernel(int n, const double *__restrict__ T, int ldt, co
 
 // One warp solves the 16 x 16 sub-block with rows R0.. and columns C0.. of a
 // leaf tile (the recurrences above restricted to it; the terms of the other,
-// already solved, sub-blocks are in VR and VC).  Lane p (and its mirror p +
-// 16, which writes nothing) owns row R0 + p: its pending values c[q] start as
-// seed + row parts - column parts of the solved sub-blocks, entry (p, q) is
-// solved at step t = 15 - p + q, and each solved value is pushed at once into
-// the entries that depend on it -- into the row's later entries by the lane
-// itself (+ v N~), into the entries above it in its column by the other
-// lanes, which receive it by shuffle (- M v).  A step thus waits only for
-// one shuffle and one multiply-add; the step loop is unrolled so that every
-// register index is a constant.
+// already solved, sub-blocks are in VR and VC).  Lane (p, h) = p + 16 h owns
+// row R0 + p, columns C0 + 8h .. C0 + 8h + 7: its pending values c[j] start
+// as seed + row parts - column parts of the solved sub-blocks; entry (p, q)
+// is solved at step t = 15 - p + q by the lane of q's half, and each solved
+// value is pushed at once into the entries that depend on it -- into the
+// row's later entries by both lanes of the row (+ v N~, the value passed to
+// the other half by a shuffle), into the entries above it in its column by
+// the other rows' lanes of the same half, which receive it by shuffle
+// (- M v).  The coefficients M^{+-}[p][k] sit in each lane rotated by 8 h,
+// so that one constant register index serves both halves; the step's pending
+// value is picked by a three-level select tree and divided by a reciprocal
+// taken off the chain.  Both halves working halves the instructions per
+// step; the step loop is unrolled so that every register index is a
+// constant.
 __device__ __forceinline__ void subblock_solve(const float *__restrict__ Mp, const float *__restrict__ Mm,
                                                const float *__restrict__ Np, const float *__restrict__ Nm,
                                                float *__restrict__ VC, float *__restrict__ VR,
@@ -176,49 +181,57 @@ __device__ __forceinline__ void subblock_solve(const float *__restrict__ Mp, con
                                                int C0, int lane)
 {
     constexpr int LD = kLeafLD;
-    const int p = lane & (kSub - 1);
+    const int p = lane & (kSub - 1), h = lane >> 4;
     const int P = R0 + p;
     // column signs of the sub-block, bit q for column C0 + q
     const unsigned colmask = __ballot_sync(0xffffffffu, lane < kSub && scol[C0 + p] > 0.f) & 0xffffu;
+    const unsigned hmask = (colmask >> (8 * h)) & 0xffu;   // this half's columns
     const float sp = srow[P], dp = drow[P];
-    float c[kSub], mp[kSub], mm[kSub];
+    float c[8], mr[24], nr[24];
 #pragma unroll
-    for (int q = 0; q < kSub; q++) c[q] = VR[P * LD + C0 + q] - VC[(C0 + q) * LD + P];
+    for (int j = 0; j < 8; j++) c[j] = VR[P * LD + C0 + 8 * h + j] - VC[(C0 + 8 * h + j) * LD + P];
+    // mr[x] = M^+[p][x - 8 + 8h], nr[x] = M^-[p][x - 8 + 8h] (0 outside the block)
 #pragma unroll
-    for (int k = 0; k < kSub; k += 4) {
-        const float4 x = *reinterpret_cast<const float4 *>(Mp + P * LD + R0 + k);
-        const float4 y = *reinterpret_cast<const float4 *>(Mm + P * LD + R0 + k);
-        mp[k] = x.x; mp[k + 1] = x.y; mp[k + 2] = x.z; mp[k + 3] = x.w;
-        mm[k] = y.x; mm[k + 1] = y.y; mm[k + 2] = y.z; mm[k + 3] = y.w;
+    for (int x = 0; x < 24; x++) {
+        const int k = x - 8 + 8 * h;
+        const bool ok = k >= 0 && k < kSub;
+        mr[x] = ok ? Mp[P * LD + R0 + k] : 0.f;
+        nr[x] = ok ? Mm[P * LD + R0 + k] : 0.f;
     }
     const float *Nt = (sp > 0.f ? Np : Nm) + C0 * LD + C0;   // N~^{s_p}, this sub-block
     float vprev = 0.f;
 #pragma unroll
     for (int t = 0; t < 2 * kSub - 1; t++) {
-        // column parts: row k solved column t - 16 + k at the previous step
+        // column parts: column q = 8h + j takes row k = q + 16 - t, solved at
+        // the previous step by lane k + 16 h (the same half)
 #pragma unroll
-        for (int k = 0; k < kSub; k++) {
-            const int qk = t - kSub + k;
-            if (t > 0 && qk >= 0 && qk < kSub) {
-                const float vk = __shfl_sync(0xffffffffu, vprev, k);
-                c[qk] = fmaf((colmask >> qk) & 1u ? -mp[k] : -mm[k], vk, c[qk]);
+        for (int j = 0; j < 8; j++) {
+            const int k0 = j + kSub - t;   // k in half 0; k0 + 8 in half 1
+            if (t > 0 && k0 >= -8 && k0 < kSub) {
+                const int src = min(max(k0 + 8 * h, 0), kSub - 1) + 16 * h;
+                const float vk = __shfl_sync(0xffffffffu, vprev, src);
+                c[j] = fmaf((hmask >> j) & 1u ? -mr[k0 + 8] : -nr[k0 + 8], vk, c[j]);
             }
         }
-        const int qp = t - (kSub - 1) + p;
-        const bool act = lane < kSub && qp >= 0 && qp < kSub;
+        const int qp = t - (kSub - 1) + p;   // the row's column at this step
+        const int hc = qp >> 3;               // its half
+        const bool act = qp >= 0 && qp < kSub && hc == h;
         const int qc = min(max(qp, 0), kSub - 1);
-        float x = 0.f;
-#pragma unroll
-        for (int q = 0; q < kSub; q++)
-            if (q >= t - (kSub - 1) && q <= t && q == qc) x = c[q];
         const bool sq = (colmask >> qc) & 1u;
         const bool opp = (sp > 0.f) != sq;
         const float den = opp ? dp - dcol[C0 + qc] : sp + (sq ? 1.f : -1.f);
-        const float v = act ? __fdividef(x, den) : 0.f;
-        // row part into the row's later entries (N~ vanishes for q <= qc)
+        const float rden = __fdividef(1.f, den);
+        const int jb = (qc - 8 * h) & 7;
+        const float s0 = (jb & 1) ? c[1] : c[0], s1 = (jb & 1) ? c[3] : c[2];
+        const float s2 = (jb & 1) ? c[5] : c[4], s3 = (jb & 1) ? c[7] : c[6];
+        const float u0 = (jb & 2) ? s1 : s0, u1 = (jb & 2) ? s3 : s2;
+        const float x = (jb & 4) ? u1 : u0;
+        const float v = act ? x * rden : 0.f;
+        // the row's solved value to both halves, then its row part
+        const float vrow = __shfl_sync(0xffffffffu, v, p + 16 * min(max(hc, 0), 1));
         if (t < 2 * kSub - 2) {
 #pragma unroll
-            for (int q = 0; q < kSub; q++) c[q] = fmaf(Nt[q * LD + qc], v, c[q]);
+            for (int j = 0; j < 8; j++) c[j] = fmaf(Nt[(8 * h + j) * LD + qc], vrow, c[j]);
         }
         if (act) {
             VC[(C0 + qc) * LD + P] = v;
