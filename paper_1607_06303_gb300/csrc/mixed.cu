@@ -199,16 +199,18 @@ __device__ __forceinline__ void subblock_solve(const float *__restrict__ Mp, con
         nr[x] = ok ? Mm[P * LD + R0 + k] : 0.f;
     }
     const float *Nt = (sp > 0.f ? Np : Nm) + C0 * LD + C0;   // N~^{s_p}, this sub-block
+    const int base = 24 * h;
     float vprev = 0.f;
 #pragma unroll
     for (int t = 0; t < 2 * kSub - 1; t++) {
         // column parts: column q = 8h + j takes row k = q + 16 - t, solved at
-        // the previous step by lane k + 16 h (the same half)
+        // the previous step by lane k + 16 h = k0 + 24 h (the same half;
+        // taken mod 32 where k is outside the block and the coefficient 0)
 #pragma unroll
         for (int j = 0; j < 8; j++) {
             const int k0 = j + kSub - t;   // k in half 0; k0 + 8 in half 1
             if (t > 0 && k0 >= -8 && k0 < kSub) {
-                const int src = min(max(k0 + 8 * h, 0), kSub - 1) + 16 * h;
+                const int src = (base + k0) & 31;
                 const float vk = __shfl_sync(0xffffffffu, vprev, src);
                 c[j] = fmaf((hmask >> j) & 1u ? -mr[k0 + 8] : -nr[k0 + 8], vk, c[j]);
             }
