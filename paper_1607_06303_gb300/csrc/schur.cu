@@ -25,16 +25,16 @@
 //     |h_{k,k-1}| <= eps (|h_{k-1,k-1}| + |h_kk|) (|z| = |Re z| + |Im z|).
 //     Deflation takes the window's last row when its subdiagonal entry is
 //     negligible.  The rotations of a sweep depend on one another (each reads
-//     what the one before wrote), so one CTA runs the sweeps with a barrier
-//     per rotation, applying each to the active window only; a launch runs
-//     sweeps until a rotation budget is spent and logs them, then a kernel on
-//     every SM applies the logged rotations to the columns right of each
-//     sweep's window and to Q, and the host relaunches until the window is
-//     empty.  The window part bounds the stage: about 3.4 sweeps per
-//     eigenvalue, sum over sweeps of (window)^2 ~ 1.1 n^3 entry updates of
-//     ~14 float64 operations on one SM, whose float64 rate is ~2 per cycle
-//     on GB300 -- the decomposition is the general-matrix front end, not a
-//     tuned hot path.
+//     what the one before wrote), so one 8-CTA cluster runs the sweeps with a
+//     cluster barrier per rotation, applying each to the active window only
+//     (schur_qr_kernel says how the work is split); a launch runs sweeps
+//     until a rotation budget is spent and logs them, then a kernel on every
+//     SM applies the logged rotations to the columns right of each sweep's
+//     window and to Q, and the host relaunches until the window is empty.
+//     The chain of rotations bounds the stage: about 3 sweeps per eigenvalue,
+//     ~1.25 n^2 rotations for n eigenvalues, each a few thousand cycles of
+//     float64 latency and a barrier -- the decomposition is the
+//     general-matrix front end, not a tuned hot path.
 //
 // Layout: A real column-major; Q, T complex interleaved (re, im) float64
 // pairs, column-major, leading dimensions counted in complex elements.
