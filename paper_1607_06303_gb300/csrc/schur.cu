@@ -314,44 +314,54 @@ __global__ void qr_state_init_kernel(int n, QrState *st)
     st->rotations = 0;
 }
 
-// One cluster of kQrCluster CTAs runs the sweeps.  On GB300 a float64 warp
-// instruction holds its SM sub-partition's float64 pipe for ~64 cycles
-// whatever the number of active lanes (and rsqrt or a division for ~430),
-// so the kernel is laid out around float64 instruction counts:
-//  * CTA 0's warp 0 (the chief warp) runs the chase's serial part alone on
-//    its sub-partition: the 2 x 2 block at (k, k) and row k+2 of columns
-//    k, k+1, where the next rotation's inputs (h_{k+1,k}, h_{k+2,k}) are
-//    formed, lane-parallel (one real output per lane: 8 lanes for G's action
-//    on the block's two columns, 12 for G^H's on its three rows, 3 float64
-//    instructions each), kept in registers from step to step; then the next
-//    rotation, its two reciprocal square roots in lanes 0 and 1 at once,
-//    stored into every
-//    CTA's shared memory (two slots, alternating).  The one entry of the next
+// One cluster of kQrCluster CTAs runs the sweeps, one or two bulges at a time.
+// Two bulges: both eigenvalues of the window's trailing 2 x 2 as shifts
+// (Francis's double shift, in complex arithmetic as two single shifts), the
+// second bulge started 3 steps behind the first; mathematically the two
+// sweeps one after the other (the rotations of the front sweep that touch
+// the rear bulge's rows and columns are all done before it gets there, and
+// the later ones act on disjoint rows and columns), with half the dependent
+// steps.  On GB300 a float64 warp instruction holds its SM sub-partition's
+// float64 pipe for ~64 cycles whatever the number of active lanes (and
+// rsqrt or a division for ~430), so the kernel is laid out around float64
+// instruction counts:
+//  * CTA 0's warp b (chief warp of bulge b) runs that chase's serial part
+//    alone on its sub-partition: the 2 x 2 block at (k, k) and row k+2 of
+//    columns k, k+1, where the next rotation's inputs (h_{k+1,k}, h_{k+2,k})
+//    are formed, lane-parallel (one real output per lane: 8 lanes for G's
+//    action on the block's two columns, 12 for G^H's on its three rows, 3
+//    float64 instructions each), kept in registers from step to step; the
+//    entry left of the block (h_{k,k-1}, zeroing the old bulge) from the
+//    rotation's own inputs; then the next rotation, its two reciprocal
+//    square roots in lanes 0 and 1 at once, stored into every CTA's shared
+//    memory (two slots per bulge, alternating).  The one entry of the next
 //    block that another thread writes, h_{k+1,k+2} (row op of column k+2),
-//    comes through shared memory too, and the entries no step touches before
-//    (h_{k+2,k+2}, h_{k+3,k+2}) are loaded two steps ahead.
+//    comes through shared memory; the front chase loads the entries no step
+//    touches before (h_{k+2,k+2}, h_{k+3,k+2}) two steps ahead, the rear
+//    chase takes them from the front chief, who wrote them one and zero
+//    steps before (h_{k+2,k+2} as its block's corner, h_{k+3,k+2} as the
+//    entry left of its block), or from T once the front chase has ended.
 //  * CTAs 1.. do the rest of every rotation (rows k, k+1 across the window,
-//    columns k, k+1 above the block), entry e to warp e / 32 of a sequence
-//    that alternates CTAs and sub-partitions, so the work fills whole warps
-//    spread over the cluster.
-// One cluster barrier per rotation; no entry is written by one thread while
-// another reads it.  CTA 0 alone takes every decision (deflation, shift,
+//    columns k, k+1 above the block) and, with two bulges, the 2 x 2 block
+//    at the rear bulge's rows and the front bulge's columns, which takes the
+//    rear rotation from the left and the front one from the right; entry e
+//    goes to warp e / 32 of a sequence that alternates CTAs and
+//    sub-partitions, so the work fills whole warps spread over the cluster.
+// One cluster barrier per step; no entry is written by one thread while
+// another reads it.  CTA 0 alone takes every decision (deflation, shifts,
 // stop) and broadcasts it, so all CTAs run the same barriers.  T is read with
 // L2-only loads (another CTA may have written it since).  The rotations'
 // action on the columns right of the window (rows there are never read by a
 // later sweep: the window only shrinks) and on Q is left to
 // apply_rotations_kernel, which runs on every SM: this kernel logs each sweep
-// and its rotations instead.
+// and its rotations instead (the rear sweep after the front one).
 constexpr int kQrCluster = 8;
 constexpr int kQrWorkers = kQrCluster - 1;                       // CTAs 1..
 constexpr int kQrWorkerThreads = kQrWorkers * kQrThreads;
+constexpr int kMaxBulges = 2;
 enum { kActSweep = 0, kActDeflate = 1, kActStop = 2 };
 
 __device__ __forceinline__ double2 ldT(const double2 *p) { return __ldcg(p); }
-__device__ __forceinline__ double2 shfl2(double2 v, int src)
-{
-    return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
-}
 // the unbiased exponent field of |x| (integer operations only)
 __device__ __forceinline__ int exp_field(double x)
 {
@@ -410,30 +420,34 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     __shared__ int redi[kQrThreads / 32];
-    __shared__ double rc[2];
-    __shared__ double2 rs[2];
-    __shared__ double2 bslot[2];   // CTA 0: h_{k+1,k+2} after step k, for step k+1
-    __shared__ int ctl[3];         // action, l, i (CTA 0's decision)
+    __shared__ double rc[kMaxBulges][2];
+    __shared__ double2 rs[kMaxBulges][2];
+    __shared__ double2 bslot[kMaxBulges][2];   // CTA 0: h_{k+1,k+2} after a step, per bulge
+    __shared__ double2 handF[2], handH[2];       // CTA 0: the front chief's corner and left entry, per step
+    __shared__ double2 sig1;                     // CTA 0: the rear bulge's shift
+    __shared__ int ctl[4];                       // action, l, i, bulges (CTA 0's decision)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned crank = cl.block_rank();
-    const bool chiefw = crank == 0 && warp == 0;   // the chief warp
-    const bool chief = chiefw && lane == 0;
+    const int cb = (crank == 0 && warp < kMaxBulges) ? warp : -1;   // the bulge of a chief warp
+    const bool chief0 = crank == 0 && warp == 0;
     // this worker thread's first entry and the stride (CTAs 1.. only)
     const int e0 = ((warp * kQrWorkers + ((int)crank - 1)) << 5) + lane;
     int i = st->ihi, its = st->its, status = st->status;
-    long long sweeps = 0, rot = 0;
+    long long logged = 0, rot = 0;
     const double eps = DBL_EPSILON;
     const double tiny = DBL_MIN * ((double)n / DBL_EPSILON);
     const double2 zero = make_double2(0.0, 0.0);
-    // the chief warp's registers, the same in every lane: the block
-    // (A B; E F) at (k, k) and Hh = h_{k+2,k+1}
-    double2 A = zero, B = zero, E = zero, F = zero, Hh = zero;
-    double2 pf_f = zero, pf_h = zero;   // h_{k+2,k+2}, h_{k+3,k+2} for step k+1, loaded a step early
-    auto put_rotation = [&](int slot, double c, double2 s) {
-        // lanes 0..kQrCluster-1 of the chief warp store into CTA `lane`
+    // a chief warp's registers, the same in every lane: the block (A B; E F)
+    // at (k, k), Hh = h_{k+2,k+1}, the rotation of the step and its inputs
+    // (X, Y) = (h_{k,k-1}, h_{k+1,k-1})
+    double2 A = zero, B = zero, E = zero, F = zero, Hh = zero, X = zero, Y = zero, s_cur = zero;
+    double c_cur = 1.0;
+    double2 pf_f = zero, pf_h = zero;   // front chase: h_{k+2,k+2}, h_{k+3,k+2} for step k+1, loaded early
+    auto put_rotation = [&](int b, int slot, double c, double2 s) {
+        // lanes 0..kQrCluster-1 of a chief warp store into CTA `lane`
         if (lane < kQrCluster) {
-            *cl.map_shared_rank(&rc[slot], lane) = c;
-            *cl.map_shared_rank(&rs[slot], lane) = s;
+            *cl.map_shared_rank(&rc[b][slot], lane) = c;
+            *cl.map_shared_rank(&rs[b][slot], lane) = s;
         }
     };
     for (;;) {
@@ -448,10 +462,10 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
             for (int o = 16; o > 0; o >>= 1) lk = max(lk, __shfl_xor_sync(0xffffffffu, lk, o));
             if (lane == 0) redi[warp] = lk;
             __syncthreads();
-            if (chiefw) {
+            if (chief0) {
                 int l = 0;
                 for (int w = 0; w < kQrThreads / 32; w++) l = max(l, redi[w]);
-                int act;
+                int act, nbul = 1;
                 if (status != 0 || i <= 0) {
                     act = kActStop;
                     if (status == 0) {
@@ -472,9 +486,9 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
                     const int sw_its = its + 1;
                     double2 sigma;
                     if (sw_its % 10 == 0) {
-                        // ad hoc shift: off the window's top (sweeps 10, 30, ..)
-                        // or bottom corner (20, 40, ..) by 3/4 of a subdiagonal
-                        // entry's real part
+                        // ad hoc shift, one bulge: off the window's top
+                        // (sweeps 10, 30, ..) or bottom corner (20, 40, ..)
+                        // by 3/4 of a subdiagonal entry's real part
                         const bool top = (sw_its / 10) % 2 == 1;
                         const double2 d = top ? ldT(&SGT_A(T, ldt, l, l)) : ldT(&SGT_A(T, ldt, i, i));
                         const double e = top ? ldT(&SGT_A(T, ldt, l + 1, l)).x : ldT(&SGT_A(T, ldt, i, i - 1)).x;
@@ -482,7 +496,8 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
                     } else {
                         // Wilkinson: with x = (a - d) / 2 and y = sqrt(x^2 + bc)
                         // signed so that |x + y| is the larger, the eigenvalue
-                        // of [a b; c d] nearer d is d - bc / (x + y)
+                        // of [a b; c d] nearer d is d - bc / (x + y); the
+                        // other one, a + d minus it, shifts the rear bulge
                         const double2 a = ldT(&SGT_A(T, ldt, i - 1, i - 1)), b = ldT(&SGT_A(T, ldt, i - 1, i));
                         const double2 cc = ldT(&SGT_A(T, ldt, i, i - 1)), d = ldT(&SGT_A(T, ldt, i, i));
                         const double2 x = make_double2(0.5 * (a.x - d.x), 0.5 * (a.y - d.y));
@@ -497,6 +512,10 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
                             const double2 q = cdiv(bc, xy);
                             sigma = make_double2(d.x - q.x, d.y - q.y);
                         }
+                        if (i - l >= 3) {
+                            nbul = 2;
+                            if (lane == 0) sig1 = make_double2(a.x + d.x - sigma.x, a.y + d.y - sigma.y);
+                        }
                     }
                     A = ldT(&SGT_A(T, ldt, l, l));
                     B = ldT(&SGT_A(T, ldt, l, l + 1));
@@ -505,14 +524,15 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
                     Hh = (l + 2 <= i) ? ldT(&SGT_A(T, ldt, l + 2, l + 1)) : zero;
                     pf_f = (l + 2 <= i) ? ldT(&SGT_A(T, ldt, l + 2, l + 2)) : zero;
                     pf_h = (l + 3 <= i) ? ldT(&SGT_A(T, ldt, l + 3, l + 2)) : zero;
-                    double c;
-                    double2 s;
-                    make_rotation_warp(make_double2(A.x - sigma.x, A.y - sigma.y), E, lane, c, s);
-                    put_rotation(l & 1, c, s);
+                    X = make_double2(A.x - sigma.x, A.y - sigma.y);
+                    Y = E;
+                    make_rotation_warp(X, Y, lane, c_cur, s_cur);
+                    put_rotation(0, 0, c_cur, s_cur);
                     if (lane == 0) {
-                        sweeplog[sweeps] = SweepRec{l, i, rot};
-                        rclog[rot] = c;
-                        rslog[rot] = s;
+                        sweeplog[logged] = SweepRec{l, i, rot};
+                        if (nbul == 2) sweeplog[logged + 1] = SweepRec{l, i, rot + (i - l)};
+                        rclog[rot] = c_cur;
+                        rslog[rot] = s_cur;
                     }
                 }
                 if (lane < kQrCluster) {
@@ -520,11 +540,12 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
                     rem[0] = act;
                     rem[1] = l;
                     rem[2] = i;
+                    rem[3] = nbul;
                 }
             }
         }
         cl.sync();
-        const int act = ctl[0], l = ctl[1];
+        const int act = ctl[0], l = ctl[1], nbul = ctl[3];
         i = ctl[2];
         if (act == kActStop) break;
         if (act == kActDeflate) {
@@ -533,102 +554,219 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
             continue;
         }
         its++;
-        sweeps++;
-        for (int k = l; k < i; k++) {
-            const double c = rc[k & 1];
-            const double2 s = rs[k & 1];
+        const int L = i - l, S = L + 3 * (nbul - 1);
+        double2 Fnext = zero;   // rear chief: its block's next corner
+        for (int s = 0; s < S; s++) {
+            const int k0 = l + s, k1 = l + s - 3;
+            const bool a0 = s < L;                    // front bulge at k0
+            const bool a1 = nbul > 1 && s >= 3;       // rear bulge at k1 (s - 3 < L always)
             if (crank > 0) {
-                // entries: the row op's columns jlo..i (the block's two
-                // apart), then the column op's rows 0..k-1; h_{k+1,k+2} also
-                // to the chief warp
-                const int jlo = (k == l) ? l : k - 1;
-                const int wr = i - jlo + 1, wtot = wr + k;
+                const double c0 = rc[0][s & 1], c1 = rc[1][s & 1];
+                const double2 s0 = rs[0][s & 1], s1 = rs[1][s & 1];
+                // items: the 2 x 2 block where the two chases meet (rows
+                // k1, k1+1 x columns k0, k0+1: the rear rotation from the
+                // left, the front one from the right; two items, lanes 0
+                // and 1 of the first warp, one column and then one row each);
+                // front rows k0, k0+1 at columns k0+2..i; front columns k0,
+                // k0+1 at rows 0..k0-1 (the rear rows apart); rear rows at
+                // columns k1+2..i (the front columns apart); rear columns at
+                // rows 0..k1-1
+                const int xn = (a0 && a1) ? 2 : 0;
+                const int r0n = a0 ? max(i - k0 - 1, 0) : 0, c0n = a0 ? k0 : 0;
+                const int r1n = a1 ? max(i - k1 - 1, 0) : 0, c1n = a1 ? k1 : 0;
+                const int wtot = xn + r0n + c0n + r1n + c1n;
                 for (int e = e0; e < wtot; e += kQrWorkerThreads) {
-                    if (e < wr) {
-                        const int j = jlo + e;
-                        if (j == k || j == k + 1) continue;
-                        double2 a = ldT(&SGT_A(T, ldt, k, j)), b = ldT(&SGT_A(T, ldt, k + 1, j));
-                        rot_rows(c, s, a, b);
-                        SGT_A(T, ldt, k, j) = a;
-                        SGT_A(T, ldt, k + 1, j) = (j == k - 1) ? zero : b;   // the old bulge, zeroed
-                        if (j == k + 2) *cl.map_shared_rank(&bslot[(k + 1) & 1], 0) = b;
-                    } else {
-                        const int r = e - wr;
-                        double2 a = ldT(&SGT_A(T, ldt, r, k)), b = ldT(&SGT_A(T, ldt, r, k + 1));
-                        rot_cols(c, s, a, b);
-                        SGT_A(T, ldt, r, k) = a;
-                        SGT_A(T, ldt, r, k + 1) = b;
+                    int f = e;
+                    if (f < xn) {
+                        // lane f: column k0 + f through the rear rotation, then
+                        // row k1 + f through the front one
+                        const int j = k0 + f;
+                        double2 a = ldT(&SGT_A(T, ldt, k1, j)), b = ldT(&SGT_A(T, ldt, k1 + 1, j));
+                        rot_rows(c1, s1, a, b);
+                        // lane 0 holds (row k1, row k1+1) of column k0, lane 1
+                        // of column k0+1; row k1 + f needs both columns
+                        const double2 mine = f ? b : a, theirs = f ? a : b;
+                        const double2 other = make_double2(__shfl_xor_sync(0x3u, theirs.x, 1),
+                                                           __shfl_xor_sync(0x3u, theirs.y, 1));
+                        double2 p = f ? other : mine, q = f ? mine : other;
+                        rot_cols(c0, s0, p, q);
+                        SGT_A(T, ldt, k1 + f, k0) = p;
+                        SGT_A(T, ldt, k1 + f, k0 + 1) = q;
+                        continue;
+                    }
+                    f -= xn;
+                    if (f < r0n) {
+                        const int j = k0 + 2 + f;
+                        double2 a = ldT(&SGT_A(T, ldt, k0, j)), b = ldT(&SGT_A(T, ldt, k0 + 1, j));
+                        rot_rows(c0, s0, a, b);
+                        SGT_A(T, ldt, k0, j) = a;
+                        SGT_A(T, ldt, k0 + 1, j) = b;
+                        if (f == 0) *cl.map_shared_rank(&bslot[0][(s + 1) & 1], 0) = b;
+                        continue;
+                    }
+                    f -= r0n;
+                    if (f < c0n) {
+                        if (a1 && (f == k1 || f == k1 + 1)) continue;
+                        double2 a = ldT(&SGT_A(T, ldt, f, k0)), b = ldT(&SGT_A(T, ldt, f, k0 + 1));
+                        rot_cols(c0, s0, a, b);
+                        SGT_A(T, ldt, f, k0) = a;
+                        SGT_A(T, ldt, f, k0 + 1) = b;
+                        continue;
+                    }
+                    f -= c0n;
+                    if (f < r1n) {
+                        const int j = k1 + 2 + f;
+                        if (a0 && (j == k0 || j == k0 + 1)) continue;
+                        double2 a = ldT(&SGT_A(T, ldt, k1, j)), b = ldT(&SGT_A(T, ldt, k1 + 1, j));
+                        rot_rows(c1, s1, a, b);
+                        SGT_A(T, ldt, k1, j) = a;
+                        SGT_A(T, ldt, k1 + 1, j) = b;
+                        if (f == 0) *cl.map_shared_rank(&bslot[1][(s + 1) & 1], 0) = b;
+                        continue;
+                    }
+                    f -= r1n;
+                    double2 a = ldT(&SGT_A(T, ldt, f, k1)), b = ldT(&SGT_A(T, ldt, f, k1 + 1));
+                    rot_cols(c1, s1, a, b);
+                    SGT_A(T, ldt, f, k1) = a;
+                    SGT_A(T, ldt, f, k1 + 1) = b;
+                }
+            } else if (cb >= 0 && cb < nbul) {
+                const int b = cb;
+                if (b == 1 && s == 2) {
+                    // the rear chase starts next step at (l, l): entries final
+                    // since step 1 (h_{l+2,l+1} comes after this step, from the
+                    // front chief), its first rotation from its own shift
+                    A = ldT(&SGT_A(T, ldt, l, l));
+                    B = ldT(&SGT_A(T, ldt, l, l + 1));
+                    E = ldT(&SGT_A(T, ldt, l + 1, l));
+                    F = ldT(&SGT_A(T, ldt, l + 1, l + 1));
+                    const double2 sg = sig1;
+                    X = make_double2(A.x - sg.x, A.y - sg.y);
+                    Y = E;
+                    make_rotation_warp(X, Y, lane, c_cur, s_cur);
+                    put_rotation(1, 1, c_cur, s_cur);
+                    if (lane == 0) {
+                        rclog[rot + L] = c_cur;
+                        rslog[rot + L] = s_cur;
                     }
                 }
-            } else if (chiefw) {
-                // entries no step writes before step k+1 reads them
-                // (h_{k+2,k+2}, h_{k+3,k+2}), loaded at step k-1; and those
-                // of step k+2
-                const double2 F2 = pf_f, H2 = pf_h;
-                pf_f = (k + 3 <= i) ? ldT(&SGT_A(T, ldt, k + 3, k + 3)) : zero;
-                pf_h = (k + 4 <= i) ? ldT(&SGT_A(T, ldt, k + 4, k + 3)) : zero;
-                // G on the block's columns: lane 4 col + part holds part
-                // (0 top.x, 1 top.y, 2 bottom.x, 3 bottom.y) of column col
-                // (0: (A, E), 1: (B, F)) -- one real output per lane
-                // (operands picked by selects, no branches: all lanes run the
-                // same three float64 instructions)
-                const int part = lane & 3;
-                const bool odd = part & 1, hi = part >= 2;
-                const bool cl1 = (lane >> 2) & 1;
-                const double2 tp = cl1 ? B : A, bt = cl1 ? F : E;
-                const double2 u1 = hi ? bt : tp, v1 = hi ? tp : bt;
-                const double r1 = pair_part(c, odd ? u1.y : u1.x, hi ? -s.x : s.x, odd ? v1.y : v1.x,
-                                            odd ? s.y : -s.y, odd ? v1.x : v1.y);
-                const double2 A1 = make_double2(__shfl_sync(0xffffffffu, r1, 0), __shfl_sync(0xffffffffu, r1, 1));
-                const double2 E1 = make_double2(__shfl_sync(0xffffffffu, r1, 2), __shfl_sync(0xffffffffu, r1, 3));
-                const double2 B1 = make_double2(__shfl_sync(0xffffffffu, r1, 4), __shfl_sync(0xffffffffu, r1, 5));
-                const double2 F1 = make_double2(__shfl_sync(0xffffffffu, r1, 6), __shfl_sync(0xffffffffu, r1, 7));
-                // G^H on the rows k, k+1, k+2: lane 4 row + part holds part
-                // (0 p.x, 1 p.y, 2 q.x, 3 q.y) of row (p, q): (A1, B1),
-                // (E1, F1), (0, Hh)
-                const int row = min(lane >> 2, 2);
-                const double2 pp = row == 0 ? A1 : (row == 1 ? E1 : zero);
-                const double2 qq = row == 0 ? B1 : (row == 1 ? F1 : Hh);
-                const double2 u2 = hi ? qq : pp, v2 = hi ? pp : qq;
-                const double r2 = pair_part(c, odd ? u2.y : u2.x, hi ? -s.x : s.x, odd ? v2.y : v2.x,
-                                            odd ? -s.y : s.y, odd ? v2.x : v2.y);
-                if (lane < 8 || (lane < 12 && k + 2 <= i))
-                    reinterpret_cast<double *>(&SGT_A(T, ldt, k + (lane >> 2), k + (part >> 1)))[part & 1] = r2;
-                if (k + 2 <= i) {
-                    // the next rotation zeroes the bulge h_{k+2,k} (lanes 8, 9)
-                    // against h_{k+1,k} (lanes 4, 5)
-                    const double2 x = make_double2(__shfl_sync(0xffffffffu, r2, 4), __shfl_sync(0xffffffffu, r2, 5));
-                    const double2 y = make_double2(__shfl_sync(0xffffffffu, r2, 8), __shfl_sync(0xffffffffu, r2, 9));
-                    const double2 f1 = make_double2(__shfl_sync(0xffffffffu, r2, 6), __shfl_sync(0xffffffffu, r2, 7));
-                    const double2 h1 = make_double2(__shfl_sync(0xffffffffu, r2, 10), __shfl_sync(0xffffffffu, r2, 11));
-                    double cn;
-                    double2 sn;
-                    make_rotation_warp(x, y, lane, cn, sn);
-                    put_rotation((k + 1) & 1, cn, sn);
-                    if (lane == 0) {
-                        rclog[rot + (k + 1 - l)] = cn;
-                        rslog[rot + (k + 1 - l)] = sn;
+                const bool act_b = (b == 0) ? a0 : a1;
+                if (act_b) {
+                    const int kb = (b == 0) ? k0 : k1;
+                    const double c = c_cur;
+                    const double2 sn = s_cur;
+                    double2 F2 = zero, H2 = zero;
+                    if (b == 0) {
+                        F2 = pf_f;
+                        H2 = pf_h;
+                        pf_f = (kb + 3 <= i) ? ldT(&SGT_A(T, ldt, kb + 3, kb + 3)) : zero;
+                        pf_h = (kb + 4 <= i) ? ldT(&SGT_A(T, ldt, kb + 4, kb + 3)) : zero;
+                    } else if (kb + 2 <= i) {
+                        // the next corner h_{k+2,k+2}: the front chief's block
+                        // corner of the previous step, or T once that chase ended
+                        Fnext = (s - 1 < L) ? handF[(s - 1) & 1] : ldT(&SGT_A(T, ldt, kb + 2, kb + 2));
                     }
-                    // the block at (k+1, k+1): (h_{k+1,k+1}, h_{k+1,k+2};
-                    // h_{k+2,k+1}, h_{k+2,k+2}), h_{k+1,k+2} from bslot after
-                    // the barrier
-                    A = f1;
-                    E = h1;
-                    F = F2;
-                    Hh = H2;
+                    const int part = lane & 3;
+                    const bool odd = part & 1, hi = part >= 2;
+                    if (kb > l) {
+                        // h_{k,k-1} = c X + s Y (the entry the rotation keeps),
+                        // h_{k+1,k-1} = 0 (the bulge it zeroes): lanes 0-3
+                        const double rz = pair_part(c, odd ? X.y : X.x, sn.x, odd ? Y.y : Y.x, odd ? sn.y : -sn.y,
+                                                    odd ? Y.x : Y.y);
+                        if (lane < 4)
+                            reinterpret_cast<double *>(&SGT_A(T, ldt, kb + (hi ? 1 : 0), kb - 1))[odd ? 1 : 0] =
+                                hi ? 0.0 : rz;
+                        if (b == 0) {
+                            const double2 r = make_double2(__shfl_sync(0xffffffffu, rz, 0),
+                                                           __shfl_sync(0xffffffffu, rz, 1));
+                            if (lane == 0) handH[s & 1] = r;
+                        }
+                    }
+                    // G on the block's columns: lane 4 col + part holds part
+                    // (0 top.x, 1 top.y, 2 bottom.x, 3 bottom.y) of column col
+                    // (0: (A, E), 1: (B, F)) -- one real output per lane
+                    // (operands picked by selects, no branches: all lanes run
+                    // the same three float64 instructions)
+                    const bool cl1 = (lane >> 2) & 1;
+                    const double2 tp = cl1 ? B : A, bt = cl1 ? F : E;
+                    const double2 u1 = hi ? bt : tp, v1 = hi ? tp : bt;
+                    const double r1 = pair_part(c, odd ? u1.y : u1.x, hi ? -sn.x : sn.x, odd ? v1.y : v1.x,
+                                                odd ? sn.y : -sn.y, odd ? v1.x : v1.y);
+                    const double2 A1 = make_double2(__shfl_sync(0xffffffffu, r1, 0), __shfl_sync(0xffffffffu, r1, 1));
+                    const double2 E1 = make_double2(__shfl_sync(0xffffffffu, r1, 2), __shfl_sync(0xffffffffu, r1, 3));
+                    const double2 B1 = make_double2(__shfl_sync(0xffffffffu, r1, 4), __shfl_sync(0xffffffffu, r1, 5));
+                    const double2 F1 = make_double2(__shfl_sync(0xffffffffu, r1, 6), __shfl_sync(0xffffffffu, r1, 7));
+                    // G^H on the rows k, k+1, k+2: lane 4 row + part holds part
+                    // (0 p.x, 1 p.y, 2 q.x, 3 q.y) of row (p, q): (A1, B1),
+                    // (E1, F1), (0, Hh)
+                    const int row = min(lane >> 2, 2);
+                    const double2 pp = row == 0 ? A1 : (row == 1 ? E1 : zero);
+                    const double2 qq = row == 0 ? B1 : (row == 1 ? F1 : Hh);
+                    const double2 u2 = hi ? qq : pp, v2 = hi ? pp : qq;
+                    const double r2 = pair_part(c, odd ? u2.y : u2.x, hi ? -sn.x : sn.x, odd ? v2.y : v2.x,
+                                                odd ? -sn.y : sn.y, odd ? v2.x : v2.y);
+                    if (lane < 8 || (lane < 12 && kb + 2 <= i))
+                        reinterpret_cast<double *>(&SGT_A(T, ldt, kb + (lane >> 2), kb + (part >> 1)))[part & 1] = r2;
+                    if (b == 0) {
+                        // the block's corner h_kk, for the rear chief two steps on
+                        const double2 corner = make_double2(__shfl_sync(0xffffffffu, r2, 0),
+                                                            __shfl_sync(0xffffffffu, r2, 1));
+                        if (lane == 0) handF[s & 1] = corner;
+                    }
+                    if (kb + 2 <= i) {
+                        // the next rotation zeroes the bulge h_{k+2,k} (lanes 8, 9)
+                        // against h_{k+1,k} (lanes 4, 5)
+                        const double2 x = make_double2(__shfl_sync(0xffffffffu, r2, 4), __shfl_sync(0xffffffffu, r2, 5));
+                        const double2 y = make_double2(__shfl_sync(0xffffffffu, r2, 8), __shfl_sync(0xffffffffu, r2, 9));
+                        const double2 f1 = make_double2(__shfl_sync(0xffffffffu, r2, 6), __shfl_sync(0xffffffffu, r2, 7));
+                        const double2 h1 = make_double2(__shfl_sync(0xffffffffu, r2, 10), __shfl_sync(0xffffffffu, r2, 11));
+                        make_rotation_warp(x, y, lane, c_cur, s_cur);
+                        put_rotation(b, (s + 1) & 1, c_cur, s_cur);
+                        if (lane == 0) {
+                            const long long at = rot + (long long)b * L + (kb + 1 - l);
+                            rclog[at] = c_cur;
+                            rslog[at] = s_cur;
+                        }
+                        X = x;
+                        Y = y;
+                        // the block at (k+1, k+1): (h_{k+1,k+1}, h_{k+1,k+2};
+                        // h_{k+2,k+1}, h_{k+2,k+2}), h_{k+1,k+2} from bslot after
+                        // the barrier, and h_{k+3,k+2}
+                        A = f1;
+                        E = h1;
+                        F = (b == 0) ? F2 : Fnext;
+                        if (b == 0) Hh = H2;
+                    }
                 }
             }
             cl.sync();
-            if (chiefw && k + 1 < i) B = bslot[(k + 1) & 1];
+            if (cb >= 0 && cb < nbul) {
+                const int b = cb;
+                const bool act_b = (b == 0) ? a0 : a1;
+                const int kb = (b == 0) ? k0 : k1;
+                if (act_b && kb + 1 < i) B = bslot[b][(s + 1) & 1];
+                if (b == 1) {
+                    if (s == 2) {
+                        Hh = (l + 2 <= i) ? handH[0] : zero;   // the front chief's h_{l+2,l+1} of step 2
+                    } else if (a1 && kb + 3 <= i) {
+                        // h_{k+3,k+2} for the next step: the front chief's
+                        // left entry of this step, or T once that chase ended
+                        Hh = a0 ? handH[s & 1] : ldT(&SGT_A(T, ldt, kb + 3, kb + 2));
+                    } else if (a1) {
+                        Hh = zero;
+                    }
+                }
+            }
         }
-        rot += i - l;
+        rot += (long long)nbul * L;
+        logged += nbul;
     }
-    if (chief) {
+    if (chief0 && lane == 0) {
         st->ihi = i;
         st->its = its;
         st->status = status;
-        st->logged = (int)sweeps;
-        st->sweeps += sweeps;
+        st->logged = (int)logged;
+        st->sweeps += logged;
         st->rotations += rot;
     }
 }
@@ -698,7 +836,7 @@ size_t schur_workspace_bytes(int n)
     if (n <= 0) return 0;
     // ten takes, each rounded up to 256 bytes; the logs hold one launch
     const size_t nn = (size_t)n * n;
-    const size_t nlog = (size_t)kRotationBudget + (size_t)n + 1;
+    const size_t nlog = (size_t)kRotationBudget + (size_t)kMaxBulges * n + 2;
     return 2 * nn * sizeof(double) + 3 * (size_t)n * sizeof(double) + sizeof(double) + sizeof(int) + sizeof(QrState) +
            nlog * (sizeof(SweepRec) + sizeof(double) + sizeof(double2)) + 10 * 256;
 }
@@ -715,9 +853,10 @@ signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, do
     auto *tau = static_cast<double *>(ws.take(sizeof(double)));
     auto *bad = static_cast<int *>(ws.take(sizeof(int)));
     auto *qs = static_cast<QrState *>(ws.take(sizeof(QrState)));
-    // a launch logs fewer than budget + n rotations (it starts a sweep only
-    // below the budget, a sweep has at most n - 1) and no more sweeps
-    const size_t nlog = (size_t)kRotationBudget + (size_t)n + 1;
+    // a launch logs fewer than budget + 2n rotations (it starts a multi-sweep
+    // only below the budget, a multi-sweep has at most 2 (n - 1)) and no
+    // more sweeps
+    const size_t nlog = (size_t)kRotationBudget + (size_t)kMaxBulges * n + 2;
     auto *sweeplog = static_cast<SweepRec *>(ws.take(nlog * sizeof(SweepRec)));
     auto *rclog = static_cast<double *>(ws.take(nlog * sizeof(double)));
     auto *rslog = static_cast<double2 *>(ws.take(nlog * sizeof(double2)));
