@@ -28,9 +28,10 @@
 //     what the one before wrote), so one 8-CTA cluster runs the sweeps with a
 //     cluster barrier per rotation, applying each to the active window only
 //     (schur_qr_kernel says how the work is split); a launch runs sweeps
-//     until a rotation budget is spent and logs them, then a kernel on every
-//     SM applies the logged rotations to the columns right of each sweep's
-//     window and to Q, and the host relaunches until the window is empty.
+//     until a rotation budget is spent and logs them, then a kernel on the
+//     other SMs applies the logged rotations to the columns right of each
+//     sweep's window and to Q, on a second stream while the next launch
+//     runs, and the host relaunches until the window is empty.
 //     The chain of rotations bounds the stage: about 3 sweeps per eigenvalue,
 //     ~1.25 n^2 rotations for n eigenvalues, each a few thousand cycles of
 //     float64 latency and a barrier -- the decomposition is the
@@ -292,7 +293,6 @@ struct QrState {
     int ihi;          // last row of the active window (-1: all converged)
     int its;          // sweeps since the last deflation
     int status;       // 0 running, 1 converged, 2 no convergence
-    int logged;       // sweeps in the log of the last launch
     long long sweeps;
     long long rotations;
 };
@@ -309,7 +309,6 @@ __global__ void qr_state_init_kernel(int n, QrState *st)
     st->ihi = n - 1;
     st->its = 0;
     st->status = 0;
-    st->logged = 0;
     st->sweeps = 0;
     st->rotations = 0;
 }
@@ -353,8 +352,9 @@ __global__ void qr_state_init_kernel(int n, QrState *st)
 // L2-only loads (another CTA may have written it since).  The rotations'
 // action on the columns right of the window (rows there are never read by a
 // later sweep: the window only shrinks) and on Q is left to
-// apply_rotations_kernel, which runs on every SM: this kernel logs each sweep
-// and its rotations instead (the rear sweep after the front one).
+// apply_rotations_kernel, which runs on other SMs alongside the next launch:
+// this kernel logs each sweep and its rotations instead (the rear sweep after
+// the front one).
 constexpr int kQrCluster = 8;
 constexpr int kQrWorkers = kQrCluster - 1;                       // CTAs 1..
 constexpr int kQrWorkerThreads = kQrWorkers * kQrThreads;
@@ -415,7 +415,8 @@ __device__ __forceinline__ double pair_part(double c, double alpha, double beta,
 
 __global__ void __cluster_dims__(kQrCluster, 1, 1) __launch_bounds__(kQrThreads)
 schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ st, long long budget,
-                SweepRec *__restrict__ sweeplog, double *__restrict__ rclog, double2 *__restrict__ rslog)
+                SweepRec *__restrict__ sweeplog, double *__restrict__ rclog, double2 *__restrict__ rslog,
+                int *__restrict__ nlogged)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -765,7 +766,7 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
         st->ihi = i;
         st->its = its;
         st->status = status;
-        st->logged = (int)logged;
+        *nlogged = (int)logged;
         st->sweeps += logged;
         st->rotations += rot;
     }
@@ -781,7 +782,7 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
 // memory, bounds this kernel), the carried entry passed by shuffles; the
 // next entry is loaded an iteration ahead.
 __global__ void apply_rotations_kernel(int n, double2 *__restrict__ T, int ldt, double2 *__restrict__ Q, int ldq,
-                                       const QrState *__restrict__ st, const SweepRec *__restrict__ sweeplog,
+                                       const int *__restrict__ nlogged, const SweepRec *__restrict__ sweeplog,
                                        const double *__restrict__ rclog, const double2 *__restrict__ rslog)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -793,7 +794,7 @@ __global__ void apply_rotations_kernel(int n, double2 *__restrict__ T, int ldt, 
     // entry k of the unit's line: T(k, j) (stride 1) or Q(r, k) (stride ldq)
     double2 *line = isT ? &SGT_A(T, ldt, 0, unit) : &SGT_A(Q, ldq, unit - n, 0);
     const size_t stride = isT ? 1 : (size_t)ldq;
-    const int logged = st->logged;
+    const int logged = *nlogged;
     for (int w = 0; w < logged; w++) {
         const SweepRec sr = sweeplog[w];
         if (isT && unit <= sr.i) continue;
@@ -831,14 +832,46 @@ __global__ void real_part_kernel(int n, const double2 *__restrict__ Sc, double *
 
 }  // namespace
 
+namespace {
+
+// The second stream of schur_run and its events.  Destroyed on every
+// return, after the stream's work has finished (the caller may reuse the
+// workspace the applies read and write as soon as schur_run returns).
+struct ApplyStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t swept[2] = {}, applied[2] = {};
+    cudaError_t init()
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        for (int p = 0; p < 2 && e == cudaSuccess; p++) {
+            e = cudaEventCreateWithFlags(&swept[p], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&applied[p], cudaEventDisableTiming);
+        }
+        return e;
+    }
+    ~ApplyStream()
+    {
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+        for (int p = 0; p < 2; p++) {
+            if (swept[p]) cudaEventDestroy(swept[p]);
+            if (applied[p]) cudaEventDestroy(applied[p]);
+        }
+    }
+};
+
+}  // namespace
+
 size_t schur_workspace_bytes(int n)
 {
     if (n <= 0) return 0;
-    // ten takes, each rounded up to 256 bytes; the logs hold one launch
+    // eleven takes, each rounded up to 256 bytes; two logs of one launch each
     const size_t nn = (size_t)n * n;
     const size_t nlog = (size_t)kRotationBudget + (size_t)kMaxBulges * n + 2;
     return 2 * nn * sizeof(double) + 3 * (size_t)n * sizeof(double) + sizeof(double) + sizeof(int) + sizeof(QrState) +
-           nlog * (sizeof(SweepRec) + sizeof(double) + sizeof(double2)) + 10 * 256;
+           2 * nlog * (sizeof(SweepRec) + sizeof(double) + sizeof(double2)) + 2 * sizeof(int) + 11 * 256;
 }
 
 signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, double *T, int ldt, Arena &ws,
@@ -855,12 +888,14 @@ signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, do
     auto *qs = static_cast<QrState *>(ws.take(sizeof(QrState)));
     // a launch logs fewer than budget + 2n rotations (it starts a multi-sweep
     // only below the budget, a multi-sweep has at most 2 (n - 1)) and no
-    // more sweeps
+    // more sweeps; launches alternate between two logs
     const size_t nlog = (size_t)kRotationBudget + (size_t)kMaxBulges * n + 2;
-    auto *sweeplog = static_cast<SweepRec *>(ws.take(nlog * sizeof(SweepRec)));
-    auto *rclog = static_cast<double *>(ws.take(nlog * sizeof(double)));
-    auto *rslog = static_cast<double2 *>(ws.take(nlog * sizeof(double2)));
-    if (!H || !Q0 || !v || !y || !tau || !bad || !qs || !sweeplog || !rclog || !rslog) return SIGNTRI_ERR_NO_WORKSPACE;
+    auto *sweeplog = static_cast<SweepRec *>(ws.take(2 * nlog * sizeof(SweepRec)));
+    auto *rclog = static_cast<double *>(ws.take(2 * nlog * sizeof(double)));
+    auto *rslog = static_cast<double2 *>(ws.take(2 * nlog * sizeof(double2)));
+    auto *nlogged = static_cast<int *>(ws.take(2 * sizeof(int)));
+    if (!H || !Q0 || !v || !y || !tau || !bad || !qs || !sweeplog || !rclog || !rslog || !nlogged)
+        return SIGNTRI_ERR_NO_WORKSPACE;
     const int big = INT_MAX;
     SGT_CUDA_TRY(cudaMemcpyAsync(bad, &big, sizeof(int), cudaMemcpyHostToDevice, st));
     {
@@ -901,27 +936,44 @@ signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, do
         qr_state_init_kernel<<<1, 1, 0, st>>>(n, qs);
         SGT_LAUNCH_CHECK();
     }
-    // relaunch until converged; a bound on the launches for safety (each
-    // launch runs at least one sweep or one deflation while status is 0)
+    // Relaunch until converged; a bound on the launches for safety (each
+    // launch runs at least one sweep or one deflation while status is 0).
+    // Launch m's rotations are applied on a second stream while launch m + 1
+    // runs: the two touch disjoint entries (launch m + 1 stays in the
+    // columns up to its window's last row i, which is where launch m ended;
+    // the applies act on columns right of each logged sweep's window, which
+    // ended at i or further down, and alone on Q), and launch m + 2 writes
+    // launch m's log only after its apply.
+    ApplyStream ap;
+    SGT_CUDA_TRY(ap.init());
     QrState h{};
     const long long max_launches = 4LL * n * kMaxSweepsPerEigenvalue + 16;
     for (long long it = 0;; it++) {
         if (it >= max_launches) return SIGNTRI_ERR_NO_CONVERGENCE;
+        const int p = (int)(it & 1);
+        const size_t lo = p * nlog;
+        if (it >= 2) SGT_CUDA_TRY(cudaStreamWaitEvent(st, ap.applied[p], 0));
         {
-            ProfScope ps(SIGNTRI_KC_SCHUR, st, true, false);
-            prof_count(SIGNTRI_KC_SCHUR, 2);
-            schur_qr_kernel<<<kQrCluster, kQrThreads, 0, st>>>(n, Tc, ldt, qs, kRotationBudget, sweeplog, rclog,
-                                                                rslog);
-            SGT_LAUNCH_CHECK();
-            apply_rotations_kernel<<<(8 * n + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, Tc, ldt, Qc, ldq, qs,
-                                                                                        sweeplog, rclog, rslog);
+            ProfScope ps(SIGNTRI_KC_SCHUR, st);
+            schur_qr_kernel<<<kQrCluster, kQrThreads, 0, st>>>(n, Tc, ldt, qs, kRotationBudget, sweeplog + lo,
+                                                                rclog + lo, rslog + lo, nlogged + p);
             SGT_LAUNCH_CHECK();
         }
+        SGT_CUDA_TRY(cudaEventRecord(ap.swept[p], st));
+        SGT_CUDA_TRY(cudaStreamWaitEvent(ap.s, ap.swept[p], 0));
+        {
+            ProfScope ps(SIGNTRI_KC_SCHUR, ap.s);
+            apply_rotations_kernel<<<(8 * n + kThreads - 1) / kThreads, kThreads, 0, ap.s>>>(
+                n, Tc, ldt, Qc, ldq, nlogged + p, sweeplog + lo, rclog + lo, rslog + lo);
+            SGT_LAUNCH_CHECK();
+        }
+        SGT_CUDA_TRY(cudaEventRecord(ap.applied[p], ap.s));
         SGT_CUDA_TRY(cudaMemcpyAsync(&h, qs, sizeof(QrState), cudaMemcpyDeviceToHost, st));
         SGT_CUDA_TRY(cudaStreamSynchronize(st));
         if (h.status == 1) break;
         if (h.status == 2) return SIGNTRI_ERR_NO_CONVERGENCE;
     }
+    SGT_CUDA_TRY(cudaStreamSynchronize(ap.s));
     if (sweeps_out) *sweeps_out = h.sweeps;
     {
         ProfScope ps(SIGNTRI_KC_FILL, st);
