@@ -25,8 +25,9 @@
 //     |h_{k,k-1}| <= eps (|h_{k-1,k-1}| + |h_kk|) (|z| = |Re z| + |Im z|).
 //     Deflation takes the window's last row when its subdiagonal entry is
 //     negligible.  The rotations of a sweep depend on one another (each reads
-//     what the one before wrote), so one 8-CTA cluster runs the sweeps with a
-//     cluster barrier per rotation, applying each to the active window only
+//     what the one before wrote), so one cluster of 16 CTAs (8 where the
+//     device cannot place 16) runs the sweeps with a cluster barrier per
+//     rotation or rotation pair, applying each to the active window only
 //     (schur_qr_kernel says how the work is split); a launch runs sweeps
 //     until a rotation budget is spent and logs them, then a kernel on the
 //     other SMs applies the logged rotations to the columns right of each
@@ -313,7 +314,7 @@ __global__ void qr_state_init_kernel(int n, QrState *st)
     st->rotations = 0;
 }
 
-// One cluster of kQrCluster CTAs runs the sweeps, one or two bulges at a time.
+// One cluster of CL CTAs runs the sweeps, one or two bulges at a time.
 // Two bulges: both eigenvalues of the window's trailing 2 x 2 as shifts
 // (Francis's double shift, in complex arithmetic as two single shifts), the
 // second bulge started 3 steps behind the first; mathematically the two
@@ -355,9 +356,6 @@ __global__ void qr_state_init_kernel(int n, QrState *st)
 // apply_rotations_kernel, which runs on other SMs alongside the next launch:
 // this kernel logs each sweep and its rotations instead (the rear sweep after
 // the front one).
-constexpr int kQrCluster = 8;
-constexpr int kQrWorkers = kQrCluster - 1;                       // CTAs 1..
-constexpr int kQrWorkerThreads = kQrWorkers * kQrThreads;
 constexpr int kMaxBulges = 2;
 enum { kActSweep = 0, kActDeflate = 1, kActStop = 2 };
 
@@ -413,12 +411,14 @@ __device__ __forceinline__ double pair_part(double c, double alpha, double beta,
     return fma(c, alpha, fma(beta, gamma, delta * epsilon));
 }
 
-__global__ void __cluster_dims__(kQrCluster, 1, 1) __launch_bounds__(kQrThreads)
+template <int CL>
+__global__ void __launch_bounds__(kQrThreads)
 schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ st, long long budget,
                 SweepRec *__restrict__ sweeplog, double *__restrict__ rclog, double2 *__restrict__ rslog,
                 int *__restrict__ nlogged)
 {
     namespace cg = cooperative_groups;
+    constexpr int kWorkers = CL - 1, kWorkerThreads = kWorkers * kQrThreads;   // CTAs 1..
     cg::cluster_group cl = cg::this_cluster();
     __shared__ int redi[kQrThreads / 32];
     __shared__ double rc[kMaxBulges][2];
@@ -432,7 +432,7 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
     const int cb = (crank == 0 && warp < kMaxBulges) ? warp : -1;   // the bulge of a chief warp
     const bool chief0 = crank == 0 && warp == 0;
     // this worker thread's first entry and the stride (CTAs 1.. only)
-    const int e0 = ((warp * kQrWorkers + ((int)crank - 1)) << 5) + lane;
+    const int e0 = ((warp * kWorkers + ((int)crank - 1)) << 5) + lane;
     int i = st->ihi, its = st->its, status = st->status;
     long long logged = 0, rot = 0;
     const double eps = DBL_EPSILON;
@@ -445,8 +445,8 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
     double c_cur = 1.0;
     double2 pf_f = zero, pf_h = zero;   // front chase: h_{k+2,k+2}, h_{k+3,k+2} for step k+1, loaded early
     auto put_rotation = [&](int b, int slot, double c, double2 s) {
-        // lanes 0..kQrCluster-1 of a chief warp store into CTA `lane`
-        if (lane < kQrCluster) {
+        // lanes 0..CL-1 of a chief warp store into CTA `lane`
+        if (lane < CL) {
             *cl.map_shared_rank(&rc[b][slot], lane) = c;
             *cl.map_shared_rank(&rs[b][slot], lane) = s;
         }
@@ -536,7 +536,7 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
                         rslog[rot] = s_cur;
                     }
                 }
-                if (lane < kQrCluster) {
+                if (lane < CL) {
                     int *rem = cl.map_shared_rank(ctl, lane);
                     rem[0] = act;
                     rem[1] = l;
@@ -576,7 +576,7 @@ schur_qr_kernel(int n, double2 *__restrict__ T, int ldt, QrState *__restrict__ s
                 const int r0n = a0 ? max(i - k0 - 1, 0) : 0, c0n = a0 ? k0 : 0;
                 const int r1n = a1 ? max(i - k1 - 1, 0) : 0, c1n = a1 ? k1 : 0;
                 const int wtot = xn + r0n + c0n + r1n + c1n;
-                for (int e = e0; e < wtot; e += kQrWorkerThreads) {
+                for (int e = e0; e < wtot; e += kWorkerThreads) {
                     int f = e;
                     if (f < xn) {
                         // lane f: column k0 + f through the rear rotation, then
@@ -834,6 +834,53 @@ __global__ void real_part_kernel(int n, const double2 *__restrict__ Sc, double *
 
 namespace {
 
+// The QR sweeps' cluster: 16 CTAs (a non-portable size: 15 worker CTAs
+// halve the float64 work of each step's row and column updates, which the
+// worker SMs' float64 pipes bound) where the device can place such a cluster
+// of the kernel, else 8.
+cudaLaunchConfig_t qr_config(int cl, cudaStream_t st, cudaLaunchAttribute *at)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl, 1, 1);
+    cfg.blockDim = dim3(kQrThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+int qr_cluster_size()
+{
+    if (cudaFuncSetAttribute(schur_qr_kernel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 8;
+    }
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = qr_config(16, nullptr, at);
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, schur_qr_kernel<16>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 8;
+    }
+    return clusters >= 1 ? 16 : 8;
+}
+
+cudaError_t launch_qr(int cl, int n, double2 *T, int ldt, QrState *st, long long budget, SweepRec *sweeplog,
+                      double *rclog, double2 *rslog, int *nlogged, cudaStream_t stream)
+{
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = qr_config(cl, stream, at);
+    return cl == 16 ? cudaLaunchKernelEx(&cfg, schur_qr_kernel<16>, n, T, ldt, st, budget, sweeplog, rclog, rslog,
+                                         nlogged)
+                    : cudaLaunchKernelEx(&cfg, schur_qr_kernel<8>, n, T, ldt, st, budget, sweeplog, rclog, rslog,
+                                         nlogged);
+}
+
 // The second stream of schur_run and its events.  Destroyed on every
 // return, after the stream's work has finished (the caller may reuse the
 // workspace the applies read and write as soon as schur_run returns).
@@ -944,8 +991,23 @@ signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, do
     // the applies act on columns right of each logged sweep's window, which
     // ended at i or further down, and alone on Q), and launch m + 2 writes
     // launch m's log only after its apply.
+    // Each launch's applies are issued after the next QR launch, so that the
+    // cluster finds its SMs free (a QR CTA takes a whole SM's registers).
     ApplyStream ap;
     SGT_CUDA_TRY(ap.init());
+    const int qr_cl = qr_cluster_size();
+    auto apply = [&](int p) -> signtri_status {
+        const size_t lo = p * nlog;
+        SGT_CUDA_TRY(cudaStreamWaitEvent(ap.s, ap.swept[p], 0));
+        {
+            ProfScope ps(SIGNTRI_KC_SCHUR, ap.s);
+            apply_rotations_kernel<<<(8 * n + kThreads - 1) / kThreads, kThreads, 0, ap.s>>>(
+                n, Tc, ldt, Qc, ldq, nlogged + p, sweeplog + lo, rclog + lo, rslog + lo);
+            SGT_LAUNCH_CHECK();
+        }
+        SGT_CUDA_TRY(cudaEventRecord(ap.applied[p], ap.s));
+        return SIGNTRI_OK;
+    };
     QrState h{};
     const long long max_launches = 4LL * n * kMaxSweepsPerEigenvalue + 16;
     for (long long it = 0;; it++) {
@@ -955,23 +1017,22 @@ signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, do
         if (it >= 2) SGT_CUDA_TRY(cudaStreamWaitEvent(st, ap.applied[p], 0));
         {
             ProfScope ps(SIGNTRI_KC_SCHUR, st);
-            schur_qr_kernel<<<kQrCluster, kQrThreads, 0, st>>>(n, Tc, ldt, qs, kRotationBudget, sweeplog + lo,
-                                                                rclog + lo, rslog + lo, nlogged + p);
-            SGT_LAUNCH_CHECK();
+            SGT_CUDA_TRY(launch_qr(qr_cl, n, Tc, ldt, qs, kRotationBudget, sweeplog + lo, rclog + lo, rslog + lo,
+                                   nlogged + p, st));
         }
         SGT_CUDA_TRY(cudaEventRecord(ap.swept[p], st));
-        SGT_CUDA_TRY(cudaStreamWaitEvent(ap.s, ap.swept[p], 0));
-        {
-            ProfScope ps(SIGNTRI_KC_SCHUR, ap.s);
-            apply_rotations_kernel<<<(8 * n + kThreads - 1) / kThreads, kThreads, 0, ap.s>>>(
-                n, Tc, ldt, Qc, ldq, nlogged + p, sweeplog + lo, rclog + lo, rslog + lo);
-            SGT_LAUNCH_CHECK();
+        if (it >= 1) {
+            const signtri_status ra = apply(1 - p);
+            if (ra != SIGNTRI_OK) return ra;
         }
-        SGT_CUDA_TRY(cudaEventRecord(ap.applied[p], ap.s));
         SGT_CUDA_TRY(cudaMemcpyAsync(&h, qs, sizeof(QrState), cudaMemcpyDeviceToHost, st));
         SGT_CUDA_TRY(cudaStreamSynchronize(st));
-        if (h.status == 1) break;
         if (h.status == 2) return SIGNTRI_ERR_NO_CONVERGENCE;
+        if (h.status == 1) {
+            const signtri_status ra = apply(p);
+            if (ra != SIGNTRI_OK) return ra;
+            break;
+        }
     }
     SGT_CUDA_TRY(cudaStreamSynchronize(ap.s));
     if (sweeps_out) *sweeps_out = h.sweeps;
