@@ -312,8 +312,13 @@ size_t signtri_complex_workspace_bytes(int n);
    (strictly lower part written 0), both complex as above (interleaved
    (re, im) float64, column-major, ld in complex elements); the diagonal of
    T holds the eigenvalues in no particular order.  The QR sweeps run on
-   one CTA (a barrier per plane rotation): the front end for a general A,
-   not a tuned path.  signtri_sign_general: S = sign(A) for real A, real
+   one thread-block cluster of 16 CTAs (8 where the device cannot place 16),
+   two bulges per sweep and a cluster barrier per pair of plane rotations;
+   the logged rotations reach the rest of T and Q on a second stream, which
+   the call creates and destroys, while the next sweeps run.  The sweeps are
+   a serial chain: on one GB300, sign(A) by this route takes about as long
+   at n = 2048 as the same route on the host through LAPACK's Schur form,
+   and longer below.  signtri_sign_general: S = sign(A) for real A, real
    n x n (device, column-major): signtri_schur, the complex sign of T
    (signtri_sign_tri_complex), Q U Q^H (as signtri_sign_schur_complex), and
    the real part (A real makes sign(A) real; the imaginary part left is
