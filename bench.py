@@ -383,6 +383,7 @@ def run_general(args):
         launches += cnt
         if cnt:
             per_class[st.signtri_kernel_class_name(c)] = {"launches": cnt, "device_ms": dms / max(args.steps, 1)}
+    info = st.signtri_get_info()   # the last solve's QR sweeps and rotations
     S = st.to_numpy(St)
     line = {
         "metric": "sign(A) of a general real A: solves per second", "value": 1e3 / ms, "unit": "solves/s",
@@ -391,6 +392,7 @@ def run_general(args):
         "config": {"workload": "sign(A), A %d x %d, entries uniform in [-50, 50], seed 0" % (n, n)},
         "gpu_launches": launches, "kernel_time_ms_per_solve": per_class, "clocks": clk,
         "involution_residual": float(np.linalg.norm(S @ S - np.eye(n)) / np.linalg.norm(S) ** 2),
+        "qr": {"sweeps": info.qr_sweeps, "rotations": info.qr_rotations},
     }
     if not args.no_cpu_baseline:
         # the oracle's route (LAPACK's Schur form, the oracle's complex sign and

@@ -130,6 +130,9 @@ typedef struct {
                                (mixed variants; see signtri_set_verification) */
     double resid_involution;/* ||U^2-I||_F / ||U||_F^2 after the last step */
     int bad_index;          /* first offending diagonal index on ZERO/NONFINITE, else -1 */
+    long long qr_sweeps;    /* signtri_schur, signtri_sign_general: QR sweeps run (each
+                               bulge's sweep counted; 0 for the other calls) */
+    long long qr_rotations; /* plane rotations those sweeps applied */
 } signtri_info;
 
 /* Human-readable name of a status code (static string, never NULL). */

@@ -884,8 +884,10 @@ signtri_status signtri_schur(int n, const double *A, int lda, double *Q, int ldq
     if (rs != SIGNTRI_OK) return rs;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int bad = -1;
-    long long sweeps = 0;
-    rs = schur_run(n, A, lda, Q, ldq, T, ldt, ws, &bad, &sweeps, st);
+    long long counts[2] = {0, 0};
+    rs = schur_run(n, A, lda, Q, ldq, T, ldt, ws, &bad, counts, st);
+    g_info.qr_sweeps = counts[0];
+    g_info.qr_rotations = counts[1];
     if (rs == SIGNTRI_ERR_NONFINITE) g_info.bad_index = bad;
     if (rs != SIGNTRI_OK) return rs;
     SGT_CUDA_TRY(cudaStreamSynchronize(st));
@@ -909,8 +911,10 @@ signtri_status signtri_sign_general(int n, const double *A, int lda, double *S, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     SGT_CUDA_TRY(cudaMemsetAsync(s->err_dev, 0, sizeof(int), st));
     int bad = -1;
-    long long sweeps = 0;
-    rs = sign_general_run(n, A, lda, S, lds, ws, s->err_dev, &bad, &sweeps, st);
+    long long counts[2] = {0, 0};
+    rs = sign_general_run(n, A, lda, S, lds, ws, s->err_dev, &bad, counts, st);
+    g_info.qr_sweeps = counts[0];
+    g_info.qr_rotations = counts[1];
     if (rs == SIGNTRI_ERR_ZERO_EIGENVALUE || rs == SIGNTRI_ERR_NONFINITE) g_info.bad_index = bad;
     if (rs != SIGNTRI_OK) return rs;
     SGT_CUDA_TRY(cudaMemcpyAsync(s->err_host, s->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -202,14 +202,14 @@ signtri_status complex_schur_run(int n, const double *Q, int ldq, const double *
 
 // Complex Schur decomposition of a real A and sign(A) through it (schur.cu).
 // Q, T complex as above; bad_index: the first column of A holding a
-// non-finite entry (NONFINITE), or as complex_sign_run; sweeps_out: QR
-// sweeps run.
+// non-finite entry (NONFINITE), or as complex_sign_run; counts_out (may be
+// null): the QR sweeps run and the plane rotations they applied.
 size_t schur_workspace_bytes(int n);
 signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, double *T, int ldt, Arena &ws,
-                         int *bad_index, long long *sweeps_out, cudaStream_t st);
+                         int *bad_index, long long counts_out[2], cudaStream_t st);
 size_t sign_general_workspace_bytes(int n);
 signtri_status sign_general_run(int n, const double *A, int lda, double *S, int lds, Arena &ws, int *d_err,
-                                int *bad_index, long long *sweeps_out, cudaStream_t st);
+                                int *bad_index, long long counts_out[2], cudaStream_t st);
 
 // Mixed precision with refinement (mixed.cu)
 struct MixedParams {

@@ -922,7 +922,7 @@ size_t schur_workspace_bytes(int n)
 }
 
 signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, double *T, int ldt, Arena &ws,
-                         int *bad_index, long long *sweeps_out, cudaStream_t st)
+                         int *bad_index, long long counts_out[2], cudaStream_t st)
 {
     if (n <= 0) return SIGNTRI_OK;
     const size_t nn = (size_t)n * n;
@@ -1035,7 +1035,10 @@ signtri_status schur_run(int n, const double *A, int lda, double *Q, int ldq, do
         }
     }
     SGT_CUDA_TRY(cudaStreamSynchronize(ap.s));
-    if (sweeps_out) *sweeps_out = h.sweeps;
+    if (counts_out) {
+        counts_out[0] = h.sweeps;
+        counts_out[1] = h.rotations;
+    }
     {
         ProfScope ps(SIGNTRI_KC_FILL, st);
         clear_lower_kernel<<<n, kThreads, 0, st>>>(n, Tc, ldt);
@@ -1052,7 +1055,7 @@ size_t sign_general_workspace_bytes(int n)
 }
 
 signtri_status sign_general_run(int n, const double *A, int lda, double *S, int lds, Arena &ws, int *d_err,
-                                int *bad_index, long long *sweeps_out, cudaStream_t st)
+                                int *bad_index, long long counts_out[2], cudaStream_t st)
 {
     if (n <= 0) return SIGNTRI_OK;
     const size_t cnn = (size_t)n * n * sizeof(double2);
@@ -1061,7 +1064,7 @@ signtri_status sign_general_run(int n, const double *A, int lda, double *S, int 
     auto *Sc = static_cast<double *>(ws.take(cnn));
     if (!Qc || !Tc || !Sc) return SIGNTRI_ERR_NO_WORKSPACE;
     const size_t mark = ws.used;
-    signtri_status rs = schur_run(n, A, lda, Qc, n, Tc, n, ws, bad_index, sweeps_out, st);
+    signtri_status rs = schur_run(n, A, lda, Qc, n, Tc, n, ws, bad_index, counts_out, st);
     if (rs != SIGNTRI_OK) return rs;
     ws.used = mark;
     rs = complex_schur_run(n, Qc, n, Tc, n, Sc, n, ws, d_err, bad_index, st);

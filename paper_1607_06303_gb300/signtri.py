@@ -60,6 +60,8 @@ class Info(ctypes.Structure):
         ("resid_commute", ctypes.c_double),
         ("resid_involution", ctypes.c_double),
         ("bad_index", ctypes.c_int),
+        ("qr_sweeps", ctypes.c_longlong),
+        ("qr_rotations", ctypes.c_longlong),
     ]
 
     def as_dict(self):

@@ -51,6 +51,31 @@ def test_schur_paper_workload(gpu_lib, n):
     _check_schur(A, Q, T)
 
 
+def test_schur_sweep_counts(gpu_lib):
+    """signtri_info's QR counts: none for a matrix that is already
+    triangular (every subdiagonal entry is 0, so each eigenvalue deflates at
+    once); for Section 6's matrices at least one sweep per four eigenvalues and
+    fewer than ten per eigenvalue (about three is usual), each sweep 1 to
+    n - 1 rotations."""
+    import torch
+    T = make_T(40, 0.5, seed=3)
+    _schur(gpu_lib, T)
+    info = gpu_lib.signtri_get_info()
+    assert info.qr_sweeps == 0 and info.qr_rotations == 0
+    for n in (64, 200):
+        A = make_A(n, seed=n)
+        _schur(gpu_lib, A)
+        info = gpu_lib.signtri_get_info()
+        assert n // 4 <= info.qr_sweeps < 10 * n
+        assert info.qr_sweeps <= info.qr_rotations <= (n - 1) * info.qr_sweeps
+        sweeps = info.qr_sweeps
+        Ad = gpu_lib.to_device(A)
+        St = torch.empty_like(Ad)
+        gpu_lib.sign_general(Ad, out=St)
+        torch.cuda.synchronize()
+        assert gpu_lib.signtri_get_info().qr_sweeps == sweeps   # the same decomposition
+
+
 def test_schur_special_matrices(gpu_lib):
     rng = np.random.Generator(np.random.PCG64(5))
     cases = {
