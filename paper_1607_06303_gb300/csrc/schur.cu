@@ -33,8 +33,9 @@
 //     other SMs applies the logged rotations to the columns right of each
 //     sweep's window and to Q, on a second stream while the next launch
 //     runs, and the host relaunches until the window is empty.
-//     The chain of rotations bounds the stage: about 3 sweeps per eigenvalue,
-//     ~1.25 n^2 rotations for n eigenvalues, each a few thousand cycles of
+//     The chain of rotations bounds the stage: about 3 sweeps per eigenvalue
+//     (4 counting each bulge's), ~1.9 n^2 rotations for n eigenvalues in
+//     ~0.9 n^2 dependent steps (n = 1024), each a few thousand cycles of
 //     float64 latency and a barrier -- the decomposition is the
 //     general-matrix front end, not a tuned hot path.
 //
